@@ -1,0 +1,292 @@
+"""Pins of the oracle's physics step against closed forms, textbook results
+and conservation laws (CPU only).
+
+Each test targets a mistake that would survive a self-comparison: a wrong
+sign or index in the quaternion/rotation formulas, a dropped r x P term in
+the impulse, a wrong effective mass, a mis-ordered integrator.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_01352_b300 import scene as S
+
+
+def _one(body, **pk):
+    p = dataclasses.replace(S.SimParams(), **pk)
+    return S.custom([body], params=p)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 3e-5)])
+def test_ballistic_closed_form(orc, prec, tol):
+    """Semi-implicit Euler with constant g: v_n = v0 + n h g and
+    x_n = x0 + n h v0 + h^2 g n(n+1)/2 (exact discrete solution)."""
+    sc = _one(dict(type="sphere", r=0.05, pos=(0.1, -0.2, 50.0), vel=(1.0, 2.0, 3.0)), substeps=4)
+    steps = 25
+    st, _, cc = orc.sim_step(sc, steps, precision=prec)
+    h = sc.params.dt / sc.params.substeps
+    n = steps * sc.params.substeps
+    g = np.array(sc.params.gravity)
+    v0 = np.array([1.0, 2.0, 3.0])
+    x0 = np.array([0.1, -0.2, 50.0], dtype=np.float32).astype(np.float64)
+    v = v0 + n * h * g
+    x = x0 + n * h * v0 + h * h * g * n * (n + 1) / 2.0
+    assert cc[0] == 0
+    np.testing.assert_allclose(st["vel"][:, 0], v, rtol=tol, atol=tol)
+    np.testing.assert_allclose(st["pos"][:, 0], x, rtol=tol, atol=tol * 50)
+
+
+def test_free_flight_energy_drift(orc):
+    """Semi-implicit Euler loses exactly m g^2 h^2 / 2 of energy per substep
+    in free flight: E_n - E_0 = -m |g|^2 h^2 n / 2."""
+    sc = _one(dict(type="box", h=(0.05, 0.07, 0.09), pos=(0.0, 0.0, 80.0), vel=(0.5, -1.0, 2.0)))
+    m = 1.0 / float(sc.inv_mass[0])
+    g = np.array(sc.params.gravity)
+    h = sc.params.dt / sc.params.substeps
+
+    def energy(st):
+        v = st["vel"][:, 0]
+        return 0.5 * m * float(v @ v) - m * float(g @ st["pos"][:, 0])
+
+    s0 = {k: v.astype(np.float64) for k, v in sc.state().items()}
+    st, _, _ = orc.sim_step(sc, 30, state=s0, precision="f64")
+    n = 30 * sc.params.substeps
+    assert energy(st) - energy(s0) == pytest.approx(-0.5 * m * float(g @ g) * h * h * n, rel=1e-7)
+
+
+@pytest.mark.parametrize("body", [
+    dict(type="sphere", r=0.08, pos=(0.0, 0.0, 10.0), angvel=(0.0, 0.0, 7.0)),
+    dict(type="box", h=(0.03, 0.06, 0.1), pos=(0.0, 0.0, 10.0), angvel=(0.0, 0.0, -5.0)),
+])
+def test_rotation_angle_closed_form(orc, body):
+    """With omega along z and no torque, each substep rotates the quaternion
+    by exactly 2 atan(h w / 2) (first-order update then renormalise)."""
+    sc = _one(body, gravity=(0.0, 0.0, 0.0))
+    steps = 40
+    st, _, _ = orc.sim_step(sc, steps, precision="f64")
+    w = body["angvel"][2]
+    h = sc.params.dt / sc.params.substeps
+    ang = 2 * steps * sc.params.substeps * math.atan(h * w / 2)
+    q = st["quat"][:, 0]
+    np.testing.assert_allclose(q, [math.cos(ang / 2), 0, 0, math.sin(ang / 2)], atol=1e-12)
+    np.testing.assert_allclose(st["angvel"][:, 0], body["angvel"], atol=0)
+
+
+def test_resting_sphere_stays(orc):
+    """A sphere touching the plane at rest: the normal impulse cancels
+    gravity every substep, no friction acts, and it stays put."""
+    r = 0.07
+    sc = _one(dict(type="sphere", r=r, pos=(0.2, 0.1, r)))
+    st, _, cc = orc.sim_step(sc, 1000)
+    assert cc[0] == 1
+    assert abs(float(st["pos"][2, 0]) - r) < 1e-5
+    assert np.abs(st["vel"][:, 0]).max() < 1e-5
+    assert np.abs(st["pos"][:2, 0] - [0.2, 0.1]).max() < 1e-7
+    assert np.abs(st["angvel"][:, 0]).max() == 0.0
+
+
+def test_resting_cube_symmetry(orc):
+    """A cube face-down on the plane: the four corner contacts are symmetric
+    and their torques cancel exactly.  With mass splitting each corner sees
+    k_n = 4 (1/m + 3/m) = 16/m, so every Jacobi iteration removes a quarter
+    of the remaining approach speed: after one substep of K iterations
+    v_z = -(3/4)^K h g."""
+    a = 0.05
+    sc = _one(dict(type="box", h=(a, a, a), pos=(0.0, 0.0, a)), substeps=1)
+    st, _, cc = orc.sim_step(sc, 1, precision="f64")
+    assert cc[0] == 4
+    assert np.abs(st["angvel"][:, 0]).max() == 0.0
+    h = sc.params.dt
+    K = sc.params.iterations
+    assert st["vel"][2, 0] == pytest.approx(-(0.75 ** K) * h * 9.81, rel=1e-6)
+    assert st["vel"][0, 0] == 0.0 and st["vel"][1, 0] == 0.0
+    sc = _one(dict(type="box", h=(a, a, a), pos=(0.0, 0.0, a)))
+    # the remaining approach speed lets it sink until the position bias,
+    # which acts only beyond the allowed penetration (slop), holds it
+    st, _, _ = orc.sim_step(sc, 1000)
+    assert float(st["pos"][2, 0]) == pytest.approx(a - sc.params.slop, abs=5e-5)
+    assert abs(float(st["vel"][2, 0])) < 1e-5
+    assert np.abs(st["angvel"][:, 0]).max() == 0.0
+
+
+def test_sliding_sphere_rolls_at_five_sevenths(orc):
+    """Textbook: a solid sphere launched sliding without spin on a rough
+    plane ends up rolling at 5/7 of its initial speed, with w r = v."""
+    r = 0.08
+    v0 = 2.0
+    sc = _one(dict(type="sphere", r=r, pos=(0.0, 0.0, r), vel=(v0, 0.0, 0.0)))
+    st, _, _ = orc.sim_step(sc, 240, precision="f64")
+    vx = st["vel"][0, 0]
+    wy = st["angvel"][1, 0]
+    assert vx == pytest.approx(5.0 / 7.0 * v0, rel=2e-3)
+    assert wy * r == pytest.approx(vx, rel=2e-3)
+
+
+def test_sliding_box_stopping_distance(orc):
+    """A cube sliding face-down decelerates at mu g: it stops after
+    v0^2 / (2 mu g)."""
+    a = 0.05
+    v0 = 1.0
+    sc = _one(dict(type="box", h=(a, a, a), pos=(0.0, 0.0, a), vel=(v0, 0.0, 0.0)))
+    st, _, _ = orc.sim_step(sc, 240, precision="f64")
+    mu, g = sc.params.friction, 9.81
+    assert abs(st["vel"][0, 0]) < 2e-3  # stopped (from 1 m/s)
+    assert st["pos"][0, 0] == pytest.approx(v0 * v0 / (2 * mu * g), rel=0.03)
+
+
+def _sphere_cloud(n, seed, spread=0.25, speed=1.0):
+    rng = np.random.default_rng(seed)
+    bodies = []
+    for i in range(n):
+        bodies.append(dict(type="sphere", r=float(rng.uniform(0.05, 0.1)),
+                           pos=tuple(rng.uniform(-spread, spread, 3) + [0, 0, 5.0]),
+                           vel=tuple(rng.uniform(-speed, speed, 3)),
+                           angvel=tuple(rng.uniform(-3, 3, 3))))
+    return bodies
+
+
+def test_momentum_conservation_pairs(orc):
+    """No gravity, no plane: pair impulses are equal and opposite at a common
+    point, so linear momentum and (for spheres, whose world inertia does not
+    rotate) angular momentum about the origin are conserved."""
+    p = dataclasses.replace(S.SimParams(), gravity=(0.0, 0.0, 0.0), plane=0)
+    sc = S.custom(_sphere_cloud(12, 3), params=p)
+    m = 1.0 / sc.inv_mass.astype(np.float64)
+    I = 1.0 / sc.inv_inertia.astype(np.float64)
+
+    def moments(st):
+        P = (m * st["vel"]).sum(1)
+        L = (I * st["angvel"]).sum(1) + (m * np.cross(st["pos"].T, st["vel"].T).T).sum(1)
+        return P, L
+
+    s0 = {k: v.astype(np.float64) for k, v in sc.state().items()}
+    P0, L0 = moments(s0)
+    st, _, _ = orc.sim_step(sc, 30, state=s0, precision="f64")
+    st1, _, cc = orc.sim_step(sc, 1, state=s0, precision="f64")
+    assert cc[0] > 0  # the cloud is in contact
+    P1, L1 = moments(st)
+    np.testing.assert_allclose(P1, P0, atol=1e-12)
+    np.testing.assert_allclose(L1, L0, atol=1e-12)
+    # and something did happen
+    assert np.abs(st["vel"] - s0["vel"]).max() > 1e-3
+
+
+def test_head_on_inelastic(orc):
+    """Equal spheres meeting head on with e = 0 stop along the normal."""
+    p = dataclasses.replace(S.SimParams(), gravity=(0.0, 0.0, 0.0), plane=0)
+    sc = S.custom([dict(type="sphere", r=0.05, pos=(-0.06, 0, 1), vel=(1, 0, 0)),
+                   dict(type="sphere", r=0.05, pos=(0.06, 0, 1), vel=(-1, 0, 0))], params=p)
+    st, _, _ = orc.sim_step(sc, 20, precision="f64")
+    np.testing.assert_allclose(st["vel"], 0.0, atol=1e-9)
+    assert st["pos"][0, 1] - st["pos"][0, 0] == pytest.approx(0.1, abs=2e-3)
+
+
+def test_mirror_symmetry(orc):
+    """A scene mirrored in x stays mirrored (f64)."""
+    p = dataclasses.replace(S.SimParams(), gravity=(0.0, 0.0, -9.81))
+    sc = S.custom([dict(type="sphere", r=0.06, pos=(-0.1, 0.0, 0.3), vel=(0.5, 0, 0)),
+                   dict(type="sphere", r=0.06, pos=(0.1, 0.0, 0.3), vel=(-0.5, 0, 0)),
+                   dict(type="sphere", r=0.05, pos=(0.0, 0.0, 0.06))], params=p)
+    st, _, _ = orc.sim_step(sc, 60, precision="f64")
+    np.testing.assert_allclose(st["pos"][0, 0], -st["pos"][0, 1], atol=1e-12)
+    np.testing.assert_allclose(st["pos"][2, 0], st["pos"][2, 1], atol=1e-12)
+    assert abs(st["pos"][0, 2]) < 1e-12
+
+
+def _rotmat(q):
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = q
+    return Rotation.from_quat([x, y, z, w]).as_matrix()
+
+
+def test_box_plane_corners_match_scipy_rotation(orc):
+    """Box-plane contacts are the corners below the margin, in sign order,
+    at positions given by an independent rotation (scipy)."""
+    q = np.array([0.9, 0.2, -0.3, 0.25])
+    q /= np.linalg.norm(q)
+    h = np.array([0.04, 0.06, 0.08])
+    sc = S.custom([dict(type="box", h=tuple(h), pos=(0.1, 0.2, 0.075), quat=tuple(q))])
+    c = orc.contacts(sc, 0)
+    R = _rotmat(sc.quat[:, 0].astype(np.float64))
+    exp = []
+    for k in range(8):
+        s = np.array([1 if k & 1 else -1, 1 if k & 2 else -1, 1 if k & 4 else -1])
+        w = R @ (s * h) + sc.pos[:, 0]
+        if w[2] < sc.params.margin:
+            exp.append(w)
+    assert c["count"] == len(exp) > 0
+    np.testing.assert_allclose(c["p"], np.array(exp), atol=2e-6)
+    np.testing.assert_allclose(c["d"], np.array(exp)[:, 2], atol=2e-6)
+    assert (c["b"] == -1).all() and (c["n"] == [0, 0, 1]).all()
+
+
+def test_sphere_box_contact_distance(orc):
+    """Sphere outside a rotated box: the signed distance is the distance from
+    the sphere centre to the box (found by dense sampling of the box) minus r;
+    the normal points from the box to the sphere."""
+    q = np.array([0.8, 0.1, 0.5, -0.3])
+    q /= np.linalg.norm(q)
+    h = np.array([0.05, 0.03, 0.07])
+    pb = np.array([0.0, 0.0, 1.0])
+    ps = np.array([0.09, 0.02, 1.05])
+    r = 0.04
+    p = dataclasses.replace(S.SimParams(), plane=0, margin=0.05)
+    sc = S.custom([dict(type="sphere", r=r, pos=tuple(ps)),
+                   dict(type="box", h=tuple(h), pos=tuple(pb), quat=tuple(q))], params=p)
+    c = orc.contacts(sc, 0)
+    assert c["count"] == 1 and c["a"][0] == 0 and c["b"][0] == 1
+    R = _rotmat(sc.quat[:, 1].astype(np.float64))
+    g = np.linspace(-1, 1, 81)
+    X, Y, Z = np.meshgrid(g * h[0], g * h[1], g * h[2], indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1) @ R.T + sc.pos[:, 1]
+    dist = np.sqrt(((pts - sc.pos[:, 0]) ** 2).sum(1))
+    k = dist.argmin()
+    assert c["d"][0] == pytest.approx(dist[k] - r, abs=3e-4)
+    nexp = (sc.pos[:, 0] - pts[k]) / dist[k]
+    assert float(c["n"][0] @ nexp) > 0.99
+
+
+def test_box_on_box_face_contacts(orc):
+    """An axis-aligned box resting on a larger one: the four bottom corners
+    of the top box lie within the lower box's top face, with n = +z (from
+    the lower body B to the upper body A... here A = 0 is the upper box)."""
+    p = dataclasses.replace(S.SimParams(), plane=0)
+    gap = 0.004
+    sc = S.custom([dict(type="box", h=(0.03, 0.03, 0.03), pos=(0.01, -0.02, 1.0 + 0.05 + 0.03 + gap)),
+                   dict(type="box", h=(0.1, 0.1, 0.05), pos=(0.0, 0.0, 1.0))], params=p)
+    c = orc.contacts(sc, 0)
+    assert c["count"] == 4
+    assert (c["a"] == 0).all() and (c["b"] == 1).all()
+    np.testing.assert_allclose(c["n"], np.tile([0, 0, 1.0], (4, 1)), atol=1e-6)
+    np.testing.assert_allclose(c["d"], gap, atol=1e-6)
+    # sign order: corners (-,-,-), (+,-,-), (-,+,-), (+,+,-)
+    np.testing.assert_allclose(c["p"][:, 0], [-0.02, 0.04, -0.02, 0.04], atol=1e-6)
+    np.testing.assert_allclose(c["p"][:, 1], [-0.05, -0.05, 0.01, 0.01], atol=1e-6)
+
+
+def test_canonical_order_and_overflow(orc):
+    """Plane contacts come first by body, then pairs (i, j) in order; with a
+    capacity of one contact per body the list is truncated and flagged."""
+    bodies = [dict(type="sphere", r=0.05, pos=(0.0, 0.0, 0.05)),
+              dict(type="sphere", r=0.05, pos=(0.095, 0.0, 0.05)),
+              dict(type="sphere", r=0.05, pos=(0.19, 0.0, 0.05))]
+    sc = S.custom(bodies)
+    c = orc.contacts(sc, 0)
+    assert list(zip(c["a"], c["b"])) == [(0, -1), (1, -1), (2, -1), (0, 1), (1, 2)]
+    p = dataclasses.replace(S.SimParams(), max_contacts_per_body=1)
+    sc2 = S.custom(bodies, params=p)
+    _, flags, cc = orc.sim_step(sc2, 1)
+    assert flags[0] & 1 and cc[0] == 3
+
+
+def test_f32_tracks_f64_on_cfg1(orc):
+    """The float step stays within float rounding of the double step over a
+    short horizon of a contact-rich batch (no discrete contact decision
+    flips in this window)."""
+    sc = S.cfg1(4)
+    s32, _, _ = orc.sim_step(sc, 5, precision="f32")
+    s64, _, _ = orc.sim_step(sc, 5, precision="f64")
+    for k in ("pos", "vel", "quat"):
+        np.testing.assert_allclose(s32[k], s64[k], rtol=1e-4, atol=1e-5)

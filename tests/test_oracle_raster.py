@@ -1,0 +1,249 @@
+"""Pins of the oracle's rasteriser and camera render (CPU only).
+
+The rasteriser is checked against geometry it must reproduce exactly
+(rectangle pixel counts, a tiling mesh covered exactly once), against an
+independent exact-rational barycentric inside test with its own top/left
+edge definition, and the render against closed forms for the ground plane.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2605_01352_b300 import scene as S
+
+FX = 256
+
+
+def _front(tri):
+    """Reorder a triangle (3 x 2 fixed-point) so that it is counter-clockwise
+    on screen as seen by the camera (clockwise in y-down coordinates)."""
+    (x0, y0), (x1, y1), (x2, y2) = tri
+    a = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0)
+    return tri if a < 0 else [tri[0], tri[2], tri[1]]
+
+
+def _rect(x0, y0, x1, y1):
+    return [_front([(x0, y0), (x1, y0), (x1, y1)]), _front([(x0, y0), (x1, y1), (x0, y1)])]
+
+
+@pytest.mark.parametrize("off", [0, 128])
+def test_rectangle_pixel_counts(orc, off):
+    """An axis-aligned rectangle [x0, x1) x [y0, y1) covers exactly
+    (x1 - x0)(y1 - y0) pixels, whether its corners sit on pixel corners or
+    on pixel centres (left/top edges in, right/bottom edges out)."""
+    rng = np.random.default_rng(1)
+    W, H = 40, 24
+    for _ in range(20):
+        x0, x1 = sorted(rng.choice(W + 1, 2, replace=False))
+        y0, y1 = sorted(rng.choice(H + 1, 2, replace=False))
+        tris = _rect(FX * x0 + off, FX * y0 + off, FX * x1 + off, FX * y1 + off)
+        tid, dep, cnt = orc.raster_screen_tris(np.array(tris), np.ones((2, 3)), W, H, count=True)
+        assert cnt.max() <= 1
+        assert int((cnt == 1).sum()) == (x1 - x0) * (y1 - y0)
+        covered = np.argwhere(cnt == 1)
+        ys, xs = covered[:, 0], covered[:, 1]
+        assert xs.min() == x0 and xs.max() == x1 - 1 and ys.min() == y0 and ys.max() == y1 - 1
+
+
+def test_back_faces_and_degenerates_are_not_drawn(orc):
+    tri = _front([(0, 0), (FX * 10, 0), (0, FX * 10)])
+    back = [tri[0], tri[2], tri[1]]
+    line = [(0, 0), (FX * 5, FX * 5), (FX * 10, FX * 10)]
+    tid, _, cnt = orc.raster_screen_tris(np.array([back, line]), np.ones((2, 3)), 16, 16, count=True)
+    assert cnt.sum() == 0 and (tid == 0xFFFFFFFF).all()
+    tid, _, cnt = orc.raster_screen_tris(np.array([tri]), np.ones((1, 3)), 16, 16, count=True)
+    assert cnt.sum() > 0
+
+
+def test_jittered_grid_covers_every_pixel_once(orc):
+    """A mesh of jittered quads (two triangles each) tiling a region larger
+    than the image covers every pixel exactly once: no gaps at shared edges
+    or vertices, no double coverage (watertightness of the tie rule)."""
+    rng = np.random.default_rng(7)
+    W, H = 48, 40
+    n = 9
+    gx = np.linspace(-2 * FX, (W + 2) * FX, n + 1)
+    gy = np.linspace(-2 * FX, (H + 2) * FX, n + 1)
+    P = np.zeros((n + 1, n + 1, 2), np.int64)
+    for i in range(n + 1):
+        for j in range(n + 1):
+            jx = rng.integers(-300, 300) if 0 < i < n else 0
+            jy = rng.integers(-300, 300) if 0 < j < n else 0
+            P[i, j] = (int(gx[i]) + jx, int(gy[j]) + jy)
+    # put a few vertices exactly on pixel centres and corners to force ties
+    P[3, 3] = (FX * 10 + 128, FX * 12 + 128)
+    P[5, 4] = (FX * 25, FX * 17)
+    tris = []
+    for i in range(n):
+        for j in range(n):
+            a, b, c, d = P[i, j], P[i + 1, j], P[i + 1, j + 1], P[i, j + 1]
+            if (i + j) % 2:
+                tris += [_front([a, b, c]), _front([a, c, d])]
+            else:
+                tris += [_front([a, b, d]), _front([b, c, d])]
+    tid, _, cnt = orc.raster_screen_tris(np.array(tris), np.ones((len(tris), 3)), W, H, count=True)
+    assert (cnt == 1).all()
+
+
+def test_fan_is_watertight(orc):
+    """A triangle fan around an interior point: no pixel is covered twice,
+    and every pixel strictly inside the polygon (by an exact test) is
+    covered."""
+    rng = np.random.default_rng(11)
+    W = H = 32
+    c = (FX * 16 + 77, FX * 15 + 13)
+    k = 13
+    ang = np.sort(rng.uniform(0, 2 * np.pi, k))
+    rad = rng.uniform(6, 15, k) * FX
+    pts = [(int(c[0] + r * math.cos(a)), int(c[1] + r * math.sin(a))) for a, r in zip(ang, rad)]
+    tris = [_front([c, pts[i], pts[(i + 1) % k]]) for i in range(k)]
+    _, _, cnt = orc.raster_screen_tris(np.array(tris), np.ones((k, 3)), W, H, count=True)
+    assert cnt.max() == 1
+    # every pixel centre strictly inside one of the fan triangles is covered
+    for y in range(H):
+        for x in range(W):
+            p = (FX * x + 128, FX * y + 128)
+            for t in tris:
+                if _strictly_inside(t, p):
+                    assert cnt[y, x] == 1
+                    break
+
+
+def _bary(t, p):
+    """Exact barycentric coordinates (Fractions) of p in triangle t."""
+    (x0, y0), (x1, y1), (x2, y2) = [(Fraction(int(a)), Fraction(int(b))) for a, b in t]
+    px, py = Fraction(int(p[0])), Fraction(int(p[1]))
+    det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0)
+    l1 = ((px - x0) * (y2 - y0) - (x2 - x0) * (py - y0)) / det
+    l2 = ((x1 - x0) * (py - y0) - (px - x0) * (y1 - y0)) / det
+    return (1 - l1 - l2, l1, l2)
+
+
+def _strictly_inside(t, p):
+    return all(l > 0 for l in _bary(t, p))
+
+
+def _owns_edge(t, i):
+    """Top-left ownership of the edge opposite vertex i, from geometry: a
+    horizontal edge is owned iff the triangle lies below it (y down); any
+    other edge is owned iff the triangle lies to its right."""
+    P, Q, R = t[(i + 1) % 3], t[(i + 2) % 3], t[i]
+    if P[1] == Q[1]:
+        return R[1] > P[1]
+    xl = Fraction(int(P[0])) + Fraction(int(R[1] - P[1]) * int(Q[0] - P[0]), int(Q[1] - P[1]))
+    return R[0] > xl
+
+
+def test_brute_force_barycentric(orc):
+    """On small images, a pixel is covered iff its exact barycentric
+    coordinates are all positive, or zero on an owned (top/left) edge; the
+    depth is the perspective-correct interpolation 1 / sum(l_i / z_i)
+    (computed in double) within 1e-6 relative."""
+    rng = np.random.default_rng(5)
+    for trial in range(60):
+        W, H = int(rng.integers(8, 17)), int(rng.integers(8, 17))
+        # vertices on a coarse sub-pixel grid so that edge ties occur often
+        q = int(rng.choice([1, 64, 128]))
+        v = rng.integers(-3 * FX // q, (W + 3) * FX // q, (3, 2)) * q
+        t = _front([tuple(int(a) for a in r) for r in v])
+        z = rng.uniform(0.5, 5.0, 3)
+        tid, dep, cnt = orc.raster_screen_tris(np.array([t]), z[None, :], W, H, count=True)
+        area = (t[1][0] - t[0][0]) * (t[2][1] - t[0][1]) - (t[1][1] - t[0][1]) * (t[2][0] - t[0][0])
+        z32 = z.astype(np.float32).astype(np.float64)
+        for y in range(H):
+            for x in range(W):
+                p = (FX * x + 128, FX * y + 128)
+                if area == 0:
+                    exp = False
+                else:
+                    lam = _bary(t, p)
+                    exp = all(l > 0 or (l == 0 and _owns_edge(t, i)) for i, l in enumerate(lam))
+                assert bool(cnt[y, x]) == exp, (trial, x, y)
+                if exp:
+                    zz = 1.0 / sum(float(l) / zi for l, zi in zip(lam, z32))
+                    assert dep[y, x] == pytest.approx(zz, rel=1e-6)
+
+
+def test_depth_order_and_ties(orc):
+    """The nearer triangle wins; at equal depth the lower id wins."""
+    a = _rect(0, 0, FX * 8, FX * 8)
+    tris = np.array(a + a + a)
+    z = np.array([[3.0] * 3, [3.0] * 3, [2.0] * 3, [2.0] * 3, [2.0] * 3, [2.0] * 3])
+    tid, dep, _ = orc.raster_screen_tris(tris, z, 8, 8)
+    assert set(np.unique(tid)) == {2, 3}
+    assert (dep == np.float32(2.0)).all()
+
+
+def _ground_only(res=64, fov=60.0, eye=(0.0, -2.5, 1.5), target=(0.0, 0.0, 0.4)):
+    sc = S.custom([dict(type="sphere", r=0.05, pos=(0.0, 0.0, -5.0))], res=res,
+                  cams=[dict(eye=eye, target=target, fov=fov)])
+    return sc
+
+
+def test_ground_depth_and_colour_closed_form(orc):
+    """Ground pixels: the depth is the view depth of the ray/plane
+    intersection, -eye_z / d_z for the pixel-centre ray d = f + a r - b u;
+    the colour is the albedo times 0.2 + 0.8 max(0, n . L) with n = +z."""
+    sc = _ground_only()
+    rgb, dep, tid, flags = orc.render(sc)
+    W = H = 64
+    eye, r, u, f = (sc.cam_eye[0].astype(np.float64), sc.cam_right[0].astype(np.float64),
+                    sc.cam_up[0].astype(np.float64), sc.cam_fwd[0].astype(np.float64))
+    fpy = float(sc.cam_fpy[0])
+    g = tid.reshape(H, W)
+    d = dep.reshape(H, W)
+    hit = 0
+    for y in range(H):
+        for x in range(W):
+            a = (x + 0.5 - W / 2) / fpy
+            b = (y + 0.5 - H / 2) / fpy
+            ray = f + a * r - b * u
+            if ray[2] >= 0:
+                continue
+            t = -eye[2] / ray[2]
+            wpt = eye + t * ray
+            if abs(wpt[0]) < 1.49 and abs(wpt[1]) < 1.49:
+                assert g[y, x] in (0, 1)
+                assert d[y, x] == pytest.approx(t, rel=2e-4)
+                hit += 1
+            elif abs(wpt[0]) > 1.51 or abs(wpt[1]) > 1.51:
+                assert g[y, x] == 0xFFFFFFFF and d[y, x] == 0.0
+    assert hit > 1000
+    L = sc.light.astype(np.float64)
+    I = 0.2 + 0.8 * max(0.0, L[2])
+    exp = int(128 * I + 0.5)
+    cols = rgb[(tid == 0) | (tid == 1)]
+    assert np.abs(cols.astype(int) - exp).max() <= 1
+    assert (rgb[tid == 0xFFFFFFFF] == 0).all()
+
+
+def test_sphere_silhouette_area(orc):
+    """A sphere straight ahead covers about the area of its projected disc:
+    between the discs of the icosphere's inscribed and circumscribed radii
+    (plus a one-pixel boundary band)."""
+    r = 0.3
+    D = 2.0
+    sc = S.custom([dict(type="sphere", r=r, pos=(0.0, 0.0, 1.0))], res=64,
+                  cams=[dict(eye=(0.0, -D, 1.0), target=(0.0, 0.0, 1.0), fov=60.0)])
+    rgb, dep, tid, _ = orc.render(sc)
+    fpy = float(sc.cam_fpy[0])
+    body = int(((tid != 0xFFFFFFFF) & (tid >= 2)).sum())
+    V, T = S.icosphere(1)
+    c = V[T].mean(1)
+    r_in = r * float(np.linalg.norm(c, axis=1).min())
+    # sphere of radius r at distance D subtends a disc of angular radius asin(r/D)
+    rad = lambda rr: fpy * math.tan(math.asin(rr / D))
+    lo, hi = math.pi * (rad(r_in) - 1) ** 2, math.pi * (rad(r) + 1) ** 2
+    assert lo <= body <= hi
+    # the nearest visible depth is D - r at the centre (within the facet error)
+    assert dep.reshape(64, 64)[32, 32] == pytest.approx(D - r, rel=0.02)
+
+
+def test_near_plane_discard(orc):
+    """A body behind the camera is discarded and flagged, not drawn."""
+    sc = S.custom([dict(type="sphere", r=0.1, pos=(0.0, -3.0, 1.5))], res=32)
+    rgb, dep, tid, flags = orc.render(sc)
+    assert flags[0] & 2
+    assert not ((tid >= 2) & (tid != 0xFFFFFFFF)).any()
