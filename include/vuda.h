@@ -1,0 +1,249 @@
+/* vuda.h -- C ABI of the co-scheduled simulate-then-render library (libvuda.so).
+ *
+ * The paper (VUDA, arxiv 2605.01352) speeds up the per-step loop of
+ * embodied-AI environments -- a physics step followed by a camera render --
+ * by letting the two phases share the GPU spatially instead of in alternating
+ * time slices.  Its application interface (Sec. 3.2, Table 1) binds a stream
+ * for co-scheduling (CUstream_bind / CUstream_unbind) and launches the two
+ * phases asynchronously (step_async / render_async) with blocking waits
+ * (wait_step / wait_render).  Sec. 3.1 gives the dependency this exploits:
+ * sim(k+1) depends only on sim(k), never on render(k).
+ *
+ * This library computes both phases itself in CUDA (sm_103a) in one context:
+ * a batched rigid-body step and a batched per-environment rasteriser, with
+ * the sim and render streams placed on disjoint SM partitions.
+ *
+ * Conventions for every entry point:
+ *  - Nothing aborts or throws across the ABI; every call returns a
+ *    vuda_status.  VUDA_ERR_CUDA carries the CUDA error text, available from
+ *    vuda_last_error().
+ *  - Host input pointers are read only during the call.  Device pointers
+ *    given by the caller (frames, forces) stay owned by the caller; the
+ *    library never frees caller memory.  The library owns all device memory
+ *    it allocates for an environment batch and frees it in vuda_env_destroy.
+ *  - Streams are cudaStream_t values passed as void*; NULL is the legacy
+ *    default stream.  Calls named *_step / *_render only enqueue work.
+ *  - Arrays called SoA are planes: pos[3][B] is x[0..B), y[0..B), z[0..B).
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef VUDA_H
+#define VUDA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VUDA_OK = 0,
+    VUDA_ERR_INVALID = 1,      /* bad argument or size */
+    VUDA_ERR_OOM = 2,          /* device allocation failed or HBM budget exceeded */
+    VUDA_ERR_CUDA = 3,         /* a CUDA call failed; see vuda_last_error() */
+    VUDA_ERR_OVERFLOW = 4,     /* a capacity was exceeded (see the env flags) */
+    VUDA_ERR_TIMEOUT = 5,      /* a bounded wait gave up */
+    VUDA_ERR_BUSY = 6,         /* resource in use (e.g. serving queue full) */
+    VUDA_ERR_UNSUPPORTED = 7   /* feature not available on this device/driver */
+} vuda_status;
+
+/* Per-environment status bits (vuda_env_status).  They accumulate until
+ * cleared and never stop the step: the work degrades deterministically. */
+#define VUDA_FLAG_CONTACT_OVERFLOW 0x1u /* contacts beyond max_contacts_per_body * N dropped */
+#define VUDA_FLAG_NEAR_DISCARD     0x2u /* a triangle with a vertex before the near plane was skipped */
+#define VUDA_FLAG_GUARD_DISCARD    0x4u /* a triangle beyond the 2^14 px guard band was skipped */
+#define VUDA_FLAG_MESH_CAPACITY    0x8u /* a mesh larger than the render vertex cache was skipped */
+#define VUDA_FLAG_TIMEOUT          0x10u /* a bounded device wait gave up */
+
+typedef void* vuda_stream_t;        /* cudaStream_t */
+typedef struct vuda_env* vuda_env_t;
+
+/* Physics step parameters.  A step of length dt is split into `substeps`
+ * substeps of h = dt / substeps; each substep integrates velocities, builds
+ * contacts, runs `iterations` Jacobi iterations and integrates positions. */
+typedef struct {
+    float dt;
+    int32_t substeps;
+    int32_t iterations;
+    float gravity[3];
+    float restitution;            /* applied to penetrating contacts approaching faster than the threshold */
+    float restitution_threshold;
+    float friction;               /* Coulomb coefficient (disk cone) */
+    float baumgarte;              /* position bias factor beyond the slop */
+    float slop;                   /* allowed penetration (m) */
+    float margin;                 /* speculative contact distance (m) */
+    float jacobi_omega;           /* relaxation of the mass-split Jacobi update */
+    int32_t plane;                /* 1: static ground plane z = 0 */
+    int32_t max_contacts_per_body;/* contact capacity per env = this * bodies */
+} vuda_sim_params;
+
+/* Host description of a batch (all arrays host memory, read during
+ * vuda_env_create only).  E environments, B = body_off[E] bodies,
+ * C = cam_off[E] cameras, M meshes.
+ *   body_off[E+1]           CSR: env e owns bodies [body_off[e], body_off[e+1])
+ *   pos[3][B] quat[4][B]    pose (quat = w, x, y, z, unit)
+ *   vel[3][B] angvel[3][B]  linear / angular velocity (world frame)
+ *   shape_type[B]           0 sphere, 1 box, 2 hull (sphere proxy of radius dims[0])
+ *   shape_dims[3][B]        sphere/hull: (r, -, -); box: half extents
+ *   inv_mass[B] inv_inertia[3][B]   body-frame principal inverse inertia
+ *   mesh_id[B] mesh_scale[3][B] albedo[B] (r | g<<8 | b<<16)
+ *   mesh_vert_off[M+1] mesh_verts[V][3]  mesh_tri_off[M+1] mesh_tris[T][3] (mesh-local,
+ *                           counter-clockwise seen from outside)
+ *   ground_mesh             mesh drawn once per env in world coordinates (ids 0..)
+ *   cam_off[E+1] cam_w[C] cam_h[C] cam_eye/right/up/fwd[C][3] cam_fpy[C]  pinhole cameras
+ *   light[3]                unit direction towards the light */
+typedef struct {
+    int32_t num_envs;
+    const int32_t* body_off;
+    const float* pos;
+    const float* quat;
+    const float* vel;
+    const float* angvel;
+    const uint8_t* shape_type;
+    const float* shape_dims;
+    const float* inv_mass;
+    const float* inv_inertia;
+    const int32_t* mesh_id;
+    const float* mesh_scale;
+    const uint32_t* albedo;
+    int32_t num_meshes;
+    const int32_t* mesh_vert_off;
+    const float* mesh_verts;
+    const int32_t* mesh_tri_off;
+    const int32_t* mesh_tris;
+    int32_t ground_mesh;
+    uint32_t ground_albedo;
+    const int32_t* cam_off;
+    const int32_t* cam_w;
+    const int32_t* cam_h;
+    const float* cam_eye;
+    const float* cam_right;
+    const float* cam_up;
+    const float* cam_fwd;
+    const float* cam_fpy;
+    float light[3];
+} vuda_scene;
+
+/* Creation options.  Zero-initialised options are valid (defaults). */
+typedef struct {
+    int64_t hbm_budget_bytes;     /* 0: no limit; else VUDA_ERR_OOM if the batch needs more */
+    int32_t device;               /* CUDA device ordinal (default 0) */
+    int32_t render_band_rows;     /* rows per render work item (0: auto) */
+    int32_t phys_smem_bytes;      /* shared memory per physics env (0: auto) */
+} vuda_env_opts;
+
+/* Sizes of a created batch. */
+typedef struct {
+    int32_t num_envs, num_bodies, num_cams, max_bodies;
+    int64_t num_pixels;           /* total pixels over all cameras */
+    int64_t num_tris;             /* total triangles drawn per step over all envs (per camera) */
+    int64_t device_bytes;         /* device memory held by the batch */
+    int64_t steps_enqueued;       /* physics steps enqueued so far */
+} vuda_env_info;
+
+/* Caller-owned device output buffers, concatenated per camera in cam order
+ * (pixel p of camera c at cam_pix_off[c] + y * W + x):
+ *   rgb[P][3] u8, depth[P] f32 (view depth, 0 = background),
+ *   triid[P] u32 (env-local triangle id, 0xFFFFFFFF = background; may be NULL). */
+typedef struct {
+    uint8_t* rgb;
+    float* depth;
+    uint32_t* triid;
+} vuda_frame;
+
+/* Host state (SoA planes of length B); used by get/set. */
+typedef struct {
+    float* pos;
+    float* quat;
+    float* vel;
+    float* angvel;
+} vuda_state;
+
+const char* vuda_status_str(vuda_status s);
+/* Text of the last error raised on this thread (empty if none). */
+const char* vuda_last_error(void);
+int32_t vuda_abi_version(void);
+
+/* Create a batch: validates the description (VUDA_ERR_INVALID), checks the
+ * HBM budget (VUDA_ERR_OOM), uploads state, meshes and cameras.  Synchronous.
+ * Problem statement: Sec. 3.1 (a batch of environments stepped and rendered
+ * in a loop). */
+vuda_status vuda_env_create(const vuda_scene* scene, const vuda_sim_params* params,
+                            const vuda_env_opts* opts, vuda_env_t* out);
+vuda_status vuda_env_destroy(vuda_env_t env);
+vuda_status vuda_env_info_get(vuda_env_t env, vuda_env_info* out);
+/* Per-camera first-pixel offsets (host array of num_cams + 1). */
+vuda_status vuda_env_cam_pix_off(vuda_env_t env, int64_t* out);
+
+/* Enqueue nsteps physics steps on `stream` (the paper's step_async, Table 1).
+ * force: optional device array [3][B] of world forces held over each step
+ * (NULL: none).  After each step the body poses are also written to pose
+ * slot (step index mod 2) for the renderer.  Async; returns after enqueue. */
+vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vuda_stream_t stream);
+
+/* Enqueue the render of every camera from pose slot `pose_slot` (0 or 1;
+ * -1 = the slot of the last enqueued step) into `frame` (the paper's
+ * render_async, Table 1).  Async. */
+vuda_status vuda_render(vuda_env_t env, int32_t pose_slot, const vuda_frame* frame, vuda_stream_t stream);
+
+/* Co-scheduling (the paper's CUstream_bind, Table 1 / Sec. 3.2):
+ * mode VUDA_COSCHED_GREEN puts a sim stream and a render stream on disjoint
+ * SM partitions (green contexts, sim_sms SMs for sim, the rest for render);
+ * VUDA_COSCHED_STREAMS uses two ordinary streams that share all SMs.
+ * The streams are owned by the library and returned for the caller to
+ * enqueue on.  vuda_coschedule_reset (CUstream_unbind) destroys them. */
+#define VUDA_COSCHED_STREAMS 1
+#define VUDA_COSCHED_GREEN 2
+typedef struct {
+    int32_t mode;
+    int32_t sim_sms;              /* SMs for the sim partition (0: half); rounded to the device granularity */
+} vuda_cosched_opts;
+typedef struct {
+    int32_t mode;
+    int32_t sim_sms, render_sms;  /* SMs actually provisioned (0 if not partitioned) */
+    int32_t sm_granularity;       /* partition alignment reported by the driver */
+} vuda_cosched_info;
+vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_stream_t* sim_stream,
+                            vuda_stream_t* render_stream, vuda_cosched_info* info);
+vuda_status vuda_coschedule_reset(vuda_env_t env);
+
+/* Run nsteps steps of the loop and block until done.  Co-scheduled
+ * (after vuda_coschedule): sim(t+1) is enqueued on the sim stream as soon as
+ * sim(t) is, render(t) on the render stream after sim(t) (Sec. 3.1 inter-step
+ * pipelining); frames alternate between ring[0] and ring[1] and pose slots
+ * alternate too, guarded by events.  Not co-scheduled: sim then render on
+ * `stream`.  step_ms (optional, host [nsteps]): per-step latency from the
+ * start of sim(t) to the end of render(t), from device events. */
+vuda_status vuda_pipeline_run(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
+                              float* step_ms);
+
+/* Block until all work enqueued by this handle on the sim (phase 0) or
+ * render (phase 1) stream has finished (wait_step / wait_render, Table 1). */
+vuda_status vuda_wait(vuda_env_t env, int32_t phase);
+
+/* Copy the state to / from host SoA arrays (synchronous). */
+vuda_status vuda_env_get_state(vuda_env_t env, const vuda_state* out);
+vuda_status vuda_env_set_state(vuda_env_t env, const vuda_state* in);
+/* Read the pose slot (pos[3][B], quat[4][B]) to host. */
+vuda_status vuda_env_get_pose(vuda_env_t env, int32_t slot, float* pos, float* quat);
+/* Write a pose slot from host arrays (used to render given poses). */
+vuda_status vuda_env_set_pose(vuda_env_t env, int32_t slot, const float* pos, const float* quat);
+
+/* Read (and optionally clear) per-env status bits into flags[E] (host, may
+ * be NULL); or_flags receives their union.  Synchronous. */
+vuda_status vuda_env_status(vuda_env_t env, uint32_t* flags, uint32_t* or_flags, int32_t clear);
+/* Number of contacts of each env at the last substep (host int32[E]). */
+vuda_status vuda_env_contact_counts(vuda_env_t env, int32_t* counts);
+
+/* Test entry point: rasterise ntri screen-space triangles with snapped 24.8
+ * fixed-point vertices xy[t][3][2] (int32) and view depths z[t][3] into a
+ * W x H image (all device pointers): triid[H][W] u32 (0xFFFFFFFF empty),
+ * depth[H][W] f32 (0 empty), count[H][W] u32 (may be NULL: number of
+ * triangles covering each pixel).  Same coverage rule and depth key as
+ * vuda_render; triangle ids are the input order.  Async on `stream`. */
+vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t ntri, int32_t W, int32_t H,
+                                    uint32_t* triid, float* depth, uint32_t* count, vuda_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VUDA_H */

@@ -1,0 +1,744 @@
+// C ABI of libvuda.so: batch creation, the two phases, co-scheduling on SM
+// partitions, the pipelined loop, state access and status (see vuda.h).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace vuda {
+
+static thread_local std::string g_err;
+void set_error(const std::string& s) { g_err = s; }
+
+}  // namespace vuda
+
+using namespace vuda;
+
+namespace {
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+            return VUDA_ERR_CUDA;                                                             \
+        }                                                                                     \
+    } while (0)
+
+vuda_status invalid(const std::string& s) {
+    set_error(s);
+    return VUDA_ERR_INVALID;
+}
+
+// ---------------------------------------------------------------------------
+// Driver entry points for green contexts (resolved at run time through the
+// runtime, so the library does not link libcuda directly).
+// ---------------------------------------------------------------------------
+struct Driver {
+    CUresult (*DeviceGet)(CUdevice*, int) = nullptr;
+    CUresult (*DeviceGetDevResource)(CUdevice, CUdevResource*, CUdevResourceType) = nullptr;
+    CUresult (*DevSmResourceSplitByCount)(CUdevResource*, unsigned*, const CUdevResource*, CUdevResource*, unsigned,
+                                          unsigned) = nullptr;
+    CUresult (*DevResourceGenerateDesc)(CUdevResourceDesc*, CUdevResource*, unsigned) = nullptr;
+    CUresult (*GreenCtxCreate)(CUgreenCtx*, CUdevResourceDesc, CUdevice, unsigned) = nullptr;
+    CUresult (*GreenCtxDestroy)(CUgreenCtx) = nullptr;
+    CUresult (*GreenCtxStreamCreate)(CUstream*, CUgreenCtx, unsigned, int) = nullptr;
+    CUresult (*StreamDestroy)(CUstream) = nullptr;
+    CUresult (*CtxFromGreenCtx)(CUcontext*, CUgreenCtx) = nullptr;
+    CUresult (*CtxGetCurrent)(CUcontext*) = nullptr;
+    CUresult (*CtxSetCurrent)(CUcontext) = nullptr;
+    CUresult (*GetErrorString)(CUresult, const char**) = nullptr;
+    bool ok = false;
+};
+
+template <typename F>
+bool resolve(const char* name, F& fn, unsigned ver) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, ver, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return false;
+    fn = reinterpret_cast<F>(p);
+    return true;
+}
+
+Driver& driver() {
+    static Driver d;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        d.ok = resolve("cuDeviceGet", d.DeviceGet, 12000) &&
+               resolve("cuDeviceGetDevResource", d.DeviceGetDevResource, 12040) &&
+               resolve("cuDevSmResourceSplitByCount", d.DevSmResourceSplitByCount, 12040) &&
+               resolve("cuDevResourceGenerateDesc", d.DevResourceGenerateDesc, 12040) &&
+               resolve("cuGreenCtxCreate", d.GreenCtxCreate, 12040) &&
+               resolve("cuGreenCtxDestroy", d.GreenCtxDestroy, 12040) &&
+               resolve("cuGreenCtxStreamCreate", d.GreenCtxStreamCreate, 12050) &&
+               resolve("cuStreamDestroy", d.StreamDestroy, 12000) &&
+               resolve("cuCtxFromGreenCtx", d.CtxFromGreenCtx, 12040) &&
+               resolve("cuCtxGetCurrent", d.CtxGetCurrent, 12000) &&
+               resolve("cuCtxSetCurrent", d.CtxSetCurrent, 12000) &&
+               resolve("cuGetErrorString", d.GetErrorString, 12000);
+    }
+    return d;
+}
+
+// Makes a context current for the lifetime of the object (no-op for null).
+struct ScopedCtx {
+    CUcontext prev = nullptr;
+    bool active = false;
+    explicit ScopedCtx(CUcontext c) {
+        if (!c) return;
+        Driver& d = driver();
+        if (d.CtxGetCurrent(&prev) == CUDA_SUCCESS && d.CtxSetCurrent(c) == CUDA_SUCCESS) active = true;
+    }
+    ~ScopedCtx() {
+        if (active) driver().CtxSetCurrent(prev);
+    }
+};
+
+std::string cu_err(CUresult r) {
+    const char* s = nullptr;
+    if (driver().GetErrorString) driver().GetErrorString(r, &s);
+    return s ? s : ("CUresult " + std::to_string((int)r));
+}
+
+}  // namespace
+
+struct vuda_env {
+    int device = 0;
+    DevBatch d{};
+    SimConst sc{};
+    vuda_sim_params params{};
+    int E = 0, B = 0, C = 0, max_bodies = 0, max_w = 0;
+    int64_t P = 0, T = 0;
+    int64_t bytes = 0;
+    int64_t steps = 0;
+    int phys_smem = 0;
+    int band_rows = 0;
+    int nitems = 0;
+    int32_t* item_cam = nullptr;
+    int32_t* item_y0 = nullptr;
+    std::vector<void*> allocs;
+    std::vector<int64_t> cam_pix_off;
+    // co-scheduling
+    int cos_mode = 0;
+    cudaStream_t sim_s = nullptr, ren_s = nullptr, own_s = nullptr;
+    CUgreenCtx g_sim = nullptr, g_ren = nullptr;
+    CUcontext c_sim = nullptr, c_ren = nullptr;  // green contexts as CUcontext (null otherwise)
+    vuda_cosched_info cos_info{};
+    std::vector<cudaEvent_t> ev_sim, ev_ren;      // event pools owned by each phase's context
+};
+
+namespace {
+
+template <typename T>
+vuda_status dalloc(vuda_env* env, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? VUDA_ERR_OOM : VUDA_ERR_CUDA;
+    }
+    env->allocs.push_back((void*)*p);
+    env->bytes += (int64_t)(n * sizeof(T));
+    return VUDA_OK;
+}
+
+template <typename T>
+vuda_status upload(vuda_env* env, T** p, const T* host, size_t n) {
+    vuda_status s = dalloc(env, p, n);
+    if (s != VUDA_OK) return s;
+    if (n) CK(cudaMemcpy(*p, host, n * sizeof(T), cudaMemcpyHostToDevice));
+    return VUDA_OK;
+}
+
+void free_env(vuda_env* env) {
+    for (void* p : env->allocs) cudaFree(p);
+    env->allocs.clear();
+}
+
+void destroy_events(vuda_env* env) {
+    {
+        ScopedCtx g(env->c_sim);
+        for (cudaEvent_t e : env->ev_sim) cudaEventDestroy(e);
+    }
+    {
+        ScopedCtx g(env->c_ren);
+        for (cudaEvent_t e : env->ev_ren) cudaEventDestroy(e);
+    }
+    env->ev_sim.clear();
+    env->ev_ren.clear();
+}
+
+vuda_status destroy_cosched(vuda_env* env) {
+    if (env->sim_s || env->ren_s) cudaDeviceSynchronize();
+    destroy_events(env);
+    Driver& dr = driver();
+    if (env->cos_mode == VUDA_COSCHED_GREEN) {
+        if (env->sim_s) dr.StreamDestroy((CUstream)env->sim_s);
+        if (env->ren_s) dr.StreamDestroy((CUstream)env->ren_s);
+        if (env->g_sim) dr.GreenCtxDestroy(env->g_sim);
+        if (env->g_ren) dr.GreenCtxDestroy(env->g_ren);
+    } else if (env->cos_mode == VUDA_COSCHED_STREAMS) {
+        if (env->sim_s) cudaStreamDestroy(env->sim_s);
+        if (env->ren_s) cudaStreamDestroy(env->ren_s);
+    }
+    env->sim_s = env->ren_s = nullptr;
+    env->g_sim = env->g_ren = nullptr;
+    env->c_sim = env->c_ren = nullptr;
+    env->cos_mode = 0;
+    env->cos_info = vuda_cosched_info{};
+    return VUDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t vuda_abi_version(void) { return 1; }
+
+const char* vuda_last_error(void) { return g_err.c_str(); }
+
+const char* vuda_status_str(vuda_status s) {
+    switch (s) {
+        case VUDA_OK: return "ok";
+        case VUDA_ERR_INVALID: return "invalid argument";
+        case VUDA_ERR_OOM: return "out of device memory or over the HBM budget";
+        case VUDA_ERR_CUDA: return "CUDA error";
+        case VUDA_ERR_OVERFLOW: return "capacity overflow";
+        case VUDA_ERR_TIMEOUT: return "timeout";
+        case VUDA_ERR_BUSY: return "busy";
+        case VUDA_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, const vuda_env_opts* opts,
+                            vuda_env_t* out) {
+    if (!sc || !prm || !out) return invalid("vuda_env_create: null argument");
+    *out = nullptr;
+    vuda_env_opts o{};
+    if (opts) o = *opts;
+    const int E = sc->num_envs;
+    if (E < 0) return invalid("num_envs < 0");
+    if (E > 0 && (!sc->body_off || !sc->cam_off)) return invalid("body_off/cam_off missing");
+    if (prm->substeps <= 0 || prm->iterations < 0 || prm->max_contacts_per_body <= 0 || !(prm->dt > 0.0f))
+        return invalid("bad sim params (dt > 0, substeps > 0, iterations >= 0, max_contacts_per_body > 0)");
+    if (E > 0 && sc->body_off[0] != 0) return invalid("body_off[0] != 0");
+    if (E > 0 && sc->cam_off[0] != 0) return invalid("cam_off[0] != 0");
+    int max_bodies = 0;
+    for (int e = 0; e < E; e++) {
+        int n = sc->body_off[e + 1] - sc->body_off[e];
+        if (n < 0) return invalid("body_off not non-decreasing");
+        if (sc->cam_off[e + 1] < sc->cam_off[e]) return invalid("cam_off not non-decreasing");
+        max_bodies = std::max(max_bodies, n);
+    }
+    if (max_bodies > 4096) return invalid("more than 4096 bodies in one environment");
+    if ((int64_t)prm->max_contacts_per_body * max_bodies > 32767)
+        return invalid("max_contacts_per_body * bodies must stay below 32768");
+    const int B = E ? sc->body_off[E] : 0;
+    const int C = E ? sc->cam_off[E] : 0;
+    const int M = sc->num_meshes;
+    if (B > 0 && (!sc->pos || !sc->quat || !sc->vel || !sc->angvel || !sc->shape_type || !sc->shape_dims ||
+                  !sc->inv_mass || !sc->inv_inertia || !sc->mesh_id || !sc->mesh_scale || !sc->albedo))
+        return invalid("body arrays missing");
+    if (M <= 0 || !sc->mesh_vert_off || !sc->mesh_verts || !sc->mesh_tri_off || !sc->mesh_tris)
+        return invalid("mesh library missing");
+    if (sc->ground_mesh < 0 || sc->ground_mesh >= M) return invalid("ground_mesh out of range");
+    if (sc->mesh_vert_off[0] != 0 || sc->mesh_tri_off[0] != 0) return invalid("mesh offsets must start at 0");
+    for (int m = 0; m < M; m++) {
+        int nv = sc->mesh_vert_off[m + 1] - sc->mesh_vert_off[m];
+        int nt = sc->mesh_tri_off[m + 1] - sc->mesh_tri_off[m];
+        if (nv < 0 || nt < 0) return invalid("mesh offsets not non-decreasing");
+        if (nv > render_vcap()) return invalid("a mesh has more vertices than the render vertex cache (1024)");
+        for (int t = sc->mesh_tri_off[m]; t < sc->mesh_tri_off[m + 1]; t++)
+            for (int k = 0; k < 3; k++) {
+                int v = sc->mesh_tris[3 * t + k];
+                if (v < 0 || v >= nv) return invalid("mesh triangle index out of range");
+            }
+    }
+    for (int b = 0; b < B; b++) {
+        if (sc->mesh_id[b] < 0 || sc->mesh_id[b] >= M) return invalid("mesh_id out of range");
+        if (sc->shape_type[b] > 2) return invalid("shape_type must be 0, 1 or 2");
+    }
+    int max_w = 0;
+    for (int c = 0; c < C; c++) {
+        if (sc->cam_w[c] <= 0 || sc->cam_h[c] <= 0 || sc->cam_w[c] > 4096 || sc->cam_h[c] > 4096)
+            return invalid("camera size must be in 1..4096");
+        max_w = std::max(max_w, sc->cam_w[c]);
+    }
+
+    vuda_env* env = new vuda_env();
+    env->device = o.device;
+    env->E = E; env->B = B; env->C = C; env->max_bodies = max_bodies; env->max_w = max_w;
+    env->params = *prm;
+    cudaError_t ce = cudaSetDevice(o.device);
+    if (ce != cudaSuccess) {
+        delete env;
+        set_error(std::string("cudaSetDevice: ") + cudaGetErrorString(ce));
+        return VUDA_ERR_CUDA;
+    }
+
+    // host-side tables
+    std::vector<int64_t> pix(C + 1, 0);
+    for (int c = 0; c < C; c++) pix[c + 1] = pix[c] + (int64_t)sc->cam_w[c] * sc->cam_h[c];
+    env->cam_pix_off = pix;
+    env->P = pix[C];
+    std::vector<int32_t> cam_env(C);
+    for (int e = 0; e < E; e++)
+        for (int c = sc->cam_off[e]; c < sc->cam_off[e + 1]; c++) cam_env[c] = e;
+    std::vector<float> cam_par((size_t)C * kCamWords);
+    for (int c = 0; c < C; c++) {
+        float* p = cam_par.data() + (size_t)c * kCamWords;
+        for (int k = 0; k < 3; k++) {
+            p[k] = sc->cam_eye[3 * c + k];
+            p[3 + k] = sc->cam_right[3 * c + k];
+            p[6 + k] = sc->cam_up[3 * c + k];
+            p[9 + k] = sc->cam_fwd[3 * c + k];
+        }
+        p[12] = sc->cam_fpy[c];
+    }
+    const int gm = sc->ground_mesh;
+    const int Tg = sc->mesh_tri_off[gm + 1] - sc->mesh_tri_off[gm];
+    const int Vg = sc->mesh_vert_off[gm + 1] - sc->mesh_vert_off[gm];
+    std::vector<int64_t> env_tri_base(E + 1, 0);
+    std::vector<int32_t> chunk_off(E + 1, 0), chunk_lo, chunk_hi;
+    const int vcap = render_vcap(), cbmax = render_chunk_bodies();
+    for (int e = 0; e < E; e++) {
+        int64_t t = Tg;
+        int lo = -1, nv = Vg, nb = 1;
+        for (int bi = 0; bi < sc->body_off[e + 1] - sc->body_off[e]; bi++) {
+            int m = sc->mesh_id[sc->body_off[e] + bi];
+            int bv = sc->mesh_vert_off[m + 1] - sc->mesh_vert_off[m];
+            t += sc->mesh_tri_off[m + 1] - sc->mesh_tri_off[m];
+            if (nv + bv > vcap || nb + 1 > cbmax) {
+                chunk_lo.push_back(lo);
+                chunk_hi.push_back(bi);
+                lo = bi;
+                nv = 0;
+                nb = 0;
+            }
+            nv += bv;
+            nb++;
+        }
+        chunk_lo.push_back(lo);
+        chunk_hi.push_back(sc->body_off[e + 1] - sc->body_off[e]);
+        chunk_off[e + 1] = (int32_t)chunk_lo.size();
+        env_tri_base[e + 1] = env_tri_base[e] + t;
+    }
+    env->T = E ? env_tri_base[E] : 0;
+
+    // physics shared memory and spill
+    const int mcpb = prm->max_contacts_per_body;
+    env->phys_smem = o.phys_smem_bytes > 0 ? o.phys_smem_bytes : phys_smem_bytes_default(max_bodies, mcpb);
+    std::vector<int64_t> spill_off(E + 1, 0);
+    for (int e = 0; e < E; e++)
+        spill_off[e + 1] = spill_off[e] + (int64_t)mcpb * (sc->body_off[e + 1] - sc->body_off[e]);
+    // render work items
+    int br = o.render_band_rows > 0 ? o.render_band_rows : std::max(1, 4096 / std::max(1, max_w));
+    env->band_rows = br;
+    std::vector<int32_t> item_cam, item_y0;
+    for (int c = 0; c < C; c++)
+        for (int y = 0; y < sc->cam_h[c]; y += br) {
+            item_cam.push_back(c);
+            item_y0.push_back(y);
+        }
+    env->nitems = (int)item_cam.size();
+    if (C && render_smem_for(br, max_w) > 227 * 1024) {
+        delete env;
+        return invalid("render band too large for shared memory (lower render_band_rows)");
+    }
+
+    // device memory budget
+    int64_t need = (int64_t)B * 4 * (3 + 4 + 3 + 3 + 3 + 1 + 3 + 3 + 2 * 7) + B * 1 + (int64_t)B * 4 * 2 +
+                   (int64_t)E * 12 + (int64_t)spill_off[E] * kContactWords * 4 + env->T * 4 + (int64_t)C * 80;
+    if (o.hbm_budget_bytes > 0 && need > o.hbm_budget_bytes) {
+        delete env;
+        set_error("batch needs " + std::to_string(need) + " bytes, over the HBM budget");
+        return VUDA_ERR_OOM;
+    }
+
+    DevBatch& d = env->d;
+    d.E = E; d.B = B; d.C = C;
+    vuda_status s = VUDA_OK;
+#define UP(field, type, host, n) \
+    if (s == VUDA_OK) s = upload(env, (type**)&d.field, (const type*)(host), (size_t)(n))
+    UP(body_off, int32_t, sc->body_off, E + 1);
+    UP(pos, float, sc->pos, 3 * (size_t)B);
+    UP(quat, float, sc->quat, 4 * (size_t)B);
+    UP(vel, float, sc->vel, 3 * (size_t)B);
+    UP(ang, float, sc->angvel, 3 * (size_t)B);
+    UP(type, uint8_t, sc->shape_type, B);
+    UP(dims, float, sc->shape_dims, 3 * (size_t)B);
+    UP(im, float, sc->inv_mass, B);
+    UP(ii, float, sc->inv_inertia, 3 * (size_t)B);
+    UP(mesh_id, int32_t, sc->mesh_id, B);
+    UP(scale, float, sc->mesh_scale, 3 * (size_t)B);
+    UP(albedo, uint32_t, sc->albedo, B);
+    UP(mesh_vert_off, int32_t, sc->mesh_vert_off, M + 1);
+    UP(mesh_verts, float, sc->mesh_verts, 3 * (size_t)sc->mesh_vert_off[M]);
+    UP(mesh_tri_off, int32_t, sc->mesh_tri_off, M + 1);
+    UP(mesh_tris, int32_t, sc->mesh_tris, 3 * (size_t)sc->mesh_tri_off[M]);
+    UP(cam_env, int32_t, cam_env.data(), C);
+    UP(cam_w, int32_t, sc->cam_w, C);
+    UP(cam_h, int32_t, sc->cam_h, C);
+    UP(cam_par, float, cam_par.data(), cam_par.size());
+    UP(cam_pix_off, int64_t, pix.data(), C + 1);
+    UP(env_tri_base, int64_t, env_tri_base.data(), E + 1);
+    UP(chunk_off, int32_t, chunk_off.data(), E + 1);
+    UP(chunk_lo, int32_t, chunk_lo.data(), chunk_lo.size());
+    UP(chunk_hi, int32_t, chunk_hi.data(), chunk_hi.size());
+    UP(spill_off, int64_t, spill_off.data(), E + 1);
+    if (s == VUDA_OK) s = upload(env, &env->item_cam, item_cam.data(), item_cam.size());
+    if (s == VUDA_OK) s = upload(env, &env->item_y0, item_y0.data(), item_y0.size());
+#undef UP
+    for (int k = 0; k < 2 && s == VUDA_OK; k++) {
+        s = dalloc(env, &d.pose[k], 7 * (size_t)B);
+        if (s == VUDA_OK) {
+            // both slots start at the initial pose
+            if (cudaMemcpy(d.pose[k], sc->pos, 3 * sizeof(float) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(d.pose[k] + 3 * (size_t)B, sc->quat, 4 * sizeof(float) * B, cudaMemcpyHostToDevice) !=
+                    cudaSuccess)
+                s = VUDA_ERR_CUDA;
+        }
+    }
+    if (s == VUDA_OK) s = dalloc(env, &d.flags, E);
+    if (s == VUDA_OK) s = dalloc(env, &d.ncontacts, E);
+    if (s == VUDA_OK) s = dalloc(env, &d.tri_color, (size_t)std::max<int64_t>(env->T, 1));
+    // spill area only if some env's contact capacity exceeds the shared-memory records
+    {
+        // the kernel keeps phys_contacts_in_smem() records per env in shared
+        // memory; envs whose capacity exceeds that spill the rest here
+        int64_t cap_smem = phys_contacts_in_smem(env->phys_smem, max_bodies, mcpb);
+        bool need_spill = (int64_t)mcpb * max_bodies > cap_smem;
+        if (s == VUDA_OK && need_spill)
+            s = dalloc(env, &d.spill, (size_t)std::max<int64_t>(spill_off[E], 1) * kContactWords);
+    }
+    if (s == VUDA_OK && E) {
+        if (cudaMemset(d.flags, 0, sizeof(uint32_t) * E) != cudaSuccess ||
+            cudaMemset(d.ncontacts, 0, sizeof(int32_t) * E) != cudaSuccess)
+            s = VUDA_ERR_CUDA;
+    }
+    if (s != VUDA_OK) {
+        free_env(env);
+        delete env;
+        return s;
+    }
+    d.ground_mesh = gm;
+    d.ground_albedo = sc->ground_albedo;
+    d.light[0] = sc->light[0]; d.light[1] = sc->light[1]; d.light[2] = sc->light[2];
+
+    SimConst& k = env->sc;
+    k.h = prm->dt / (float)prm->substeps;
+    k.substeps = prm->substeps;
+    k.iterations = prm->iterations;
+    for (int i = 0; i < 3; i++) k.g[i] = prm->gravity[i];
+    k.restitution = prm->restitution;
+    k.rest_thr = prm->restitution_threshold;
+    k.mu = prm->friction;
+    k.beta = prm->baumgarte;
+    k.slop = prm->slop;
+    k.margin = prm->margin;
+    k.omega = prm->jacobi_omega;
+    k.plane = prm->plane;
+    k.mcpb = mcpb;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_env(env);
+        delete env;
+        set_error("device synchronize after upload failed");
+        return VUDA_ERR_CUDA;
+    }
+    *out = env;
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_destroy(vuda_env_t env) {
+    if (!env) return VUDA_OK;
+    cudaSetDevice(env->device);
+    destroy_cosched(env);
+    destroy_events(env);
+    free_env(env);
+    delete env;
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_info_get(vuda_env_t env, vuda_env_info* out) {
+    if (!env || !out) return invalid("null argument");
+    out->num_envs = env->E;
+    out->num_bodies = env->B;
+    out->num_cams = env->C;
+    out->max_bodies = env->max_bodies;
+    out->num_pixels = env->P;
+    out->num_tris = env->T;
+    out->device_bytes = env->bytes;
+    out->steps_enqueued = env->steps;
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_cam_pix_off(vuda_env_t env, int64_t* out) {
+    if (!env || !out) return invalid("null argument");
+    std::memcpy(out, env->cam_pix_off.data(), sizeof(int64_t) * (env->C + 1));
+    return VUDA_OK;
+}
+
+vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vuda_stream_t stream) {
+    if (!env) return invalid("null env");
+    if (nsteps < 0) return invalid("nsteps < 0");
+    if (nsteps == 0) return VUDA_OK;
+    cudaError_t e = launch_sim(env->d, env->sc, nsteps, force, (int)(env->steps & 1), env->phys_smem,
+                               env->max_bodies, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("sim launch: ") + cudaGetErrorString(e));
+        return VUDA_ERR_CUDA;
+    }
+    env->steps += nsteps;
+    return VUDA_OK;
+}
+
+static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, cudaStream_t stream) {
+    cudaError_t e = launch_render_items(env->d, env->d.pose[slot], *fr, env->item_cam, env->item_y0, env->nitems,
+                                        env->band_rows, env->max_w, stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("render launch: ") + cudaGetErrorString(e));
+        return VUDA_ERR_CUDA;
+    }
+    return VUDA_OK;
+}
+
+vuda_status vuda_render(vuda_env_t env, int32_t pose_slot, const vuda_frame* fr, vuda_stream_t stream) {
+    if (!env || !fr) return invalid("null argument");
+    if (env->P > 0 && (!fr->rgb || !fr->depth)) return invalid("frame rgb/depth required");
+    int slot = pose_slot;
+    if (slot < 0) slot = env->steps > 0 ? (int)((env->steps - 1) & 1) : 0;
+    if (slot > 1) return invalid("pose_slot must be -1, 0 or 1");
+    return render_slot(env, slot, fr, (cudaStream_t)stream);
+}
+
+vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_stream_t* sim_stream,
+                            vuda_stream_t* render_stream, vuda_cosched_info* info) {
+    if (!env || !opts) return invalid("null argument");
+    CK(cudaSetDevice(env->device));
+    destroy_cosched(env);
+    if (opts->mode == VUDA_COSCHED_STREAMS) {
+        CK(cudaStreamCreateWithFlags(&env->sim_s, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&env->ren_s, cudaStreamNonBlocking));
+        env->cos_mode = VUDA_COSCHED_STREAMS;
+        env->cos_info.mode = VUDA_COSCHED_STREAMS;
+    } else if (opts->mode == VUDA_COSCHED_GREEN) {
+        Driver& dr = driver();
+        if (!dr.ok) {
+            set_error("green-context driver entry points unavailable");
+            return VUDA_ERR_UNSUPPORTED;
+        }
+        CK(cudaFree(0));
+        CUdevice dev;
+        CUresult r = dr.DeviceGet(&dev, env->device);
+        CUdevResource all{};
+        if (r == CUDA_SUCCESS) r = dr.DeviceGetDevResource(dev, &all, CU_DEV_RESOURCE_TYPE_SM);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuDeviceGetDevResource: " + cu_err(r));
+            return VUDA_ERR_UNSUPPORTED;
+        }
+        int total = (int)all.sm.smCount;
+        int want = opts->sim_sms > 0 ? opts->sim_sms : total / 2;
+        if (want >= total) return invalid("sim_sms must be below the device SM count");
+        CUdevResource part{}, rest{};
+        unsigned nb = 1;
+        r = dr.DevSmResourceSplitByCount(&part, &nb, &all, &rest, 0, (unsigned)want);
+        if (r != CUDA_SUCCESS || nb != 1) {
+            set_error("cuDevSmResourceSplitByCount: " + cu_err(r));
+            return VUDA_ERR_UNSUPPORTED;
+        }
+        CUdevResourceDesc dsim = nullptr, dren = nullptr;
+        r = dr.DevResourceGenerateDesc(&dsim, &part, 1);
+        if (r == CUDA_SUCCESS) r = dr.DevResourceGenerateDesc(&dren, &rest, 1);
+        if (r == CUDA_SUCCESS) r = dr.GreenCtxCreate(&env->g_sim, dsim, dev, CU_GREEN_CTX_DEFAULT_STREAM);
+        if (r == CUDA_SUCCESS) r = dr.GreenCtxCreate(&env->g_ren, dren, dev, CU_GREEN_CTX_DEFAULT_STREAM);
+        CUstream a = nullptr, b = nullptr;
+        if (r == CUDA_SUCCESS) r = dr.GreenCtxStreamCreate(&a, env->g_sim, CU_STREAM_NON_BLOCKING, 0);
+        if (r == CUDA_SUCCESS) r = dr.GreenCtxStreamCreate(&b, env->g_ren, CU_STREAM_NON_BLOCKING, 0);
+        if (r == CUDA_SUCCESS) r = dr.CtxFromGreenCtx(&env->c_sim, env->g_sim);
+        if (r == CUDA_SUCCESS) r = dr.CtxFromGreenCtx(&env->c_ren, env->g_ren);
+        env->cos_mode = VUDA_COSCHED_GREEN;
+        env->sim_s = (cudaStream_t)a;
+        env->ren_s = (cudaStream_t)b;
+        if (r != CUDA_SUCCESS) {
+            set_error("green context setup: " + cu_err(r));
+            destroy_cosched(env);
+            return VUDA_ERR_UNSUPPORTED;
+        }
+        env->cos_info.mode = VUDA_COSCHED_GREEN;
+        env->cos_info.sim_sms = (int)part.sm.smCount;
+        env->cos_info.render_sms = (int)rest.sm.smCount;
+        env->cos_info.sm_granularity = (int)all.sm.smCoscheduledAlignment;
+    } else {
+        return invalid("unknown co-scheduling mode");
+    }
+    if (sim_stream) *sim_stream = env->sim_s;
+    if (render_stream) *render_stream = env->ren_s;
+    if (info) *info = env->cos_info;
+    return VUDA_OK;
+}
+
+vuda_status vuda_coschedule_reset(vuda_env_t env) {
+    if (!env) return invalid("null env");
+    cudaSetDevice(env->device);
+    return destroy_cosched(env);
+}
+
+static vuda_status ensure_events(std::vector<cudaEvent_t>& pool, CUcontext ctx, size_t n) {
+    ScopedCtx g(ctx);
+    while (pool.size() < n) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        pool.push_back(e);
+    }
+    return VUDA_OK;
+}
+
+vuda_status vuda_pipeline_run(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
+                              float* step_ms) {
+    if (!env || !ring) return invalid("null argument");
+    if (nsteps < 0) return invalid("nsteps < 0");
+    const bool timing = step_ms != nullptr;
+    const bool co = env->cos_mode != 0;
+    // sim pool: [0,1] sim done per pose slot, [2] spare, then nsteps step starts
+    // render pool: [0,1] render done per pose slot, then nsteps step ends
+    // Without co-scheduling everything runs on `stream` and both pools live in
+    // the current context.
+    vuda_status s = ensure_events(env->ev_sim, env->c_sim, 3 + (timing ? (size_t)nsteps : 0));
+    if (s == VUDA_OK) s = ensure_events(env->ev_ren, env->c_ren, 2 + (timing ? (size_t)nsteps : 0));
+    if (s != VUDA_OK) return s;
+    cudaEvent_t* es = env->ev_sim.data();
+    cudaEvent_t* er = env->ev_ren.data();
+    cudaEvent_t* t0 = es + 3;
+    cudaEvent_t* t1 = er + 2;
+    cudaStream_t ss = co ? env->sim_s : (cudaStream_t)stream;
+    cudaStream_t rs = co ? env->ren_s : (cudaStream_t)stream;
+    if (co) CK(cudaStreamSynchronize((cudaStream_t)stream));  // start after the caller's prior work
+    for (int t = 0; t < nsteps; t++) {
+        const int slot = (int)(env->steps & 1);
+        {
+            ScopedCtx g(env->c_sim);
+            if (co && t >= 2) CK(cudaStreamWaitEvent(ss, er[slot], 0));  // render(t-2) released this slot
+            if (timing) CK(cudaEventRecord(t0[t], ss));
+            s = vuda_sim_step(env, 1, nullptr, ss);
+            if (s != VUDA_OK) return s;
+            if (co) CK(cudaEventRecord(es[slot], ss));
+        }
+        {
+            ScopedCtx g(env->c_ren);
+            if (co) CK(cudaStreamWaitEvent(rs, es[slot], 0));
+            s = render_slot(env, slot, &ring[t & 1], rs);
+            if (s != VUDA_OK) return s;
+            if (co) CK(cudaEventRecord(er[slot], rs));
+            if (timing) CK(cudaEventRecord(t1[t], rs));
+        }
+    }
+    if (co) {
+        CK(cudaStreamSynchronize(ss));
+        CK(cudaStreamSynchronize(rs));
+    } else {
+        CK(cudaStreamSynchronize((cudaStream_t)stream));
+    }
+    if (timing)
+        for (int t = 0; t < nsteps; t++) {
+            cudaError_t e = cudaEventElapsedTime(step_ms + t, t0[t], t1[t]);
+            if (e != cudaSuccess) {
+                set_error(std::string("step latency events: ") + cudaGetErrorString(e));
+                return VUDA_ERR_CUDA;
+            }
+        }
+    return VUDA_OK;
+}
+
+vuda_status vuda_wait(vuda_env_t env, int32_t phase) {
+    if (!env) return invalid("null env");
+    if (phase != 0 && phase != 1) return invalid("phase must be 0 (sim) or 1 (render)");
+    cudaStream_t s = phase == 0 ? env->sim_s : env->ren_s;
+    if (s) CK(cudaStreamSynchronize(s));
+    else CK(cudaDeviceSynchronize());
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_get_state(vuda_env_t env, const vuda_state* out) {
+    if (!env || !out) return invalid("null argument");
+    CK(cudaDeviceSynchronize());
+    size_t B = env->B;
+    if (out->pos) CK(cudaMemcpy(out->pos, env->d.pos, 3 * B * 4, cudaMemcpyDeviceToHost));
+    if (out->quat) CK(cudaMemcpy(out->quat, env->d.quat, 4 * B * 4, cudaMemcpyDeviceToHost));
+    if (out->vel) CK(cudaMemcpy(out->vel, env->d.vel, 3 * B * 4, cudaMemcpyDeviceToHost));
+    if (out->angvel) CK(cudaMemcpy(out->angvel, env->d.ang, 3 * B * 4, cudaMemcpyDeviceToHost));
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_set_state(vuda_env_t env, const vuda_state* in) {
+    if (!env || !in) return invalid("null argument");
+    CK(cudaDeviceSynchronize());
+    size_t B = env->B;
+    if (in->pos) CK(cudaMemcpy(env->d.pos, in->pos, 3 * B * 4, cudaMemcpyHostToDevice));
+    if (in->quat) CK(cudaMemcpy(env->d.quat, in->quat, 4 * B * 4, cudaMemcpyHostToDevice));
+    if (in->vel) CK(cudaMemcpy(env->d.vel, in->vel, 3 * B * 4, cudaMemcpyHostToDevice));
+    if (in->angvel) CK(cudaMemcpy(env->d.ang, in->angvel, 3 * B * 4, cudaMemcpyHostToDevice));
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_get_pose(vuda_env_t env, int32_t slot, float* pos, float* quat) {
+    if (!env || slot < 0 || slot > 1) return invalid("bad argument");
+    CK(cudaDeviceSynchronize());
+    size_t B = env->B;
+    if (pos) CK(cudaMemcpy(pos, env->d.pose[slot], 3 * B * 4, cudaMemcpyDeviceToHost));
+    if (quat) CK(cudaMemcpy(quat, env->d.pose[slot] + 3 * B, 4 * B * 4, cudaMemcpyDeviceToHost));
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_set_pose(vuda_env_t env, int32_t slot, const float* pos, const float* quat) {
+    if (!env || slot < 0 || slot > 1) return invalid("bad argument");
+    CK(cudaDeviceSynchronize());
+    size_t B = env->B;
+    if (pos) CK(cudaMemcpy(env->d.pose[slot], pos, 3 * B * 4, cudaMemcpyHostToDevice));
+    if (quat) CK(cudaMemcpy(env->d.pose[slot] + 3 * B, quat, 4 * B * 4, cudaMemcpyHostToDevice));
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_status(vuda_env_t env, uint32_t* flags, uint32_t* or_flags, int32_t clear) {
+    if (!env) return invalid("null env");
+    CK(cudaDeviceSynchronize());
+    std::vector<uint32_t> f(env->E);
+    if (env->E) CK(cudaMemcpy(f.data(), env->d.flags, 4 * (size_t)env->E, cudaMemcpyDeviceToHost));
+    uint32_t o = 0;
+    for (uint32_t x : f) o |= x;
+    if (flags && env->E) std::memcpy(flags, f.data(), 4 * (size_t)env->E);
+    if (or_flags) *or_flags = o;
+    if (clear && env->E) CK(cudaMemset(env->d.flags, 0, 4 * (size_t)env->E));
+    return VUDA_OK;
+}
+
+vuda_status vuda_env_contact_counts(vuda_env_t env, int32_t* counts) {
+    if (!env || !counts) return invalid("null argument");
+    CK(cudaDeviceSynchronize());
+    if (env->E) CK(cudaMemcpy(counts, env->d.ncontacts, 4 * (size_t)env->E, cudaMemcpyDeviceToHost));
+    return VUDA_OK;
+}
+
+vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t ntri, int32_t W, int32_t H,
+                                    uint32_t* triid, float* depth, uint32_t* count, vuda_stream_t stream) {
+    if (ntri < 0 || W <= 0 || H <= 0 || W > 4096 || H > 4096) return invalid("bad size");
+    if ((ntri > 0 && (!xy || !z)) || !triid || !depth) return invalid("null buffer");
+    cudaError_t e = launch_raster_screen(xy, z, ntri, W, H, triid, depth, count, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("raster launch: ") + cudaGetErrorString(e));
+        return VUDA_ERR_CUDA;
+    }
+    return VUDA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of libvuda.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "vuda.h"
+
+namespace vuda {
+
+constexpr int kShapeSphere = 0;
+constexpr int kShapeBox = 1;
+constexpr int kShapeHull = 2;
+
+// Device-resident batch.  All arrays are device pointers.
+struct DevBatch {
+    int E, B, C;
+    const int32_t* body_off;      // [E+1]
+    float* pos;                   // [3][B]
+    float* quat;                  // [4][B]
+    float* vel;                   // [3][B]
+    float* ang;                   // [3][B]
+    const uint8_t* type;          // [B]
+    const float* dims;            // [3][B]
+    const float* im;              // [B]
+    const float* ii;              // [3][B]
+    float* pose[2];               // [7][B] each: pos xyz, quat wxyz
+    uint32_t* flags;              // [E]
+    int32_t* ncontacts;           // [E] contacts at the last substep
+    // physics contact spill area (contacts beyond the shared-memory capacity)
+    float* spill;                 // [sum_e cmax_e * kContactWords]
+    const int64_t* spill_off;     // [E] first spill entry of env e (in contacts)
+    // render
+    const int32_t* mesh_id;       // [B]
+    const float* scale;           // [3][B]
+    const uint32_t* albedo;       // [B]
+    const int32_t* mesh_vert_off; // [M+1]
+    const float* mesh_verts;      // [V][3]
+    const int32_t* mesh_tri_off;  // [M+1]
+    const int32_t* mesh_tris;     // [T][3]
+    int ground_mesh;
+    uint32_t ground_albedo;
+    const int32_t* cam_env;       // [C] env of camera c
+    const int32_t* cam_w;
+    const int32_t* cam_h;
+    const float* cam_par;         // [C][13]: eye3 right3 up3 fwd3 fpy
+    const int64_t* cam_pix_off;   // [C+1]
+    const int64_t* env_tri_base;  // [E] first triangle of env e in the colour scratch
+    uint32_t* tri_color;          // [sum_e tris_e] colour scratch
+    const int32_t* chunk_off;     // [E+1] render vertex-cache chunks of env e
+    const int32_t* chunk_lo;      // [chunks] first env-local body of the chunk (-1 = ground quad)
+    const int32_t* chunk_hi;      // [chunks] one past its last body
+    float light[3];
+};
+
+struct SimConst {
+    float h;                      // dt / substeps
+    int substeps, iterations;
+    float g[3];
+    float restitution, rest_thr, mu, beta, slop, margin, omega;
+    int plane, mcpb;
+};
+
+constexpr int kContactWords = 26;  // floats per contact record
+constexpr int kCamWords = 13;
+
+// Launchers (physics.cu, render.cu)
+cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const float* force, int pose_slot_first,
+                       int smem_per_env, int max_bodies, cudaStream_t stream);
+int phys_smem_bytes_default(int max_bodies, int mcpb);
+int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb);
+cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda_frame& fr, const int32_t* item_cam,
+                                const int32_t* item_y0, int nitems, int band_rows, int max_w, cudaStream_t stream);
+size_t render_smem_for(int band_rows, int W);
+int render_chunk_bodies();
+cudaError_t launch_raster_screen(const int32_t* xy, const float* z, int ntri, int W, int H, uint32_t* triid,
+                                 float* depth, uint32_t* count, cudaStream_t stream);
+int render_vcap();
+
+void set_error(const std::string& s);
+
+}  // namespace vuda

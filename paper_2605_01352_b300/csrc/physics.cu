@@ -1,0 +1,642 @@
+// Batched rigid-body step (the physics phase of the simulate-then-render
+// loop; the paper characterises it as collision detection plus constraint
+// solving in many fine-grained, low-occupancy stages, Sec. 2.1).
+//
+// One warp owns one environment for a whole launch: its bodies and contacts
+// live in shared memory across all substeps, so the serial chain of
+// substeps x (contacts + Jacobi iterations) runs on warp-synchronous
+// barriers (__syncwarp) instead of kernel launches or block barriers.  The
+// phase is latency-bound by construction -- which is exactly what leaves SM
+// issue slots free for the co-scheduled renderer.
+//
+// Arithmetic: every float expression is evaluated in the written order
+// (the library is built with -fmad=false), so results reproduce a plain
+// sequential evaluation of the same formulas.
+//
+// Per substep (h = dt / substeps):
+//   1. v += h (g + F / m); rotation R(q) and world inverse inertia R I^-1 R^T
+//   2. contacts in canonical order: plane contacts by body (box corners in
+//      sign-bit order), then pairs (i, j), i < j, that pass a bounding-sphere
+//      test: sphere-sphere, sphere-box, box-box (A's corners inside B, then
+//      B's corners inside A); capacity max_contacts_per_body * N
+//   3. per contact: lever arms, tangent basis, mass-split effective masses,
+//      velocity target (speculative for d >= 0, bias beyond slop, restitution)
+//   4. Jacobi iterations: every contact solves against the iteration's
+//      velocities, then every body sums its contacts' impulses in ascending
+//      contact order
+//   5. x += h v, q <- normalize(q + h/2 (0, w) q)
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace vuda {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Field indices of a contact record (kContactWords floats).
+enum : int {
+    F_AB = 0, F_N = 1, F_RA = 4, F_RB = 7, F_T1 = 10, F_T2 = 13, F_KN = 16, F_KT1 = 17, F_KT2 = 18,
+    F_VMIN = 19, F_LN = 20, F_LT1 = 21, F_LT2 = 22, F_P = 23
+};
+
+struct Contacts {
+    float* s;       // shared SoA, stride cap
+    int cap;        // records in shared memory
+    float* g;       // global spill SoA, stride gstride (record c at c - cap)
+    int gstride;
+    __device__ __forceinline__ float* f(int field, int c) const {
+        return c < cap ? s + field * cap + c : g + (size_t)field * gstride + (c - cap);
+    }
+};
+
+// Per-env body arrays in shared memory (SoA over the env's bodies, stride NB).
+struct Bodies {
+    float *pos, *quat, *vel, *ang, *dims, *im, *ii, *brad, *R, *Iw;
+    int *type, *ncb, *loff;
+    int NB;
+    __device__ __forceinline__ float& P(int k, int i) const { return pos[k * NB + i]; }
+    __device__ __forceinline__ float& Q(int k, int i) const { return quat[k * NB + i]; }
+    __device__ __forceinline__ float& V(int k, int i) const { return vel[k * NB + i]; }
+    __device__ __forceinline__ float& W(int k, int i) const { return ang[k * NB + i]; }
+    __device__ __forceinline__ float& D(int k, int i) const { return dims[k * NB + i]; }
+    __device__ __forceinline__ float& Rm(int k, int i) const { return R[k * NB + i]; }
+    __device__ __forceinline__ float& I(int k, int i) const { return Iw[k * NB + i]; }
+};
+
+struct f3 { float x, y, z; };
+
+__device__ __forceinline__ float dot3(f3 a, f3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+__device__ __forceinline__ f3 cross3(f3 a, f3 b) {
+    return f3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ f3 sub3(f3 a, f3 b) { return f3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 add3(f3 a, f3 b) { return f3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+
+__device__ __forceinline__ f3 ldpos(const Bodies& B, int i) { return f3{B.P(0, i), B.P(1, i), B.P(2, i)}; }
+__device__ __forceinline__ f3 ldvel(const Bodies& B, int i) { return f3{B.V(0, i), B.V(1, i), B.V(2, i)}; }
+__device__ __forceinline__ f3 ldang(const Bodies& B, int i) { return f3{B.W(0, i), B.W(1, i), B.W(2, i)}; }
+
+// R v with R row major in the body's 9 planes
+__device__ __forceinline__ f3 rmul(const Bodies& B, int i, f3 v) {
+    return f3{(B.Rm(0, i) * v.x + B.Rm(1, i) * v.y) + B.Rm(2, i) * v.z,
+              (B.Rm(3, i) * v.x + B.Rm(4, i) * v.y) + B.Rm(5, i) * v.z,
+              (B.Rm(6, i) * v.x + B.Rm(7, i) * v.y) + B.Rm(8, i) * v.z};
+}
+// R^T v
+__device__ __forceinline__ f3 rtmul(const Bodies& B, int i, f3 v) {
+    return f3{(B.Rm(0, i) * v.x + B.Rm(3, i) * v.y) + B.Rm(6, i) * v.z,
+              (B.Rm(1, i) * v.x + B.Rm(4, i) * v.y) + B.Rm(7, i) * v.z,
+              (B.Rm(2, i) * v.x + B.Rm(5, i) * v.y) + B.Rm(8, i) * v.z};
+}
+// Iw v
+__device__ __forceinline__ f3 imul(const Bodies& B, int i, f3 v) {
+    return f3{(B.I(0, i) * v.x + B.I(1, i) * v.y) + B.I(2, i) * v.z,
+              (B.I(3, i) * v.x + B.I(4, i) * v.y) + B.I(5, i) * v.z,
+              (B.I(6, i) * v.x + B.I(7, i) * v.y) + B.I(8, i) * v.z};
+}
+
+__device__ __forceinline__ f3 box_corner(const Bodies& B, int i, int k) {
+    f3 l{(k & 1) ? B.D(0, i) : -B.D(0, i), (k & 2) ? B.D(1, i) : -B.D(1, i), (k & 4) ? B.D(2, i) : -B.D(2, i)};
+    f3 w = rmul(B, i, l);
+    return add3(w, ldpos(B, i));
+}
+
+__device__ __forceinline__ void put_contact(const Contacts& C, int c, int a, int b, f3 n, f3 p, float d) {
+    *C.f(F_AB, c) = __int_as_float(a | ((b + 1) << 16));
+    *C.f(F_N, c) = n.x; *C.f(F_N + 1, c) = n.y; *C.f(F_N + 2, c) = n.z;
+    *C.f(F_RA, c) = p.x; *C.f(F_RA + 1, c) = p.y; *C.f(F_RA + 2, c) = p.z;  // point, converted later
+    *C.f(F_VMIN, c) = d;                                                     // distance, converted later
+}
+
+// Sphere s against box x: normal from the box to the sphere, point on the box, distance.
+__device__ void sphere_box(const Bodies& B, int s, int x, f3& n, f3& pt, float& d) {
+    f3 ps = ldpos(B, s), px = ldpos(B, x);
+    float h[3] = {B.D(0, x), B.D(1, x), B.D(2, x)};
+    float r = B.D(0, s);
+    f3 l3 = rtmul(B, x, sub3(ps, px));
+    float l[3] = {l3.x, l3.y, l3.z}, q[3], nl[3], pl[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) q[k] = l[k] < -h[k] ? -h[k] : (l[k] > h[k] ? h[k] : l[k]);
+    if (q[0] != l[0] || q[1] != l[1] || q[2] != l[2]) {
+        f3 df{l[0] - q[0], l[1] - q[1], l[2] - q[2]};
+        float dist = sqrtf(dot3(df, df));
+        nl[0] = df.x / dist; nl[1] = df.y / dist; nl[2] = df.z / dist;
+        d = dist - r;
+        pl[0] = q[0]; pl[1] = q[1]; pl[2] = q[2];
+    } else {
+        float pen[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) pen[k] = h[k] - fabsf(l[k]);
+        int m = 0;
+        if (pen[1] < pen[m]) m = 1;
+        if (pen[2] < pen[m]) m = 2;
+        float sg = l[m] >= 0.0f ? 1.0f : -1.0f;
+        nl[0] = nl[1] = nl[2] = 0.0f;
+        nl[m] = sg;
+        d = -pen[m] - r;
+        pl[0] = l[0]; pl[1] = l[1]; pl[2] = l[2];
+        pl[m] = sg * h[m];
+    }
+    n = rmul(B, x, f3{nl[0], nl[1], nl[2]});
+    pt = add3(rmul(B, x, f3{pl[0], pl[1], pl[2]}), px);
+}
+
+// Corner k of box a tested against box b: returns true if within the margin.
+__device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int k, float margin, f3& c, f3& nB,
+                                              float& d) {
+    c = box_corner(B, a, k);
+    f3 l3 = rtmul(B, b, sub3(c, ldpos(B, b)));
+    float l[3] = {l3.x, l3.y, l3.z};
+    float pen[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) pen[j] = B.D(j, b) - fabsf(l[j]);
+    int m = 0;
+    if (pen[1] < pen[m]) m = 1;
+    if (pen[2] < pen[m]) m = 2;
+    d = -pen[m];
+    if (!(d < margin)) return false;
+    float sg = l[m] >= 0.0f ? 1.0f : -1.0f;
+    nB = f3{sg * B.Rm(m, b), sg * B.Rm(3 + m, b), sg * B.Rm(6 + m, b)};  // column m of R_b
+    return true;
+}
+
+__device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.type[i] == kShapeBox; }
+
+// Number of plane contacts of body i (write = false) or write them from index base.
+__device__ int plane_contacts(const Bodies& B, int i, float margin, bool write, const Contacts& C, int base,
+                              int cmax, bool& ovf) {
+    int k0 = 0;
+    const f3 up{0.0f, 0.0f, 1.0f};
+    if (is_box(B, i)) {
+        for (int k = 0; k < 8; k++) {
+            f3 c = box_corner(B, i, k);
+            if (c.z < margin) {
+                if (write) {
+                    int idx = base + k0;
+                    if (idx < cmax) put_contact(C, idx, i, -1, up, c, c.z); else ovf = true;
+                }
+                k0++;
+            }
+        }
+    } else {
+        float r = B.D(0, i);
+        f3 p = ldpos(B, i);
+        float d = p.z - r;
+        if (d < margin) {
+            if (write) {
+                if (base < cmax) put_contact(C, base, i, -1, up, f3{p.x, p.y, p.z - r}, d); else ovf = true;
+            }
+            k0 = 1;
+        }
+    }
+    return k0;
+}
+
+__device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margin) {
+    f3 dx = sub3(ldpos(B, i), ldpos(B, j));
+    float d2 = dot3(dx, dx);
+    float rs = (B.brad[i] + B.brad[j]) + margin;
+    return d2 < rs * rs;
+}
+
+// Contacts of pair (i, j), i < j, that passed the broad test.
+__device__ int pair_contacts(const Bodies& B, int i, int j, float margin, bool write, const Contacts& C, int base,
+                             int cmax, bool& ovf) {
+    int cnt = 0;
+    bool bi = is_box(B, i), bj = is_box(B, j);
+    auto emit = [&](f3 n, f3 p, float d) {
+        if (write) {
+            int idx = base + cnt;
+            if (idx < cmax) put_contact(C, idx, i, j, n, p, d); else ovf = true;
+        }
+        cnt++;
+    };
+    if (!bi && !bj) {
+        f3 pa = ldpos(B, i), pb = ldpos(B, j);
+        f3 dx = sub3(pa, pb);
+        float d2 = dot3(dx, dx);
+        float ra = B.D(0, i), rb = B.D(0, j);
+        float dist = sqrtf(d2);
+        f3 n;
+        if (dist > 0.0f) n = f3{dx.x / dist, dx.y / dist, dx.z / dist};
+        else n = f3{0.0f, 0.0f, 1.0f};
+        float d = (dist - ra) - rb;
+        if (d < margin) emit(n, f3{pa.x - n.x * ra, pa.y - n.y * ra, pa.z - n.z * ra}, d);
+    } else if (!bi && bj) {
+        f3 n, pt; float d;
+        sphere_box(B, i, j, n, pt, d);
+        if (d < margin) emit(n, pt, d);
+    } else if (bi && !bj) {
+        f3 n, pt; float d;
+        sphere_box(B, j, i, n, pt, d);
+        if (d < margin) emit(f3{-n.x, -n.y, -n.z}, pt, d);
+    } else {
+        for (int k = 0; k < 8; k++) {
+            f3 c, n; float d;
+            if (corner_in_box(B, i, j, k, margin, c, n, d)) emit(n, c, d);
+        }
+        for (int k = 0; k < 8; k++) {
+            f3 c, n; float d;
+            if (corner_in_box(B, j, i, k, margin, c, n, d)) emit(f3{-n.x, -n.y, -n.z}, c, d);
+        }
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(kFull, x, 31);
+    return x - v;
+}
+
+__device__ __forceinline__ void unpack_ab(const Contacts& C, int c, int& a, int& b) {
+    int ab = __float_as_int(*C.f(F_AB, c));
+    a = ab & 0xffff;
+    b = (ab >> 16) - 1;
+}
+
+__device__ __forceinline__ f3 ldc3(const Contacts& C, int field, int c) {
+    return f3{*C.f(field, c), *C.f(field + 1, c), *C.f(field + 2, c)};
+}
+
+// mass-split effective mass along dir (see the oracle's definition)
+__device__ __forceinline__ float eff_mass(const Bodies& B, int a, int b, f3 rA, f3 rB, f3 dir) {
+    f3 u = cross3(rA, dir);
+    float kA = (float)B.ncb[a] * (B.im[a] + dot3(u, imul(B, a, u)));
+    float kB = 0.0f;
+    if (b >= 0) {
+        u = cross3(rB, dir);
+        kB = (float)B.ncb[b] * (B.im[b] + dot3(u, imul(B, b, u)));
+    }
+    return kA + kB;
+}
+
+__device__ __forceinline__ f3 rel_vel(const Bodies& B, int a, int b, f3 rA, f3 rB) {
+    f3 va = add3(ldvel(B, a), cross3(ldang(B, a), rA));
+    if (b >= 0) {
+        f3 vb = add3(ldvel(B, b), cross3(ldang(B, b), rB));
+        return sub3(va, vb);
+    }
+    return va;
+}
+
+struct Layout {
+    int NB, cmax, cap;
+    size_t bytes_fixed;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Bytes of per-env shared memory before the contact records.
+__host__ __device__ inline size_t phys_fixed_bytes(int NB, int cmax) {
+    size_t f = (size_t)39 * NB * 4;          // float body planes
+    f += (size_t)(3 * NB + 1) * 4;           // type, ncb, loff[NB+1]
+    f += (size_t)2 * cmax * 2;               // per-body contact lists (int16)
+    return align16(f);
+}
+
+__global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
+                                                 int slot0, int smem_per_env, int NB) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int e = blockIdx.x;
+    const int lane = threadIdx.x;
+    const int b0 = b.body_off[e];
+    const int N = b.body_off[e + 1] - b0;
+    const int B = b.B;
+    const int cmax = sc.mcpb * N;
+    const int cmax_nb = sc.mcpb * NB;
+
+    Bodies S;
+    S.NB = NB;
+    float* fp = reinterpret_cast<float*>(smem);
+    S.pos = fp; fp += 3 * NB;
+    S.quat = fp; fp += 4 * NB;
+    S.vel = fp; fp += 3 * NB;
+    S.ang = fp; fp += 3 * NB;
+    S.dims = fp; fp += 3 * NB;
+    S.im = fp; fp += NB;
+    S.ii = fp; fp += 3 * NB;
+    S.brad = fp; fp += NB;
+    S.R = fp; fp += 9 * NB;
+    S.Iw = fp; fp += 9 * NB;
+    int* ip = reinterpret_cast<int*>(fp);
+    S.type = ip; ip += NB;
+    S.ncb = ip; ip += NB;
+    S.loff = ip; ip += NB + 1;
+    short* lists = reinterpret_cast<short*>(ip);
+    const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
+    Contacts C;
+    C.s = reinterpret_cast<float*>(smem + fixed);
+    int capS = (int)((smem_per_env - (long)fixed) / (kContactWords * 4));
+    if (capS > cmax) capS = cmax;
+    if (capS < 0) capS = 0;
+    C.cap = capS;
+    C.g = b.spill + (size_t)b.spill_off[e] * kContactWords;
+    C.gstride = cmax;
+
+    // load state
+    for (int i = lane; i < N; i += 32) {
+        int g = b0 + i;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            S.P(k, i) = b.pos[k * B + g];
+            S.V(k, i) = b.vel[k * B + g];
+            S.W(k, i) = b.ang[k * B + g];
+            S.D(k, i) = b.dims[k * B + g];
+            S.ii[k * NB + i] = b.ii[k * B + g];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) S.Q(k, i) = b.quat[k * B + g];
+        S.im[i] = b.im[g];
+        int t = b.type[g];
+        S.type[i] = t;
+        S.brad[i] = t == kShapeBox
+                        ? sqrtf((S.D(0, i) * S.D(0, i) + S.D(1, i) * S.D(1, i)) + S.D(2, i) * S.D(2, i))
+                        : S.D(0, i);
+    }
+    __syncwarp();
+
+    bool ovf = false;
+    int nc = 0;
+    const float h = sc.h;
+    for (int step = 0; step < nsteps; step++) {
+        for (int ss = 0; ss < sc.substeps; ss++) {
+            // 1. velocities, rotation, world inverse inertia
+            for (int i = lane; i < N; i += 32) {
+                float im = S.im[i];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    float f = force ? force[k * B + b0 + i] : 0.0f;
+                    S.V(k, i) = S.V(k, i) + h * (sc.g[k] + f * im);
+                }
+                float w = S.Q(0, i), x = S.Q(1, i), y = S.Q(2, i), z = S.Q(3, i);
+                float R[9];
+                R[0] = 1.0f - 2.0f * (y * y + z * z);
+                R[1] = 2.0f * (x * y - w * z);
+                R[2] = 2.0f * (x * z + w * y);
+                R[3] = 2.0f * (x * y + w * z);
+                R[4] = 1.0f - 2.0f * (x * x + z * z);
+                R[5] = 2.0f * (y * z - w * x);
+                R[6] = 2.0f * (x * z - w * y);
+                R[7] = 2.0f * (y * z + w * x);
+                R[8] = 1.0f - 2.0f * (x * x + y * y);
+                float ib0 = S.ii[i], ib1 = S.ii[NB + i], ib2 = S.ii[2 * NB + i];
+#pragma unroll
+                for (int k = 0; k < 9; k++) S.Rm(k, i) = R[k];
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        S.I(3 * r + c, i) = ((R[3 * r] * ib0) * R[3 * c] + (R[3 * r + 1] * ib1) * R[3 * c + 1]) +
+                                            (R[3 * r + 2] * ib2) * R[3 * c + 2];
+            }
+            __syncwarp();
+
+            // 2. contacts in canonical order
+            nc = 0;
+            if (sc.plane) {
+                for (int i0 = 0; i0 < N; i0 += 32) {
+                    int i = i0 + lane;
+                    int cnt = i < N ? plane_contacts(S, i, sc.margin, false, C, 0, cmax, ovf) : 0;
+                    int tot;
+                    int ex = warp_excl_scan(cnt, lane, tot);
+                    if (cnt) plane_contacts(S, i, sc.margin, true, C, nc + ex, cmax, ovf);
+                    nc += tot;
+                }
+            }
+            for (int i = 0; i < N - 1; i++) {
+                for (int j0 = i + 1; j0 < N; j0 += 32) {
+                    int j = j0 + lane;
+                    bool pass = j < N && broad(S, i, j, sc.margin);
+                    if (!__any_sync(kFull, pass)) continue;
+                    int cnt = pass ? pair_contacts(S, i, j, sc.margin, false, C, 0, cmax, ovf) : 0;
+                    int tot;
+                    int ex = warp_excl_scan(cnt, lane, tot);
+                    if (cnt) pair_contacts(S, i, j, sc.margin, true, C, nc + ex, cmax, ovf);
+                    nc += tot;
+                }
+            }
+            if (nc > cmax) nc = cmax;
+            __syncwarp();
+
+            // contacts per body and ascending per-body lists
+            for (int i = lane; i < N; i += 32) {
+                int cnt = 0;
+                for (int c = 0; c < nc; c++) {
+                    int a, bb;
+                    unpack_ab(C, c, a, bb);
+                    cnt += (a == i) | (bb == i);
+                }
+                S.ncb[i] = cnt;
+            }
+            __syncwarp();
+            {
+                int run = 0;
+                for (int i0 = 0; i0 < N; i0 += 32) {
+                    int i = i0 + lane;
+                    int v = i < N ? S.ncb[i] : 0;
+                    int tot;
+                    int ex = warp_excl_scan(v, lane, tot);
+                    if (i < N) S.loff[i] = run + ex;
+                    run += tot;
+                }
+                if (lane == 0) S.loff[N] = run;
+            }
+            __syncwarp();
+            for (int i = lane; i < N; i += 32) {
+                int o = S.loff[i];
+                for (int c = 0; c < nc; c++) {
+                    int a, bb;
+                    unpack_ab(C, c, a, bb);
+                    if (a == i || bb == i) lists[o++] = (short)c;
+                }
+            }
+
+            // 3. per-contact constants
+            for (int c = lane; c < nc; c += 32) {
+                int a, bb;
+                unpack_ab(C, c, a, bb);
+                f3 n = ldc3(C, F_N, c);
+                f3 pt = ldc3(C, F_RA, c);
+                float d = *C.f(F_VMIN, c);
+                f3 rA = sub3(pt, ldpos(S, a));
+                f3 rB = bb >= 0 ? sub3(pt, ldpos(S, bb)) : f3{0.0f, 0.0f, 0.0f};
+                f3 ex = fabsf(n.x) < 0.9f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
+                f3 t = cross3(n, ex);
+                float tl = sqrtf(dot3(t, t));
+                f3 t1{t.x / tl, t.y / tl, t.z / tl};
+                f3 t2 = cross3(n, t1);
+                float kN = eff_mass(S, a, bb, rA, rB, n);
+                float kT1 = eff_mass(S, a, bb, rA, rB, t1);
+                float kT2 = eff_mass(S, a, bb, rA, rB, t2);
+                float vn0 = dot3(n, rel_vel(S, a, bb, rA, rB));
+                float vmin;
+                if (d >= 0.0f) {
+                    vmin = -d / h;
+                } else {
+                    float pen = -d - sc.slop;
+                    vmin = (sc.beta * (pen > 0.0f ? pen : 0.0f)) / h;
+                }
+                if (d < 0.0f && vn0 < -sc.rest_thr) {
+                    float vb = -sc.restitution * vn0;
+                    if (vb > vmin) vmin = vb;
+                }
+                *C.f(F_RA, c) = rA.x; *C.f(F_RA + 1, c) = rA.y; *C.f(F_RA + 2, c) = rA.z;
+                *C.f(F_RB, c) = rB.x; *C.f(F_RB + 1, c) = rB.y; *C.f(F_RB + 2, c) = rB.z;
+                *C.f(F_T1, c) = t1.x; *C.f(F_T1 + 1, c) = t1.y; *C.f(F_T1 + 2, c) = t1.z;
+                *C.f(F_T2, c) = t2.x; *C.f(F_T2 + 1, c) = t2.y; *C.f(F_T2 + 2, c) = t2.z;
+                *C.f(F_KN, c) = kN; *C.f(F_KT1, c) = kT1; *C.f(F_KT2, c) = kT2;
+                *C.f(F_VMIN, c) = vmin;
+                *C.f(F_LN, c) = 0.0f; *C.f(F_LT1, c) = 0.0f; *C.f(F_LT2, c) = 0.0f;
+            }
+            __syncwarp();
+
+            // 4. Jacobi iterations
+            for (int it = 0; it < sc.iterations; it++) {
+                for (int c = lane; c < nc; c += 32) {
+                    int a, bb;
+                    unpack_ab(C, c, a, bb);
+                    f3 n = ldc3(C, F_N, c), t1 = ldc3(C, F_T1, c), t2 = ldc3(C, F_T2, c);
+                    f3 vr = rel_vel(S, a, bb, ldc3(C, F_RA, c), ldc3(C, F_RB, c));
+                    float vn = dot3(n, vr);
+                    float ln = *C.f(F_LN, c);
+                    float dl = (*C.f(F_VMIN, c) - vn) / *C.f(F_KN, c);
+                    float lnew = ln + dl;
+                    if (!(lnew > 0.0f)) lnew = 0.0f;
+                    float dln = lnew - ln;
+                    *C.f(F_LN, c) = lnew;
+                    float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
+                    float l1 = *C.f(F_LT1, c), l2 = *C.f(F_LT2, c);
+                    float a1 = l1 - vt1 / *C.f(F_KT1, c);
+                    float a2 = l2 - vt2 / *C.f(F_KT2, c);
+                    float lim = sc.mu * lnew;
+                    float m2 = a1 * a1 + a2 * a2;
+                    if (m2 > lim * lim) {
+                        float s = lim / sqrtf(m2);
+                        a1 = a1 * s;
+                        a2 = a2 * s;
+                    }
+                    float dl1 = a1 - l1, dl2 = a2 - l2;
+                    *C.f(F_LT1, c) = a1;
+                    *C.f(F_LT2, c) = a2;
+                    *C.f(F_P, c) = (dln * n.x + dl1 * t1.x) + dl2 * t2.x;
+                    *C.f(F_P + 1, c) = (dln * n.y + dl1 * t1.y) + dl2 * t2.y;
+                    *C.f(F_P + 2, c) = (dln * n.z + dl1 * t1.z) + dl2 * t2.z;
+                }
+                __syncwarp();
+                for (int i = lane; i < N; i += 32) {
+                    f3 sp{0.0f, 0.0f, 0.0f}, sl{0.0f, 0.0f, 0.0f};
+                    for (int k = S.loff[i]; k < S.loff[i + 1]; k++) {
+                        int c = lists[k];
+                        int a, bb;
+                        unpack_ab(C, c, a, bb);
+                        f3 P = ldc3(C, F_P, c);
+                        if (a == i) {
+                            f3 t = cross3(ldc3(C, F_RA, c), P);
+                            sp = add3(sp, P);
+                            sl = add3(sl, t);
+                        } else {
+                            f3 t = cross3(ldc3(C, F_RB, c), P);
+                            sp = sub3(sp, P);
+                            sl = sub3(sl, t);
+                        }
+                    }
+                    f3 dw = imul(S, i, sl);
+                    float im = S.im[i];
+                    S.V(0, i) = S.V(0, i) + sc.omega * (im * sp.x);
+                    S.V(1, i) = S.V(1, i) + sc.omega * (im * sp.y);
+                    S.V(2, i) = S.V(2, i) + sc.omega * (im * sp.z);
+                    S.W(0, i) = S.W(0, i) + sc.omega * dw.x;
+                    S.W(1, i) = S.W(1, i) + sc.omega * dw.y;
+                    S.W(2, i) = S.W(2, i) + sc.omega * dw.z;
+                }
+                __syncwarp();
+            }
+
+            // 5. positions and orientations
+            const float hh = 0.5f * h;
+            for (int i = lane; i < N; i += 32) {
+                S.P(0, i) = S.P(0, i) + h * S.V(0, i);
+                S.P(1, i) = S.P(1, i) + h * S.V(1, i);
+                S.P(2, i) = S.P(2, i) + h * S.V(2, i);
+                float qw = S.Q(0, i), qx = S.Q(1, i), qy = S.Q(2, i), qz = S.Q(3, i);
+                float wx = S.W(0, i), wy = S.W(1, i), wz = S.W(2, i);
+                float dw = -((wx * qx + wy * qy) + wz * qz);
+                float dx = qw * wx + (wy * qz - wz * qy);
+                float dy = qw * wy + (wz * qx - wx * qz);
+                float dz = qw * wz + (wx * qy - wy * qx);
+                float nw = qw + hh * dw, nx = qx + hh * dx, ny = qy + hh * dy, nz = qz + hh * dz;
+                float len = sqrtf(((nw * nw + nx * nx) + ny * ny) + nz * nz);
+                S.Q(0, i) = nw / len; S.Q(1, i) = nx / len; S.Q(2, i) = ny / len; S.Q(3, i) = nz / len;
+            }
+            __syncwarp();
+        }
+        // pose of this step for the renderer
+        float* pose = b.pose[(slot0 + step) & 1];
+        for (int i = lane; i < N; i += 32) {
+            int g = b0 + i;
+            pose[0 * B + g] = S.P(0, i);
+            pose[1 * B + g] = S.P(1, i);
+            pose[2 * B + g] = S.P(2, i);
+            pose[3 * B + g] = S.Q(0, i);
+            pose[4 * B + g] = S.Q(1, i);
+            pose[5 * B + g] = S.Q(2, i);
+            pose[6 * B + g] = S.Q(3, i);
+        }
+    }
+    // state back
+    for (int i = lane; i < N; i += 32) {
+        int g = b0 + i;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            b.pos[k * B + g] = S.P(k, i);
+            b.vel[k * B + g] = S.V(k, i);
+            b.ang[k * B + g] = S.W(k, i);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) b.quat[k * B + g] = S.Q(k, i);
+    }
+    bool any_ovf = __any_sync(kFull, ovf);
+    if (lane == 0) {
+        if (nsteps > 0) b.ncontacts[e] = nc;
+        if (any_ovf) atomicOr(b.flags + e, (unsigned)VUDA_FLAG_CONTACT_OVERFLOW);
+    }
+}
+
+}  // namespace
+
+int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb) {
+    size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
+    if ((size_t)smem_per_env < fixed) return 0;
+    return (int)(((size_t)smem_per_env - fixed) / (kContactWords * 4));
+}
+
+int phys_smem_bytes_default(int max_bodies, int mcpb) {
+    size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
+    // room for 6 contacts per body in shared memory, more spill to global
+    size_t want = fixed + (size_t)kContactWords * 4 * 6 * max_bodies;
+    if (want > 200 * 1024) want = 200 * 1024;
+    if (want < fixed) want = fixed;
+    return (int)align16(want);
+}
+
+cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const float* force, int slot0,
+                       int smem_per_env, int max_bodies, cudaStream_t stream) {
+    if (b.E == 0 || nsteps == 0) return cudaSuccess;
+    size_t fixed = phys_fixed_bytes(max_bodies, sc.mcpb * max_bodies);
+    if ((size_t)smem_per_env < fixed) smem_per_env = (int)fixed;
+    // set on every launch: the attribute is tracked per context and the
+    // kernel may be launched into different (green) contexts
+    cudaError_t e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    if (e != cudaSuccess) return e;
+    sim_kernel<<<b.E, 32, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
+    return cudaGetLastError();
+}
+
+}  // namespace vuda

@@ -1,0 +1,524 @@
+// Batched per-environment camera render: a tile/band-binned fixed-point
+// compute rasteriser (the rendering phase the paper runs through Vulkan's
+// vertex -> rasterisation -> fragment pipeline, Sec. 2.1).
+//
+// Work item = (camera, band of rows).  One CTA per work item:
+//   1. for each chunk of the env's bodies (ground quad first) whose vertices
+//      fit the shared-memory vertex cache: transform every vertex
+//      world = R(q) (s * v) + p, view = basis . (world - eye), project
+//      sx = W/2 + fpy xc / zc, sy = H/2 - fpy yc / zc, snap to 24.8 fixed
+//      point (round to nearest even); vertices before the near plane
+//      (zc < 0.01) or beyond the 2^14 px guard band invalidate their
+//      triangles (flagged, not clipped)
+//   2. one thread per triangle: flat colour from the world face normal,
+//      integer signed area (back faces and degenerate triangles culled),
+//      bounding box clipped to the band; small boxes are rasterised by the
+//      owning thread, large ones are queued for the whole CTA
+//   3. coverage by 64-bit integer edge functions at pixel centres with the
+//      top-left tie rule; perspective-correct depth
+//      area2 / (E0/z0 + E1/z1 + E2/z2); visibility by atomicMin on the
+//      shared-memory key depth_bits << 32 | triangle id (ties -> lower id)
+//   4. resolve the band: RGB8 from the per-triangle colour table, FP32 depth,
+//      u32 triangle id, written with 16-byte stores
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace vuda {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kVcap = 1024;        // vertices per chunk
+constexpr int kChunkBodies = 128;  // bodies per chunk
+constexpr int kSmallPx = 16;       // triangles with at most this many bbox pixels stay thread-local
+constexpr float kNear = 0.01f;
+constexpr float kGuard = 16384.0f;
+
+struct Tri {              // a visible, front-facing triangle, vertices oriented to positive area
+    int X[3], Y[3];       // 24.8 fixed point
+    float iz[3];
+    uint32_t id;
+    int x0, x1, y0, y1;   // pixel bbox (inclusive), clipped
+};
+
+struct Band {
+    int W, y0, y1;        // rows [y0, y1)
+    unsigned long long* z;  // keys of rows [y0, y1), row stride W
+    unsigned* count;      // optional coverage counts
+};
+
+// Orients and bounds a snapped triangle.  Returns false if it is culled
+// (back-facing / degenerate) or misses the band.
+__device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const float* iz, uint32_t id, const Band& bd,
+                                          Tri& t) {
+    long long x0 = X[0], y0 = Y[0], x1 = X[1], y1 = Y[1], x2 = X[2], y2 = Y[2];
+    long long area2 = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0);
+    if (area2 >= 0) return false;
+    t.X[0] = X[0]; t.Y[0] = Y[0]; t.iz[0] = iz[0];
+    t.X[1] = X[2]; t.Y[1] = Y[2]; t.iz[1] = iz[2];
+    t.X[2] = X[1]; t.Y[2] = Y[1]; t.iz[2] = iz[1];
+    t.id = id;
+    int mnx = min(X[0], min(X[1], X[2])), mxx = max(X[0], max(X[1], X[2]));
+    int mny = min(Y[0], min(Y[1], Y[2])), mxy = max(Y[0], max(Y[1], Y[2]));
+    int px0 = (mnx - 128 + 255) >> 8, px1 = (mxx - 128) >> 8;
+    int py0 = (mny - 128 + 255) >> 8, py1 = (mxy - 128) >> 8;
+    px0 = max(px0, 0);
+    px1 = min(px1, bd.W - 1);
+    py0 = max(py0, bd.y0);
+    py1 = min(py1, bd.y1 - 1);
+    t.x0 = px0; t.x1 = px1; t.y0 = py0; t.y1 = py1;
+    return px0 <= px1 && py0 <= py1;
+}
+
+struct Edges {
+    long long A[3], B[3], C[3];
+    bool tl[3];
+    float af;
+};
+
+__device__ __forceinline__ void edges(const Tri& t, Edges& e) {
+    long long area2 = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        int j = i == 2 ? 0 : i + 1, k = i == 0 ? 2 : i - 1;
+        long long A = (long long)t.Y[j] - t.Y[k];
+        long long B = (long long)t.X[k] - t.X[j];
+        e.A[i] = A;
+        e.B[i] = B;
+        e.C[i] = -A * t.X[j] - B * t.Y[j];
+        e.tl[i] = (A > 0) || (A == 0 && B > 0);
+    }
+    area2 = ((long long)t.X[1] - t.X[0]) * ((long long)t.Y[2] - t.Y[0]) -
+            ((long long)t.Y[1] - t.Y[0]) * ((long long)t.X[2] - t.X[0]);
+    e.af = (float)area2;
+}
+
+__device__ __forceinline__ void shade_px(const Tri& t, const Edges& e, int px, int py, const Band& bd) {
+    long long cx = 256LL * px + 128, cy = 256LL * py + 128;
+    long long E0 = e.A[0] * cx + e.B[0] * cy + e.C[0];
+    long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
+    long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
+    bool in = (E0 > 0 || (E0 == 0 && e.tl[0])) && (E1 > 0 || (E1 == 0 && e.tl[1])) &&
+              (E2 > 0 || (E2 == 0 && e.tl[2]));
+    if (!in) return;
+    float den = ((float)E0 * t.iz[0] + (float)E1 * t.iz[1]) + (float)E2 * t.iz[2];
+    float depth = e.af / den;
+    unsigned long long key = ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
+    int o = (py - bd.y0) * bd.W + px;
+    atomicMin(bd.z + o, key);
+    if (bd.count) atomicAdd(bd.count + o, 1u);
+}
+
+__device__ __forceinline__ void raster_thread(const Tri& t, const Band& bd) {
+    Edges e;
+    edges(t, e);
+    for (int py = t.y0; py <= t.y1; py++)
+        for (int px = t.x0; px <= t.x1; px++) shade_px(t, e, px, py, bd);
+}
+
+// All threads of the CTA rasterise one triangle, striding over its bbox.
+__device__ __forceinline__ void raster_cta(const Tri& t, const Band& bd) {
+    Edges e;
+    edges(t, e);
+    int bw = t.x1 - t.x0 + 1;
+    int npx = bw * (t.y1 - t.y0 + 1);
+    int p = threadIdx.x;
+    if (p >= npx) return;
+    int oy = p / bw, ox = p - oy * bw;
+    const int qy = kThreads / bw, qx = kThreads - qy * bw;
+    for (; p < npx; p += kThreads) {
+        shade_px(t, e, t.x0 + ox, t.y0 + oy, bd);
+        ox += qx;
+        oy += qy;
+        if (ox >= bw) { ox -= bw; oy++; }
+    }
+}
+
+struct Shared {
+    unsigned long long* z;
+    unsigned* count;
+    int* vX;
+    int* vY;
+    float* viz;
+    float* vw;        // [3][kVcap] world
+    int* vflag;       // 0 ok, else VUDA_FLAG_NEAR/GUARD
+    int* cb_v;        // [kChunkBodies+1] chunk-local vertex start per body
+    int* cb_t;        // [kChunkBodies+1] chunk-local triangle start per body
+    Tri* big;         // [kThreads]
+    int* nbig;
+    unsigned* flags;
+};
+
+__device__ __forceinline__ void init_band(const Band& bd) {
+    int n = (bd.y1 - bd.y0) * bd.W;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        bd.z[i] = ~0ULL;
+        if (bd.count) bd.count[i] = 0u;
+    }
+}
+
+// Rasterise (per thread) one candidate triangle: small ones immediately,
+// large ones queued.  Then (CTA-wide) drain the queue.  Must be called by all
+// threads of the CTA.
+__device__ __forceinline__ void raster_batch(bool have, const Tri& t, const Band& bd, Shared& sh) {
+    if (have) {
+        int npx = (t.x1 - t.x0 + 1) * (t.y1 - t.y0 + 1);
+        if (npx <= kSmallPx) {
+            raster_thread(t, bd);
+        } else {
+            int k = atomicAdd(sh.nbig, 1);
+            sh.big[k] = t;
+        }
+    }
+    __syncthreads();
+    int nb = *sh.nbig;
+    for (int k = 0; k < nb; k++) raster_cta(sh.big[k], bd);
+    __syncthreads();
+    if (threadIdx.x == 0) *sh.nbig = 0;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void quat_mat(float w, float x, float y, float z, float* R) {
+    R[0] = 1.0f - 2.0f * (y * y + z * z);
+    R[1] = 2.0f * (x * y - w * z);
+    R[2] = 2.0f * (x * z + w * y);
+    R[3] = 2.0f * (x * y + w * z);
+    R[4] = 1.0f - 2.0f * (x * x + z * z);
+    R[5] = 2.0f * (y * z - w * x);
+    R[6] = 2.0f * (x * z - w * y);
+    R[7] = 2.0f * (y * z + w * x);
+    R[8] = 1.0f - 2.0f * (x * x + y * y);
+}
+
+__device__ __forceinline__ int upper_bound_smem(const int* a, int n, int v) {
+    // largest k in [0, n) with a[k] <= v (a[0] = 0 <= v)
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct RenderArgs {
+    DevBatch b;
+    const float* pose;       // [7][B]
+    vuda_frame fr;
+    const int32_t* item_cam; // [items]
+    const int32_t* item_y0;  // [items]
+    int band_rows;
+};
+
+__global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevBatch& b = a.b;
+    const int item = blockIdx.x;
+    const int cam = a.item_cam[item];
+    const int e = b.cam_env[cam];
+    const int W = b.cam_w[cam], H = b.cam_h[cam];
+    Band bd;
+    bd.W = W;
+    bd.y0 = a.item_y0[item];
+    bd.y1 = min(H, bd.y0 + a.band_rows);
+    bd.count = nullptr;
+
+    Shared sh;
+    unsigned char* p = smem;
+    sh.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)a.band_rows * W * 8;
+    sh.big = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kThreads;
+    sh.vX = reinterpret_cast<int*>(p); p += 4 * kVcap;
+    sh.vY = reinterpret_cast<int*>(p); p += 4 * kVcap;
+    sh.viz = reinterpret_cast<float*>(p); p += 4 * kVcap;
+    sh.vw = reinterpret_cast<float*>(p); p += 12 * kVcap;
+    sh.vflag = reinterpret_cast<int*>(p); p += 4 * kVcap;
+    sh.cb_v = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
+    sh.cb_t = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
+    sh.nbig = reinterpret_cast<int*>(p); p += 4;
+    sh.flags = reinterpret_cast<unsigned*>(p); p += 4;
+    bd.z = sh.z;
+
+    const float* cp = b.cam_par + (size_t)cam * kCamWords;
+    const float ex = cp[0], ey = cp[1], ez = cp[2];
+    const float rx = cp[3], ry = cp[4], rz = cp[5];
+    const float ux = cp[6], uy = cp[7], uz = cp[8];
+    const float fx = cp[9], fy = cp[10], fz = cp[11];
+    const float fpy = cp[12];
+    const float hw = (float)W * 0.5f, hh = (float)H * 0.5f;
+    const int B = b.B;
+    const int b0 = b.body_off[e];
+    const int nbody = b.body_off[e + 1] - b0;
+    const int gm = b.ground_mesh;
+    const int Tg = b.mesh_tri_off[gm + 1] - b.mesh_tri_off[gm];
+    uint32_t* colors = b.tri_color + b.env_tri_base[e];
+
+    if (threadIdx.x == 0) { *sh.nbig = 0; *sh.flags = 0u; }
+    init_band(bd);
+    __syncthreads();
+
+    uint32_t tri_base_running = 0;  // env-local triangle id of the chunk's first triangle
+    for (int ck = b.chunk_off[e]; ck < b.chunk_off[e + 1]; ck++) {
+        const int cb0 = b.chunk_lo[ck], cb1 = b.chunk_hi[ck];  // env-local bodies, -1 = ground
+        const int nb = cb1 - cb0;
+        // chunk body table: vertex and triangle starts (prefix sums)
+        if (threadIdx.x == 0) {
+            int v = 0, t = 0;
+            for (int k = 0; k < nb; k++) {
+                int bi = cb0 + k;
+                int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
+                sh.cb_v[k] = v;
+                sh.cb_t[k] = t;
+                v += b.mesh_vert_off[m + 1] - b.mesh_vert_off[m];
+                t += b.mesh_tri_off[m + 1] - b.mesh_tri_off[m];
+            }
+            sh.cb_v[nb] = v;
+            sh.cb_t[nb] = t;
+        }
+        __syncthreads();
+        const int nv = sh.cb_v[nb], nt = sh.cb_t[nb];
+        // 1. vertices
+        for (int v = threadIdx.x; v < nv; v += kThreads) {
+            int k = upper_bound_smem(sh.cb_v, nb, v);
+            int bi = cb0 + k;
+            int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
+            const float* mv = b.mesh_verts + 3 * (size_t)(b.mesh_vert_off[m] + (v - sh.cb_v[k]));
+            float wx, wy, wz;
+            if (bi < 0) {
+                wx = mv[0]; wy = mv[1]; wz = mv[2];
+            } else {
+                int g = b0 + bi;
+                float R[9];
+                quat_mat(a.pose[3 * B + g], a.pose[4 * B + g], a.pose[5 * B + g], a.pose[6 * B + g], R);
+                float sx = b.scale[g] * mv[0], sy = b.scale[B + g] * mv[1], sz = b.scale[2 * B + g] * mv[2];
+                float tx = (R[0] * sx + R[1] * sy) + R[2] * sz;
+                float ty = (R[3] * sx + R[4] * sy) + R[5] * sz;
+                float tz = (R[6] * sx + R[7] * sy) + R[8] * sz;
+                wx = tx + a.pose[g];
+                wy = ty + a.pose[B + g];
+                wz = tz + a.pose[2 * B + g];
+            }
+            sh.vw[v] = wx; sh.vw[kVcap + v] = wy; sh.vw[2 * kVcap + v] = wz;
+            float dx = wx - ex, dy = wy - ey, dz = wz - ez;
+            float xc = (rx * dx + ry * dy) + rz * dz;
+            float yc = (ux * dx + uy * dy) + uz * dz;
+            float zc = (fx * dx + fy * dy) + fz * dz;
+            int flag = 0;
+            if (!(zc >= kNear)) {
+                flag = VUDA_FLAG_NEAR_DISCARD;
+            } else {
+                float sxp = hw + (fpy * xc) / zc;
+                float syp = hh - (fpy * yc) / zc;
+                if (!(fabsf(sxp) < kGuard && fabsf(syp) < kGuard)) {
+                    flag = VUDA_FLAG_GUARD_DISCARD;
+                } else {
+                    sh.vX[v] = __float2int_rn(sxp * 256.0f);
+                    sh.vY[v] = __float2int_rn(syp * 256.0f);
+                    sh.viz[v] = 1.0f / zc;
+                }
+            }
+            sh.vflag[v] = flag;
+        }
+        __syncthreads();
+        // 2-3. triangles, in batches of one per thread
+        for (int t0 = 0; t0 < nt; t0 += kThreads) {
+            int t = t0 + threadIdx.x;
+            bool have = false;
+            Tri tri;
+            if (t < nt) {
+                int k = upper_bound_smem(sh.cb_t, nb, t);
+                int bi = cb0 + k;
+                int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
+                const int32_t* tv = b.mesh_tris + 3 * (size_t)(b.mesh_tri_off[m] + (t - sh.cb_t[k]));
+                int vb = sh.cb_v[k];
+                int i0 = vb + tv[0], i1 = vb + tv[1], i2 = vb + tv[2];
+                uint32_t id = tri_base_running + (uint32_t)t;
+                // flat colour from the world face normal
+                float e1x = sh.vw[i1] - sh.vw[i0], e1y = sh.vw[kVcap + i1] - sh.vw[kVcap + i0],
+                      e1z = sh.vw[2 * kVcap + i1] - sh.vw[2 * kVcap + i0];
+                float e2x = sh.vw[i2] - sh.vw[i0], e2y = sh.vw[kVcap + i2] - sh.vw[kVcap + i0],
+                      e2z = sh.vw[2 * kVcap + i2] - sh.vw[2 * kVcap + i0];
+                float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+                float len = sqrtf((nx * nx + ny * ny) + nz * nz);
+                float ndl = 0.0f;
+                if (len > 0.0f) ndl = ((nx / len) * b.light[0] + (ny / len) * b.light[1]) + (nz / len) * b.light[2];
+                float I = 0.2f + 0.8f * (ndl > 0.0f ? ndl : 0.0f);
+                uint32_t alb = bi < 0 ? b.ground_albedo : b.albedo[b0 + bi];
+                uint32_t col = 0;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    float av = (float)((alb >> (8 * c)) & 255u);
+                    int v = (int)(av * I + 0.5f);
+                    v = v > 255 ? 255 : v;
+                    col |= (uint32_t)v << (8 * c);
+                }
+                int fl = sh.vflag[i0] | sh.vflag[i1] | sh.vflag[i2];
+                if (fl) {
+                    atomicOr(sh.flags, (unsigned)fl);
+                } else {
+                    int X[3] = {sh.vX[i0], sh.vX[i1], sh.vX[i2]};
+                    int Y[3] = {sh.vY[i0], sh.vY[i1], sh.vY[i2]};
+                    float iz[3] = {sh.viz[i0], sh.viz[i1], sh.viz[i2]};
+                    have = setup_tri(X, Y, iz, id, bd, tri);
+                    if (have) colors[id] = col;
+                }
+            }
+            raster_batch(have, tri, bd, sh);
+        }
+        tri_base_running += (uint32_t)nt;
+        __syncthreads();
+    }
+    (void)Tg;
+    (void)nbody;
+
+    // 4. resolve the band
+    const int64_t pix0 = b.cam_pix_off[cam] + (int64_t)bd.y0 * W;
+    const int npx = (bd.y1 - bd.y0) * W;
+    uint8_t* rgb = a.fr.rgb + 3 * pix0;
+    float* dep = a.fr.depth + pix0;
+    uint32_t* tid = a.fr.triid ? a.fr.triid + pix0 : nullptr;
+    const bool vec = ((pix0 & 3) == 0) && ((npx & 3) == 0);
+    if (vec) {
+        for (int q = threadIdx.x; q < (npx >> 2); q += kThreads) {
+            float d4[4];
+            uint32_t t4[4];
+            uint32_t c4[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                unsigned long long key = sh.z[4 * q + j];
+                if (key == ~0ULL) {
+                    d4[j] = 0.0f; t4[j] = 0xFFFFFFFFu; c4[j] = 0u;
+                } else {
+                    t4[j] = (uint32_t)(key & 0xFFFFFFFFull);
+                    d4[j] = __uint_as_float((uint32_t)(key >> 32));
+                    c4[j] = colors[t4[j]];
+                }
+            }
+            reinterpret_cast<float4*>(dep)[q] = make_float4(d4[0], d4[1], d4[2], d4[3]);
+            if (tid) reinterpret_cast<uint4*>(tid)[q] = make_uint4(t4[0], t4[1], t4[2], t4[3]);
+            // 4 pixels = 12 bytes = 3 words, little endian r g b r | g b r g | b r g b
+            uint32_t w0 = (c4[0] & 0xFFFFFFu) | ((c4[1] & 0xFFu) << 24);
+            uint32_t w1 = ((c4[1] >> 8) & 0xFFFFu) | ((c4[2] & 0xFFFFu) << 16);
+            uint32_t w2 = ((c4[2] >> 16) & 0xFFu) | ((c4[3] & 0xFFFFFFu) << 8);
+            uint32_t* r32 = reinterpret_cast<uint32_t*>(rgb) + 3 * q;
+            r32[0] = w0; r32[1] = w1; r32[2] = w2;
+        }
+    } else {
+        for (int i = threadIdx.x; i < npx; i += kThreads) {
+            unsigned long long key = sh.z[i];
+            uint32_t c = 0u;
+            if (key == ~0ULL) {
+                dep[i] = 0.0f;
+                if (tid) tid[i] = 0xFFFFFFFFu;
+            } else {
+                uint32_t t = (uint32_t)(key & 0xFFFFFFFFull);
+                dep[i] = __uint_as_float((uint32_t)(key >> 32));
+                if (tid) tid[i] = t;
+                c = colors[t];
+            }
+            rgb[3 * i] = c & 255u;
+            rgb[3 * i + 1] = (c >> 8) & 255u;
+            rgb[3 * i + 2] = (c >> 16) & 255u;
+        }
+    }
+    if (threadIdx.x == 0 && *sh.flags) atomicOr(b.flags + e, *sh.flags);
+}
+
+// Test hook: screen-space triangles, one CTA per band of the W x H image.
+__global__ void __launch_bounds__(kThreads) raster_screen_kernel(const int32_t* __restrict__ xy,
+                                                                 const float* __restrict__ z, int ntri, int W, int H,
+                                                                 int band_rows, uint32_t* triid, float* depth,
+                                                                 uint32_t* count) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Band bd;
+    bd.W = W;
+    bd.y0 = blockIdx.x * band_rows;
+    bd.y1 = min(H, bd.y0 + band_rows);
+    Shared sh;
+    unsigned char* p = smem;
+    sh.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)band_rows * W * 8;
+    sh.count = reinterpret_cast<unsigned*>(p); p += (size_t)band_rows * W * 4;
+    sh.big = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kThreads;
+    sh.nbig = reinterpret_cast<int*>(p); p += 4;
+    bd.z = sh.z;
+    bd.count = count ? sh.count : nullptr;
+    if (threadIdx.x == 0) *sh.nbig = 0;
+    init_band(bd);
+    __syncthreads();
+    for (int t0 = 0; t0 < ntri; t0 += kThreads) {
+        int t = t0 + threadIdx.x;
+        bool have = false;
+        Tri tri;
+        if (t < ntri) {
+            int X[3], Y[3];
+            float iz[3];
+#pragma unroll
+            for (int v = 0; v < 3; v++) {
+                X[v] = xy[6 * t + 2 * v];
+                Y[v] = xy[6 * t + 2 * v + 1];
+                iz[v] = 1.0f / z[3 * t + v];
+            }
+            have = setup_tri(X, Y, iz, (uint32_t)t, bd, tri);
+        }
+        raster_batch(have, tri, bd, sh);
+    }
+    int npx = (bd.y1 - bd.y0) * W;
+    int64_t o = (int64_t)bd.y0 * W;
+    for (int i = threadIdx.x; i < npx; i += kThreads) {
+        unsigned long long key = sh.z[i];
+        if (key == ~0ULL) {
+            triid[o + i] = 0xFFFFFFFFu;
+            depth[o + i] = 0.0f;
+        } else {
+            triid[o + i] = (uint32_t)(key & 0xFFFFFFFFull);
+            depth[o + i] = __uint_as_float((uint32_t)(key >> 32));
+        }
+        if (count) count[o + i] = sh.count[i];
+    }
+}
+
+size_t render_smem_bytes(int band_rows, int W) {
+    size_t s = (size_t)band_rows * W * 8 + sizeof(Tri) * kThreads + (size_t)kVcap * (4 + 4 + 4 + 12 + 4) +
+               (size_t)2 * 4 * (kChunkBodies + 2) + 8;
+    return (s + 15) & ~(size_t)15;
+}
+
+}  // namespace
+
+int render_vcap() { return kVcap; }
+int render_chunk_bodies() { return kChunkBodies; }
+
+// Work items (camera, first row) for a given band height; built by the host
+// and cached by the caller.
+cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda_frame& fr, const int32_t* item_cam,
+                                const int32_t* item_y0, int nitems, int band_rows, int max_w, cudaStream_t stream) {
+    if (nitems == 0) return cudaSuccess;
+    size_t smem = render_smem_bytes(band_rows, max_w);
+    cudaError_t err = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    RenderArgs a;
+    a.b = b;
+    a.pose = pose;
+    a.fr = fr;
+    a.item_cam = item_cam;
+    a.item_y0 = item_y0;
+    a.band_rows = band_rows;
+    render_kernel<<<nitems, kThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+size_t render_smem_for(int band_rows, int W) { return render_smem_bytes(band_rows, W); }
+
+cudaError_t launch_raster_screen(const int32_t* xy, const float* z, int ntri, int W, int H, uint32_t* triid,
+                                 float* depth, uint32_t* count, cudaStream_t stream) {
+    int band_rows = 4096 / W;
+    if (band_rows < 1) band_rows = 1;
+    if (band_rows > H) band_rows = H;
+    size_t smem = (size_t)band_rows * W * 12 + sizeof(Tri) * kThreads + 16;
+    cudaError_t err =
+        cudaFuncSetAttribute(raster_screen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int grid = (H + band_rows - 1) / band_rows;
+    raster_screen_kernel<<<grid, kThreads, smem, stream>>>(xy, z, ntri, W, H, band_rows, triid, depth, count);
+    return cudaGetLastError();
+}
+
+}  // namespace vuda

@@ -1,0 +1,327 @@
+"""Thin ctypes binding of libvuda.so (include/vuda.h).
+
+Argument marshalling only: every step of the simulate-then-render path runs
+in the library's CUDA kernels.  PyTorch supplies device memory (frames,
+forces) and streams.  Importing this module raises if the library has not
+been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvuda.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libvuda.so is not built (python -m paper_2605_01352_b300.build); "
+                      "the CUDA library is required and there is no fallback")
+
+lib = C.CDLL(LIB_PATH)
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_BUSY, ERR_UNSUPPORTED = range(8)
+FLAG_CONTACT_OVERFLOW, FLAG_NEAR_DISCARD, FLAG_GUARD_DISCARD, FLAG_MESH_CAPACITY, FLAG_TIMEOUT = 1, 2, 4, 8, 16
+COSCHED_STREAMS, COSCHED_GREEN = 1, 2
+
+vp = C.c_void_p
+
+
+class SimParams(C.Structure):
+    _fields_ = [("dt", C.c_float), ("substeps", C.c_int32), ("iterations", C.c_int32),
+                ("gravity", C.c_float * 3), ("restitution", C.c_float), ("restitution_threshold", C.c_float),
+                ("friction", C.c_float), ("baumgarte", C.c_float), ("slop", C.c_float), ("margin", C.c_float),
+                ("jacobi_omega", C.c_float), ("plane", C.c_int32), ("max_contacts_per_body", C.c_int32)]
+
+
+class Scene(C.Structure):
+    _fields_ = [("num_envs", C.c_int32), ("body_off", vp), ("pos", vp), ("quat", vp), ("vel", vp),
+                ("angvel", vp), ("shape_type", vp), ("shape_dims", vp), ("inv_mass", vp), ("inv_inertia", vp),
+                ("mesh_id", vp), ("mesh_scale", vp), ("albedo", vp), ("num_meshes", C.c_int32),
+                ("mesh_vert_off", vp), ("mesh_verts", vp), ("mesh_tri_off", vp), ("mesh_tris", vp),
+                ("ground_mesh", C.c_int32), ("ground_albedo", C.c_uint32), ("cam_off", vp), ("cam_w", vp),
+                ("cam_h", vp), ("cam_eye", vp), ("cam_right", vp), ("cam_up", vp), ("cam_fwd", vp),
+                ("cam_fpy", vp), ("light", C.c_float * 3)]
+
+
+class EnvOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("device", C.c_int32), ("render_band_rows", C.c_int32),
+                ("phys_smem_bytes", C.c_int32)]
+
+
+class EnvInfo(C.Structure):
+    _fields_ = [("num_envs", C.c_int32), ("num_bodies", C.c_int32), ("num_cams", C.c_int32),
+                ("max_bodies", C.c_int32), ("num_pixels", C.c_int64), ("num_tris", C.c_int64),
+                ("device_bytes", C.c_int64), ("steps_enqueued", C.c_int64)]
+
+
+class Frame(C.Structure):
+    _fields_ = [("rgb", vp), ("depth", vp), ("triid", vp)]
+
+
+class State(C.Structure):
+    _fields_ = [("pos", vp), ("quat", vp), ("vel", vp), ("angvel", vp)]
+
+
+class CoschedOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("sim_sms", C.c_int32)]
+
+
+class CoschedInfo(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("sim_sms", C.c_int32), ("render_sms", C.c_int32),
+                ("sm_granularity", C.c_int32)]
+
+
+def _sig(name, args, res=C.c_int):
+    f = getattr(lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("vuda_status_str", [C.c_int], C.c_char_p)
+_sig("vuda_last_error", [], C.c_char_p)
+_sig("vuda_abi_version", [], C.c_int32)
+_sig("vuda_env_create", [C.POINTER(Scene), C.POINTER(SimParams), C.POINTER(EnvOpts), C.POINTER(vp)])
+_sig("vuda_env_destroy", [vp])
+_sig("vuda_env_info_get", [vp, C.POINTER(EnvInfo)])
+_sig("vuda_env_cam_pix_off", [vp, vp])
+_sig("vuda_sim_step", [vp, C.c_int32, vp, vp])
+_sig("vuda_render", [vp, C.c_int32, C.POINTER(Frame), vp])
+_sig("vuda_coschedule", [vp, C.POINTER(CoschedOpts), C.POINTER(vp), C.POINTER(vp), C.POINTER(CoschedInfo)])
+_sig("vuda_coschedule_reset", [vp])
+_sig("vuda_pipeline_run", [vp, C.c_int32, C.POINTER(Frame), vp, vp])
+_sig("vuda_wait", [vp, C.c_int32])
+_sig("vuda_env_get_state", [vp, C.POINTER(State)])
+_sig("vuda_env_set_state", [vp, C.POINTER(State)])
+_sig("vuda_env_get_pose", [vp, C.c_int32, vp, vp])
+_sig("vuda_env_set_pose", [vp, C.c_int32, vp, vp])
+_sig("vuda_env_status", [vp, vp, vp, C.c_int32])
+_sig("vuda_env_contact_counts", [vp, vp])
+_sig("vuda_raster_screen_tris", [vp, vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp])
+
+
+class VudaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib.vuda_last_error().decode(errors="replace")
+        super().__init__("%s: %s (%s)" % (where, lib.vuda_status_str(status).decode(), msg))
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != OK:
+        raise VudaError(status, where)
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _ptr(a):
+    return None if a is None else vp(a.ctypes.data)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return vp(t.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return vp(s)
+    return vp(s.cuda_stream)
+
+
+def sim_params(p) -> SimParams:
+    return SimParams(p.dt, p.substeps, p.iterations, (C.c_float * 3)(*p.gravity), p.restitution,
+                     p.restitution_threshold, p.friction, p.baumgarte, p.slop, p.margin, p.jacobi_omega,
+                     p.plane, p.max_contacts_per_body)
+
+
+class Env:
+    """A batch of environments resident on the GPU."""
+
+    def __init__(self, scene, params=None, hbm_budget_bytes: int = 0, device: int = 0, band_rows: int = 0,
+                 phys_smem_bytes: int = 0):
+        self.scene = scene
+        keep = []
+
+        def h(a, dt):
+            x = _np(a, dt)
+            keep.append(x)
+            return _ptr(x)
+
+        sc = Scene()
+        sc.num_envs = scene.num_envs
+        sc.body_off = h(scene.body_off, np.int32)
+        sc.pos = h(scene.pos, np.float32)
+        sc.quat = h(scene.quat, np.float32)
+        sc.vel = h(scene.vel, np.float32)
+        sc.angvel = h(scene.angvel, np.float32)
+        sc.shape_type = h(scene.shape_type, np.uint8)
+        sc.shape_dims = h(scene.shape_dims, np.float32)
+        sc.inv_mass = h(scene.inv_mass, np.float32)
+        sc.inv_inertia = h(scene.inv_inertia, np.float32)
+        sc.mesh_id = h(scene.mesh_id, np.int32)
+        sc.mesh_scale = h(scene.mesh_scale, np.float32)
+        sc.albedo = h(scene.albedo, np.uint32)
+        sc.num_meshes = len(scene.mesh_vert_off) - 1
+        sc.mesh_vert_off = h(scene.mesh_vert_off, np.int32)
+        sc.mesh_verts = h(scene.mesh_verts, np.float32)
+        sc.mesh_tri_off = h(scene.mesh_tri_off, np.int32)
+        sc.mesh_tris = h(scene.mesh_tris, np.int32)
+        sc.ground_mesh = scene.ground_mesh
+        sc.ground_albedo = scene.ground_albedo
+        sc.cam_off = h(scene.cam_off, np.int32)
+        sc.cam_w = h(scene.cam_w, np.int32)
+        sc.cam_h = h(scene.cam_h, np.int32)
+        sc.cam_eye = h(scene.cam_eye, np.float32)
+        sc.cam_right = h(scene.cam_right, np.float32)
+        sc.cam_up = h(scene.cam_up, np.float32)
+        sc.cam_fwd = h(scene.cam_fwd, np.float32)
+        sc.cam_fpy = h(scene.cam_fpy, np.float32)
+        sc.light = (C.c_float * 3)(*[float(x) for x in scene.light])
+        self.params = params or scene.params
+        prm = sim_params(self.params)
+        opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes)
+        handle = vp()
+        check(lib.vuda_env_create(C.byref(sc), C.byref(prm), C.byref(opts), C.byref(handle)), "vuda_env_create")
+        self.h = handle
+        info = EnvInfo()
+        check(lib.vuda_env_info_get(self.h, C.byref(info)), "vuda_env_info_get")
+        self.E, self.B, self.C = info.num_envs, info.num_bodies, info.num_cams
+        self.P = info.num_pixels
+        self.T = info.num_tris
+        self.device_bytes = info.device_bytes
+        pix = np.zeros(self.C + 1, np.int64)
+        check(lib.vuda_env_cam_pix_off(self.h, _ptr(pix)), "vuda_env_cam_pix_off")
+        self.cam_pix_off = pix
+        self.sim_stream = None
+        self.render_stream = None
+        self.cosched = None
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib.vuda_env_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> EnvInfo:
+        i = EnvInfo()
+        check(lib.vuda_env_info_get(self.h, C.byref(i)), "vuda_env_info_get")
+        return i
+
+    # -- frames -------------------------------------------------------------------
+    def alloc_frame(self, triid: bool = True):
+        import torch
+        dev = torch.device("cuda")
+        return dict(rgb=torch.empty((self.P, 3), dtype=torch.uint8, device=dev),
+                    depth=torch.empty(self.P, dtype=torch.float32, device=dev),
+                    triid=torch.empty(self.P, dtype=torch.int32, device=dev) if triid else None)
+
+    @staticmethod
+    def frame_struct(fr) -> Frame:
+        return Frame(_dptr(fr["rgb"]), _dptr(fr["depth"]), _dptr(fr.get("triid")))
+
+    # -- the two phases -----------------------------------------------------------
+    def sim_step(self, nsteps: int = 1, force=None, stream=None):
+        check(lib.vuda_sim_step(self.h, nsteps, _dptr(force), _stream(stream)), "vuda_sim_step")
+
+    def render(self, frame, pose_slot: int = -1, stream=None):
+        fs = self.frame_struct(frame)
+        check(lib.vuda_render(self.h, pose_slot, C.byref(fs), _stream(stream)), "vuda_render")
+
+    # -- co-scheduling ----------------------------------------------------------------
+    def coschedule(self, mode: int = COSCHED_GREEN, sim_sms: int = 0):
+        import torch
+        s1, s2 = vp(), vp()
+        info = CoschedInfo()
+        check(lib.vuda_coschedule(self.h, C.byref(CoschedOpts(mode, sim_sms)), C.byref(s1), C.byref(s2),
+                                  C.byref(info)), "vuda_coschedule")
+        self.sim_stream = torch.cuda.ExternalStream(s1.value)
+        self.render_stream = torch.cuda.ExternalStream(s2.value)
+        self.cosched = dict(mode=info.mode, sim_sms=info.sim_sms, render_sms=info.render_sms,
+                            sm_granularity=info.sm_granularity)
+        return self.cosched
+
+    def coschedule_reset(self):
+        check(lib.vuda_coschedule_reset(self.h), "vuda_coschedule_reset")
+        self.sim_stream = self.render_stream = None
+        self.cosched = None
+
+    def pipeline_run(self, nsteps: int, ring: Sequence[dict], stream=None, timing: bool = False):
+        frames = (Frame * 2)(self.frame_struct(ring[0]), self.frame_struct(ring[1 % len(ring)]))
+        ms = np.zeros(max(nsteps, 1), np.float32) if timing else None
+        check(lib.vuda_pipeline_run(self.h, nsteps, frames, _stream(stream), _ptr(ms)), "vuda_pipeline_run")
+        return ms[:nsteps] if timing else None
+
+    def wait(self, phase: int):
+        check(lib.vuda_wait(self.h, phase), "vuda_wait")
+
+    # -- state ------------------------------------------------------------------------
+    def get_state(self):
+        B = self.B
+        s = dict(pos=np.zeros((3, B), np.float32), quat=np.zeros((4, B), np.float32),
+                 vel=np.zeros((3, B), np.float32), angvel=np.zeros((3, B), np.float32))
+        st = State(_ptr(s["pos"]), _ptr(s["quat"]), _ptr(s["vel"]), _ptr(s["angvel"]))
+        check(lib.vuda_env_get_state(self.h, C.byref(st)), "vuda_env_get_state")
+        return s
+
+    def set_state(self, s):
+        arrs = {k: _np(s[k], np.float32) for k in ("pos", "quat", "vel", "angvel")}
+        st = State(*[_ptr(arrs[k]) for k in ("pos", "quat", "vel", "angvel")])
+        check(lib.vuda_env_set_state(self.h, C.byref(st)), "vuda_env_set_state")
+
+    def get_pose(self, slot: int):
+        pos = np.zeros((3, self.B), np.float32)
+        quat = np.zeros((4, self.B), np.float32)
+        check(lib.vuda_env_get_pose(self.h, slot, _ptr(pos), _ptr(quat)), "vuda_env_get_pose")
+        return pos, quat
+
+    def set_pose(self, slot: int, pos, quat):
+        p = _np(pos, np.float32)
+        q = _np(quat, np.float32)
+        check(lib.vuda_env_set_pose(self.h, slot, _ptr(p), _ptr(q)), "vuda_env_set_pose")
+
+    def status(self, clear: bool = False):
+        f = np.zeros(max(self.E, 1), np.uint32)
+        o = C.c_uint32()
+        check(lib.vuda_env_status(self.h, _ptr(f), C.byref(o), int(clear)), "vuda_env_status")
+        return f[:self.E], int(o.value)
+
+    def contact_counts(self):
+        c = np.zeros(max(self.E, 1), np.int32)
+        check(lib.vuda_env_contact_counts(self.h, _ptr(c)), "vuda_env_contact_counts")
+        return c[:self.E]
+
+
+def raster_screen_tris(xy, z, W: int, H: int, count: bool = False, stream=None):
+    """Rasterise snapped 24.8 fixed-point triangles (torch int32 [n,3,2] and
+    float32 [n,3] on the GPU).  Returns (triid, depth, count) device tensors."""
+    import torch
+    dev = xy.device
+    tid = torch.empty((H, W), dtype=torch.int32, device=dev)
+    dep = torch.empty((H, W), dtype=torch.float32, device=dev)
+    cnt = torch.empty((H, W), dtype=torch.int32, device=dev) if count else None
+    n = int(xy.shape[0])
+    check(lib.vuda_raster_screen_tris(_dptr(xy.contiguous()) if n else None, _dptr(z.contiguous()) if n else None,
+                                      n, W, H, _dptr(tid), _dptr(dep), _dptr(cnt), _stream(stream)),
+          "vuda_raster_screen_tris")
+    return tid, dep, cnt

@@ -1,0 +1,262 @@
+"""GPU path (through the C ABI) against the CPU oracle on identical seeded
+inputs.
+
+Bars: coverage / triangle ids bit-exact, depth within 1e-6 relative, colour
+within 1 LSB; physics state within 1e-5 relative (absolute floor 1e-5 in
+units of 1 m, 1 m/s, 1) after every step of a 10-step horizon, with
+identical contact counts and status flags.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2605_01352_b300 import scene as S
+
+pytestmark = pytest.mark.gpu
+
+PHYS_RTOL = 1e-5
+PHYS_ATOL = 1e-5
+DEPTH_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2605_01352_b300 import build
+    build.build()
+    from paper_2605_01352_b300 import vuda
+    return vuda
+
+
+def _cmp_state(g, o, where):
+    for k in ("pos", "vel", "angvel", "quat"):
+        np.testing.assert_allclose(g[k], o[k], rtol=PHYS_RTOL, atol=PHYS_ATOL, err_msg="%s %s" % (where, k))
+
+
+def _physics_horizon(V, orc, sc, steps=10, force=None, **env_kw):
+    import torch
+    env = V.Env(sc, **env_kw)
+    st_o = sc.state()
+    ft = None if force is None else torch.from_numpy(np.ascontiguousarray(force, np.float32)).cuda()
+    for s in range(steps):
+        env.sim_step(1, force=ft)
+        torch.cuda.synchronize()
+        g = env.get_state()
+        st_o, fl_o, cc_o = orc.sim_step(sc, 1, state=st_o, force=force)
+        _cmp_state(g, st_o, "step %d" % s)
+        np.testing.assert_array_equal(env.contact_counts(), cc_o)
+        fl_g, _ = env.status()
+        np.testing.assert_array_equal(fl_g & 1, fl_o & 1)
+    # the pose slot of the last step is the state's pose
+    pos, quat = env.get_pose((steps - 1) & 1)
+    np.testing.assert_array_equal(pos, g["pos"])
+    np.testing.assert_array_equal(quat, g["quat"])
+    env.close()
+    return g
+
+
+def _render_cmp(V, orc, sc, pos=None, quat=None, env=None):
+    import torch
+    own = env is None
+    if own:
+        env = V.Env(sc)
+    pos = sc.pos if pos is None else pos
+    quat = sc.quat if quat is None else quat
+    env.set_pose(0, pos, quat)
+    fr = env.alloc_frame()
+    env.render(fr, pose_slot=0)
+    torch.cuda.synchronize()
+    rgb = fr["rgb"].cpu().numpy()
+    dep = fr["depth"].cpu().numpy()
+    tid = fr["triid"].cpu().numpy().view(np.uint32)
+    o_rgb, o_dep, o_tid, o_fl = orc.render(sc, pos, quat)
+    np.testing.assert_array_equal(tid, o_tid)
+    np.testing.assert_allclose(dep, o_dep, rtol=DEPTH_RTOL, atol=0)
+    assert np.abs(rgb.astype(int) - o_rgb.astype(int)).max() <= 1
+    fl, _ = env.status()
+    np.testing.assert_array_equal(fl & 6, o_fl & 6)
+    if own:
+        env.close()
+    return tid
+
+
+def test_physics_cfg1_horizon(V, orc):
+    _physics_horizon(V, orc, S.cfg1())
+
+
+def test_physics_cfg2_subset_horizon(V, orc):
+    """Spheres and randomly oriented boxes (box-box, sphere-box contacts)."""
+    sc = S.cfg2(24)
+    st, _, _ = orc.sim_step(sc, 60)   # let them land and pile up first
+    sc = dataclasses.replace(sc, **{k: st[k] for k in ("pos", "quat", "vel", "angvel")})
+    _physics_horizon(V, orc, sc, steps=10)
+
+
+def test_physics_with_forces(V, orc):
+    sc = S.cfg1(4)
+    rng = np.random.default_rng(3)
+    f = rng.normal(0, 0.5, (3, sc.num_bodies)).astype(np.float32)
+    _physics_horizon(V, orc, sc, steps=5, force=f)
+
+
+def test_physics_contact_overflow_matches(V, orc):
+    """A capacity of 1 contact per body truncates identically on both sides."""
+    sc = S.cfg2(8)
+    st, _, _ = orc.sim_step(sc, 80)
+    p = dataclasses.replace(sc.params, max_contacts_per_body=1)
+    sc = dataclasses.replace(sc, params=p, **{k: st[k] for k in ("pos", "quat", "vel", "angvel")})
+    _, fl, _ = orc.sim_step(sc, 1)
+    assert fl.any()
+    _physics_horizon(V, orc, sc, steps=3)
+
+
+def test_physics_uneven_and_empty_envs(V, orc):
+    """Ragged batch: 0, 1, 3, 40 and 70 bodies; more contacts than the shared
+    memory holds spill to global memory."""
+    nb = np.array([0, 1, 3, 40, 70], np.int32)
+    sc = S.generate(5, nb, 1234, kinds="mixed", res=64, substeps=4)
+    st, _, _ = orc.sim_step(sc, 40)
+    sc = dataclasses.replace(sc, **{k: st[k] for k in ("pos", "quat", "vel", "angvel")})
+    _physics_horizon(V, orc, sc, steps=4)
+
+
+def test_physics_contact_spill_to_global(V, orc):
+    """Shared memory for only 8 contact records: the rest live in the global
+    spill area, with the same results."""
+    sc = S.cfg2(8)
+    st, _, _ = orc.sim_step(sc, 80)
+    sc = dataclasses.replace(sc, **{k: st[k] for k in ("pos", "quat", "vel", "angvel")})
+    NB, cmax = 32, 16 * 32
+    fixed = 39 * NB * 4 + (3 * NB + 1) * 4 + 2 * cmax * 2
+    fixed = (fixed + 15) // 16 * 16
+    _physics_horizon(V, orc, sc, steps=3, phys_smem_bytes=fixed + 26 * 4 * 8)
+
+
+def test_render_cfg1(V, orc):
+    sc = S.cfg1()
+    st, _, _ = orc.sim_step(sc, 50)
+    _render_cmp(V, orc, sc, st["pos"], st["quat"])
+
+
+def test_render_cfg2_subset(V, orc):
+    sc = S.cfg2(16)
+    st, _, _ = orc.sim_step(sc, 50)
+    _render_cmp(V, orc, sc, st["pos"], st["quat"])
+
+
+def test_render_mixed_resolutions_and_bands(V, orc):
+    """Cameras of 64, 128 and 256 pixels in one batch, and non-default band
+    heights (ragged last band)."""
+    sc = S.generate(3, np.array([6, 10, 3]), 77, kinds="mixed", res=np.array([64, 256, 128]), substeps=4)
+    st, _, _ = orc.sim_step(sc, 20)
+    for rows in (0, 7, 13):
+        env = V.Env(sc, band_rows=rows)
+        _render_cmp(V, orc, sc, st["pos"], st["quat"], env=env)
+        env.close()
+
+
+def test_render_near_plane_flags(V, orc):
+    sc = S.custom([dict(type="sphere", r=0.1, pos=(0.0, -3.0, 1.5)),
+                   dict(type="box", h=(0.05, 0.05, 0.05), pos=(0.1, 0.0, 0.05))], res=64)
+    _render_cmp(V, orc, sc)
+
+
+def test_raster_screen_tris_matches_oracle(V, orc):
+    import torch
+    rng = np.random.default_rng(9)
+    for W, H, n in ((16, 16, 40), (64, 48, 300), (200, 37, 800)):
+        xy = rng.integers(-3 * 256, (max(W, H) + 3) * 256, (n, 3, 2)).astype(np.int32)
+        xy[: n // 3] = (xy[: n // 3] // 128) * 128   # many ties on pixel centres
+        z = rng.uniform(0.2, 5.0, (n, 3)).astype(np.float32)
+        tid, dep, cnt = V.raster_screen_tris(torch.from_numpy(xy).cuda(), torch.from_numpy(z).cuda(), W, H,
+                                             count=True)
+        o_tid, o_dep, o_cnt = orc.raster_screen_tris(xy, z, W, H, count=True)
+        np.testing.assert_array_equal(tid.cpu().numpy().view(np.uint32), o_tid)
+        np.testing.assert_allclose(dep.cpu().numpy(), o_dep, rtol=DEPTH_RTOL, atol=0)
+        np.testing.assert_array_equal(cnt.cpu().numpy(), o_cnt)
+
+
+def test_raster_screen_tris_empty(V):
+    import torch
+    tid, dep, cnt = V.raster_screen_tris(torch.zeros((0, 3, 2), dtype=torch.int32, device="cuda"),
+                                         torch.zeros((0, 3), device="cuda"), 8, 8, count=True)
+    assert (tid.cpu().numpy().view(np.uint32) == 0xFFFFFFFF).all()
+    assert (dep.cpu().numpy() == 0).all() and (cnt.cpu().numpy() == 0).all()
+
+
+def _run_loop(V, sc, steps, mode):
+    import torch
+    env = V.Env(sc)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    if mode:
+        env.coschedule(mode)
+    env.pipeline_run(steps, ring)
+    torch.cuda.synchronize()
+    st = env.get_state()
+    out = [{k: v.cpu().numpy().copy() for k, v in f.items()} for f in ring]
+    env.close()
+    return st, out
+
+
+@pytest.mark.parametrize("mode", ["streams", "green"])
+def test_coscheduled_equals_serialized(V, mode):
+    """Pipelined sim(t+1) || render(t) on two streams (shared SMs or disjoint
+    green-context partitions) gives the same state and frames as the
+    serialized loop, bit for bit."""
+    sc = S.cfg2(64)
+    m = V.COSCHED_STREAMS if mode == "streams" else V.COSCHED_GREEN
+    st0, fr0 = _run_loop(V, sc, 7, 0)
+    st1, fr1 = _run_loop(V, sc, 7, m)
+    for k in st0:
+        np.testing.assert_array_equal(st0[k], st1[k])
+    for a, b in zip(fr0, fr1):
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_pipeline_frames_match_oracle(V, orc):
+    """The co-scheduled loop's last two frames are the oracle's renders of
+    the oracle's states after steps n-1 and n."""
+    sc = S.cfg1(8)
+    n = 6
+    st, fr = _run_loop(V, sc, n, V.COSCHED_STREAMS)
+    s_prev, _, _ = orc.sim_step(sc, n - 1)
+    s_last, _, _ = orc.sim_step(sc, 1, state=s_prev)
+    _cmp_state(st, s_last, "final")
+    for k, s in ((n - 1, s_last), (n - 2, s_prev)):
+        o_rgb, o_dep, o_tid, _ = orc.render(sc, s["pos"], s["quat"])
+        f = fr[k & 1]
+        np.testing.assert_array_equal(f["triid"].view(np.uint32), o_tid)
+        np.testing.assert_allclose(f["depth"], o_dep, rtol=DEPTH_RTOL)
+
+
+def test_full_size_cfg2_sampled(V, orc):
+    """1024 envs x 32 bodies at 128x128, in the benchmark's launch
+    configuration: sampled environments match the oracle run on those
+    environments alone (environments are independent)."""
+    import torch
+    sc = S.cfg2()
+    env = V.Env(sc)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    env.coschedule(V.COSCHED_GREEN)
+    steps = 3
+    env.pipeline_run(steps, ring)
+    torch.cuda.synchronize()
+    g = env.get_state()
+    assert env.status()[1] == 0
+    pix = env.cam_pix_off
+    for e in (0, 1, 511, 777, 1023):
+        sub = sc.subset([e])
+        so, _, _ = orc.sim_step(sub, steps)
+        b0, b1 = sc.body_off[e], sc.body_off[e + 1]
+        for k in ("pos", "vel", "quat", "angvel"):
+            np.testing.assert_allclose(g[k][:, b0:b1], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL)
+        o_rgb, o_dep, o_tid, _ = orc.render(sub, so["pos"], so["quat"])
+        f = ring[(steps - 1) & 1]
+        sl = slice(pix[e], pix[e + 1])
+        np.testing.assert_array_equal(f["triid"][sl].cpu().numpy().view(np.uint32), o_tid)
+        np.testing.assert_allclose(f["depth"][sl].cpu().numpy(), o_dep, rtol=DEPTH_RTOL)
+        assert np.abs(f["rgb"][sl].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1
+    env.close()
