@@ -206,15 +206,41 @@ vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_
                             vuda_stream_t* render_stream, vuda_cosched_info* info);
 vuda_status vuda_coschedule_reset(vuda_env_t env);
 
+/* Optional timing of a loop run (host arrays of nsteps entries, each may be
+ * NULL), from device events:
+ *   step_ms[t]   start of sim(t) to the end of render(t) (step latency)
+ *   sim_ms[t]    duration of sim(t) on the sim stream
+ *   render_ms[t] duration of render(t) on the render stream
+ *   total_ms     start of sim(0) to the end of render(nsteps-1)
+ * Intervals between the two co-scheduled streams are NaN if the driver
+ * cannot relate their events. */
+typedef struct {
+    float* step_ms;
+    float* sim_ms;
+    float* render_ms;
+    float total_ms;
+} vuda_timing;
+
 /* Run nsteps steps of the loop and block until done.  Co-scheduled
  * (after vuda_coschedule): sim(t+1) is enqueued on the sim stream as soon as
  * sim(t) is, render(t) on the render stream after sim(t) (Sec. 3.1 inter-step
  * pipelining); frames alternate between ring[0] and ring[1] and pose slots
  * alternate too, guarded by events.  Not co-scheduled: sim then render on
- * `stream`.  step_ms (optional, host [nsteps]): per-step latency from the
- * start of sim(t) to the end of render(t), from device events. */
+ * `stream`.  timing may be NULL. */
 vuda_status vuda_pipeline_run(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
-                              float* step_ms);
+                              vuda_timing* timing);
+
+/* The same loop with host buffers (end-to-end use): each step copies its
+ * force input from host memory (h_force: [3][B] floats, or [nsteps][3][B]
+ * when force_per_step != 0; NULL for none) to the device before sim(t), and
+ * copies the frame of step t (RGB and depth) from the device ring slot t & 1
+ * into the host ring slot t & 1 (h_rgb: [2][P][3] bytes, h_depth: [2][P]
+ * floats) on a copy stream, overlapped with the following steps.  Host
+ * buffers must be page-locked for the copies to be asynchronous.  ring: the
+ * two device frames used as staging.  Blocks until everything is done. */
+vuda_status vuda_pipeline_run_host(vuda_env_t env, int32_t nsteps, const float* h_force, int32_t force_per_step,
+                                   uint8_t* h_rgb, float* h_depth, const vuda_frame* ring, vuda_stream_t stream,
+                                   vuda_timing* timing);
 
 /* Block until all work enqueued by this handle on the sim (phase 0) or
  * render (phase 1) stream has finished (wait_step / wait_render, Table 1). */

@@ -134,6 +134,10 @@ struct vuda_env {
     CUcontext c_sim = nullptr, c_ren = nullptr;  // green contexts as CUcontext (null otherwise)
     vuda_cosched_info cos_info{};
     std::vector<cudaEvent_t> ev_sim, ev_ren;      // event pools owned by each phase's context
+    // host-buffer loop: device force ring and a copy stream (primary context)
+    float* dforce = nullptr;                      // [2][3][B]
+    cudaStream_t copy_s = nullptr;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -465,6 +469,9 @@ vuda_status vuda_env_destroy(vuda_env_t env) {
     cudaSetDevice(env->device);
     destroy_cosched(env);
     destroy_events(env);
+    if (env->copy_s) cudaStreamDestroy(env->copy_s);
+    for (cudaEvent_t e : env->copy_done)
+        if (e) cudaEventDestroy(e);
     free_env(env);
     delete env;
     return VUDA_OK;
@@ -604,60 +611,117 @@ static vuda_status ensure_events(std::vector<cudaEvent_t>& pool, CUcontext ctx, 
     return VUDA_OK;
 }
 
-vuda_status vuda_pipeline_run(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
-                              float* step_ms) {
+namespace {
+// Fills the timing record from the per-step events (t0: sim start, t0e: sim
+// end on the sim stream; t1s: render start, t1: render end on the render
+// stream).  Differences between events of two different contexts that the
+// driver cannot relate are reported as NaN.
+void fill_timing(vuda_timing* tm, int n, cudaEvent_t* t0, cudaEvent_t* t0e, cudaEvent_t* t1s, cudaEvent_t* t1) {
+    auto el = [](cudaEvent_t a, cudaEvent_t b) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            cudaGetLastError();
+            return __builtin_nanf("");
+        }
+        return ms;
+    };
+    for (int t = 0; t < n; t++) {
+        if (tm->step_ms) tm->step_ms[t] = el(t0[t], t1[t]);
+        if (tm->sim_ms) tm->sim_ms[t] = el(t0[t], t0e[t]);
+        if (tm->render_ms) tm->render_ms[t] = el(t1s[t], t1[t]);
+    }
+    tm->total_ms = n > 0 ? el(t0[0], t1[n - 1]) : 0.0f;
+}
+}  // namespace
+
+static vuda_status pipeline(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
+                            vuda_timing* tm, const float* h_force, int32_t force_per_step, uint8_t* h_rgb,
+                            float* h_depth) {
     if (!env || !ring) return invalid("null argument");
     if (nsteps < 0) return invalid("nsteps < 0");
-    const bool timing = step_ms != nullptr;
+    const bool timing = tm != nullptr;
     const bool co = env->cos_mode != 0;
-    // sim pool: [0,1] sim done per pose slot, [2] spare, then nsteps step starts
-    // render pool: [0,1] render done per pose slot, then nsteps step ends
-    // Without co-scheduling everything runs on `stream` and both pools live in
-    // the current context.
-    vuda_status s = ensure_events(env->ev_sim, env->c_sim, 3 + (timing ? (size_t)nsteps : 0));
-    if (s == VUDA_OK) s = ensure_events(env->ev_ren, env->c_ren, 2 + (timing ? (size_t)nsteps : 0));
+    const bool host = h_rgb != nullptr;
+    const size_t B = env->B, P = (size_t)env->P;
+    if (host) {
+        if (!h_depth) return invalid("h_depth required with h_rgb");
+        if (h_force && !env->dforce) {
+            vuda_status a = dalloc(env, &env->dforce, 2 * 3 * std::max<size_t>(B, 1));
+            if (a != VUDA_OK) return a;
+        }
+        if (!env->copy_s) {
+            CK(cudaStreamCreateWithFlags(&env->copy_s, cudaStreamNonBlocking));
+            for (auto& e : env->copy_done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+    }
+    // sim pool: [0,1] sim done per pose slot, then per step: sim start, sim end
+    // render pool: [0,1] render done per pose slot, then per step: render start, render end
+    const size_t per = timing ? (size_t)nsteps : 0;
+    vuda_status s = ensure_events(env->ev_sim, env->c_sim, 2 + 2 * per);
+    if (s == VUDA_OK) s = ensure_events(env->ev_ren, env->c_ren, 2 + 2 * per);
     if (s != VUDA_OK) return s;
     cudaEvent_t* es = env->ev_sim.data();
     cudaEvent_t* er = env->ev_ren.data();
-    cudaEvent_t* t0 = es + 3;
-    cudaEvent_t* t1 = er + 2;
+    cudaEvent_t *t0 = es + 2, *t0e = es + 2 + per, *t1s = er + 2, *t1 = er + 2 + per;
     cudaStream_t ss = co ? env->sim_s : (cudaStream_t)stream;
     cudaStream_t rs = co ? env->ren_s : (cudaStream_t)stream;
-    if (co) CK(cudaStreamSynchronize((cudaStream_t)stream));  // start after the caller's prior work
+    if (co || host) CK(cudaStreamSynchronize((cudaStream_t)stream));  // start after the caller's prior work
     for (int t = 0; t < nsteps; t++) {
         const int slot = (int)(env->steps & 1);
+        const int fs = t & 1;
         {
             ScopedCtx g(env->c_sim);
-            if (co && t >= 2) CK(cudaStreamWaitEvent(ss, er[slot], 0));  // render(t-2) released this slot
+            if (co && t >= 2) CK(cudaStreamWaitEvent(ss, er[slot], 0));  // render(t-2) released this pose slot
             if (timing) CK(cudaEventRecord(t0[t], ss));
-            s = vuda_sim_step(env, 1, nullptr, ss);
+            const float* dfo = nullptr;
+            if (host && h_force) {
+                const float* src = h_force + (force_per_step ? (size_t)t * 3 * B : 0);
+                float* dst = env->dforce + (size_t)fs * 3 * B;
+                CK(cudaMemcpyAsync(dst, src, 3 * B * sizeof(float), cudaMemcpyHostToDevice, ss));
+                dfo = dst;
+            }
+            s = vuda_sim_step(env, 1, dfo, ss);
             if (s != VUDA_OK) return s;
-            if (co) CK(cudaEventRecord(es[slot], ss));
+            if (timing) CK(cudaEventRecord(t0e[t], ss));
+            CK(cudaEventRecord(es[slot], ss));
         }
         {
             ScopedCtx g(env->c_ren);
             if (co) CK(cudaStreamWaitEvent(rs, es[slot], 0));
-            s = render_slot(env, slot, &ring[t & 1], rs);
+            if (host && t >= 2) CK(cudaStreamWaitEvent(rs, env->copy_done[fs], 0));  // frame slot copied out
+            if (timing) CK(cudaEventRecord(t1s[t], rs));
+            s = render_slot(env, slot, &ring[fs], rs);
             if (s != VUDA_OK) return s;
-            if (co) CK(cudaEventRecord(er[slot], rs));
             if (timing) CK(cudaEventRecord(t1[t], rs));
+            CK(cudaEventRecord(er[slot], rs));
+        }
+        if (host) {
+            // device -> host copy of the frame of step t into host ring slot t & 1
+            CK(cudaStreamWaitEvent(env->copy_s, er[slot], 0));
+            CK(cudaMemcpyAsync(h_rgb + (size_t)fs * 3 * P, ring[fs].rgb, 3 * P, cudaMemcpyDeviceToHost,
+                               env->copy_s));
+            CK(cudaMemcpyAsync(h_depth + (size_t)fs * P, ring[fs].depth, 4 * P, cudaMemcpyDeviceToHost,
+                               env->copy_s));
+            CK(cudaEventRecord(env->copy_done[fs], env->copy_s));
         }
     }
-    if (co) {
-        CK(cudaStreamSynchronize(ss));
-        CK(cudaStreamSynchronize(rs));
-    } else {
-        CK(cudaStreamSynchronize((cudaStream_t)stream));
-    }
-    if (timing)
-        for (int t = 0; t < nsteps; t++) {
-            cudaError_t e = cudaEventElapsedTime(step_ms + t, t0[t], t1[t]);
-            if (e != cudaSuccess) {
-                set_error(std::string("step latency events: ") + cudaGetErrorString(e));
-                return VUDA_ERR_CUDA;
-            }
-        }
+    CK(cudaStreamSynchronize(ss));
+    CK(cudaStreamSynchronize(rs));
+    if (host) CK(cudaStreamSynchronize(env->copy_s));
+    if (timing) fill_timing(tm, nsteps, t0, t0e, t1s, t1);
     return VUDA_OK;
+}
+
+vuda_status vuda_pipeline_run(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
+                              vuda_timing* timing) {
+    return pipeline(env, nsteps, ring, stream, timing, nullptr, 0, nullptr, nullptr);
+}
+
+vuda_status vuda_pipeline_run_host(vuda_env_t env, int32_t nsteps, const float* h_force, int32_t force_per_step,
+                                   uint8_t* h_rgb, float* h_depth, const vuda_frame* ring, vuda_stream_t stream,
+                                   vuda_timing* timing) {
+    if (!h_rgb || !h_depth) return invalid("host frame ring required");
+    return pipeline(env, nsteps, ring, stream, timing, h_force, force_per_step, h_rgb, h_depth);
 }
 
 vuda_status vuda_wait(vuda_env_t env, int32_t phase) {

@@ -65,6 +65,10 @@ class State(C.Structure):
     _fields_ = [("pos", vp), ("quat", vp), ("vel", vp), ("angvel", vp)]
 
 
+class Timing(C.Structure):
+    _fields_ = [("step_ms", vp), ("sim_ms", vp), ("render_ms", vp), ("total_ms", C.c_float)]
+
+
 class CoschedOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("sim_sms", C.c_int32)]
 
@@ -92,7 +96,8 @@ _sig("vuda_sim_step", [vp, C.c_int32, vp, vp])
 _sig("vuda_render", [vp, C.c_int32, C.POINTER(Frame), vp])
 _sig("vuda_coschedule", [vp, C.POINTER(CoschedOpts), C.POINTER(vp), C.POINTER(vp), C.POINTER(CoschedInfo)])
 _sig("vuda_coschedule_reset", [vp])
-_sig("vuda_pipeline_run", [vp, C.c_int32, C.POINTER(Frame), vp, vp])
+_sig("vuda_pipeline_run", [vp, C.c_int32, C.POINTER(Frame), vp, C.POINTER(Timing)])
+_sig("vuda_pipeline_run_host", [vp, C.c_int32, vp, C.c_int32, vp, vp, C.POINTER(Frame), vp, C.POINTER(Timing)])
 _sig("vuda_wait", [vp, C.c_int32])
 _sig("vuda_env_get_state", [vp, C.POINTER(State)])
 _sig("vuda_env_set_state", [vp, C.POINTER(State)])
@@ -266,11 +271,39 @@ class Env:
         self.sim_stream = self.render_stream = None
         self.cosched = None
 
+    @staticmethod
+    def _timing(n):
+        arr = {k: np.zeros(max(n, 1), np.float32) for k in ("step_ms", "sim_ms", "render_ms")}
+        tm = Timing(_ptr(arr["step_ms"]), _ptr(arr["sim_ms"]), _ptr(arr["render_ms"]), 0.0)
+        return tm, arr
+
+    @staticmethod
+    def _timing_out(tm, arr, n):
+        out = {k: v[:n] for k, v in arr.items()}
+        out["total_ms"] = float(tm.total_ms)
+        return out
+
     def pipeline_run(self, nsteps: int, ring: Sequence[dict], stream=None, timing: bool = False):
+        """Run the loop (pipelined when co-scheduled).  With timing=True
+        returns dict(step_ms, sim_ms, render_ms, total_ms)."""
         frames = (Frame * 2)(self.frame_struct(ring[0]), self.frame_struct(ring[1 % len(ring)]))
-        ms = np.zeros(max(nsteps, 1), np.float32) if timing else None
-        check(lib.vuda_pipeline_run(self.h, nsteps, frames, _stream(stream), _ptr(ms)), "vuda_pipeline_run")
-        return ms[:nsteps] if timing else None
+        tm, arr = self._timing(nsteps) if timing else (None, None)
+        check(lib.vuda_pipeline_run(self.h, nsteps, frames, _stream(stream), C.byref(tm) if timing else None),
+              "vuda_pipeline_run")
+        return self._timing_out(tm, arr, nsteps) if timing else None
+
+    def pipeline_run_host(self, nsteps: int, ring: Sequence[dict], h_rgb, h_depth, h_force=None,
+                          force_per_step: bool = False, stream=None, timing: bool = False):
+        """Loop with host buffers: h_force (pinned torch CPU tensor [3,B] or
+        [nsteps,3,B]) in, frames out into the pinned host ring h_rgb [2,P,3],
+        h_depth [2,P]."""
+        frames = (Frame * 2)(self.frame_struct(ring[0]), self.frame_struct(ring[1 % len(ring)]))
+        tm, arr = self._timing(nsteps) if timing else (None, None)
+        hf = None if h_force is None else vp(h_force.data_ptr())
+        check(lib.vuda_pipeline_run_host(self.h, nsteps, hf, int(force_per_step), vp(h_rgb.data_ptr()),
+                                         vp(h_depth.data_ptr()), frames, _stream(stream),
+                                         C.byref(tm) if timing else None), "vuda_pipeline_run_host")
+        return self._timing_out(tm, arr, nsteps) if timing else None
 
     def wait(self, phase: int):
         check(lib.vuda_wait(self.h, phase), "vuda_wait")
