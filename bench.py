@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--settle", type=int, default=120, help="untimed steps before measuring (bodies land)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serial-only", action="store_true", help="only the serialized loop (for profiling)")
     return ap.parse_args()
 
 
@@ -245,6 +246,13 @@ def main():
     Ts = float(np.mean(tm_ser["sim_ms"]))
     Tr = float(np.mean(tm_ser["render_ms"]))
 
+    if args.serial_only:
+        clk.stop()
+        if rank == 0:
+            print(json.dumps({"serialized_env_steps_per_s": ws * E * args.steps / t_ser, "phase_ms":
+                              {"sim": Ts, "render": Tr}}), flush=True)
+        env.close()
+        return
     # co-scheduled: disjoint SM partitions (green contexts)
     cos = env.coschedule(V.COSCHED_GREEN, args.sim_sms)
     env.pipeline_run(args.warmup, ring)

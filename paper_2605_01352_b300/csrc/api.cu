@@ -314,30 +314,42 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     const int Tg = sc->mesh_tri_off[gm + 1] - sc->mesh_tri_off[gm];
     const int Vg = sc->mesh_vert_off[gm + 1] - sc->mesh_vert_off[gm];
     std::vector<int64_t> env_tri_base(E + 1, 0);
-    std::vector<int32_t> chunk_off(E + 1, 0), chunk_lo, chunk_hi;
+    std::vector<int32_t> chunk_off(E + 1, 0), chunk_lo, chunk_hi, chunk_tab_off, chunk_tri0;
+    std::vector<int2> chunk_vt;
     const int vcap = render_vcap(), cbmax = render_chunk_bodies();
+    auto mesh_nv = [&](int m) { return sc->mesh_vert_off[m + 1] - sc->mesh_vert_off[m]; };
+    auto mesh_nt = [&](int m) { return sc->mesh_tri_off[m + 1] - sc->mesh_tri_off[m]; };
     for (int e = 0; e < E; e++) {
-        int64_t t = Tg;
-        int lo = -1, nv = Vg, nb = 1;
-        for (int bi = 0; bi < sc->body_off[e + 1] - sc->body_off[e]; bi++) {
-            int m = sc->mesh_id[sc->body_off[e] + bi];
-            int bv = sc->mesh_vert_off[m + 1] - sc->mesh_vert_off[m];
-            t += sc->mesh_tri_off[m + 1] - sc->mesh_tri_off[m];
-            if (nv + bv > vcap || nb + 1 > cbmax) {
-                chunk_lo.push_back(lo);
-                chunk_hi.push_back(bi);
-                lo = bi;
-                nv = 0;
-                nb = 0;
+        const int nbody = sc->body_off[e + 1] - sc->body_off[e];
+        auto body_mesh = [&](int bi) { return bi < 0 ? gm : sc->mesh_id[sc->body_off[e] + bi]; };
+        int64_t t_env = 0;
+        int lo = -1;
+        while (lo < nbody) {
+            // grow the chunk [lo, hi) while its vertices fit the cache
+            int hi = lo, nv = 0;
+            while (hi < nbody && hi - lo < cbmax && nv + mesh_nv(body_mesh(hi)) <= vcap) {
+                nv += mesh_nv(body_mesh(hi));
+                hi++;
             }
-            nv += bv;
-            nb++;
+            chunk_lo.push_back(lo);
+            chunk_hi.push_back(hi);
+            chunk_tab_off.push_back((int32_t)chunk_vt.size());
+            chunk_tri0.push_back((int32_t)t_env);
+            int v = 0, t = 0;
+            for (int bi = lo; bi < hi; bi++) {
+                chunk_vt.push_back(make_int2(v, t));
+                v += mesh_nv(body_mesh(bi));
+                t += mesh_nt(body_mesh(bi));
+            }
+            chunk_vt.push_back(make_int2(v, t));
+            t_env += t;
+            lo = hi;
         }
-        chunk_lo.push_back(lo);
-        chunk_hi.push_back(sc->body_off[e + 1] - sc->body_off[e]);
         chunk_off[e + 1] = (int32_t)chunk_lo.size();
-        env_tri_base[e + 1] = env_tri_base[e] + t;
+        env_tri_base[e + 1] = env_tri_base[e] + t_env;
     }
+    (void)Tg;
+    (void)Vg;
     env->T = E ? env_tri_base[E] : 0;
 
     // physics shared memory and spill
@@ -347,7 +359,9 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     for (int e = 0; e < E; e++)
         spill_off[e + 1] = spill_off[e] + (int64_t)mcpb * (sc->body_off[e + 1] - sc->body_off[e]);
     // render work items
-    int br = o.render_band_rows > 0 ? o.render_band_rows : std::max(1, 4096 / std::max(1, max_w));
+    int max_h = 1;
+    for (int c = 0; c < C; c++) max_h = std::max(max_h, sc->cam_h[c]);
+    int br = o.render_band_rows > 0 ? o.render_band_rows : render_default_band_rows(std::max(1, max_w), max_h);
     env->band_rows = br;
     std::vector<int32_t> item_cam, item_y0;
     for (int c = 0; c < C; c++)
@@ -400,6 +414,9 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     UP(chunk_off, int32_t, chunk_off.data(), E + 1);
     UP(chunk_lo, int32_t, chunk_lo.data(), chunk_lo.size());
     UP(chunk_hi, int32_t, chunk_hi.data(), chunk_hi.size());
+    UP(chunk_tab_off, int32_t, chunk_tab_off.data(), chunk_tab_off.size());
+    UP(chunk_vt, int2, chunk_vt.data(), chunk_vt.size());
+    UP(chunk_tri0, int32_t, chunk_tri0.data(), chunk_tri0.size());
     UP(spill_off, int64_t, spill_off.data(), E + 1);
     if (s == VUDA_OK) s = upload(env, &env->item_cam, item_cam.data(), item_cam.size());
     if (s == VUDA_OK) s = upload(env, &env->item_y0, item_y0.data(), item_y0.size());

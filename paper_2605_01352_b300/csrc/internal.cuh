@@ -52,6 +52,9 @@ struct DevBatch {
     const int32_t* chunk_off;     // [E+1] render vertex-cache chunks of env e
     const int32_t* chunk_lo;      // [chunks] first env-local body of the chunk (-1 = ground quad)
     const int32_t* chunk_hi;      // [chunks] one past its last body
+    const int32_t* chunk_tab_off; // [chunks] first entry of the chunk in chunk_vt
+    const int2* chunk_vt;         // per chunk, per body k = 0..nb: (first vertex, first triangle), chunk-local
+    const int32_t* chunk_tri0;    // [chunks] env-local id of the chunk's first triangle
     float light[3];
 };
 
@@ -74,6 +77,7 @@ int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb);
 cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda_frame& fr, const int32_t* item_cam,
                                 const int32_t* item_y0, int nitems, int band_rows, int max_w, cudaStream_t stream);
 size_t render_smem_for(int band_rows, int W);
+int render_default_band_rows(int max_w, int max_h);
 int render_chunk_bodies();
 cudaError_t launch_raster_screen(const int32_t* xy, const float* z, int ntri, int W, int H, uint32_t* triid,
                                  float* depth, uint32_t* count, cudaStream_t stream);

@@ -163,7 +163,11 @@ __device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int
 
 __device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.type[i] == kShapeBox; }
 
-// Number of plane contacts of body i (write = false) or write them from index base.
+constexpr int kT = 128;          // threads per environment (one CTA)
+constexpr int kPairChunk = 512;  // candidate pairs per round of the pair phase
+
+// Plane contacts of body i: returns how many (write = false) or writes them
+// from index base (write = true).  Box corners in sign-bit order.
 __device__ int plane_contacts(const Bodies& B, int i, float margin, bool write, const Contacts& C, int base,
                               int cmax, bool& ovf) {
     int k0 = 0;
@@ -200,59 +204,65 @@ __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margi
     return d2 < rs * rs;
 }
 
-// Contacts of pair (i, j), i < j, that passed the broad test.
-__device__ int pair_contacts(const Bodies& B, int i, int j, float margin, bool write, const Contacts& C, int base,
-                             int cmax, bool& ovf) {
-    int cnt = 0;
+// One narrow-phase test of pair (i, j): sub 0 for sphere-sphere and
+// sphere-box; for box-box sub 0..7 tests A's corner sub inside B and
+// sub 8..15 tests B's corner sub-8 inside A.
+__device__ bool pair_test(const Bodies& B, int i, int j, int sub, float margin, f3& n, f3& pt, float& d) {
     bool bi = is_box(B, i), bj = is_box(B, j);
-    auto emit = [&](f3 n, f3 p, float d) {
-        if (write) {
-            int idx = base + cnt;
-            if (idx < cmax) put_contact(C, idx, i, j, n, p, d); else ovf = true;
-        }
-        cnt++;
-    };
     if (!bi && !bj) {
         f3 pa = ldpos(B, i), pb = ldpos(B, j);
         f3 dx = sub3(pa, pb);
         float d2 = dot3(dx, dx);
         float ra = B.D(0, i), rb = B.D(0, j);
         float dist = sqrtf(d2);
-        f3 n;
         if (dist > 0.0f) n = f3{dx.x / dist, dx.y / dist, dx.z / dist};
         else n = f3{0.0f, 0.0f, 1.0f};
-        float d = (dist - ra) - rb;
-        if (d < margin) emit(n, f3{pa.x - n.x * ra, pa.y - n.y * ra, pa.z - n.z * ra}, d);
-    } else if (!bi && bj) {
-        f3 n, pt; float d;
-        sphere_box(B, i, j, n, pt, d);
-        if (d < margin) emit(n, pt, d);
-    } else if (bi && !bj) {
-        f3 n, pt; float d;
-        sphere_box(B, j, i, n, pt, d);
-        if (d < margin) emit(f3{-n.x, -n.y, -n.z}, pt, d);
-    } else {
-        for (int k = 0; k < 8; k++) {
-            f3 c, n; float d;
-            if (corner_in_box(B, i, j, k, margin, c, n, d)) emit(n, c, d);
-        }
-        for (int k = 0; k < 8; k++) {
-            f3 c, n; float d;
-            if (corner_in_box(B, j, i, k, margin, c, n, d)) emit(f3{-n.x, -n.y, -n.z}, c, d);
-        }
+        d = (dist - ra) - rb;
+        pt = f3{pa.x - n.x * ra, pa.y - n.y * ra, pa.z - n.z * ra};
+        return d < margin;
     }
-    return cnt;
+    if (!bi && bj) {
+        sphere_box(B, i, j, n, pt, d);
+        return d < margin;
+    }
+    if (bi && !bj) {
+        sphere_box(B, j, i, n, pt, d);
+        n = f3{-n.x, -n.y, -n.z};
+        return d < margin;
+    }
+    if (sub < 8) return corner_in_box(B, i, j, sub, margin, pt, n, d);
+    bool hit = corner_in_box(B, j, i, sub - 8, margin, pt, n, d);
+    n = f3{-n.x, -n.y, -n.z};
+    return hit;
 }
 
-__device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(kFull, x, o);
         if (lane >= o) x += y;
     }
-    total = __shfl_sync(kFull, x, 31);
-    return x - v;
+    return x;
+}
+
+// Exclusive prefix sum over the CTA's kT threads in thread order.  Must be
+// called by all threads.  wsum: kT/32 ints of shared scratch.
+__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = warp_incl_scan(v, lane);
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int off = 0;
+    total = 0;
+#pragma unroll
+    for (int k = 0; k < kT / 32; k++) {
+        int s = wsum[k];
+        if (k < w) off += s;
+        total += s;
+    }
+    __syncthreads();
+    return off + x - v;
 }
 
 __device__ __forceinline__ void unpack_ab(const Contacts& C, int c, int& a, int& b) {
@@ -265,7 +275,7 @@ __device__ __forceinline__ f3 ldc3(const Contacts& C, int field, int c) {
     return f3{*C.f(field, c), *C.f(field + 1, c), *C.f(field + 2, c)};
 }
 
-// mass-split effective mass along dir (see the oracle's definition)
+// mass-split effective mass along dir
 __device__ __forceinline__ float eff_mass(const Bodies& B, int a, int b, f3 rA, f3 rB, f3 dir) {
     f3 u = cross3(rA, dir);
     float kA = (float)B.ncb[a] * (B.im[a] + dot3(u, imul(B, a, u)));
@@ -286,26 +296,39 @@ __device__ __forceinline__ f3 rel_vel(const Bodies& B, int a, int b, f3 rA, f3 r
     return va;
 }
 
-struct Layout {
-    int NB, cmax, cap;
-    size_t bytes_fixed;
-};
-
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Bytes of per-env shared memory before the contact records.
 __host__ __device__ inline size_t phys_fixed_bytes(int NB, int cmax) {
     size_t f = (size_t)39 * NB * 4;          // float body planes
     f += (size_t)(3 * NB + 1) * 4;           // type, ncb, loff[NB+1]
+    f += (size_t)4 * NB * 4;                 // per-quarter list counters
+    f += (size_t)2 * kPairChunk * 4;         // passing pairs and their item prefix
+    f += (size_t)8 * 4;                      // scan scratch
     f += (size_t)2 * cmax * 2;               // per-body contact lists (int16)
     return align16(f);
 }
 
-__global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
+// First pair (i, j), i < j, of flat index k in lexicographic order.
+__device__ __forceinline__ void pair_of_index(int k, int N, int& i, int& j) {
+    // start(i) = i (2N - i - 1) / 2 is the flat index of (i, i + 1)
+    float b = (float)(2 * N - 1);
+    float disc = b * b - 8.0f * (float)k;
+    int ii = (int)floorf((b - sqrtf(fmaxf(disc, 0.0f))) * 0.5f);
+    ii = max(0, min(ii, N - 2));
+    auto start = [N](int x) { return x * (2 * N - x - 1) / 2; };
+    while (ii > 0 && start(ii) > k) ii--;
+    while (ii < N - 2 && start(ii + 1) <= k) ii++;
+    i = ii;
+    j = k - start(ii) + ii + 1;
+}
+
+__global__ void __launch_bounds__(kT) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
                                                  int slot0, int smem_per_env, int NB) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int e = blockIdx.x;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int b0 = b.body_off[e];
     const int N = b.body_off[e + 1] - b0;
     const int B = b.B;
@@ -329,6 +352,10 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
     S.type = ip; ip += NB;
     S.ncb = ip; ip += NB;
     S.loff = ip; ip += NB + 1;
+    int* qcnt = ip; ip += 4 * NB;        // [4][NB] contacts of each body in each quarter of the list
+    int* plist = ip; ip += kPairChunk;   // passing pairs (i | j << 16)
+    int* pitem = ip; ip += kPairChunk;   // first narrow-phase item of each passing pair
+    int* wsum = ip; ip += 8;
     short* lists = reinterpret_cast<short*>(ip);
     const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
     Contacts C;
@@ -340,8 +367,7 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
     C.g = b.spill + (size_t)b.spill_off[e] * kContactWords;
     C.gstride = cmax;
 
-    // load state
-    for (int i = lane; i < N; i += 32) {
+    for (int i = tid; i < N; i += kT) {
         int g = b0 + i;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -360,15 +386,16 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
                         ? sqrtf((S.D(0, i) * S.D(0, i) + S.D(1, i) * S.D(1, i)) + S.D(2, i) * S.D(2, i))
                         : S.D(0, i);
     }
-    __syncwarp();
+    __syncthreads();
 
     bool ovf = false;
     int nc = 0;
     const float h = sc.h;
+    const int npairs = N * (N - 1) / 2;
     for (int step = 0; step < nsteps; step++) {
         for (int ss = 0; ss < sc.substeps; ss++) {
             // 1. velocities, rotation, world inverse inertia
-            for (int i = lane; i < N; i += 32) {
+            for (int i = tid; i < N; i += kT) {
                 float im = S.im[i];
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
@@ -396,70 +423,135 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
                         S.I(3 * r + c, i) = ((R[3 * r] * ib0) * R[3 * c] + (R[3 * r + 1] * ib1) * R[3 * c + 1]) +
                                             (R[3 * r + 2] * ib2) * R[3 * c + 2];
             }
-            __syncwarp();
+            __syncthreads();
 
-            // 2. contacts in canonical order
+            // 2a. plane contacts, bodies in order
             nc = 0;
             if (sc.plane) {
-                for (int i0 = 0; i0 < N; i0 += 32) {
-                    int i = i0 + lane;
+                for (int i0 = 0; i0 < N; i0 += kT) {
+                    int i = i0 + tid;
                     int cnt = i < N ? plane_contacts(S, i, sc.margin, false, C, 0, cmax, ovf) : 0;
                     int tot;
-                    int ex = warp_excl_scan(cnt, lane, tot);
+                    int ex = block_excl_scan(cnt, wsum, tot);
                     if (cnt) plane_contacts(S, i, sc.margin, true, C, nc + ex, cmax, ovf);
                     nc += tot;
                 }
             }
-            for (int i = 0; i < N - 1; i++) {
-                for (int j0 = i + 1; j0 < N; j0 += 32) {
-                    int j = j0 + lane;
-                    bool pass = j < N && broad(S, i, j, sc.margin);
-                    if (!__any_sync(kFull, pass)) continue;
-                    int cnt = pass ? pair_contacts(S, i, j, sc.margin, false, C, 0, cmax, ovf) : 0;
-                    int tot;
-                    int ex = warp_excl_scan(cnt, lane, tot);
-                    if (cnt) pair_contacts(S, i, j, sc.margin, true, C, nc + ex, cmax, ovf);
-                    nc += tot;
+            // 2b. pairs in (i, j) order, kPairChunk candidates per round
+            for (int k0 = 0; k0 < npairs; k0 += kPairChunk) {
+                const int per = kPairChunk / kT;   // consecutive candidates per thread
+                int kbeg = k0 + tid * per;
+                int pi = 0, pj = 0;
+                if (kbeg < npairs) pair_of_index(kbeg, N, pi, pj);
+                unsigned passmask = 0;
+                int npass = 0, nsub = 0;
+                {
+                    int i = pi, j = pj;
+                    for (int r = 0; r < per; r++) {
+                        if (kbeg + r < npairs) {
+                            if (broad(S, i, j, sc.margin)) {
+                                passmask |= 1u << r;
+                                npass++;
+                                nsub += (is_box(S, i) && is_box(S, j)) ? 16 : 1;
+                            }
+                            if (++j == N) { i++; j = i + 1; }
+                        }
+                    }
+                }
+                int tot;
+                int ex = block_excl_scan(npass | (nsub << 16), wsum, tot);
+                int np = tot & 0xffff, nitems = tot >> 16;
+                {
+                    int o = ex & 0xffff, it = ex >> 16;
+                    int i = pi, j = pj;
+                    for (int r = 0; r < per; r++) {
+                        if (kbeg + r < npairs) {
+                            if (passmask & (1u << r)) {
+                                plist[o] = i | (j << 16);
+                                pitem[o] = it;
+                                o++;
+                                it += (is_box(S, i) && is_box(S, j)) ? 16 : 1;
+                            }
+                            if (++j == N) { i++; j = i + 1; }
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int u0 = 0; u0 < nitems; u0 += kT) {
+                    int u = u0 + tid;
+                    bool hit = false;
+                    int i = 0, j = 0;
+                    f3 n, pt;
+                    float d = 0.0f;
+                    if (u < nitems) {
+                        int lo = 0, hi = np - 1;   // last passing pair whose first item is <= u
+                        while (lo < hi) {
+                            int mid = (lo + hi + 1) >> 1;
+                            if (pitem[mid] <= u) lo = mid; else hi = mid - 1;
+                        }
+                        int pr = plist[lo];
+                        i = pr & 0xffff;
+                        j = pr >> 16;
+                        hit = pair_test(S, i, j, u - pitem[lo], sc.margin, n, pt, d);
+                    }
+                    int t2;
+                    int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
+                    if (hit) {
+                        int idx = nc + ex2;
+                        if (idx < cmax) put_contact(C, idx, i, j, n, pt, d); else ovf = true;
+                    }
+                    nc += t2;
                 }
             }
             if (nc > cmax) nc = cmax;
-            __syncwarp();
 
-            // contacts per body and ascending per-body lists
-            for (int i = lane; i < N; i += 32) {
-                int cnt = 0;
-                for (int c = 0; c < nc; c++) {
-                    int a, bb;
-                    unpack_ab(C, c, a, bb);
-                    cnt += (a == i) | (bb == i);
-                }
-                S.ncb[i] = cnt;
+            // contacts per body, and per-body lists in ascending contact order
+            for (int i = tid; i < 4 * N; i += kT) qcnt[(i / N) * NB + (i % N)] = 0;
+            __syncthreads();
+            const int qlen = (nc + 3) / 4;
+            for (int c = tid; c < nc; c += kT) {
+                int a, bb;
+                unpack_ab(C, c, a, bb);
+                int q = c / qlen;
+                atomicAdd(qcnt + q * NB + a, 1);
+                if (bb >= 0) atomicAdd(qcnt + q * NB + bb, 1);
             }
-            __syncwarp();
+            __syncthreads();
             {
                 int run = 0;
-                for (int i0 = 0; i0 < N; i0 += 32) {
-                    int i = i0 + lane;
-                    int v = i < N ? S.ncb[i] : 0;
+                for (int i0 = 0; i0 < N; i0 += kT) {
+                    int i = i0 + tid;
+                    int v = 0;
+                    if (i < N) v = (qcnt[i] + qcnt[NB + i]) + (qcnt[2 * NB + i] + qcnt[3 * NB + i]);
                     int tot;
-                    int ex = warp_excl_scan(v, lane, tot);
-                    if (i < N) S.loff[i] = run + ex;
+                    int ex = block_excl_scan(v, wsum, tot);
+                    if (i < N) {
+                        S.ncb[i] = v;
+                        S.loff[i] = run + ex;
+                    }
                     run += tot;
                 }
-                if (lane == 0) S.loff[N] = run;
+                if (tid == 0) S.loff[N] = run;
             }
-            __syncwarp();
-            for (int i = lane; i < N; i += 32) {
-                int o = S.loff[i];
-                for (int c = 0; c < nc; c++) {
-                    int a, bb;
-                    unpack_ab(C, c, a, bb);
-                    if (a == i || bb == i) lists[o++] = (short)c;
+            __syncthreads();
+            // warp q fills the entries of contacts in quarter q of the list
+            for (int i0 = 0; i0 < N; i0 += 32) {
+                int i = i0 + lane;
+                if (i < N) {
+                    int o = S.loff[i];
+                    for (int q = 0; q < warp; q++) o += qcnt[q * NB + i];
+                    int cend = min(nc, (warp + 1) * qlen);
+                    for (int c = warp * qlen; c < cend; c++) {
+                        int a, bb;
+                        unpack_ab(C, c, a, bb);
+                        if (a == i || bb == i) lists[o++] = (short)c;
+                    }
                 }
             }
+            __syncthreads();
 
             // 3. per-contact constants
-            for (int c = lane; c < nc; c += 32) {
+            for (int c = tid; c < nc; c += kT) {
                 int a, bb;
                 unpack_ab(C, c, a, bb);
                 f3 n = ldc3(C, F_N, c);
@@ -495,11 +587,11 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
                 *C.f(F_VMIN, c) = vmin;
                 *C.f(F_LN, c) = 0.0f; *C.f(F_LT1, c) = 0.0f; *C.f(F_LT2, c) = 0.0f;
             }
-            __syncwarp();
+            __syncthreads();
 
             // 4. Jacobi iterations
             for (int it = 0; it < sc.iterations; it++) {
-                for (int c = lane; c < nc; c += 32) {
+                for (int c = tid; c < nc; c += kT) {
                     int a, bb;
                     unpack_ab(C, c, a, bb);
                     f3 n = ldc3(C, F_N, c), t1 = ldc3(C, F_T1, c), t2 = ldc3(C, F_T2, c);
@@ -529,8 +621,8 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
                     *C.f(F_P + 1, c) = (dln * n.y + dl1 * t1.y) + dl2 * t2.y;
                     *C.f(F_P + 2, c) = (dln * n.z + dl1 * t1.z) + dl2 * t2.z;
                 }
-                __syncwarp();
-                for (int i = lane; i < N; i += 32) {
+                __syncthreads();
+                for (int i = tid; i < N; i += kT) {
                     f3 sp{0.0f, 0.0f, 0.0f}, sl{0.0f, 0.0f, 0.0f};
                     for (int k = S.loff[i]; k < S.loff[i + 1]; k++) {
                         int c = lists[k];
@@ -556,12 +648,12 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
                     S.W(1, i) = S.W(1, i) + sc.omega * dw.y;
                     S.W(2, i) = S.W(2, i) + sc.omega * dw.z;
                 }
-                __syncwarp();
+                __syncthreads();
             }
 
             // 5. positions and orientations
             const float hh = 0.5f * h;
-            for (int i = lane; i < N; i += 32) {
+            for (int i = tid; i < N; i += kT) {
                 S.P(0, i) = S.P(0, i) + h * S.V(0, i);
                 S.P(1, i) = S.P(1, i) + h * S.V(1, i);
                 S.P(2, i) = S.P(2, i) + h * S.V(2, i);
@@ -575,11 +667,11 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
                 float len = sqrtf(((nw * nw + nx * nx) + ny * ny) + nz * nz);
                 S.Q(0, i) = nw / len; S.Q(1, i) = nx / len; S.Q(2, i) = ny / len; S.Q(3, i) = nz / len;
             }
-            __syncwarp();
+            __syncthreads();
         }
         // pose of this step for the renderer
         float* pose = b.pose[(slot0 + step) & 1];
-        for (int i = lane; i < N; i += 32) {
+        for (int i = tid; i < N; i += kT) {
             int g = b0 + i;
             pose[0 * B + g] = S.P(0, i);
             pose[1 * B + g] = S.P(1, i);
@@ -590,8 +682,7 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
             pose[6 * B + g] = S.Q(3, i);
         }
     }
-    // state back
-    for (int i = lane; i < N; i += 32) {
+    for (int i = tid; i < N; i += kT) {
         int g = b0 + i;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -602,8 +693,8 @@ __global__ void __launch_bounds__(32) sim_kernel(DevBatch b, SimConst sc, int ns
 #pragma unroll
         for (int k = 0; k < 4; k++) b.quat[k * B + g] = S.Q(k, i);
     }
-    bool any_ovf = __any_sync(kFull, ovf);
-    if (lane == 0) {
+    int any_ovf = __syncthreads_or(ovf ? 1 : 0);
+    if (tid == 0) {
         if (nsteps > 0) b.ncontacts[e] = nc;
         if (any_ovf) atomicOr(b.flags + e, (unsigned)VUDA_FLAG_CONTACT_OVERFLOW);
     }
@@ -635,7 +726,7 @@ cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const 
     // kernel may be launched into different (green) contexts
     cudaError_t e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
     if (e != cudaSuccess) return e;
-    sim_kernel<<<b.E, 32, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
+    sim_kernel<<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
     return cudaGetLastError();
 }
 

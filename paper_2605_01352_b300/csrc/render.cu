@@ -1,25 +1,29 @@
-// Batched per-environment camera render: a tile/band-binned fixed-point
-// compute rasteriser (the rendering phase the paper runs through Vulkan's
-// vertex -> rasterisation -> fragment pipeline, Sec. 2.1).
+// Batched per-environment camera render: a tile-binned fixed-point compute
+// rasteriser (the rendering phase the paper runs through Vulkan's vertex ->
+// rasterisation -> fragment pipeline, Sec. 2.1).
 //
-// Work item = (camera, band of rows).  One CTA per work item:
+// Work item = (camera, band of rows).  One CTA of 512 threads per work item:
 //   1. for each chunk of the env's bodies (ground quad first) whose vertices
 //      fit the shared-memory vertex cache: transform every vertex
 //      world = R(q) (s * v) + p, view = basis . (world - eye), project
 //      sx = W/2 + fpy xc / zc, sy = H/2 - fpy yc / zc, snap to 24.8 fixed
-//      point (round to nearest even); vertices before the near plane
+//      point (round to nearest even).  Vertices before the near plane
 //      (zc < 0.01) or beyond the 2^14 px guard band invalidate their
-//      triangles (flagged, not clipped)
-//   2. one thread per triangle: flat colour from the world face normal,
-//      integer signed area (back faces and degenerate triangles culled),
-//      bounding box clipped to the band; small boxes are rasterised by the
-//      owning thread, large ones are queued for the whole CTA
-//   3. coverage by 64-bit integer edge functions at pixel centres with the
-//      top-left tie rule; perspective-correct depth
-//      area2 / (E0/z0 + E1/z1 + E2/z2); visibility by atomicMin on the
-//      shared-memory key depth_bits << 32 | triangle id (ties -> lower id)
+//      triangles (flagged, not clipped).
+//   2. one thread per triangle: integer signed area (back faces and
+//      degenerate triangles culled), bounding box clipped to the band, flat
+//      colour from the world face normal.  Triangles covering at most 16
+//      bounding-box pixels are rasterised by their thread straight into the
+//      shared-memory z-buffer (atomicMin); larger ones are recorded and
+//      binned into 16 x 16 pixel tiles in shared memory.
+//   3. tile pass: one warp per tile, each lane owns a run of 8 pixels and
+//      keeps their keys in registers while it walks the tile's bin.
+//   Coverage: 64-bit integer edge functions at pixel centres with the
+//   top-left tie rule.  Depth: perspective-correct area2 / (E0/z0 + E1/z1 +
+//   E2/z2).  Visibility: minimum of the 64-bit key depth_bits << 32 | id
+//   (ties go to the lower triangle id).
 //   4. resolve the band: RGB8 from the per-triangle colour table, FP32 depth,
-//      u32 triangle id, written with 16-byte stores
+//      u32 triangle id, written with 16-byte stores.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -27,10 +31,13 @@
 namespace vuda {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kRT = 512;           // threads per CTA
+constexpr int kWarps = kRT / 32;
 constexpr int kVcap = 1024;        // vertices per chunk
 constexpr int kChunkBodies = 128;  // bodies per chunk
 constexpr int kSmallPx = 16;       // triangles with at most this many bbox pixels stay thread-local
+constexpr int kBigCap = 128;       // binned triangles per round
+constexpr int kTile = 16;          // tile edge in pixels
 constexpr float kNear = 0.01f;
 constexpr float kGuard = 16384.0f;
 
@@ -38,13 +45,13 @@ struct Tri {              // a visible, front-facing triangle, vertices oriented
     int X[3], Y[3];       // 24.8 fixed point
     float iz[3];
     uint32_t id;
-    int x0, x1, y0, y1;   // pixel bbox (inclusive), clipped
+    short x0, x1, y0, y1; // pixel bbox (inclusive), clipped to the band
 };
 
 struct Band {
-    int W, y0, y1;        // rows [y0, y1)
+    int W, y0, y1;          // rows [y0, y1)
     unsigned long long* z;  // keys of rows [y0, y1), row stride W
-    unsigned* count;      // optional coverage counts
+    unsigned* count;        // optional coverage counts
 };
 
 // Orients and bounds a snapped triangle.  Returns false if it is culled
@@ -54,10 +61,6 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     long long x0 = X[0], y0 = Y[0], x1 = X[1], y1 = Y[1], x2 = X[2], y2 = Y[2];
     long long area2 = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0);
     if (area2 >= 0) return false;
-    t.X[0] = X[0]; t.Y[0] = Y[0]; t.iz[0] = iz[0];
-    t.X[1] = X[2]; t.Y[1] = Y[2]; t.iz[1] = iz[2];
-    t.X[2] = X[1]; t.Y[2] = Y[1]; t.iz[2] = iz[1];
-    t.id = id;
     int mnx = min(X[0], min(X[1], X[2])), mxx = max(X[0], max(X[1], X[2]));
     int mny = min(Y[0], min(Y[1], Y[2])), mxy = max(Y[0], max(Y[1], Y[2]));
     int px0 = (mnx - 128 + 255) >> 8, px1 = (mxx - 128) >> 8;
@@ -66,8 +69,13 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     px1 = min(px1, bd.W - 1);
     py0 = max(py0, bd.y0);
     py1 = min(py1, bd.y1 - 1);
-    t.x0 = px0; t.x1 = px1; t.y0 = py0; t.y1 = py1;
-    return px0 <= px1 && py0 <= py1;
+    if (px0 > px1 || py0 > py1) return false;
+    t.X[0] = X[0]; t.Y[0] = Y[0]; t.iz[0] = iz[0];
+    t.X[1] = X[2]; t.Y[1] = Y[2]; t.iz[1] = iz[2];
+    t.X[2] = X[1]; t.Y[2] = Y[1]; t.iz[2] = iz[1];
+    t.id = id;
+    t.x0 = (short)px0; t.x1 = (short)px1; t.y0 = (short)py0; t.y1 = (short)py1;
+    return true;
 }
 
 struct Edges {
@@ -77,7 +85,6 @@ struct Edges {
 };
 
 __device__ __forceinline__ void edges(const Tri& t, Edges& e) {
-    long long area2 = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         int j = i == 2 ? 0 : i + 1, k = i == 0 ? 2 : i - 1;
@@ -88,94 +95,148 @@ __device__ __forceinline__ void edges(const Tri& t, Edges& e) {
         e.C[i] = -A * t.X[j] - B * t.Y[j];
         e.tl[i] = (A > 0) || (A == 0 && B > 0);
     }
-    area2 = ((long long)t.X[1] - t.X[0]) * ((long long)t.Y[2] - t.Y[0]) -
-            ((long long)t.Y[1] - t.Y[0]) * ((long long)t.X[2] - t.X[0]);
+    long long area2 = ((long long)t.X[1] - t.X[0]) * ((long long)t.Y[2] - t.Y[0]) -
+                      ((long long)t.Y[1] - t.Y[0]) * ((long long)t.X[2] - t.X[0]);
     e.af = (float)area2;
 }
 
-__device__ __forceinline__ void shade_px(const Tri& t, const Edges& e, int px, int py, const Band& bd) {
-    long long cx = 256LL * px + 128, cy = 256LL * py + 128;
-    long long E0 = e.A[0] * cx + e.B[0] * cy + e.C[0];
-    long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
-    long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
-    bool in = (E0 > 0 || (E0 == 0 && e.tl[0])) && (E1 > 0 || (E1 == 0 && e.tl[1])) &&
-              (E2 > 0 || (E2 == 0 && e.tl[2]));
-    if (!in) return;
-    float den = ((float)E0 * t.iz[0] + (float)E1 * t.iz[1]) + (float)E2 * t.iz[2];
-    float depth = e.af / den;
-    unsigned long long key = ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
-    int o = (py - bd.y0) * bd.W + px;
-    atomicMin(bd.z + o, key);
-    if (bd.count) atomicAdd(bd.count + o, 1u);
+__device__ __forceinline__ bool inside(long long E0, long long E1, long long E2, const Edges& e) {
+    return (E0 > 0 || (E0 == 0 && e.tl[0])) && (E1 > 0 || (E1 == 0 && e.tl[1])) && (E2 > 0 || (E2 == 0 && e.tl[2]));
 }
 
+__device__ __forceinline__ unsigned long long frag_key(long long E0, long long E1, long long E2, const Tri& t,
+                                                       const Edges& e) {
+    float den = ((float)E0 * t.iz[0] + (float)E1 * t.iz[1]) + (float)E2 * t.iz[2];
+    float depth = e.af / den;
+    return ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
+}
+
+// One thread rasterises a small triangle into the shared-memory z-buffer.
 __device__ __forceinline__ void raster_thread(const Tri& t, const Band& bd) {
     Edges e;
     edges(t, e);
-    for (int py = t.y0; py <= t.y1; py++)
-        for (int px = t.x0; px <= t.x1; px++) shade_px(t, e, px, py, bd);
-}
-
-// All threads of the CTA rasterise one triangle, striding over its bbox.
-__device__ __forceinline__ void raster_cta(const Tri& t, const Band& bd) {
-    Edges e;
-    edges(t, e);
-    int bw = t.x1 - t.x0 + 1;
-    int npx = bw * (t.y1 - t.y0 + 1);
-    int p = threadIdx.x;
-    if (p >= npx) return;
-    int oy = p / bw, ox = p - oy * bw;
-    const int qy = kThreads / bw, qx = kThreads - qy * bw;
-    for (; p < npx; p += kThreads) {
-        shade_px(t, e, t.x0 + ox, t.y0 + oy, bd);
-        ox += qx;
-        oy += qy;
-        if (ox >= bw) { ox -= bw; oy++; }
+    for (int py = t.y0; py <= t.y1; py++) {
+        long long cy = 256LL * py + 128;
+        long long cx = 256LL * t.x0 + 128;
+        long long E0 = e.A[0] * cx + e.B[0] * cy + e.C[0];
+        long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
+        long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
+        for (int px = t.x0; px <= t.x1; px++) {
+            if (inside(E0, E1, E2, e)) {
+                int o = (py - bd.y0) * bd.W + px;
+                atomicMin(bd.z + o, frag_key(E0, E1, E2, t, e));
+                if (bd.count) atomicAdd(bd.count + o, 1u);
+            }
+            E0 += e.A[0] * 256;
+            E1 += e.A[1] * 256;
+            E2 += e.A[2] * 256;
+        }
     }
 }
 
-struct Shared {
-    unsigned long long* z;
-    unsigned* count;
-    int* vX;
-    int* vY;
-    float* viz;
-    float* vw;        // [3][kVcap] world
-    int* vflag;       // 0 ok, else VUDA_FLAG_NEAR/GUARD
-    int* cb_v;        // [kChunkBodies+1] chunk-local vertex start per body
-    int* cb_t;        // [kChunkBodies+1] chunk-local triangle start per body
-    Tri* big;         // [kThreads]
-    int* nbig;
-    unsigned* flags;
+struct Bins {
+    Tri* rec;            // [kBigCap]
+    int* nrec;
+    int* cnt;            // [ntiles]
+    unsigned char* idx;  // [ntiles][kBigCap]
+    int tiles_x, ntiles;
 };
+
+// Bin a recorded triangle into the tiles its bbox overlaps.
+__device__ __forceinline__ void bin_tri(const Tri& t, int r, const Band& bd, Bins& bn) {
+    int tx0 = t.x0 / kTile, tx1 = t.x1 / kTile;
+    int ty0 = (t.y0 - bd.y0) / kTile, ty1 = (t.y1 - bd.y0) / kTile;
+    for (int ty = ty0; ty <= ty1; ty++)
+        for (int tx = tx0; tx <= tx1; tx++) {
+            int tile = ty * bn.tiles_x + tx;
+            int k = atomicAdd(bn.cnt + tile, 1);
+            bn.idx[tile * kBigCap + k] = (unsigned char)r;
+        }
+}
+
+// Tile pass: warp w walks tiles w, w + kWarps, ...; lane l owns pixels
+// (row l / 2, columns 8 (l % 2) .. +7) of the tile and keeps their keys in
+// registers while it walks the tile's bin.
+__device__ void tile_pass(const Band& bd, const Bins& bn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int tile = warp; tile < bn.ntiles; tile += kWarps) {
+        int n = bn.cnt[tile];
+        if (n == 0) continue;
+        int tx = tile % bn.tiles_x, ty = tile / bn.tiles_x;
+        int y = bd.y0 + ty * kTile + (lane >> 1);
+        int xs = tx * kTile + (lane & 1) * 8;
+        bool rowok = y < bd.y1;
+        int nx = rowok ? min(8, bd.W - xs) : 0;
+        unsigned long long key[8];
+        unsigned long long* zrow = bd.z + (size_t)(y - bd.y0) * bd.W + xs;
+#pragma unroll
+        for (int k = 0; k < 8; k++) key[k] = k < nx ? zrow[k] : ~0ULL;
+        unsigned cnt8[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) cnt8[k] = 0;
+        for (int q = 0; q < n; q++) {
+            const Tri& t = bn.rec[bn.idx[tile * kBigCap + q]];
+            if (nx <= 0 || y < t.y0 || y > t.y1 || xs + nx - 1 < t.x0 || xs > t.x1) continue;
+            Edges e;
+            edges(t, e);
+            long long cy = 256LL * y + 128;
+            long long cx = 256LL * xs + 128;
+            long long E0 = e.A[0] * cx + e.B[0] * cy + e.C[0];
+            long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
+            long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k < nx && inside(E0, E1, E2, e)) {
+                    unsigned long long kk = frag_key(E0, E1, E2, t, e);
+                    key[k] = kk < key[k] ? kk : key[k];
+                    cnt8[k]++;
+                }
+                E0 += e.A[0] * 256;
+                E1 += e.A[1] * 256;
+                E2 += e.A[2] * 256;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (k < nx) {
+                zrow[k] = key[k];
+                if (bd.count) bd.count[(size_t)(y - bd.y0) * bd.W + xs + k] += cnt8[k];
+            }
+    }
+}
 
 __device__ __forceinline__ void init_band(const Band& bd) {
     int n = (bd.y1 - bd.y0) * bd.W;
-    for (int i = threadIdx.x; i < n; i += kThreads) {
+    for (int i = threadIdx.x; i < n; i += kRT) {
         bd.z[i] = ~0ULL;
         if (bd.count) bd.count[i] = 0u;
     }
 }
 
-// Rasterise (per thread) one candidate triangle: small ones immediately,
-// large ones queued.  Then (CTA-wide) drain the queue.  Must be called by all
-// threads of the CTA.
-__device__ __forceinline__ void raster_batch(bool have, const Tri& t, const Band& bd, Shared& sh) {
+// Hand one candidate per thread to the small (thread-local) or binned path,
+// then run the tile pass.  Must be called by all threads of the CTA.
+__device__ __forceinline__ void raster_round(bool have, const Tri& t, const Band& bd, Bins& bn) {
     if (have) {
         int npx = (t.x1 - t.x0 + 1) * (t.y1 - t.y0 + 1);
-        if (npx <= kSmallPx) {
-            raster_thread(t, bd);
-        } else {
-            int k = atomicAdd(sh.nbig, 1);
-            sh.big[k] = t;
+        bool small = npx <= kSmallPx;
+        int r = -1;
+        if (!small) {
+            r = atomicAdd(bn.nrec, 1);
+            if (r < kBigCap) {
+                bn.rec[r] = t;
+                bin_tri(t, r, bd, bn);
+            }
         }
+        if (small || r >= kBigCap) raster_thread(t, bd);  // queue full: exact, just slower
     }
     __syncthreads();
-    int nb = *sh.nbig;
-    for (int k = 0; k < nb; k++) raster_cta(sh.big[k], bd);
-    __syncthreads();
-    if (threadIdx.x == 0) *sh.nbig = 0;
-    __syncthreads();
+    if (*bn.nrec > 0) {  // uniform after the barrier
+        tile_pass(bd, bn);
+        __syncthreads();
+        for (int i = threadIdx.x; i < bn.ntiles; i += kRT) bn.cnt[i] = 0;
+        if (threadIdx.x == 0) *bn.nrec = 0;
+        __syncthreads();
+    }
 }
 
 __device__ __forceinline__ void quat_mat(float w, float x, float y, float z, float* R) {
@@ -190,7 +251,7 @@ __device__ __forceinline__ void quat_mat(float w, float x, float y, float z, flo
     R[8] = 1.0f - 2.0f * (x * x + y * y);
 }
 
-__device__ __forceinline__ int upper_bound_smem(const int* a, int n, int v) {
+__device__ __forceinline__ int last_le(const int* a, int n, int v) {
     // largest k in [0, n) with a[k] <= v (a[0] = 0 <= v)
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -206,10 +267,24 @@ struct RenderArgs {
     vuda_frame fr;
     const int32_t* item_cam; // [items]
     const int32_t* item_y0;  // [items]
-    int band_rows;
+    int band_rows, max_w;
 };
 
-__global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
+__host__ __device__ inline int tiles_for(int rows, int W) {
+    return ((rows + kTile - 1) / kTile) * ((W + kTile - 1) / kTile);
+}
+
+__host__ __device__ inline size_t render_smem_bytes(int band_rows, int W) {
+    size_t s = (size_t)band_rows * W * 8;                        // z keys
+    s += sizeof(Tri) * kBigCap;                                  // binned triangles
+    s += (size_t)kVcap * (4 + 4 + 4 + 12 + 4);                   // vertex cache
+    s += (size_t)2 * 4 * (kChunkBodies + 2);                     // chunk tables
+    int nt = tiles_for(band_rows, W);
+    s += (size_t)nt * 4 + 16 + (size_t)nt * kBigCap;             // bins
+    return (s + 15) & ~(size_t)15;
+}
+
+__global__ void __launch_bounds__(kRT, 2) render_kernel(RenderArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevBatch& b = a.b;
     const int item = blockIdx.x;
@@ -222,20 +297,24 @@ __global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
     bd.y1 = min(H, bd.y0 + a.band_rows);
     bd.count = nullptr;
 
-    Shared sh;
     unsigned char* p = smem;
-    sh.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)a.band_rows * W * 8;
-    sh.big = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kThreads;
-    sh.vX = reinterpret_cast<int*>(p); p += 4 * kVcap;
-    sh.vY = reinterpret_cast<int*>(p); p += 4 * kVcap;
-    sh.viz = reinterpret_cast<float*>(p); p += 4 * kVcap;
-    sh.vw = reinterpret_cast<float*>(p); p += 12 * kVcap;
-    sh.vflag = reinterpret_cast<int*>(p); p += 4 * kVcap;
-    sh.cb_v = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
-    sh.cb_t = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
-    sh.nbig = reinterpret_cast<int*>(p); p += 4;
-    sh.flags = reinterpret_cast<unsigned*>(p); p += 4;
-    bd.z = sh.z;
+    bd.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)a.band_rows * a.max_w * 8;
+    Bins bn;
+    bn.rec = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kBigCap;
+    int* vX = reinterpret_cast<int*>(p); p += 4 * kVcap;
+    int* vY = reinterpret_cast<int*>(p); p += 4 * kVcap;
+    float* viz = reinterpret_cast<float*>(p); p += 4 * kVcap;
+    float* vw = reinterpret_cast<float*>(p); p += 12 * kVcap;
+    int* vflag = reinterpret_cast<int*>(p); p += 4 * kVcap;
+    int* cbv = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
+    int* cbt = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
+    bn.tiles_x = (W + kTile - 1) / kTile;
+    bn.ntiles = tiles_for(bd.y1 - bd.y0, W);
+    const int ntiles_max = tiles_for(a.band_rows, a.max_w);
+    bn.cnt = reinterpret_cast<int*>(p); p += 4 * (size_t)ntiles_max;
+    bn.nrec = reinterpret_cast<int*>(p); p += 4;
+    unsigned* sflags = reinterpret_cast<unsigned*>(p); p += 12;
+    bn.idx = p;
 
     const float* cp = b.cam_par + (size_t)cam * kCamWords;
     const float ex = cp[0], ey = cp[1], ez = cp[2];
@@ -246,41 +325,32 @@ __global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
     const float hw = (float)W * 0.5f, hh = (float)H * 0.5f;
     const int B = b.B;
     const int b0 = b.body_off[e];
-    const int nbody = b.body_off[e + 1] - b0;
     const int gm = b.ground_mesh;
-    const int Tg = b.mesh_tri_off[gm + 1] - b.mesh_tri_off[gm];
     uint32_t* colors = b.tri_color + b.env_tri_base[e];
 
-    if (threadIdx.x == 0) { *sh.nbig = 0; *sh.flags = 0u; }
+    if (threadIdx.x == 0) { *bn.nrec = 0; *sflags = 0u; }
+    for (int i = threadIdx.x; i < bn.ntiles; i += kRT) bn.cnt[i] = 0;
     init_band(bd);
-    __syncthreads();
 
-    uint32_t tri_base_running = 0;  // env-local triangle id of the chunk's first triangle
     for (int ck = b.chunk_off[e]; ck < b.chunk_off[e + 1]; ck++) {
-        const int cb0 = b.chunk_lo[ck], cb1 = b.chunk_hi[ck];  // env-local bodies, -1 = ground
-        const int nb = cb1 - cb0;
-        // chunk body table: vertex and triangle starts (prefix sums)
-        if (threadIdx.x == 0) {
-            int v = 0, t = 0;
-            for (int k = 0; k < nb; k++) {
-                int bi = cb0 + k;
-                int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
-                sh.cb_v[k] = v;
-                sh.cb_t[k] = t;
-                v += b.mesh_vert_off[m + 1] - b.mesh_vert_off[m];
-                t += b.mesh_tri_off[m + 1] - b.mesh_tri_off[m];
-            }
-            sh.cb_v[nb] = v;
-            sh.cb_t[nb] = t;
+        const int cb0 = b.chunk_lo[ck];   // env-local first body, -1 = ground
+        const int nb = b.chunk_hi[ck] - cb0;
+        const int2* tab = b.chunk_vt + b.chunk_tab_off[ck];
+        const uint32_t tri0 = (uint32_t)b.chunk_tri0[ck];
+        __syncthreads();  // previous chunk's readers of the tables are done
+        for (int k = threadIdx.x; k <= nb; k += kRT) {
+            int2 vt = tab[k];
+            cbv[k] = vt.x;
+            cbt[k] = vt.y;
         }
         __syncthreads();
-        const int nv = sh.cb_v[nb], nt = sh.cb_t[nb];
+        const int nv = cbv[nb], nt = cbt[nb];
         // 1. vertices
-        for (int v = threadIdx.x; v < nv; v += kThreads) {
-            int k = upper_bound_smem(sh.cb_v, nb, v);
+        for (int v = threadIdx.x; v < nv; v += kRT) {
+            int k = last_le(cbv, nb, v);
             int bi = cb0 + k;
             int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
-            const float* mv = b.mesh_verts + 3 * (size_t)(b.mesh_vert_off[m] + (v - sh.cb_v[k]));
+            const float* mv = b.mesh_verts + 3 * (size_t)(b.mesh_vert_off[m] + (v - cbv[k]));
             float wx, wy, wz;
             if (bi < 0) {
                 wx = mv[0]; wy = mv[1]; wz = mv[2];
@@ -296,7 +366,7 @@ __global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
                 wy = ty + a.pose[B + g];
                 wz = tz + a.pose[2 * B + g];
             }
-            sh.vw[v] = wx; sh.vw[kVcap + v] = wy; sh.vw[2 * kVcap + v] = wz;
+            vw[v] = wx; vw[kVcap + v] = wy; vw[2 * kVcap + v] = wz;
             float dx = wx - ex, dy = wy - ey, dz = wz - ez;
             float xc = (rx * dx + ry * dy) + rz * dz;
             float yc = (ux * dx + uy * dy) + uz * dz;
@@ -310,64 +380,64 @@ __global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
                 if (!(fabsf(sxp) < kGuard && fabsf(syp) < kGuard)) {
                     flag = VUDA_FLAG_GUARD_DISCARD;
                 } else {
-                    sh.vX[v] = __float2int_rn(sxp * 256.0f);
-                    sh.vY[v] = __float2int_rn(syp * 256.0f);
-                    sh.viz[v] = 1.0f / zc;
+                    vX[v] = __float2int_rn(sxp * 256.0f);
+                    vY[v] = __float2int_rn(syp * 256.0f);
+                    viz[v] = 1.0f / zc;
                 }
             }
-            sh.vflag[v] = flag;
+            vflag[v] = flag;
         }
         __syncthreads();
-        // 2-3. triangles, in batches of one per thread
-        for (int t0 = 0; t0 < nt; t0 += kThreads) {
+        // 2-3. triangles, one per thread per round
+        for (int t0 = 0; t0 < nt; t0 += kRT) {
             int t = t0 + threadIdx.x;
             bool have = false;
             Tri tri;
             if (t < nt) {
-                int k = upper_bound_smem(sh.cb_t, nb, t);
+                int k = last_le(cbt, nb, t);
                 int bi = cb0 + k;
                 int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
-                const int32_t* tv = b.mesh_tris + 3 * (size_t)(b.mesh_tri_off[m] + (t - sh.cb_t[k]));
-                int vb = sh.cb_v[k];
+                const int32_t* tv = b.mesh_tris + 3 * (size_t)(b.mesh_tri_off[m] + (t - cbt[k]));
+                int vb = cbv[k];
                 int i0 = vb + tv[0], i1 = vb + tv[1], i2 = vb + tv[2];
-                uint32_t id = tri_base_running + (uint32_t)t;
-                // flat colour from the world face normal
-                float e1x = sh.vw[i1] - sh.vw[i0], e1y = sh.vw[kVcap + i1] - sh.vw[kVcap + i0],
-                      e1z = sh.vw[2 * kVcap + i1] - sh.vw[2 * kVcap + i0];
-                float e2x = sh.vw[i2] - sh.vw[i0], e2y = sh.vw[kVcap + i2] - sh.vw[kVcap + i0],
-                      e2z = sh.vw[2 * kVcap + i2] - sh.vw[2 * kVcap + i0];
-                float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-                float len = sqrtf((nx * nx + ny * ny) + nz * nz);
-                float ndl = 0.0f;
-                if (len > 0.0f) ndl = ((nx / len) * b.light[0] + (ny / len) * b.light[1]) + (nz / len) * b.light[2];
-                float I = 0.2f + 0.8f * (ndl > 0.0f ? ndl : 0.0f);
-                uint32_t alb = bi < 0 ? b.ground_albedo : b.albedo[b0 + bi];
-                uint32_t col = 0;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    float av = (float)((alb >> (8 * c)) & 255u);
-                    int v = (int)(av * I + 0.5f);
-                    v = v > 255 ? 255 : v;
-                    col |= (uint32_t)v << (8 * c);
-                }
-                int fl = sh.vflag[i0] | sh.vflag[i1] | sh.vflag[i2];
+                int fl = vflag[i0] | vflag[i1] | vflag[i2];
                 if (fl) {
-                    atomicOr(sh.flags, (unsigned)fl);
+                    atomicOr(sflags, (unsigned)fl);
                 } else {
-                    int X[3] = {sh.vX[i0], sh.vX[i1], sh.vX[i2]};
-                    int Y[3] = {sh.vY[i0], sh.vY[i1], sh.vY[i2]};
-                    float iz[3] = {sh.viz[i0], sh.viz[i1], sh.viz[i2]};
+                    int X[3] = {vX[i0], vX[i1], vX[i2]};
+                    int Y[3] = {vY[i0], vY[i1], vY[i2]};
+                    float iz[3] = {viz[i0], viz[i1], viz[i2]};
+                    uint32_t id = tri0 + (uint32_t)t;
                     have = setup_tri(X, Y, iz, id, bd, tri);
-                    if (have) colors[id] = col;
+                    if (have) {
+                        // flat colour from the world face normal
+                        float e1x = vw[i1] - vw[i0], e1y = vw[kVcap + i1] - vw[kVcap + i0],
+                              e1z = vw[2 * kVcap + i1] - vw[2 * kVcap + i0];
+                        float e2x = vw[i2] - vw[i0], e2y = vw[kVcap + i2] - vw[kVcap + i0],
+                              e2z = vw[2 * kVcap + i2] - vw[2 * kVcap + i0];
+                        float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+                        float len = sqrtf((nx * nx + ny * ny) + nz * nz);
+                        float ndl = 0.0f;
+                        if (len > 0.0f)
+                            ndl = ((nx / len) * b.light[0] + (ny / len) * b.light[1]) + (nz / len) * b.light[2];
+                        float I = 0.2f + 0.8f * (ndl > 0.0f ? ndl : 0.0f);
+                        uint32_t alb = bi < 0 ? b.ground_albedo : b.albedo[b0 + bi];
+                        uint32_t col = 0;
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            float av = (float)((alb >> (8 * c)) & 255u);
+                            int vv = (int)(av * I + 0.5f);
+                            vv = vv > 255 ? 255 : vv;
+                            col |= (uint32_t)vv << (8 * c);
+                        }
+                        colors[id] = col;
+                    }
                 }
             }
-            raster_batch(have, tri, bd, sh);
+            raster_round(have, tri, bd, bn);
         }
-        tri_base_running += (uint32_t)nt;
-        __syncthreads();
     }
-    (void)Tg;
-    (void)nbody;
+    __syncthreads();
 
     // 4. resolve the band
     const int64_t pix0 = b.cam_pix_off[cam] + (int64_t)bd.y0 * W;
@@ -377,13 +447,13 @@ __global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
     uint32_t* tid = a.fr.triid ? a.fr.triid + pix0 : nullptr;
     const bool vec = ((pix0 & 3) == 0) && ((npx & 3) == 0);
     if (vec) {
-        for (int q = threadIdx.x; q < (npx >> 2); q += kThreads) {
+        for (int q = threadIdx.x; q < (npx >> 2); q += kRT) {
             float d4[4];
             uint32_t t4[4];
             uint32_t c4[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                unsigned long long key = sh.z[4 * q + j];
+                unsigned long long key = bd.z[4 * q + j];
                 if (key == ~0ULL) {
                     d4[j] = 0.0f; t4[j] = 0xFFFFFFFFu; c4[j] = 0u;
                 } else {
@@ -402,8 +472,8 @@ __global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
             r32[0] = w0; r32[1] = w1; r32[2] = w2;
         }
     } else {
-        for (int i = threadIdx.x; i < npx; i += kThreads) {
-            unsigned long long key = sh.z[i];
+        for (int i = threadIdx.x; i < npx; i += kRT) {
+            unsigned long long key = bd.z[i];
             uint32_t c = 0u;
             if (key == ~0ULL) {
                 dep[i] = 0.0f;
@@ -419,31 +489,35 @@ __global__ void __launch_bounds__(kThreads) render_kernel(RenderArgs a) {
             rgb[3 * i + 2] = (c >> 16) & 255u;
         }
     }
-    if (threadIdx.x == 0 && *sh.flags) atomicOr(b.flags + e, *sh.flags);
+    if (threadIdx.x == 0 && *sflags) atomicOr(b.flags + e, *sflags);
 }
 
 // Test hook: screen-space triangles, one CTA per band of the W x H image.
-__global__ void __launch_bounds__(kThreads) raster_screen_kernel(const int32_t* __restrict__ xy,
-                                                                 const float* __restrict__ z, int ntri, int W, int H,
-                                                                 int band_rows, uint32_t* triid, float* depth,
-                                                                 uint32_t* count) {
+__global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __restrict__ xy,
+                                                            const float* __restrict__ z, int ntri, int W, int H,
+                                                            int band_rows, uint32_t* triid, float* depth,
+                                                            uint32_t* count) {
     extern __shared__ __align__(16) unsigned char smem[];
     Band bd;
     bd.W = W;
     bd.y0 = blockIdx.x * band_rows;
     bd.y1 = min(H, bd.y0 + band_rows);
-    Shared sh;
     unsigned char* p = smem;
-    sh.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)band_rows * W * 8;
-    sh.count = reinterpret_cast<unsigned*>(p); p += (size_t)band_rows * W * 4;
-    sh.big = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kThreads;
-    sh.nbig = reinterpret_cast<int*>(p); p += 4;
-    bd.z = sh.z;
-    bd.count = count ? sh.count : nullptr;
-    if (threadIdx.x == 0) *sh.nbig = 0;
+    bd.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)band_rows * W * 8;
+    unsigned* scount = reinterpret_cast<unsigned*>(p); p += (size_t)band_rows * W * 4;
+    Bins bn;
+    bn.rec = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kBigCap;
+    bn.tiles_x = (W + kTile - 1) / kTile;
+    bn.ntiles = tiles_for(bd.y1 - bd.y0, W);
+    bn.cnt = reinterpret_cast<int*>(p); p += 4 * (size_t)tiles_for(band_rows, W);
+    bn.nrec = reinterpret_cast<int*>(p); p += 16;
+    bn.idx = p;
+    bd.count = count ? scount : nullptr;
+    if (threadIdx.x == 0) *bn.nrec = 0;
+    for (int i = threadIdx.x; i < bn.ntiles; i += kRT) bn.cnt[i] = 0;
     init_band(bd);
     __syncthreads();
-    for (int t0 = 0; t0 < ntri; t0 += kThreads) {
+    for (int t0 = 0; t0 < ntri; t0 += kRT) {
         int t = t0 + threadIdx.x;
         bool have = false;
         Tri tri;
@@ -458,12 +532,13 @@ __global__ void __launch_bounds__(kThreads) raster_screen_kernel(const int32_t* 
             }
             have = setup_tri(X, Y, iz, (uint32_t)t, bd, tri);
         }
-        raster_batch(have, tri, bd, sh);
+        raster_round(have, tri, bd, bn);
     }
+    __syncthreads();
     int npx = (bd.y1 - bd.y0) * W;
     int64_t o = (int64_t)bd.y0 * W;
-    for (int i = threadIdx.x; i < npx; i += kThreads) {
-        unsigned long long key = sh.z[i];
+    for (int i = threadIdx.x; i < npx; i += kRT) {
+        unsigned long long key = bd.z[i];
         if (key == ~0ULL) {
             triid[o + i] = 0xFFFFFFFFu;
             depth[o + i] = 0.0f;
@@ -471,13 +546,13 @@ __global__ void __launch_bounds__(kThreads) raster_screen_kernel(const int32_t* 
             triid[o + i] = (uint32_t)(key & 0xFFFFFFFFull);
             depth[o + i] = __uint_as_float((uint32_t)(key >> 32));
         }
-        if (count) count[o + i] = sh.count[i];
+        if (count) count[o + i] = scount[i];
     }
 }
 
-size_t render_smem_bytes(int band_rows, int W) {
-    size_t s = (size_t)band_rows * W * 8 + sizeof(Tri) * kThreads + (size_t)kVcap * (4 + 4 + 4 + 12 + 4) +
-               (size_t)2 * 4 * (kChunkBodies + 2) + 8;
+size_t screen_smem_bytes(int band_rows, int W) {
+    int nt = tiles_for(band_rows, W);
+    size_t s = (size_t)band_rows * W * 12 + sizeof(Tri) * kBigCap + (size_t)nt * 4 + 16 + (size_t)nt * kBigCap;
     return (s + 15) & ~(size_t)15;
 }
 
@@ -485,13 +560,21 @@ size_t render_smem_bytes(int band_rows, int W) {
 
 int render_vcap() { return kVcap; }
 int render_chunk_bodies() { return kChunkBodies; }
+size_t render_smem_for(int band_rows, int W) { return render_smem_bytes(band_rows, W); }
 
-// Work items (camera, first row) for a given band height; built by the host
-// and cached by the caller.
+int render_default_band_rows(int max_w, int max_h) {
+    // z-buffer of at most 64 KB per work item, in whole tiles
+    int rows = 8192 / max_w;
+    rows = rows >= kTile ? rows / kTile * kTile : (rows < 1 ? 1 : rows);
+    return rows > max_h ? max_h : rows;
+}
+
 cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda_frame& fr, const int32_t* item_cam,
                                 const int32_t* item_y0, int nitems, int band_rows, int max_w, cudaStream_t stream) {
     if (nitems == 0) return cudaSuccess;
     size_t smem = render_smem_bytes(band_rows, max_w);
+    // set on every launch: the attribute is tracked per context and the
+    // kernel may be launched into different (green) contexts
     cudaError_t err = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     RenderArgs a;
@@ -501,23 +584,22 @@ cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda
     a.item_cam = item_cam;
     a.item_y0 = item_y0;
     a.band_rows = band_rows;
-    render_kernel<<<nitems, kThreads, smem, stream>>>(a);
+    a.max_w = max_w;
+    render_kernel<<<nitems, kRT, smem, stream>>>(a);
     return cudaGetLastError();
 }
-
-size_t render_smem_for(int band_rows, int W) { return render_smem_bytes(band_rows, W); }
 
 cudaError_t launch_raster_screen(const int32_t* xy, const float* z, int ntri, int W, int H, uint32_t* triid,
                                  float* depth, uint32_t* count, cudaStream_t stream) {
     int band_rows = 4096 / W;
     if (band_rows < 1) band_rows = 1;
     if (band_rows > H) band_rows = H;
-    size_t smem = (size_t)band_rows * W * 12 + sizeof(Tri) * kThreads + 16;
+    size_t smem = screen_smem_bytes(band_rows, W);
     cudaError_t err =
         cudaFuncSetAttribute(raster_screen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int grid = (H + band_rows - 1) / band_rows;
-    raster_screen_kernel<<<grid, kThreads, smem, stream>>>(xy, z, ntri, W, H, band_rows, triid, depth, count);
+    raster_screen_kernel<<<grid, kRT, smem, stream>>>(xy, z, ntri, W, H, band_rows, triid, depth, count);
     return cudaGetLastError();
 }
 
