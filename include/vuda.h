@@ -269,6 +269,32 @@ vuda_status vuda_env_contact_counts(vuda_env_t env, int32_t* counts);
 vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t ntri, int32_t W, int32_t H,
                                     uint32_t* triid, float* depth, uint32_t* count, vuda_stream_t stream);
 
+/* Physics step that allocates no device memory, for callers that cannot
+ * allocate: code running inside a graph or stream region it does not own,
+ * plug-ins handed a fixed device arena by their host application, processes
+ * whose allocator belongs to another runtime.  The paper has no counterpart;
+ * the arithmetic is exactly vuda_sim_step's.
+ *   All arrays are caller-owned device memory with the layouts of vuda_scene
+ *   (body_off[E+1], SoA planes of length num_bodies); pos/quat/vel/angvel are
+ *   updated in place; pose[7][B] receives the final pose (xyz, wxyz);
+ *   flags[E] receives VUDA_FLAG_CONTACT_OVERFLOW bits by OR (clear it first);
+ *   ncontacts[E] the contact count of the last substep; force may be NULL.
+ *   max_bodies bounds body_off[e+1] - body_off[e]; smem_per_env 0 = default.
+ * Scratch (contact spill records and their per-environment offsets) lives in
+ * one fixed 16 MiB device array inside the library, held by every device that
+ * loads it until the process exits.  Batches needing more scratch
+ * (4 bytes x (2 (E + 1) rounded up to 64 + 26 x max_contacts_per_body x B))
+ * are rejected with VUDA_ERR_INVALID before anything is launched.  The first
+ * call on a device resolves the array's device address; make that first call
+ * before any stream capture.  Every call shares the array: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race and
+ * must be serialised by the caller.  Async on `stream`. */
+vuda_status vuda_sim_step_noalloc(int32_t num_envs, int32_t num_bodies, int32_t max_bodies, const int32_t* body_off,
+                                  float* pos, float* quat, float* vel, float* angvel, const uint8_t* shape_type,
+                                  const float* shape_dims, const float* inv_mass, const float* inv_inertia,
+                                  const float* force, const vuda_sim_params* params, int32_t nsteps, float* pose,
+                                  uint32_t* flags, int32_t* ncontacts, int32_t smem_per_env, vuda_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,8 @@ _sig("vuda_env_set_pose", [vp, C.c_int32, vp, vp])
 _sig("vuda_env_status", [vp, vp, vp, C.c_int32])
 _sig("vuda_env_contact_counts", [vp, vp])
 _sig("vuda_raster_screen_tris", [vp, vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp])
+_sig("vuda_sim_step_noalloc", [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                               C.POINTER(SimParams), C.c_int32, vp, vp, vp, C.c_int32, vp])
 
 
 class VudaError(RuntimeError):
@@ -358,3 +360,19 @@ def raster_screen_tris(xy, z, W: int, H: int, count: bool = False, stream=None):
                                       n, W, H, _dptr(tid), _dptr(dep), _dptr(cnt), _stream(stream)),
           "vuda_raster_screen_tris")
     return tid, dep, cnt
+
+
+def sim_step_noalloc(arrays: dict, params, nsteps: int, max_bodies: int, smem_per_env: int = 0, stream=None):
+    """Physics step on caller-owned device tensors without any device
+    allocation by the library (see vuda_sim_step_noalloc in vuda.h).
+    arrays: body_off, pos, quat, vel, angvel, shape_type, shape_dims,
+    inv_mass, inv_inertia, pose, flags, ncontacts (CUDA tensors) and an
+    optional force."""
+    E = int(arrays["body_off"].numel()) - 1
+    B = int(arrays["inv_mass"].numel())
+    prm = sim_params(params)
+    g = lambda k: _dptr(arrays.get(k))
+    check(lib.vuda_sim_step_noalloc(E, B, max_bodies, g("body_off"), g("pos"), g("quat"), g("vel"), g("angvel"),
+                                    g("shape_type"), g("shape_dims"), g("inv_mass"), g("inv_inertia"), g("force"),
+                                    C.byref(prm), nsteps, g("pose"), g("flags"), g("ncontacts"), smem_per_env,
+                                    _stream(stream)), "vuda_sim_step_noalloc")
