@@ -329,7 +329,7 @@ def main():
         "e2e": e2e,
         "roofline": roof,
         "cpu_baseline": cpu,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,   # sim_kernel, shade_kernel, render_kernel per step
         "status_flags": flags,
         "clocks": clk.summary(),
         "wall_s_coscheduled": wall_co,

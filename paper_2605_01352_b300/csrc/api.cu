@@ -348,6 +348,15 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         chunk_off[e + 1] = (int32_t)chunk_lo.size();
         env_tri_base[e + 1] = env_tri_base[e] + t_env;
     }
+    // first colour-table entry of every body: ground triangles first, then bodies in order
+    std::vector<int64_t> body_tri_base(std::max(B, 1), 0);
+    for (int e = 0; e < E; e++) {
+        int64_t t = env_tri_base[e] + Tg;
+        for (int bi = sc->body_off[e]; bi < sc->body_off[e + 1]; bi++) {
+            body_tri_base[bi] = t;
+            t += mesh_nt(sc->mesh_id[bi]);
+        }
+    }
     (void)Tg;
     (void)Vg;
     env->T = E ? env_tri_base[E] : 0;
@@ -417,6 +426,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     UP(chunk_tab_off, int32_t, chunk_tab_off.data(), chunk_tab_off.size());
     UP(chunk_vt, int2, chunk_vt.data(), chunk_vt.size());
     UP(chunk_tri0, int32_t, chunk_tri0.data(), chunk_tri0.size());
+    UP(body_tri_base, int64_t, body_tri_base.data(), body_tri_base.size());
     UP(spill_off, int64_t, spill_off.data(), E + 1);
     if (s == VUDA_OK) s = upload(env, &env->item_cam, item_cam.data(), item_cam.size());
     if (s == VUDA_OK) s = upload(env, &env->item_y0, item_y0.data(), item_y0.size());

@@ -49,6 +49,7 @@ struct DevBatch {
     const int64_t* cam_pix_off;   // [C+1]
     const int64_t* env_tri_base;  // [E] first triangle of env e in the colour scratch
     uint32_t* tri_color;          // [sum_e tris_e] colour scratch
+    const int64_t* body_tri_base; // [B] index in tri_color of body b's first triangle
     const int32_t* chunk_off;     // [E+1] render vertex-cache chunks of env e
     const int32_t* chunk_lo;      // [chunks] first env-local body of the chunk (-1 = ground quad)
     const int32_t* chunk_hi;      // [chunks] one past its last body

@@ -164,7 +164,7 @@ __device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int
 __device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.type[i] == kShapeBox; }
 
 constexpr int kT = 128;          // threads per environment (one CTA)
-constexpr int kPairChunk = 512;  // candidate pairs per round of the pair phase
+constexpr int kPairChunk = 256;  // candidate pairs per round of the pair phase
 
 // Plane contacts of body i: returns how many (write = false) or writes them
 // from index base (write = true).  Box corners in sign-bit order.
@@ -323,7 +323,7 @@ __device__ __forceinline__ void pair_of_index(int k, int N, int& i, int& j) {
     j = k - start(ii) + ii + 1;
 }
 
-__global__ void __launch_bounds__(kT) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
+__global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
                                                  int slot0, int smem_per_env, int NB) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int e = blockIdx.x;
@@ -564,9 +564,10 @@ __global__ void __launch_bounds__(kT) sim_kernel(DevBatch b, SimConst sc, int ns
                 float tl = sqrtf(dot3(t, t));
                 f3 t1{t.x / tl, t.y / tl, t.z / tl};
                 f3 t2 = cross3(n, t1);
-                float kN = eff_mass(S, a, bb, rA, rB, n);
-                float kT1 = eff_mass(S, a, bb, rA, rB, t1);
-                float kT2 = eff_mass(S, a, bb, rA, rB, t2);
+                // inverse effective masses, once per substep
+                float kN = 1.0f / eff_mass(S, a, bb, rA, rB, n);
+                float kT1 = 1.0f / eff_mass(S, a, bb, rA, rB, t1);
+                float kT2 = 1.0f / eff_mass(S, a, bb, rA, rB, t2);
                 float vn0 = dot3(n, rel_vel(S, a, bb, rA, rB));
                 float vmin;
                 if (d >= 0.0f) {
@@ -598,15 +599,15 @@ __global__ void __launch_bounds__(kT) sim_kernel(DevBatch b, SimConst sc, int ns
                     f3 vr = rel_vel(S, a, bb, ldc3(C, F_RA, c), ldc3(C, F_RB, c));
                     float vn = dot3(n, vr);
                     float ln = *C.f(F_LN, c);
-                    float dl = (*C.f(F_VMIN, c) - vn) / *C.f(F_KN, c);
+                    float dl = (*C.f(F_VMIN, c) - vn) * *C.f(F_KN, c);
                     float lnew = ln + dl;
                     if (!(lnew > 0.0f)) lnew = 0.0f;
                     float dln = lnew - ln;
                     *C.f(F_LN, c) = lnew;
                     float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
                     float l1 = *C.f(F_LT1, c), l2 = *C.f(F_LT2, c);
-                    float a1 = l1 - vt1 / *C.f(F_KT1, c);
-                    float a2 = l2 - vt2 / *C.f(F_KT2, c);
+                    float a1 = l1 - vt1 * *C.f(F_KT1, c);
+                    float a2 = l2 - vt2 * *C.f(F_KT2, c);
                     float lim = sc.mu * lnew;
                     float m2 = a1 * a1 + a2 * a2;
                     if (m2 > lim * lim) {
@@ -710,8 +711,10 @@ int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb) {
 
 int phys_smem_bytes_default(int max_bodies, int mcpb) {
     size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
-    // room for 6 contacts per body in shared memory, more spill to global
-    size_t want = fixed + (size_t)kContactWords * 4 * 6 * max_bodies;
+    // room for 5 contacts per body in shared memory (a settled pile of spheres
+    // and boxes has about 3.5), more spill to global memory; with 32 bodies
+    // this is 26 KB, so 8 environments fit on one SM
+    size_t want = fixed + (size_t)kContactWords * 4 * 5 * max_bodies;
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;
     return (int)align16(want);
@@ -725,6 +728,8 @@ cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const 
     // set on every launch: the attribute is tracked per context and the
     // kernel may be launched into different (green) contexts
     cudaError_t e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     sim_kernel<<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
     return cudaGetLastError();

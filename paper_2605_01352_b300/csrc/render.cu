@@ -31,12 +31,13 @@
 namespace vuda {
 namespace {
 
-constexpr int kRT = 512;           // threads per CTA
+constexpr int kRT = 256;           // threads per CTA
 constexpr int kWarps = kRT / 32;
 constexpr int kVcap = 1024;        // vertices per chunk
 constexpr int kChunkBodies = 128;  // bodies per chunk
 constexpr int kSmallPx = 16;       // triangles with at most this many bbox pixels stay thread-local
-constexpr int kBigCap = 128;       // binned triangles per round
+constexpr int kBigCap = 256;       // binned triangles per chunk pass
+constexpr int kMaskWords = kBigCap / 32;
 constexpr int kTile = 16;          // tile edge in pixels
 constexpr float kNear = 0.01f;
 constexpr float kGuard = 16384.0f;
@@ -137,8 +138,7 @@ __device__ __forceinline__ void raster_thread(const Tri& t, const Band& bd) {
 struct Bins {
     Tri* rec;            // [kBigCap]
     int* nrec;
-    int* cnt;            // [ntiles]
-    unsigned char* idx;  // [ntiles][kBigCap]
+    unsigned* mask;      // [ntiles][kMaskWords]: bit r set if record r overlaps the tile
     int tiles_x, ntiles;
 };
 
@@ -147,21 +147,22 @@ __device__ __forceinline__ void bin_tri(const Tri& t, int r, const Band& bd, Bin
     int tx0 = t.x0 / kTile, tx1 = t.x1 / kTile;
     int ty0 = (t.y0 - bd.y0) / kTile, ty1 = (t.y1 - bd.y0) / kTile;
     for (int ty = ty0; ty <= ty1; ty++)
-        for (int tx = tx0; tx <= tx1; tx++) {
-            int tile = ty * bn.tiles_x + tx;
-            int k = atomicAdd(bn.cnt + tile, 1);
-            bn.idx[tile * kBigCap + k] = (unsigned char)r;
-        }
+        for (int tx = tx0; tx <= tx1; tx++)
+            atomicOr(bn.mask + (ty * bn.tiles_x + tx) * kMaskWords + (r >> 5), 1u << (r & 31));
 }
 
 // Tile pass: warp w walks tiles w, w + kWarps, ...; lane l owns pixels
 // (row l / 2, columns 8 (l % 2) .. +7) of the tile and keeps their keys in
-// registers while it walks the tile's bin.
+// registers while it walks the tile's records (any order: the key minimum
+// does not depend on it).
 __device__ void tile_pass(const Band& bd, const Bins& bn) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int tile = warp; tile < bn.ntiles; tile += kWarps) {
-        int n = bn.cnt[tile];
-        if (n == 0) continue;
+        const unsigned* m = bn.mask + tile * kMaskWords;
+        unsigned any = 0;
+#pragma unroll
+        for (int w = 0; w < kMaskWords; w++) any |= m[w];
+        if (!any) continue;
         int tx = tile % bn.tiles_x, ty = tile / bn.tiles_x;
         int y = bd.y0 + ty * kTile + (lane >> 1);
         int xs = tx * kTile + (lane & 1) * 8;
@@ -174,26 +175,31 @@ __device__ void tile_pass(const Band& bd, const Bins& bn) {
         unsigned cnt8[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) cnt8[k] = 0;
-        for (int q = 0; q < n; q++) {
-            const Tri& t = bn.rec[bn.idx[tile * kBigCap + q]];
-            if (nx <= 0 || y < t.y0 || y > t.y1 || xs + nx - 1 < t.x0 || xs > t.x1) continue;
-            Edges e;
-            edges(t, e);
-            long long cy = 256LL * y + 128;
-            long long cx = 256LL * xs + 128;
-            long long E0 = e.A[0] * cx + e.B[0] * cy + e.C[0];
-            long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
-            long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
+        for (int w = 0; w < kMaskWords; w++) {
+            unsigned bits = m[w];
+            while (bits) {
+                int r = (w << 5) + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const Tri& t = bn.rec[r];
+                if (nx <= 0 || y < t.y0 || y > t.y1 || xs + nx - 1 < t.x0 || xs > t.x1) continue;
+                Edges e;
+                edges(t, e);
+                long long cy = 256LL * y + 128;
+                long long cx = 256LL * xs + 128;
+                long long E0 = e.A[0] * cx + e.B[0] * cy + e.C[0];
+                long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
+                long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                if (k < nx && inside(E0, E1, E2, e)) {
-                    unsigned long long kk = frag_key(E0, E1, E2, t, e);
-                    key[k] = kk < key[k] ? kk : key[k];
-                    cnt8[k]++;
+                for (int k = 0; k < 8; k++) {
+                    if (k < nx && inside(E0, E1, E2, e)) {
+                        unsigned long long kk = frag_key(E0, E1, E2, t, e);
+                        key[k] = kk < key[k] ? kk : key[k];
+                        cnt8[k]++;
+                    }
+                    E0 += e.A[0] * 256;
+                    E1 += e.A[1] * 256;
+                    E2 += e.A[2] * 256;
                 }
-                E0 += e.A[0] * 256;
-                E1 += e.A[1] * 256;
-                E2 += e.A[2] * 256;
             }
         }
 #pragma unroll
@@ -213,27 +219,29 @@ __device__ __forceinline__ void init_band(const Band& bd) {
     }
 }
 
-// Hand one candidate per thread to the small (thread-local) or binned path,
-// then run the tile pass.  Must be called by all threads of the CTA.
-__device__ __forceinline__ void raster_round(bool have, const Tri& t, const Band& bd, Bins& bn) {
-    if (have) {
-        int npx = (t.x1 - t.x0 + 1) * (t.y1 - t.y0 + 1);
-        bool small = npx <= kSmallPx;
-        int r = -1;
-        if (!small) {
-            r = atomicAdd(bn.nrec, 1);
-            if (r < kBigCap) {
-                bn.rec[r] = t;
-                bin_tri(t, r, bd, bn);
-            }
+// A visible triangle goes to the small (thread-local) path or is recorded
+// and binned; when the records are full it is rasterised by its thread
+// (exact either way, only slower).
+__device__ __forceinline__ void submit_tri(const Tri& t, const Band& bd, Bins& bn) {
+    int npx = (t.x1 - t.x0 + 1) * (t.y1 - t.y0 + 1);
+    if (npx > kSmallPx) {
+        int r = atomicAdd(bn.nrec, 1);
+        if (r < kBigCap) {
+            bn.rec[r] = t;
+            bin_tri(t, r, bd, bn);
+            return;
         }
-        if (small || r >= kBigCap) raster_thread(t, bd);  // queue full: exact, just slower
     }
-    __syncthreads();
+    raster_thread(t, bd);
+}
+
+// Rasterise the recorded triangles and clear the records.  Must be called by
+// all threads of the CTA, after a barrier that follows the last submit_tri.
+__device__ __forceinline__ void drain(const Band& bd, Bins& bn) {
     if (*bn.nrec > 0) {  // uniform after the barrier
         tile_pass(bd, bn);
         __syncthreads();
-        for (int i = threadIdx.x; i < bn.ntiles; i += kRT) bn.cnt[i] = 0;
+        for (int i = threadIdx.x; i < bn.ntiles * kMaskWords; i += kRT) bn.mask[i] = 0u;
         if (threadIdx.x == 0) *bn.nrec = 0;
         __syncthreads();
     }
@@ -277,14 +285,14 @@ __host__ __device__ inline int tiles_for(int rows, int W) {
 __host__ __device__ inline size_t render_smem_bytes(int band_rows, int W) {
     size_t s = (size_t)band_rows * W * 8;                        // z keys
     s += sizeof(Tri) * kBigCap;                                  // binned triangles
-    s += (size_t)kVcap * (4 + 4 + 4 + 12 + 4);                   // vertex cache
+    s += (size_t)kVcap * (4 + 4 + 4 + 4);                        // vertex cache
     s += (size_t)2 * 4 * (kChunkBodies + 2);                     // chunk tables
     int nt = tiles_for(band_rows, W);
-    s += (size_t)nt * 4 + 16 + (size_t)nt * kBigCap;             // bins
+    s += (size_t)nt * kMaskWords * 4 + 16;                       // tile masks, counters
     return (s + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(kRT, 2) render_kernel(RenderArgs a) {
+__global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevBatch& b = a.b;
     const int item = blockIdx.x;
@@ -304,17 +312,15 @@ __global__ void __launch_bounds__(kRT, 2) render_kernel(RenderArgs a) {
     int* vX = reinterpret_cast<int*>(p); p += 4 * kVcap;
     int* vY = reinterpret_cast<int*>(p); p += 4 * kVcap;
     float* viz = reinterpret_cast<float*>(p); p += 4 * kVcap;
-    float* vw = reinterpret_cast<float*>(p); p += 12 * kVcap;
     int* vflag = reinterpret_cast<int*>(p); p += 4 * kVcap;
     int* cbv = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
     int* cbt = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
     bn.tiles_x = (W + kTile - 1) / kTile;
     bn.ntiles = tiles_for(bd.y1 - bd.y0, W);
     const int ntiles_max = tiles_for(a.band_rows, a.max_w);
-    bn.cnt = reinterpret_cast<int*>(p); p += 4 * (size_t)ntiles_max;
+    bn.mask = reinterpret_cast<unsigned*>(p); p += 4 * (size_t)ntiles_max * kMaskWords;
     bn.nrec = reinterpret_cast<int*>(p); p += 4;
     unsigned* sflags = reinterpret_cast<unsigned*>(p); p += 12;
-    bn.idx = p;
 
     const float* cp = b.cam_par + (size_t)cam * kCamWords;
     const float ex = cp[0], ey = cp[1], ez = cp[2];
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(kRT, 2) render_kernel(RenderArgs a) {
     uint32_t* colors = b.tri_color + b.env_tri_base[e];
 
     if (threadIdx.x == 0) { *bn.nrec = 0; *sflags = 0u; }
-    for (int i = threadIdx.x; i < bn.ntiles; i += kRT) bn.cnt[i] = 0;
+    for (int i = threadIdx.x; i < bn.ntiles * kMaskWords; i += kRT) bn.mask[i] = 0u;
     init_band(bd);
 
     for (int ck = b.chunk_off[e]; ck < b.chunk_off[e + 1]; ck++) {
@@ -366,7 +372,6 @@ __global__ void __launch_bounds__(kRT, 2) render_kernel(RenderArgs a) {
                 wy = ty + a.pose[B + g];
                 wz = tz + a.pose[2 * B + g];
             }
-            vw[v] = wx; vw[kVcap + v] = wy; vw[2 * kVcap + v] = wz;
             float dx = wx - ex, dy = wy - ey, dz = wz - ez;
             float xc = (rx * dx + ry * dy) + rz * dz;
             float yc = (ux * dx + uy * dy) + uz * dz;
@@ -388,54 +393,28 @@ __global__ void __launch_bounds__(kRT, 2) render_kernel(RenderArgs a) {
             vflag[v] = flag;
         }
         __syncthreads();
-        // 2-3. triangles, one per thread per round
-        for (int t0 = 0; t0 < nt; t0 += kRT) {
-            int t = t0 + threadIdx.x;
-            bool have = false;
-            Tri tri;
-            if (t < nt) {
-                int k = last_le(cbt, nb, t);
-                int bi = cb0 + k;
-                int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
-                const int32_t* tv = b.mesh_tris + 3 * (size_t)(b.mesh_tri_off[m] + (t - cbt[k]));
-                int vb = cbv[k];
-                int i0 = vb + tv[0], i1 = vb + tv[1], i2 = vb + tv[2];
-                int fl = vflag[i0] | vflag[i1] | vflag[i2];
-                if (fl) {
-                    atomicOr(sflags, (unsigned)fl);
-                } else {
-                    int X[3] = {vX[i0], vX[i1], vX[i2]};
-                    int Y[3] = {vY[i0], vY[i1], vY[i2]};
-                    float iz[3] = {viz[i0], viz[i1], viz[i2]};
-                    uint32_t id = tri0 + (uint32_t)t;
-                    have = setup_tri(X, Y, iz, id, bd, tri);
-                    if (have) {
-                        // flat colour from the world face normal
-                        float e1x = vw[i1] - vw[i0], e1y = vw[kVcap + i1] - vw[kVcap + i0],
-                              e1z = vw[2 * kVcap + i1] - vw[2 * kVcap + i0];
-                        float e2x = vw[i2] - vw[i0], e2y = vw[kVcap + i2] - vw[kVcap + i0],
-                              e2z = vw[2 * kVcap + i2] - vw[2 * kVcap + i0];
-                        float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-                        float len = sqrtf((nx * nx + ny * ny) + nz * nz);
-                        float ndl = 0.0f;
-                        if (len > 0.0f)
-                            ndl = ((nx / len) * b.light[0] + (ny / len) * b.light[1]) + (nz / len) * b.light[2];
-                        float I = 0.2f + 0.8f * (ndl > 0.0f ? ndl : 0.0f);
-                        uint32_t alb = bi < 0 ? b.ground_albedo : b.albedo[b0 + bi];
-                        uint32_t col = 0;
-#pragma unroll
-                        for (int c = 0; c < 3; c++) {
-                            float av = (float)((alb >> (8 * c)) & 255u);
-                            int vv = (int)(av * I + 0.5f);
-                            vv = vv > 255 ? 255 : vv;
-                            col |= (uint32_t)vv << (8 * c);
-                        }
-                        colors[id] = col;
-                    }
-                }
+        // 2. triangles: strided over the CTA, no barrier until all are submitted
+        for (int t = threadIdx.x; t < nt; t += kRT) {
+            int k = last_le(cbt, nb, t);
+            int bi = cb0 + k;
+            int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
+            const int32_t* tv = b.mesh_tris + 3 * (size_t)(b.mesh_tri_off[m] + (t - cbt[k]));
+            int vb = cbv[k];
+            int i0 = vb + tv[0], i1 = vb + tv[1], i2 = vb + tv[2];
+            int fl = vflag[i0] | vflag[i1] | vflag[i2];
+            if (fl) {
+                atomicOr(sflags, (unsigned)fl);
+                continue;
             }
-            raster_round(have, tri, bd, bn);
+            int X[3] = {vX[i0], vX[i1], vX[i2]};
+            int Y[3] = {vY[i0], vY[i1], vY[i2]};
+            float iz[3] = {viz[i0], viz[i1], viz[i2]};
+            Tri tri;
+            if (setup_tri(X, Y, iz, tri0 + (uint32_t)t, bd, tri)) submit_tri(tri, bd, bn);
         }
+        __syncthreads();
+        // 3. binned triangles, tile by tile
+        drain(bd, bn);
     }
     __syncthreads();
 
@@ -492,7 +471,8 @@ __global__ void __launch_bounds__(kRT, 2) render_kernel(RenderArgs a) {
     if (threadIdx.x == 0 && *sflags) atomicOr(b.flags + e, *sflags);
 }
 
-// Test hook: screen-space triangles, one CTA per band of the W x H image.
+// Test hook: screen-space triangles, one CTA per band of the W x H image,
+// through the same submit / tile-pass path as render_kernel.
 __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __restrict__ xy,
                                                             const float* __restrict__ z, int ntri, int W, int H,
                                                             int band_rows, uint32_t* triid, float* depth,
@@ -509,19 +489,15 @@ __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __res
     bn.rec = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kBigCap;
     bn.tiles_x = (W + kTile - 1) / kTile;
     bn.ntiles = tiles_for(bd.y1 - bd.y0, W);
-    bn.cnt = reinterpret_cast<int*>(p); p += 4 * (size_t)tiles_for(band_rows, W);
-    bn.nrec = reinterpret_cast<int*>(p); p += 16;
-    bn.idx = p;
+    bn.mask = reinterpret_cast<unsigned*>(p); p += 4 * (size_t)tiles_for(band_rows, W) * kMaskWords;
+    bn.nrec = reinterpret_cast<int*>(p);
     bd.count = count ? scount : nullptr;
     if (threadIdx.x == 0) *bn.nrec = 0;
-    for (int i = threadIdx.x; i < bn.ntiles; i += kRT) bn.cnt[i] = 0;
+    for (int i = threadIdx.x; i < bn.ntiles * kMaskWords; i += kRT) bn.mask[i] = 0u;
     init_band(bd);
     __syncthreads();
-    for (int t0 = 0; t0 < ntri; t0 += kRT) {
-        int t = t0 + threadIdx.x;
-        bool have = false;
-        Tri tri;
-        if (t < ntri) {
+    for (int t0 = 0; t0 < ntri; t0 += kBigCap) {   // at most kBigCap submissions between drains
+        for (int t = t0 + threadIdx.x; t < min(ntri, t0 + kBigCap); t += kRT) {
             int X[3], Y[3];
             float iz[3];
 #pragma unroll
@@ -530,9 +506,11 @@ __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __res
                 Y[v] = xy[6 * t + 2 * v + 1];
                 iz[v] = 1.0f / z[3 * t + v];
             }
-            have = setup_tri(X, Y, iz, (uint32_t)t, bd, tri);
+            Tri tri;
+            if (setup_tri(X, Y, iz, (uint32_t)t, bd, tri)) submit_tri(tri, bd, bn);
         }
-        raster_round(have, tri, bd, bn);
+        __syncthreads();
+        drain(bd, bn);
     }
     __syncthreads();
     int npx = (bd.y1 - bd.y0) * W;
@@ -550,9 +528,74 @@ __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __res
     }
 }
 
+// Flat colour of every triangle from its world face normal (independent of
+// the camera, so computed once per step for all cameras).  One warp per unit:
+// units [0, B) are bodies, [B, B + E) the ground quads of the environments.
+__global__ void __launch_bounds__(256) shade_kernel(DevBatch b, const float* __restrict__ pose,
+                                                    const int64_t* __restrict__ body_tri_base) {
+    const int lane = threadIdx.x & 31;
+    const int unit = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int B = b.B;
+    if (unit >= B + b.E) return;
+    int m;
+    uint32_t alb;
+    uint32_t* out;
+    float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    float s0 = 1, s1 = 1, s2 = 1, p0 = 0, p1 = 0, p2 = 0;
+    bool body = unit < B;
+    if (body) {
+        const int g = unit;
+        m = b.mesh_id[g];
+        alb = b.albedo[g];
+        out = b.tri_color + body_tri_base[g];
+        quat_mat(pose[3 * B + g], pose[4 * B + g], pose[5 * B + g], pose[6 * B + g], R);
+        s0 = b.scale[g]; s1 = b.scale[B + g]; s2 = b.scale[2 * B + g];
+        p0 = pose[g]; p1 = pose[B + g]; p2 = pose[2 * B + g];
+    } else {
+        m = b.ground_mesh;
+        alb = b.ground_albedo;
+        out = b.tri_color + b.env_tri_base[unit - B];
+    }
+    const int t0 = b.mesh_tri_off[m], nt = b.mesh_tri_off[m + 1] - t0;
+    const float* mv = b.mesh_verts + 3 * (size_t)b.mesh_vert_off[m];
+    for (int t = lane; t < nt; t += 32) {
+        const int32_t* tv = b.mesh_tris + 3 * (size_t)(t0 + t);
+        float w[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float* v = mv + 3 * tv[k];
+            if (body) {
+                float sx = s0 * v[0], sy = s1 * v[1], sz = s2 * v[2];
+                float tx = (R[0] * sx + R[1] * sy) + R[2] * sz;
+                float ty = (R[3] * sx + R[4] * sy) + R[5] * sz;
+                float tz = (R[6] * sx + R[7] * sy) + R[8] * sz;
+                w[k][0] = tx + p0; w[k][1] = ty + p1; w[k][2] = tz + p2;
+            } else {
+                w[k][0] = v[0]; w[k][1] = v[1]; w[k][2] = v[2];
+            }
+        }
+        float e1x = w[1][0] - w[0][0], e1y = w[1][1] - w[0][1], e1z = w[1][2] - w[0][2];
+        float e2x = w[2][0] - w[0][0], e2y = w[2][1] - w[0][1], e2z = w[2][2] - w[0][2];
+        float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+        float len = sqrtf((nx * nx + ny * ny) + nz * nz);
+        float ndl = 0.0f;
+        if (len > 0.0f) ndl = ((nx / len) * b.light[0] + (ny / len) * b.light[1]) + (nz / len) * b.light[2];
+        float I = 0.2f + 0.8f * (ndl > 0.0f ? ndl : 0.0f);
+        uint32_t col = 0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float av = (float)((alb >> (8 * c)) & 255u);
+            int vv = (int)(av * I + 0.5f);
+            vv = vv > 255 ? 255 : vv;
+            col |= (uint32_t)vv << (8 * c);
+        }
+        out[t] = col;
+    }
+}
+
 size_t screen_smem_bytes(int band_rows, int W) {
     int nt = tiles_for(band_rows, W);
-    size_t s = (size_t)band_rows * W * 12 + sizeof(Tri) * kBigCap + (size_t)nt * 4 + 16 + (size_t)nt * kBigCap;
+    size_t s = (size_t)band_rows * W * 12 + sizeof(Tri) * kBigCap + (size_t)nt * kMaskWords * 4 + 16;
     return (s + 15) & ~(size_t)15;
 }
 
@@ -563,8 +606,8 @@ int render_chunk_bodies() { return kChunkBodies; }
 size_t render_smem_for(int band_rows, int W) { return render_smem_bytes(band_rows, W); }
 
 int render_default_band_rows(int max_w, int max_h) {
-    // z-buffer of at most 64 KB per work item, in whole tiles
-    int rows = 8192 / max_w;
+    // z-buffer of at most 32 KB per work item, in whole tiles
+    int rows = 4096 / max_w;
     rows = rows >= kTile ? rows / kTile * kTile : (rows < 1 ? 1 : rows);
     return rows > max_h ? max_h : rows;
 }
@@ -577,6 +620,12 @@ cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda
     // kernel may be launched into different (green) contexts
     cudaError_t err = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
+    if (b.B + b.E > 0) {
+        int units = b.B + b.E;
+        shade_kernel<<<(units * 32 + 255) / 256, 256, 0, stream>>>(b, pose, b.body_tri_base);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
     RenderArgs a;
     a.b = b;
     a.pose = pose;
