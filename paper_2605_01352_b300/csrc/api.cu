@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -314,8 +315,11 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     const int Tg = sc->mesh_tri_off[gm + 1] - sc->mesh_tri_off[gm];
     const int Vg = sc->mesh_vert_off[gm + 1] - sc->mesh_vert_off[gm];
     std::vector<int64_t> env_tri_base(E + 1, 0);
-    std::vector<int32_t> chunk_off(E + 1, 0), chunk_lo, chunk_hi, chunk_tab_off, chunk_tri0;
-    std::vector<int2> chunk_vt;
+    std::vector<int32_t> chunk_off(E + 1, 0), chunk_lo, chunk_hi, chunk_tri0, chunk_nv, chunk_nt, chunk_vtab,
+        chunk_ttab;
+    std::vector<int2> vtab;
+    std::vector<uint2> ttab;
+    std::map<std::vector<int>, std::pair<int32_t, int32_t>> tab_of;  // mesh sequence -> table offsets
     const int vcap = render_vcap(), cbmax = render_chunk_bodies();
     auto mesh_nv = [&](int m) { return sc->mesh_vert_off[m + 1] - sc->mesh_vert_off[m]; };
     auto mesh_nt = [&](int m) { return sc->mesh_tri_off[m + 1] - sc->mesh_tri_off[m]; };
@@ -326,28 +330,43 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         int lo = -1;
         while (lo < nbody) {
             // grow the chunk [lo, hi) while its vertices fit the cache
-            int hi = lo, nv = 0;
+            int hi = lo, nv = 0, nt = 0;
+            std::vector<int> seq;
             while (hi < nbody && hi - lo < cbmax && nv + mesh_nv(body_mesh(hi)) <= vcap) {
                 nv += mesh_nv(body_mesh(hi));
+                nt += mesh_nt(body_mesh(hi));
+                seq.push_back(body_mesh(hi));
                 hi++;
+            }
+            auto it = tab_of.find(seq);
+            if (it == tab_of.end()) {
+                std::pair<int32_t, int32_t> off((int32_t)vtab.size(), (int32_t)ttab.size());
+                int vb = 0;
+                for (size_t k = 0; k < seq.size(); k++) {
+                    int m = seq[k];
+                    for (int v = 0; v < mesh_nv(m); v++) vtab.push_back(make_int2(sc->mesh_vert_off[m] + v, (int)k));
+                    for (int t = sc->mesh_tri_off[m]; t < sc->mesh_tri_off[m + 1]; t++)
+                        ttab.push_back(make_uint2((unsigned)(vb + sc->mesh_tris[3 * t]) |
+                                                      ((unsigned)(vb + sc->mesh_tris[3 * t + 1]) << 16),
+                                                  (unsigned)(vb + sc->mesh_tris[3 * t + 2])));
+                    vb += mesh_nv(m);
+                }
+                it = tab_of.emplace(seq, off).first;
             }
             chunk_lo.push_back(lo);
             chunk_hi.push_back(hi);
-            chunk_tab_off.push_back((int32_t)chunk_vt.size());
             chunk_tri0.push_back((int32_t)t_env);
-            int v = 0, t = 0;
-            for (int bi = lo; bi < hi; bi++) {
-                chunk_vt.push_back(make_int2(v, t));
-                v += mesh_nv(body_mesh(bi));
-                t += mesh_nt(body_mesh(bi));
-            }
-            chunk_vt.push_back(make_int2(v, t));
-            t_env += t;
+            chunk_nv.push_back(nv);
+            chunk_nt.push_back(nt);
+            chunk_vtab.push_back(it->second.first);
+            chunk_ttab.push_back(it->second.second);
+            t_env += nt;
             lo = hi;
         }
         chunk_off[e + 1] = (int32_t)chunk_lo.size();
         env_tri_base[e + 1] = env_tri_base[e] + t_env;
     }
+    (void)Vg;
     // first colour-table entry of every body: ground triangles first, then bodies in order
     std::vector<int64_t> body_tri_base(std::max(B, 1), 0);
     for (int e = 0; e < E; e++) {
@@ -423,9 +442,13 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     UP(chunk_off, int32_t, chunk_off.data(), E + 1);
     UP(chunk_lo, int32_t, chunk_lo.data(), chunk_lo.size());
     UP(chunk_hi, int32_t, chunk_hi.data(), chunk_hi.size());
-    UP(chunk_tab_off, int32_t, chunk_tab_off.data(), chunk_tab_off.size());
-    UP(chunk_vt, int2, chunk_vt.data(), chunk_vt.size());
     UP(chunk_tri0, int32_t, chunk_tri0.data(), chunk_tri0.size());
+    UP(chunk_nv, int32_t, chunk_nv.data(), chunk_nv.size());
+    UP(chunk_nt, int32_t, chunk_nt.data(), chunk_nt.size());
+    UP(chunk_vtab, int32_t, chunk_vtab.data(), chunk_vtab.size());
+    UP(chunk_ttab, int32_t, chunk_ttab.data(), chunk_ttab.size());
+    UP(vtab, int2, vtab.data(), vtab.size());
+    UP(ttab, uint2, ttab.data(), ttab.size());
     UP(body_tri_base, int64_t, body_tri_base.data(), body_tri_base.size());
     UP(spill_off, int64_t, spill_off.data(), E + 1);
     if (s == VUDA_OK) s = upload(env, &env->item_cam, item_cam.data(), item_cam.size());

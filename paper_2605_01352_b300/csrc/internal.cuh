@@ -53,9 +53,14 @@ struct DevBatch {
     const int32_t* chunk_off;     // [E+1] render vertex-cache chunks of env e
     const int32_t* chunk_lo;      // [chunks] first env-local body of the chunk (-1 = ground quad)
     const int32_t* chunk_hi;      // [chunks] one past its last body
-    const int32_t* chunk_tab_off; // [chunks] first entry of the chunk in chunk_vt
-    const int2* chunk_vt;         // per chunk, per body k = 0..nb: (first vertex, first triangle), chunk-local
     const int32_t* chunk_tri0;    // [chunks] env-local id of the chunk's first triangle
+    const int32_t* chunk_nv;      // [chunks] vertices of the chunk
+    const int32_t* chunk_nt;      // [chunks] triangles of the chunk
+    const int32_t* chunk_vtab;    // [chunks] first entry of the chunk's vertex table in vtab
+    const int32_t* chunk_ttab;    // [chunks] first entry of the chunk's triangle table in ttab
+    const int2* vtab;             // vertex v of a chunk: (mesh_verts index, body index k within the chunk)
+    const uint2* ttab;            // triangle t of a chunk: chunk-local vertices (i0 | i1 << 16, i2)
+    // vtab / ttab entries are shared by every chunk with the same sequence of meshes
     float light[3];
 };
 
@@ -67,7 +72,7 @@ struct SimConst {
     int plane, mcpb;
 };
 
-constexpr int kContactWords = 26;  // floats per contact record
+constexpr int kContactWords = 32;  // floats per contact record
 constexpr int kCamWords = 13;
 
 // Launchers (physics.cu, render.cu)

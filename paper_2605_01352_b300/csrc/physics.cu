@@ -35,9 +35,19 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 // Field indices of a contact record (kContactWords floats).
+// KN, KT1, KT2 hold inverse effective masses; P is the impulse of the
+// current iteration, LA = rA x P and LB = rB x P its angular parts.
 enum : int {
     F_AB = 0, F_N = 1, F_RA = 4, F_RB = 7, F_T1 = 10, F_T2 = 13, F_KN = 16, F_KT1 = 17, F_KT2 = 18,
-    F_VMIN = 19, F_LN = 20, F_LT1 = 21, F_LT2 = 22, F_P = 23
+    F_VMIN = 19, F_LN = 20, F_LT1 = 21, F_LT2 = 22, F_P = 23, F_LA = 26, F_LB = 29
+};
+static_assert(F_LB + 3 == kContactWords, "contact record layout");
+
+// One contact record: field f at p[f * stride].
+struct Rec {
+    float* p;
+    int stride;
+    __device__ __forceinline__ float& operator[](int f) const { return p[f * stride]; }
 };
 
 struct Contacts {
@@ -45,8 +55,8 @@ struct Contacts {
     int cap;        // records in shared memory
     float* g;       // global spill SoA, stride gstride (record c at c - cap)
     int gstride;
-    __device__ __forceinline__ float* f(int field, int c) const {
-        return c < cap ? s + field * cap + c : g + (size_t)field * gstride + (c - cap);
+    __device__ __forceinline__ Rec rec(int c) const {
+        return c < cap ? Rec{s + c, cap} : Rec{g + (c - cap), gstride};
     }
 };
 
@@ -103,10 +113,11 @@ __device__ __forceinline__ f3 box_corner(const Bodies& B, int i, int k) {
 }
 
 __device__ __forceinline__ void put_contact(const Contacts& C, int c, int a, int b, f3 n, f3 p, float d) {
-    *C.f(F_AB, c) = __int_as_float(a | ((b + 1) << 16));
-    *C.f(F_N, c) = n.x; *C.f(F_N + 1, c) = n.y; *C.f(F_N + 2, c) = n.z;
-    *C.f(F_RA, c) = p.x; *C.f(F_RA + 1, c) = p.y; *C.f(F_RA + 2, c) = p.z;  // point, converted later
-    *C.f(F_VMIN, c) = d;                                                     // distance, converted later
+    Rec r = C.rec(c);
+    r[F_AB] = __int_as_float(a | ((b + 1) << 16));
+    r[F_N] = n.x; r[F_N + 1] = n.y; r[F_N + 2] = n.z;
+    r[F_RA] = p.x; r[F_RA + 1] = p.y; r[F_RA + 2] = p.z;  // point, converted later
+    r[F_VMIN] = d;                                          // distance, converted later
 }
 
 // Sphere s against box x: normal from the box to the sphere, point on the box, distance.
@@ -165,37 +176,6 @@ __device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.type[i
 
 constexpr int kT = 128;          // threads per environment (one CTA)
 constexpr int kPairChunk = 256;  // candidate pairs per round of the pair phase
-
-// Plane contacts of body i: returns how many (write = false) or writes them
-// from index base (write = true).  Box corners in sign-bit order.
-__device__ int plane_contacts(const Bodies& B, int i, float margin, bool write, const Contacts& C, int base,
-                              int cmax, bool& ovf) {
-    int k0 = 0;
-    const f3 up{0.0f, 0.0f, 1.0f};
-    if (is_box(B, i)) {
-        for (int k = 0; k < 8; k++) {
-            f3 c = box_corner(B, i, k);
-            if (c.z < margin) {
-                if (write) {
-                    int idx = base + k0;
-                    if (idx < cmax) put_contact(C, idx, i, -1, up, c, c.z); else ovf = true;
-                }
-                k0++;
-            }
-        }
-    } else {
-        float r = B.D(0, i);
-        f3 p = ldpos(B, i);
-        float d = p.z - r;
-        if (d < margin) {
-            if (write) {
-                if (base < cmax) put_contact(C, base, i, -1, up, f3{p.x, p.y, p.z - r}, d); else ovf = true;
-            }
-            k0 = 1;
-        }
-    }
-    return k0;
-}
 
 __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margin) {
     f3 dx = sub3(ldpos(B, i), ldpos(B, j));
@@ -265,14 +245,17 @@ __device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
     return off + x - v;
 }
 
-__device__ __forceinline__ void unpack_ab(const Contacts& C, int c, int& a, int& b) {
-    int ab = __float_as_int(*C.f(F_AB, c));
+__device__ __forceinline__ void unpack_ab(const Rec& r, int& a, int& b) {
+    int ab = __float_as_int(r[F_AB]);
     a = ab & 0xffff;
     b = (ab >> 16) - 1;
 }
 
-__device__ __forceinline__ f3 ldc3(const Contacts& C, int field, int c) {
-    return f3{*C.f(field, c), *C.f(field + 1, c), *C.f(field + 2, c)};
+__device__ __forceinline__ f3 ld3(const Rec& r, int field) { return f3{r[field], r[field + 1], r[field + 2]}; }
+__device__ __forceinline__ void st3(const Rec& r, int field, f3 v) {
+    r[field] = v.x;
+    r[field + 1] = v.y;
+    r[field + 2] = v.z;
 }
 
 // mass-split effective mass along dir
@@ -300,12 +283,12 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 
 // Bytes of per-env shared memory before the contact records.
 __host__ __device__ inline size_t phys_fixed_bytes(int NB, int cmax) {
-    size_t f = (size_t)39 * NB * 4;          // float body planes
+    size_t f = (size_t)45 * NB * 4;          // float body planes (incl. 6 planes of per-body sums)
     f += (size_t)(3 * NB + 1) * 4;           // type, ncb, loff[NB+1]
     f += (size_t)4 * NB * 4;                 // per-quarter list counters
     f += (size_t)2 * kPairChunk * 4;         // passing pairs and their item prefix
     f += (size_t)8 * 4;                      // scan scratch
-    f += (size_t)2 * cmax * 2;               // per-body contact lists (int16)
+    f += (size_t)2 * cmax * 2;               // per-body contact lists (u16: contact << 1 | side)
     return align16(f);
 }
 
@@ -323,8 +306,12 @@ __device__ __forceinline__ void pair_of_index(int k, int N, int& i, int& j) {
     j = k - start(ii) + ii + 1;
 }
 
-__global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
-                                                 int slot0, int smem_per_env, int NB) {
+// Ordered expansion over the CTA: each thread offers `nsub` sub-items for its
+// unit; returns the exclusive item prefix and the total (block scan).
+// Items are later tested one per thread and their hits compacted in order.
+
+__global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
+                                                    int slot0, int smem_per_env, int NB) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int e = blockIdx.x;
     const int tid = threadIdx.x;
@@ -348,15 +335,16 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
     S.brad = fp; fp += NB;
     S.R = fp; fp += 9 * NB;
     S.Iw = fp; fp += 9 * NB;
+    float* acc = fp; fp += 6 * NB;       // per-body impulse sums (P xyz, L xyz) of one iteration
     int* ip = reinterpret_cast<int*>(fp);
     S.type = ip; ip += NB;
     S.ncb = ip; ip += NB;
     S.loff = ip; ip += NB + 1;
     int* qcnt = ip; ip += 4 * NB;        // [4][NB] contacts of each body in each quarter of the list
-    int* plist = ip; ip += kPairChunk;   // passing pairs (i | j << 16)
-    int* pitem = ip; ip += kPairChunk;   // first narrow-phase item of each passing pair
+    int* plist = ip; ip += kPairChunk;   // units (passing pairs or plane bodies) of the current round
+    int* pitem = ip; ip += kPairChunk;   // first narrow-phase item of each unit
     int* wsum = ip; ip += 8;
-    short* lists = reinterpret_cast<short*>(ip);
+    unsigned short* lists = reinterpret_cast<unsigned short*>(ip);
     const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
     Contacts C;
     C.s = reinterpret_cast<float*>(smem + fixed);
@@ -392,6 +380,7 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
     int nc = 0;
     const float h = sc.h;
     const int npairs = N * (N - 1) / 2;
+    const f3 up{0.0f, 0.0f, 1.0f};
     for (int step = 0; step < nsteps; step++) {
         for (int ss = 0; ss < sc.substeps; ss++) {
             // 1. velocities, rotation, world inverse inertia
@@ -425,16 +414,54 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
             }
             __syncthreads();
 
-            // 2a. plane contacts, bodies in order
+            // 2a. plane contacts: units = bodies in order, one item per sphere,
+            // eight per box (its corners in sign-bit order)
             nc = 0;
             if (sc.plane) {
                 for (int i0 = 0; i0 < N; i0 += kT) {
                     int i = i0 + tid;
-                    int cnt = i < N ? plane_contacts(S, i, sc.margin, false, C, 0, cmax, ovf) : 0;
+                    int nsub = i < N ? (is_box(S, i) ? 8 : 1) : 0;
                     int tot;
-                    int ex = block_excl_scan(cnt, wsum, tot);
-                    if (cnt) plane_contacts(S, i, sc.margin, true, C, nc + ex, cmax, ovf);
-                    nc += tot;
+                    int ex = block_excl_scan(nsub, wsum, tot);
+                    if (nsub) {
+                        plist[tid] = i;
+                        pitem[tid] = ex;
+                    }
+                    const int nu = min(kT, N - i0);
+                    __syncthreads();
+                    for (int u0 = 0; u0 < tot; u0 += kT) {
+                        int u = u0 + tid;
+                        bool hit = false;
+                        int bi = 0;
+                        f3 pt{0.0f, 0.0f, 0.0f};
+                        float d = 0.0f;
+                        if (u < tot) {
+                            int lo = 0, hi = nu - 1;
+                            while (lo < hi) {
+                                int mid = (lo + hi + 1) >> 1;
+                                if (pitem[mid] <= u) lo = mid; else hi = mid - 1;
+                            }
+                            bi = plist[lo];
+                            int k = u - pitem[lo];
+                            if (is_box(S, bi)) {
+                                pt = box_corner(S, bi, k);
+                                d = pt.z;
+                            } else {
+                                float r = S.D(0, bi);
+                                f3 p = ldpos(S, bi);
+                                d = p.z - r;
+                                pt = f3{p.x, p.y, p.z - r};
+                            }
+                            hit = d < sc.margin;
+                        }
+                        int t2;
+                        int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
+                        if (hit) {
+                            int idx = nc + ex2;
+                            if (idx < cmax) put_contact(C, idx, bi, -1, up, pt, d); else ovf = true;
+                        }
+                        nc += t2;
+                    }
                 }
             }
             // 2b. pairs in (i, j) order, kPairChunk candidates per round
@@ -505,13 +532,14 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
             }
             if (nc > cmax) nc = cmax;
 
-            // contacts per body, and per-body lists in ascending contact order
+            // contacts per body, and per-body lists (contact << 1 | side) in
+            // ascending contact order
             for (int i = tid; i < 4 * N; i += kT) qcnt[(i / N) * NB + (i % N)] = 0;
             __syncthreads();
             const int qlen = (nc + 3) / 4;
             for (int c = tid; c < nc; c += kT) {
                 int a, bb;
-                unpack_ab(C, c, a, bb);
+                unpack_ab(C.rec(c), a, bb);
                 int q = c / qlen;
                 atomicAdd(qcnt + q * NB + a, 1);
                 if (bb >= 0) atomicAdd(qcnt + q * NB + bb, 1);
@@ -543,8 +571,9 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
                     int cend = min(nc, (warp + 1) * qlen);
                     for (int c = warp * qlen; c < cend; c++) {
                         int a, bb;
-                        unpack_ab(C, c, a, bb);
-                        if (a == i || bb == i) lists[o++] = (short)c;
+                        unpack_ab(C.rec(c), a, bb);
+                        if (a == i) lists[o++] = (unsigned short)(c << 1);
+                        else if (bb == i) lists[o++] = (unsigned short)((c << 1) | 1);
                     }
                 }
             }
@@ -552,11 +581,12 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
 
             // 3. per-contact constants
             for (int c = tid; c < nc; c += kT) {
+                Rec r = C.rec(c);
                 int a, bb;
-                unpack_ab(C, c, a, bb);
-                f3 n = ldc3(C, F_N, c);
-                f3 pt = ldc3(C, F_RA, c);
-                float d = *C.f(F_VMIN, c);
+                unpack_ab(r, a, bb);
+                f3 n = ld3(r, F_N);
+                f3 pt = ld3(r, F_RA);
+                float d = r[F_VMIN];
                 f3 rA = sub3(pt, ldpos(S, a));
                 f3 rB = bb >= 0 ? sub3(pt, ldpos(S, bb)) : f3{0.0f, 0.0f, 0.0f};
                 f3 ex = fabsf(n.x) < 0.9f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
@@ -580,34 +610,36 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
                     float vb = -sc.restitution * vn0;
                     if (vb > vmin) vmin = vb;
                 }
-                *C.f(F_RA, c) = rA.x; *C.f(F_RA + 1, c) = rA.y; *C.f(F_RA + 2, c) = rA.z;
-                *C.f(F_RB, c) = rB.x; *C.f(F_RB + 1, c) = rB.y; *C.f(F_RB + 2, c) = rB.z;
-                *C.f(F_T1, c) = t1.x; *C.f(F_T1 + 1, c) = t1.y; *C.f(F_T1 + 2, c) = t1.z;
-                *C.f(F_T2, c) = t2.x; *C.f(F_T2 + 1, c) = t2.y; *C.f(F_T2 + 2, c) = t2.z;
-                *C.f(F_KN, c) = kN; *C.f(F_KT1, c) = kT1; *C.f(F_KT2, c) = kT2;
-                *C.f(F_VMIN, c) = vmin;
-                *C.f(F_LN, c) = 0.0f; *C.f(F_LT1, c) = 0.0f; *C.f(F_LT2, c) = 0.0f;
+                st3(r, F_RA, rA);
+                st3(r, F_RB, rB);
+                st3(r, F_T1, t1);
+                st3(r, F_T2, t2);
+                r[F_KN] = kN; r[F_KT1] = kT1; r[F_KT2] = kT2;
+                r[F_VMIN] = vmin;
+                r[F_LN] = 0.0f; r[F_LT1] = 0.0f; r[F_LT2] = 0.0f;
             }
             __syncthreads();
 
             // 4. Jacobi iterations
             for (int it = 0; it < sc.iterations; it++) {
                 for (int c = tid; c < nc; c += kT) {
+                    Rec r = C.rec(c);
                     int a, bb;
-                    unpack_ab(C, c, a, bb);
-                    f3 n = ldc3(C, F_N, c), t1 = ldc3(C, F_T1, c), t2 = ldc3(C, F_T2, c);
-                    f3 vr = rel_vel(S, a, bb, ldc3(C, F_RA, c), ldc3(C, F_RB, c));
+                    unpack_ab(r, a, bb);
+                    f3 n = ld3(r, F_N), t1 = ld3(r, F_T1), t2 = ld3(r, F_T2);
+                    f3 rA = ld3(r, F_RA), rB = ld3(r, F_RB);
+                    f3 vr = rel_vel(S, a, bb, rA, rB);
                     float vn = dot3(n, vr);
-                    float ln = *C.f(F_LN, c);
-                    float dl = (*C.f(F_VMIN, c) - vn) * *C.f(F_KN, c);
+                    float ln = r[F_LN];
+                    float dl = (r[F_VMIN] - vn) * r[F_KN];
                     float lnew = ln + dl;
                     if (!(lnew > 0.0f)) lnew = 0.0f;
                     float dln = lnew - ln;
-                    *C.f(F_LN, c) = lnew;
+                    r[F_LN] = lnew;
                     float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
-                    float l1 = *C.f(F_LT1, c), l2 = *C.f(F_LT2, c);
-                    float a1 = l1 - vt1 * *C.f(F_KT1, c);
-                    float a2 = l2 - vt2 * *C.f(F_KT2, c);
+                    float l1 = r[F_LT1], l2 = r[F_LT2];
+                    float a1 = l1 - vt1 * r[F_KT1];
+                    float a2 = l2 - vt2 * r[F_KT2];
                     float lim = sc.mu * lnew;
                     float m2 = a1 * a1 + a2 * a2;
                     if (m2 > lim * lim) {
@@ -616,30 +648,43 @@ __global__ void __launch_bounds__(kT, 8) sim_kernel(DevBatch b, SimConst sc, int
                         a2 = a2 * s;
                     }
                     float dl1 = a1 - l1, dl2 = a2 - l2;
-                    *C.f(F_LT1, c) = a1;
-                    *C.f(F_LT2, c) = a2;
-                    *C.f(F_P, c) = (dln * n.x + dl1 * t1.x) + dl2 * t2.x;
-                    *C.f(F_P + 1, c) = (dln * n.y + dl1 * t1.y) + dl2 * t2.y;
-                    *C.f(F_P + 2, c) = (dln * n.z + dl1 * t1.z) + dl2 * t2.z;
+                    r[F_LT1] = a1;
+                    r[F_LT2] = a2;
+                    f3 P{(dln * n.x + dl1 * t1.x) + dl2 * t2.x, (dln * n.y + dl1 * t1.y) + dl2 * t2.y,
+                         (dln * n.z + dl1 * t1.z) + dl2 * t2.z};
+                    st3(r, F_P, P);
+                    st3(r, F_LA, cross3(rA, P));
+                    if (bb >= 0) st3(r, F_LB, cross3(rB, P));
+                }
+                __syncthreads();
+                // per-body sums in ascending contact order; the six components
+                // are independent sums, two per thread, in warps 0..2
+                if (warp < 3) {
+                    const int q0 = 2 * warp;
+                    for (int i0 = 0; i0 < N; i0 += 32) {
+                        int i = i0 + lane;
+                        if (i < N) {
+                            float s0 = 0.0f, s1 = 0.0f;
+                            for (int k = S.loff[i]; k < S.loff[i + 1]; k++) {
+                                int ent = lists[k];
+                                Rec r = C.rec(ent >> 1);
+                                bool side = ent & 1;
+                                // component q: 0..2 impulse, 3..5 its moment about the body
+                                int f0 = q0 < 3 ? F_P + q0 : (side ? F_LB : F_LA) + q0 - 3;
+                                int f1 = q0 + 1 < 3 ? F_P + q0 + 1 : (side ? F_LB : F_LA) + q0 - 2;
+                                float v0 = r[f0], v1 = r[f1];
+                                if (!side) { s0 = s0 + v0; s1 = s1 + v1; }
+                                else { s0 = s0 - v0; s1 = s1 - v1; }
+                            }
+                            acc[q0 * NB + i] = s0;
+                            acc[(q0 + 1) * NB + i] = s1;
+                        }
+                    }
                 }
                 __syncthreads();
                 for (int i = tid; i < N; i += kT) {
-                    f3 sp{0.0f, 0.0f, 0.0f}, sl{0.0f, 0.0f, 0.0f};
-                    for (int k = S.loff[i]; k < S.loff[i + 1]; k++) {
-                        int c = lists[k];
-                        int a, bb;
-                        unpack_ab(C, c, a, bb);
-                        f3 P = ldc3(C, F_P, c);
-                        if (a == i) {
-                            f3 t = cross3(ldc3(C, F_RA, c), P);
-                            sp = add3(sp, P);
-                            sl = add3(sl, t);
-                        } else {
-                            f3 t = cross3(ldc3(C, F_RB, c), P);
-                            sp = sub3(sp, P);
-                            sl = sub3(sl, t);
-                        }
-                    }
+                    f3 sp{acc[i], acc[NB + i], acc[2 * NB + i]};
+                    f3 sl{acc[3 * NB + i], acc[4 * NB + i], acc[5 * NB + i]};
                     f3 dw = imul(S, i, sl);
                     float im = S.im[i];
                     S.V(0, i) = S.V(0, i) + sc.omega * (im * sp.x);
@@ -713,7 +758,7 @@ int phys_smem_bytes_default(int max_bodies, int mcpb) {
     size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
     // room for 5 contacts per body in shared memory (a settled pile of spheres
     // and boxes has about 3.5), more spill to global memory; with 32 bodies
-    // this is 26 KB, so 8 environments fit on one SM
+    // this is 31 KB, so 7 environments fit on one SM
     size_t want = fixed + (size_t)kContactWords * 4 * 5 * max_bodies;
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;

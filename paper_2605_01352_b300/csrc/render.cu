@@ -59,9 +59,6 @@ struct Band {
 // (back-facing / degenerate) or misses the band.
 __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const float* iz, uint32_t id, const Band& bd,
                                           Tri& t) {
-    long long x0 = X[0], y0 = Y[0], x1 = X[1], y1 = Y[1], x2 = X[2], y2 = Y[2];
-    long long area2 = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0);
-    if (area2 >= 0) return false;
     int mnx = min(X[0], min(X[1], X[2])), mxx = max(X[0], max(X[1], X[2]));
     int mny = min(Y[0], min(Y[1], Y[2])), mxy = max(Y[0], max(Y[1], Y[2]));
     int px0 = (mnx - 128 + 255) >> 8, px1 = (mxx - 128) >> 8;
@@ -70,7 +67,10 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     px1 = min(px1, bd.W - 1);
     py0 = max(py0, bd.y0);
     py1 = min(py1, bd.y1 - 1);
-    if (px0 > px1 || py0 > py1) return false;
+    if (px0 > px1 || py0 > py1) return false;   // misses the band (cheap test first)
+    long long x0 = X[0], y0 = Y[0], x1 = X[1], y1 = Y[1], x2 = X[2], y2 = Y[2];
+    long long area2 = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0);
+    if (area2 >= 0) return false;               // back-facing or degenerate
     t.X[0] = X[0]; t.Y[0] = Y[0]; t.iz[0] = iz[0];
     t.X[1] = X[2]; t.Y[1] = Y[2]; t.iz[1] = iz[2];
     t.X[2] = X[1]; t.Y[2] = Y[1]; t.iz[2] = iz[1];
@@ -259,16 +259,6 @@ __device__ __forceinline__ void quat_mat(float w, float x, float y, float z, flo
     R[8] = 1.0f - 2.0f * (x * x + y * y);
 }
 
-__device__ __forceinline__ int last_le(const int* a, int n, int v) {
-    // largest k in [0, n) with a[k] <= v (a[0] = 0 <= v)
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (a[mid] <= v) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 struct RenderArgs {
     DevBatch b;
     const float* pose;       // [7][B]
@@ -286,7 +276,6 @@ __host__ __device__ inline size_t render_smem_bytes(int band_rows, int W) {
     size_t s = (size_t)band_rows * W * 8;                        // z keys
     s += sizeof(Tri) * kBigCap;                                  // binned triangles
     s += (size_t)kVcap * (4 + 4 + 4 + 4);                        // vertex cache
-    s += (size_t)2 * 4 * (kChunkBodies + 2);                     // chunk tables
     int nt = tiles_for(band_rows, W);
     s += (size_t)nt * kMaskWords * 4 + 16;                       // tile masks, counters
     return (s + 15) & ~(size_t)15;
@@ -313,8 +302,6 @@ __global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs a) {
     int* vY = reinterpret_cast<int*>(p); p += 4 * kVcap;
     float* viz = reinterpret_cast<float*>(p); p += 4 * kVcap;
     int* vflag = reinterpret_cast<int*>(p); p += 4 * kVcap;
-    int* cbv = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
-    int* cbt = reinterpret_cast<int*>(p); p += 4 * (kChunkBodies + 2);
     bn.tiles_x = (W + kTile - 1) / kTile;
     bn.ntiles = tiles_for(bd.y1 - bd.y0, W);
     const int ntiles_max = tiles_for(a.band_rows, a.max_w);
@@ -331,7 +318,6 @@ __global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs a) {
     const float hw = (float)W * 0.5f, hh = (float)H * 0.5f;
     const int B = b.B;
     const int b0 = b.body_off[e];
-    const int gm = b.ground_mesh;
     uint32_t* colors = b.tri_color + b.env_tri_base[e];
 
     if (threadIdx.x == 0) { *bn.nrec = 0; *sflags = 0u; }
@@ -340,23 +326,16 @@ __global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs a) {
 
     for (int ck = b.chunk_off[e]; ck < b.chunk_off[e + 1]; ck++) {
         const int cb0 = b.chunk_lo[ck];   // env-local first body, -1 = ground
-        const int nb = b.chunk_hi[ck] - cb0;
-        const int2* tab = b.chunk_vt + b.chunk_tab_off[ck];
+        const int nv = b.chunk_nv[ck], nt = b.chunk_nt[ck];
+        const int2* vt = b.vtab + b.chunk_vtab[ck];
+        const uint2* tt = b.ttab + b.chunk_ttab[ck];
         const uint32_t tri0 = (uint32_t)b.chunk_tri0[ck];
-        __syncthreads();  // previous chunk's readers of the tables are done
-        for (int k = threadIdx.x; k <= nb; k += kRT) {
-            int2 vt = tab[k];
-            cbv[k] = vt.x;
-            cbt[k] = vt.y;
-        }
-        __syncthreads();
-        const int nv = cbv[nb], nt = cbt[nb];
+        __syncthreads();  // the previous chunk's triangles are done with the vertex cache
         // 1. vertices
         for (int v = threadIdx.x; v < nv; v += kRT) {
-            int k = last_le(cbv, nb, v);
-            int bi = cb0 + k;
-            int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
-            const float* mv = b.mesh_verts + 3 * (size_t)(b.mesh_vert_off[m] + (v - cbv[k]));
+            int2 ent = vt[v];
+            int bi = cb0 + ent.y;
+            const float* mv = b.mesh_verts + 3 * (size_t)ent.x;
             float wx, wy, wz;
             if (bi < 0) {
                 wx = mv[0]; wy = mv[1]; wz = mv[2];
@@ -395,12 +374,8 @@ __global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs a) {
         __syncthreads();
         // 2. triangles: strided over the CTA, no barrier until all are submitted
         for (int t = threadIdx.x; t < nt; t += kRT) {
-            int k = last_le(cbt, nb, t);
-            int bi = cb0 + k;
-            int m = bi < 0 ? gm : b.mesh_id[b0 + bi];
-            const int32_t* tv = b.mesh_tris + 3 * (size_t)(b.mesh_tri_off[m] + (t - cbt[k]));
-            int vb = cbv[k];
-            int i0 = vb + tv[0], i1 = vb + tv[1], i2 = vb + tv[2];
+            uint2 tv = tt[t];
+            int i0 = tv.x & 0xffff, i1 = tv.x >> 16, i2 = tv.y;
             int fl = vflag[i0] | vflag[i1] | vflag[i2];
             if (fl) {
                 atomicOr(sflags, (unsigned)fl);
