@@ -283,7 +283,7 @@ vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t n
  * Scratch (contact spill records and their per-environment offsets) lives in
  * one fixed 16 MiB device array inside the library, held by every device that
  * loads it until the process exits.  Batches needing more scratch
- * (4 bytes x (2 (E + 1) rounded up to 64 + 32 x max_contacts_per_body x B))
+ * (4 bytes x (2 (E + 1) rounded up to 64 + 33 x max_contacts_per_body x B))
  * are rejected with VUDA_ERR_INVALID before anything is launched.  The first
  * call on a device resolves the array's device address; make that first call
  * before any stream capture.  Every call shares the array: calls whose work

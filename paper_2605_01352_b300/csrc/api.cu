@@ -405,7 +405,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
 
     // device memory budget
     int64_t need = (int64_t)B * 4 * (3 + 4 + 3 + 3 + 3 + 1 + 3 + 3 + 2 * 7) + B * 1 + (int64_t)B * 4 * 2 +
-                   (int64_t)E * 12 + (int64_t)spill_off[E] * kContactWords * 4 + env->T * 4 + (int64_t)C * 80;
+                   (int64_t)E * 12 + (int64_t)spill_off[E] * kContactStride * 4 + env->T * 4 + (int64_t)C * 80;
     if (o.hbm_budget_bytes > 0 && need > o.hbm_budget_bytes) {
         delete env;
         set_error("batch needs " + std::to_string(need) + " bytes, over the HBM budget");
@@ -474,7 +474,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         int64_t cap_smem = phys_contacts_in_smem(env->phys_smem, max_bodies, mcpb);
         bool need_spill = (int64_t)mcpb * max_bodies > cap_smem;
         if (s == VUDA_OK && need_spill)
-            s = dalloc(env, &d.spill, (size_t)std::max<int64_t>(spill_off[E], 1) * kContactWords);
+            s = dalloc(env, &d.spill, (size_t)std::max<int64_t>(spill_off[E], 1) * kContactStride);
     }
     if (s == VUDA_OK && E) {
         if (cudaMemset(d.flags, 0, sizeof(uint32_t) * E) != cudaSuccess ||

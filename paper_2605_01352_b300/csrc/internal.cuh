@@ -30,7 +30,7 @@ struct DevBatch {
     uint32_t* flags;              // [E]
     int32_t* ncontacts;           // [E] contacts at the last substep
     // physics contact spill area (contacts beyond the shared-memory capacity)
-    float* spill;                 // [sum_e cmax_e * kContactWords]
+    float* spill;                 // [sum_e cmax_e * kContactStride] contact records that exceed shared memory
     const int64_t* spill_off;     // [E] first spill entry of env e (in contacts)
     // render
     const int32_t* mesh_id;       // [B]
@@ -73,6 +73,7 @@ struct SimConst {
 };
 
 constexpr int kContactWords = 32;  // floats per contact record
+constexpr int kContactStride = kContactWords + 1;  // words between records (odd: bank-conflict free)
 constexpr int kCamWords = 13;
 
 // Launchers (physics.cu, render.cu)

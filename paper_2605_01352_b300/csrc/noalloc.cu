@@ -21,8 +21,8 @@ namespace vuda {
 namespace {
 
 // Scratch capacity in 4-byte words: 16 MiB.  The first (E + 1) * 2 words hold
-// the int64 spill offsets, the rest holds spill records of kContactWords
-// floats, max_contacts_per_body per body.
+// the int64 spill offsets, the rest holds spill records of kContactStride
+// words, max_contacts_per_body per body.
 constexpr size_t kNoAllocWords = 4u << 20;
 
 __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
@@ -76,7 +76,7 @@ extern "C" vuda_status vuda_sim_step_noalloc(int32_t num_envs, int32_t num_bodie
     }
     const size_t off_words = 2 * ((size_t)num_envs + 1);
     const size_t off_words_al = (off_words + 63) & ~(size_t)63;  // keep the records 256-byte aligned
-    const size_t need = off_words_al + (size_t)prm->max_contacts_per_body * num_bodies * kContactWords;
+    const size_t need = off_words_al + (size_t)prm->max_contacts_per_body * num_bodies * kContactStride;
     if (need > kNoAllocWords) {
         set_error("vuda_sim_step_noalloc: batch needs " + std::to_string(need * 4) +
                   " bytes of scratch, more than the fixed " + std::to_string(kNoAllocWords * 4) +

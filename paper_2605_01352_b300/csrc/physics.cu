@@ -43,35 +43,49 @@ enum : int {
 };
 static_assert(F_LB + 3 == kContactWords, "contact record layout");
 
-// One contact record: field f at p[f * stride].
+// One contact record: kContactWords fields at p[0..), records kCS words apart
+// (odd stride: 32 consecutive records on 32 different banks).
+constexpr int kCS = kContactStride;
 struct Rec {
     float* p;
-    int stride;
-    __device__ __forceinline__ float& operator[](int f) const { return p[f * stride]; }
+    __device__ __forceinline__ float& operator[](int f) const { return p[f]; }
 };
 
 struct Contacts {
-    float* s;       // shared SoA, stride cap
+    float* s;       // shared records [cap][kCS]
     int cap;        // records in shared memory
-    float* g;       // global spill SoA, stride gstride (record c at c - cap)
-    int gstride;
+    float* g;       // global spill records (record c at c - cap)
     __device__ __forceinline__ Rec rec(int c) const {
-        return c < cap ? Rec{s + c, cap} : Rec{g + (c - cap), gstride};
+        return c < cap ? Rec{s + c * kCS} : Rec{g + (size_t)(c - cap) * kCS};
     }
 };
 
-// Per-env body arrays in shared memory (SoA over the env's bodies, stride NB).
+// Per-env bodies in shared memory: one record of kBW words per body.  The
+// odd stride keeps 32 consecutive bodies on 32 different banks, and every
+// field sits at an immediate offset from the record base.
+enum : int {
+    B_P = 0, B_Q = 3, B_V = 7, B_W = 10, B_D = 13, B_IM = 16, B_II = 17, B_BR = 20, B_R = 21, B_I = 30,
+    B_ACC = 39, B_TYPE = 45, B_NCB = 46
+};
+constexpr int kBW = 47;
+
 struct Bodies {
-    float *pos, *quat, *vel, *ang, *dims, *im, *ii, *brad, *R, *Iw;
-    int *type, *ncb, *loff;
-    int NB;
-    __device__ __forceinline__ float& P(int k, int i) const { return pos[k * NB + i]; }
-    __device__ __forceinline__ float& Q(int k, int i) const { return quat[k * NB + i]; }
-    __device__ __forceinline__ float& V(int k, int i) const { return vel[k * NB + i]; }
-    __device__ __forceinline__ float& W(int k, int i) const { return ang[k * NB + i]; }
-    __device__ __forceinline__ float& D(int k, int i) const { return dims[k * NB + i]; }
-    __device__ __forceinline__ float& Rm(int k, int i) const { return R[k * NB + i]; }
-    __device__ __forceinline__ float& I(int k, int i) const { return Iw[k * NB + i]; }
+    float* base;
+    int* loff;
+    __device__ __forceinline__ float* b(int i) const { return base + i * kBW; }
+    __device__ __forceinline__ float& P(int k, int i) const { return b(i)[B_P + k]; }
+    __device__ __forceinline__ float& Q(int k, int i) const { return b(i)[B_Q + k]; }
+    __device__ __forceinline__ float& V(int k, int i) const { return b(i)[B_V + k]; }
+    __device__ __forceinline__ float& W(int k, int i) const { return b(i)[B_W + k]; }
+    __device__ __forceinline__ float& D(int k, int i) const { return b(i)[B_D + k]; }
+    __device__ __forceinline__ float& Rm(int k, int i) const { return b(i)[B_R + k]; }
+    __device__ __forceinline__ float& I(int k, int i) const { return b(i)[B_I + k]; }
+    __device__ __forceinline__ float& IM(int i) const { return b(i)[B_IM]; }
+    __device__ __forceinline__ float& II(int k, int i) const { return b(i)[B_II + k]; }
+    __device__ __forceinline__ float& BR(int i) const { return b(i)[B_BR]; }
+    __device__ __forceinline__ float& ACC(int q, int i) const { return b(i)[B_ACC + q]; }
+    __device__ __forceinline__ int& TYPE(int i) const { return reinterpret_cast<int*>(b(i))[B_TYPE]; }
+    __device__ __forceinline__ int& NCB(int i) const { return reinterpret_cast<int*>(b(i))[B_NCB]; }
 };
 
 struct f3 { float x, y, z; };
@@ -172,7 +186,7 @@ __device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int
     return true;
 }
 
-__device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.type[i] == kShapeBox; }
+__device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.TYPE(i) == kShapeBox; }
 
 constexpr int kT = 128;          // threads per environment (one CTA)
 constexpr int kPairChunk = 256;  // candidate pairs per round of the pair phase
@@ -180,7 +194,7 @@ constexpr int kPairChunk = 256;  // candidate pairs per round of the pair phase
 __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margin) {
     f3 dx = sub3(ldpos(B, i), ldpos(B, j));
     float d2 = dot3(dx, dx);
-    float rs = (B.brad[i] + B.brad[j]) + margin;
+    float rs = (B.BR(i) + B.BR(j)) + margin;
     return d2 < rs * rs;
 }
 
@@ -261,11 +275,11 @@ __device__ __forceinline__ void st3(const Rec& r, int field, f3 v) {
 // mass-split effective mass along dir
 __device__ __forceinline__ float eff_mass(const Bodies& B, int a, int b, f3 rA, f3 rB, f3 dir) {
     f3 u = cross3(rA, dir);
-    float kA = (float)B.ncb[a] * (B.im[a] + dot3(u, imul(B, a, u)));
+    float kA = (float)B.NCB(a) * (B.IM(a) + dot3(u, imul(B, a, u)));
     float kB = 0.0f;
     if (b >= 0) {
         u = cross3(rB, dir);
-        kB = (float)B.ncb[b] * (B.im[b] + dot3(u, imul(B, b, u)));
+        kB = (float)B.NCB(b) * (B.IM(b) + dot3(u, imul(B, b, u)));
     }
     return kA + kB;
 }
@@ -283,8 +297,8 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 
 // Bytes of per-env shared memory before the contact records.
 __host__ __device__ inline size_t phys_fixed_bytes(int NB, int cmax) {
-    size_t f = (size_t)45 * NB * 4;          // float body planes (incl. 6 planes of per-body sums)
-    f += (size_t)(3 * NB + 1) * 4;           // type, ncb, loff[NB+1]
+    size_t f = (size_t)kBW * NB * 4;         // body records
+    f += (size_t)(NB + 1) * 4;               // loff[NB+1]
     f += (size_t)4 * NB * 4;                 // per-quarter list counters
     f += (size_t)2 * kPairChunk * 4;         // passing pairs and their item prefix
     f += (size_t)8 * 4;                      // scan scratch
@@ -323,22 +337,9 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
     const int cmax_nb = sc.mcpb * NB;
 
     Bodies S;
-    S.NB = NB;
     float* fp = reinterpret_cast<float*>(smem);
-    S.pos = fp; fp += 3 * NB;
-    S.quat = fp; fp += 4 * NB;
-    S.vel = fp; fp += 3 * NB;
-    S.ang = fp; fp += 3 * NB;
-    S.dims = fp; fp += 3 * NB;
-    S.im = fp; fp += NB;
-    S.ii = fp; fp += 3 * NB;
-    S.brad = fp; fp += NB;
-    S.R = fp; fp += 9 * NB;
-    S.Iw = fp; fp += 9 * NB;
-    float* acc = fp; fp += 6 * NB;       // per-body impulse sums (P xyz, L xyz) of one iteration
+    S.base = fp; fp += kBW * NB;
     int* ip = reinterpret_cast<int*>(fp);
-    S.type = ip; ip += NB;
-    S.ncb = ip; ip += NB;
     S.loff = ip; ip += NB + 1;
     int* qcnt = ip; ip += 4 * NB;        // [4][NB] contacts of each body in each quarter of the list
     int* plist = ip; ip += kPairChunk;   // units (passing pairs or plane bodies) of the current round
@@ -348,12 +349,11 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
     const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
     Contacts C;
     C.s = reinterpret_cast<float*>(smem + fixed);
-    int capS = (int)((smem_per_env - (long)fixed) / (kContactWords * 4));
+    int capS = (int)((smem_per_env - (long)fixed) / (kCS * 4));
     if (capS > cmax) capS = cmax;
     if (capS < 0) capS = 0;
     C.cap = capS;
-    C.g = b.spill + (size_t)b.spill_off[e] * kContactWords;
-    C.gstride = cmax;
+    C.g = b.spill + (size_t)b.spill_off[e] * kCS;
 
     for (int i = tid; i < N; i += kT) {
         int g = b0 + i;
@@ -363,14 +363,14 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
             S.V(k, i) = b.vel[k * B + g];
             S.W(k, i) = b.ang[k * B + g];
             S.D(k, i) = b.dims[k * B + g];
-            S.ii[k * NB + i] = b.ii[k * B + g];
+            S.II(k, i) = b.ii[k * B + g];
         }
 #pragma unroll
         for (int k = 0; k < 4; k++) S.Q(k, i) = b.quat[k * B + g];
-        S.im[i] = b.im[g];
+        S.IM(i) = b.im[g];
         int t = b.type[g];
-        S.type[i] = t;
-        S.brad[i] = t == kShapeBox
+        S.TYPE(i) = t;
+        S.BR(i) = t == kShapeBox
                         ? sqrtf((S.D(0, i) * S.D(0, i) + S.D(1, i) * S.D(1, i)) + S.D(2, i) * S.D(2, i))
                         : S.D(0, i);
     }
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
         for (int ss = 0; ss < sc.substeps; ss++) {
             // 1. velocities, rotation, world inverse inertia
             for (int i = tid; i < N; i += kT) {
-                float im = S.im[i];
+                float im = S.IM(i);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
                     float f = force ? force[k * B + b0 + i] : 0.0f;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
                 R[6] = 2.0f * (x * z - w * y);
                 R[7] = 2.0f * (y * z + w * x);
                 R[8] = 1.0f - 2.0f * (x * x + y * y);
-                float ib0 = S.ii[i], ib1 = S.ii[NB + i], ib2 = S.ii[2 * NB + i];
+                float ib0 = S.II(0, i), ib1 = S.II(1, i), ib2 = S.II(2, i);
 #pragma unroll
                 for (int k = 0; k < 9; k++) S.Rm(k, i) = R[k];
 #pragma unroll
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
                     int tot;
                     int ex = block_excl_scan(v, wsum, tot);
                     if (i < N) {
-                        S.ncb[i] = v;
+                        S.NCB(i) = v;
                         S.loff[i] = run + ex;
                     }
                     run += tot;
@@ -676,17 +676,17 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
                                 if (!side) { s0 = s0 + v0; s1 = s1 + v1; }
                                 else { s0 = s0 - v0; s1 = s1 - v1; }
                             }
-                            acc[q0 * NB + i] = s0;
-                            acc[(q0 + 1) * NB + i] = s1;
+                            S.ACC(q0, i) = s0;
+                            S.ACC(q0 + 1, i) = s1;
                         }
                     }
                 }
                 __syncthreads();
                 for (int i = tid; i < N; i += kT) {
-                    f3 sp{acc[i], acc[NB + i], acc[2 * NB + i]};
-                    f3 sl{acc[3 * NB + i], acc[4 * NB + i], acc[5 * NB + i]};
+                    f3 sp{S.ACC(0, i), S.ACC(1, i), S.ACC(2, i)};
+                    f3 sl{S.ACC(3, i), S.ACC(4, i), S.ACC(5, i)};
                     f3 dw = imul(S, i, sl);
-                    float im = S.im[i];
+                    float im = S.IM(i);
                     S.V(0, i) = S.V(0, i) + sc.omega * (im * sp.x);
                     S.V(1, i) = S.V(1, i) + sc.omega * (im * sp.y);
                     S.V(2, i) = S.V(2, i) + sc.omega * (im * sp.z);
@@ -751,15 +751,15 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
 int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb) {
     size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
     if ((size_t)smem_per_env < fixed) return 0;
-    return (int)(((size_t)smem_per_env - fixed) / (kContactWords * 4));
+    return (int)(((size_t)smem_per_env - fixed) / (kCS * 4));
 }
 
 int phys_smem_bytes_default(int max_bodies, int mcpb) {
     size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
-    // room for 5 contacts per body in shared memory (a settled pile of spheres
-    // and boxes has about 3.5), more spill to global memory; with 32 bodies
-    // this is 31 KB, so 7 environments fit on one SM
-    size_t want = fixed + (size_t)kContactWords * 4 * 5 * max_bodies;
+    // room for 4.5 contacts per body in shared memory (a settled pile of
+    // spheres and boxes has about 3.5), more spill to global memory; with 32
+    // bodies this is 31 KB, so 7 environments fit on one SM
+    size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2);
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;
     return (int)align16(want);

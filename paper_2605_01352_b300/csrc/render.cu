@@ -79,6 +79,28 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     return true;
 }
 
+// int64 -> float, round to nearest even, in integer arithmetic.  The
+// hardware 64-bit conversion runs on the FP64 pipe, which is narrow on this
+// GPU; values that fit in 32 bits use the 32-bit conversion (the same
+// rounding of the same integer), larger ones keep the top 24 significant
+// bits and round on the dropped ones.
+__device__ __forceinline__ float i64_to_f32(long long x) {
+    if (x == (long long)(int)x) return __int2float_rn((int)x);
+    unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    int shift = 40 - __clzll((long long)a);   // bits below the 24 kept (a >= 2^31, so shift >= 8)
+    unsigned long long m = a >> shift;
+    unsigned long long rem = a & ((1ull << shift) - 1);
+    unsigned long long half = 1ull << (shift - 1);
+    if (rem > half || (rem == half && (m & 1ull))) m++;
+    if (m == (1ull << 24)) {
+        m >>= 1;
+        shift++;
+    }
+    unsigned bits = ((unsigned)(150 + shift) << 23) | ((unsigned)m & 0x7fffffu);   // value m * 2^shift
+    if (x < 0) bits |= 0x80000000u;
+    return __uint_as_float(bits);
+}
+
 struct Edges {
     long long A[3], B[3], C[3];
     bool tl[3];
@@ -98,7 +120,7 @@ __device__ __forceinline__ void edges(const Tri& t, Edges& e) {
     }
     long long area2 = ((long long)t.X[1] - t.X[0]) * ((long long)t.Y[2] - t.Y[0]) -
                       ((long long)t.Y[1] - t.Y[0]) * ((long long)t.X[2] - t.X[0]);
-    e.af = (float)area2;
+    e.af = i64_to_f32(area2);
 }
 
 __device__ __forceinline__ bool inside(long long E0, long long E1, long long E2, const Edges& e) {
@@ -107,7 +129,7 @@ __device__ __forceinline__ bool inside(long long E0, long long E1, long long E2,
 
 __device__ __forceinline__ unsigned long long frag_key(long long E0, long long E1, long long E2, const Tri& t,
                                                        const Edges& e) {
-    float den = ((float)E0 * t.iz[0] + (float)E1 * t.iz[1]) + (float)E2 * t.iz[2];
+    float den = (i64_to_f32(E0) * t.iz[0] + i64_to_f32(E1) * t.iz[1]) + i64_to_f32(E2) * t.iz[2];
     float depth = e.af / den;
     return ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
 }
