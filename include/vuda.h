@@ -129,6 +129,9 @@ typedef struct {
     int32_t device;               /* CUDA device ordinal (default 0) */
     int32_t render_band_rows;     /* rows per render work item (0: auto) */
     int32_t phys_smem_bytes;      /* shared memory per physics env (0: auto) */
+    int32_t persistent;           /* 1: one persistent launch per phase pulls work items (environments,
+                                     camera bands) largest first from an atomic counter -- for batches of
+                                     uneven environments; 0: one CTA per item */
 } vuda_env_opts;
 
 /* Sizes of a created batch. */

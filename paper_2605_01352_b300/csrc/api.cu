@@ -135,6 +135,15 @@ struct vuda_env {
     CUcontext c_sim = nullptr, c_ren = nullptr;  // green contexts as CUcontext (null otherwise)
     vuda_cosched_info cos_info{};
     std::vector<cudaEvent_t> ev_sim, ev_ren;      // event pools owned by each phase's context
+    // persistent work-list launches (uneven batches)
+    int persistent = 0;
+    DevBatch* d_desc = nullptr;                   // device copy of d
+    int2* sim_items[2] = {nullptr, nullptr};      // per pose slot: (0 | slot << 24, env), largest first
+    int4* ren_items[2] = {nullptr, nullptr};      // per pose slot: (0 | slot << 24, cam, y0, 0), largest first
+    int2* shade_items[2] = {nullptr, nullptr};
+    int nshade = 0;
+    int* counters = nullptr;                      // [2]: sim, render
+    int sim_grid = 0, ren_grid = 0;
     // host-buffer loop: device force ring and a copy stream (primary context)
     float* dforce = nullptr;                      // [2][3][B]
     cudaStream_t copy_s = nullptr;
@@ -504,6 +513,49 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     k.omega = prm->jacobi_omega;
     k.plane = prm->plane;
     k.mcpb = mcpb;
+    d.sc = k;
+    d.max_bodies = max_bodies;
+    if (o.persistent) {
+        // work items, largest first: environments by body count, camera bands by pixels x triangles
+        env->persistent = 1;
+        std::vector<int> eo(E);
+        for (int e = 0; e < E; e++) eo[e] = e;
+        std::stable_sort(eo.begin(), eo.end(), [&](int a, int b2) {
+            return sc->body_off[a + 1] - sc->body_off[a] > sc->body_off[b2 + 1] - sc->body_off[b2];
+        });
+        std::vector<int> io(item_cam.size());
+        for (size_t i = 0; i < io.size(); i++) io[i] = (int)i;
+        auto cost = [&](int i) {
+            int c = item_cam[i], e = cam_env[c];
+            int rows = std::min(br, sc->cam_h[c] - item_y0[i]);
+            return (double)rows * sc->cam_w[c] + 4.0 * (double)(env_tri_base[e + 1] - env_tri_base[e]);
+        };
+        std::stable_sort(io.begin(), io.end(), [&](int a, int b2) { return cost(a) > cost(b2); });
+        for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
+            std::vector<int2> si(E);
+            for (int k2 = 0; k2 < E; k2++) si[k2] = make_int2(slot << 24, eo[k2]);
+            std::vector<int4> ri(io.size());
+            for (size_t k2 = 0; k2 < io.size(); k2++)
+                ri[k2] = make_int4(slot << 24, item_cam[io[k2]], item_y0[io[k2]], 0);
+            std::vector<int2> sh(B + E);
+            for (int u = 0; u < B + E; u++) sh[u] = make_int2(slot << 24, u);
+            s = upload(env, &env->sim_items[slot], si.data(), si.size());
+            if (s == VUDA_OK) s = upload(env, &env->ren_items[slot], ri.data(), ri.size());
+            if (s == VUDA_OK) s = upload(env, &env->shade_items[slot], sh.data(), sh.size());
+        }
+        env->nshade = B + E;
+        if (s == VUDA_OK) s = dalloc(env, &env->counters, 2);
+        if (s == VUDA_OK) s = upload(env, &env->d_desc, &d, 1);
+        int dev_sms = 0;
+        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, o.device);
+        env->sim_grid = std::max(1, std::min(E, dev_sms * sim_ctas_per_sm(env->phys_smem)));
+        env->ren_grid = std::max(1, std::min((int)item_cam.size(), dev_sms * render_ctas_per_sm(br, max_w)));
+        if (s != VUDA_OK) {
+            free_env(env);
+            delete env;
+            return s;
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) {
         free_env(env);
         delete env;
@@ -550,8 +602,17 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
     if (!env) return invalid("null env");
     if (nsteps < 0) return invalid("nsteps < 0");
     if (nsteps == 0) return VUDA_OK;
-    cudaError_t e = launch_sim(env->d, env->sc, nsteps, force, (int)(env->steps & 1), env->phys_smem,
-                               env->max_bodies, (cudaStream_t)stream);
+    cudaError_t e = cudaSuccess;
+    if (env->persistent && !force) {
+        for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
+            int slot = (int)((env->steps + t) & 1);
+            e = launch_sim_items(env->d_desc, env->sim_items[slot], env->E, env->counters, env->sim_grid,
+                                 env->phys_smem, env->max_bodies, (cudaStream_t)stream);
+        }
+    } else {
+        e = launch_sim(env->d, env->sc, nsteps, force, (int)(env->steps & 1), env->phys_smem, env->max_bodies,
+                       (cudaStream_t)stream);
+    }
     if (e != cudaSuccess) {
         set_error(std::string("sim launch: ") + cudaGetErrorString(e));
         return VUDA_ERR_CUDA;
@@ -561,8 +622,13 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
 }
 
 static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, cudaStream_t stream) {
-    cudaError_t e = launch_render_items(env->d, env->d.pose[slot], *fr, env->item_cam, env->item_y0, env->nitems,
-                                        env->band_rows, env->max_w, stream);
+    cudaError_t e;
+    if (env->persistent)
+        e = launch_render_list(env->d_desc, env->ren_items[slot], env->nitems, env->counters + 1, env->ren_grid,
+                               env->shade_items[slot], env->nshade, env->band_rows, env->max_w, fr, stream);
+    else
+        e = launch_render_items(env->d, env->d.pose[slot], *fr, env->item_cam, env->item_y0, env->nitems,
+                                env->band_rows, env->max_w, stream);
     if (e != cudaSuccess) {
         set_error(std::string("render launch: ") + cudaGetErrorString(e));
         return VUDA_ERR_CUDA;

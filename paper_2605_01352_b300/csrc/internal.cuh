@@ -14,6 +14,14 @@ constexpr int kShapeSphere = 0;
 constexpr int kShapeBox = 1;
 constexpr int kShapeHull = 2;
 
+struct SimConst {
+    float h;                      // dt / substeps
+    int substeps, iterations;
+    float g[3];
+    float restitution, rest_thr, mu, beta, slop, margin, omega;
+    int plane, mcpb;
+};
+
 // Device-resident batch.  All arrays are device pointers.
 struct DevBatch {
     int E, B, C;
@@ -62,15 +70,21 @@ struct DevBatch {
     const uint2* ttab;            // triangle t of a chunk: chunk-local vertices (i0 | i1 << 16, i2)
     // vtab / ttab entries are shared by every chunk with the same sequence of meshes
     float light[3];
+    SimConst sc;                  // physics constants of this batch
+    vuda_frame frame;             // output frame (work-list launches; single-batch launches pass it)
+    int max_bodies;               // largest environment of the batch
 };
 
-struct SimConst {
-    float h;                      // dt / substeps
-    int substeps, iterations;
-    float g[3];
-    float restitution, rest_thr, mu, beta, slop, margin, omega;
-    int plane, mcpb;
-};
+// Work-list items.  A launch either covers one batch directly (items == null:
+// item i is environment i, or render work item i of the batch) or walks a
+// list of items over several batches (descs[desc] for each item), pulled from
+// an atomic counter by persistent CTAs.
+//   sim item:    (desc | slot << 24, env)
+//   render item: (desc | slot << 24, camera, first row, 0)
+//   shade item:  (desc | slot << 24, unit)   unit < B: body, else ground of env unit - B
+constexpr int kItemDescMask = 0xffffff;
+
+
 
 constexpr int kContactWords = 32;  // floats per contact record
 constexpr int kContactStride = kContactWords + 1;  // words between records (odd: bank-conflict free)
@@ -79,10 +93,20 @@ constexpr int kCamWords = 13;
 // Launchers (physics.cu, render.cu)
 cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const float* force, int pose_slot_first,
                        int smem_per_env, int max_bodies, cudaStream_t stream);
+// Work-list form: grid CTAs pull items [0, nitems) from *counter (zeroed here
+// on the stream first); max_bodies bounds every listed environment.
+cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
+                             int smem_per_env, int max_bodies, cudaStream_t stream);
+int sim_ctas_per_sm(int smem_per_env);
 int phys_smem_bytes_default(int max_bodies, int mcpb);
 int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb);
 cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda_frame& fr, const int32_t* item_cam,
                                 const int32_t* item_y0, int nitems, int band_rows, int max_w, cudaStream_t stream);
+// Work-list form over several batches (frames from each descriptor).
+cudaError_t launch_render_list(const DevBatch* descs, const int4* items, int nitems, int* counter, int grid,
+                               const int2* shade_items, int nshade, int band_rows, int max_w, const vuda_frame* fr0,
+                               cudaStream_t stream);
+int render_ctas_per_sm(int band_rows, int max_w);
 size_t render_smem_for(int band_rows, int W);
 int render_default_band_rows(int max_w, int max_h);
 int render_chunk_bodies();

@@ -324,10 +324,12 @@ __device__ __forceinline__ void pair_of_index(int k, int N, int& i, int& j) {
 // unit; returns the exclusive item prefix and the total (block scan).
 // Items are later tested one per thread and their hits compacted in order.
 
-__global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int nsteps, const float* __restrict__ force,
-                                                    int slot0, int smem_per_env, int NB) {
+// One environment for nsteps steps, by the whole CTA.  b lives in shared
+// memory (copied there by the kernels below).
+__device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, const float* __restrict__ force, int slot0,
+                                     int smem_per_env, int NB) {
+    const SimConst& sc = b.sc;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int e = blockIdx.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int b0 = b.body_off[e];
@@ -746,6 +748,45 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b, SimConst sc, int
     }
 }
 
+// Copies a descriptor into shared memory with the whole CTA.
+__device__ __forceinline__ void load_desc(DevBatch& dst, const DevBatch& src) {
+    const int* a = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(DevBatch) / 4); k += blockDim.x) d[k] = a[k];
+}
+
+// Single batch: CTA e steps environment e.
+__global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b0, SimConst sc0, int nsteps,
+                                                    const float* __restrict__ force, int slot0, int smem_per_env,
+                                                    int NB) {
+    __shared__ DevBatch sb;
+    load_desc(sb, b0);
+    __syncthreads();
+    if (threadIdx.x == 0) sb.sc = sc0;
+    __syncthreads();
+    sim_env(sb, blockIdx.x, nsteps, force, slot0, smem_per_env, NB);
+}
+
+// Work list over several batches: persistent CTAs pull (batch, environment,
+// pose slot) items from an atomic counter; one step each.
+__global__ void __launch_bounds__(kT, 7) sim_list_kernel(const DevBatch* __restrict__ descs,
+                                                         const int2* __restrict__ items, int nitems, int* counter,
+                                                         int smem_per_env, int NB) {
+    __shared__ DevBatch sb;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const int2 it = items[item];
+        load_desc(sb, descs[it.x & kItemDescMask]);
+        __syncthreads();
+        sim_env(sb, it.y, 1, nullptr, (it.x >> 24) & 1, smem_per_env, NB);
+        __syncthreads();  // everyone is done with sb and s_item
+    }
+}
+
 }  // namespace
 
 int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb) {
@@ -763,6 +804,30 @@ int phys_smem_bytes_default(int max_bodies, int mcpb) {
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;
     return (int)align16(want);
+}
+
+int sim_ctas_per_sm(int smem_per_env) {
+    int n = 0;
+    cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_list_kernel, kT, smem_per_env) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
+                             int smem_per_env, int max_bodies, cudaStream_t stream) {
+    if (nitems == 0) return cudaSuccess;
+    const int mcpb_max = 0;
+    (void)mcpb_max;
+    cudaError_t e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    sim_list_kernel<<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, smem_per_env, max_bodies);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const float* force, int slot0,

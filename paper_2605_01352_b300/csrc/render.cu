@@ -79,26 +79,12 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     return true;
 }
 
-// int64 -> float, round to nearest even, in integer arithmetic.  The
-// hardware 64-bit conversion runs on the FP64 pipe, which is narrow on this
-// GPU; values that fit in 32 bits use the 32-bit conversion (the same
-// rounding of the same integer), larger ones keep the top 24 significant
-// bits and round on the dropped ones.
+// int64 -> float (round to nearest even).  Values that fit in 32 bits take
+// the 32-bit conversion (the same rounding of the same integer); only larger
+// ones use the 64-bit conversion, which runs on the narrow FP64 pipe.
 __device__ __forceinline__ float i64_to_f32(long long x) {
     if (x == (long long)(int)x) return __int2float_rn((int)x);
-    unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-    int shift = 40 - __clzll((long long)a);   // bits below the 24 kept (a >= 2^31, so shift >= 8)
-    unsigned long long m = a >> shift;
-    unsigned long long rem = a & ((1ull << shift) - 1);
-    unsigned long long half = 1ull << (shift - 1);
-    if (rem > half || (rem == half && (m & 1ull))) m++;
-    if (m == (1ull << 24)) {
-        m >>= 1;
-        shift++;
-    }
-    unsigned bits = ((unsigned)(150 + shift) << 23) | ((unsigned)m & 0x7fffffu);   // value m * 2^shift
-    if (x < 0) bits |= 0x80000000u;
-    return __uint_as_float(bits);
+    return (float)x;
 }
 
 struct Edges {
@@ -303,16 +289,20 @@ __host__ __device__ inline size_t render_smem_bytes(int band_rows, int W) {
     return (s + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs a) {
+// One (camera, band) work item by the whole CTA.  b lives in shared memory.
+__device__ __forceinline__ void render_band(const DevBatch& b, int cam, int y0, const float* __restrict__ pose,
+                                            const vuda_frame& fr, int band_rows, int max_w) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const DevBatch& b = a.b;
-    const int item = blockIdx.x;
-    const int cam = a.item_cam[item];
+    struct {
+        int band_rows, max_w;
+        const float* pose;
+        vuda_frame fr;
+    } a{band_rows, max_w, pose, fr};
     const int e = b.cam_env[cam];
     const int W = b.cam_w[cam], H = b.cam_h[cam];
     Band bd;
     bd.W = W;
-    bd.y0 = a.item_y0[item];
+    bd.y0 = y0;
     bd.y1 = min(H, bd.y0 + a.band_rows);
     bd.count = nullptr;
 
@@ -468,6 +458,42 @@ __global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs a) {
     if (threadIdx.x == 0 && *sflags) atomicOr(b.flags + e, *sflags);
 }
 
+__device__ __forceinline__ void load_desc(DevBatch& dst, const DevBatch& src) {
+    const int* a = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(DevBatch) / 4); k += blockDim.x) d[k] = a[k];
+}
+
+// Single batch: CTA i renders work item i of the batch.
+__global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs args) {
+    __shared__ DevBatch sb;
+    load_desc(sb, args.b);
+    __syncthreads();
+    render_band(sb, args.item_cam[blockIdx.x], args.item_y0[blockIdx.x], args.pose, args.fr, args.band_rows,
+                args.max_w);
+}
+
+// Work list over several batches: persistent CTAs pull (batch, camera, band,
+// pose slot) items from an atomic counter; frames come from each batch.
+__global__ void __launch_bounds__(kRT, 4) render_list_kernel(const DevBatch* __restrict__ descs,
+                                                             const int4* __restrict__ items, int nitems,
+                                                             int* counter, int band_rows, int max_w, vuda_frame fr0,
+                                                             int use_fr0) {
+    __shared__ DevBatch sb;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const int4 it = items[item];
+        load_desc(sb, descs[it.x & kItemDescMask]);
+        __syncthreads();
+        render_band(sb, it.y, it.z, sb.pose[(it.x >> 24) & 1], use_fr0 ? fr0 : sb.frame, band_rows, max_w);
+        __syncthreads();
+    }
+}
+
 // Test hook: screen-space triangles, one CTA per band of the W x H image,
 // through the same submit / tile-pass path as render_kernel.
 __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __restrict__ xy,
@@ -525,15 +551,12 @@ __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __res
     }
 }
 
-// Flat colour of every triangle from its world face normal (independent of
-// the camera, so computed once per step for all cameras).  One warp per unit:
-// units [0, B) are bodies, [B, B + E) the ground quads of the environments.
-__global__ void __launch_bounds__(256) shade_kernel(DevBatch b, const float* __restrict__ pose,
-                                                    const int64_t* __restrict__ body_tri_base) {
+// Flat colour of every triangle of one unit from its world face normal
+// (independent of the camera, so computed once per step for all cameras), by
+// one warp.  Units [0, B) are bodies, [B, B + E) the ground quads.
+__device__ __forceinline__ void shade_unit(const DevBatch& b, int unit, const float* __restrict__ pose) {
     const int lane = threadIdx.x & 31;
-    const int unit = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int B = b.B;
-    if (unit >= B + b.E) return;
     int m;
     uint32_t alb;
     uint32_t* out;
@@ -544,7 +567,7 @@ __global__ void __launch_bounds__(256) shade_kernel(DevBatch b, const float* __r
         const int g = unit;
         m = b.mesh_id[g];
         alb = b.albedo[g];
-        out = b.tri_color + body_tri_base[g];
+        out = b.tri_color + b.body_tri_base[g];
         quat_mat(pose[3 * B + g], pose[4 * B + g], pose[5 * B + g], pose[6 * B + g], R);
         s0 = b.scale[g]; s1 = b.scale[B + g]; s2 = b.scale[2 * B + g];
         p0 = pose[g]; p1 = pose[B + g]; p2 = pose[2 * B + g];
@@ -590,6 +613,22 @@ __global__ void __launch_bounds__(256) shade_kernel(DevBatch b, const float* __r
     }
 }
 
+__global__ void __launch_bounds__(256) shade_kernel(DevBatch b, const float* __restrict__ pose) {
+    const int unit = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (unit >= b.B + b.E) return;
+    shade_unit(b, unit, pose);
+}
+
+// Work list over several batches: warp w shades item w.
+__global__ void __launch_bounds__(256) shade_list_kernel(const DevBatch* __restrict__ descs,
+                                                         const int2* __restrict__ items, int nitems) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nitems) return;
+    const int2 it = items[w];
+    const DevBatch& b = descs[it.x & kItemDescMask];
+    shade_unit(b, it.y, b.pose[(it.x >> 24) & 1]);
+}
+
 size_t screen_smem_bytes(int band_rows, int W) {
     int nt = tiles_for(band_rows, W);
     size_t s = (size_t)band_rows * W * 12 + sizeof(Tri) * kBigCap + (size_t)nt * kMaskWords * 4 + 16;
@@ -619,7 +658,7 @@ cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda
     if (err != cudaSuccess) return err;
     if (b.B + b.E > 0) {
         int units = b.B + b.E;
-        shade_kernel<<<(units * 32 + 255) / 256, 256, 0, stream>>>(b, pose, b.body_tri_base);
+        shade_kernel<<<(units * 32 + 255) / 256, 256, 0, stream>>>(b, pose);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
@@ -632,6 +671,35 @@ cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda
     a.band_rows = band_rows;
     a.max_w = max_w;
     render_kernel<<<nitems, kRT, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int render_ctas_per_sm(int band_rows, int max_w) {
+    int n = 0;
+    size_t smem = render_smem_bytes(band_rows, max_w);
+    cudaFuncSetAttribute(render_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_list_kernel, kRT, smem) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_render_list(const DevBatch* descs, const int4* items, int nitems, int* counter, int grid,
+                               const int2* shade_items, int nshade, int band_rows, int max_w, const vuda_frame* fr0,
+                               cudaStream_t stream) {
+    cudaError_t err;
+    if (nshade > 0) {
+        shade_list_kernel<<<(nshade * 32 + 255) / 256, 256, 0, stream>>>(descs, shade_items, nshade);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    if (nitems == 0) return cudaSuccess;
+    size_t smem = render_smem_bytes(band_rows, max_w);
+    err = cudaFuncSetAttribute(render_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    if (err != cudaSuccess) return err;
+    vuda_frame f{};
+    if (fr0) f = *fr0;
+    render_list_kernel<<<grid, kRT, smem, stream>>>(descs, items, nitems, counter, band_rows, max_w, f, fr0 ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ class Scene(C.Structure):
 
 class EnvOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("device", C.c_int32), ("render_band_rows", C.c_int32),
-                ("phys_smem_bytes", C.c_int32)]
+                ("phys_smem_bytes", C.c_int32), ("persistent", C.c_int32)]
 
 
 class EnvInfo(C.Structure):
@@ -160,7 +160,7 @@ class Env:
     """A batch of environments resident on the GPU."""
 
     def __init__(self, scene, params=None, hbm_budget_bytes: int = 0, device: int = 0, band_rows: int = 0,
-                 phys_smem_bytes: int = 0):
+                 phys_smem_bytes: int = 0, persistent: bool = False):
         self.scene = scene
         keep = []
 
@@ -201,7 +201,7 @@ class Env:
         sc.light = (C.c_float * 3)(*[float(x) for x in scene.light])
         self.params = params or scene.params
         prm = sim_params(self.params)
-        opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes)
+        opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes, int(persistent))
         handle = vp()
         check(lib.vuda_env_create(C.byref(sc), C.byref(prm), C.byref(opts), C.byref(handle)), "vuda_env_create")
         self.h = handle

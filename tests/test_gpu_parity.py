@@ -257,3 +257,39 @@ def test_full_size_cfg2_sampled(V, orc):
         np.testing.assert_allclose(f["depth"][sl].cpu().numpy(), o_dep, rtol=DEPTH_RTOL)
         assert np.abs(f["rgb"][sl].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1
     env.close()
+
+
+def test_persistent_uneven_batch_matches(V, orc):
+    """Uneven batch (body counts log-uniform in [4, 256], cameras of 64, 128
+    and 256 pixels): the persistent work-list launches (largest items first,
+    pulled from an atomic counter) give the same state and frames as one CTA
+    per item, and sampled environments match the oracle."""
+    import torch
+    sc = S.cfg4(40)
+    out = []
+    for persistent in (False, True):
+        env = V.Env(sc, persistent=persistent)
+        ring = [env.alloc_frame(), env.alloc_frame()]
+        env.pipeline_run(3, ring)
+        torch.cuda.synchronize()
+        out.append((env.get_state(), {k: v.cpu().numpy().copy() for k, v in ring[0].items()}, env.status()[0]))
+        env.close()
+    (s0, f0, fl0), (s1, f1, fl1) = out
+    for k in s0:
+        np.testing.assert_array_equal(s0[k], s1[k])
+    for k in f0:
+        np.testing.assert_array_equal(f0[k], f1[k])
+    np.testing.assert_array_equal(fl0, fl1)
+    pix = sc.cam_pix_off()
+    for e in (0, 7, 21, 39):
+        sub = sc.subset([e])
+        so, _, _ = orc.sim_step(sub, 3)
+        b0, b1 = sc.body_off[e], sc.body_off[e + 1]
+        for k in ("pos", "vel", "quat", "angvel"):
+            np.testing.assert_allclose(s1[k][:, b0:b1], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL)
+    # frame 0 of the ring holds step 2 (third step): render it with the oracle from the oracle's state
+    s_prev, _, _ = orc.sim_step(sc, 2)
+    s_step3, _, _ = orc.sim_step(sc, 1, state=s_prev)
+    o_rgb, o_dep, o_tid, _ = orc.render(sc, s_step3["pos"], s_step3["quat"])
+    np.testing.assert_array_equal(f1["triid"].view(np.uint32), o_tid)
+    np.testing.assert_allclose(f1["depth"], o_dep, rtol=DEPTH_RTOL)
