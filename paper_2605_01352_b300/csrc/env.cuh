@@ -1,0 +1,48 @@
+// The environment-batch handle shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+struct vuda_env {
+    int device = 0;
+    vuda::DevBatch d{};
+    vuda::SimConst sc{};
+    vuda_sim_params params{};
+    int E = 0, B = 0, C = 0, max_bodies = 0, max_w = 0;
+    int64_t P = 0, T = 0;
+    int64_t bytes = 0;
+    int64_t steps = 0;
+    int phys_smem = 0;
+    int band_rows = 0;
+    int nitems = 0;
+    int32_t* item_cam = nullptr;
+    int32_t* item_y0 = nullptr;
+    std::vector<void*> allocs;
+    std::vector<int64_t> cam_pix_off;
+    std::vector<int32_t> h_item_cam, h_item_y0;   // host copies of the render work items
+    // co-scheduling
+    int cos_mode = 0;
+    cudaStream_t sim_s = nullptr, ren_s = nullptr, own_s = nullptr;
+    CUgreenCtx g_sim = nullptr, g_ren = nullptr;
+    CUcontext c_sim = nullptr, c_ren = nullptr;  // green contexts as CUcontext (null otherwise)
+    vuda_cosched_info cos_info{};
+    std::vector<cudaEvent_t> ev_sim, ev_ren;      // event pools owned by each phase's context
+    // persistent work-list launches (uneven batches)
+    int persistent = 0;
+    vuda::DevBatch* d_desc = nullptr;                   // device copy of d
+    int2* sim_items[2] = {nullptr, nullptr};      // per pose slot: (0 | slot << 24, env), largest first
+    int4* ren_items[2] = {nullptr, nullptr};      // per pose slot: (0 | slot << 24, cam, y0, 0), largest first
+    int2* shade_items[2] = {nullptr, nullptr};
+    int nshade = 0;
+    int* counters = nullptr;                      // [2]: sim, render
+    int sim_grid = 0, ren_grid = 0;
+    // host-buffer loop: device force ring and a copy stream (primary context)
+    float* dforce = nullptr;                      // [2][3][B]
+    cudaStream_t copy_s = nullptr;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
+};
