@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serial-only", action="store_true", help="only the serialized loop (for profiling)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-jobs", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -178,6 +181,67 @@ def run_reference(args):
     }), flush=True)
 
 
+def serving_bench(V, S, njobs: int, nreq: int):
+    """Serving workload (jobs of 16-1024 envs with 4-256 bodies and 64-256 px
+    cameras): capacity from a burst, then Poisson arrivals at 80 % of it, for
+    continuous batching and for a serialized FIFO (one request at a time)."""
+    import torch
+    jobs = S.cfg5_jobs(njobs)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+
+    def run(serialized: bool, rate_hz: float):
+        srv = V.Server(hbm_budget_bytes=budget, max_inflight=1 if serialized else 2,
+                       max_batch_jobs=1 if serialized else 0, serialized=serialized)
+        ids = [srv.add_job(j) for j in jobs]
+        envs = {i: j.num_envs for i, j in zip(ids, jobs)}
+        for i in ids:                       # admit and warm up
+            srv.submit(i)
+        srv.wait_all(len(ids), timeout_s=600)
+        if rate_hz <= 0:                    # capacity: a burst of 4 requests per job
+            t = time.perf_counter()
+            for _ in range(4):
+                for i in ids:
+                    srv.submit(i)
+            res = srv.wait_all(4 * len(ids), timeout_s=600)
+            dt = time.perf_counter() - t
+            srv.close()
+            return len(res) / dt
+        rng = np.random.default_rng(55)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, nreq))
+        pick = rng.integers(0, len(ids), nreq)
+        done = []
+        t0 = time.perf_counter()
+        k = 0
+        while k < nreq:
+            now = time.perf_counter() - t0
+            while k < nreq and arrivals[k] <= now:
+                srv.submit(ids[pick[k]])
+                k += 1
+            done += srv.poll()
+            if k < nreq:
+                time.sleep(max(0.0, min(arrivals[k] - (time.perf_counter() - t0), 0.001)))
+        done += srv.wait_all(nreq - len(done), timeout_s=600)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in done])
+        es = sum(envs[r["job"]] for r in done)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "requests_per_s": nreq / wall, "env_steps_per_s": es / wall, "mean_batch_jobs": st["mean_batch"],
+                "peak_resident_bytes": st["peak_bytes"]}
+
+    cap = run(False, 0.0)
+    cap_fifo = run(True, 0.0)
+    rate = 0.8 * cap
+    cb = run(False, rate)
+    fifo = run(True, rate)
+    return {"workload": "%d jobs of the serving recipe (16-1024 envs, 4-256 bodies, 64-256 px), %d Poisson requests "
+                        "at 80%% of the continuous-batching capacity; HBM budget 60%% of free memory" % (njobs, nreq),
+            "capacity_requests_per_s": cap, "capacity_fifo_requests_per_s": cap_fifo, "arrival_rate_hz": rate,
+            "continuous_batching": cb, "serialized_fifo": fifo}
+
+
 def kernel_traffic(kind: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
@@ -284,6 +348,13 @@ def main():
 
     flags = env.status()[1]
     clk.stop()
+    serving = None
+    if not args.no_serve and rank == 0:
+        env.close()
+        try:
+            serving = serving_bench(V, S, args.serve_jobs, args.serve_requests)
+        except Exception as ex:  # report why, keep the main line
+            serving = {"error": repr(ex)}
     if rank != 0:
         env.close()
         return
@@ -329,13 +400,15 @@ def main():
         "e2e": e2e,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "serving": serving,
         "gpu_launches": 3 * args.steps,   # sim_kernel, shade_kernel, render_kernel per step
         "status_flags": flags,
         "clocks": clk.summary(),
         "wall_s_coscheduled": wall_co,
     }
     print(json.dumps(out), flush=True)
-    env.close()
+    if args.no_serve:
+        env.close()
 
 
 if __name__ == "__main__":

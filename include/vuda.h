@@ -173,6 +173,9 @@ int32_t vuda_abi_version(void);
 vuda_status vuda_env_create(const vuda_scene* scene, const vuda_sim_params* params,
                             const vuda_env_opts* opts, vuda_env_t* out);
 vuda_status vuda_env_destroy(vuda_env_t env);
+/* Device bytes vuda_env_create would hold for this batch (an upper estimate,
+ * the figure the serving loop admits jobs by).  Host only. */
+vuda_status vuda_env_estimate_bytes(const vuda_scene* scene, const vuda_sim_params* params, int64_t* bytes);
 vuda_status vuda_env_info_get(vuda_env_t env, vuda_env_info* out);
 /* Per-camera first-pixel offsets (host array of num_cams + 1). */
 vuda_status vuda_env_cam_pix_off(vuda_env_t env, int64_t* out);
@@ -271,6 +274,62 @@ vuda_status vuda_env_contact_counts(vuda_env_t env, int32_t* counts);
  * vuda_render; triangle ids are the input order.  Async on `stream`. */
 vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t ntri, int32_t W, int32_t H,
                                     uint32_t* triid, float* depth, uint32_t* count, vuda_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of step+render requests from many jobs.     */
+/* ------------------------------------------------------------------------ */
+/* A job is a batch of environments (a vuda_scene plus sim params) that stays
+ * resident on the device once admitted.  A request asks for one physics step
+ * of all the job's environments followed by the render of all its cameras.
+ * Jobs are admitted in arrival order while their device memory fits
+ * hbm_budget_bytes (0: no limit); a worker thread batches the pending
+ * request of every admitted job into one launch per phase, and pipelines the
+ * launches (the sim phase of the next batch overlaps the render phase of the
+ * current one), so requests arriving while others run join the next batch.
+ * A job's results are the same alone and in any mix. */
+typedef struct vuda_server* vuda_server_t;
+typedef struct {
+    int32_t device;
+    int64_t hbm_budget_bytes;     /* admission limit for resident jobs (0: none) */
+    int32_t max_jobs;             /* resident jobs at once (0: 64) */
+    int32_t max_inflight;         /* batches on the GPU at once, 1..3 (0: 2) */
+    int32_t max_batch_jobs;       /* jobs per batch (0: all pending) */
+    int32_t serialized;           /* 1: sim and render on one stream, no overlap */
+} vuda_serve_opts;
+typedef struct {
+    uint64_t req_id;
+    int64_t job_id;
+    int32_t status;               /* VUDA_OK, VUDA_ERR_BUSY (cancelled), or the admission error */
+    int64_t step;                 /* the job's step index this request computed */
+    double t_submit_ms, t_start_ms, t_done_ms;   /* host steady clock */
+} vuda_result;
+typedef struct {
+    int32_t jobs, admitted, waiting, inflight;
+    int64_t iterations, requests_done;
+    double mean_batch;            /* jobs per launched batch */
+    int32_t max_batch;
+    int64_t used_bytes, peak_bytes;
+} vuda_serve_stats;
+
+vuda_status vuda_serve_create(const vuda_serve_opts* opts, vuda_server_t* out);
+vuda_status vuda_serve_destroy(vuda_server_t server);
+/* Queue a job for admission (the scene is copied).  VUDA_ERR_OOM if the job
+ * alone exceeds the budget. */
+vuda_status vuda_serve_add_job(vuda_server_t server, const vuda_scene* scene, const vuda_sim_params* params,
+                               int64_t* job_id);
+/* Request one step + render of the job; requests of a job run in order. */
+vuda_status vuda_serve_submit(vuda_server_t server, int64_t job_id, uint64_t* req_id);
+/* Completed requests (up to max), waiting up to wait_ms for the first. */
+vuda_status vuda_serve_poll(vuda_server_t server, vuda_result* out, int32_t max, int32_t* n, int32_t wait_ms);
+/* Cancel the job's queued requests and free it once its running ones finish. */
+vuda_status vuda_serve_remove_job(vuda_server_t server, int64_t job_id);
+/* The job's environment handle and frame (for reading results; call while
+ * the job has no request queued or running).  VUDA_ERR_BUSY if not admitted. */
+vuda_status vuda_serve_job_env(vuda_server_t server, int64_t job_id, vuda_env_t* env, vuda_frame* frame);
+vuda_status vuda_serve_stats_get(vuda_server_t server, vuda_serve_stats* out);
+/* Copy the job's last frame to host memory (rgb[P][3], depth[P], triid[P];
+ * any may be NULL).  The job must be idle (VUDA_ERR_BUSY otherwise). */
+vuda_status vuda_serve_read_frame(vuda_server_t server, int64_t job_id, uint8_t* rgb, float* depth, uint32_t* triid);
 
 /* Physics step that allocates no device memory, for callers that cannot
  * allocate: code running inside a graph or stream region it does not own,

@@ -179,9 +179,43 @@ vuda_status destroy_cosched(vuda_env* env) {
 
 }  // namespace
 
+namespace vuda {
+vuda_status env_estimate_bytes(const vuda_scene* sc, const vuda_sim_params* p, int64_t* out) {
+    if (!sc || !p || !out) return (set_error("null argument"), VUDA_ERR_INVALID);
+    const int E = sc->num_envs;
+    if (E < 0 || (E > 0 && (!sc->body_off || !sc->cam_off)) || sc->num_meshes <= 0 || !sc->mesh_tri_off ||
+        !sc->mesh_vert_off)
+        return (set_error("bad scene"), VUDA_ERR_INVALID);
+    const int64_t B = E ? sc->body_off[E] : 0, C = E ? sc->cam_off[E] : 0;
+    int64_t T = 0, P = 0;
+    const int gm = sc->ground_mesh;
+    if (gm < 0 || gm >= sc->num_meshes) return (set_error("bad ground mesh"), VUDA_ERR_INVALID);
+    const int64_t tg = sc->mesh_tri_off[gm + 1] - sc->mesh_tri_off[gm];
+    for (int64_t b = 0; b < B; b++) {
+        int m = sc->mesh_id[b];
+        if (m < 0 || m >= sc->num_meshes) return (set_error("mesh_id out of range"), VUDA_ERR_INVALID);
+        T += sc->mesh_tri_off[m + 1] - sc->mesh_tri_off[m];
+    }
+    T += tg * E;
+    for (int64_t c = 0; c < C; c++) P += (int64_t)sc->cam_w[c] * sc->cam_h[c];
+    int64_t bytes = B * 4 * (3 + 4 + 3 + 3 + 3 + 1 + 3 + 3 + 2 * 7 + 2 + 2) + B + E * 40;
+    bytes += (int64_t)p->max_contacts_per_body * B * kContactStride * 4;   // contact spill (upper bound)
+    bytes += T * 4;                                                          // colour table
+    bytes += (int64_t)sc->mesh_vert_off[sc->num_meshes] * 12 + (int64_t)sc->mesh_tri_off[sc->num_meshes] * 12;
+    bytes += C * 128 + (P / 16 + C) * 16 + 64 * 1024;                       // cameras, items, slack
+    bytes += (int64_t)sc->mesh_tri_off[sc->num_meshes] * 8 + (int64_t)sc->mesh_vert_off[sc->num_meshes] * 8;
+    *out = bytes;
+    return VUDA_OK;
+}
+}  // namespace vuda
+
 extern "C" {
 
 int32_t vuda_abi_version(void) { return 1; }
+
+vuda_status vuda_env_estimate_bytes(const vuda_scene* scene, const vuda_sim_params* params, int64_t* bytes) {
+    return env_estimate_bytes(scene, params, bytes);
+}
 
 const char* vuda_last_error(void) { return g_err.c_str(); }
 

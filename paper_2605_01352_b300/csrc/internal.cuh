@@ -115,5 +115,7 @@ cudaError_t launch_raster_screen(const int32_t* xy, const float* z, int ntri, in
 int render_vcap();
 
 void set_error(const std::string& s);
+// Device bytes a batch will hold once created (an upper estimate).
+vuda_status env_estimate_bytes(const vuda_scene* sc, const vuda_sim_params* p, int64_t* out);
 
 }  // namespace vuda

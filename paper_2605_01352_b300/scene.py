@@ -543,3 +543,19 @@ def custom(bodies: List[dict], *, res: int = 64, params: Optional[SimParams] = N
         cam_w=np.full(C, res, np.int32), cam_h=np.full(C, res, np.int32),
         cam_eye=eye, cam_right=rr, cam_up=uu, cam_fwd=ff, cam_fpy=fpy, light=L,
         params=params or SimParams(), name="custom")
+
+
+def cfg5_jobs(num_jobs: int = 16, max_envs: int = 1024, max_bodies: int = 256, res_choices=(64, 128, 256),
+              seed: int = config_seed(5)) -> List[Scene]:
+    """Serving workload: jobs of log-uniform size in [16, max_envs] envs, each
+    with its own body count (log-uniform in [4, max_bodies], spheres and boxes)
+    and camera resolution."""
+    st = Streams(seed ^ 0x5E4F_0005, 1)
+    jobs = []
+    for j in range(num_jobs):
+        E = int(round(math.exp(st.uniform(math.log(16), math.log(max_envs))[0])))
+        N = int(round(math.exp(st.uniform(math.log(4), math.log(max_bodies))[0])))
+        res = int(res_choices[int(st.next_u64()[0] % np.uint64(len(res_choices)))])
+        jobs.append(generate(E, N, seed + 1000 * (j + 1), kinds="mixed", res=res, substeps=8,
+                             name="cfg5 job %d: %d envs x %d bodies, %dx%d" % (j, E, N, res, res)))
+    return jobs

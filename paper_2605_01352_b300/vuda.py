@@ -90,6 +90,7 @@ _sig("vuda_last_error", [], C.c_char_p)
 _sig("vuda_abi_version", [], C.c_int32)
 _sig("vuda_env_create", [C.POINTER(Scene), C.POINTER(SimParams), C.POINTER(EnvOpts), C.POINTER(vp)])
 _sig("vuda_env_destroy", [vp])
+_sig("vuda_env_estimate_bytes", [C.POINTER(Scene), C.POINTER(SimParams), C.POINTER(C.c_int64)])
 _sig("vuda_env_info_get", [vp, C.POINTER(EnvInfo)])
 _sig("vuda_env_cam_pix_off", [vp, vp])
 _sig("vuda_sim_step", [vp, C.c_int32, vp, vp])
@@ -156,55 +157,81 @@ def sim_params(p) -> SimParams:
                      p.plane, p.max_contacts_per_body)
 
 
+def scene_struct(scene):
+    """vuda_scene view of a paper_2605_01352_b300.scene.Scene; the second value
+    keeps the numpy buffers alive for the duration of the call."""
+    keep = []
+
+    def h(a, dt):
+        x = _np(a, dt)
+        keep.append(x)
+        return _ptr(x)
+
+    sc = Scene()
+    sc.num_envs = scene.num_envs
+    sc.body_off = h(scene.body_off, np.int32)
+    sc.pos = h(scene.pos, np.float32)
+    sc.quat = h(scene.quat, np.float32)
+    sc.vel = h(scene.vel, np.float32)
+    sc.angvel = h(scene.angvel, np.float32)
+    sc.shape_type = h(scene.shape_type, np.uint8)
+    sc.shape_dims = h(scene.shape_dims, np.float32)
+    sc.inv_mass = h(scene.inv_mass, np.float32)
+    sc.inv_inertia = h(scene.inv_inertia, np.float32)
+    sc.mesh_id = h(scene.mesh_id, np.int32)
+    sc.mesh_scale = h(scene.mesh_scale, np.float32)
+    sc.albedo = h(scene.albedo, np.uint32)
+    sc.num_meshes = len(scene.mesh_vert_off) - 1
+    sc.mesh_vert_off = h(scene.mesh_vert_off, np.int32)
+    sc.mesh_verts = h(scene.mesh_verts, np.float32)
+    sc.mesh_tri_off = h(scene.mesh_tri_off, np.int32)
+    sc.mesh_tris = h(scene.mesh_tris, np.int32)
+    sc.ground_mesh = scene.ground_mesh
+    sc.ground_albedo = scene.ground_albedo
+    sc.cam_off = h(scene.cam_off, np.int32)
+    sc.cam_w = h(scene.cam_w, np.int32)
+    sc.cam_h = h(scene.cam_h, np.int32)
+    sc.cam_eye = h(scene.cam_eye, np.float32)
+    sc.cam_right = h(scene.cam_right, np.float32)
+    sc.cam_up = h(scene.cam_up, np.float32)
+    sc.cam_fwd = h(scene.cam_fwd, np.float32)
+    sc.cam_fpy = h(scene.cam_fpy, np.float32)
+    sc.light = (C.c_float * 3)(*[float(x) for x in scene.light])
+    return sc, keep
+
+
+def estimate_bytes(scene, params=None) -> int:
+    """Device bytes a batch of this scene would hold (host-side estimate)."""
+    sc, keep = scene_struct(scene)
+    out = C.c_int64()
+    check(lib.vuda_env_estimate_bytes(C.byref(sc), C.byref(sim_params(params or scene.params)), C.byref(out)),
+          "vuda_env_estimate_bytes")
+    return out.value
+
+
 class Env:
     """A batch of environments resident on the GPU."""
 
     def __init__(self, scene, params=None, hbm_budget_bytes: int = 0, device: int = 0, band_rows: int = 0,
-                 phys_smem_bytes: int = 0, persistent: bool = False):
+                 phys_smem_bytes: int = 0, persistent: bool = False, _handle=None):
         self.scene = scene
-        keep = []
-
-        def h(a, dt):
-            x = _np(a, dt)
-            keep.append(x)
-            return _ptr(x)
-
-        sc = Scene()
-        sc.num_envs = scene.num_envs
-        sc.body_off = h(scene.body_off, np.int32)
-        sc.pos = h(scene.pos, np.float32)
-        sc.quat = h(scene.quat, np.float32)
-        sc.vel = h(scene.vel, np.float32)
-        sc.angvel = h(scene.angvel, np.float32)
-        sc.shape_type = h(scene.shape_type, np.uint8)
-        sc.shape_dims = h(scene.shape_dims, np.float32)
-        sc.inv_mass = h(scene.inv_mass, np.float32)
-        sc.inv_inertia = h(scene.inv_inertia, np.float32)
-        sc.mesh_id = h(scene.mesh_id, np.int32)
-        sc.mesh_scale = h(scene.mesh_scale, np.float32)
-        sc.albedo = h(scene.albedo, np.uint32)
-        sc.num_meshes = len(scene.mesh_vert_off) - 1
-        sc.mesh_vert_off = h(scene.mesh_vert_off, np.int32)
-        sc.mesh_verts = h(scene.mesh_verts, np.float32)
-        sc.mesh_tri_off = h(scene.mesh_tri_off, np.int32)
-        sc.mesh_tris = h(scene.mesh_tris, np.int32)
-        sc.ground_mesh = scene.ground_mesh
-        sc.ground_albedo = scene.ground_albedo
-        sc.cam_off = h(scene.cam_off, np.int32)
-        sc.cam_w = h(scene.cam_w, np.int32)
-        sc.cam_h = h(scene.cam_h, np.int32)
-        sc.cam_eye = h(scene.cam_eye, np.float32)
-        sc.cam_right = h(scene.cam_right, np.float32)
-        sc.cam_up = h(scene.cam_up, np.float32)
-        sc.cam_fwd = h(scene.cam_fwd, np.float32)
-        sc.cam_fpy = h(scene.cam_fpy, np.float32)
-        sc.light = (C.c_float * 3)(*[float(x) for x in scene.light])
+        if _handle is not None:            # a handle owned elsewhere (a serving job)
+            self.h = _handle
+            self._owned = False
+            self._read_info()
+            return
+        self._owned = True
+        sc, keep = scene_struct(scene)
         self.params = params or scene.params
         prm = sim_params(self.params)
         opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes, int(persistent))
         handle = vp()
         check(lib.vuda_env_create(C.byref(sc), C.byref(prm), C.byref(opts), C.byref(handle)), "vuda_env_create")
+        del keep
         self.h = handle
+        self._read_info()
+
+    def _read_info(self):
         info = EnvInfo()
         check(lib.vuda_env_info_get(self.h, C.byref(info)), "vuda_env_info_get")
         self.E, self.B, self.C = info.num_envs, info.num_bodies, info.num_cams
@@ -221,7 +248,8 @@ class Env:
     # -- lifetime ---------------------------------------------------------------
     def close(self):
         if getattr(self, "h", None):
-            lib.vuda_env_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lib.vuda_env_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -376,3 +404,111 @@ def sim_step_noalloc(arrays: dict, params, nsteps: int, max_bodies: int, smem_pe
                                     g("shape_type"), g("shape_dims"), g("inv_mass"), g("inv_inertia"), g("force"),
                                     C.byref(prm), nsteps, g("pose"), g("flags"), g("ncontacts"), smem_per_env,
                                     _stream(stream)), "vuda_sim_step_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+class ServeOpts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("max_jobs", C.c_int32),
+                ("max_inflight", C.c_int32), ("max_batch_jobs", C.c_int32), ("serialized", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("req_id", C.c_uint64), ("job_id", C.c_int64), ("status", C.c_int32), ("step", C.c_int64),
+                ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("jobs", C.c_int32), ("admitted", C.c_int32), ("waiting", C.c_int32), ("inflight", C.c_int32),
+                ("iterations", C.c_int64), ("requests_done", C.c_int64), ("mean_batch", C.c_double),
+                ("max_batch", C.c_int32), ("used_bytes", C.c_int64), ("peak_bytes", C.c_int64)]
+
+
+_sig("vuda_serve_create", [C.POINTER(ServeOpts), C.POINTER(vp)])
+_sig("vuda_serve_destroy", [vp])
+_sig("vuda_serve_add_job", [vp, C.POINTER(Scene), C.POINTER(SimParams), C.POINTER(C.c_int64)])
+_sig("vuda_serve_submit", [vp, C.c_int64, C.POINTER(C.c_uint64)])
+_sig("vuda_serve_poll", [vp, C.POINTER(Result), C.c_int32, C.POINTER(C.c_int32), C.c_int32])
+_sig("vuda_serve_remove_job", [vp, C.c_int64])
+_sig("vuda_serve_job_env", [vp, C.c_int64, C.POINTER(vp), C.POINTER(Frame)])
+_sig("vuda_serve_stats_get", [vp, C.POINTER(ServeStats)])
+_sig("vuda_serve_read_frame", [vp, C.c_int64, vp, vp, vp])
+
+
+class Server:
+    """Continuous-batching server for step+render requests of many jobs."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_jobs: int = 64, max_inflight: int = 2,
+                 max_batch_jobs: int = 0, serialized: bool = False, device: int = 0):
+        h = vp()
+        check(lib.vuda_serve_create(C.byref(ServeOpts(device, hbm_budget_bytes, max_jobs, max_inflight,
+                                                      max_batch_jobs, int(serialized))), C.byref(h)),
+              "vuda_serve_create")
+        self.h = h
+        self.scenes = {}
+        self._buf = (Result * 4096)()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.vuda_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_job(self, scene, params=None) -> int:
+        sc, keep = scene_struct(scene)
+        jid = C.c_int64()
+        check(lib.vuda_serve_add_job(self.h, C.byref(sc), C.byref(sim_params(params or scene.params)),
+                                     C.byref(jid)), "vuda_serve_add_job")
+        self.scenes[jid.value] = scene
+        return jid.value
+
+    def submit(self, job: int) -> int:
+        r = C.c_uint64()
+        check(lib.vuda_serve_submit(self.h, job, C.byref(r)), "vuda_serve_submit")
+        return r.value
+
+    def poll(self, wait_ms: int = 0, max_results: int = 4096):
+        n = C.c_int32()
+        check(lib.vuda_serve_poll(self.h, self._buf, min(max_results, 4096), C.byref(n), wait_ms), "vuda_serve_poll")
+        return [dict(req_id=r.req_id, job=r.job_id, status=r.status, step=r.step, t_submit_ms=r.t_submit_ms,
+                     t_start_ms=r.t_start_ms, t_done_ms=r.t_done_ms) for r in self._buf[:n.value]]
+
+    def remove_job(self, job: int):
+        check(lib.vuda_serve_remove_job(self.h, job), "vuda_serve_remove_job")
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        check(lib.vuda_serve_stats_get(self.h, C.byref(st)), "vuda_serve_stats_get")
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def job_env(self, job: int) -> Env:
+        """The job's resident batch (borrowed; read it while the job is idle)."""
+        e = vp()
+        check(lib.vuda_serve_job_env(self.h, job, C.byref(e), None), "vuda_serve_job_env")
+        return Env(self.scenes[job], _handle=e)
+
+    def read_frame(self, job: int):
+        env = self.job_env(job)
+        P = env.P
+        rgb = np.zeros((P, 3), np.uint8)
+        dep = np.zeros(P, np.float32)
+        tid = np.zeros(P, np.uint32)
+        check(lib.vuda_serve_read_frame(self.h, job, _ptr(rgb), _ptr(dep), _ptr(tid)), "vuda_serve_read_frame")
+        return rgb, dep, tid
+
+    def wait_all(self, n: int, timeout_s: float = 60.0):
+        """Collect n results (blocking)."""
+        import time
+        out = []
+        t0 = time.time()
+        while len(out) < n:
+            out += self.poll(wait_ms=50)
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("serving results did not arrive")
+        return out

@@ -1,0 +1,123 @@
+"""Serving loop: continuous batching of step+render requests from several
+jobs, admission by HBM budget, cancellation.  A job's results are the same
+alone and in a mix (bit for bit), and match the oracle."""
+import random
+import time
+
+import numpy as np
+import pytest
+
+from paper_2605_01352_b300 import scene as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2605_01352_b300 import build
+    build.build()
+    from paper_2605_01352_b300 import vuda
+    return vuda
+
+
+def _jobs():
+    return {"A": S.cfg2(8), "B": S.cfg1(6), "C": S.cfg4(5), "D": S.cfg2(4, env_base=100)}
+
+
+def _alone(V, sc, n):
+    srv = V.Server()
+    j = srv.add_job(sc)
+    for _ in range(n):
+        srv.submit(j)
+    res = srv.wait_all(n)
+    assert all(r["status"] == 0 for r in res)
+    st = srv.job_env(j).get_state()
+    fr = srv.read_frame(j)
+    srv.close()
+    return st, fr
+
+
+def test_job_results_are_the_same_alone_and_in_a_mix(V, orc):
+    jobs = _jobs()
+    counts = {"A": 5, "B": 7, "C": 4, "D": 6}
+    srv = V.Server(max_inflight=2)
+    ids = {k: srv.add_job(sc) for k, sc in jobs.items()}
+    order = [k for k, n in counts.items() for _ in range(n)]
+    random.Random(4).shuffle(order)
+    for k in order:
+        srv.submit(ids[k])
+        time.sleep(random.Random(len(order)).random() * 0.002)
+    res = srv.wait_all(sum(counts.values()))
+    assert all(r["status"] == 0 for r in res)
+    # requests of a job complete in order, with consecutive step indices
+    for k, jid in ids.items():
+        steps = [r["step"] for r in res if r["job"] == jid]
+        assert steps == list(range(counts[k]))
+    st = srv.stats()
+    assert st["requests_done"] == sum(counts.values())
+    assert st["max_batch"] >= 2          # requests of several jobs shared a launch
+    mixed = {k: (srv.job_env(ids[k]).get_state(), srv.read_frame(ids[k])) for k in jobs}
+    srv.close()
+    for k in ("A", "C"):
+        st_a, fr_a = _alone(V, jobs[k], counts[k])
+        st_m, fr_m = mixed[k]
+        for f in st_a:
+            np.testing.assert_array_equal(st_a[f], st_m[f])
+        for x, y in zip(fr_a, fr_m):
+            np.testing.assert_array_equal(x, y)
+    # and the job matches the oracle
+    sc = jobs["A"]
+    so, _, _ = orc.sim_step(sc, counts["A"])
+    for f in ("pos", "vel", "quat", "angvel"):
+        np.testing.assert_allclose(mixed["A"][0][f], so[f], rtol=1e-5, atol=1e-5)
+    o_rgb, o_dep, o_tid, _ = orc.render(sc, so["pos"], so["quat"])
+    np.testing.assert_array_equal(mixed["A"][1][2], o_tid)
+    np.testing.assert_allclose(mixed["A"][1][1], o_dep, rtol=1e-6)
+
+
+def test_admission_waits_for_budget(V):
+    """With room for one job at a time, the second job is admitted only after
+    the first is removed; its requests then complete."""
+    a, b = S.cfg1(4), S.cfg1(4, )
+    est = V.estimate_bytes(a)
+    srv = V.Server(hbm_budget_bytes=int(est * 1.5))
+    ja = srv.add_job(a)
+    jb = srv.add_job(b)
+    for _ in range(2):
+        srv.submit(ja)
+        srv.submit(jb)
+    got = srv.wait_all(2)
+    assert {r["job"] for r in got} == {ja}
+    st = srv.stats()
+    assert st["admitted"] == 1 and st["waiting"] == 1
+    time.sleep(0.05)
+    assert srv.poll() == []                # b's requests are still waiting for admission
+    srv.remove_job(ja)
+    got = srv.wait_all(2)
+    assert {r["job"] for r in got} == {jb} and all(r["status"] == 0 for r in got)
+    srv.close()
+
+
+def test_errors_and_cancellation(V):
+    sc = S.cfg1(2)
+    srv = V.Server(hbm_budget_bytes=1024)
+    with pytest.raises(V.VudaError) as ex:
+        srv.add_job(sc)                     # larger than the whole budget
+    assert ex.value.status == V.ERR_OOM
+    with pytest.raises(V.VudaError) as ex:
+        srv.submit(12345)
+    assert ex.value.status == V.ERR_INVALID
+    srv.close()
+    srv = V.Server(hbm_budget_bytes=int(V.estimate_bytes(sc) * 1.5))
+    j1 = srv.add_job(sc)
+    j2 = srv.add_job(sc)                    # waits for admission
+    r = [srv.submit(j2) for _ in range(3)]
+    srv.remove_job(j2)                      # its queued requests are cancelled
+    got = srv.wait_all(3)
+    assert sorted(x["req_id"] for x in got) == sorted(r)
+    assert all(x["status"] == V.ERR_BUSY for x in got)
+    srv.submit(j1)
+    assert srv.wait_all(1)[0]["status"] == 0
+    srv.close()
