@@ -328,6 +328,15 @@ def main():
     env.coschedule(V.COSCHED_STREAMS)
     env.pipeline_run(args.warmup, ring)
     t_st, _, _ = timed(args.steps)
+    # the same, replayed from a captured CUDA graph of 8 pipelined steps
+    t_graph = None
+    try:
+        env.pipeline_capture(8, ring)
+        env.pipeline_run(8, ring)
+        t_graph, _, _ = timed(args.steps - args.steps % 8)
+        t_graph = t_graph * args.steps / (args.steps - args.steps % 8)
+    except Exception as ex:  # report why, keep the main line
+        t_graph = repr(ex)
     env.coschedule(V.COSCHED_GREEN, args.sim_sms)
 
     # end to end through the host-buffer loop: forces in, frames out
@@ -393,6 +402,8 @@ def main():
                    "l2": "per-step working set (frames 2 x %.0f MB) exceeds the 126 MB L2" % (bytes_out / 1e6)},
         "serialized": {"value": v_ser, "ms_per_step": 1000.0 * t_ser / args.steps},
         "coscheduled_streams_shared_sms": {"value": v_st, "ms_per_step": 1000.0 * t_st / args.steps},
+        "coscheduled_streams_graph": ({"value": ws * E * args.steps / t_graph, "ms_per_step": 1000.0 * t_graph / args.steps}
+                                      if isinstance(t_graph, float) else {"error": t_graph}),
         "speedup_vs_serialized": v_co / v_ser,
         "phase_ms": {"sim": Ts, "render": Tr, "ideal_overlap": (Ts + Tr) / max(Ts, Tr)},
         "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,

@@ -236,6 +236,17 @@ typedef struct {
 vuda_status vuda_pipeline_run(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
                               vuda_timing* timing);
 
+/* Capture steps_per_graph (even) pipelined steps of the loop -- as
+ * vuda_pipeline_run would enqueue them with this ring and the current
+ * co-scheduling -- into a CUDA graph.  Later vuda_pipeline_run calls with the
+ * same ring, a multiple of steps_per_graph steps and the same pose-slot
+ * parity replay the graph instead of launching kernel by kernel (step
+ * latencies are then reported as NaN).  Returns VUDA_ERR_UNSUPPORTED if the
+ * driver refuses the capture.  Invalidated by vuda_coschedule*. */
+vuda_status vuda_pipeline_capture(vuda_env_t env, int32_t steps_per_graph, const vuda_frame* ring,
+                                  vuda_stream_t stream);
+vuda_status vuda_pipeline_release_graph(vuda_env_t env);
+
 /* The same loop with host buffers (end-to-end use): each step copies its
  * force input from host memory (h_force: [3][B] floats, or [nsteps][3][B]
  * when force_per_step != 0; NULL for none) to the device before sim(t), and

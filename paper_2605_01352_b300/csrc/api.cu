@@ -158,6 +158,11 @@ void destroy_events(vuda_env* env) {
 
 vuda_status destroy_cosched(vuda_env* env) {
     if (env->sim_s || env->ren_s) cudaDeviceSynchronize();
+    if (env->gexec) {
+        cudaGraphExecDestroy(env->gexec);
+        env->gexec = nullptr;
+        env->gsteps = 0;
+    }
     destroy_events(env);
     Driver& dr = driver();
     if (env->cos_mode == VUDA_COSCHED_GREEN) {
@@ -570,6 +575,7 @@ vuda_status vuda_env_destroy(vuda_env_t env) {
     if (!env) return VUDA_OK;
     cudaSetDevice(env->device);
     destroy_cosched(env);
+    if (env->gexec) cudaGraphExecDestroy(env->gexec);
     destroy_events(env);
     if (env->copy_s) cudaStreamDestroy(env->copy_s);
     for (cudaEvent_t e : env->copy_done)
@@ -750,11 +756,58 @@ void fill_timing(vuda_timing* tm, int n, cudaEvent_t* t0, cudaEvent_t* t0e, cuda
 }
 }  // namespace
 
+static bool same_frame(const vuda_frame& a, const vuda_frame& b) {
+    return a.rgb == b.rgb && a.depth == b.depth && a.triid == b.triid;
+}
+
+static void drop_graph(vuda_env_t env) {
+    if (env->gexec) cudaGraphExecDestroy(env->gexec);
+    env->gexec = nullptr;
+    env->gsteps = 0;
+}
+
+// Replays of the captured pipeline: nsteps / gsteps graph launches on the
+// sim stream (or `stream`); each graph holds gsteps pipelined steps and ends
+// joined, so consecutive launches are ordered.
+static vuda_status run_graph(vuda_env_t env, int32_t nsteps, vuda_stream_t stream, vuda_timing* tm) {
+    cudaStream_t ss = env->cos_mode ? env->sim_s : (cudaStream_t)stream;
+    vuda_status s = ensure_events(env->ev_sim, env->c_sim, 2);
+    if (s != VUDA_OK) return s;
+    cudaEvent_t* es = env->ev_sim.data();
+    if (env->cos_mode) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    {
+        ScopedCtx g(env->c_sim);
+        if (tm) CK(cudaEventRecord(es[0], ss));
+        for (int k = 0; k < nsteps / env->gsteps; k++) CK(cudaGraphLaunch(env->gexec, ss));
+        if (tm) CK(cudaEventRecord(es[1], ss));
+    }
+    CK(cudaStreamSynchronize(ss));
+    env->steps += nsteps;
+    if (tm) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, es[0], es[1]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = __builtin_nanf("");
+        }
+        tm->total_ms = ms;
+        for (int t = 0; t < nsteps; t++) {
+            if (tm->step_ms) tm->step_ms[t] = __builtin_nanf("");
+            if (tm->sim_ms) tm->sim_ms[t] = __builtin_nanf("");
+            if (tm->render_ms) tm->render_ms[t] = __builtin_nanf("");
+        }
+    }
+    return VUDA_OK;
+}
+
 static vuda_status pipeline(vuda_env_t env, int32_t nsteps, const vuda_frame* ring, vuda_stream_t stream,
                             vuda_timing* tm, const float* h_force, int32_t force_per_step, uint8_t* h_rgb,
-                            float* h_depth) {
+                            float* h_depth, bool capture = false) {
     if (!env || !ring) return invalid("null argument");
     if (nsteps < 0) return invalid("nsteps < 0");
+    if (!capture && !h_rgb && env->gexec && env->gmode == env->cos_mode && nsteps % env->gsteps == 0 &&
+        (int)(env->steps & 1) == env->gparity && same_frame(ring[0], env->gring[0]) &&
+        same_frame(ring[1], env->gring[1]))
+        return run_graph(env, nsteps, stream, tm);
     const bool timing = tm != nullptr;
     const bool co = env->cos_mode != 0;
     const bool host = h_rgb != nullptr;
@@ -781,7 +834,7 @@ static vuda_status pipeline(vuda_env_t env, int32_t nsteps, const vuda_frame* ri
     cudaEvent_t *t0 = es + 2, *t0e = es + 2 + per, *t1s = er + 2, *t1 = er + 2 + per;
     cudaStream_t ss = co ? env->sim_s : (cudaStream_t)stream;
     cudaStream_t rs = co ? env->ren_s : (cudaStream_t)stream;
-    if (co || host) CK(cudaStreamSynchronize((cudaStream_t)stream));  // start after the caller's prior work
+    if ((co || host) && !capture) CK(cudaStreamSynchronize((cudaStream_t)stream));  // after the caller's prior work
     for (int t = 0; t < nsteps; t++) {
         const int slot = (int)(env->steps & 1);
         const int fs = t & 1;
@@ -821,10 +874,78 @@ static vuda_status pipeline(vuda_env_t env, int32_t nsteps, const vuda_frame* ri
             CK(cudaEventRecord(env->copy_done[fs], env->copy_s));
         }
     }
+    if (capture) {
+        // join the render stream back into the capturing sim stream
+        if (co) {
+            {
+                ScopedCtx g(env->c_ren);
+                CK(cudaEventRecord(er[2], rs));
+            }
+            ScopedCtx g(env->c_sim);
+            CK(cudaStreamWaitEvent(ss, er[2], 0));
+        }
+        return VUDA_OK;
+    }
     CK(cudaStreamSynchronize(ss));
     CK(cudaStreamSynchronize(rs));
     if (host) CK(cudaStreamSynchronize(env->copy_s));
     if (timing) fill_timing(tm, nsteps, t0, t0e, t1s, t1);
+    return VUDA_OK;
+}
+
+vuda_status vuda_pipeline_capture(vuda_env_t env, int32_t steps_per_graph, const vuda_frame* ring,
+                                  vuda_stream_t stream) {
+    if (!env || !ring) return invalid("null argument");
+    if (steps_per_graph <= 0 || (steps_per_graph & 1)) return invalid("steps_per_graph must be even and positive");
+    drop_graph(env);
+    const bool co = env->cos_mode != 0;
+    cudaStream_t ss = co ? env->sim_s : (cudaStream_t)stream;
+    if (!co && ss == nullptr) return invalid("capture needs a non-default stream (or co-scheduling)");
+    // make sure the event pools exist before capture starts (3 render events: 2 slots + join)
+    vuda_status st = ensure_events(env->ev_sim, env->c_sim, 2);
+    if (st == VUDA_OK) st = ensure_events(env->ev_ren, env->c_ren, 3);
+    if (st != VUDA_OK) return st;
+    CK(cudaStreamSynchronize(ss));
+    const int64_t steps0 = env->steps;
+    cudaGraph_t graph = nullptr;
+    {
+        ScopedCtx g(env->c_sim);
+        CK(cudaStreamBeginCapture(ss, cudaStreamCaptureModeThreadLocal));
+    }
+    st = pipeline(env, steps_per_graph, ring, stream, nullptr, nullptr, 0, nullptr, nullptr, true);
+    cudaError_t ce;
+    {
+        ScopedCtx g(env->c_sim);
+        ce = cudaStreamEndCapture(ss, &graph);
+    }
+    env->steps = steps0;   // nothing ran yet
+    if (st != VUDA_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (st == VUDA_OK) {
+            set_error(std::string("stream capture: ") + cudaGetErrorString(ce));
+            st = VUDA_ERR_UNSUPPORTED;
+        }
+        return st;
+    }
+    ce = cudaGraphInstantiate(&env->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        env->gexec = nullptr;
+        set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        return VUDA_ERR_UNSUPPORTED;
+    }
+    env->gsteps = steps_per_graph;
+    env->gparity = (int)(steps0 & 1);
+    env->gmode = env->cos_mode;
+    env->gring[0] = ring[0];
+    env->gring[1] = ring[1];
+    return VUDA_OK;
+}
+
+vuda_status vuda_pipeline_release_graph(vuda_env_t env) {
+    if (!env) return invalid("null env");
+    drop_graph(env);
     return VUDA_OK;
 }
 

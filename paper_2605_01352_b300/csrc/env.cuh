@@ -41,6 +41,10 @@ struct vuda_env {
     int nshade = 0;
     int* counters = nullptr;                      // [2]: sim, render
     int sim_grid = 0, ren_grid = 0;
+    // captured pipeline (CUDA graph of gsteps pipelined steps)
+    cudaGraphExec_t gexec = nullptr;
+    int gsteps = 0, gparity = 0, gmode = 0;
+    vuda_frame gring[2] = {};
     // host-buffer loop: device force ring and a copy stream (primary context)
     float* dforce = nullptr;                      // [2][3][B]
     cudaStream_t copy_s = nullptr;

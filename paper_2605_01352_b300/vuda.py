@@ -99,6 +99,8 @@ _sig("vuda_coschedule", [vp, C.POINTER(CoschedOpts), C.POINTER(vp), C.POINTER(vp
 _sig("vuda_coschedule_reset", [vp])
 _sig("vuda_pipeline_run", [vp, C.c_int32, C.POINTER(Frame), vp, C.POINTER(Timing)])
 _sig("vuda_pipeline_run_host", [vp, C.c_int32, vp, C.c_int32, vp, vp, C.POINTER(Frame), vp, C.POINTER(Timing)])
+_sig("vuda_pipeline_capture", [vp, C.c_int32, C.POINTER(Frame), vp])
+_sig("vuda_pipeline_release_graph", [vp])
 _sig("vuda_wait", [vp, C.c_int32])
 _sig("vuda_env_get_state", [vp, C.POINTER(State)])
 _sig("vuda_env_set_state", [vp, C.POINTER(State)])
@@ -334,6 +336,15 @@ class Env:
                                          vp(h_depth.data_ptr()), frames, _stream(stream),
                                          C.byref(tm) if timing else None), "vuda_pipeline_run_host")
         return self._timing_out(tm, arr, nsteps) if timing else None
+
+    def pipeline_capture(self, steps_per_graph: int, ring: Sequence[dict], stream=None):
+        """Capture steps_per_graph pipelined steps into a CUDA graph that later
+        pipeline_run calls with this ring replay."""
+        frames = (Frame * 2)(self.frame_struct(ring[0]), self.frame_struct(ring[1 % len(ring)]))
+        check(lib.vuda_pipeline_capture(self.h, steps_per_graph, frames, _stream(stream)), "vuda_pipeline_capture")
+
+    def pipeline_release_graph(self):
+        check(lib.vuda_pipeline_release_graph(self.h), "vuda_pipeline_release_graph")
 
     def wait(self, phase: int):
         check(lib.vuda_wait(self.h, phase), "vuda_wait")

@@ -46,9 +46,13 @@ def test_job_results_are_the_same_alone_and_in_a_mix(V, orc):
     ids = {k: srv.add_job(sc) for k, sc in jobs.items()}
     order = [k for k, n in counts.items() for _ in range(n)]
     random.Random(4).shuffle(order)
-    for k in order:
+    # two waves submitted back to back: requests arriving while a launch is on
+    # the GPU are batched into the next one
+    for k in order[: len(order) // 2]:
         srv.submit(ids[k])
-        time.sleep(random.Random(len(order)).random() * 0.002)
+    time.sleep(0.003)
+    for k in order[len(order) // 2:]:
+        srv.submit(ids[k])
     res = srv.wait_all(sum(counts.values()))
     assert all(r["status"] == 0 for r in res)
     # requests of a job complete in order, with consecutive step indices
