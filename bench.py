@@ -242,6 +242,20 @@ def serving_bench(V, S, njobs: int, nreq: int):
             "continuous_batching": cb, "serialized_fifo": fifo}
 
 
+def sim_flops(contacts: float, bodies: int, substeps: int, iterations: int) -> float:
+    """Floating-point operations of one environment-step of the physics as
+    the method defines them (each add, mul, div and sqrt counted once): per
+    body and substep 116 (velocity, rotation, world inverse inertia,
+    position and quaternion update); per candidate pair 12 (bounding-sphere
+    test); about 40 per narrow-phase item (taken as 2.7 items per contact);
+    per contact 160 to set up and 95 per Jacobi iteration; per body-contact
+    list entry 6 and per body 27 per iteration for the sums and update."""
+    n, c = bodies, contacts
+    entries = 2.0 * c - n   # pair contacts appear in two bodies' lists
+    per_sub = 116 * n + 12 * n * (n - 1) / 2 + 40 * 2.7 * c + 160 * c + iterations * (95 * c + 6 * entries + 27 * n)
+    return per_sub * substeps
+
+
 def kernel_traffic(kind: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
@@ -337,6 +351,12 @@ def main():
         t_graph = t_graph * args.steps / (args.steps - args.steps % 8)
     except Exception as ex:  # report why, keep the main line
         t_graph = repr(ex)
+    # the autotuner's own choice (band height, co-scheduling mode and split, graph)
+    try:
+        tuned = env.autotune(ring, steps=6, use_cache=False)
+        tuned["env_steps_per_s"] = ws * E * 1000.0 / tuned["ms_per_step"]
+    except Exception as ex:  # report why, keep the main line
+        tuned = {"error": repr(ex)}
     env.coschedule(V.COSCHED_GREEN, args.sim_sms)
 
     # end to end through the host-buffer loop: forces in, frames out
@@ -356,6 +376,8 @@ def main():
                "path": "vuda_pipeline_run_host (co-scheduled), pinned host buffers, wall clock"}
 
     flags = env.status()[1]
+    env_stats = {"contacts_mean": float(env.contact_counts().mean()), "bodies": 32,
+                 "substeps": sc.params.substeps, "iterations": sc.params.iterations}
     clk.stop()
     serving = None
     if not args.no_serve and rank == 0:
@@ -368,11 +390,13 @@ def main():
         env.close()
         return
 
+    dom = "render" if Tr >= Ts else "sim"
     v_co = ws * E * args.steps / t_co
     v_ser = ws * E * args.steps / t_ser
     v_st = ws * E * args.steps / t_st
     # dominant kernel by share of the serialized step
-    dom = "render" if Tr >= Ts else "sim"
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sm_count * 128 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12   # TFLOP/s, one op per lane
     if dom == "render":
         alg = bytes_out + bytes_pose
         ach = alg / (Tr / 1000.0) / 1e9
@@ -381,11 +405,14 @@ def main():
                 "algorithmic_bytes_per_launch": alg, "launch_ms": Tr,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
     else:
-        alg = bytes_state
-        ach = alg / (Ts / 1000.0) / 1e9
-        roof = {"kernel": "sim_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": kernel_traffic("sim"), "algorithmic_bytes_per_launch": alg,
-                "launch_ms": Ts, "peak_source": peak_src}
+        flops = sim_flops(env_stats["contacts_mean"], env_stats["bodies"], env_stats["substeps"],
+                          env_stats["iterations"]) * E
+        ach = flops / (Ts / 1000.0) / 1e12
+        roof = {"kernel": "sim_kernel", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": kernel_traffic("sim"), "algorithmic_flops_per_launch": flops,
+                "launch_ms": Ts, "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock (unfused ops; the "
+                "path is built without FMA contraction)", "hbm_bytes_per_launch": bytes_state,
+                "hbm_achieved_gbs": bytes_state / (Ts / 1000.0) / 1e9}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         try:
@@ -402,6 +429,7 @@ def main():
                    "l2": "per-step working set (frames 2 x %.0f MB) exceeds the 126 MB L2" % (bytes_out / 1e6)},
         "serialized": {"value": v_ser, "ms_per_step": 1000.0 * t_ser / args.steps},
         "coscheduled_streams_shared_sms": {"value": v_st, "ms_per_step": 1000.0 * t_st / args.steps},
+        "autotuned": tuned,
         "coscheduled_streams_graph": ({"value": ws * E * args.steps / t_graph, "ms_per_step": 1000.0 * t_graph / args.steps}
                                       if isinstance(t_graph, float) else {"error": t_graph}),
         "speedup_vs_serialized": v_co / v_ser,

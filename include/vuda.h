@@ -247,6 +247,24 @@ vuda_status vuda_pipeline_capture(vuda_env_t env, int32_t steps_per_graph, const
                                   vuda_stream_t stream);
 vuda_status vuda_pipeline_release_graph(vuda_env_t env);
 
+/* Autotuner: measures the loop under candidate configurations -- render band
+ * height (16/32/64/128 rows), serialized / co-scheduled on shared SMs /
+ * co-scheduled on disjoint partitions of 1/4, 1/2 and 3/4 of the SMs, and CUDA
+ * graph replay -- and leaves the batch configured with the fastest.  Results
+ * are cached per batch shape for the process (use_cache = 1 reuses them
+ * without measuring).  The trials step the batch; its state and pose slots
+ * are restored afterwards.  ring: the two frames the loop will use. */
+typedef struct {
+    int32_t steps;                /* measured steps per trial (0: 6) */
+    int32_t use_cache;
+} vuda_tune_opts;
+typedef struct {
+    int32_t band_rows, cosched_mode, sim_sms, graph_steps;
+    float ms_per_step, ms_per_step_serialized;
+    int32_t trials, from_cache;
+} vuda_tune_result;
+vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda_frame* ring, vuda_tune_result* out);
+
 /* The same loop with host buffers (end-to-end use): each step copies its
  * force input from host memory (h_force: [3][B] floats, or [nsteps][3][B]
  * when force_per_step != 0; NULL for none) to the device before sim(t), and

@@ -4,9 +4,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -214,6 +217,65 @@ vuda_status env_estimate_bytes(const vuda_scene* sc, const vuda_sim_params* p, i
 }
 }  // namespace vuda
 
+namespace {
+
+// Rebuild the render work items (and their persistent lists) for a new band
+// height.  The previous device arrays stay owned by the batch until destroy.
+vuda_status set_band_rows(vuda_env* env, int br) {
+    if (br <= 0 || (env->C && render_smem_for(br, env->max_w) > 227 * 1024)) return invalid("band rows out of range");
+    std::vector<int32_t> ic, iy;
+    for (int c = 0; c < env->C; c++)
+        for (int y = 0; y < env->h_cam_h[c]; y += br) {
+            ic.push_back(c);
+            iy.push_back(y);
+        }
+    vuda_status s = upload(env, &env->item_cam, ic.data(), ic.size());
+    if (s == VUDA_OK) s = upload(env, &env->item_y0, iy.data(), iy.size());
+    if (s != VUDA_OK) return s;
+    if (env->persistent) {
+        std::vector<int> io(ic.size());
+        for (size_t i = 0; i < io.size(); i++) io[i] = (int)i;
+        auto cost = [&](int i) {
+            int c = ic[i], e = env->h_cam_env[c];
+            int rows = std::min(br, env->h_cam_h[c] - iy[i]);
+            return (double)rows * env->h_cam_w[c] + 4.0 * (double)(env->h_env_tri_base[e + 1] - env->h_env_tri_base[e]);
+        };
+        std::stable_sort(io.begin(), io.end(), [&](int a, int b) { return cost(a) > cost(b); });
+        for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
+            std::vector<int4> ri(io.size());
+            for (size_t k = 0; k < io.size(); k++) ri[k] = make_int4(slot << 24, ic[io[k]], iy[io[k]], 0);
+            s = upload(env, &env->ren_items[slot], ri.data(), ri.size());
+        }
+        int dev_sms = 0;
+        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
+        env->ren_grid = std::max(1, std::min((int)ic.size(), dev_sms * render_ctas_per_sm(br, env->max_w)));
+    }
+    if (s != VUDA_OK) return s;
+    env->band_rows = br;
+    env->nitems = (int)ic.size();
+    env->h_item_cam = ic;
+    env->h_item_y0 = iy;
+    if (env->gexec) {
+        cudaGraphExecDestroy(env->gexec);
+        env->gexec = nullptr;
+        env->gsteps = 0;
+    }
+    return VUDA_OK;
+}
+
+struct TuneKey {
+    int E, B, C, max_bodies, max_w, max_h, persistent;
+    int64_t T;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(E, B, C, max_bodies, max_w, max_h, persistent, T) <
+               std::tie(o.E, o.B, o.C, o.max_bodies, o.max_w, o.max_h, o.persistent, o.T);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, vuda_tune_result> g_tune_cache;
+
+}  // namespace
+
 extern "C" {
 
 int32_t vuda_abi_version(void) { return 1; }
@@ -391,6 +453,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     (void)Tg;
     (void)Vg;
     env->T = E ? env_tri_base[E] : 0;
+    env->h_env_tri_base = env_tri_base;
 
     // physics shared memory and spill
     const int mcpb = prm->max_contacts_per_body;
@@ -412,6 +475,11 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     env->nitems = (int)item_cam.size();
     env->h_item_cam = item_cam;
     env->h_item_y0 = item_y0;
+    env->h_cam_w.assign(sc->cam_w, sc->cam_w + C);
+    env->h_cam_h.assign(sc->cam_h, sc->cam_h + C);
+    env->h_cam_env = cam_env;
+    env->h_body_off.assign(sc->body_off, sc->body_off + E + 1);
+    env->max_h = max_h;
     if (C && render_smem_for(br, max_w) > 227 * 1024) {
         delete env;
         return invalid("render band too large for shared memory (lower render_band_rows)");
@@ -1039,6 +1107,139 @@ vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t n
         set_error(std::string("raster launch: ") + cudaGetErrorString(e));
         return VUDA_ERR_CUDA;
     }
+    return VUDA_OK;
+}
+
+vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda_frame* ring, vuda_tune_result* out) {
+    if (!env || !ring || !out) return invalid("null argument");
+    vuda_tune_opts o{};
+    if (opts) o = *opts;
+    const int K = o.steps > 0 ? o.steps : 6;
+    TuneKey key{env->E, env->B, env->C, env->max_bodies, env->max_w, env->max_h, env->persistent, env->T};
+    vuda_tune_result best{};
+    bool cached = false;
+    if (o.use_cache) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    // the trials step the batch: keep its state and restore it afterwards
+    const size_t B = env->B;
+    std::vector<float> pos(3 * B), quat(4 * B), vel(3 * B), ang(3 * B), p0(7 * B), p1(7 * B);
+    vuda_state st{pos.data(), quat.data(), vel.data(), ang.data()};
+    vuda_status s = vuda_env_get_state(env, &st);
+    if (s != VUDA_OK) return s;
+    if (B) {
+        CK(cudaMemcpy(p0.data(), env->d.pose[0], 7 * B * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(p1.data(), env->d.pose[1], 7 * B * 4, cudaMemcpyDeviceToHost));
+    }
+    const int64_t steps0 = env->steps;
+    int trials = 0;
+    auto measure = [&](float* ms) -> vuda_status {
+        vuda_status r = vuda_pipeline_run(env, 2, ring, nullptr, nullptr);
+        if (r != VUDA_OK) return r;
+        std::vector<float> sm(K), rm(K), stp(K);
+        vuda_timing tm{stp.data(), sm.data(), rm.data(), 0.0f};
+        auto t = std::chrono::steady_clock::now();
+        r = vuda_pipeline_run(env, K, ring, nullptr, &tm);
+        double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+        *ms = (tm.total_ms == tm.total_ms && tm.total_ms > 0) ? tm.total_ms / K : (float)(wall / K);
+        trials++;
+        return r;
+    };
+    auto apply_mode = [&](int mode, int sims) -> vuda_status {
+        if (mode == 0) return vuda_coschedule_reset(env);
+        vuda_cosched_opts co{mode, sims};
+        return vuda_coschedule(env, &co, nullptr, nullptr, nullptr);
+    };
+    if (!cached) {
+        float ms = 0.0f, best_ms = 1e30f;
+        // 1. band height, serialized
+        s = vuda_coschedule_reset(env);
+        const int cands[] = {16, 32, 64, 128};
+        int best_br = env->band_rows;
+        for (int br : cands) {
+            if (s != VUDA_OK) break;
+            if (br > std::max(16, env->max_h) || render_smem_for(br, env->max_w) > 227 * 1024) continue;
+            s = set_band_rows(env, br);
+            if (s == VUDA_OK) s = measure(&ms);
+            if (s == VUDA_OK && ms < best_ms) { best_ms = ms; best_br = br; }
+        }
+        if (s == VUDA_OK) s = set_band_rows(env, best_br);
+        best.band_rows = best_br;
+        best.ms_per_step_serialized = best_ms;
+        best.cosched_mode = 0;
+        best.sim_sms = 0;
+        // 2. co-scheduling: shared SMs, and disjoint partitions of a quarter to three quarters of the SMs
+        int dev_sms = 0;
+        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
+        std::vector<std::pair<int, int>> modes = {{VUDA_COSCHED_STREAMS, 0}};
+        for (int q = 1; q <= 3; q++) modes.push_back({VUDA_COSCHED_GREEN, (dev_sms * q / 4) / 8 * 8});
+        for (auto& m : modes) {
+            if (s != VUDA_OK) break;
+            vuda_status ms_st = apply_mode(m.first, m.second);
+            if (ms_st != VUDA_OK) continue;  // e.g. no green contexts here
+            s = measure(&ms);
+            if (s == VUDA_OK && ms < best_ms) {
+                best_ms = ms;
+                best.cosched_mode = m.first;
+                best.sim_sms = env->cos_info.sim_sms;
+            }
+        }
+        // 3. graph replay of the winner
+        best.graph_steps = 0;
+        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms);
+        if (s == VUDA_OK && (best.cosched_mode != 0)) {
+            if (vuda_pipeline_capture(env, 8, ring, nullptr) == VUDA_OK) {
+                vuda_status r = vuda_pipeline_run(env, 8, ring, nullptr, nullptr);
+                if (r == VUDA_OK) {
+                    auto t = std::chrono::steady_clock::now();
+                    r = vuda_pipeline_run(env, 16, ring, nullptr, nullptr);
+                    double w = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+                    trials++;
+                    if (r == VUDA_OK && w / 16 < best_ms) {
+                        best_ms = (float)(w / 16);
+                        best.graph_steps = 8;
+                    }
+                }
+                if (!best.graph_steps) drop_graph(env);
+            }
+            cudaGetLastError();
+        }
+        best.ms_per_step = best_ms;
+        if (s != VUDA_OK) return s;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    } else {
+        s = set_band_rows(env, best.band_rows);
+        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms);
+        if (s == VUDA_OK && best.graph_steps) {
+            if ((env->steps & 1) != 0) s = vuda_pipeline_run(env, 1, ring, nullptr, nullptr);
+            if (s == VUDA_OK && vuda_pipeline_capture(env, best.graph_steps, ring, nullptr) != VUDA_OK) best.graph_steps = 0;
+        }
+        if (s != VUDA_OK) return s;
+    }
+    // restore the batch as it was (the tuned configuration stays)
+    s = vuda_env_set_state(env, &st);
+    if (s != VUDA_OK) return s;
+    if (B) {
+        CK(cudaMemcpy(env->d.pose[0], p0.data(), 7 * B * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(env->d.pose[1], p1.data(), 7 * B * 4, cudaMemcpyHostToDevice));
+    }
+    env->steps = steps0;
+    if (env->gexec && (int)(steps0 & 1) != env->gparity) {
+        drop_graph(env);
+        if (best.graph_steps) {
+            // recapture at the restored parity
+            if (vuda_pipeline_capture(env, best.graph_steps, ring, nullptr) != VUDA_OK) best.graph_steps = 0;
+        }
+    }
+    best.trials = trials;
+    best.from_cache = cached ? 1 : 0;
+    *out = best;
     return VUDA_OK;
 }
 

@@ -25,6 +25,9 @@ struct vuda_env {
     std::vector<void*> allocs;
     std::vector<int64_t> cam_pix_off;
     std::vector<int32_t> h_item_cam, h_item_y0;   // host copies of the render work items
+    std::vector<int32_t> h_cam_w, h_cam_h, h_cam_env, h_body_off;
+    std::vector<int64_t> h_env_tri_base;
+    int max_h = 0;
     // co-scheduling
     int cos_mode = 0;
     cudaStream_t sim_s = nullptr, ren_s = nullptr, own_s = nullptr;

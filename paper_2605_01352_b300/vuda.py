@@ -69,6 +69,16 @@ class Timing(C.Structure):
     _fields_ = [("step_ms", vp), ("sim_ms", vp), ("render_ms", vp), ("total_ms", C.c_float)]
 
 
+class TuneOpts(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("use_cache", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("band_rows", C.c_int32), ("cosched_mode", C.c_int32), ("sim_sms", C.c_int32),
+                ("graph_steps", C.c_int32), ("ms_per_step", C.c_float), ("ms_per_step_serialized", C.c_float),
+                ("trials", C.c_int32), ("from_cache", C.c_int32)]
+
+
 class CoschedOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("sim_sms", C.c_int32)]
 
@@ -101,6 +111,7 @@ _sig("vuda_pipeline_run", [vp, C.c_int32, C.POINTER(Frame), vp, C.POINTER(Timing
 _sig("vuda_pipeline_run_host", [vp, C.c_int32, vp, C.c_int32, vp, vp, C.POINTER(Frame), vp, C.POINTER(Timing)])
 _sig("vuda_pipeline_capture", [vp, C.c_int32, C.POINTER(Frame), vp])
 _sig("vuda_pipeline_release_graph", [vp])
+_sig("vuda_autotune", [vp, C.POINTER(TuneOpts), C.POINTER(Frame), C.POINTER(TuneResult)])
 _sig("vuda_wait", [vp, C.c_int32])
 _sig("vuda_env_get_state", [vp, C.POINTER(State)])
 _sig("vuda_env_set_state", [vp, C.POINTER(State)])
@@ -345,6 +356,14 @@ class Env:
 
     def pipeline_release_graph(self):
         check(lib.vuda_pipeline_release_graph(self.h), "vuda_pipeline_release_graph")
+
+    def autotune(self, ring: Sequence[dict], steps: int = 6, use_cache: bool = True) -> dict:
+        """Measure candidate configurations and keep the fastest (see vuda.h)."""
+        frames = (Frame * 2)(self.frame_struct(ring[0]), self.frame_struct(ring[1 % len(ring)]))
+        r = TuneResult()
+        check(lib.vuda_autotune(self.h, C.byref(TuneOpts(steps, int(use_cache))), frames, C.byref(r)),
+              "vuda_autotune")
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def wait(self, phase: int):
         check(lib.vuda_wait(self.h, phase), "vuda_wait")

@@ -326,3 +326,61 @@ def test_graph_replay_equals_launches(V, mode):
     for a, b in zip(f0, f1):
         for k in a:
             np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_autotune_keeps_results_and_caches(V):
+    """The autotuner leaves the batch's state untouched and its choice gives
+    the same results as the default configuration; a second batch of the
+    same shape reuses the cached choice."""
+    import torch
+    sc = S.cfg2(64)
+    ref = V.Env(sc)
+    ring_r = [ref.alloc_frame(), ref.alloc_frame()]
+    ref.pipeline_run(4, ring_r)
+    torch.cuda.synchronize()
+    s_ref = ref.get_state()
+    f_ref = ring_r[1]["triid"].cpu().numpy().copy()
+    ref.close()
+    env = V.Env(sc)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    res = env.autotune(ring, steps=3, use_cache=True)
+    assert res["trials"] > 0 and res["band_rows"] in (16, 32, 64, 128)
+    assert res["cosched_mode"] in (0, V.COSCHED_STREAMS, V.COSCHED_GREEN)
+    assert env.info().steps_enqueued == 0
+    env.pipeline_run(4, ring)
+    torch.cuda.synchronize()
+    s = env.get_state()
+    for k in s:
+        np.testing.assert_array_equal(s[k], s_ref[k])
+    np.testing.assert_array_equal(ring[1]["triid"].cpu().numpy(), f_ref)
+    env.close()
+    env2 = V.Env(sc)
+    ring2 = [env2.alloc_frame(), env2.alloc_frame()]
+    res2 = env2.autotune(ring2, use_cache=True)
+    assert res2["from_cache"] == 1 and res2["trials"] == 0
+    assert (res2["band_rows"], res2["cosched_mode"]) == (res["band_rows"], res["cosched_mode"])
+    env2.close()
+
+
+def test_hull_meshes_two_cameras(V, orc):
+    """Convex-hull bodies (500-2000 triangles each, sphere proxies in the
+    physics) seen by two cameras per environment: physics and both cameras'
+    frames match the oracle."""
+    import torch
+    sc = S.generate(3, 64, S.config_seed(3), kinds="hulls", res=128, cams_per_env=2, substeps=8,
+                    n_hull_meshes=8)
+    env = V.Env(sc)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    env.pipeline_run(2, ring)
+    torch.cuda.synchronize()
+    g = env.get_state()
+    so, _, _ = orc.sim_step(sc, 2)
+    for k in ("pos", "vel", "quat", "angvel"):
+        np.testing.assert_allclose(g[k], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL)
+    o_rgb, o_dep, o_tid, _ = orc.render(sc, so["pos"], so["quat"])
+    f = ring[1]
+    np.testing.assert_array_equal(f["triid"].cpu().numpy().view(np.uint32), o_tid)
+    np.testing.assert_allclose(f["depth"].cpu().numpy(), o_dep, rtol=DEPTH_RTOL)
+    assert np.abs(f["rgb"].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1
+    assert env.C == 6 and env.T > 3 * 64 * 500
+    env.close()

@@ -247,3 +247,26 @@ def test_near_plane_discard(orc):
     rgb, dep, tid, flags = orc.render(sc)
     assert flags[0] & 2
     assert not ((tid >= 2) & (tid != 0xFFFFFFFF)).any()
+
+
+def test_scene_meshes_are_closed_and_outward():
+    """Input meshes (icosphere, cube, convex hulls): closed 2-manifolds with
+    Euler characteristic 2 whose triangles all face away from the centre."""
+    from paper_2605_01352_b300 import scene as S
+    meshes = [S.icosphere(1), S.cube()]
+    st = S.Streams(7, 1)
+    meshes += [S.convex_hull_mesh(st, t) for t in (500, 512)]
+    for V, T in meshes:
+        edges = {}
+        for a, b, c in T:
+            for u, v in ((a, b), (b, c), (c, a)):
+                edges[(u, v)] = edges.get((u, v), 0) + 1
+        # every directed edge once and its reverse once: closed and consistently oriented
+        assert all(n == 1 for n in edges.values())
+        assert all((v, u) in edges for (u, v) in edges)
+        nE = len(edges) // 2
+        assert len(V) - nE + len(T) == 2
+        Vd = V.astype(np.float64)
+        n = np.cross(Vd[T[:, 1]] - Vd[T[:, 0]], Vd[T[:, 2]] - Vd[T[:, 0]])
+        assert (np.einsum("ij,ij->i", n, Vd[T].mean(1)) > 0).all()
+    assert S.icosphere(1)[1].shape == (80, 3) and S.icosphere(1)[0].shape == (42, 3)
