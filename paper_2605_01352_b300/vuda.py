@@ -14,7 +14,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libvuda.so")
+# VUDA_LIBRARY selects another build of the same library (e.g. an instrumented one)
+LIB_PATH = os.environ.get("VUDA_LIBRARY") or os.path.join(_HERE, "libvuda.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libvuda.so is not built (python -m paper_2605_01352_b300.build); "
