@@ -571,7 +571,19 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                     int o = S.loff[i];
                     for (int q = 0; q < warp; q++) o += qcnt[q * NB + i];
                     int cend = min(nc, (warp + 1) * qlen);
-                    for (int c = warp * qlen; c < cend; c++) {
+                    int c = warp * qlen;
+                    for (; c + 4 <= cend; c += 4) {
+                        int ab[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) ab[u] = __float_as_int(C.rec(c + u)[F_AB]);
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            int a = ab[u] & 0xffff, bb = (ab[u] >> 16) - 1;
+                            if (a == i) lists[o++] = (unsigned short)((c + u) << 1);
+                            else if (bb == i) lists[o++] = (unsigned short)(((c + u) << 1) | 1);
+                        }
+                    }
+                    for (; c < cend; c++) {
                         int a, bb;
                         unpack_ab(C.rec(c), a, bb);
                         if (a == i) lists[o++] = (unsigned short)(c << 1);
@@ -663,20 +675,45 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                 // are independent sums, two per thread, in warps 0..2
                 if (warp < 3) {
                     const int q0 = 2 * warp;
+                    // component q of an entry: 0..2 impulse, 3..5 its moment about
+                    // the body; the B side enters with the opposite sign
+                    auto load = [&](int ent, float& a, float& bv) {
+                        Rec r = C.rec(ent >> 1);
+                        const bool side = ent & 1;
+                        const int fl = side ? F_LB : F_LA;
+                        const int f0 = q0 < 3 ? F_P + q0 : fl + q0 - 3;
+                        const int f1 = q0 + 1 < 3 ? F_P + q0 + 1 : fl + q0 - 2;
+                        a = r[f0];
+                        bv = r[f1];
+                        if (side) {
+                            a = -a;
+                            bv = -bv;
+                        }
+                    };
                     for (int i0 = 0; i0 < N; i0 += 32) {
                         int i = i0 + lane;
                         if (i < N) {
                             float s0 = 0.0f, s1 = 0.0f;
-                            for (int k = S.loff[i]; k < S.loff[i + 1]; k++) {
-                                int ent = lists[k];
-                                Rec r = C.rec(ent >> 1);
-                                bool side = ent & 1;
-                                // component q: 0..2 impulse, 3..5 its moment about the body
-                                int f0 = q0 < 3 ? F_P + q0 : (side ? F_LB : F_LA) + q0 - 3;
-                                int f1 = q0 + 1 < 3 ? F_P + q0 + 1 : (side ? F_LB : F_LA) + q0 - 2;
-                                float v0 = r[f0], v1 = r[f1];
-                                if (!side) { s0 = s0 + v0; s1 = s1 + v1; }
-                                else { s0 = s0 - v0; s1 = s1 - v1; }
+                            const int k1 = S.loff[i + 1];
+                            int k = S.loff[i];
+                            // loads of four entries are independent: issue them
+                            // together, then add in list order
+                            for (; k + 4 <= k1; k += 4) {
+                                float a0, b0, a1, b1, a2, b2, a3, b3;
+                                load(lists[k], a0, b0);
+                                load(lists[k + 1], a1, b1);
+                                load(lists[k + 2], a2, b2);
+                                load(lists[k + 3], a3, b3);
+                                s0 = s0 + a0; s1 = s1 + b0;
+                                s0 = s0 + a1; s1 = s1 + b1;
+                                s0 = s0 + a2; s1 = s1 + b2;
+                                s0 = s0 + a3; s1 = s1 + b3;
+                            }
+                            for (; k < k1; k++) {
+                                float a0, b0;
+                                load(lists[k], a0, b0);
+                                s0 = s0 + a0;
+                                s1 = s1 + b0;
                             }
                             S.ACC(q0, i) = s0;
                             S.ACC(q0 + 1, i) = s1;

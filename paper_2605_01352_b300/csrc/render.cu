@@ -120,6 +120,18 @@ __device__ __forceinline__ unsigned long long frag_key(long long E0, long long E
     return ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
 }
 
+// A binned triangle with its edge functions set up once, by the thread that
+// submitted it, for all the lanes of the tile pass.
+struct BigRec {
+    int A[3], B[3];       // |A|, |B| < 2^23 inside the guard band
+    long long C[3];
+    float iz[3];
+    float af;             // (float) area2
+    uint32_t id;
+    short x0, x1, y0, y1;
+    unsigned tl;          // bit i: edge i owns its pixels
+};
+
 // One thread rasterises a small triangle into the shared-memory z-buffer.
 __device__ __forceinline__ void raster_thread(const Tri& t, const Band& bd) {
     Edges e;
@@ -144,7 +156,7 @@ __device__ __forceinline__ void raster_thread(const Tri& t, const Band& bd) {
 }
 
 struct Bins {
-    Tri* rec;            // [kBigCap]
+    BigRec* rec;         // [kBigCap]
     int* nrec;
     unsigned* mask;      // [ntiles][kMaskWords]: bit r set if record r overlaps the tile
     int tiles_x, ntiles;
@@ -188,25 +200,28 @@ __device__ void tile_pass(const Band& bd, const Bins& bn) {
             while (bits) {
                 int r = (w << 5) + __ffs(bits) - 1;
                 bits &= bits - 1;
-                const Tri& t = bn.rec[r];
+                const BigRec& t = bn.rec[r];
                 if (nx <= 0 || y < t.y0 || y > t.y1 || xs + nx - 1 < t.x0 || xs > t.x1) continue;
-                Edges e;
-                edges(t, e);
-                long long cy = 256LL * y + 128;
-                long long cx = 256LL * xs + 128;
-                long long E0 = e.A[0] * cx + e.B[0] * cy + e.C[0];
-                long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
-                long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
+                const long long cy = 256LL * y + 128;
+                const long long cx = 256LL * xs + 128;
+                long long E0 = (long long)t.A[0] * cx + (long long)t.B[0] * cy + t.C[0];
+                long long E1 = (long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1];
+                long long E2 = (long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2];
+                const long long d0 = 256LL * t.A[0], d1 = 256LL * t.A[1], d2 = 256LL * t.A[2];
+                const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    if (k < nx && inside(E0, E1, E2, e)) {
-                        unsigned long long kk = frag_key(E0, E1, E2, t, e);
+                    if (k < nx && (E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) &&
+                        (E2 > 0 || (E2 == 0 && tl2))) {
+                        float den = (i64_to_f32(E0) * t.iz[0] + i64_to_f32(E1) * t.iz[1]) + i64_to_f32(E2) * t.iz[2];
+                        float depth = t.af / den;
+                        unsigned long long kk = ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
                         key[k] = kk < key[k] ? kk : key[k];
                         cnt8[k]++;
                     }
-                    E0 += e.A[0] * 256;
-                    E1 += e.A[1] * 256;
-                    E2 += e.A[2] * 256;
+                    E0 += d0;
+                    E1 += d1;
+                    E2 += d2;
                 }
             }
         }
@@ -235,7 +250,20 @@ __device__ __forceinline__ void submit_tri(const Tri& t, const Band& bd, Bins& b
     if (npx > kSmallPx) {
         int r = atomicAdd(bn.nrec, 1);
         if (r < kBigCap) {
-            bn.rec[r] = t;
+            Edges e;
+            edges(t, e);
+            BigRec& g = bn.rec[r];
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                g.A[i] = (int)e.A[i];
+                g.B[i] = (int)e.B[i];
+                g.C[i] = e.C[i];
+                g.iz[i] = t.iz[i];
+            }
+            g.af = e.af;
+            g.id = t.id;
+            g.x0 = t.x0; g.x1 = t.x1; g.y0 = t.y0; g.y1 = t.y1;
+            g.tl = (e.tl[0] ? 1u : 0u) | (e.tl[1] ? 2u : 0u) | (e.tl[2] ? 4u : 0u);
             bin_tri(t, r, bd, bn);
             return;
         }
@@ -282,7 +310,7 @@ __host__ __device__ inline int tiles_for(int rows, int W) {
 
 __host__ __device__ inline size_t render_smem_bytes(int band_rows, int W) {
     size_t s = (size_t)band_rows * W * 8;                        // z keys
-    s += sizeof(Tri) * kBigCap;                                  // binned triangles
+    s += sizeof(BigRec) * kBigCap;                               // binned triangles
     s += (size_t)kVcap * (4 + 4 + 4 + 4);                        // vertex cache
     int nt = tiles_for(band_rows, W);
     s += (size_t)nt * kMaskWords * 4 + 16;                       // tile masks, counters
@@ -309,7 +337,7 @@ __device__ __forceinline__ void render_band(const DevBatch& b, int cam, int y0, 
     unsigned char* p = smem;
     bd.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)a.band_rows * a.max_w * 8;
     Bins bn;
-    bn.rec = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kBigCap;
+    bn.rec = reinterpret_cast<BigRec*>(p); p += sizeof(BigRec) * kBigCap;
     int* vX = reinterpret_cast<int*>(p); p += 4 * kVcap;
     int* vY = reinterpret_cast<int*>(p); p += 4 * kVcap;
     float* viz = reinterpret_cast<float*>(p); p += 4 * kVcap;
@@ -509,7 +537,7 @@ __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __res
     bd.z = reinterpret_cast<unsigned long long*>(p); p += (size_t)band_rows * W * 8;
     unsigned* scount = reinterpret_cast<unsigned*>(p); p += (size_t)band_rows * W * 4;
     Bins bn;
-    bn.rec = reinterpret_cast<Tri*>(p); p += sizeof(Tri) * kBigCap;
+    bn.rec = reinterpret_cast<BigRec*>(p); p += sizeof(BigRec) * kBigCap;
     bn.tiles_x = (W + kTile - 1) / kTile;
     bn.ntiles = tiles_for(bd.y1 - bd.y0, W);
     bn.mask = reinterpret_cast<unsigned*>(p); p += 4 * (size_t)tiles_for(band_rows, W) * kMaskWords;
@@ -631,7 +659,7 @@ __global__ void __launch_bounds__(256) shade_list_kernel(const DevBatch* __restr
 
 size_t screen_smem_bytes(int band_rows, int W) {
     int nt = tiles_for(band_rows, W);
-    size_t s = (size_t)band_rows * W * 12 + sizeof(Tri) * kBigCap + (size_t)nt * kMaskWords * 4 + 16;
+    size_t s = (size_t)band_rows * W * 12 + sizeof(BigRec) * kBigCap + (size_t)nt * kMaskWords * 4 + 16;
     return (s + 15) & ~(size_t)15;
 }
 
