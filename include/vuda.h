@@ -194,19 +194,29 @@ vuda_status vuda_render(vuda_env_t env, int32_t pose_slot, const vuda_frame* fra
 /* Co-scheduling (the paper's CUstream_bind, Table 1 / Sec. 3.2):
  * mode VUDA_COSCHED_GREEN puts a sim stream and a render stream on disjoint
  * SM partitions (green contexts, sim_sms SMs for sim, the rest for render);
- * VUDA_COSCHED_STREAMS uses two ordinary streams that share all SMs.
+ * VUDA_COSCHED_STREAMS uses two ordinary streams that share all SMs;
+ * VUDA_COSCHED_SHARED partitions every SM instead of the set of SMs: both
+ * phases run as persistent work-list launches, and a CTA is admitted only
+ * while its SM holds fewer than sim_ctas_per_sm (render_ctas_per_sm) CTAs of
+ * its phase, so that sim(t+1) and render(t) are resident side by side on
+ * every SM (0: a default pair that fits; VUDA_ERR_INVALID if a pair does not
+ * fit one SM together).
  * The streams are owned by the library and returned for the caller to
  * enqueue on.  vuda_coschedule_reset (CUstream_unbind) destroys them. */
 #define VUDA_COSCHED_STREAMS 1
 #define VUDA_COSCHED_GREEN 2
+#define VUDA_COSCHED_SHARED 3
 typedef struct {
     int32_t mode;
-    int32_t sim_sms;              /* SMs for the sim partition (0: half); rounded to the device granularity */
+    int32_t sim_sms;              /* GREEN: SMs for the sim partition (0: half); rounded to the device granularity */
+    int32_t sim_ctas_per_sm;      /* SHARED: sim CTAs per SM (0: default) */
+    int32_t render_ctas_per_sm;   /* SHARED: render CTAs per SM (0: default) */
 } vuda_cosched_opts;
 typedef struct {
     int32_t mode;
     int32_t sim_sms, render_sms;  /* SMs actually provisioned (0 if not partitioned) */
     int32_t sm_granularity;       /* partition alignment reported by the driver */
+    int32_t sim_ctas_per_sm, render_ctas_per_sm;  /* SHARED: the per-SM quotas in use */
 } vuda_cosched_info;
 vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_stream_t* sim_stream,
                             vuda_stream_t* render_stream, vuda_cosched_info* info);
@@ -249,8 +259,10 @@ vuda_status vuda_pipeline_release_graph(vuda_env_t env);
 
 /* Autotuner: measures the loop under candidate configurations -- render band
  * height (16/32/64/128 rows), serialized / co-scheduled on shared SMs /
- * co-scheduled on disjoint partitions of 1/4, 1/2 and 3/4 of the SMs, and CUDA
- * graph replay -- and leaves the batch configured with the fastest.  Results
+ * co-scheduled on disjoint partitions of 1/4, 1/2 and 3/4 of the SMs /
+ * co-scheduled with per-SM quotas (every pair that fits one SM, the most sim
+ * CTAs for each render count), and CUDA graph replay -- and leaves the batch
+ * configured with the fastest.  Results
  * are cached per batch shape for the process (use_cache = 1 reuses them
  * without measuring).  The trials step the batch; its state and pose slots
  * are restored afterwards.  ring: the two frames the loop will use. */
@@ -262,6 +274,7 @@ typedef struct {
     int32_t band_rows, cosched_mode, sim_sms, graph_steps;
     float ms_per_step, ms_per_step_serialized;
     int32_t trials, from_cache;
+    int32_t sim_ctas_per_sm, render_ctas_per_sm;  /* SHARED winner's quotas */
 } vuda_tune_result;
 vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda_frame* ring, vuda_tune_result* out);
 
@@ -300,7 +313,9 @@ vuda_status vuda_env_contact_counts(vuda_env_t env, int32_t* counts);
  * W x H image (all device pointers): triid[H][W] u32 (0xFFFFFFFF empty),
  * depth[H][W] f32 (0 empty), count[H][W] u32 (may be NULL: number of
  * triangles covering each pixel).  Same coverage rule and depth key as
- * vuda_render; triangle ids are the input order.  Async on `stream`. */
+ * vuda_render; triangle ids are the input order.  As in vuda_render, a
+ * triangle with a vertex beyond the 2^14-pixel guard band (|x| or |y| above
+ * 2^22) is discarded.  Async on `stream`. */
 vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t ntri, int32_t W, int32_t H,
                                     uint32_t* triid, float* depth, uint32_t* count, vuda_stream_t stream);
 

@@ -62,6 +62,7 @@ typedef struct {
 #define FLAG_GUARD 4u
 #define SUBPIX 256.0f      /* 8 sub-pixel bits: fixed point 24.8 */
 #define GUARD 16384.0f     /* |sx|, |sy| limit in pixels */
+#define SCREEN_LIMIT 4194304 /* GUARD * SUBPIX: largest |X|, |Y| a snapped vertex can have */
 #define NEAR_Z 0.01f
 
 typedef struct {
@@ -136,7 +137,9 @@ static void raster_tri(const int* X, const int* Y, const float* izv, uint32_t id
 /* Rasterise ntri screen-space triangles given as snapped 24.8 fixed-point
  * vertices xy[t][v][2] and view depths z[t][v] into W x H buffers of the
  * nearest triangle id (0xFFFFFFFF where empty) and its depth (0 where empty).
- * count (optional) gets the number of triangles covering each pixel. */
+ * count (optional) gets the number of triangles covering each pixel.  As in
+ * the renderer, a triangle with a vertex beyond the 2^14-pixel guard band
+ * (|x| or |y| above 2^22 in 1/256 px) is discarded. */
 int oracle_raster_screen_tris(const int32_t* xy, const float* z, int ntri, int W, int H,
                               uint32_t* triid, float* depth, int* count) {
     if (W <= 0 || H <= 0 || ntri < 0) return 1;
@@ -151,6 +154,10 @@ int oracle_raster_screen_tris(const int32_t* xy, const float* z, int ntri, int W
             Y[v] = xy[6 * t + 2 * v + 1];
             iz[v] = 1.0f / z[3 * t + v];
         }
+        int out = 0;
+        for (int v = 0; v < 3; v++)
+            if (X[v] > SCREEN_LIMIT || X[v] < -SCREEN_LIMIT || Y[v] > SCREEN_LIMIT || Y[v] < -SCREEN_LIMIT) out = 1;
+        if (out) continue;
         raster_tri(X, Y, iz, (uint32_t)t, W, H, zb, count);
     }
     for (size_t i = 0; i < (size_t)W * H; i++) {

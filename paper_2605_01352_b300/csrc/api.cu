@@ -173,7 +173,7 @@ vuda_status destroy_cosched(vuda_env* env) {
         if (env->ren_s) dr.StreamDestroy((CUstream)env->ren_s);
         if (env->g_sim) dr.GreenCtxDestroy(env->g_sim);
         if (env->g_ren) dr.GreenCtxDestroy(env->g_ren);
-    } else if (env->cos_mode == VUDA_COSCHED_STREAMS) {
+    } else if (env->cos_mode == VUDA_COSCHED_STREAMS || env->cos_mode == VUDA_COSCHED_SHARED) {
         if (env->sim_s) cudaStreamDestroy(env->sim_s);
         if (env->ren_s) cudaStreamDestroy(env->ren_s);
     }
@@ -182,6 +182,7 @@ vuda_status destroy_cosched(vuda_env* env) {
     env->c_sim = env->c_ren = nullptr;
     env->cos_mode = 0;
     env->cos_info = vuda_cosched_info{};
+    env->sim_quota = env->ren_quota = 0;
     return VUDA_OK;
 }
 
@@ -219,6 +220,87 @@ vuda_status env_estimate_bytes(const vuda_scene* sc, const vuda_sim_params* p, i
 
 namespace {
 
+// Whether ns sim CTAs and nr render CTAs fit one SM together: threads,
+// CTA slots, registers (allocated per warp in units of 8 per thread) and
+// shared memory (each CTA also holds the reserved per-block amount).
+bool pair_fits(int device, const CtaFootprint& a, int na, const CtaFootprint& b, int nr) {
+    cudaDeviceProp p{};
+    if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return false;
+    auto regs = [](const CtaFootprint& f) { return ((f.regs + 7) / 8 * 8) * 32 * ((f.threads + 31) / 32); };
+    const long threads = (long)na * a.threads + (long)nr * b.threads;
+    const long rg = (long)na * regs(a) + (long)nr * regs(b);
+    const long sm = (long)na * (a.smem + (long)p.reservedSharedMemPerBlock) +
+                    (long)nr * (b.smem + (long)p.reservedSharedMemPerBlock);
+    return threads <= p.maxThreadsPerMultiProcessor && na + nr <= p.maxBlocksPerMultiProcessor &&
+           rg <= p.regsPerMultiprocessor && sm <= (long)p.sharedMemPerMultiprocessor;
+}
+
+// Most sim CTAs per SM that fit beside nr render CTAs (0 if none).
+int max_sim_beside(vuda_env* env, int nr) {
+    const CtaFootprint a = sim_list_footprint(env->phys_smem);
+    const CtaFootprint b = render_list_footprint(env->band_rows, env->max_w);
+    int ns = 0;
+    while (ns < 32 && pair_fits(env->device, a, ns + 1, b, nr)) ns++;
+    return ns;
+}
+
+// Persistent render work list for pose slots 0 and 1, largest items first
+// (pixels of the band plus four per triangle of its environment).
+vuda_status build_render_list(vuda_env* env, int br, const std::vector<int32_t>& ic, const std::vector<int32_t>& iy) {
+    std::vector<int> io(ic.size());
+    for (size_t i = 0; i < io.size(); i++) io[i] = (int)i;
+    auto cost = [&](int i) {
+        int c = ic[i], e = env->h_cam_env[c];
+        int rows = std::min(br, env->h_cam_h[c] - iy[i]);
+        return (double)rows * env->h_cam_w[c] + 4.0 * (double)(env->h_env_tri_base[e + 1] - env->h_env_tri_base[e]);
+    };
+    std::stable_sort(io.begin(), io.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    vuda_status s = VUDA_OK;
+    for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
+        std::vector<int4> ri(io.size());
+        for (size_t k = 0; k < io.size(); k++) ri[k] = make_int4(slot << 24, ic[io[k]], iy[io[k]], 0);
+        s = upload(env, &env->ren_items[slot], ri.data(), ri.size());
+    }
+    if (s != VUDA_OK) return s;
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
+    env->ren_grid = std::max(1, std::min((int)ic.size(), dev_sms * render_ctas_per_sm(br, env->max_w)));
+    return VUDA_OK;
+}
+
+// Work lists for the persistent launches: environments by body count and the
+// shading units for both pose slots, the render list, the batch descriptor,
+// the work counters and the per-SM slot counters.  Built once.
+vuda_status build_lists(vuda_env* env) {
+    if (env->lists) return VUDA_OK;
+    const int E = env->E, B = env->B;
+    const std::vector<int32_t>& bo = env->h_body_off;
+    std::vector<int> eo(E);
+    for (int e = 0; e < E; e++) eo[e] = e;
+    std::stable_sort(eo.begin(), eo.end(), [&](int a, int b) { return bo[a + 1] - bo[a] > bo[b + 1] - bo[b]; });
+    vuda_status s = VUDA_OK;
+    for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
+        std::vector<int2> si(E);
+        for (int k = 0; k < E; k++) si[k] = make_int2(slot << 24, eo[k]);
+        std::vector<int2> sh(B + E);
+        for (int u = 0; u < B + E; u++) sh[u] = make_int2(slot << 24, u);
+        s = upload(env, &env->sim_items[slot], si.data(), si.size());
+        if (s == VUDA_OK) s = upload(env, &env->shade_items[slot], sh.data(), sh.size());
+    }
+    env->nshade = B + E;
+    if (s == VUDA_OK) s = build_render_list(env, env->band_rows, env->h_item_cam, env->h_item_y0);
+    if (s == VUDA_OK) s = dalloc(env, &env->counters, 2);
+    if (s == VUDA_OK) s = dalloc(env, &env->sm_slots, 2 * (size_t)kMaxSmSlots);
+    if (s == VUDA_OK) CK(cudaMemset(env->sm_slots, 0, 2 * sizeof(int) * kMaxSmSlots));
+    if (s == VUDA_OK) s = upload(env, &env->d_desc, &env->d, 1);
+    if (s != VUDA_OK) return s;
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
+    env->sim_grid = std::max(1, std::min(E, dev_sms * sim_ctas_per_sm(env->phys_smem)));
+    env->lists = 1;
+    return VUDA_OK;
+}
+
 // Rebuild the render work items (and their persistent lists) for a new band
 // height.  The previous device arrays stay owned by the batch until destroy.
 vuda_status set_band_rows(vuda_env* env, int br) {
@@ -232,24 +314,7 @@ vuda_status set_band_rows(vuda_env* env, int br) {
     vuda_status s = upload(env, &env->item_cam, ic.data(), ic.size());
     if (s == VUDA_OK) s = upload(env, &env->item_y0, iy.data(), iy.size());
     if (s != VUDA_OK) return s;
-    if (env->persistent) {
-        std::vector<int> io(ic.size());
-        for (size_t i = 0; i < io.size(); i++) io[i] = (int)i;
-        auto cost = [&](int i) {
-            int c = ic[i], e = env->h_cam_env[c];
-            int rows = std::min(br, env->h_cam_h[c] - iy[i]);
-            return (double)rows * env->h_cam_w[c] + 4.0 * (double)(env->h_env_tri_base[e + 1] - env->h_env_tri_base[e]);
-        };
-        std::stable_sort(io.begin(), io.end(), [&](int a, int b) { return cost(a) > cost(b); });
-        for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
-            std::vector<int4> ri(io.size());
-            for (size_t k = 0; k < io.size(); k++) ri[k] = make_int4(slot << 24, ic[io[k]], iy[io[k]], 0);
-            s = upload(env, &env->ren_items[slot], ri.data(), ri.size());
-        }
-        int dev_sms = 0;
-        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
-        env->ren_grid = std::max(1, std::min((int)ic.size(), dev_sms * render_ctas_per_sm(br, env->max_w)));
-    }
+    if (env->lists) s = build_render_list(env, br, ic, iy);
     if (s != VUDA_OK) return s;
     env->band_rows = br;
     env->nitems = (int)ic.size();
@@ -278,7 +343,7 @@ std::map<TuneKey, vuda_tune_result> g_tune_cache;
 
 extern "C" {
 
-int32_t vuda_abi_version(void) { return 1; }
+int32_t vuda_abi_version(void) { return 2; }
 
 vuda_status vuda_env_estimate_bytes(const vuda_scene* scene, const vuda_sim_params* params, int64_t* bytes) {
     return env_estimate_bytes(scene, params, bytes);
@@ -589,40 +654,8 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     d.sc = k;
     d.max_bodies = max_bodies;
     if (o.persistent) {
-        // work items, largest first: environments by body count, camera bands by pixels x triangles
         env->persistent = 1;
-        std::vector<int> eo(E);
-        for (int e = 0; e < E; e++) eo[e] = e;
-        std::stable_sort(eo.begin(), eo.end(), [&](int a, int b2) {
-            return sc->body_off[a + 1] - sc->body_off[a] > sc->body_off[b2 + 1] - sc->body_off[b2];
-        });
-        std::vector<int> io(item_cam.size());
-        for (size_t i = 0; i < io.size(); i++) io[i] = (int)i;
-        auto cost = [&](int i) {
-            int c = item_cam[i], e = cam_env[c];
-            int rows = std::min(br, sc->cam_h[c] - item_y0[i]);
-            return (double)rows * sc->cam_w[c] + 4.0 * (double)(env_tri_base[e + 1] - env_tri_base[e]);
-        };
-        std::stable_sort(io.begin(), io.end(), [&](int a, int b2) { return cost(a) > cost(b2); });
-        for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
-            std::vector<int2> si(E);
-            for (int k2 = 0; k2 < E; k2++) si[k2] = make_int2(slot << 24, eo[k2]);
-            std::vector<int4> ri(io.size());
-            for (size_t k2 = 0; k2 < io.size(); k2++)
-                ri[k2] = make_int4(slot << 24, item_cam[io[k2]], item_y0[io[k2]], 0);
-            std::vector<int2> sh(B + E);
-            for (int u = 0; u < B + E; u++) sh[u] = make_int2(slot << 24, u);
-            s = upload(env, &env->sim_items[slot], si.data(), si.size());
-            if (s == VUDA_OK) s = upload(env, &env->ren_items[slot], ri.data(), ri.size());
-            if (s == VUDA_OK) s = upload(env, &env->shade_items[slot], sh.data(), sh.size());
-        }
-        env->nshade = B + E;
-        if (s == VUDA_OK) s = dalloc(env, &env->counters, 2);
-        if (s == VUDA_OK) s = upload(env, &env->d_desc, &d, 1);
-        int dev_sms = 0;
-        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, o.device);
-        env->sim_grid = std::max(1, std::min(E, dev_sms * sim_ctas_per_sm(env->phys_smem)));
-        env->ren_grid = std::max(1, std::min((int)item_cam.size(), dev_sms * render_ctas_per_sm(br, max_w)));
+        s = build_lists(env);
         if (s != VUDA_OK) {
             free_env(env);
             delete env;
@@ -677,11 +710,14 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
     if (nsteps < 0) return invalid("nsteps < 0");
     if (nsteps == 0) return VUDA_OK;
     cudaError_t e = cudaSuccess;
-    if (env->persistent && !force) {
+    const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
+    if (env->persistent || shared) {
+        const SmGate gate = shared ? SmGate{env->sm_slots, env->sim_quota} : SmGate{nullptr, 0};
+        const int grid = shared ? env->sim_grid_sh : env->sim_grid;
         for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
             int slot = (int)((env->steps + t) & 1);
-            e = launch_sim_items(env->d_desc, env->sim_items[slot], env->E, env->counters, env->sim_grid,
-                                 env->phys_smem, env->max_bodies, (cudaStream_t)stream);
+            e = launch_sim_items(env->d_desc, env->sim_items[slot], env->E, env->counters, grid, env->phys_smem,
+                                 env->max_bodies, force, gate, (cudaStream_t)stream);
         }
     } else {
         e = launch_sim(env->d, env->sc, nsteps, force, (int)(env->steps & 1), env->phys_smem, env->max_bodies,
@@ -697,9 +733,13 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
 
 static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, cudaStream_t stream) {
     cudaError_t e;
-    if (env->persistent)
-        e = launch_render_list(env->d_desc, env->ren_items[slot], env->nitems, env->counters + 1, env->ren_grid,
-                               env->shade_items[slot], env->nshade, env->band_rows, env->max_w, fr, stream);
+    const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
+    if (env->persistent || shared)
+        e = launch_render_list(env->d_desc, env->ren_items[slot], env->nitems, env->counters + 1,
+                               shared ? env->ren_grid_sh : env->ren_grid, env->shade_items[slot], env->nshade,
+                               env->band_rows, env->max_w, fr,
+                               shared ? SmGate{env->sm_slots + kMaxSmSlots, env->ren_quota} : SmGate{nullptr, 0},
+                               stream);
     else
         e = launch_render_items(env->d, env->d.pose[slot], *fr, env->item_cam, env->item_y0, env->nitems,
                                 env->band_rows, env->max_w, stream);
@@ -776,6 +816,37 @@ vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_
         env->cos_info.sim_sms = (int)part.sm.smCount;
         env->cos_info.render_sms = (int)rest.sm.smCount;
         env->cos_info.sm_granularity = (int)all.sm.smCoscheduledAlignment;
+    } else if (opts->mode == VUDA_COSCHED_SHARED) {
+        vuda_status st = build_lists(env);
+        if (st != VUDA_OK) return st;
+        int nr = opts->render_ctas_per_sm, ns = opts->sim_ctas_per_sm;
+        if (nr < 0 || ns < 0) return invalid("CTAs per SM must be >= 0");
+        if (nr == 0) {
+            // default: half of what the render kernel gets alone (rounded up),
+            // then as many sim CTAs as fit beside it
+            nr = (render_ctas_per_sm(env->band_rows, env->max_w) + 1) / 2;
+            while (nr > 1 && max_sim_beside(env, nr) == 0) nr--;
+        }
+        if (ns == 0) ns = max_sim_beside(env, nr);
+        if (ns <= 0 || nr <= 0 ||
+            !pair_fits(env->device, sim_list_footprint(env->phys_smem), ns,
+                       render_list_footprint(env->band_rows, env->max_w), nr))
+            return invalid("sim and render CTAs per SM do not fit one SM together");
+        int dev_sms = 0;
+        CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device));
+        CK(cudaStreamCreateWithFlags(&env->sim_s, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&env->ren_s, cudaStreamNonBlocking));
+        env->cos_mode = VUDA_COSCHED_SHARED;
+        env->sim_quota = ns;
+        env->ren_quota = nr;
+        // one CTA per SM beyond the quota, so that an SM the block scheduler
+        // under-fills first still reaches its quota; the extra CTAs exit at the gate
+        env->sim_grid_sh = std::max(1, std::min(dev_sms * (ns + 1), dev_sms * sim_ctas_per_sm(env->phys_smem)));
+        env->ren_grid_sh =
+            std::max(1, std::min(dev_sms * (nr + 1), dev_sms * render_ctas_per_sm(env->band_rows, env->max_w)));
+        env->cos_info.mode = VUDA_COSCHED_SHARED;
+        env->cos_info.sim_ctas_per_sm = ns;
+        env->cos_info.render_ctas_per_sm = nr;
     } else {
         return invalid("unknown co-scheduling mode");
     }
@@ -1150,9 +1221,9 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
         trials++;
         return r;
     };
-    auto apply_mode = [&](int mode, int sims) -> vuda_status {
+    auto apply_mode = [&](int mode, int sims, int ns, int nr) -> vuda_status {
         if (mode == 0) return vuda_coschedule_reset(env);
-        vuda_cosched_opts co{mode, sims};
+        vuda_cosched_opts co{mode, sims, ns, nr};
         return vuda_coschedule(env, &co, nullptr, nullptr, nullptr);
     };
     if (!cached) {
@@ -1173,25 +1244,39 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
         best.ms_per_step_serialized = best_ms;
         best.cosched_mode = 0;
         best.sim_sms = 0;
-        // 2. co-scheduling: shared SMs, and disjoint partitions of a quarter to three quarters of the SMs
+        best.sim_ctas_per_sm = best.render_ctas_per_sm = 0;
+        // 2. co-scheduling: shared SMs, disjoint partitions of a quarter to
+        // three quarters of the SMs, and per-SM quotas (for each render count,
+        // the most sim CTAs that fit beside it and one fewer)
         int dev_sms = 0;
         cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
-        std::vector<std::pair<int, int>> modes = {{VUDA_COSCHED_STREAMS, 0}};
-        for (int q = 1; q <= 3; q++) modes.push_back({VUDA_COSCHED_GREEN, (dev_sms * q / 4) / 8 * 8});
+        struct Cand { int mode, sims, ns, nr; };
+        std::vector<Cand> modes = {{VUDA_COSCHED_STREAMS, 0, 0, 0}};
+        for (int q = 1; q <= 3; q++) modes.push_back({VUDA_COSCHED_GREEN, (dev_sms * q / 4) / 8 * 8, 0, 0});
+        if (build_lists(env) == VUDA_OK) {
+            const int rmax = render_ctas_per_sm(env->band_rows, env->max_w);
+            for (int nr = 1; nr <= rmax; nr++) {
+                const int ns = max_sim_beside(env, nr);
+                if (ns >= 1) modes.push_back({VUDA_COSCHED_SHARED, 0, ns, nr});
+                if (ns >= 2) modes.push_back({VUDA_COSCHED_SHARED, 0, ns - 1, nr});
+            }
+        }
         for (auto& m : modes) {
             if (s != VUDA_OK) break;
-            vuda_status ms_st = apply_mode(m.first, m.second);
+            vuda_status ms_st = apply_mode(m.mode, m.sims, m.ns, m.nr);
             if (ms_st != VUDA_OK) continue;  // e.g. no green contexts here
             s = measure(&ms);
             if (s == VUDA_OK && ms < best_ms) {
                 best_ms = ms;
-                best.cosched_mode = m.first;
+                best.cosched_mode = m.mode;
                 best.sim_sms = env->cos_info.sim_sms;
+                best.sim_ctas_per_sm = env->cos_info.sim_ctas_per_sm;
+                best.render_ctas_per_sm = env->cos_info.render_ctas_per_sm;
             }
         }
         // 3. graph replay of the winner
         best.graph_steps = 0;
-        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms);
+        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms, best.sim_ctas_per_sm, best.render_ctas_per_sm);
         if (s == VUDA_OK && (best.cosched_mode != 0)) {
             if (vuda_pipeline_capture(env, 8, ring, nullptr) == VUDA_OK) {
                 vuda_status r = vuda_pipeline_run(env, 8, ring, nullptr, nullptr);
@@ -1215,7 +1300,7 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
         g_tune_cache[key] = best;
     } else {
         s = set_band_rows(env, best.band_rows);
-        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms);
+        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms, best.sim_ctas_per_sm, best.render_ctas_per_sm);
         if (s == VUDA_OK && best.graph_steps) {
             if ((env->steps & 1) != 0) s = vuda_pipeline_run(env, 1, ring, nullptr, nullptr);
             if (s == VUDA_OK && vuda_pipeline_capture(env, best.graph_steps, ring, nullptr) != VUDA_OK) best.graph_steps = 0;

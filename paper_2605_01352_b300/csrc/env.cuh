@@ -44,6 +44,12 @@ struct vuda_env {
     int nshade = 0;
     int* counters = nullptr;                      // [2]: sim, render
     int sim_grid = 0, ren_grid = 0;
+    int lists = 0;                                // the work lists above are built
+    // SM-shared co-scheduling: per-SM slot counters ([2][kMaxSmSlots]: sim,
+    // render), CTAs per SM of each phase and the launch grids
+    int* sm_slots = nullptr;
+    int sim_quota = 0, ren_quota = 0;
+    int sim_grid_sh = 0, ren_grid_sh = 0;
     // captured pipeline (CUDA graph of gsteps pipelined steps)
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0, gparity = 0, gmode = 0;

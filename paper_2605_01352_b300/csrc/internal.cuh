@@ -84,7 +84,44 @@ struct DevBatch {
 //   shade item:  (desc | slot << 24, unit)   unit < B: body, else ground of env unit - B
 constexpr int kItemDescMask = 0xffffff;
 
+// Per-SM admission of the CTAs of a work-list launch.  With SM-shared
+// co-scheduling the sim and render launches each get a quota of CTAs per SM,
+// so that both stay resident on every SM at once: a CTA stays only while
+// fewer than `quota` CTAs of its launch hold a slot on its SM (slots[%smid]),
+// otherwise it exits before taking work.  quota 0 admits every CTA.  The
+// counts return to zero when the launch ends.
+constexpr int kMaxSmSlots = 1024;
+struct SmGate {
+    int* slots;  // [kMaxSmSlots] device counters, zero between launches
+    int quota;
+};
+constexpr int kGateOpen = -1;  // not gated (no quota, or an SM id beyond the table)
+constexpr int kGateFull = -2;  // this SM already holds `quota` CTAs of the launch
 
+#ifdef __CUDACC__
+// Thread 0 of a CTA: take a slot on this SM.  Returns the SM id whose slot is
+// held, kGateOpen, or kGateFull (the CTA must exit without work).
+__device__ __forceinline__ int sm_gate_take(const SmGate& g) {
+    if (g.quota <= 0 || g.slots == nullptr) return kGateOpen;
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    if (sm >= (unsigned)kMaxSmSlots) return kGateOpen;
+    if (atomicAdd(g.slots + sm, 1) < g.quota) return (int)sm;
+    atomicSub(g.slots + sm, 1);
+    return kGateFull;
+}
+// Thread 0, once the CTA has finished: give back the slot it took (if any).
+__device__ __forceinline__ void sm_gate_release(const SmGate& g, int held) {
+    if (held >= 0) atomicSub(g.slots + held, 1);
+}
+#endif
+
+// Resources one CTA of a work-list kernel holds on an SM.
+struct CtaFootprint {
+    int threads;
+    int regs;   // per thread
+    int smem;   // static + dynamic shared memory, bytes
+};
 
 constexpr int kContactWords = 32;  // floats per contact record
 constexpr int kContactStride = kContactWords + 1;  // words between records (odd: bank-conflict free)
@@ -95,9 +132,11 @@ cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const 
                        int smem_per_env, int max_bodies, cudaStream_t stream);
 // Work-list form: grid CTAs pull items [0, nitems) from *counter (zeroed here
 // on the stream first); max_bodies bounds every listed environment.
+// force: optional [3][B] world forces, only for a list over one batch.
 cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
-                             int smem_per_env, int max_bodies, cudaStream_t stream);
+                             int smem_per_env, int max_bodies, const float* force, SmGate gate, cudaStream_t stream);
 int sim_ctas_per_sm(int smem_per_env);
+CtaFootprint sim_list_footprint(int smem_per_env);
 int phys_smem_bytes_default(int max_bodies, int mcpb);
 int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb);
 cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda_frame& fr, const int32_t* item_cam,
@@ -105,8 +144,9 @@ cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda
 // Work-list form over several batches (frames from each descriptor).
 cudaError_t launch_render_list(const DevBatch* descs, const int4* items, int nitems, int* counter, int grid,
                                const int2* shade_items, int nshade, int band_rows, int max_w, const vuda_frame* fr0,
-                               cudaStream_t stream);
+                               SmGate gate, cudaStream_t stream);
 int render_ctas_per_sm(int band_rows, int max_w);
+CtaFootprint render_list_footprint(int band_rows, int max_w);
 size_t render_smem_for(int band_rows, int W);
 int render_default_band_rows(int max_w, int max_h);
 int render_chunk_bodies();

@@ -808,9 +808,13 @@ __global__ void __launch_bounds__(kT, 7) sim_kernel(DevBatch b0, SimConst sc0, i
 // pose slot) items from an atomic counter; one step each.
 __global__ void __launch_bounds__(kT, 7) sim_list_kernel(const DevBatch* __restrict__ descs,
                                                          const int2* __restrict__ items, int nitems, int* counter,
-                                                         int smem_per_env, int NB) {
+                                                         const float* __restrict__ force, int smem_per_env, int NB,
+                                                         SmGate gate) {
     __shared__ DevBatch sb;
-    __shared__ int s_item;
+    __shared__ int s_item, s_gate;
+    if (threadIdx.x == 0) s_gate = sm_gate_take(gate);
+    __syncthreads();
+    if (s_gate == kGateFull) return;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -819,9 +823,10 @@ __global__ void __launch_bounds__(kT, 7) sim_list_kernel(const DevBatch* __restr
         const int2 it = items[item];
         load_desc(sb, descs[it.x & kItemDescMask]);
         __syncthreads();
-        sim_env(sb, it.y, 1, nullptr, (it.x >> 24) & 1, smem_per_env, NB);
+        sim_env(sb, it.y, 1, force, (it.x >> 24) & 1, smem_per_env, NB);
         __syncthreads();  // everyone is done with sb and s_item
     }
+    if (threadIdx.x == 0) sm_gate_release(gate, s_gate);
 }
 
 }  // namespace
@@ -851,11 +856,15 @@ int sim_ctas_per_sm(int smem_per_env) {
     return n > 0 ? n : 1;
 }
 
+CtaFootprint sim_list_footprint(int smem_per_env) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, sim_list_kernel) != cudaSuccess) return CtaFootprint{kT, 255, 227 * 1024};
+    return CtaFootprint{kT, fa.numRegs, (int)fa.sharedSizeBytes + smem_per_env};
+}
+
 cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
-                             int smem_per_env, int max_bodies, cudaStream_t stream) {
+                             int smem_per_env, int max_bodies, const float* force, SmGate gate, cudaStream_t stream) {
     if (nitems == 0) return cudaSuccess;
-    const int mcpb_max = 0;
-    (void)mcpb_max;
     cudaError_t e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -863,7 +872,8 @@ cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitem
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    sim_list_kernel<<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, smem_per_env, max_bodies);
+    sim_list_kernel<<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force, smem_per_env,
+                                                        max_bodies, gate);
     return cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ constexpr int kMaskWords = kBigCap / 32;
 constexpr int kTile = 16;          // tile edge in pixels
 constexpr float kNear = 0.01f;
 constexpr float kGuard = 16384.0f;
+constexpr int kScreenLimit = 4194304;  // kGuard x 256: largest |X|, |Y| of a snapped vertex
 
 struct Tri {              // a visible, front-facing triangle, vertices oriented to positive area
     int X[3], Y[3];       // 24.8 fixed point
@@ -79,12 +80,19 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     return true;
 }
 
-// int64 -> float (round to nearest even).  Values that fit in 32 bits take
-// the 32-bit conversion (the same rounding of the same integer); only larger
-// ones use the 64-bit conversion, which runs on the narrow FP64 pipe.
+// int64 -> float, round to nearest even, without the 64-bit conversion
+// (which runs on the narrow FP64 pipe).  Split x = H 2^23 + R with
+// H = floor(x / 2^23) and 0 <= R < 2^23.  For |x| < 2^46 (every edge value
+// inside the guard band) |H| < 2^24, so H 2^23 and R are both exact floats,
+// their exact sum is x, and one IEEE single-precision addition returns
+// RN(x): the same value as the correctly rounded conversion.  R goes through
+// the exponent-bias identity float(2^23 + R) - 2^23 = R (exact for R < 2^23).
 __device__ __forceinline__ float i64_to_f32(long long x) {
-    if (x == (long long)(int)x) return __int2float_rn((int)x);
-    return (float)x;
+    const int H = (int)(x >> 23);
+    const unsigned R = (unsigned)x & 0x7FFFFFu;
+    const float hf = __int2float_rn(H) * 8388608.0f;
+    const float rf = __uint_as_float(0x4B000000u | R) - 8388608.0f;
+    return hf + rf;
 }
 
 struct Edges {
@@ -506,9 +514,12 @@ __global__ void __launch_bounds__(kRT, 4) render_kernel(RenderArgs args) {
 __global__ void __launch_bounds__(kRT, 4) render_list_kernel(const DevBatch* __restrict__ descs,
                                                              const int4* __restrict__ items, int nitems,
                                                              int* counter, int band_rows, int max_w, vuda_frame fr0,
-                                                             int use_fr0) {
+                                                             int use_fr0, SmGate gate) {
     __shared__ DevBatch sb;
-    __shared__ int s_item;
+    __shared__ int s_item, s_gate;
+    if (threadIdx.x == 0) s_gate = sm_gate_take(gate);
+    __syncthreads();
+    if (s_gate == kGateFull) return;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -520,6 +531,7 @@ __global__ void __launch_bounds__(kRT, 4) render_list_kernel(const DevBatch* __r
         render_band(sb, it.y, it.z, sb.pose[(it.x >> 24) & 1], use_fr0 ? fr0 : sb.frame, band_rows, max_w);
         __syncthreads();
     }
+    if (threadIdx.x == 0) sm_gate_release(gate, s_gate);
 }
 
 // Test hook: screen-space triangles, one CTA per band of the W x H image,
@@ -557,8 +569,13 @@ __global__ void __launch_bounds__(kRT) raster_screen_kernel(const int32_t* __res
                 Y[v] = xy[6 * t + 2 * v + 1];
                 iz[v] = 1.0f / z[3 * t + v];
             }
+            // vertices beyond the guard band are discarded, as in the renderer
+            bool out = false;
+#pragma unroll
+            for (int v = 0; v < 3; v++)
+                out |= X[v] > kScreenLimit || X[v] < -kScreenLimit || Y[v] > kScreenLimit || Y[v] < -kScreenLimit;
             Tri tri;
-            if (setup_tri(X, Y, iz, (uint32_t)t, bd, tri)) submit_tri(tri, bd, bn);
+            if (!out && setup_tri(X, Y, iz, (uint32_t)t, bd, tri)) submit_tri(tri, bd, bn);
         }
         __syncthreads();
         drain(bd, bn);
@@ -710,9 +727,16 @@ int render_ctas_per_sm(int band_rows, int max_w) {
     return n > 0 ? n : 1;
 }
 
+CtaFootprint render_list_footprint(int band_rows, int max_w) {
+    cudaFuncAttributes fa{};
+    const int dyn = (int)render_smem_bytes(band_rows, max_w);
+    if (cudaFuncGetAttributes(&fa, render_list_kernel) != cudaSuccess) return CtaFootprint{kRT, 255, 227 * 1024};
+    return CtaFootprint{kRT, fa.numRegs, (int)fa.sharedSizeBytes + dyn};
+}
+
 cudaError_t launch_render_list(const DevBatch* descs, const int4* items, int nitems, int* counter, int grid,
                                const int2* shade_items, int nshade, int band_rows, int max_w, const vuda_frame* fr0,
-                               cudaStream_t stream) {
+                               SmGate gate, cudaStream_t stream) {
     cudaError_t err;
     if (nshade > 0) {
         shade_list_kernel<<<(nshade * 32 + 255) / 256, 256, 0, stream>>>(descs, shade_items, nshade);
@@ -727,7 +751,8 @@ cudaError_t launch_render_list(const DevBatch* descs, const int4* items, int nit
     if (err != cudaSuccess) return err;
     vuda_frame f{};
     if (fr0) f = *fr0;
-    render_list_kernel<<<grid, kRT, smem, stream>>>(descs, items, nitems, counter, band_rows, max_w, f, fr0 ? 1 : 0);
+    render_list_kernel<<<grid, kRT, smem, stream>>>(descs, items, nitems, counter, band_rows, max_w, f, fr0 ? 1 : 0,
+                                                    gate);
     return cudaGetLastError();
 }
 

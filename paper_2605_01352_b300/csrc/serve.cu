@@ -318,14 +318,15 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
     // pose slots are reused two iterations later: wait for that render
     if (no >= 2) e = cudaStreamWaitEvent(s->sim_s, s->ev_done[(no - 2) % vuda_server::kRing], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(si.d, si.h, nsim * sizeof(int2), cudaMemcpyHostToDevice, s->sim_s);
-    if (e == cudaSuccess) e = launch_sim_items(s->descs, si.d, (int)nsim, s->counters, sim_grid, smem, max_bodies, s->sim_s);
+    if (e == cudaSuccess) e = launch_sim_items(s->descs, si.d, (int)nsim, s->counters, sim_grid, smem, max_bodies, nullptr,
+                                                SmGate{nullptr, 0}, s->sim_s);
     if (e == cudaSuccess) e = cudaEventRecord(ev_sim, s->sim_s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ri.d, ri.h, nren * sizeof(int4), cudaMemcpyHostToDevice, s->ren_s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hi.d, hi.h, nshade * sizeof(int2), cudaMemcpyHostToDevice, s->ren_s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->ren_s, ev_sim, 0);
     if (e == cudaSuccess)
         e = launch_render_list(s->descs, ri.d, (int)nren, s->counters + 1, ren_grid, hi.d, (int)nshade, br, max_w,
-                               nullptr, s->ren_s);
+                               nullptr, SmGate{nullptr, 0}, s->ren_s);
     if (e == cudaSuccess) e = cudaEventRecord(ev_done, s->ren_s);
     if (e != cudaSuccess) {
         s->fatal = std::string("serving launch: ") + cudaGetErrorString(e);

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(built):
 
 def test_status_strings_without_gpu(built):
     from paper_2605_01352_b300 import vuda
-    assert vuda.lib.vuda_abi_version() == 1
+    assert vuda.lib.vuda_abi_version() == 2
     assert vuda.lib.vuda_status_str(0) == b"ok"
     assert b"invalid" in vuda.lib.vuda_status_str(1)
 

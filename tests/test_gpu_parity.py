@@ -175,6 +175,29 @@ def test_raster_screen_tris_matches_oracle(V, orc):
         np.testing.assert_array_equal(cnt.cpu().numpy(), o_cnt)
 
 
+def test_raster_screen_tris_guard_band_extremes(V, orc):
+    """Triangles with vertices anywhere in the guard band (|x|, |y| up to
+    2^22 in 1/256 px) give edge values up to about 2^46 at the pixel centres;
+    their conversions to float must still be the correctly rounded ones.
+    Vertices beyond the band discard the triangle on both sides."""
+    import torch
+    rng = np.random.default_rng(21)
+    lim = 1 << 22
+    for W, H, n in ((64, 64, 120), (130, 70, 200)):
+        xy = rng.integers(-lim, lim + 1, (n, 3, 2)).astype(np.int64)
+        xy[::7] = rng.choice([-lim, lim], (len(xy[::7]), 3, 2))          # on the band's edge
+        xy[3::11, 1, 0] = lim + rng.integers(1, 1000, len(xy[3::11]))     # beyond it: discarded
+        xy = xy.astype(np.int32)
+        z = rng.uniform(0.05, 50.0, (n, 3)).astype(np.float32)
+        tid, dep, cnt = V.raster_screen_tris(torch.from_numpy(xy).cuda(), torch.from_numpy(z).cuda(), W, H,
+                                             count=True)
+        o_tid, o_dep, o_cnt = orc.raster_screen_tris(xy, z, W, H, count=True)
+        assert (o_tid != 0xFFFFFFFF).mean() > 0.5          # the image is mostly covered
+        np.testing.assert_array_equal(tid.cpu().numpy().view(np.uint32), o_tid)
+        np.testing.assert_array_equal(dep.cpu().numpy(), o_dep)
+        np.testing.assert_array_equal(cnt.cpu().numpy(), o_cnt)
+
+
 def test_raster_screen_tris_empty(V):
     import torch
     tid, dep, cnt = V.raster_screen_tris(torch.zeros((0, 3, 2), dtype=torch.int32, device="cuda"),
@@ -183,12 +206,12 @@ def test_raster_screen_tris_empty(V):
     assert (dep.cpu().numpy() == 0).all() and (cnt.cpu().numpy() == 0).all()
 
 
-def _run_loop(V, sc, steps, mode):
+def _run_loop(V, sc, steps, mode, **co):
     import torch
     env = V.Env(sc)
     ring = [env.alloc_frame(), env.alloc_frame()]
     if mode:
-        env.coschedule(mode)
+        env.coschedule(mode, **co)
     env.pipeline_run(steps, ring)
     torch.cuda.synchronize()
     st = env.get_state()
@@ -197,20 +220,40 @@ def _run_loop(V, sc, steps, mode):
     return st, out
 
 
-@pytest.mark.parametrize("mode", ["streams", "green"])
+@pytest.mark.parametrize("mode", ["streams", "green", "shared", "shared-1-1"])
 def test_coscheduled_equals_serialized(V, mode):
-    """Pipelined sim(t+1) || render(t) on two streams (shared SMs or disjoint
-    green-context partitions) gives the same state and frames as the
-    serialized loop, bit for bit."""
+    """Pipelined sim(t+1) || render(t) on two streams (shared SMs, disjoint
+    green-context partitions, or per-SM CTA quotas with both phases resident
+    on every SM) gives the same state and frames as the serialized loop, bit
+    for bit."""
     sc = S.cfg2(64)
-    m = V.COSCHED_STREAMS if mode == "streams" else V.COSCHED_GREEN
+    m = {"streams": V.COSCHED_STREAMS, "green": V.COSCHED_GREEN}.get(mode, V.COSCHED_SHARED)
+    co = dict(sim_ctas_per_sm=1, render_ctas_per_sm=1) if mode == "shared-1-1" else {}
     st0, fr0 = _run_loop(V, sc, 7, 0)
-    st1, fr1 = _run_loop(V, sc, 7, m)
+    st1, fr1 = _run_loop(V, sc, 7, m, **co)
     for k in st0:
         np.testing.assert_array_equal(st0[k], st1[k])
     for a, b in zip(fr0, fr1):
         for k in a:
             np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_shared_quotas_reported_and_checked(V):
+    """Per-SM quotas: the default pair fits one SM and is reported; a pair
+    that cannot fit one SM together is refused before anything launches;
+    reset returns the batch to serialized launches."""
+    sc = S.cfg2(16)
+    env = V.Env(sc)
+    info = env.coschedule(V.COSCHED_SHARED)
+    assert info["mode"] == V.COSCHED_SHARED
+    assert info["sim_ctas_per_sm"] >= 1 and info["render_ctas_per_sm"] >= 1
+    with pytest.raises(V.VudaError) as ex:
+        env.coschedule(V.COSCHED_SHARED, sim_ctas_per_sm=32, render_ctas_per_sm=32)
+    assert ex.value.status == V.ERR_INVALID
+    with pytest.raises(V.VudaError):
+        env.coschedule(V.COSCHED_SHARED, sim_ctas_per_sm=-1)
+    env.coschedule_reset()
+    env.close()
 
 
 def test_pipeline_frames_match_oracle(V, orc):
@@ -295,13 +338,13 @@ def test_persistent_uneven_batch_matches(V, orc):
     np.testing.assert_allclose(f1["depth"], o_dep, rtol=DEPTH_RTOL)
 
 
-@pytest.mark.parametrize("mode", ["single", "streams", "green"])
+@pytest.mark.parametrize("mode", ["single", "streams", "green", "shared"])
 def test_graph_replay_equals_launches(V, mode):
     """A captured CUDA graph of pipelined steps replays to the same state and
     frames as launching the steps one by one."""
     import torch
     sc = S.cfg2(32)
-    m = {"single": 0, "streams": V.COSCHED_STREAMS, "green": V.COSCHED_GREEN}[mode]
+    m = {"single": 0, "streams": V.COSCHED_STREAMS, "green": V.COSCHED_GREEN, "shared": V.COSCHED_SHARED}[mode]
     out = []
     for use_graph in (False, True):
         env = V.Env(sc)
@@ -345,7 +388,9 @@ def test_autotune_keeps_results_and_caches(V):
     ring = [env.alloc_frame(), env.alloc_frame()]
     res = env.autotune(ring, steps=3, use_cache=True)
     assert res["trials"] > 0 and res["band_rows"] in (16, 32, 64, 128)
-    assert res["cosched_mode"] in (0, V.COSCHED_STREAMS, V.COSCHED_GREEN)
+    assert res["cosched_mode"] in (0, V.COSCHED_STREAMS, V.COSCHED_GREEN, V.COSCHED_SHARED)
+    if res["cosched_mode"] == V.COSCHED_SHARED:
+        assert res["sim_ctas_per_sm"] >= 1 and res["render_ctas_per_sm"] >= 1
     assert env.info().steps_enqueued == 0
     env.pipeline_run(4, ring)
     torch.cuda.synchronize()

@@ -270,3 +270,16 @@ def test_scene_meshes_are_closed_and_outward():
         n = np.cross(Vd[T[:, 1]] - Vd[T[:, 0]], Vd[T[:, 2]] - Vd[T[:, 0]])
         assert (np.einsum("ij,ij->i", n, Vd[T].mean(1)) > 0).all()
     assert S.icosphere(1)[1].shape == (80, 3) and S.icosphere(1)[0].shape == (42, 3)
+
+
+def test_guard_band_vertex_discards_triangle(orc):
+    """A vertex beyond the 2^14-pixel guard band (2^22 in 1/256 px) discards
+    its triangle; one exactly on the band's edge is kept (hook rule, as the
+    projection's guard-band discard in the renderer)."""
+    lim = 1 << 22
+    big = _front([(lim, lim), (-lim, lim), (lim, -lim)])   # covers x + y > 0: the whole image
+    tid, _, _ = orc.raster_screen_tris(np.array([big]), np.ones((1, 3)), 8, 8)
+    assert (tid == 0).all()
+    over = _front([(lim + 1, lim), (-lim, lim), (lim, -lim)])
+    tid, _, _ = orc.raster_screen_tris(np.array([over]), np.ones((1, 3)), 8, 8)
+    assert (tid == 0xFFFFFFFF).all()
