@@ -132,7 +132,22 @@ typedef struct {
     int32_t persistent;           /* 1: one persistent launch per phase pulls work items (environments,
                                      camera bands) largest first from an atomic counter -- for batches of
                                      uneven environments; 0: one CTA per item */
+    int32_t render_path;          /* VUDA_RENDER_AUTO / _BAND / _TILED (see below) */
 } vuda_env_opts;
+
+/* Render paths (identical frames; they differ in how work is split):
+ * BAND: one CTA per band of rows of a camera sets up every triangle of the
+ * environment and rasterises the band in shared memory.  TILED: one CTA per
+ * camera sets up every triangle once into a device scratch area and bins it
+ * into 16 x 16 tiles, then one warp per tile rasterises and resolves it
+ * (needs cameras of at most 1024 tiles, and scratch of about
+ * 120 bytes per triangle and camera).  AUTO: TILED where it applies and its
+ * scratch fits (at most 8 GiB, and within hbm_budget_bytes), else BAND.
+ * Persistent work-list launches (persistent = 1, VUDA_COSCHED_SHARED and the
+ * serving loop) use the band kernel. */
+#define VUDA_RENDER_AUTO 0
+#define VUDA_RENDER_BAND 1
+#define VUDA_RENDER_TILED 2
 
 /* Sizes of a created batch. */
 typedef struct {
@@ -141,6 +156,7 @@ typedef struct {
     int64_t num_tris;             /* total triangles drawn per step over all envs (per camera) */
     int64_t device_bytes;         /* device memory held by the batch */
     int64_t steps_enqueued;       /* physics steps enqueued so far */
+    int32_t render_path;          /* VUDA_RENDER_BAND or VUDA_RENDER_TILED: the path the batch renders with */
 } vuda_env_info;
 
 /* Caller-owned device output buffers, concatenated per camera in cam order

@@ -553,6 +553,38 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     // device memory budget
     int64_t need = (int64_t)B * 4 * (3 + 4 + 3 + 3 + 3 + 1 + 3 + 3 + 2 * 7) + B * 1 + (int64_t)B * 4 * 2 +
                    (int64_t)E * 12 + (int64_t)spill_off[E] * kContactStride * 4 + env->T * 4 + (int64_t)C * 80;
+    // render path: tiled where every camera fits the per-camera tile table
+    // and its scratch fits (records, wide list and tile lists per triangle of
+    // each camera, list offsets per tile)
+    if (o.render_path < VUDA_RENDER_AUTO || o.render_path > VUDA_RENDER_TILED) {
+        delete env;
+        return invalid("render_path must be VUDA_RENDER_AUTO, _BAND or _TILED");
+    }
+    std::vector<int64_t> rec_base(C + 1, 0), ent_base(C + 1, 0), toff_base(C + 1, 0);
+    std::vector<int2> titems;
+    bool can_tile = C > 0;
+    const int tpi = tiled_tiles_per_item();
+    for (int c = 0; c < C; c++) {
+        const int e = cam_env[c];
+        const int64_t tc = env_tri_base[e + 1] - env_tri_base[e];
+        const int ntl = ((sc->cam_w[c] + 15) / 16) * ((sc->cam_h[c] + 15) / 16);
+        if (ntl > tiled_max_tiles()) can_tile = false;
+        rec_base[c + 1] = rec_base[c] + tc;
+        ent_base[c + 1] = ent_base[c] + tc * tiled_narrow_tiles();
+        toff_base[c + 1] = toff_base[c] + ntl + 2;
+        for (int t0 = 0; t0 < ntl; t0 += tpi) titems.push_back(make_int2(c, t0));
+    }
+    const int64_t tile_bytes = rec_base[C] * (int64_t)(tiled_record_bytes() + 4) + ent_base[C] * 4 +
+                               toff_base[C] * 4 + (int64_t)C * 24 + (int64_t)titems.size() * 8;
+    if (o.render_path == VUDA_RENDER_TILED && !can_tile) {
+        delete env;
+        return invalid("tiled render path: a camera has more than " + std::to_string(tiled_max_tiles()) +
+                       " tiles of 16 x 16 pixels");
+    }
+    env->tiled = o.render_path == VUDA_RENDER_TILED ||
+                 (o.render_path == VUDA_RENDER_AUTO && can_tile && tile_bytes <= (int64_t(8) << 30) &&
+                  (o.hbm_budget_bytes <= 0 || need + tile_bytes <= o.hbm_budget_bytes));
+    if (env->tiled) need += tile_bytes;
     if (o.hbm_budget_bytes > 0 && need > o.hbm_budget_bytes) {
         delete env;
         set_error("batch needs " + std::to_string(need) + " bytes, over the HBM budget");
@@ -622,6 +654,26 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         bool need_spill = (int64_t)mcpb * max_bodies > cap_smem;
         if (s == VUDA_OK && need_spill)
             s = dalloc(env, &d.spill, (size_t)std::max<int64_t>(spill_off[E], 1) * kContactStride);
+    }
+    if (s == VUDA_OK && env->tiled) {
+        TileScratch& ts = env->ts;
+        uint8_t* rec = nullptr;
+        s = dalloc(env, &rec, (size_t)rec_base[C] * tiled_record_bytes());
+        ts.rec = rec;
+        if (s == VUDA_OK) s = dalloc(env, &ts.wide, (size_t)rec_base[C]);
+        if (s == VUDA_OK) s = dalloc(env, &ts.ent, (size_t)ent_base[C]);
+        if (s == VUDA_OK) s = dalloc(env, &ts.toff, (size_t)toff_base[C]);
+        int64_t* d_rb = nullptr;
+        int64_t* d_eb = nullptr;
+        int64_t* d_tb = nullptr;
+        if (s == VUDA_OK) s = upload(env, &d_rb, rec_base.data(), (size_t)C);
+        if (s == VUDA_OK) s = upload(env, &d_eb, ent_base.data(), (size_t)C);
+        if (s == VUDA_OK) s = upload(env, &d_tb, toff_base.data(), (size_t)C);
+        ts.rec_base = d_rb;
+        ts.ent_base = d_eb;
+        ts.toff_base = d_tb;
+        if (s == VUDA_OK) s = upload(env, &env->titems, titems.data(), titems.size());
+        env->ntitems = (int)titems.size();
     }
     if (s == VUDA_OK && E) {
         if (cudaMemset(d.flags, 0, sizeof(uint32_t) * E) != cudaSuccess ||
@@ -696,6 +748,7 @@ vuda_status vuda_env_info_get(vuda_env_t env, vuda_env_info* out) {
     out->num_tris = env->T;
     out->device_bytes = env->bytes;
     out->steps_enqueued = env->steps;
+    out->render_path = env->tiled ? VUDA_RENDER_TILED : VUDA_RENDER_BAND;
     return VUDA_OK;
 }
 
@@ -734,7 +787,9 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
 static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, cudaStream_t stream) {
     cudaError_t e;
     const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
-    if (env->persistent || shared)
+    if (env->tiled && !env->persistent && !shared)
+        e = launch_render_tiled(env->d, env->d.pose[slot], *fr, env->ts, env->titems, env->ntitems, stream);
+    else if (env->persistent || shared)
         e = launch_render_list(env->d_desc, env->ren_items[slot], env->nitems, env->counters + 1,
                                shared ? env->ren_grid_sh : env->ren_grid, env->shade_items[slot], env->nshade,
                                env->band_rows, env->max_w, fr,

@@ -50,6 +50,11 @@ struct vuda_env {
     int* sm_slots = nullptr;
     int sim_quota = 0, ren_quota = 0;
     int sim_grid_sh = 0, ren_grid_sh = 0;
+    // tiled render path: scratch and work items (camera, first tile)
+    int tiled = 0;
+    vuda::TileScratch ts{};
+    int2* titems = nullptr;
+    int ntitems = 0;
     // captured pipeline (CUDA graph of gsteps pipelined steps)
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0, gparity = 0, gmode = 0;

@@ -153,6 +153,31 @@ int render_chunk_bodies();
 cudaError_t launch_raster_screen(const int32_t* xy, const float* z, int ntri, int W, int H, uint32_t* triid,
                                  float* depth, uint32_t* count, cudaStream_t stream);
 int render_vcap();
+// Per-triangle flat colours of the batch for the poses `pose` (render.cu).
+cudaError_t launch_shade(const DevBatch& b, const float* pose, cudaStream_t stream);
+
+// Scratch of the tiled render path (tiled.cu), per camera c of env e with
+// T_e triangles and n_c 16 x 16 tiles: records [rec_base[c], + T_e) of
+// tiled_record_bytes() each, wide list [rec_base[c], + T_e), tile lists
+// [ent_base[c], + kNarrowTiles T_e), offsets [toff_base[c], + n_c + 2)
+// (n_c + 1 list offsets, then the wide-list length).
+struct TileScratch {
+    void* rec;
+    uint32_t* ent;
+    uint32_t* wide;
+    int32_t* toff;
+    const int64_t* rec_base;
+    const int64_t* ent_base;
+    const int64_t* toff_base;
+};
+int tiled_max_tiles();        // tiles per camera the path supports
+int tiled_narrow_tiles();     // list entries per triangle at most
+int tiled_tiles_per_item();   // tiles per raster work item
+size_t tiled_record_bytes();
+// Shade, set up and bin every camera, then rasterise and resolve the work
+// items (camera, first tile) of tiled_tiles_per_item() tiles each.
+cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
+                                const int2* items, int nitems, cudaStream_t stream);
 
 void set_error(const std::string& s);
 // Device bytes a batch will hold once created (an upper estimate).

@@ -2,7 +2,7 @@
 // rasteriser (the rendering phase the paper runs through Vulkan's vertex ->
 // rasterisation -> fragment pipeline, Sec. 2.1).
 //
-// Work item = (camera, band of rows).  One CTA of 512 threads per work item:
+// Work item = (camera, band of rows).  One CTA of 256 threads per work item:
 //   1. for each chunk of the env's bodies (ground quad first) whose vertices
 //      fit the shared-memory vertex cache: transform every vertex
 //      world = R(q) (s * v) + p, view = basis . (world - eye), project
@@ -27,21 +27,18 @@
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
+#include "raster.cuh"
 
 namespace vuda {
 namespace {
 
 constexpr int kRT = 256;           // threads per CTA
 constexpr int kWarps = kRT / 32;
-constexpr int kVcap = 1024;        // vertices per chunk
+constexpr int kVcap = kVertexCache; // vertices per chunk
 constexpr int kChunkBodies = 128;  // bodies per chunk
 constexpr int kSmallPx = 16;       // triangles with at most this many bbox pixels stay thread-local
 constexpr int kBigCap = 256;       // binned triangles per chunk pass
 constexpr int kMaskWords = kBigCap / 32;
-constexpr int kTile = 16;          // tile edge in pixels
-constexpr float kNear = 0.01f;
-constexpr float kGuard = 16384.0f;
-constexpr int kScreenLimit = 4194304;  // kGuard x 256: largest |X|, |Y| of a snapped vertex
 
 struct Tri {              // a visible, front-facing triangle, vertices oriented to positive area
     int X[3], Y[3];       // 24.8 fixed point
@@ -78,21 +75,6 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     t.id = id;
     t.x0 = (short)px0; t.x1 = (short)px1; t.y0 = (short)py0; t.y1 = (short)py1;
     return true;
-}
-
-// int64 -> float, round to nearest even, without the 64-bit conversion
-// (which runs on the narrow FP64 pipe).  Split x = H 2^23 + R with
-// H = floor(x / 2^23) and 0 <= R < 2^23.  For |x| < 2^46 (every edge value
-// inside the guard band) |H| < 2^24, so H 2^23 and R are both exact floats,
-// their exact sum is x, and one IEEE single-precision addition returns
-// RN(x): the same value as the correctly rounded conversion.  R goes through
-// the exponent-bias identity float(2^23 + R) - 2^23 = R (exact for R < 2^23).
-__device__ __forceinline__ float i64_to_f32(long long x) {
-    const int H = (int)(x >> 23);
-    const unsigned R = (unsigned)x & 0x7FFFFFu;
-    const float hf = __int2float_rn(H) * 8388608.0f;
-    const float rf = __uint_as_float(0x4B000000u | R) - 8388608.0f;
-    return hf + rf;
 }
 
 struct Edges {
@@ -291,18 +273,6 @@ __device__ __forceinline__ void drain(const Band& bd, Bins& bn) {
     }
 }
 
-__device__ __forceinline__ void quat_mat(float w, float x, float y, float z, float* R) {
-    R[0] = 1.0f - 2.0f * (y * y + z * z);
-    R[1] = 2.0f * (x * y - w * z);
-    R[2] = 2.0f * (x * z + w * y);
-    R[3] = 2.0f * (x * y + w * z);
-    R[4] = 1.0f - 2.0f * (x * x + z * z);
-    R[5] = 2.0f * (y * z - w * x);
-    R[6] = 2.0f * (x * z - w * y);
-    R[7] = 2.0f * (y * z + w * x);
-    R[8] = 1.0f - 2.0f * (x * x + y * y);
-}
-
 struct RenderArgs {
     DevBatch b;
     const float* pose;       // [7][B]
@@ -357,14 +327,7 @@ __device__ __forceinline__ void render_band(const DevBatch& b, int cam, int y0, 
     bn.nrec = reinterpret_cast<int*>(p); p += 4;
     unsigned* sflags = reinterpret_cast<unsigned*>(p); p += 12;
 
-    const float* cp = b.cam_par + (size_t)cam * kCamWords;
-    const float ex = cp[0], ey = cp[1], ez = cp[2];
-    const float rx = cp[3], ry = cp[4], rz = cp[5];
-    const float ux = cp[6], uy = cp[7], uz = cp[8];
-    const float fx = cp[9], fy = cp[10], fz = cp[11];
-    const float fpy = cp[12];
-    const float hw = (float)W * 0.5f, hh = (float)H * 0.5f;
-    const int B = b.B;
+    const CamView cv = load_cam(b, cam);
     const int b0 = b.body_off[e];
     uint32_t* colors = b.tri_color + b.env_tri_base[e];
 
@@ -381,43 +344,12 @@ __device__ __forceinline__ void render_band(const DevBatch& b, int cam, int y0, 
         __syncthreads();  // the previous chunk's triangles are done with the vertex cache
         // 1. vertices
         for (int v = threadIdx.x; v < nv; v += kRT) {
-            int2 ent = vt[v];
-            int bi = cb0 + ent.y;
-            const float* mv = b.mesh_verts + 3 * (size_t)ent.x;
-            float wx, wy, wz;
-            if (bi < 0) {
-                wx = mv[0]; wy = mv[1]; wz = mv[2];
-            } else {
-                int g = b0 + bi;
-                float R[9];
-                quat_mat(a.pose[3 * B + g], a.pose[4 * B + g], a.pose[5 * B + g], a.pose[6 * B + g], R);
-                float sx = b.scale[g] * mv[0], sy = b.scale[B + g] * mv[1], sz = b.scale[2 * B + g] * mv[2];
-                float tx = (R[0] * sx + R[1] * sy) + R[2] * sz;
-                float ty = (R[3] * sx + R[4] * sy) + R[5] * sz;
-                float tz = (R[6] * sx + R[7] * sy) + R[8] * sz;
-                wx = tx + a.pose[g];
-                wy = ty + a.pose[B + g];
-                wz = tz + a.pose[2 * B + g];
-            }
-            float dx = wx - ex, dy = wy - ey, dz = wz - ez;
-            float xc = (rx * dx + ry * dy) + rz * dz;
-            float yc = (ux * dx + uy * dy) + uz * dz;
-            float zc = (fx * dx + fy * dy) + fz * dz;
-            int flag = 0;
-            if (!(zc >= kNear)) {
-                flag = VUDA_FLAG_NEAR_DISCARD;
-            } else {
-                float sxp = hw + (fpy * xc) / zc;
-                float syp = hh - (fpy * yc) / zc;
-                if (!(fabsf(sxp) < kGuard && fabsf(syp) < kGuard)) {
-                    flag = VUDA_FLAG_GUARD_DISCARD;
-                } else {
-                    vX[v] = __float2int_rn(sxp * 256.0f);
-                    vY[v] = __float2int_rn(syp * 256.0f);
-                    viz[v] = 1.0f / zc;
-                }
-            }
-            vflag[v] = flag;
+            int X = 0, Y = 0;
+            float iz = 0.0f;
+            vflag[v] = project_vertex(b, a.pose, cv, b0, cb0, vt[v], X, Y, iz);
+            vX[v] = X;
+            vY[v] = Y;
+            viz[v] = iz;
         }
         __syncthreads();
         // 2. triangles: strided over the CTA, no barrier until all are submitted
@@ -682,6 +614,13 @@ size_t screen_smem_bytes(int band_rows, int W) {
 
 }  // namespace
 
+cudaError_t launch_shade(const DevBatch& b, const float* pose, cudaStream_t stream) {
+    if (b.B + b.E == 0) return cudaSuccess;
+    const int units = b.B + b.E;
+    shade_kernel<<<(units * 32 + 255) / 256, 256, 0, stream>>>(b, pose);
+    return cudaGetLastError();
+}
+
 int render_vcap() { return kVcap; }
 int render_chunk_bodies() { return kChunkBodies; }
 size_t render_smem_for(int band_rows, int W) { return render_smem_bytes(band_rows, W); }
@@ -701,12 +640,8 @@ cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda
     // kernel may be launched into different (green) contexts
     cudaError_t err = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    if (b.B + b.E > 0) {
-        int units = b.B + b.E;
-        shade_kernel<<<(units * 32 + 255) / 256, 256, 0, stream>>>(b, pose);
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
-    }
+    err = launch_shade(b, pose, stream);
+    if (err != cudaSuccess) return err;
     RenderArgs a;
     a.b = b;
     a.pose = pose;

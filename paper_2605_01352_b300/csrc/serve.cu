@@ -210,6 +210,7 @@ void admit(vuda_server* s) {
         s->admit_queue.pop_front();
         vuda_env_opts eo{};
         eo.device = s->o.device;
+        eo.render_path = VUDA_RENDER_BAND;   // jobs render through the band work list
         vuda_status st = vuda_env_create(&j->scene->view, &j->params, &eo, &j->env);
         if (st == VUDA_OK) {
             size_t P = (size_t)j->env->P;

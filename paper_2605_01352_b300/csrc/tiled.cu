@@ -1,0 +1,432 @@
+// Tiled render path: the rasteriser of render.cu split so that no work is
+// repeated across a camera's image (the band kernel transforms and sets up
+// every triangle of the environment once per band of rows).
+//
+//   bin_kernel, one CTA per camera: for each chunk of the environment's
+//   bodies (ground quad first), transform and project the chunk's vertices
+//   into shared memory, then set up every triangle once -- signed area (back
+//   faces and degenerate triangles culled), bounding box clipped to the
+//   image, edge functions and top-left bits -- and write it as an 80-byte
+//   record to the camera's scratch area in global memory (read back by the
+//   raster kernel from L2).  A counting sort in shared memory lists each
+//   record that overlaps at most kNarrowTiles 16 x 16 tiles under every one
+//   of them; records over more tiles go to one wide list of the camera.
+//   tile_kernel, one warp per tile and no CTA barriers: records whose
+//   unclipped bounding box has at most kLanePx pixel centres are rasterised
+//   one per lane with 32-bit edge functions (exact for boxes that small)
+//   into the warp's 16 x 16 key buffer in shared memory (atomicMin); larger
+//   records and the wide list go through the warp-wide pass, in which every
+//   lane keeps the keys of its run of 8 pixels in registers.  The tile is
+//   then resolved from min(register key, shared key) to RGB8, FP32 depth and
+//   u32 triangle id.
+// Coverage rule, depth and key are those of the band kernel (integer edge
+// functions at pixel centres with the top-left rule, depth
+// area2 / (E0/z0 + E1/z1 + E2/z2), minimum of depth_bits << 32 | id), and the
+// minimum does not depend on the order of the fragments, so both paths give
+// identical frames.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+#include "raster.cuh"
+
+namespace vuda {
+namespace {
+
+constexpr int kBT = 256;          // bin_kernel threads
+constexpr int kNarrowTiles = 9;   // records over more tiles go to the camera's wide list
+constexpr int kMaxTiles = 1024;   // tiles per camera the counting sort holds in shared memory
+constexpr int kLanePx = 64;       // unclipped bounding-box pixels up to which one lane rasterises a record
+constexpr int kTW = 8;            // tiles (warps) per tile_kernel CTA
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr unsigned kSmallBit = 8u;  // TriRec::tl bit: the record takes the per-lane path
+
+// A set-up triangle, vertices oriented to positive area (80 bytes, 16-byte
+// aligned in the scratch array).
+struct __align__(16) TriRec {
+    int A[3], B[3];        // edge i: E_i = A_i x + B_i y + C_i in 1/256 px; |A|, |B| <= 2^23
+    long long C[3];
+    float iz[3];           // 1 / view depth of the vertices
+    float af;              // (float) doubled area
+    short x0, x1, y0, y1;  // pixel bounding box, clipped to the image
+    uint32_t id;           // env-local triangle id
+    unsigned tl;           // bits 0..2: edge i owns its pixels (top-left rule); kSmallBit
+};
+static_assert(sizeof(TriRec) == 80, "TriRec layout");
+
+__device__ __forceinline__ TriRec load_rec(const TriRec* __restrict__ p) {
+    union {
+        int4 v[5];
+        TriRec t;
+    } u;
+    const int4* q = reinterpret_cast<const int4*>(p);
+#pragma unroll
+    for (int k = 0; k < 5; k++) u.v[k] = __ldg(q + k);
+    return u.t;
+}
+
+__device__ __forceinline__ void store_rec(TriRec* p, const TriRec& t) {
+    union {
+        int4 v[5];
+        TriRec t;
+    } u;
+    u.t = t;
+    int4* q = reinterpret_cast<int4*>(p);
+#pragma unroll
+    for (int k = 0; k < 5; k++) q[k] = u.v[k];
+}
+
+// Exclusive prefix sum over the kBT threads of the CTA, in thread order.
+__device__ __forceinline__ int cta_excl_scan(int v, int* wsum, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFullMask, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int off = 0;
+    total = 0;
+#pragma unroll
+    for (int k = 0; k < kBT / 32; k++) {
+        int s = wsum[k];
+        if (k < w) off += s;
+        total += s;
+    }
+    __syncthreads();
+    return off + x - v;
+}
+
+__global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts) {
+    __shared__ int vX[kVertexCache], vY[kVertexCache], vflag[kVertexCache];
+    __shared__ float viz[kVertexCache];
+    __shared__ int s_cnt[kMaxTiles];
+    __shared__ int s_wsum[kBT / 32];
+    __shared__ int s_nrec, s_nwide;
+    __shared__ unsigned s_flags;
+
+    const int cam = blockIdx.x;
+    const int e = b.cam_env[cam];
+    const int W = b.cam_w[cam], H = b.cam_h[cam];
+    const int tiles_x = (W + kTile - 1) / kTile;
+    const int ntiles = tiles_x * ((H + kTile - 1) / kTile);
+    TriRec* rec = reinterpret_cast<TriRec*>(ts.rec) + ts.rec_base[cam];
+    uint32_t* wide = ts.wide + ts.rec_base[cam];
+    uint32_t* ent = ts.ent + ts.ent_base[cam];
+    int32_t* toff = ts.toff + ts.toff_base[cam];
+    const CamView cv = load_cam(b, cam);
+    const int b0 = b.body_off[e];
+
+    for (int i = threadIdx.x; i < ntiles; i += kBT) s_cnt[i] = 0;
+    if (threadIdx.x == 0) {
+        s_nrec = 0;
+        s_nwide = 0;
+        s_flags = 0u;
+    }
+    for (int ck = b.chunk_off[e]; ck < b.chunk_off[e + 1]; ck++) {
+        const int cb0 = b.chunk_lo[ck];   // env-local first body, -1 = ground
+        const int nv = b.chunk_nv[ck], nt = b.chunk_nt[ck];
+        const int2* vt = b.vtab + b.chunk_vtab[ck];
+        const uint2* tt = b.ttab + b.chunk_ttab[ck];
+        const uint32_t tri0 = (uint32_t)b.chunk_tri0[ck];
+        __syncthreads();  // counters set; the previous chunk is done with the vertex cache
+        for (int v = threadIdx.x; v < nv; v += kBT) {
+            int X = 0, Y = 0;
+            float iz = 0.0f;
+            vflag[v] = project_vertex(b, pose, cv, b0, cb0, vt[v], X, Y, iz);
+            vX[v] = X;
+            vY[v] = Y;
+            viz[v] = iz;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nt; t += kBT) {
+            const uint2 tv = tt[t];
+            const int i0 = tv.x & 0xffff, i1 = tv.x >> 16, i2 = tv.y;
+            const int fl = vflag[i0] | vflag[i1] | vflag[i2];
+            if (fl) {
+                atomicOr(&s_flags, (unsigned)fl);
+                continue;
+            }
+            const int X0 = vX[i0], X1 = vX[i1], X2 = vX[i2];
+            const int Y0 = vY[i0], Y1 = vY[i1], Y2 = vY[i2];
+            const int mnx = min(X0, min(X1, X2)), mxx = max(X0, max(X1, X2));
+            const int mny = min(Y0, min(Y1, Y2)), mxy = max(Y0, max(Y1, Y2));
+            // pixel centres 256 p + 128 inside [mn, mx], before and after clipping to the image
+            const int ux0 = (mnx - 128 + 255) >> 8, ux1 = (mxx - 128) >> 8;
+            const int uy0 = (mny - 128 + 255) >> 8, uy1 = (mxy - 128) >> 8;
+            const int px0 = max(ux0, 0), px1 = min(ux1, W - 1);
+            const int py0 = max(uy0, 0), py1 = min(uy1, H - 1);
+            if (px0 > px1 || py0 > py1) continue;
+            const long long area2 = ((long long)X1 - X0) * ((long long)Y2 - Y0) - ((long long)Y1 - Y0) * ((long long)X2 - X0);
+            if (area2 >= 0) continue;   // back-facing or degenerate
+            // oriented to positive area: (v0, v2, v1)
+            const int X[3] = {X0, X2, X1}, Y[3] = {Y0, Y2, Y1};
+            TriRec g;
+            unsigned tl = 0u;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const int j = i == 2 ? 0 : i + 1, k = i == 0 ? 2 : i - 1;
+                const long long A = (long long)Y[j] - Y[k];
+                const long long Bv = (long long)X[k] - X[j];
+                g.A[i] = (int)A;
+                g.B[i] = (int)Bv;
+                g.C[i] = -A * X[j] - Bv * Y[j];
+                if ((A > 0) || (A == 0 && Bv > 0)) tl |= 1u << i;
+            }
+            const long long pa = ((long long)X[1] - X[0]) * ((long long)Y[2] - Y[0]) -
+                                 ((long long)Y[1] - Y[0]) * ((long long)X[2] - X[0]);
+            g.af = i64_to_f32(pa);
+            g.iz[0] = viz[i0];
+            g.iz[1] = viz[i2];
+            g.iz[2] = viz[i1];
+            g.id = tri0 + (uint32_t)t;
+            g.x0 = (short)px0; g.x1 = (short)px1; g.y0 = (short)py0; g.y1 = (short)py1;
+            if ((long long)(ux1 - ux0 + 1) * (uy1 - uy0 + 1) <= kLanePx) tl |= kSmallBit;
+            g.tl = tl;
+            const int r = atomicAdd(&s_nrec, 1);
+            store_rec(rec + r, g);
+            const int tx0 = px0 / kTile, tx1 = px1 / kTile, ty0 = py0 / kTile, ty1 = py1 / kTile;
+            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kNarrowTiles) {
+                for (int ty = ty0; ty <= ty1; ty++)
+                    for (int tx = tx0; tx <= tx1; tx++) atomicAdd(&s_cnt[ty * tiles_x + tx], 1);
+            } else {
+                wide[atomicAdd(&s_nwide, 1)] = (uint32_t)r;
+            }
+        }
+    }
+    __syncthreads();
+    // list offsets: exclusive prefix sum of the tile counts (at most 4 tiles per thread)
+    const int per = (ntiles + kBT - 1) / kBT;
+    const int i0 = threadIdx.x * per;
+    int loc[kMaxTiles / kBT];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxTiles / kBT; k++) {
+        loc[k] = sum;
+        if (k < per && i0 + k < ntiles) sum += s_cnt[i0 + k];
+    }
+    int total;
+    const int off = cta_excl_scan(sum, s_wsum, total);   // its barriers order the reads above
+#pragma unroll
+    for (int k = 0; k < kMaxTiles / kBT; k++)
+        if (k < per && i0 + k < ntiles) {
+            s_cnt[i0 + k] = off + loc[k];   // becomes the fill cursor of the tile
+            toff[i0 + k] = off + loc[k];
+        }
+    if (threadIdx.x == 0) {
+        toff[ntiles] = total;
+        toff[ntiles + 1] = s_nwide;
+    }
+    __syncthreads();
+    // fill the tile lists (the order inside a list is free: the key minimum does not depend on it)
+    const int nrec = s_nrec;
+    for (int r = threadIdx.x; r < nrec; r += kBT) {
+        const int2 bb = *reinterpret_cast<const int2*>(reinterpret_cast<const char*>(rec + r) + 64);
+        const int px0 = (short)(bb.x & 0xffff), px1 = bb.x >> 16;
+        const int py0 = (short)(bb.y & 0xffff), py1 = bb.y >> 16;
+        const int tx0 = px0 / kTile, tx1 = px1 / kTile, ty0 = py0 / kTile, ty1 = py1 / kTile;
+        if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kNarrowTiles) {
+            for (int ty = ty0; ty <= ty1; ty++)
+                for (int tx = tx0; tx <= tx1; tx++) ent[atomicAdd(&s_cnt[ty * tiles_x + tx], 1)] = (uint32_t)r;
+        }
+    }
+    if (threadIdx.x == 0 && s_flags) atomicOr(b.flags + e, s_flags);
+}
+
+// One lane rasterises a small record over the pixels [x0, x1] x [y0, y1] of
+// its tile (origin tx0, ty0) into the warp's shared key buffer.  The record's
+// unclipped bounding box has at most kLanePx pixel centres, so its vertex
+// spans and |A|, |B| stay below 65 x 256 < 2^14.1 and every edge value at a
+// pixel centre of the box (or one step past it) below 2^30: 32-bit integers
+// hold them exactly, and their float conversions are the correctly rounded
+// ones.
+__device__ __forceinline__ void lane_raster(const TriRec& t, int x0, int x1, int y0, int y1, int tx0, int ty0,
+                                            unsigned long long* sk) {
+    const long long cx = 256LL * x0 + 128, cy = 256LL * y0 + 128;
+    int R0 = (int)((long long)t.A[0] * cx + (long long)t.B[0] * cy + t.C[0]);
+    int R1 = (int)((long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1]);
+    int R2 = (int)((long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2]);
+    const int dx0 = t.A[0] * 256, dx1 = t.A[1] * 256, dx2 = t.A[2] * 256;
+    const int dy0 = t.B[0] * 256, dy1 = t.B[1] * 256, dy2 = t.B[2] * 256;
+    const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
+    for (int py = y0; py <= y1; py++) {
+        int E0 = R0, E1 = R1, E2 = R2;
+        unsigned long long* row = sk + (py - ty0) * kTile - tx0;
+        for (int px = x0; px <= x1; px++) {
+            if ((E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) && (E2 > 0 || (E2 == 0 && tl2))) {
+                const float den =
+                    (__int2float_rn(E0) * t.iz[0] + __int2float_rn(E1) * t.iz[1]) + __int2float_rn(E2) * t.iz[2];
+                const float depth = t.af / den;
+                atomicMin(row + px, ((unsigned long long)__float_as_uint(depth) << 32) | t.id);
+            }
+            E0 += dx0;
+            E1 += dx1;
+            E2 += dx2;
+        }
+        R0 += dy0;
+        R1 += dy1;
+        R2 += dy2;
+    }
+}
+
+// Warp-wide pass of one record over the tile: the lane tests its run of nx
+// pixels (row y, columns xs ..) with 64-bit edge functions and keeps the
+// minimum keys in registers.  The record address is the same in all lanes.
+__device__ __forceinline__ void warp_pass(const TriRec* __restrict__ p, int y, int xs, int nx,
+                                          unsigned long long* key) {
+    const TriRec t = load_rec(p);
+    if (nx <= 0 || y < t.y0 || y > t.y1 || xs + nx - 1 < t.x0 || xs > t.x1) return;
+    const long long cy = 256LL * y + 128;
+    const long long cx = 256LL * xs + 128;
+    long long E0 = (long long)t.A[0] * cx + (long long)t.B[0] * cy + t.C[0];
+    long long E1 = (long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1];
+    long long E2 = (long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2];
+    const long long d0 = 256LL * t.A[0], d1 = 256LL * t.A[1], d2 = 256LL * t.A[2];
+    const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (k < nx && (E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) &&
+            (E2 > 0 || (E2 == 0 && tl2))) {
+            const float den = (i64_to_f32(E0) * t.iz[0] + i64_to_f32(E1) * t.iz[1]) + i64_to_f32(E2) * t.iz[2];
+            const float depth = t.af / den;
+            const unsigned long long kk = ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
+            key[k] = kk < key[k] ? kk : key[k];
+        }
+        E0 += d0;
+        E1 += d1;
+        E2 += d2;
+    }
+}
+
+// Work item (camera, first tile): warp w rasterises and resolves tile
+// first + w of the camera.
+__global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr,
+                                                         const int2* __restrict__ items) {
+    __shared__ unsigned long long s_key[kTW][kTile * kTile];
+    __shared__ int s_big[kTW][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int2 it = items[blockIdx.x];
+    const int cam = it.x, tile = it.y + w;
+    const int W = b.cam_w[cam], H = b.cam_h[cam];
+    const int tiles_x = (W + kTile - 1) / kTile;
+    const int ntiles = tiles_x * ((H + kTile - 1) / kTile);
+    if (tile >= ntiles) return;   // whole warp; no CTA barrier follows
+    const TriRec* __restrict__ rec = reinterpret_cast<const TriRec*>(ts.rec) + ts.rec_base[cam];
+    const uint32_t* __restrict__ wide = ts.wide + ts.rec_base[cam];
+    const uint32_t* __restrict__ ent = ts.ent + ts.ent_base[cam];
+    const int32_t* __restrict__ toff = ts.toff + ts.toff_base[cam];
+    const int tx0 = (tile % tiles_x) * kTile, ty0 = (tile / tiles_x) * kTile;
+    const int tx1 = min(tx0 + kTile, W) - 1, ty1 = min(ty0 + kTile, H) - 1;
+    // lane: row lane / 2 of the tile, columns 8 (lane % 2) .. + 7
+    const int y = ty0 + (lane >> 1), xs = tx0 + 8 * (lane & 1);
+    const int nx = y <= ty1 ? max(0, min(8, tx1 - xs + 1)) : 0;
+    unsigned long long* sk = s_key[w];
+#pragma unroll
+    for (int k = 0; k < 8; k++) sk[lane + 32 * k] = ~0ULL;
+    __syncwarp();
+    unsigned long long key[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) key[k] = ~0ULL;
+
+    const int beg = __ldg(toff + tile), end = __ldg(toff + tile + 1);
+    for (int base = beg; base < end; base += 32) {
+        const int i = base + lane;
+        bool big = false;
+        uint32_t r = 0;
+        if (i < end) {
+            r = __ldg(ent + i);
+            const TriRec t = load_rec(rec + r);
+            const int x0 = max((int)t.x0, tx0), x1 = min((int)t.x1, tx1);
+            const int y0 = max((int)t.y0, ty0), y1 = min((int)t.y1, ty1);
+            if (x0 <= x1 && y0 <= y1) {
+                if (t.tl & kSmallBit) lane_raster(t, x0, x1, y0, y1, tx0, ty0, sk);
+                else big = true;
+            }
+        }
+        const unsigned m = __ballot_sync(kFullMask, big);
+        if (big) s_big[w][__popc(m & ((1u << lane) - 1u))] = (int)r;
+        __syncwarp();
+        const int nb = __popc(m);
+        for (int q = 0; q < nb; q++) warp_pass(rec + s_big[w][q], y, xs, nx, key);
+        __syncwarp();   // s_big is reused by the next batch
+    }
+    const int nw = __ldg(toff + ntiles + 1);
+    for (int q = 0; q < nw; q++) warp_pass(rec + __ldg(wide + q), y, xs, nx, key);
+    __syncwarp();       // the lanes' shared-memory keys are complete
+
+    if (nx <= 0) return;
+    const int e = b.cam_env[cam];
+    const uint32_t* colors = b.tri_color + b.env_tri_base[e];
+    const int64_t p0 = b.cam_pix_off[cam] + (int64_t)y * W + xs;
+    const unsigned long long* sl = sk + (lane >> 1) * kTile + 8 * (lane & 1);
+    float d[8];
+    uint32_t tid[8], col[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        unsigned long long kk = sl[k];
+        kk = key[k] < kk ? key[k] : kk;
+        if (kk == ~0ULL) {
+            d[k] = 0.0f;
+            tid[k] = 0xFFFFFFFFu;
+            col[k] = 0u;
+        } else {
+            tid[k] = (uint32_t)(kk & 0xFFFFFFFFull);
+            d[k] = __uint_as_float((uint32_t)(kk >> 32));
+            col[k] = k < nx ? __ldg(colors + tid[k]) : 0u;
+        }
+    }
+    const bool vec = nx == 8 && ((reinterpret_cast<uintptr_t>(fr.depth + p0) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(fr.rgb + 3 * p0) & 3) == 0) &&
+                     (!fr.triid || (reinterpret_cast<uintptr_t>(fr.triid + p0) & 15) == 0);
+    if (vec) {
+        float4* dp = reinterpret_cast<float4*>(fr.depth + p0);
+        dp[0] = make_float4(d[0], d[1], d[2], d[3]);
+        dp[1] = make_float4(d[4], d[5], d[6], d[7]);
+        if (fr.triid) {
+            uint4* tp = reinterpret_cast<uint4*>(fr.triid + p0);
+            tp[0] = make_uint4(tid[0], tid[1], tid[2], tid[3]);
+            tp[1] = make_uint4(tid[4], tid[5], tid[6], tid[7]);
+        }
+        // 8 pixels = 24 bytes = 6 words, little endian r g b r | g b r g | b r g b | ...
+        uint32_t* r32 = reinterpret_cast<uint32_t*>(fr.rgb + 3 * p0);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint32_t c0 = col[4 * h], c1 = col[4 * h + 1], c2 = col[4 * h + 2], c3 = col[4 * h + 3];
+            r32[3 * h] = (c0 & 0xFFFFFFu) | ((c1 & 0xFFu) << 24);
+            r32[3 * h + 1] = ((c1 >> 8) & 0xFFFFu) | ((c2 & 0xFFFFu) << 16);
+            r32[3 * h + 2] = ((c2 >> 16) & 0xFFu) | ((c3 & 0xFFFFFFu) << 8);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (k < nx) {
+                fr.depth[p0 + k] = d[k];
+                if (fr.triid) fr.triid[p0 + k] = tid[k];
+                fr.rgb[3 * (p0 + k)] = col[k] & 255u;
+                fr.rgb[3 * (p0 + k) + 1] = (col[k] >> 8) & 255u;
+                fr.rgb[3 * (p0 + k) + 2] = (col[k] >> 16) & 255u;
+            }
+    }
+}
+
+}  // namespace
+
+int tiled_max_tiles() { return kMaxTiles; }
+int tiled_narrow_tiles() { return kNarrowTiles; }
+int tiled_tiles_per_item() { return kTW; }
+size_t tiled_record_bytes() { return sizeof(TriRec); }
+
+cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
+                                const int2* items, int nitems, cudaStream_t stream) {
+    if (b.C == 0) return cudaSuccess;
+    cudaError_t err = launch_shade(b, pose, stream);
+    if (err != cudaSuccess) return err;
+    bin_kernel<<<b.C, kBT, 0, stream>>>(b, pose, ts);
+    err = cudaGetLastError();
+    if (err != cudaSuccess || nitems == 0) return err;
+    tile_kernel<<<nitems, kTW * 32, 0, stream>>>(b, ts, fr, items);
+    return cudaGetLastError();
+}
+
+}  // namespace vuda

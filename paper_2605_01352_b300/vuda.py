@@ -26,6 +26,7 @@ lib = C.CDLL(LIB_PATH)
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_BUSY, ERR_UNSUPPORTED = range(8)
 FLAG_CONTACT_OVERFLOW, FLAG_NEAR_DISCARD, FLAG_GUARD_DISCARD, FLAG_MESH_CAPACITY, FLAG_TIMEOUT = 1, 2, 4, 8, 16
 COSCHED_STREAMS, COSCHED_GREEN, COSCHED_SHARED = 1, 2, 3
+RENDER_AUTO, RENDER_BAND, RENDER_TILED = 0, 1, 2
 
 vp = C.c_void_p
 
@@ -49,13 +50,13 @@ class Scene(C.Structure):
 
 class EnvOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("device", C.c_int32), ("render_band_rows", C.c_int32),
-                ("phys_smem_bytes", C.c_int32), ("persistent", C.c_int32)]
+                ("phys_smem_bytes", C.c_int32), ("persistent", C.c_int32), ("render_path", C.c_int32)]
 
 
 class EnvInfo(C.Structure):
     _fields_ = [("num_envs", C.c_int32), ("num_bodies", C.c_int32), ("num_cams", C.c_int32),
                 ("max_bodies", C.c_int32), ("num_pixels", C.c_int64), ("num_tris", C.c_int64),
-                ("device_bytes", C.c_int64), ("steps_enqueued", C.c_int64)]
+                ("device_bytes", C.c_int64), ("steps_enqueued", C.c_int64), ("render_path", C.c_int32)]
 
 
 class Frame(C.Structure):
@@ -229,7 +230,7 @@ class Env:
     """A batch of environments resident on the GPU."""
 
     def __init__(self, scene, params=None, hbm_budget_bytes: int = 0, device: int = 0, band_rows: int = 0,
-                 phys_smem_bytes: int = 0, persistent: bool = False, _handle=None):
+                 phys_smem_bytes: int = 0, persistent: bool = False, render_path: int = 0, _handle=None):
         self.scene = scene
         if _handle is not None:            # a handle owned elsewhere (a serving job)
             self.h = _handle
@@ -240,7 +241,7 @@ class Env:
         sc, keep = scene_struct(scene)
         self.params = params or scene.params
         prm = sim_params(self.params)
-        opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes, int(persistent))
+        opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes, int(persistent), render_path)
         handle = vp()
         check(lib.vuda_env_create(C.byref(sc), C.byref(prm), C.byref(opts), C.byref(handle)), "vuda_env_create")
         del keep

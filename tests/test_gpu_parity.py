@@ -57,11 +57,19 @@ def _physics_horizon(V, orc, sc, steps=10, force=None, **env_kw):
     return g
 
 
-def _render_cmp(V, orc, sc, pos=None, quat=None, env=None):
+PATHS = ["band", "tiled"]
+
+
+def _path(V, name):
+    return {"band": V.RENDER_BAND, "tiled": V.RENDER_TILED}[name]
+
+
+def _render_cmp(V, orc, sc, pos=None, quat=None, env=None, path="tiled"):
     import torch
     own = env is None
     if own:
-        env = V.Env(sc)
+        env = V.Env(sc, render_path=_path(V, path))
+        assert env.info().render_path == _path(V, path)
     pos = sc.pos if pos is None else pos
     quat = sc.quat if quat is None else quat
     env.set_pose(0, pos, quat)
@@ -131,16 +139,18 @@ def test_physics_contact_spill_to_global(V, orc):
     _physics_horizon(V, orc, sc, steps=3, phys_smem_bytes=1024)
 
 
-def test_render_cfg1(V, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_render_cfg1(V, orc, path):
     sc = S.cfg1()
     st, _, _ = orc.sim_step(sc, 50)
-    _render_cmp(V, orc, sc, st["pos"], st["quat"])
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], path=path)
 
 
-def test_render_cfg2_subset(V, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_render_cfg2_subset(V, orc, path):
     sc = S.cfg2(16)
     st, _, _ = orc.sim_step(sc, 50)
-    _render_cmp(V, orc, sc, st["pos"], st["quat"])
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], path=path)
 
 
 def test_render_mixed_resolutions_and_bands(V, orc):
@@ -149,15 +159,46 @@ def test_render_mixed_resolutions_and_bands(V, orc):
     sc = S.generate(3, np.array([6, 10, 3]), 77, kinds="mixed", res=np.array([64, 256, 128]), substeps=4)
     st, _, _ = orc.sim_step(sc, 20)
     for rows in (0, 7, 13):
-        env = V.Env(sc, band_rows=rows)
+        env = V.Env(sc, band_rows=rows, render_path=V.RENDER_BAND)
         _render_cmp(V, orc, sc, st["pos"], st["quat"], env=env)
         env.close()
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], path="tiled")
 
 
-def test_render_near_plane_flags(V, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_render_ragged_tiles(V, orc, path):
+    """Camera sizes that are not multiples of the 16-pixel tile or of the
+    8-pixel runs (partial tiles, unaligned first pixels of later cameras),
+    bodies close to the camera (large triangles) and far (small ones)."""
+    sc = S.generate(4, np.array([7, 12, 5, 9]), 303, kinds="mixed", res=np.array([40, 71, 9, 100]), substeps=4)
+    st, _, _ = orc.sim_step(sc, 30)
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], path=path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_render_near_plane_flags(V, orc, path):
     sc = S.custom([dict(type="sphere", r=0.1, pos=(0.0, -3.0, 1.5)),
                    dict(type="box", h=(0.05, 0.05, 0.05), pos=(0.1, 0.0, 0.05))], res=64)
-    _render_cmp(V, orc, sc)
+    _render_cmp(V, orc, sc, path=path)
+
+
+def test_render_paths_identical_frames_full_size(V):
+    """The band and tiled paths give identical frames, bit for bit, on the
+    1024-environment batch of 128 x 128 cameras (settled piles)."""
+    import torch
+    sc = S.cfg2()
+    out = []
+    for path in (V.RENDER_BAND, V.RENDER_TILED):
+        env = V.Env(sc, render_path=path)
+        assert env.info().render_path == path
+        ring = [env.alloc_frame(), env.alloc_frame()]
+        env.pipeline_run(40, ring)
+        torch.cuda.synchronize()
+        out.append({k: v.cpu().numpy() for k, v in ring[1].items()})
+        out[-1]["flags"] = env.status()[0]
+        env.close()
+    for k in out[0]:
+        np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
 
 
 def test_raster_screen_tris_matches_oracle(V, orc):
@@ -407,14 +448,15 @@ def test_autotune_keeps_results_and_caches(V):
     env2.close()
 
 
-def test_hull_meshes_two_cameras(V, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_hull_meshes_two_cameras(V, orc, path):
     """Convex-hull bodies (500-2000 triangles each, sphere proxies in the
     physics) seen by two cameras per environment: physics and both cameras'
     frames match the oracle."""
     import torch
     sc = S.generate(3, 64, S.config_seed(3), kinds="hulls", res=128, cams_per_env=2, substeps=8,
                     n_hull_meshes=8)
-    env = V.Env(sc)
+    env = V.Env(sc, render_path=_path(V, path))
     ring = [env.alloc_frame(), env.alloc_frame()]
     env.pipeline_run(2, ring)
     torch.cuda.synchronize()
