@@ -60,14 +60,20 @@ struct Contacts {
     }
 };
 
+// The same records when all of them are in shared memory.
+struct SmemContacts {
+    float* s;
+    __device__ __forceinline__ Rec rec(int c) const { return Rec{s + c * kCS}; }
+};
+
 // Per-env bodies in shared memory: one record of kBW words per body.  The
 // odd stride keeps 32 consecutive bodies on 32 different banks, and every
 // field sits at an immediate offset from the record base.
 enum : int {
     B_P = 0, B_Q = 3, B_V = 7, B_W = 10, B_D = 13, B_IM = 16, B_II = 17, B_BR = 20, B_R = 21, B_I = 30,
-    B_ACC = 39, B_TYPE = 45, B_NCB = 46
+    B_TYPE = 39, B_NCB = 40
 };
-constexpr int kBW = 47;
+constexpr int kBW = 41;
 
 struct Bodies {
     float* base;
@@ -83,7 +89,6 @@ struct Bodies {
     __device__ __forceinline__ float& IM(int i) const { return b(i)[B_IM]; }
     __device__ __forceinline__ float& II(int k, int i) const { return b(i)[B_II + k]; }
     __device__ __forceinline__ float& BR(int i) const { return b(i)[B_BR]; }
-    __device__ __forceinline__ float& ACC(int q, int i) const { return b(i)[B_ACC + q]; }
     __device__ __forceinline__ int& TYPE(int i) const { return reinterpret_cast<int*>(b(i))[B_TYPE]; }
     __device__ __forceinline__ int& NCB(int i) const { return reinterpret_cast<int*>(b(i))[B_NCB]; }
 };
@@ -326,6 +331,214 @@ __device__ __forceinline__ void pair_of_index(int k, int N, int& i, int& j) {
 
 // One environment for nsteps steps, by the whole CTA.  b lives in shared
 // memory (copied there by the kernels below).
+// Per-body contact lists, per-contact constants and the Jacobi iterations of
+// one substep.  CA is the contact-record accessor: shared memory only when
+// every contact of the env fits there (the common case, 32-bit shared
+// addressing), or shared then global spill.
+template <class CA>
+__device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int* qcnt, unsigned short* lists,
+                                              int* wsum, int nc, int N, int NB, const SimConst& sc, float h) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    // contacts per body, and per-body lists (contact << 1 | side) in
+    // ascending contact order
+    for (int i = tid; i < 4 * N; i += kT) qcnt[(i / N) * NB + (i % N)] = 0;
+    __syncthreads();
+    const int qlen = (nc + 3) / 4;
+    for (int c = tid; c < nc; c += kT) {
+        int a, bb;
+        unpack_ab(C.rec(c), a, bb);
+        int q = c / qlen;
+        atomicAdd(qcnt + q * NB + a, 1);
+        if (bb >= 0) atomicAdd(qcnt + q * NB + bb, 1);
+    }
+    __syncthreads();
+    {
+        int run = 0;
+        for (int i0 = 0; i0 < N; i0 += kT) {
+            int i = i0 + tid;
+            int v = 0;
+            if (i < N) v = (qcnt[i] + qcnt[NB + i]) + (qcnt[2 * NB + i] + qcnt[3 * NB + i]);
+            int tot;
+            int ex = block_excl_scan(v, wsum, tot);
+            if (i < N) {
+                S.NCB(i) = v;
+                S.loff[i] = run + ex;
+            }
+            run += tot;
+        }
+        if (tid == 0) S.loff[N] = run;
+    }
+    __syncthreads();
+    // warp q fills the entries of contacts in quarter q of the list
+    for (int i0 = 0; i0 < N; i0 += 32) {
+        int i = i0 + lane;
+        if (i < N) {
+            int o = S.loff[i];
+            for (int q = 0; q < warp; q++) o += qcnt[q * NB + i];
+            int cend = min(nc, (warp + 1) * qlen);
+            int c = warp * qlen;
+            for (; c + 4 <= cend; c += 4) {
+                int ab[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) ab[u] = __float_as_int(C.rec(c + u)[F_AB]);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    int a = ab[u] & 0xffff, bb = (ab[u] >> 16) - 1;
+                    if (a == i) lists[o++] = (unsigned short)((c + u) << 1);
+                    else if (bb == i) lists[o++] = (unsigned short)(((c + u) << 1) | 1);
+                }
+            }
+            for (; c < cend; c++) {
+                int a, bb;
+                unpack_ab(C.rec(c), a, bb);
+                if (a == i) lists[o++] = (unsigned short)(c << 1);
+                else if (bb == i) lists[o++] = (unsigned short)((c << 1) | 1);
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. per-contact constants
+    for (int c = tid; c < nc; c += kT) {
+        Rec r = C.rec(c);
+        int a, bb;
+        unpack_ab(r, a, bb);
+        f3 n = ld3(r, F_N);
+        f3 pt = ld3(r, F_RA);
+        float d = r[F_VMIN];
+        f3 rA = sub3(pt, ldpos(S, a));
+        f3 rB = bb >= 0 ? sub3(pt, ldpos(S, bb)) : f3{0.0f, 0.0f, 0.0f};
+        f3 ex = fabsf(n.x) < 0.9f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
+        f3 t = cross3(n, ex);
+        float tl = sqrtf(dot3(t, t));
+        f3 t1{t.x / tl, t.y / tl, t.z / tl};
+        f3 t2 = cross3(n, t1);
+        // inverse effective masses, once per substep
+        float kN = 1.0f / eff_mass(S, a, bb, rA, rB, n);
+        float kT1 = 1.0f / eff_mass(S, a, bb, rA, rB, t1);
+        float kT2 = 1.0f / eff_mass(S, a, bb, rA, rB, t2);
+        float vn0 = dot3(n, rel_vel(S, a, bb, rA, rB));
+        float vmin;
+        if (d >= 0.0f) {
+            vmin = -d / h;
+        } else {
+            float pen = -d - sc.slop;
+            vmin = (sc.beta * (pen > 0.0f ? pen : 0.0f)) / h;
+        }
+        if (d < 0.0f && vn0 < -sc.rest_thr) {
+            float vb = -sc.restitution * vn0;
+            if (vb > vmin) vmin = vb;
+        }
+        st3(r, F_RA, rA);
+        st3(r, F_RB, rB);
+        st3(r, F_T1, t1);
+        st3(r, F_T2, t2);
+        r[F_KN] = kN; r[F_KT1] = kT1; r[F_KT2] = kT2;
+        r[F_VMIN] = vmin;
+        r[F_LN] = 0.0f; r[F_LT1] = 0.0f; r[F_LT2] = 0.0f;
+    }
+    __syncthreads();
+
+    // 4. Jacobi iterations
+    for (int it = 0; it < sc.iterations; it++) {
+        for (int c = tid; c < nc; c += kT) {
+            Rec r = C.rec(c);
+            int a, bb;
+            unpack_ab(r, a, bb);
+            f3 n = ld3(r, F_N), t1 = ld3(r, F_T1), t2 = ld3(r, F_T2);
+            f3 rA = ld3(r, F_RA), rB = ld3(r, F_RB);
+            f3 vr = rel_vel(S, a, bb, rA, rB);
+            float vn = dot3(n, vr);
+            float ln = r[F_LN];
+            float dl = (r[F_VMIN] - vn) * r[F_KN];
+            float lnew = ln + dl;
+            if (!(lnew > 0.0f)) lnew = 0.0f;
+            float dln = lnew - ln;
+            r[F_LN] = lnew;
+            float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
+            float l1 = r[F_LT1], l2 = r[F_LT2];
+            float a1 = l1 - vt1 * r[F_KT1];
+            float a2 = l2 - vt2 * r[F_KT2];
+            float lim = sc.mu * lnew;
+            float m2 = a1 * a1 + a2 * a2;
+            if (m2 > lim * lim) {
+                float s = lim / sqrtf(m2);
+                a1 = a1 * s;
+                a2 = a2 * s;
+            }
+            float dl1 = a1 - l1, dl2 = a2 - l2;
+            r[F_LT1] = a1;
+            r[F_LT2] = a2;
+            f3 P{(dln * n.x + dl1 * t1.x) + dl2 * t2.x, (dln * n.y + dl1 * t1.y) + dl2 * t2.y,
+                 (dln * n.z + dl1 * t1.z) + dl2 * t2.z};
+            st3(r, F_P, P);
+            st3(r, F_LA, cross3(rA, P));
+            if (bb >= 0) st3(r, F_LB, cross3(rB, P));
+        }
+        __syncthreads();
+        // per-body sums in ascending contact order, applied at once: unit u
+        // is body (u / 64) * 32 + u % 32 and half (u / 32) % 2 -- the impulse
+        // sum and linear velocity (0), or the moment sum and angular
+        // velocity (1); consecutive lanes take consecutive bodies.  The B
+        // side of a contact enters with the opposite sign.
+        for (int u = tid; u < 2 * ((N + 31) & ~31); u += kT) {
+            const int half = (u >> 5) & 1;
+            const int i = ((u >> 6) << 5) + (u & 31);
+            if (i >= N) continue;
+            auto load = [&](int ent, float& x, float& y, float& z) {
+                Rec r = C.rec(ent >> 1);
+                const bool side = ent & 1;
+                const int f = half == 0 ? F_P : (side ? F_LB : F_LA);
+                x = r[f];
+                y = r[f + 1];
+                z = r[f + 2];
+                if (side) {
+                    x = -x;
+                    y = -y;
+                    z = -z;
+                }
+            };
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+            const int k1 = S.loff[i + 1];
+            int k = S.loff[i];
+            // loads of four entries are independent: issue them together,
+            // then add in list order
+            for (; k + 4 <= k1; k += 4) {
+                float x[4], y[4], z[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) load(lists[k + q], x[q], y[q], z[q]);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    s0 = s0 + x[q];
+                    s1 = s1 + y[q];
+                    s2 = s2 + z[q];
+                }
+            }
+            for (; k < k1; k++) {
+                float x, y, z;
+                load(lists[k], x, y, z);
+                s0 = s0 + x;
+                s1 = s1 + y;
+                s2 = s2 + z;
+            }
+            if (half == 0) {
+                const float im = S.IM(i);
+                S.V(0, i) = S.V(0, i) + sc.omega * (im * s0);
+                S.V(1, i) = S.V(1, i) + sc.omega * (im * s1);
+                S.V(2, i) = S.V(2, i) + sc.omega * (im * s2);
+            } else {
+                const f3 dw = imul(S, i, f3{s0, s1, s2});
+                S.W(0, i) = S.W(0, i) + sc.omega * dw.x;
+                S.W(1, i) = S.W(1, i) + sc.omega * dw.y;
+                S.W(2, i) = S.W(2, i) + sc.omega * dw.z;
+            }
+        }
+        __syncthreads();
+    }
+
+}
+
 __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, const float* __restrict__ force, int slot0,
                                      int smem_per_env, int NB) {
     const SimConst& sc = b.sc;
@@ -534,207 +747,8 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
             }
             if (nc > cmax) nc = cmax;
 
-            // contacts per body, and per-body lists (contact << 1 | side) in
-            // ascending contact order
-            for (int i = tid; i < 4 * N; i += kT) qcnt[(i / N) * NB + (i % N)] = 0;
-            __syncthreads();
-            const int qlen = (nc + 3) / 4;
-            for (int c = tid; c < nc; c += kT) {
-                int a, bb;
-                unpack_ab(C.rec(c), a, bb);
-                int q = c / qlen;
-                atomicAdd(qcnt + q * NB + a, 1);
-                if (bb >= 0) atomicAdd(qcnt + q * NB + bb, 1);
-            }
-            __syncthreads();
-            {
-                int run = 0;
-                for (int i0 = 0; i0 < N; i0 += kT) {
-                    int i = i0 + tid;
-                    int v = 0;
-                    if (i < N) v = (qcnt[i] + qcnt[NB + i]) + (qcnt[2 * NB + i] + qcnt[3 * NB + i]);
-                    int tot;
-                    int ex = block_excl_scan(v, wsum, tot);
-                    if (i < N) {
-                        S.NCB(i) = v;
-                        S.loff[i] = run + ex;
-                    }
-                    run += tot;
-                }
-                if (tid == 0) S.loff[N] = run;
-            }
-            __syncthreads();
-            // warp q fills the entries of contacts in quarter q of the list
-            for (int i0 = 0; i0 < N; i0 += 32) {
-                int i = i0 + lane;
-                if (i < N) {
-                    int o = S.loff[i];
-                    for (int q = 0; q < warp; q++) o += qcnt[q * NB + i];
-                    int cend = min(nc, (warp + 1) * qlen);
-                    int c = warp * qlen;
-                    for (; c + 4 <= cend; c += 4) {
-                        int ab[4];
-#pragma unroll
-                        for (int u = 0; u < 4; u++) ab[u] = __float_as_int(C.rec(c + u)[F_AB]);
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            int a = ab[u] & 0xffff, bb = (ab[u] >> 16) - 1;
-                            if (a == i) lists[o++] = (unsigned short)((c + u) << 1);
-                            else if (bb == i) lists[o++] = (unsigned short)(((c + u) << 1) | 1);
-                        }
-                    }
-                    for (; c < cend; c++) {
-                        int a, bb;
-                        unpack_ab(C.rec(c), a, bb);
-                        if (a == i) lists[o++] = (unsigned short)(c << 1);
-                        else if (bb == i) lists[o++] = (unsigned short)((c << 1) | 1);
-                    }
-                }
-            }
-            __syncthreads();
-
-            // 3. per-contact constants
-            for (int c = tid; c < nc; c += kT) {
-                Rec r = C.rec(c);
-                int a, bb;
-                unpack_ab(r, a, bb);
-                f3 n = ld3(r, F_N);
-                f3 pt = ld3(r, F_RA);
-                float d = r[F_VMIN];
-                f3 rA = sub3(pt, ldpos(S, a));
-                f3 rB = bb >= 0 ? sub3(pt, ldpos(S, bb)) : f3{0.0f, 0.0f, 0.0f};
-                f3 ex = fabsf(n.x) < 0.9f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
-                f3 t = cross3(n, ex);
-                float tl = sqrtf(dot3(t, t));
-                f3 t1{t.x / tl, t.y / tl, t.z / tl};
-                f3 t2 = cross3(n, t1);
-                // inverse effective masses, once per substep
-                float kN = 1.0f / eff_mass(S, a, bb, rA, rB, n);
-                float kT1 = 1.0f / eff_mass(S, a, bb, rA, rB, t1);
-                float kT2 = 1.0f / eff_mass(S, a, bb, rA, rB, t2);
-                float vn0 = dot3(n, rel_vel(S, a, bb, rA, rB));
-                float vmin;
-                if (d >= 0.0f) {
-                    vmin = -d / h;
-                } else {
-                    float pen = -d - sc.slop;
-                    vmin = (sc.beta * (pen > 0.0f ? pen : 0.0f)) / h;
-                }
-                if (d < 0.0f && vn0 < -sc.rest_thr) {
-                    float vb = -sc.restitution * vn0;
-                    if (vb > vmin) vmin = vb;
-                }
-                st3(r, F_RA, rA);
-                st3(r, F_RB, rB);
-                st3(r, F_T1, t1);
-                st3(r, F_T2, t2);
-                r[F_KN] = kN; r[F_KT1] = kT1; r[F_KT2] = kT2;
-                r[F_VMIN] = vmin;
-                r[F_LN] = 0.0f; r[F_LT1] = 0.0f; r[F_LT2] = 0.0f;
-            }
-            __syncthreads();
-
-            // 4. Jacobi iterations
-            for (int it = 0; it < sc.iterations; it++) {
-                for (int c = tid; c < nc; c += kT) {
-                    Rec r = C.rec(c);
-                    int a, bb;
-                    unpack_ab(r, a, bb);
-                    f3 n = ld3(r, F_N), t1 = ld3(r, F_T1), t2 = ld3(r, F_T2);
-                    f3 rA = ld3(r, F_RA), rB = ld3(r, F_RB);
-                    f3 vr = rel_vel(S, a, bb, rA, rB);
-                    float vn = dot3(n, vr);
-                    float ln = r[F_LN];
-                    float dl = (r[F_VMIN] - vn) * r[F_KN];
-                    float lnew = ln + dl;
-                    if (!(lnew > 0.0f)) lnew = 0.0f;
-                    float dln = lnew - ln;
-                    r[F_LN] = lnew;
-                    float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
-                    float l1 = r[F_LT1], l2 = r[F_LT2];
-                    float a1 = l1 - vt1 * r[F_KT1];
-                    float a2 = l2 - vt2 * r[F_KT2];
-                    float lim = sc.mu * lnew;
-                    float m2 = a1 * a1 + a2 * a2;
-                    if (m2 > lim * lim) {
-                        float s = lim / sqrtf(m2);
-                        a1 = a1 * s;
-                        a2 = a2 * s;
-                    }
-                    float dl1 = a1 - l1, dl2 = a2 - l2;
-                    r[F_LT1] = a1;
-                    r[F_LT2] = a2;
-                    f3 P{(dln * n.x + dl1 * t1.x) + dl2 * t2.x, (dln * n.y + dl1 * t1.y) + dl2 * t2.y,
-                         (dln * n.z + dl1 * t1.z) + dl2 * t2.z};
-                    st3(r, F_P, P);
-                    st3(r, F_LA, cross3(rA, P));
-                    if (bb >= 0) st3(r, F_LB, cross3(rB, P));
-                }
-                __syncthreads();
-                // per-body sums in ascending contact order; the six components
-                // are independent sums, two per thread, in warps 0..2
-                if (warp < 3) {
-                    const int q0 = 2 * warp;
-                    // component q of an entry: 0..2 impulse, 3..5 its moment about
-                    // the body; the B side enters with the opposite sign
-                    auto load = [&](int ent, float& a, float& bv) {
-                        Rec r = C.rec(ent >> 1);
-                        const bool side = ent & 1;
-                        const int fl = side ? F_LB : F_LA;
-                        const int f0 = q0 < 3 ? F_P + q0 : fl + q0 - 3;
-                        const int f1 = q0 + 1 < 3 ? F_P + q0 + 1 : fl + q0 - 2;
-                        a = r[f0];
-                        bv = r[f1];
-                        if (side) {
-                            a = -a;
-                            bv = -bv;
-                        }
-                    };
-                    for (int i0 = 0; i0 < N; i0 += 32) {
-                        int i = i0 + lane;
-                        if (i < N) {
-                            float s0 = 0.0f, s1 = 0.0f;
-                            const int k1 = S.loff[i + 1];
-                            int k = S.loff[i];
-                            // loads of four entries are independent: issue them
-                            // together, then add in list order
-                            for (; k + 4 <= k1; k += 4) {
-                                float a0, b0, a1, b1, a2, b2, a3, b3;
-                                load(lists[k], a0, b0);
-                                load(lists[k + 1], a1, b1);
-                                load(lists[k + 2], a2, b2);
-                                load(lists[k + 3], a3, b3);
-                                s0 = s0 + a0; s1 = s1 + b0;
-                                s0 = s0 + a1; s1 = s1 + b1;
-                                s0 = s0 + a2; s1 = s1 + b2;
-                                s0 = s0 + a3; s1 = s1 + b3;
-                            }
-                            for (; k < k1; k++) {
-                                float a0, b0;
-                                load(lists[k], a0, b0);
-                                s0 = s0 + a0;
-                                s1 = s1 + b0;
-                            }
-                            S.ACC(q0, i) = s0;
-                            S.ACC(q0 + 1, i) = s1;
-                        }
-                    }
-                }
-                __syncthreads();
-                for (int i = tid; i < N; i += kT) {
-                    f3 sp{S.ACC(0, i), S.ACC(1, i), S.ACC(2, i)};
-                    f3 sl{S.ACC(3, i), S.ACC(4, i), S.ACC(5, i)};
-                    f3 dw = imul(S, i, sl);
-                    float im = S.IM(i);
-                    S.V(0, i) = S.V(0, i) + sc.omega * (im * sp.x);
-                    S.V(1, i) = S.V(1, i) + sc.omega * (im * sp.y);
-                    S.V(2, i) = S.V(2, i) + sc.omega * (im * sp.z);
-                    S.W(0, i) = S.W(0, i) + sc.omega * dw.x;
-                    S.W(1, i) = S.W(1, i) + sc.omega * dw.y;
-                    S.W(2, i) = S.W(2, i) + sc.omega * dw.z;
-                }
-                __syncthreads();
-            }
+            if (nc <= C.cap) solve_substep(SmemContacts{C.s}, S, qcnt, lists, wsum, nc, N, NB, sc, h);
+            else solve_substep(C, S, qcnt, lists, wsum, nc, N, NB, sc, h);
 
             // 5. positions and orientations
             const float hh = 0.5f * h;
