@@ -140,7 +140,7 @@ __device__ __forceinline__ void put_contact(const Contacts& C, int c, int a, int
 }
 
 // Sphere s against box x: normal from the box to the sphere, point on the box, distance.
-__device__ void sphere_box(const Bodies& B, int s, int x, f3& n, f3& pt, float& d) {
+__device__ __forceinline__ void sphere_box(const Bodies& B, int s, int x, f3& n, f3& pt, float& d) {
     f3 ps = ldpos(B, s), px = ldpos(B, x);
     float h[3] = {B.D(0, x), B.D(1, x), B.D(2, x)};
     float r = B.D(0, s);
@@ -158,15 +158,21 @@ __device__ void sphere_box(const Bodies& B, int s, int x, f3& n, f3& pt, float& 
         float pen[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) pen[k] = h[k] - fabsf(l[k]);
-        int m = 0;
-        if (pen[1] < pen[m]) m = 1;
-        if (pen[2] < pen[m]) m = 2;
-        float sg = l[m] >= 0.0f ? 1.0f : -1.0f;
-        nl[0] = nl[1] = nl[2] = 0.0f;
-        nl[m] = sg;
-        d = -pen[m] - r;
-        pl[0] = l[0]; pl[1] = l[1]; pl[2] = l[2];
-        pl[m] = sg * h[m];
+        // axis of least penetration (lowest index on ties), selected without
+        // indexing the arrays by it, so that they stay in registers
+        const bool m1 = pen[1] < pen[0];
+        const float pm01 = m1 ? pen[1] : pen[0];
+        const bool m2 = pen[2] < pm01;
+        const int m = m2 ? 2 : (m1 ? 1 : 0);
+        const float penm = m2 ? pen[2] : pm01;
+        const float lm = m2 ? l[2] : (m1 ? l[1] : l[0]);
+        float sg = lm >= 0.0f ? 1.0f : -1.0f;
+        d = -penm - r;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            nl[k] = k == m ? sg : 0.0f;
+            pl[k] = k == m ? sg * h[k] : l[k];
+        }
     }
     n = rmul(B, x, f3{nl[0], nl[1], nl[2]});
     pt = add3(rmul(B, x, f3{pl[0], pl[1], pl[2]}), px);
@@ -181,12 +187,16 @@ __device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int
     float pen[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) pen[j] = B.D(j, b) - fabsf(l[j]);
-    int m = 0;
-    if (pen[1] < pen[m]) m = 1;
-    if (pen[2] < pen[m]) m = 2;
-    d = -pen[m];
+    // axis of least penetration (lowest index on ties), selected without
+    // indexing the arrays by it
+    const bool m1 = pen[1] < pen[0];
+    const float pm01 = m1 ? pen[1] : pen[0];
+    const bool m2 = pen[2] < pm01;
+    const int m = m2 ? 2 : (m1 ? 1 : 0);
+    d = -(m2 ? pen[2] : pm01);
     if (!(d < margin)) return false;
-    float sg = l[m] >= 0.0f ? 1.0f : -1.0f;
+    const float lm = m2 ? l[2] : (m1 ? l[1] : l[0]);
+    float sg = lm >= 0.0f ? 1.0f : -1.0f;
     nB = f3{sg * B.Rm(m, b), sg * B.Rm(3 + m, b), sg * B.Rm(6 + m, b)};  // column m of R_b
     return true;
 }
@@ -194,7 +204,7 @@ __device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int
 __device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.TYPE(i) == kShapeBox; }
 
 constexpr int kT = 128;          // threads per environment (one CTA)
-constexpr int kPairChunk = 256;  // candidate pairs per round of the pair phase
+constexpr int kPairChunk = 512;  // candidate pairs per round of the pair phase
 
 __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margin) {
     f3 dx = sub3(ldpos(B, i), ldpos(B, j));
@@ -206,7 +216,7 @@ __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margi
 // One narrow-phase test of pair (i, j): sub 0 for sphere-sphere and
 // sphere-box; for box-box sub 0..7 tests A's corner sub inside B and
 // sub 8..15 tests B's corner sub-8 inside A.
-__device__ bool pair_test(const Bodies& B, int i, int j, int sub, float margin, f3& n, f3& pt, float& d) {
+__device__ __forceinline__ bool pair_test(const Bodies& B, int i, int j, int sub, float margin, f3& n, f3& pt, float& d) {
     bool bi = is_box(B, i), bj = is_box(B, j);
     if (!bi && !bj) {
         f3 pa = ldpos(B, i), pb = ldpos(B, j);
@@ -245,10 +255,22 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return x;
 }
 
+// Shared scratch of the CTA-wide scans: two halves of kT/32 ints used by
+// consecutive scans in turn.  A scan needs one barrier (between the warps'
+// writes and everyone's reads): a thread writes a half again only two scans
+// later, after passing the barrier of the scan in between, which every
+// reader of the half reaches only after its reads.
+struct ScanBuf {
+    int* w;     // [2][kT / 32]
+    int k;      // scans so far (the same in every thread)
+};
+
 // Exclusive prefix sum over the CTA's kT threads in thread order.  Must be
-// called by all threads.  wsum: kT/32 ints of shared scratch.
-__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
+// called by all threads, in the same sequence of scans.
+__device__ __forceinline__ int block_excl_scan(int v, ScanBuf& sb, int& total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int* wsum = sb.w + (sb.k & 1) * (kT / 32);
+    sb.k++;
     int x = warp_incl_scan(v, lane);
     if (lane == 31) wsum[w] = x;
     __syncthreads();
@@ -260,7 +282,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
         if (k < w) off += s;
         total += s;
     }
-    __syncthreads();
     return off + x - v;
 }
 
@@ -337,7 +358,7 @@ __device__ __forceinline__ void pair_of_index(int k, int N, int& i, int& j) {
 // addressing), or shared then global spill.
 template <class CA>
 __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int* qcnt, unsigned short* lists,
-                                              int* wsum, int nc, int N, int NB, const SimConst& sc, float h) {
+                                              ScanBuf& wsum, int nc, int N, int NB, const SimConst& sc, float h) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     // contacts per body, and per-body lists (contact << 1 | side) in
@@ -559,7 +580,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     int* qcnt = ip; ip += 4 * NB;        // [4][NB] contacts of each body in each quarter of the list
     int* plist = ip; ip += kPairChunk;   // units (passing pairs or plane bodies) of the current round
     int* pitem = ip; ip += kPairChunk;   // first narrow-phase item of each unit
-    int* wsum = ip; ip += 8;
+    ScanBuf wsum{ip, 0}; ip += 2 * (kT / 32);
     unsigned short* lists = reinterpret_cast<unsigned short*>(ip);
     const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
     Contacts C;
