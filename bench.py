@@ -256,16 +256,27 @@ def sim_flops(contacts: float, bodies: int, substeps: int, iterations: int) -> f
     return per_sub * substeps
 
 
-def kernel_traffic(kind: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+def csrc_sha() -> str:
+    """Hash of every CUDA source of the library (a change anywhere
+    invalidates the committed counters)."""
+    d = os.path.join(ROOT, "paper_2605_01352_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))[kind]
-        src = os.path.join(ROOT, "paper_2605_01352_b300", "csrc", rec["source"])
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+        rec = json.load(open(path))
+        if rec.get("csrc_sha256") != csrc_sha():
             return None
-        return float(rec["bytes_per_launch"]) * float(rec.get("scale", 1.0))
+        return float(rec["kernels"][kernel]["bytes_per_launch"])
     except Exception:
         return None
 
@@ -295,6 +306,8 @@ def main():
     E = args.envs
     sc = S.cfg2(E, env_base=rank * E)
     env = V.Env(sc)
+    env_info_path = env.info().render_path
+    launches_per_step = 4 if env_info_path == V.RENDER_TILED else 3
     ring = [env.alloc_frame(triid=False), env.alloc_frame(triid=False)]
     P = env.P
     bytes_out = P * 7                                  # RGB8 + f32 depth
@@ -331,33 +344,42 @@ def main():
                               {"sim": Ts, "render": Tr}}), flush=True)
         env.close()
         return
-    # co-scheduled: disjoint SM partitions (green contexts)
+    # co-scheduled: disjoint SM partitions (green contexts) at the fixed 50/50 split
     cos = env.coschedule(V.COSCHED_GREEN, args.sim_sms)
     env.pipeline_run(args.warmup, ring)
-    t_co, tm_co, wall_co = timed(args.steps)
-    lat = tm_co["step_ms"]
-    lat = lat[np.isfinite(lat)]
-
-    # co-scheduled on two plain streams sharing all SMs (context)
+    t_gr, tm_gr, wall_gr = timed(args.steps)
+    # co-scheduled on two plain streams sharing all SMs
     env.coschedule(V.COSCHED_STREAMS)
     env.pipeline_run(args.warmup, ring)
-    t_st, _, _ = timed(args.steps)
-    # the same, replayed from a captured CUDA graph of 8 pipelined steps
+    t_st, tm_st, wall_st = timed(args.steps)
+    # the better of the two, replayed from a captured CUDA graph of 8 pipelined steps
+    best_mode = V.COSCHED_STREAMS if t_st <= t_gr else V.COSCHED_GREEN
     t_graph = None
     try:
+        env.coschedule(best_mode, args.sim_sms)
         env.pipeline_capture(8, ring)
         env.pipeline_run(8, ring)
         t_graph, _, _ = timed(args.steps - args.steps % 8)
         t_graph = t_graph * args.steps / (args.steps - args.steps % 8)
     except Exception as ex:  # report why, keep the main line
         t_graph = repr(ex)
+    # headline: the fastest co-scheduled configuration measured above
+    cands = [("green_50_50", t_gr, tm_gr, wall_gr), ("streams_shared_sms", t_st, tm_st, wall_st)]
+    if isinstance(t_graph, float):
+        cands.append(("%s_graph8" % ("streams_shared_sms" if best_mode == V.COSCHED_STREAMS else "green_50_50"),
+                      t_graph, None, None))
+    head = min(cands, key=lambda c: c[1])
+    t_co, wall_co = head[1], head[3]
+    tm_lat = head[2] if head[2] is not None else (tm_st if best_mode == V.COSCHED_STREAMS else tm_gr)
+    lat = tm_lat["step_ms"]
+    lat = lat[np.isfinite(lat)]
     # the autotuner's own choice (band height, co-scheduling mode and split, graph)
     try:
         tuned = env.autotune(ring, steps=6, use_cache=False)
         tuned["env_steps_per_s"] = ws * E * 1000.0 / tuned["ms_per_step"]
     except Exception as ex:  # report why, keep the main line
         tuned = {"error": repr(ex)}
-    env.coschedule(V.COSCHED_GREEN, args.sim_sms)
+    env.coschedule(V.COSCHED_STREAMS)
 
     # end to end through the host-buffer loop: forces in, frames out
     e2e = None
@@ -390,29 +412,31 @@ def main():
         env.close()
         return
 
-    dom = "render" if Tr >= Ts else "sim"
     v_co = ws * E * args.steps / t_co
     v_ser = ws * E * args.steps / t_ser
     v_st = ws * E * args.steps / t_st
-    # dominant kernel by share of the serialized step
+    v_gr = ws * E * args.steps / t_gr
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = sm_count * 128 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12   # TFLOP/s, one op per lane
-    if dom == "render":
-        alg = bytes_out + bytes_pose
-        ach = alg / (Tr / 1000.0) / 1e9
-        roof = {"kernel": "render_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": kernel_traffic("render"),
-                "algorithmic_bytes_per_launch": alg, "launch_ms": Tr,
+    # physics: plain FP32 arithmetic (no FMA contraction), bound by the FP32 lanes
+    flops = sim_flops(env_stats["contacts_mean"], env_stats["bodies"], env_stats["substeps"],
+                      env_stats["iterations"]) * E
+    ach = flops / (Ts / 1000.0) / 1e12
+    roof_sim = {"kernel": "sim_kernel", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": kernel_traffic("sim_kernel"),
+                "algorithmic_flops_per_launch": flops, "launch_ms": Ts,
+                "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock (unfused ops; the path is built "
+                               "without FMA contraction)",
+                "hbm_bytes_per_launch": bytes_state, "hbm_achieved_gbs": bytes_state / (Ts / 1000.0) / 1e9}
+    # renderer: the frame it must write and the poses it reads, over the render phase
+    alg = bytes_out + bytes_pose
+    ach_r = alg / (Tr / 1000.0) / 1e9
+    roof_ren = {"kernel": "tile_kernel (+ shade_kernel, bin_kernel: the render phase)", "bound": "hbm",
+                "achieved": ach_r, "peak": hbm_peak, "unit": "GB/s", "frac": ach_r / hbm_peak,
+                "traffic": kernel_traffic("tile_kernel"), "algorithmic_bytes_per_launch": alg, "launch_ms": Tr,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
-    else:
-        flops = sim_flops(env_stats["contacts_mean"], env_stats["bodies"], env_stats["substeps"],
-                          env_stats["iterations"]) * E
-        ach = flops / (Ts / 1000.0) / 1e12
-        roof = {"kernel": "sim_kernel", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": kernel_traffic("sim"), "algorithmic_flops_per_launch": flops,
-                "launch_ms": Ts, "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock (unfused ops; the "
-                "path is built without FMA contraction)", "hbm_bytes_per_launch": bytes_state,
-                "hbm_achieved_gbs": bytes_state / (Ts / 1000.0) / 1e9}
+    roof = roof_sim if Ts >= Tr else roof_ren
+    roof_other = roof_ren if Ts >= Tr else roof_sim
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         try:
@@ -425,22 +449,26 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "envs_per_gpu": E, "bodies_per_env": 32, "substeps": 8,
                    "iterations": 8, "camera": "128x128 RGB8 + f32 depth", "parallelism": "replicas" if ws > 1
-                   else "single GPU", "sm_split": cos,
+                   else "single GPU", "render_path": "tiled" if env_info_path == V.RENDER_TILED else "band",
                    "l2": "per-step working set (frames 2 x %.0f MB) exceeds the 126 MB L2" % (bytes_out / 1e6)},
+        "coscheduled_mode": head[0],
         "serialized": {"value": v_ser, "ms_per_step": 1000.0 * t_ser / args.steps},
+        "coscheduled_green_50_50": {"value": v_gr, "ms_per_step": 1000.0 * t_gr / args.steps, "partition": cos},
         "coscheduled_streams_shared_sms": {"value": v_st, "ms_per_step": 1000.0 * t_st / args.steps},
+        "coscheduled_graph8": ({"value": ws * E * args.steps / t_graph, "ms_per_step": 1000.0 * t_graph / args.steps,
+                                "mode": "streams" if best_mode == V.COSCHED_STREAMS else "green_50_50"}
+                               if isinstance(t_graph, float) else {"error": t_graph}),
         "autotuned": tuned,
-        "coscheduled_streams_graph": ({"value": ws * E * args.steps / t_graph, "ms_per_step": 1000.0 * t_graph / args.steps}
-                                      if isinstance(t_graph, float) else {"error": t_graph}),
         "speedup_vs_serialized": v_co / v_ser,
         "phase_ms": {"sim": Ts, "render": Tr, "ideal_overlap": (Ts + Tr) / max(Ts, Tr)},
         "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
                        "p99": float(np.percentile(lat, 99)) if lat.size else None},
         "e2e": e2e,
         "roofline": roof,
+        "roofline_other_phase": roof_other,
         "cpu_baseline": cpu,
         "serving": serving,
-        "gpu_launches": 3 * args.steps,   # sim_kernel, shade_kernel, render_kernel per step
+        "gpu_launches": launches_per_step * args.steps,   # per step: sim_kernel, then shade/bin/tile or shade/band kernels
         "status_flags": flags,
         "clocks": clk.summary(),
         "wall_s_coscheduled": wall_co,

@@ -565,7 +565,6 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     const SimConst& sc = b.sc;
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
     const int b0 = b.body_off[e];
     const int N = b.body_off[e + 1] - b0;
     const int B = b.B;
