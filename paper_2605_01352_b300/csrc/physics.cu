@@ -230,18 +230,20 @@ __device__ __forceinline__ bool pair_test(const Bodies& B, int i, int j, int sub
         pt = f3{pa.x - n.x * ra, pa.y - n.y * ra, pa.z - n.z * ra};
         return d < margin;
     }
-    if (!bi && bj) {
-        sphere_box(B, i, j, n, pt, d);
-        return d < margin;
+    // one call site per test (the narrow phase is inlined): the box of a
+    // sphere-box pair, or the box whose corner is tested, given explicitly;
+    // the normal always points from j to i
+    bool flip;
+    bool hit;
+    if (!bi || !bj) {
+        flip = bi;   // box i, sphere j: the test gives the normal from i to j
+        sphere_box(B, bi ? j : i, bi ? i : j, n, pt, d);
+        hit = d < margin;
+    } else {
+        flip = sub >= 8;   // B's corner inside A: the normal from i to j
+        hit = corner_in_box(B, flip ? j : i, flip ? i : j, sub & 7, margin, pt, n, d);
     }
-    if (bi && !bj) {
-        sphere_box(B, j, i, n, pt, d);
-        n = f3{-n.x, -n.y, -n.z};
-        return d < margin;
-    }
-    if (sub < 8) return corner_in_box(B, i, j, sub, margin, pt, n, d);
-    bool hit = corner_in_box(B, j, i, sub - 8, margin, pt, n, d);
-    n = f3{-n.x, -n.y, -n.z};
+    if (flip) n = f3{-n.x, -n.y, -n.z};
     return hit;
 }
 

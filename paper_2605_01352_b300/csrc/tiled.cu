@@ -379,23 +379,25 @@ __global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScrat
     const bool vec = nx == 8 && ((reinterpret_cast<uintptr_t>(fr.depth + p0) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(fr.rgb + 3 * p0) & 3) == 0) &&
                      (!fr.triid || (reinterpret_cast<uintptr_t>(fr.triid + p0) & 15) == 0);
+    // the frame is not read again on the device: streaming (evict-first)
+    // stores keep the L2 for the triangle records still to be read
     if (vec) {
         float4* dp = reinterpret_cast<float4*>(fr.depth + p0);
-        dp[0] = make_float4(d[0], d[1], d[2], d[3]);
-        dp[1] = make_float4(d[4], d[5], d[6], d[7]);
+        __stcs(dp, make_float4(d[0], d[1], d[2], d[3]));
+        __stcs(dp + 1, make_float4(d[4], d[5], d[6], d[7]));
         if (fr.triid) {
             uint4* tp = reinterpret_cast<uint4*>(fr.triid + p0);
-            tp[0] = make_uint4(tid[0], tid[1], tid[2], tid[3]);
-            tp[1] = make_uint4(tid[4], tid[5], tid[6], tid[7]);
+            __stcs(tp, make_uint4(tid[0], tid[1], tid[2], tid[3]));
+            __stcs(tp + 1, make_uint4(tid[4], tid[5], tid[6], tid[7]));
         }
         // 8 pixels = 24 bytes = 6 words, little endian r g b r | g b r g | b r g b | ...
-        uint32_t* r32 = reinterpret_cast<uint32_t*>(fr.rgb + 3 * p0);
+        unsigned int* r32 = reinterpret_cast<unsigned int*>(fr.rgb + 3 * p0);
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const uint32_t c0 = col[4 * h], c1 = col[4 * h + 1], c2 = col[4 * h + 2], c3 = col[4 * h + 3];
-            r32[3 * h] = (c0 & 0xFFFFFFu) | ((c1 & 0xFFu) << 24);
-            r32[3 * h + 1] = ((c1 >> 8) & 0xFFFFu) | ((c2 & 0xFFFFu) << 16);
-            r32[3 * h + 2] = ((c2 >> 16) & 0xFFu) | ((c3 & 0xFFFFFFu) << 8);
+            __stcs(r32 + 3 * h, (c0 & 0xFFFFFFu) | ((c1 & 0xFFu) << 24));
+            __stcs(r32 + 3 * h + 1, ((c1 >> 8) & 0xFFFFu) | ((c2 & 0xFFFFu) << 16));
+            __stcs(r32 + 3 * h + 2, ((c2 >> 16) & 0xFFu) | ((c3 & 0xFFFFFFu) << 8));
         }
     } else {
 #pragma unroll
