@@ -365,13 +365,13 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
     const int lane = tid & 31, warp = tid >> 5;
     // contacts per body, and per-body lists (contact << 1 | side) in
     // ascending contact order
-    for (int i = tid; i < 4 * N; i += kT) qcnt[(i / N) * NB + (i % N)] = 0;
+    for (int i = tid; i < 4 * NB; i += kT) qcnt[i] = 0;
     __syncthreads();
     const int qlen = (nc + 3) / 4;
     for (int c = tid; c < nc; c += kT) {
         int a, bb;
         unpack_ab(C.rec(c), a, bb);
-        int q = c / qlen;
+        const int q = (c >= qlen) + (c >= 2 * qlen) + (c >= 3 * qlen);   // c / qlen, c < 4 qlen
         atomicAdd(qcnt + q * NB + a, 1);
         if (bb >= 0) atomicAdd(qcnt + q * NB + bb, 1);
     }
