@@ -561,21 +561,38 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         return invalid("render_path must be VUDA_RENDER_AUTO, _BAND or _TILED");
     }
     std::vector<int64_t> rec_base(C + 1, 0), ent_base(C + 1, 0), toff_base(C + 1, 0);
-    std::vector<int2> titems;
+    std::vector<TileItem> tcams(C), titems;
     bool can_tile = C > 0;
     const int tpi = tiled_tiles_per_item();
     for (int c = 0; c < C; c++) {
         const int e = cam_env[c];
         const int64_t tc = env_tri_base[e + 1] - env_tri_base[e];
-        const int ntl = ((sc->cam_w[c] + 15) / 16) * ((sc->cam_h[c] + 15) / 16);
+        const int tx = (sc->cam_w[c] + 15) / 16;
+        const int ntl = tx * ((sc->cam_h[c] + 15) / 16);
         if (ntl > tiled_max_tiles()) can_tile = false;
         rec_base[c + 1] = rec_base[c] + tc;
         ent_base[c + 1] = ent_base[c] + tc * tiled_narrow_tiles();
         toff_base[c + 1] = toff_base[c] + ntl + 2;
-        for (int t0 = 0; t0 < ntl; t0 += tpi) titems.push_back(make_int2(c, t0));
+        TileItem ti{};
+        ti.cam = c;
+        ti.W = sc->cam_w[c];
+        ti.H = sc->cam_h[c];
+        ti.tiles_x = tx;
+        ti.ntiles = ntl;
+        ti.env = e;
+        ti.rec_base = rec_base[c];
+        ti.ent_base = ent_base[c];
+        ti.toff_base = toff_base[c];
+        ti.pix_off = pix[c];
+        ti.col_base = env_tri_base[e];
+        tcams[c] = ti;
+        for (int t0 = 0; t0 < ntl; t0 += tpi) {
+            ti.tile0 = t0;
+            titems.push_back(ti);
+        }
     }
     const int64_t tile_bytes = rec_base[C] * (int64_t)(tiled_record_bytes() + 4) + ent_base[C] * 4 +
-                               toff_base[C] * 4 + (int64_t)C * 24 + (int64_t)titems.size() * 8;
+                               toff_base[C] * 4 + ((int64_t)C + (int64_t)titems.size()) * (int64_t)sizeof(TileItem);
     if (o.render_path == VUDA_RENDER_TILED && !can_tile) {
         delete env;
         return invalid("tiled render path: a camera has more than " + std::to_string(tiled_max_tiles()) +
@@ -663,15 +680,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         if (s == VUDA_OK) s = dalloc(env, &ts.wide, (size_t)rec_base[C]);
         if (s == VUDA_OK) s = dalloc(env, &ts.ent, (size_t)ent_base[C]);
         if (s == VUDA_OK) s = dalloc(env, &ts.toff, (size_t)toff_base[C]);
-        int64_t* d_rb = nullptr;
-        int64_t* d_eb = nullptr;
-        int64_t* d_tb = nullptr;
-        if (s == VUDA_OK) s = upload(env, &d_rb, rec_base.data(), (size_t)C);
-        if (s == VUDA_OK) s = upload(env, &d_eb, ent_base.data(), (size_t)C);
-        if (s == VUDA_OK) s = upload(env, &d_tb, toff_base.data(), (size_t)C);
-        ts.rec_base = d_rb;
-        ts.ent_base = d_eb;
-        ts.toff_base = d_tb;
+        if (s == VUDA_OK) s = upload(env, &env->tcams, tcams.data(), tcams.size());
         if (s == VUDA_OK) s = upload(env, &env->titems, titems.data(), titems.size());
         env->ntitems = (int)titems.size();
     }
@@ -788,7 +797,8 @@ static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, c
     cudaError_t e;
     const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
     if (env->tiled && !env->persistent && !shared)
-        e = launch_render_tiled(env->d, env->d.pose[slot], *fr, env->ts, env->titems, env->ntitems, stream);
+        e = launch_render_tiled(env->d, env->d.pose[slot], *fr, env->ts, env->tcams, env->titems, env->ntitems,
+                                stream);
     else if (env->persistent || shared)
         e = launch_render_list(env->d_desc, env->ren_items[slot], env->nitems, env->counters + 1,
                                shared ? env->ren_grid_sh : env->ren_grid, env->shade_items[slot], env->nshade,

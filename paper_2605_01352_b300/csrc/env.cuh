@@ -53,7 +53,8 @@ struct vuda_env {
     // tiled render path: scratch and work items (camera, first tile)
     int tiled = 0;
     vuda::TileScratch ts{};
-    int2* titems = nullptr;
+    vuda::TileItem* tcams = nullptr;    // [C]
+    vuda::TileItem* titems = nullptr;   // [ntitems]
     int ntitems = 0;
     // captured pipeline (CUDA graph of gsteps pipelined steps)
     cudaGraphExec_t gexec = nullptr;

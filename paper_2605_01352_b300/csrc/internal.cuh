@@ -157,18 +157,26 @@ int render_vcap();
 cudaError_t launch_shade(const DevBatch& b, const float* pose, cudaStream_t stream);
 
 // Scratch of the tiled render path (tiled.cu), per camera c of env e with
-// T_e triangles and n_c 16 x 16 tiles: records [rec_base[c], + T_e) of
-// tiled_record_bytes() each, wide list [rec_base[c], + T_e), tile lists
-// [ent_base[c], + kNarrowTiles T_e), offsets [toff_base[c], + n_c + 2)
-// (n_c + 1 list offsets, then the wide-list length).
+// T_e triangles and n_c 16 x 16 tiles: records [rec_base, + T_e) of
+// tiled_record_bytes() each, wide list [rec_base, + T_e), tile lists
+// [ent_base, + kNarrowTiles T_e), offsets [toff_base, + n_c + 2) (n_c + 1
+// list offsets, then the wide-list length).
 struct TileScratch {
     void* rec;
     uint32_t* ent;
     uint32_t* wide;
     int32_t* toff;
-    const int64_t* rec_base;
-    const int64_t* ent_base;
-    const int64_t* toff_base;
+};
+// A camera (bin_kernel, tile0 = 0) or a raster work item of
+// tiled_tiles_per_item() tiles from tile0 (tile_kernel), with everything the
+// kernels need about the camera in one 80-byte record.
+struct __align__(16) TileItem {
+    int cam, tile0, W, H;         // bytes 0..15
+    int tiles_x, ntiles, env, pad;  // 16..31
+    long long rec_base, ent_base; // 32..47
+    long long toff_base, pad2;    // 48..63
+    long long pix_off;            // 64: first pixel of the camera in the frame
+    long long col_base;           // 72: first triangle of the environment in the colour table
 };
 int tiled_max_tiles();        // tiles per camera the path supports
 int tiled_narrow_tiles();     // list entries per triangle at most
@@ -177,7 +185,7 @@ size_t tiled_record_bytes();
 // Shade, set up and bin every camera, then rasterise and resolve the work
 // items (camera, first tile) of tiled_tiles_per_item() tiles each.
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
-                                const int2* items, int nitems, cudaStream_t stream);
+                                const TileItem* cams, const TileItem* items, int nitems, cudaStream_t stream);
 
 void set_error(const std::string& s);
 // Device bytes a batch will hold once created (an upper estimate).

@@ -26,6 +26,8 @@
 // identical frames.
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include "internal.cuh"
 #include "raster.cuh"
 
@@ -75,6 +77,20 @@ __device__ __forceinline__ void store_rec(TriRec* p, const TriRec& t) {
     for (int k = 0; k < 5; k++) q[k] = u.v[k];
 }
 
+__device__ __forceinline__ TileItem load_item(const TileItem* __restrict__ p) {
+    union {
+        int4 v[5];
+        TileItem t;
+    } u;
+    const int4* q = reinterpret_cast<const int4*>(p);
+#pragma unroll
+    for (int k = 0; k < 5; k++) u.v[k] = __ldg(q + k);
+    return u.t;
+}
+static_assert(sizeof(TileItem) == 80 && offsetof(TileItem, rec_base) == 32 && offsetof(TileItem, toff_base) == 48 &&
+                  offsetof(TileItem, pix_off) == 64 && offsetof(TileItem, col_base) == 72,
+              "TileItem layout");
+
 // Exclusive prefix sum over the kBT threads of the CTA, in thread order.
 __device__ __forceinline__ int cta_excl_scan(int v, int* wsum, int& total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -98,7 +114,8 @@ __device__ __forceinline__ int cta_excl_scan(int v, int* wsum, int& total) {
     return off + x - v;
 }
 
-__global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts) {
+__global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts,
+                                                  const TileItem* __restrict__ cams) {
     __shared__ int vX[kVertexCache], vY[kVertexCache], vflag[kVertexCache];
     __shared__ float viz[kVertexCache];
     __shared__ int s_cnt[kMaxTiles];
@@ -106,15 +123,14 @@ __global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __res
     __shared__ int s_nrec, s_nwide;
     __shared__ unsigned s_flags;
 
-    const int cam = blockIdx.x;
-    const int e = b.cam_env[cam];
-    const int W = b.cam_w[cam], H = b.cam_h[cam];
-    const int tiles_x = (W + kTile - 1) / kTile;
-    const int ntiles = tiles_x * ((H + kTile - 1) / kTile);
-    TriRec* rec = reinterpret_cast<TriRec*>(ts.rec) + ts.rec_base[cam];
-    uint32_t* wide = ts.wide + ts.rec_base[cam];
-    uint32_t* ent = ts.ent + ts.ent_base[cam];
-    int32_t* toff = ts.toff + ts.toff_base[cam];
+    const TileItem ci = load_item(cams + blockIdx.x);
+    const int cam = ci.cam, e = ci.env;
+    const int W = ci.W, H = ci.H;
+    const int tiles_x = ci.tiles_x, ntiles = ci.ntiles;
+    TriRec* rec = reinterpret_cast<TriRec*>(ts.rec) + ci.rec_base;
+    uint32_t* wide = ts.wide + ci.rec_base;
+    uint32_t* ent = ts.ent + ci.ent_base;
+    int32_t* toff = ts.toff + ci.toff_base;
     const CamView cv = load_cam(b, cam);
     const int b0 = b.body_off[e];
 
@@ -302,20 +318,23 @@ __device__ __forceinline__ void warp_pass(const TriRec* __restrict__ p, int y, i
 // Work item (camera, first tile): warp w rasterises and resolves tile
 // first + w of the camera.
 __global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr,
-                                                         const int2* __restrict__ items) {
+                                                            const TileItem* __restrict__ items) {
     __shared__ unsigned long long s_key[kTW][kTile * kTile];
     __shared__ int s_big[kTW][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int2 it = items[blockIdx.x];
-    const int cam = it.x, tile = it.y + w;
-    const int W = b.cam_w[cam], H = b.cam_h[cam];
-    const int tiles_x = (W + kTile - 1) / kTile;
-    const int ntiles = tiles_x * ((H + kTile - 1) / kTile);
+    const TileItem* itp = items + blockIdx.x;
+    const int4 geo = __ldg(reinterpret_cast<const int4*>(itp));        // cam, tile0, W, H
+    const int2 tl2 = __ldg(reinterpret_cast<const int2*>(itp) + 2);    // tiles_x, ntiles
+    const longlong2 rb = __ldg(reinterpret_cast<const longlong2*>(itp) + 2);   // rec_base, ent_base
+    const long long toff_base = __ldg(reinterpret_cast<const long long*>(itp) + 6);
+    const int tile = geo.y + w;
+    const int W = geo.z, H = geo.w;
+    const int tiles_x = tl2.x, ntiles = tl2.y;
     if (tile >= ntiles) return;   // whole warp; no CTA barrier follows
-    const TriRec* __restrict__ rec = reinterpret_cast<const TriRec*>(ts.rec) + ts.rec_base[cam];
-    const uint32_t* __restrict__ wide = ts.wide + ts.rec_base[cam];
-    const uint32_t* __restrict__ ent = ts.ent + ts.ent_base[cam];
-    const int32_t* __restrict__ toff = ts.toff + ts.toff_base[cam];
+    const TriRec* __restrict__ rec = reinterpret_cast<const TriRec*>(ts.rec) + rb.x;
+    const uint32_t* __restrict__ wide = ts.wide + rb.x;
+    const uint32_t* __restrict__ ent = ts.ent + rb.y;
+    const int32_t* __restrict__ toff = ts.toff + toff_base;
     const int tx0 = (tile % tiles_x) * kTile, ty0 = (tile / tiles_x) * kTile;
     const int tx1 = min(tx0 + kTile, W) - 1, ty1 = min(ty0 + kTile, H) - 1;
     // lane: row lane / 2 of the tile, columns 8 (lane % 2) .. + 7
@@ -356,9 +375,9 @@ __global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScrat
     __syncwarp();       // the lanes' shared-memory keys are complete
 
     if (nx <= 0) return;
-    const int e = b.cam_env[cam];
-    const uint32_t* colors = b.tri_color + b.env_tri_base[e];
-    const int64_t p0 = b.cam_pix_off[cam] + (int64_t)y * W + xs;
+    const longlong2 pc = __ldg(reinterpret_cast<const longlong2*>(itp) + 4);   // pix_off, col_base
+    const uint32_t* colors = b.tri_color + pc.y;
+    const int64_t p0 = pc.x + (int64_t)y * W + xs;
     const unsigned long long* sl = sk + (lane >> 1) * kTile + 8 * (lane & 1);
     float d[8];
     uint32_t tid[8], col[8];
@@ -420,11 +439,11 @@ int tiled_tiles_per_item() { return kTW; }
 size_t tiled_record_bytes() { return sizeof(TriRec); }
 
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
-                                const int2* items, int nitems, cudaStream_t stream) {
+                                const TileItem* cams, const TileItem* items, int nitems, cudaStream_t stream) {
     if (b.C == 0) return cudaSuccess;
     cudaError_t err = launch_shade(b, pose, stream);
     if (err != cudaSuccess) return err;
-    bin_kernel<<<b.C, kBT, 0, stream>>>(b, pose, ts);
+    bin_kernel<<<b.C, kBT, 0, stream>>>(b, pose, ts, cams);
     err = cudaGetLastError();
     if (err != cudaSuccess || nitems == 0) return err;
     tile_kernel<<<nitems, kTW * 32, 0, stream>>>(b, ts, fr, items);
