@@ -105,14 +105,19 @@ class Clocks:
 
 
 def dist_setup():
+    """Rank, world size and local rank from the launcher's environment; for
+    more than one rank a process group (NCCL with a GPU per rank, else gloo)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     return ws, rank, local
 
 
@@ -123,13 +128,28 @@ def barrier(ws):
 
 
 def allreduce_max(ws, x: float) -> float:
+    """Maximum of x over the ranks (the job's time is its slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_scene(S, rank: int, envs: int):
+    """The environments of one rank: environments [rank envs, (rank + 1) envs)
+    of the benchmark scene (each environment's content depends only on its
+    index, so N ranks together step the first N envs environments)."""
+    return S.cfg2(envs, env_base=rank * envs)
+
+
+def job_throughput(ws: int, envs: int, steps: int, seconds: float) -> float:
+    """Whole-job env-steps/s: every rank's environments over the slowest
+    rank's time."""
+    return ws * envs * steps / seconds
 
 
 def cpu_baseline(envs: int = 8, secs: float = 1.5):
@@ -354,7 +374,7 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     E = args.envs
-    sc = S.cfg2(E, env_base=rank * E)
+    sc = rank_scene(S, rank, E)
     env = V.Env(sc)
     env_info_path = env.info().render_path
     launches_per_step = 4 if env_info_path == V.RENDER_TILED else 3
@@ -468,10 +488,10 @@ def main():
         env.close()
         return
 
-    v_co = ws * E * args.steps / t_co
-    v_ser = ws * E * args.steps / t_ser
-    v_st = ws * E * args.steps / t_st
-    v_gr = ws * E * args.steps / t_gr
+    v_co = job_throughput(ws, E, args.steps, t_co)
+    v_ser = job_throughput(ws, E, args.steps, t_ser)
+    v_st = job_throughput(ws, E, args.steps, t_st)
+    v_gr = job_throughput(ws, E, args.steps, t_gr)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = sm_count * 128 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12   # TFLOP/s, one op per lane
     # physics: plain FP32 arithmetic (no FMA contraction), bound by the FP32 lanes
