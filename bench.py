@@ -420,30 +420,57 @@ def main():
                               {"sim": Ts, "render": Tr}}), flush=True)
         env.close()
         return
+    def graph_timed(n, stream=None):
+        """Steps replayed from a captured graph of 8 pipelined steps (median
+        of 5 runs of n steps, rounded down to whole graphs, scaled to n)."""
+        n8 = max(8, n - n % 8)
+        env.pipeline_capture(8, ring, stream=stream)
+        env.pipeline_run(8, ring, stream=stream)
+        res = []
+        for _ in range(5):
+            barrier(ws)
+            torch.cuda.synchronize()
+            clk.on = True
+            t = time.perf_counter()
+            tm = env.pipeline_run(n8, ring, stream=stream, timing=True)
+            wall = time.perf_counter() - t
+            clk.on = False
+            dev = tm["total_ms"] / 1000.0
+            res.append(allreduce_max(ws, dev if (dev == dev and dev > 0) else wall))
+        env.pipeline_release_graph()
+        return float(np.median(res)) * n / n8
+
+    # serialized, replayed from a graph as well (launch gaps removed on both sides)
+    t_serg = None
+    try:
+        t_serg = graph_timed(args.steps, stream=torch.cuda.Stream())
+    except Exception as ex:  # report why, keep the main line
+        t_serg = repr(ex)
     # co-scheduled: disjoint SM partitions (green contexts) at the fixed 50/50 split
     cos = env.coschedule(V.COSCHED_GREEN, args.sim_sms)
     env.pipeline_run(args.warmup, ring)
     t_gr, tm_gr, wall_gr = timed(args.steps)
-    # co-scheduled on two plain streams sharing all SMs
-    env.coschedule(V.COSCHED_STREAMS)
-    env.pipeline_run(args.warmup, ring)
-    t_st, tm_st, wall_st = timed(args.steps)
-    # the better of the two, replayed from a captured CUDA graph of 8 pipelined steps
+    # co-scheduled on two plain streams sharing all SMs, with each stream priority
+    st_runs = {}
+    for pname, prio in (("none", V.PRIORITY_NONE), ("sim_first", V.PRIORITY_SIM), ("render_first", V.PRIORITY_RENDER)):
+        env.coschedule(V.COSCHED_STREAMS, priority=prio)
+        env.pipeline_run(args.warmup, ring)
+        st_runs[pname] = (prio,) + tuple(timed(args.steps))
+    best_p = min(st_runs, key=lambda k: st_runs[k][1])
+    prio_best, t_st, tm_st, wall_st = st_runs[best_p]
+    # the better of green and streams, replayed from a captured CUDA graph of 8 pipelined steps
     best_mode = V.COSCHED_STREAMS if t_st <= t_gr else V.COSCHED_GREEN
     t_graph = None
     try:
-        env.coschedule(best_mode, args.sim_sms)
-        env.pipeline_capture(8, ring)
-        env.pipeline_run(8, ring)
-        t_graph, _, _ = timed(args.steps - args.steps % 8)
-        t_graph = t_graph * args.steps / (args.steps - args.steps % 8)
+        env.coschedule(best_mode, args.sim_sms, priority=prio_best if best_mode == V.COSCHED_STREAMS else 0)
+        t_graph = graph_timed(args.steps)
     except Exception as ex:  # report why, keep the main line
         t_graph = repr(ex)
+    best_name = ("streams_shared_sms_priority_" + best_p) if best_mode == V.COSCHED_STREAMS else "green_50_50"
     # headline: the fastest co-scheduled configuration measured above
-    cands = [("green_50_50", t_gr, tm_gr, wall_gr), ("streams_shared_sms", t_st, tm_st, wall_st)]
+    cands = [("green_50_50", t_gr, tm_gr, wall_gr), ("streams_shared_sms_priority_" + best_p, t_st, tm_st, wall_st)]
     if isinstance(t_graph, float):
-        cands.append(("%s_graph8" % ("streams_shared_sms" if best_mode == V.COSCHED_STREAMS else "green_50_50"),
-                      t_graph, None, None))
+        cands.append((best_name + "_graph8", t_graph, None, None))
     head = min(cands, key=lambda c: c[1])
     t_co, wall_co = head[1], head[3]
     tm_lat = head[2] if head[2] is not None else (tm_st if best_mode == V.COSCHED_STREAMS else tm_gr)
@@ -455,7 +482,7 @@ def main():
         tuned["env_steps_per_s"] = ws * E * 1000.0 / tuned["ms_per_step"]
     except Exception as ex:  # report why, keep the main line
         tuned = {"error": repr(ex)}
-    env.coschedule(V.COSCHED_STREAMS)
+    env.coschedule(V.COSCHED_STREAMS, priority=prio_best)
 
     # end to end through the host-buffer loop: forces in, frames out
     e2e = None
@@ -490,7 +517,6 @@ def main():
 
     v_co = job_throughput(ws, E, args.steps, t_co)
     v_ser = job_throughput(ws, E, args.steps, t_ser)
-    v_st = job_throughput(ws, E, args.steps, t_st)
     v_gr = job_throughput(ws, E, args.steps, t_gr)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = sm_count * 128 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12   # TFLOP/s, one op per lane
@@ -530,13 +556,20 @@ def main():
                    "l2": "per-step working set (frames 2 x %.0f MB) exceeds the 126 MB L2" % (bytes_out / 1e6)},
         "coscheduled_mode": head[0],
         "serialized": {"value": v_ser, "ms_per_step": 1000.0 * t_ser / args.steps},
+        "serialized_graph8": ({"value": job_throughput(ws, E, args.steps, t_serg),
+                               "ms_per_step": 1000.0 * t_serg / args.steps}
+                              if isinstance(t_serg, float) else {"error": t_serg}),
         "coscheduled_green_50_50": {"value": v_gr, "ms_per_step": 1000.0 * t_gr / args.steps, "partition": cos},
-        "coscheduled_streams_shared_sms": {"value": v_st, "ms_per_step": 1000.0 * t_st / args.steps},
-        "coscheduled_graph8": ({"value": ws * E * args.steps / t_graph, "ms_per_step": 1000.0 * t_graph / args.steps,
-                                "mode": "streams" if best_mode == V.COSCHED_STREAMS else "green_50_50"}
+        "coscheduled_streams_shared_sms": {k: {"value": job_throughput(ws, E, args.steps, v[1]),
+                                               "ms_per_step": 1000.0 * v[1] / args.steps}
+                                           for k, v in st_runs.items()},
+        "coscheduled_graph8": ({"value": job_throughput(ws, E, args.steps, t_graph),
+                                "ms_per_step": 1000.0 * t_graph / args.steps, "mode": best_name}
                                if isinstance(t_graph, float) else {"error": t_graph}),
         "autotuned": tuned,
         "speedup_vs_serialized": v_co / v_ser,
+        "speedup_vs_serialized_graph8": (v_co / job_throughput(ws, E, args.steps, t_serg)
+                                         if isinstance(t_serg, float) else None),
         "phase_ms": {"sim": Ts, "render": Tr, "ideal_overlap": (Ts + Tr) / max(Ts, Tr)},
         "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
                        "p99": float(np.percentile(lat, 99)) if lat.size else None},

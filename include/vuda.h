@@ -227,12 +227,18 @@ typedef struct {
     int32_t sim_sms;              /* GREEN: SMs for the sim partition (0: half); rounded to the device granularity */
     int32_t sim_ctas_per_sm;      /* SHARED: sim CTAs per SM (0: default) */
     int32_t render_ctas_per_sm;   /* SHARED: render CTAs per SM (0: default) */
+    int32_t priority;             /* VUDA_PRIORITY_*: which stream's CTAs the block scheduler dispatches first
+                                     when both have work (STREAMS and SHARED share SMs) */
 } vuda_cosched_opts;
+#define VUDA_PRIORITY_NONE 0
+#define VUDA_PRIORITY_SIM 1
+#define VUDA_PRIORITY_RENDER 2
 typedef struct {
     int32_t mode;
     int32_t sim_sms, render_sms;  /* SMs actually provisioned (0 if not partitioned) */
     int32_t sm_granularity;       /* partition alignment reported by the driver */
     int32_t sim_ctas_per_sm, render_ctas_per_sm;  /* SHARED: the per-SM quotas in use */
+    int32_t priority;
 } vuda_cosched_info;
 vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_stream_t* sim_stream,
                             vuda_stream_t* render_stream, vuda_cosched_info* info);
@@ -291,6 +297,7 @@ typedef struct {
     float ms_per_step, ms_per_step_serialized;
     int32_t trials, from_cache;
     int32_t sim_ctas_per_sm, render_ctas_per_sm;  /* SHARED winner's quotas */
+    int32_t priority;                             /* the winner's stream priority */
 } vuda_tune_result;
 vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda_frame* ring, vuda_tune_result* out);
 

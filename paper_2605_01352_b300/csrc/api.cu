@@ -824,14 +824,27 @@ vuda_status vuda_render(vuda_env_t env, int32_t pose_slot, const vuda_frame* fr,
     return render_slot(env, slot, fr, (cudaStream_t)stream);
 }
 
+// Stream priorities of (sim, render) for a VUDA_PRIORITY_* choice: the
+// favoured stream gets the device's greatest priority, the other its least.
+static void stream_priorities(int choice, int* ps, int* pr) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+    *ps = *pr = least;
+    if (choice == VUDA_PRIORITY_SIM) *ps = greatest;
+    if (choice == VUDA_PRIORITY_RENDER) *pr = greatest;
+}
+
 vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_stream_t* sim_stream,
                             vuda_stream_t* render_stream, vuda_cosched_info* info) {
     if (!env || !opts) return invalid("null argument");
+    if (opts->priority < VUDA_PRIORITY_NONE || opts->priority > VUDA_PRIORITY_RENDER) return invalid("bad priority");
     CK(cudaSetDevice(env->device));
     destroy_cosched(env);
+    int prio_sim = 0, prio_ren = 0;
+    stream_priorities(opts->priority, &prio_sim, &prio_ren);
     if (opts->mode == VUDA_COSCHED_STREAMS) {
-        CK(cudaStreamCreateWithFlags(&env->sim_s, cudaStreamNonBlocking));
-        CK(cudaStreamCreateWithFlags(&env->ren_s, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithPriority(&env->sim_s, cudaStreamNonBlocking, prio_sim));
+        CK(cudaStreamCreateWithPriority(&env->ren_s, cudaStreamNonBlocking, prio_ren));
         env->cos_mode = VUDA_COSCHED_STREAMS;
         env->cos_info.mode = VUDA_COSCHED_STREAMS;
     } else if (opts->mode == VUDA_COSCHED_GREEN) {
@@ -865,8 +878,8 @@ vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_
         if (r == CUDA_SUCCESS) r = dr.GreenCtxCreate(&env->g_sim, dsim, dev, CU_GREEN_CTX_DEFAULT_STREAM);
         if (r == CUDA_SUCCESS) r = dr.GreenCtxCreate(&env->g_ren, dren, dev, CU_GREEN_CTX_DEFAULT_STREAM);
         CUstream a = nullptr, b = nullptr;
-        if (r == CUDA_SUCCESS) r = dr.GreenCtxStreamCreate(&a, env->g_sim, CU_STREAM_NON_BLOCKING, 0);
-        if (r == CUDA_SUCCESS) r = dr.GreenCtxStreamCreate(&b, env->g_ren, CU_STREAM_NON_BLOCKING, 0);
+        if (r == CUDA_SUCCESS) r = dr.GreenCtxStreamCreate(&a, env->g_sim, CU_STREAM_NON_BLOCKING, prio_sim);
+        if (r == CUDA_SUCCESS) r = dr.GreenCtxStreamCreate(&b, env->g_ren, CU_STREAM_NON_BLOCKING, prio_ren);
         if (r == CUDA_SUCCESS) r = dr.CtxFromGreenCtx(&env->c_sim, env->g_sim);
         if (r == CUDA_SUCCESS) r = dr.CtxFromGreenCtx(&env->c_ren, env->g_ren);
         env->cos_mode = VUDA_COSCHED_GREEN;
@@ -899,8 +912,8 @@ vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_
             return invalid("sim and render CTAs per SM do not fit one SM together");
         int dev_sms = 0;
         CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device));
-        CK(cudaStreamCreateWithFlags(&env->sim_s, cudaStreamNonBlocking));
-        CK(cudaStreamCreateWithFlags(&env->ren_s, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithPriority(&env->sim_s, cudaStreamNonBlocking, prio_sim));
+        CK(cudaStreamCreateWithPriority(&env->ren_s, cudaStreamNonBlocking, prio_ren));
         env->cos_mode = VUDA_COSCHED_SHARED;
         env->sim_quota = ns;
         env->ren_quota = nr;
@@ -915,6 +928,7 @@ vuda_status vuda_coschedule(vuda_env_t env, const vuda_cosched_opts* opts, vuda_
     } else {
         return invalid("unknown co-scheduling mode");
     }
+    env->cos_info.priority = opts->priority;
     if (sim_stream) *sim_stream = env->sim_s;
     if (render_stream) *render_stream = env->ren_s;
     if (info) *info = env->cos_info;
@@ -1286,9 +1300,9 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
         trials++;
         return r;
     };
-    auto apply_mode = [&](int mode, int sims, int ns, int nr) -> vuda_status {
+    auto apply_mode = [&](int mode, int sims, int ns, int nr, int prio) -> vuda_status {
         if (mode == 0) return vuda_coschedule_reset(env);
-        vuda_cosched_opts co{mode, sims, ns, nr};
+        vuda_cosched_opts co{mode, sims, ns, nr, prio};
         return vuda_coschedule(env, &co, nullptr, nullptr, nullptr);
     };
     if (!cached) {
@@ -1310,25 +1324,27 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
         best.cosched_mode = 0;
         best.sim_sms = 0;
         best.sim_ctas_per_sm = best.render_ctas_per_sm = 0;
+        best.priority = 0;
         // 2. co-scheduling: shared SMs, disjoint partitions of a quarter to
         // three quarters of the SMs, and per-SM quotas (for each render count,
         // the most sim CTAs that fit beside it and one fewer)
         int dev_sms = 0;
         cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
-        struct Cand { int mode, sims, ns, nr; };
-        std::vector<Cand> modes = {{VUDA_COSCHED_STREAMS, 0, 0, 0}};
-        for (int q = 1; q <= 3; q++) modes.push_back({VUDA_COSCHED_GREEN, (dev_sms * q / 4) / 8 * 8, 0, 0});
+        struct Cand { int mode, sims, ns, nr, prio; };
+        std::vector<Cand> modes;
+        for (int pr = VUDA_PRIORITY_NONE; pr <= VUDA_PRIORITY_RENDER; pr++) modes.push_back({VUDA_COSCHED_STREAMS, 0, 0, 0, pr});
+        for (int q = 1; q <= 3; q++) modes.push_back({VUDA_COSCHED_GREEN, (dev_sms * q / 4) / 8 * 8, 0, 0, 0});
         if (build_lists(env) == VUDA_OK) {
             const int rmax = render_ctas_per_sm(env->band_rows, env->max_w);
             for (int nr = 1; nr <= rmax; nr++) {
                 const int ns = max_sim_beside(env, nr);
-                if (ns >= 1) modes.push_back({VUDA_COSCHED_SHARED, 0, ns, nr});
-                if (ns >= 2) modes.push_back({VUDA_COSCHED_SHARED, 0, ns - 1, nr});
+                if (ns >= 1) modes.push_back({VUDA_COSCHED_SHARED, 0, ns, nr, 0});
+                if (ns >= 2) modes.push_back({VUDA_COSCHED_SHARED, 0, ns - 1, nr, 0});
             }
         }
         for (auto& m : modes) {
             if (s != VUDA_OK) break;
-            vuda_status ms_st = apply_mode(m.mode, m.sims, m.ns, m.nr);
+            vuda_status ms_st = apply_mode(m.mode, m.sims, m.ns, m.nr, m.prio);
             if (ms_st != VUDA_OK) continue;  // e.g. no green contexts here
             s = measure(&ms);
             if (s == VUDA_OK && ms < best_ms) {
@@ -1337,11 +1353,13 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
                 best.sim_sms = env->cos_info.sim_sms;
                 best.sim_ctas_per_sm = env->cos_info.sim_ctas_per_sm;
                 best.render_ctas_per_sm = env->cos_info.render_ctas_per_sm;
+                best.priority = m.prio;
             }
         }
         // 3. graph replay of the winner
         best.graph_steps = 0;
-        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms, best.sim_ctas_per_sm, best.render_ctas_per_sm);
+        if (s == VUDA_OK)
+            s = apply_mode(best.cosched_mode, best.sim_sms, best.sim_ctas_per_sm, best.render_ctas_per_sm, best.priority);
         if (s == VUDA_OK && (best.cosched_mode != 0)) {
             if (vuda_pipeline_capture(env, 8, ring, nullptr) == VUDA_OK) {
                 vuda_status r = vuda_pipeline_run(env, 8, ring, nullptr, nullptr);
@@ -1365,7 +1383,8 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
         g_tune_cache[key] = best;
     } else {
         s = set_band_rows(env, best.band_rows);
-        if (s == VUDA_OK) s = apply_mode(best.cosched_mode, best.sim_sms, best.sim_ctas_per_sm, best.render_ctas_per_sm);
+        if (s == VUDA_OK)
+            s = apply_mode(best.cosched_mode, best.sim_sms, best.sim_ctas_per_sm, best.render_ctas_per_sm, best.priority);
         if (s == VUDA_OK && best.graph_steps) {
             if ((env->steps & 1) != 0) s = vuda_pipeline_run(env, 1, ring, nullptr, nullptr);
             if (s == VUDA_OK && vuda_pipeline_capture(env, best.graph_steps, ring, nullptr) != VUDA_OK) best.graph_steps = 0;

@@ -27,6 +27,7 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_BUSY, ERR_UNS
 FLAG_CONTACT_OVERFLOW, FLAG_NEAR_DISCARD, FLAG_GUARD_DISCARD, FLAG_MESH_CAPACITY, FLAG_TIMEOUT = 1, 2, 4, 8, 16
 COSCHED_STREAMS, COSCHED_GREEN, COSCHED_SHARED = 1, 2, 3
 RENDER_AUTO, RENDER_BAND, RENDER_TILED = 0, 1, 2
+PRIORITY_NONE, PRIORITY_SIM, PRIORITY_RENDER = 0, 1, 2
 
 vp = C.c_void_p
 
@@ -79,17 +80,18 @@ class TuneResult(C.Structure):
     _fields_ = [("band_rows", C.c_int32), ("cosched_mode", C.c_int32), ("sim_sms", C.c_int32),
                 ("graph_steps", C.c_int32), ("ms_per_step", C.c_float), ("ms_per_step_serialized", C.c_float),
                 ("trials", C.c_int32), ("from_cache", C.c_int32), ("sim_ctas_per_sm", C.c_int32),
-                ("render_ctas_per_sm", C.c_int32)]
+                ("render_ctas_per_sm", C.c_int32), ("priority", C.c_int32)]
 
 
 class CoschedOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("sim_sms", C.c_int32), ("sim_ctas_per_sm", C.c_int32),
-                ("render_ctas_per_sm", C.c_int32)]
+                ("render_ctas_per_sm", C.c_int32), ("priority", C.c_int32)]
 
 
 class CoschedInfo(C.Structure):
     _fields_ = [("mode", C.c_int32), ("sim_sms", C.c_int32), ("render_sms", C.c_int32),
-                ("sm_granularity", C.c_int32), ("sim_ctas_per_sm", C.c_int32), ("render_ctas_per_sm", C.c_int32)]
+                ("sm_granularity", C.c_int32), ("sim_ctas_per_sm", C.c_int32), ("render_ctas_per_sm", C.c_int32),
+                ("priority", C.c_int32)]
 
 
 def _sig(name, args, res=C.c_int):
@@ -302,18 +304,18 @@ class Env:
 
     # -- co-scheduling ----------------------------------------------------------------
     def coschedule(self, mode: int = COSCHED_GREEN, sim_sms: int = 0, sim_ctas_per_sm: int = 0,
-                   render_ctas_per_sm: int = 0):
+                   render_ctas_per_sm: int = 0, priority: int = 0):
         import torch
         s1, s2 = vp(), vp()
         info = CoschedInfo()
-        opts = CoschedOpts(mode, sim_sms, sim_ctas_per_sm, render_ctas_per_sm)
+        opts = CoschedOpts(mode, sim_sms, sim_ctas_per_sm, render_ctas_per_sm, priority)
         check(lib.vuda_coschedule(self.h, C.byref(opts), C.byref(s1), C.byref(s2), C.byref(info)),
               "vuda_coschedule")
         self.sim_stream = torch.cuda.ExternalStream(s1.value)
         self.render_stream = torch.cuda.ExternalStream(s2.value)
         self.cosched = dict(mode=info.mode, sim_sms=info.sim_sms, render_sms=info.render_sms,
                             sm_granularity=info.sm_granularity, sim_ctas_per_sm=info.sim_ctas_per_sm,
-                            render_ctas_per_sm=info.render_ctas_per_sm)
+                            render_ctas_per_sm=info.render_ctas_per_sm, priority=info.priority)
         return self.cosched
 
     def coschedule_reset(self):
