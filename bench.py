@@ -377,7 +377,7 @@ def main():
     sc = rank_scene(S, rank, E)
     env = V.Env(sc)
     env_info_path = env.info().render_path
-    launches_per_step = 4 if env_info_path == V.RENDER_TILED else 3
+    launches_per_step = 3   # sim_kernel, then bin_kernel + tile_kernel (tiled) or shade_kernel + render_kernel (band)
     ring = [env.alloc_frame(triid=False), env.alloc_frame(triid=False)]
     P = env.P
     bytes_out = P * 7                                  # RGB8 + f32 depth
@@ -579,7 +579,7 @@ def main():
         "cpu_baseline": cpu,
         "cpu_baseline_single_thread": cpu1,
         "serving": serving,
-        "gpu_launches": launches_per_step * args.steps,   # per step: sim_kernel, then shade/bin/tile or shade/band kernels
+        "gpu_launches": launches_per_step * args.steps,
         "status_flags": flags,
         "clocks": clk.summary(),
         "wall_s_coscheduled": wall_co,

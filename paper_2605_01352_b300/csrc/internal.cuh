@@ -182,7 +182,7 @@ int tiled_max_tiles();        // tiles per camera the path supports
 int tiled_narrow_tiles();     // list entries per triangle at most
 int tiled_tiles_per_item();   // tiles per raster work item
 size_t tiled_record_bytes();
-// Shade, set up and bin every camera, then rasterise and resolve the work
+// Set up, shade and bin every camera, then rasterise and resolve the work
 // items (camera, first tile) of tiled_tiles_per_item() tiles each.
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
                                 const TileItem* cams, const TileItem* items, int nitems, cudaStream_t stream);

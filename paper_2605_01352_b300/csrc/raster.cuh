@@ -66,13 +66,14 @@ __device__ __forceinline__ CamView load_cam(const DevBatch& b, int cam) {
 // Vertex ent of a chunk whose first env-local body is cb0 (-1 = the ground
 // quad): world = R(q) (s * v) + p, view = basis . (world - eye), projected
 // and snapped to 24.8 fixed point.  Returns 0 and sets X, Y, iz, or returns
-// the discard flag (near plane or guard band).
+// the discard flag (near plane or guard band); the world position is set
+// either way.
 __device__ __forceinline__ int project_vertex(const DevBatch& b, const float* __restrict__ pose, const CamView& c,
-                                              int b0, int cb0, int2 ent, int& X, int& Y, float& iz) {
+                                              int b0, int cb0, int2 ent, int& X, int& Y, float& iz, float& wx,
+                                              float& wy, float& wz) {
     const int B = b.B;
     const int bi = cb0 + ent.y;
     const float* mv = b.mesh_verts + 3 * (size_t)ent.x;
-    float wx, wy, wz;
     if (bi < 0) {
         wx = mv[0]; wy = mv[1]; wz = mv[2];
     } else {
@@ -99,6 +100,36 @@ __device__ __forceinline__ int project_vertex(const DevBatch& b, const float* __
     Y = __float2int_rn(syp * 256.0f);
     iz = 1.0f / zc;
     return 0;
+}
+
+__device__ __forceinline__ int project_vertex(const DevBatch& b, const float* __restrict__ pose, const CamView& c,
+                                              int b0, int cb0, int2 ent, int& X, int& Y, float& iz) {
+    float wx, wy, wz;
+    return project_vertex(b, pose, c, b0, cb0, ent, X, Y, iz, wx, wy, wz);
+}
+
+// Flat colour of a triangle with world vertices w0, w1, w2 (mesh order):
+// I = 0.2 + 0.8 max(0, n . L) with n the normalised face normal
+// (w1 - w0) x (w2 - w0), each 8-bit channel of the albedo scaled by I,
+// rounded and clamped.
+__device__ __forceinline__ uint32_t flat_color(const float* w0, const float* w1, const float* w2, uint32_t alb,
+                                               const float* light) {
+    float e1x = w1[0] - w0[0], e1y = w1[1] - w0[1], e1z = w1[2] - w0[2];
+    float e2x = w2[0] - w0[0], e2y = w2[1] - w0[1], e2z = w2[2] - w0[2];
+    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    float len = sqrtf((nx * nx + ny * ny) + nz * nz);
+    float ndl = 0.0f;
+    if (len > 0.0f) ndl = ((nx / len) * light[0] + (ny / len) * light[1]) + (nz / len) * light[2];
+    float I = 0.2f + 0.8f * (ndl > 0.0f ? ndl : 0.0f);
+    uint32_t col = 0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float av = (float)((alb >> (8 * ch)) & 255u);
+        int vv = (int)(av * I + 0.5f);
+        vv = vv > 255 ? 255 : vv;
+        col |= (uint32_t)vv << (8 * ch);
+    }
+    return col;
 }
 
 }  // namespace vuda

@@ -571,22 +571,7 @@ __device__ __forceinline__ void shade_unit(const DevBatch& b, int unit, const fl
                 w[k][0] = v[0]; w[k][1] = v[1]; w[k][2] = v[2];
             }
         }
-        float e1x = w[1][0] - w[0][0], e1y = w[1][1] - w[0][1], e1z = w[1][2] - w[0][2];
-        float e2x = w[2][0] - w[0][0], e2y = w[2][1] - w[0][1], e2z = w[2][2] - w[0][2];
-        float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-        float len = sqrtf((nx * nx + ny * ny) + nz * nz);
-        float ndl = 0.0f;
-        if (len > 0.0f) ndl = ((nx / len) * b.light[0] + (ny / len) * b.light[1]) + (nz / len) * b.light[2];
-        float I = 0.2f + 0.8f * (ndl > 0.0f ? ndl : 0.0f);
-        uint32_t col = 0;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            float av = (float)((alb >> (8 * c)) & 255u);
-            int vv = (int)(av * I + 0.5f);
-            vv = vv > 255 ? 255 : vv;
-            col |= (uint32_t)vv << (8 * c);
-        }
-        out[t] = col;
+        out[t] = flat_color(w[0], w[1], w[2], alb, b.light);
     }
 }
 

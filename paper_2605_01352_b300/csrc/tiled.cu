@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __res
                                                   const TileItem* __restrict__ cams) {
     __shared__ int vX[kVertexCache], vY[kVertexCache], vflag[kVertexCache];
     __shared__ float viz[kVertexCache];
+    __shared__ float vW[kVertexCache][3];   // world positions, for the flat colours
     __shared__ int s_cnt[kMaxTiles];
     __shared__ int s_wsum[kBT / 32];
     __shared__ int s_nrec, s_nwide;
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __res
     int32_t* toff = ts.toff + ci.toff_base;
     const CamView cv = load_cam(b, cam);
     const int b0 = b.body_off[e];
+    uint32_t* colors = b.tri_color + ci.col_base;
 
     for (int i = threadIdx.x; i < ntiles; i += kBT) s_cnt[i] = 0;
     if (threadIdx.x == 0) {
@@ -149,11 +151,14 @@ __global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __res
         __syncthreads();  // counters set; the previous chunk is done with the vertex cache
         for (int v = threadIdx.x; v < nv; v += kBT) {
             int X = 0, Y = 0;
-            float iz = 0.0f;
-            vflag[v] = project_vertex(b, pose, cv, b0, cb0, vt[v], X, Y, iz);
+            float iz = 0.0f, wx, wy, wz;
+            vflag[v] = project_vertex(b, pose, cv, b0, cb0, vt[v], X, Y, iz, wx, wy, wz);
             vX[v] = X;
             vY[v] = Y;
             viz[v] = iz;
+            vW[v][0] = wx;
+            vW[v][1] = wy;
+            vW[v][2] = wz;
         }
         __syncthreads();
         for (int t = threadIdx.x; t < nt; t += kBT) {
@@ -202,6 +207,14 @@ __global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __res
             g.tl = tl;
             const int r = atomicAdd(&s_nrec, 1);
             store_rec(rec + r, g);
+            // flat colour of the recorded triangle (only recorded triangles
+            // can be the nearest at a pixel); the cameras of one environment
+            // write the same value
+            {
+                const int bi = cb0 + vt[i0].y;
+                const uint32_t alb = bi < 0 ? b.ground_albedo : __ldg(b.albedo + b0 + bi);
+                colors[g.id] = flat_color(vW[i0], vW[i1], vW[i2], alb, b.light);
+            }
             const int tx0 = px0 / kTile, tx1 = px1 / kTile, ty0 = py0 / kTile, ty1 = py1 / kTile;
             if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kNarrowTiles) {
                 for (int ty = ty0; ty <= ty1; ty++)
@@ -441,9 +454,8 @@ size_t tiled_record_bytes() { return sizeof(TriRec); }
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
                                 const TileItem* cams, const TileItem* items, int nitems, cudaStream_t stream) {
     if (b.C == 0) return cudaSuccess;
-    cudaError_t err = launch_shade(b, pose, stream);
-    if (err != cudaSuccess) return err;
     bin_kernel<<<b.C, kBT, 0, stream>>>(b, pose, ts, cams);
+    cudaError_t err;
     err = cudaGetLastError();
     if (err != cudaSuccess || nitems == 0) return err;
     tile_kernel<<<nitems, kTW * 32, 0, stream>>>(b, ts, fr, items);
