@@ -533,9 +533,11 @@ def main():
     # renderer: the frame it must write and the poses it reads, over the render phase
     alg = bytes_out + bytes_pose
     ach_r = alg / (Tr / 1000.0) / 1e9
-    roof_ren = {"kernel": "tile_kernel (+ shade_kernel, bin_kernel: the render phase)", "bound": "hbm",
+    roof_ren = {"kernel": "tile_kernel (+ bin_kernel: the render phase)" if env_info_path == V.RENDER_TILED
+                else "render_kernel (+ shade_kernel: the render phase)", "bound": "hbm",
                 "achieved": ach_r, "peak": hbm_peak, "unit": "GB/s", "frac": ach_r / hbm_peak,
-                "traffic": kernel_traffic("tile_kernel"), "algorithmic_bytes_per_launch": alg, "launch_ms": Tr,
+                "traffic": kernel_traffic("tile_kernel" if env_info_path == V.RENDER_TILED else "render_kernel"),
+                "algorithmic_bytes_per_launch": alg, "launch_ms": Tr,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
     roof = roof_sim if Ts >= Tr else roof_ren
     roof_other = roof_ren if Ts >= Tr else roof_sim
