@@ -143,8 +143,9 @@ typedef struct {
  * (needs cameras of at most 1024 tiles, and scratch of about
  * 120 bytes per triangle and camera).  AUTO: TILED where it applies and its
  * scratch fits (at most 8 GiB, and within hbm_budget_bytes), else BAND.
- * Persistent work-list launches (persistent = 1, VUDA_COSCHED_SHARED and the
- * serving loop) use the band kernel. */
+ * The render work-list launches of VUDA_COSCHED_SHARED and of the serving
+ * loop use the band kernel; persistent = 1 makes the physics a work-list
+ * launch and keeps the chosen render path. */
 #define VUDA_RENDER_AUTO 0
 #define VUDA_RENDER_BAND 1
 #define VUDA_RENDER_TILED 2
@@ -412,7 +413,7 @@ vuda_status vuda_serve_read_frame(vuda_server_t server, int64_t job_id, uint8_t*
  * Scratch (contact spill records and their per-environment offsets) lives in
  * one fixed 16 MiB device array inside the library, held by every device that
  * loads it until the process exits.  Batches needing more scratch
- * (4 bytes x (2 (E + 1) rounded up to 64 + 33 x max_contacts_per_body x B))
+ * (4 bytes x (2 (E + 1) rounded up to 64 + 36 x max_contacts_per_body x B))
  * are rejected with VUDA_ERR_INVALID before anything is launched.  The first
  * call on a device resolves the array's device address; make that first call
  * before any stream capture.  Every call shares the array: calls whose work

@@ -796,7 +796,7 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
 static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, cudaStream_t stream) {
     cudaError_t e;
     const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
-    if (env->tiled && !env->persistent && !shared)
+    if (env->tiled && !shared)
         e = launch_render_tiled(env->d, env->d.pose[slot], *fr, env->ts, env->tcams, env->titems, env->ntitems,
                                 stream);
     else if (env->persistent || shared)

@@ -123,8 +123,11 @@ struct CtaFootprint {
     int smem;   // static + dynamic shared memory, bytes
 };
 
-constexpr int kContactWords = 32;  // floats per contact record
-constexpr int kContactStride = kContactWords + 1;  // words between records (odd: bank-conflict free)
+constexpr int kContactWords = 32;  // floats per contact record: eight groups of four
+// words between records: a multiple of four (16-byte groups) with an odd
+// number of groups, so that 128-bit accesses by consecutive lanes to
+// consecutive records fall in distinct bank groups
+constexpr int kContactStride = kContactWords + 4;
 constexpr int kCamWords = 13;
 
 // Launchers (physics.cu, render.cu)

@@ -34,21 +34,25 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Field indices of a contact record (kContactWords floats).
+// Field indices of a contact record (kContactWords floats in eight 16-byte
+// groups: n|KN, rA|VMIN, rB|LN, t1|KT1, t2|KT2, P|LT1, LA|LT2, LB|AB).
 // KN, KT1, KT2 hold inverse effective masses; P is the impulse of the
-// current iteration, LA = rA x P and LB = rB x P its angular parts.
+// current iteration, LA = rA x P and LB = rB x P its angular parts.  Between
+// generation and the per-contact constants, RA holds the contact point and
+// VMIN the distance.
 enum : int {
-    F_AB = 0, F_N = 1, F_RA = 4, F_RB = 7, F_T1 = 10, F_T2 = 13, F_KN = 16, F_KT1 = 17, F_KT2 = 18,
-    F_VMIN = 19, F_LN = 20, F_LT1 = 21, F_LT2 = 22, F_P = 23, F_LA = 26, F_LB = 29
+    F_N = 0, F_KN = 3, F_RA = 4, F_VMIN = 7, F_RB = 8, F_LN = 11, F_T1 = 12, F_KT1 = 15, F_T2 = 16, F_KT2 = 19,
+    F_P = 20, F_LT1 = 23, F_LA = 24, F_LT2 = 27, F_LB = 28, F_AB = 31
 };
-static_assert(F_LB + 3 == kContactWords, "contact record layout");
+static_assert(F_AB + 1 == kContactWords, "contact record layout");
 
-// One contact record: kContactWords fields at p[0..), records kCS words apart
-// (odd stride: 32 consecutive records on 32 different banks).
+// One contact record: kContactWords fields at p[0..), records kCS words apart.
 constexpr int kCS = kContactStride;
 struct Rec {
     float* p;
     __device__ __forceinline__ float& operator[](int f) const { return p[f]; }
+    // the 16-byte group starting at field f (a multiple of 4)
+    __device__ __forceinline__ float4& g(int f) const { return *reinterpret_cast<float4*>(p + f); }
 };
 
 struct Contacts {
@@ -133,10 +137,9 @@ __device__ __forceinline__ f3 box_corner(const Bodies& B, int i, int k) {
 
 __device__ __forceinline__ void put_contact(const Contacts& C, int c, int a, int b, f3 n, f3 p, float d) {
     Rec r = C.rec(c);
-    r[F_AB] = __int_as_float(a | ((b + 1) << 16));
-    r[F_N] = n.x; r[F_N + 1] = n.y; r[F_N + 2] = n.z;
-    r[F_RA] = p.x; r[F_RA + 1] = p.y; r[F_RA + 2] = p.z;  // point, converted later
-    r[F_VMIN] = d;                                          // distance, converted later
+    r.g(F_N) = make_float4(n.x, n.y, n.z, 0.0f);
+    r.g(F_RA) = make_float4(p.x, p.y, p.z, d);   // point and distance, converted later
+    r.g(F_LB) = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(a | ((b + 1) << 16)));
 }
 
 // Sphere s against box x: normal from the box to the sphere, point on the box, distance.
@@ -288,17 +291,11 @@ __device__ __forceinline__ int block_excl_scan(int v, ScanBuf& sb, int& total) {
 }
 
 __device__ __forceinline__ void unpack_ab(const Rec& r, int& a, int& b) {
-    int ab = __float_as_int(r[F_AB]);
+    int ab = __float_as_int(r.g(F_LB).w);   // a 128-bit load: no bank conflict across consecutive records
     a = ab & 0xffff;
     b = (ab >> 16) - 1;
 }
 
-__device__ __forceinline__ f3 ld3(const Rec& r, int field) { return f3{r[field], r[field + 1], r[field + 2]}; }
-__device__ __forceinline__ void st3(const Rec& r, int field, f3 v) {
-    r[field] = v.x;
-    r[field + 1] = v.y;
-    r[field + 2] = v.z;
-}
 
 // mass-split effective mass along dir
 __device__ __forceinline__ float eff_mass(const Bodies& B, int a, int b, f3 rA, f3 rB, f3 dir) {
@@ -328,7 +325,7 @@ __host__ __device__ inline size_t phys_fixed_bytes(int NB, int cmax) {
     size_t f = (size_t)kBW * NB * 4;         // body records
     f += (size_t)(NB + 1) * 4;               // loff[NB+1]
     f += (size_t)4 * NB * 4;                 // per-quarter list counters
-    f += (size_t)2 * kPairChunk * 4;         // passing pairs and their item prefix
+    f += (size_t)kPairChunk * (4 + 2);       // passing pairs and their first item
     f += (size_t)8 * 4;                      // scan scratch
     f += (size_t)2 * cmax * 2;               // per-body contact lists (u16: contact << 1 | side)
     return align16(f);
@@ -404,7 +401,7 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
             for (; c + 4 <= cend; c += 4) {
                 int ab[4];
 #pragma unroll
-                for (int u = 0; u < 4; u++) ab[u] = __float_as_int(C.rec(c + u)[F_AB]);
+                for (int u = 0; u < 4; u++) ab[u] = __float_as_int(C.rec(c + u).g(F_LB).w);
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     int a = ab[u] & 0xffff, bb = (ab[u] >> 16) - 1;
@@ -425,11 +422,12 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
     // 3. per-contact constants
     for (int c = tid; c < nc; c += kT) {
         Rec r = C.rec(c);
-        int a, bb;
-        unpack_ab(r, a, bb);
-        f3 n = ld3(r, F_N);
-        f3 pt = ld3(r, F_RA);
-        float d = r[F_VMIN];
+        const float4 gn = r.g(F_N), gp = r.g(F_RA);
+        const int ab = __float_as_int(r.g(F_LB).w);
+        const int a = ab & 0xffff, bb = (ab >> 16) - 1;
+        f3 n{gn.x, gn.y, gn.z};
+        f3 pt{gp.x, gp.y, gp.z};
+        float d = gp.w;
         f3 rA = sub3(pt, ldpos(S, a));
         f3 rB = bb >= 0 ? sub3(pt, ldpos(S, bb)) : f3{0.0f, 0.0f, 0.0f};
         f3 ex = fabsf(n.x) < 0.9f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
@@ -453,13 +451,13 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
             float vb = -sc.restitution * vn0;
             if (vb > vmin) vmin = vb;
         }
-        st3(r, F_RA, rA);
-        st3(r, F_RB, rB);
-        st3(r, F_T1, t1);
-        st3(r, F_T2, t2);
-        r[F_KN] = kN; r[F_KT1] = kT1; r[F_KT2] = kT2;
-        r[F_VMIN] = vmin;
-        r[F_LN] = 0.0f; r[F_LT1] = 0.0f; r[F_LT2] = 0.0f;
+        r.g(F_N) = make_float4(n.x, n.y, n.z, kN);
+        r.g(F_RA) = make_float4(rA.x, rA.y, rA.z, vmin);
+        r.g(F_RB) = make_float4(rB.x, rB.y, rB.z, 0.0f);     // LN = 0
+        r.g(F_T1) = make_float4(t1.x, t1.y, t1.z, kT1);
+        r.g(F_T2) = make_float4(t2.x, t2.y, t2.z, kT2);
+        r.g(F_P) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);      // LT1 = 0
+        r.g(F_LA) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);     // LT2 = 0
     }
     __syncthreads();
 
@@ -467,22 +465,23 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
     for (int it = 0; it < sc.iterations; it++) {
         for (int c = tid; c < nc; c += kT) {
             Rec r = C.rec(c);
-            int a, bb;
-            unpack_ab(r, a, bb);
-            f3 n = ld3(r, F_N), t1 = ld3(r, F_T1), t2 = ld3(r, F_T2);
-            f3 rA = ld3(r, F_RA), rB = ld3(r, F_RB);
+            const float4 gn = r.g(F_N), ga = r.g(F_RA), gb = r.g(F_RB), g1 = r.g(F_T1), g2 = r.g(F_T2);
+            const float l1 = r.g(F_P).w, l2 = r.g(F_LA).w;
+            const int ab = __float_as_int(r.g(F_LB).w);
+            const int a = ab & 0xffff, bb = (ab >> 16) - 1;
+            f3 n{gn.x, gn.y, gn.z}, t1{g1.x, g1.y, g1.z}, t2{g2.x, g2.y, g2.z};
+            f3 rA{ga.x, ga.y, ga.z}, rB{gb.x, gb.y, gb.z};
             f3 vr = rel_vel(S, a, bb, rA, rB);
             float vn = dot3(n, vr);
-            float ln = r[F_LN];
-            float dl = (r[F_VMIN] - vn) * r[F_KN];
+            float ln = gb.w;
+            float dl = (ga.w - vn) * gn.w;
             float lnew = ln + dl;
             if (!(lnew > 0.0f)) lnew = 0.0f;
             float dln = lnew - ln;
             r[F_LN] = lnew;
             float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
-            float l1 = r[F_LT1], l2 = r[F_LT2];
-            float a1 = l1 - vt1 * r[F_KT1];
-            float a2 = l2 - vt2 * r[F_KT2];
+            float a1 = l1 - vt1 * g1.w;
+            float a2 = l2 - vt2 * g2.w;
             float lim = sc.mu * lnew;
             float m2 = a1 * a1 + a2 * a2;
             if (m2 > lim * lim) {
@@ -491,13 +490,15 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
                 a2 = a2 * s;
             }
             float dl1 = a1 - l1, dl2 = a2 - l2;
-            r[F_LT1] = a1;
-            r[F_LT2] = a2;
             f3 P{(dln * n.x + dl1 * t1.x) + dl2 * t2.x, (dln * n.y + dl1 * t1.y) + dl2 * t2.y,
                  (dln * n.z + dl1 * t1.z) + dl2 * t2.z};
-            st3(r, F_P, P);
-            st3(r, F_LA, cross3(rA, P));
-            if (bb >= 0) st3(r, F_LB, cross3(rB, P));
+            const f3 LA = cross3(rA, P);
+            r.g(F_P) = make_float4(P.x, P.y, P.z, a1);
+            r.g(F_LA) = make_float4(LA.x, LA.y, LA.z, a2);
+            if (bb >= 0) {
+                const f3 LB = cross3(rB, P);
+                r.g(F_LB) = make_float4(LB.x, LB.y, LB.z, __int_as_float(ab));
+            }
         }
         __syncthreads();
         // per-body sums in ascending contact order, applied at once: unit u
@@ -512,10 +513,10 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
             auto load = [&](int ent, float& x, float& y, float& z) {
                 Rec r = C.rec(ent >> 1);
                 const bool side = ent & 1;
-                const int f = half == 0 ? F_P : (side ? F_LB : F_LA);
-                x = r[f];
-                y = r[f + 1];
-                z = r[f + 2];
+                const float4 v = r.g(half == 0 ? F_P : (side ? F_LB : F_LA));
+                x = v.x;
+                y = v.y;
+                z = v.z;
                 if (side) {
                     x = -x;
                     y = -y;
@@ -580,7 +581,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     S.loff = ip; ip += NB + 1;
     int* qcnt = ip; ip += 4 * NB;        // [4][NB] contacts of each body in each quarter of the list
     int* plist = ip; ip += kPairChunk;   // units (passing pairs or plane bodies) of the current round
-    int* pitem = ip; ip += kPairChunk;   // first narrow-phase item of each unit
+    unsigned short* pitem = reinterpret_cast<unsigned short*>(ip); ip += kPairChunk / 2;   // their first item
     ScanBuf wsum{ip, 0}; ip += 2 * (kT / 32);
     unsigned short* lists = reinterpret_cast<unsigned short*>(ip);
     const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
@@ -662,7 +663,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                     int ex = block_excl_scan(nsub, wsum, tot);
                     if (nsub) {
                         plist[tid] = i;
-                        pitem[tid] = ex;
+                        pitem[tid] = (unsigned short)ex;
                     }
                     const int nu = min(kT, N - i0);
                     __syncthreads();
@@ -732,7 +733,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                         if (kbeg + r < npairs) {
                             if (passmask & (1u << r)) {
                                 plist[o] = i | (j << 16);
-                                pitem[o] = it;
+                                pitem[o] = (unsigned short)it;
                                 o++;
                                 it += (is_box(S, i) && is_box(S, j)) ? 16 : 1;
                             }

@@ -343,6 +343,61 @@ def test_full_size_cfg2_sampled(V, orc):
     env.close()
 
 
+def _sampled_env_check(orc, sc, env, ring, steps, envs, frame_slot):
+    """Sampled environments of a batch stepped `steps` times match the oracle
+    run on each of them alone (state, and every camera of the environment
+    in frame ring[frame_slot])."""
+    g = env.get_state()
+    pix = env.cam_pix_off
+    for e in envs:
+        sub = sc.subset([e])
+        so, _, _ = orc.sim_step(sub, steps)
+        b0, b1 = sc.body_off[e], sc.body_off[e + 1]
+        for k in ("pos", "vel", "quat", "angvel"):
+            np.testing.assert_allclose(g[k][:, b0:b1], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL, err_msg="env %d" % e)
+        o_rgb, o_dep, o_tid, _ = orc.render(sub, so["pos"], so["quat"])
+        c0, c1 = sc.cam_off[e], sc.cam_off[e + 1]
+        sl = slice(pix[c0], pix[c1])
+        f = ring[frame_slot]
+        np.testing.assert_array_equal(f["triid"][sl].cpu().numpy().view(np.uint32), o_tid, err_msg="env %d" % e)
+        np.testing.assert_allclose(f["depth"][sl].cpu().numpy(), o_dep, rtol=DEPTH_RTOL)
+        assert np.abs(f["rgb"][sl].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1
+
+
+def test_full_size_cfg3_graph_sampled(V, orc):
+    """The RL-rollout shape at full size: 4096 envs x 64 convex hulls of
+    500-2000 triangles, two 128 x 128 cameras each (about 330 M triangles per
+    camera-step), two pipelined steps replayed from a CUDA graph on
+    co-scheduled streams; sampled environments match the oracle."""
+    import torch
+    sc = S.cfg3()
+    env = V.Env(sc)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    env.coschedule(V.COSCHED_STREAMS)
+    env.pipeline_capture(2, ring)
+    env.pipeline_run(2, ring)
+    torch.cuda.synchronize()
+    assert env.info().steps_enqueued == 2 and env.C == 8192
+    _sampled_env_check(orc, sc, env, ring, 2, (0, 1, 2047, 4095), 1)
+    env.close()
+
+
+def test_full_size_cfg4_persistent_sampled(V, orc):
+    """The uneven batch at full size: 2048 envs with 4-256 bodies and 64,
+    128 or 256 pixel cameras through one persistent launch per phase;
+    sampled environments (including the largest) match the oracle."""
+    import torch
+    sc = S.cfg4()
+    env = V.Env(sc, persistent=True)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    env.pipeline_run(3, ring)
+    torch.cuda.synchronize()
+    sizes = np.diff(sc.body_off)
+    picks = (0, 1023, 2047, int(np.argmax(sizes)), int(np.argmin(sizes)))
+    _sampled_env_check(orc, sc, env, ring, 3, picks, 0)
+    env.close()
+
+
 def test_persistent_uneven_batch_matches(V, orc):
     """Uneven batch (body counts log-uniform in [4, 256], cameras of 64, 128
     and 256 pixels): the persistent work-list launches (largest items first,
