@@ -141,8 +141,10 @@ typedef struct {
  * camera sets up every triangle once into a device scratch area and bins it
  * into 16 x 16 tiles, then one warp per tile rasterises and resolves it
  * (needs cameras of at most 1024 tiles, and scratch of about
- * 120 bytes per triangle and camera).  AUTO: TILED where it applies and its
- * scratch fits (at most 8 GiB, and within hbm_budget_bytes), else BAND.
+ * 120 bytes per triangle and camera, an upper bound of which only the
+ * visible part is written).  AUTO: TILED where it applies and its scratch
+ * fits (at most half of the free device memory, and within
+ * hbm_budget_bytes), else BAND.
  * The render work-list launches of VUDA_COSCHED_SHARED and of the serving
  * loop use the band kernel; persistent = 1 makes the physics a work-list
  * launch and keeps the chosen render path. */

@@ -598,8 +598,16 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         return invalid("tiled render path: a camera has more than " + std::to_string(tiled_max_tiles()) +
                        " tiles of 16 x 16 pixels");
     }
+    // the scratch is an upper bound (only records that cover a pixel centre are
+    // written): take the tiled path while it stays within half of the free
+    // device memory
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
     env->tiled = o.render_path == VUDA_RENDER_TILED ||
-                 (o.render_path == VUDA_RENDER_AUTO && can_tile && tile_bytes <= (int64_t(8) << 30) &&
+                 (o.render_path == VUDA_RENDER_AUTO && can_tile && tile_bytes <= (int64_t)(free_b / 2) &&
                   (o.hbm_budget_bytes <= 0 || need + tile_bytes <= o.hbm_budget_bytes));
     if (env->tiled) need += tile_bytes;
     if (o.hbm_budget_bytes > 0 && need > o.hbm_budget_bytes) {
