@@ -114,7 +114,7 @@ __device__ __forceinline__ int cta_excl_scan(int v, int* wsum, int& total) {
     return off + x - v;
 }
 
-__global__ void __launch_bounds__(kBT) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts,
+__global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts,
                                                   const TileItem* __restrict__ cams) {
     __shared__ int vX[kVertexCache], vY[kVertexCache], vflag[kVertexCache];
     __shared__ float viz[kVertexCache];
@@ -312,6 +312,10 @@ __device__ __forceinline__ void warp_pass(const TriRec* __restrict__ p, int y, i
     long long E1 = (long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1];
     long long E2 = (long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2];
     const long long d0 = 256LL * t.A[0], d1 = 256LL * t.A[1], d2 = 256LL * t.A[2];
+    // the edge functions are affine along the run: negative at both of its
+    // ends for one edge means no pixel of the run is covered
+    const long long m = nx - 1;
+    if ((E0 < 0 && E0 + m * d0 < 0) || (E1 < 0 && E1 + m * d1 < 0) || (E2 < 0 && E2 + m * d2 < 0)) return;
     const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
 #pragma unroll
     for (int k = 0; k < 8; k++) {
