@@ -288,8 +288,47 @@ vuda_status build_lists(vuda_env* env) {
         if (s == VUDA_OK) s = upload(env, &env->shade_items[slot], sh.data(), sh.size());
     }
     env->nshade = B + E;
+    // size classes of the persistent physics: up to 32 bodies and up to
+    // kWideBodies on 128-thread CTAs, more on 512-thread CTAs; largest first
+    {
+        const int bounds[3] = {32, kWideBodies, 1 << 30};
+        int lo = 0;
+        bool class_spill = false;
+        env->sim_classes.clear();
+        for (int k = 2; k >= 0 && s == VUDA_OK; k--) {
+            lo = k == 0 ? 0 : bounds[k - 1];
+            vuda_env::SimClass cl;
+            std::vector<int2> ci;
+            for (int q = 0; q < E; q++) {
+                const int n = bo[eo[q] + 1] - bo[eo[q]];
+                if (n > lo && n <= bounds[k]) {
+                    ci.push_back(make_int2(0, eo[q]));
+                    cl.max_bodies = std::max(cl.max_bodies, n);
+                }
+            }
+            if (ci.empty()) continue;
+            cl.nitems = (int)ci.size();
+            cl.wide = k == 2;
+            const int mcpb = env->params.max_contacts_per_body;
+            cl.smem = cl.wide ? wide::phys_smem_bytes_default(cl.max_bodies, mcpb)
+                              : phys_smem_bytes_default(cl.max_bodies, mcpb);
+            cl.smem = std::min(std::max(cl.smem, env->phys_smem_user), 227 * 1024);
+            const int cap = cl.wide ? wide::phys_contacts_in_smem(cl.smem, cl.max_bodies, mcpb)
+                                    : phys_contacts_in_smem(cl.smem, cl.max_bodies, mcpb);
+            class_spill = class_spill || (int64_t)mcpb * cl.max_bodies > cap;
+            for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
+                for (auto& it : ci) it.x = slot << 24;
+                s = upload(env, &cl.items[slot], ci.data(), ci.size());
+            }
+            env->sim_classes.push_back(cl);
+        }
+        // a class whose contacts may exceed its shared-memory records needs the spill area
+        if (s == VUDA_OK && class_spill && !env->d.spill)
+            s = dalloc(env, &env->d.spill,
+                       (size_t)std::max<int64_t>((int64_t)env->params.max_contacts_per_body * B, 1) * kContactStride);
+    }
     if (s == VUDA_OK) s = build_render_list(env, env->band_rows, env->h_item_cam, env->h_item_y0);
-    if (s == VUDA_OK) s = dalloc(env, &env->counters, 2);
+    if (s == VUDA_OK) s = dalloc(env, &env->counters, 2 + env->sim_classes.size());
     if (s == VUDA_OK) s = dalloc(env, &env->sm_slots, 2 * (size_t)kMaxSmSlots);
     if (s == VUDA_OK) CK(cudaMemset(env->sm_slots, 0, 2 * sizeof(int) * kMaxSmSlots));
     if (s == VUDA_OK) s = upload(env, &env->d_desc, &env->d, 1);
@@ -297,6 +336,10 @@ vuda_status build_lists(vuda_env* env) {
     int dev_sms = 0;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
     env->sim_grid = std::max(1, std::min(E, dev_sms * sim_ctas_per_sm(env->phys_smem)));
+    for (auto& cl : env->sim_classes) {
+        const int per_sm = cl.wide ? wide::sim_ctas_per_sm(cl.smem) : sim_ctas_per_sm(cl.smem);
+        cl.grid = std::max(1, std::min(cl.nitems, dev_sms * per_sm));
+    }
     env->lists = 1;
     return VUDA_OK;
 }
@@ -522,7 +565,10 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
 
     // physics shared memory and spill
     const int mcpb = prm->max_contacts_per_body;
-    env->phys_smem = o.phys_smem_bytes > 0 ? o.phys_smem_bytes : phys_smem_bytes_default(max_bodies, mcpb);
+    // a given size below the layout's fixed part is raised to it (all contacts then spill)
+    env->phys_smem = o.phys_smem_bytes > 0 ? std::max(o.phys_smem_bytes, phys_min_smem_bytes(max_bodies, mcpb))
+                                           : phys_smem_bytes_default(max_bodies, mcpb);
+    env->phys_smem_user = o.phys_smem_bytes > 0 ? env->phys_smem : 0;
     std::vector<int64_t> spill_off(E + 1, 0);
     for (int e = 0; e < E; e++)
         spill_off[e + 1] = spill_off[e] + (int64_t)mcpb * (sc->body_off[e + 1] - sc->body_off[e]);
@@ -781,13 +827,25 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
     if (nsteps == 0) return VUDA_OK;
     cudaError_t e = cudaSuccess;
     const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
-    if (env->persistent || shared) {
-        const SmGate gate = shared ? SmGate{env->sm_slots, env->sim_quota} : SmGate{nullptr, 0};
-        const int grid = shared ? env->sim_grid_sh : env->sim_grid;
+    if (shared) {
+        const SmGate gate{env->sm_slots, env->sim_quota};
         for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
             int slot = (int)((env->steps + t) & 1);
-            e = launch_sim_items(env->d_desc, env->sim_items[slot], env->E, env->counters, grid, env->phys_smem,
-                                 env->max_bodies, force, gate, (cudaStream_t)stream);
+            e = launch_sim_items(env->d_desc, env->sim_items[slot], env->E, env->counters, env->sim_grid_sh,
+                                 env->phys_smem, env->max_bodies, force, gate, (cudaStream_t)stream);
+        }
+    } else if (env->persistent) {
+        // one work-list launch per size class, largest class first
+        for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
+            int slot = (int)((env->steps + t) & 1);
+            for (size_t k = 0; k < env->sim_classes.size() && e == cudaSuccess; k++) {
+                const vuda_env::SimClass& cl = env->sim_classes[k];
+                int* counter = env->counters + 2 + k;
+                e = cl.wide ? wide::launch_sim_items(env->d_desc, cl.items[slot], cl.nitems, counter, cl.grid, cl.smem,
+                                                     cl.max_bodies, force, SmGate{nullptr, 0}, (cudaStream_t)stream)
+                            : launch_sim_items(env->d_desc, cl.items[slot], cl.nitems, counter, cl.grid, cl.smem,
+                                               cl.max_bodies, force, SmGate{nullptr, 0}, (cudaStream_t)stream);
+            }
         }
     } else {
         e = launch_sim(env->d, env->sc, nsteps, force, (int)(env->steps & 1), env->phys_smem, env->max_bodies,

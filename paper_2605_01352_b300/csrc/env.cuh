@@ -18,6 +18,7 @@ struct vuda_env {
     int64_t bytes = 0;
     int64_t steps = 0;
     int phys_smem = 0;
+    int phys_smem_user = 0;        // the caller's shared memory per env (0: automatic)
     int band_rows = 0;
     int nitems = 0;
     int32_t* item_cam = nullptr;
@@ -39,10 +40,18 @@ struct vuda_env {
     int persistent = 0;
     vuda::DevBatch* d_desc = nullptr;                   // device copy of d
     int2* sim_items[2] = {nullptr, nullptr};      // per pose slot: (0 | slot << 24, env), largest first
+    // the same environments by size class for the persistent physics: each
+    // class has its own shared-memory layout (its largest environment), CTA
+    // size and work list
+    struct SimClass {
+        int2* items[2] = {nullptr, nullptr};
+        int nitems = 0, max_bodies = 0, smem = 0, grid = 0, wide = 0;
+    };
+    std::vector<SimClass> sim_classes;
     int4* ren_items[2] = {nullptr, nullptr};      // per pose slot: (0 | slot << 24, cam, y0, 0), largest first
     int2* shade_items[2] = {nullptr, nullptr};
     int nshade = 0;
-    int* counters = nullptr;                      // [2]: sim, render
+    int* counters = nullptr;                      // [2 + size classes]: sim, render, one per physics class
     int sim_grid = 0, ren_grid = 0;
     int lists = 0;                                // the work lists above are built
     // SM-shared co-scheduling: per-SM slot counters ([2][kMaxSmSlots]: sim,

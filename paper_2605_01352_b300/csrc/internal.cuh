@@ -130,18 +130,28 @@ constexpr int kContactWords = 32;  // floats per contact record: eight groups of
 constexpr int kContactStride = kContactWords + 4;
 constexpr int kCamWords = 13;
 
-// Launchers (physics.cu, render.cu)
-cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const float* force, int pose_slot_first,
-                       int smem_per_env, int max_bodies, cudaStream_t stream);
-// Work-list form: grid CTAs pull items [0, nitems) from *counter (zeroed here
-// on the stream first); max_bodies bounds every listed environment.
-// force: optional [3][B] world forces, only for a list over one batch.
-cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
-                             int smem_per_env, int max_bodies, const float* force, SmGate gate, cudaStream_t stream);
-int sim_ctas_per_sm(int smem_per_env);
-CtaFootprint sim_list_footprint(int smem_per_env);
-int phys_smem_bytes_default(int max_bodies, int mcpb);
-int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb);
+// Physics launchers (physics_impl.cuh): 128 threads per environment in
+// namespace vuda (physics.cu), 512 in vuda::wide (physics_wide.cu).
+#define VUDA_SIM_LAUNCHERS                                                                                      \
+    cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const float* force,               \
+                           int pose_slot_first, int smem_per_env, int max_bodies, cudaStream_t stream);         \
+    /* Work-list form: grid CTAs pull items [0, nitems) from *counter (zeroed here on the stream first);     \
+       max_bodies bounds every listed environment; force: optional [3][B] world forces, only for a list     \
+       over one batch. */                                                                                     \
+    cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid, \
+                                 int smem_per_env, int max_bodies, const float* force, SmGate gate,           \
+                                 cudaStream_t stream);                                                        \
+    int sim_ctas_per_sm(int smem_per_env);                                                                    \
+    CtaFootprint sim_list_footprint(int smem_per_env);                                                        \
+    int phys_smem_bytes_default(int max_bodies, int mcpb);                                                    \
+    int phys_min_smem_bytes(int max_bodies, int mcpb); /* the layout without contact records */               \
+    int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb);
+VUDA_SIM_LAUNCHERS
+namespace wide {
+VUDA_SIM_LAUNCHERS
+}
+constexpr int kWideBodies = 64;   // environments with more bodies take the 512-thread physics kernel
+// Launchers (render.cu, tiled.cu)
 cudaError_t launch_render_items(const DevBatch& b, const float* pose, const vuda_frame& fr, const int32_t* item_cam,
                                 const int32_t* item_y0, int nitems, int band_rows, int max_w, cudaStream_t stream);
 // Work-list form over several batches (frames from each descriptor).

@@ -1,0 +1,950 @@
+// Batched rigid-body step (the physics phase of the simulate-then-render
+// loop; the paper characterises it as collision detection plus constraint
+// solving in many fine-grained, low-occupancy stages, Sec. 2.1).
+//
+// One CTA of VUDA_SIM_THREADS threads owns one environment for a whole
+// launch: its bodies and contacts live in shared memory across all
+// substeps, so the serial chain of substeps x (contacts + Jacobi iterations)
+// runs on block barriers instead of kernel launches.  This file is compiled
+// twice: 128 threads per environment (physics.cu, namespace vuda) for the
+// common case of a few dozen bodies, and 512 threads (physics_wide.cu,
+// namespace vuda::wide) for environments of more than 64 bodies.
+//
+// Arithmetic: every float expression is evaluated in the written order
+// (the library is built with -fmad=false), so results reproduce a plain
+// sequential evaluation of the same formulas.
+//
+// Per substep (h = dt / substeps):
+//   1. v += h (g + F / m); rotation R(q) and world inverse inertia R I^-1 R^T
+//   2. contacts in canonical order: plane contacts by body (box corners in
+//      sign-bit order), then pairs (i, j), i < j, that pass a bounding-sphere
+//      test: sphere-sphere, sphere-box, box-box (A's corners inside B, then
+//      B's corners inside A); capacity max_contacts_per_body * N
+//   3. per contact: lever arms, tangent basis, mass-split effective masses,
+//      velocity target (speculative for d >= 0, bias beyond slop, restitution)
+//   4. Jacobi iterations: every contact solves against the iteration's
+//      velocities, then every body sums its contacts' impulses in ascending
+//      contact order
+//   5. x += h v, q <- normalize(q + h/2 (0, w) q)
+#pragma once
+#ifndef VUDA_SIM_THREADS
+#error "define VUDA_SIM_THREADS (threads per environment) before including physics_impl.cuh"
+#endif
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace vuda {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Field indices of a contact record (kContactWords floats in eight 16-byte
+// groups: n|KN, rA|VMIN, rB|LN, t1|KT1, t2|KT2, P|LT1, LA|LT2, LB|AB).
+// KN, KT1, KT2 hold inverse effective masses; P is the impulse of the
+// current iteration, LA = rA x P and LB = rB x P its angular parts.  Between
+// generation and the per-contact constants, RA holds the contact point and
+// VMIN the distance.
+enum : int {
+    F_N = 0, F_KN = 3, F_RA = 4, F_VMIN = 7, F_RB = 8, F_LN = 11, F_T1 = 12, F_KT1 = 15, F_T2 = 16, F_KT2 = 19,
+    F_P = 20, F_LT1 = 23, F_LA = 24, F_LT2 = 27, F_LB = 28, F_AB = 31
+};
+static_assert(F_AB + 1 == kContactWords, "contact record layout");
+
+// One contact record: kContactWords fields at p[0..), records kCS words apart.
+constexpr int kCS = kContactStride;
+struct Rec {
+    float* p;
+    __device__ __forceinline__ float& operator[](int f) const { return p[f]; }
+    // the 16-byte group starting at field f (a multiple of 4)
+    __device__ __forceinline__ float4& g(int f) const { return *reinterpret_cast<float4*>(p + f); }
+};
+
+struct Contacts {
+    float* s;       // shared records [cap][kCS]
+    int cap;        // records in shared memory
+    float* g;       // global spill records (record c at c - cap)
+    __device__ __forceinline__ Rec rec(int c) const {
+        return c < cap ? Rec{s + c * kCS} : Rec{g + (size_t)(c - cap) * kCS};
+    }
+};
+
+// The same records when all of them are in shared memory.
+struct SmemContacts {
+    float* s;
+    __device__ __forceinline__ Rec rec(int c) const { return Rec{s + c * kCS}; }
+};
+
+// Per-env bodies in shared memory: one record of kBW words per body.  The
+// odd stride keeps 32 consecutive bodies on 32 different banks, and every
+// field sits at an immediate offset from the record base.
+enum : int {
+    B_P = 0, B_Q = 3, B_V = 7, B_W = 10, B_D = 13, B_IM = 16, B_II = 17, B_BR = 20, B_R = 21, B_I = 30,
+    B_TYPE = 39, B_NCB = 40
+};
+constexpr int kBW = 41;
+
+struct Bodies {
+    float* base;
+    int* loff;
+    __device__ __forceinline__ float* b(int i) const { return base + i * kBW; }
+    __device__ __forceinline__ float& P(int k, int i) const { return b(i)[B_P + k]; }
+    __device__ __forceinline__ float& Q(int k, int i) const { return b(i)[B_Q + k]; }
+    __device__ __forceinline__ float& V(int k, int i) const { return b(i)[B_V + k]; }
+    __device__ __forceinline__ float& W(int k, int i) const { return b(i)[B_W + k]; }
+    __device__ __forceinline__ float& D(int k, int i) const { return b(i)[B_D + k]; }
+    __device__ __forceinline__ float& Rm(int k, int i) const { return b(i)[B_R + k]; }
+    __device__ __forceinline__ float& I(int k, int i) const { return b(i)[B_I + k]; }
+    __device__ __forceinline__ float& IM(int i) const { return b(i)[B_IM]; }
+    __device__ __forceinline__ float& II(int k, int i) const { return b(i)[B_II + k]; }
+    __device__ __forceinline__ float& BR(int i) const { return b(i)[B_BR]; }
+    __device__ __forceinline__ int& TYPE(int i) const { return reinterpret_cast<int*>(b(i))[B_TYPE]; }
+    __device__ __forceinline__ int& NCB(int i) const { return reinterpret_cast<int*>(b(i))[B_NCB]; }
+};
+
+struct f3 { float x, y, z; };
+
+__device__ __forceinline__ float dot3(f3 a, f3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+__device__ __forceinline__ f3 cross3(f3 a, f3 b) {
+    return f3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ f3 sub3(f3 a, f3 b) { return f3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 add3(f3 a, f3 b) { return f3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+
+__device__ __forceinline__ f3 ldpos(const Bodies& B, int i) { return f3{B.P(0, i), B.P(1, i), B.P(2, i)}; }
+__device__ __forceinline__ f3 ldvel(const Bodies& B, int i) { return f3{B.V(0, i), B.V(1, i), B.V(2, i)}; }
+__device__ __forceinline__ f3 ldang(const Bodies& B, int i) { return f3{B.W(0, i), B.W(1, i), B.W(2, i)}; }
+
+// R v with R row major in the body's 9 planes
+__device__ __forceinline__ f3 rmul(const Bodies& B, int i, f3 v) {
+    return f3{(B.Rm(0, i) * v.x + B.Rm(1, i) * v.y) + B.Rm(2, i) * v.z,
+              (B.Rm(3, i) * v.x + B.Rm(4, i) * v.y) + B.Rm(5, i) * v.z,
+              (B.Rm(6, i) * v.x + B.Rm(7, i) * v.y) + B.Rm(8, i) * v.z};
+}
+// R^T v
+__device__ __forceinline__ f3 rtmul(const Bodies& B, int i, f3 v) {
+    return f3{(B.Rm(0, i) * v.x + B.Rm(3, i) * v.y) + B.Rm(6, i) * v.z,
+              (B.Rm(1, i) * v.x + B.Rm(4, i) * v.y) + B.Rm(7, i) * v.z,
+              (B.Rm(2, i) * v.x + B.Rm(5, i) * v.y) + B.Rm(8, i) * v.z};
+}
+// Iw v
+__device__ __forceinline__ f3 imul(const Bodies& B, int i, f3 v) {
+    return f3{(B.I(0, i) * v.x + B.I(1, i) * v.y) + B.I(2, i) * v.z,
+              (B.I(3, i) * v.x + B.I(4, i) * v.y) + B.I(5, i) * v.z,
+              (B.I(6, i) * v.x + B.I(7, i) * v.y) + B.I(8, i) * v.z};
+}
+
+__device__ __forceinline__ f3 box_corner(const Bodies& B, int i, int k) {
+    f3 l{(k & 1) ? B.D(0, i) : -B.D(0, i), (k & 2) ? B.D(1, i) : -B.D(1, i), (k & 4) ? B.D(2, i) : -B.D(2, i)};
+    f3 w = rmul(B, i, l);
+    return add3(w, ldpos(B, i));
+}
+
+__device__ __forceinline__ void put_contact(const Contacts& C, int c, int a, int b, f3 n, f3 p, float d) {
+    Rec r = C.rec(c);
+    r.g(F_N) = make_float4(n.x, n.y, n.z, 0.0f);
+    r.g(F_RA) = make_float4(p.x, p.y, p.z, d);   // point and distance, converted later
+    r.g(F_LB) = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(a | ((b + 1) << 16)));
+}
+
+// Sphere s against box x: normal from the box to the sphere, point on the box, distance.
+__device__ __forceinline__ void sphere_box(const Bodies& B, int s, int x, f3& n, f3& pt, float& d) {
+    f3 ps = ldpos(B, s), px = ldpos(B, x);
+    float h[3] = {B.D(0, x), B.D(1, x), B.D(2, x)};
+    float r = B.D(0, s);
+    f3 l3 = rtmul(B, x, sub3(ps, px));
+    float l[3] = {l3.x, l3.y, l3.z}, q[3], nl[3], pl[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) q[k] = l[k] < -h[k] ? -h[k] : (l[k] > h[k] ? h[k] : l[k]);
+    if (q[0] != l[0] || q[1] != l[1] || q[2] != l[2]) {
+        f3 df{l[0] - q[0], l[1] - q[1], l[2] - q[2]};
+        float dist = sqrtf(dot3(df, df));
+        nl[0] = df.x / dist; nl[1] = df.y / dist; nl[2] = df.z / dist;
+        d = dist - r;
+        pl[0] = q[0]; pl[1] = q[1]; pl[2] = q[2];
+    } else {
+        float pen[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) pen[k] = h[k] - fabsf(l[k]);
+        // axis of least penetration (lowest index on ties), selected without
+        // indexing the arrays by it, so that they stay in registers
+        const bool m1 = pen[1] < pen[0];
+        const float pm01 = m1 ? pen[1] : pen[0];
+        const bool m2 = pen[2] < pm01;
+        const int m = m2 ? 2 : (m1 ? 1 : 0);
+        const float penm = m2 ? pen[2] : pm01;
+        const float lm = m2 ? l[2] : (m1 ? l[1] : l[0]);
+        float sg = lm >= 0.0f ? 1.0f : -1.0f;
+        d = -penm - r;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            nl[k] = k == m ? sg : 0.0f;
+            pl[k] = k == m ? sg * h[k] : l[k];
+        }
+    }
+    n = rmul(B, x, f3{nl[0], nl[1], nl[2]});
+    pt = add3(rmul(B, x, f3{pl[0], pl[1], pl[2]}), px);
+}
+
+// Corner k of box a tested against box b: returns true if within the margin.
+__device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int k, float margin, f3& c, f3& nB,
+                                              float& d) {
+    c = box_corner(B, a, k);
+    f3 l3 = rtmul(B, b, sub3(c, ldpos(B, b)));
+    float l[3] = {l3.x, l3.y, l3.z};
+    float pen[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) pen[j] = B.D(j, b) - fabsf(l[j]);
+    // axis of least penetration (lowest index on ties), selected without
+    // indexing the arrays by it
+    const bool m1 = pen[1] < pen[0];
+    const float pm01 = m1 ? pen[1] : pen[0];
+    const bool m2 = pen[2] < pm01;
+    const int m = m2 ? 2 : (m1 ? 1 : 0);
+    d = -(m2 ? pen[2] : pm01);
+    if (!(d < margin)) return false;
+    const float lm = m2 ? l[2] : (m1 ? l[1] : l[0]);
+    float sg = lm >= 0.0f ? 1.0f : -1.0f;
+    nB = f3{sg * B.Rm(m, b), sg * B.Rm(3 + m, b), sg * B.Rm(6 + m, b)};  // column m of R_b
+    return true;
+}
+
+__device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.TYPE(i) == kShapeBox; }
+
+constexpr int kT = VUDA_SIM_THREADS;   // threads per environment (one CTA)
+constexpr int kParts = kT / 32;        // parts of the contact list, one per warp, when building per-body lists
+constexpr int kMinCtas = kT == 128 ? 7 : 2;   // CTAs per SM the register budget is set for
+constexpr int kPairChunk = 4 * kT;  // candidate pairs per round of the pair phase (4 per thread)
+
+__device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margin) {
+    f3 dx = sub3(ldpos(B, i), ldpos(B, j));
+    float d2 = dot3(dx, dx);
+    float rs = (B.BR(i) + B.BR(j)) + margin;
+    return d2 < rs * rs;
+}
+
+// One narrow-phase test of pair (i, j): sub 0 for sphere-sphere and
+// sphere-box; for box-box sub 0..7 tests A's corner sub inside B and
+// sub 8..15 tests B's corner sub-8 inside A.
+__device__ __forceinline__ bool pair_test(const Bodies& B, int i, int j, int sub, float margin, f3& n, f3& pt, float& d) {
+    bool bi = is_box(B, i), bj = is_box(B, j);
+    if (!bi && !bj) {
+        f3 pa = ldpos(B, i), pb = ldpos(B, j);
+        f3 dx = sub3(pa, pb);
+        float d2 = dot3(dx, dx);
+        float ra = B.D(0, i), rb = B.D(0, j);
+        float dist = sqrtf(d2);
+        if (dist > 0.0f) n = f3{dx.x / dist, dx.y / dist, dx.z / dist};
+        else n = f3{0.0f, 0.0f, 1.0f};
+        d = (dist - ra) - rb;
+        pt = f3{pa.x - n.x * ra, pa.y - n.y * ra, pa.z - n.z * ra};
+        return d < margin;
+    }
+    // one call site per test (the narrow phase is inlined): the box of a
+    // sphere-box pair, or the box whose corner is tested, given explicitly;
+    // the normal always points from j to i
+    bool flip;
+    bool hit;
+    if (!bi || !bj) {
+        flip = bi;   // box i, sphere j: the test gives the normal from i to j
+        sphere_box(B, bi ? j : i, bi ? i : j, n, pt, d);
+        hit = d < margin;
+    } else {
+        flip = sub >= 8;   // B's corner inside A: the normal from i to j
+        hit = corner_in_box(B, flip ? j : i, flip ? i : j, sub & 7, margin, pt, n, d);
+    }
+    if (flip) n = f3{-n.x, -n.y, -n.z};
+    return hit;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Shared scratch of the CTA-wide scans: two halves of kT/32 ints used by
+// consecutive scans in turn.  A scan needs one barrier (between the warps'
+// writes and everyone's reads): a thread writes a half again only two scans
+// later, after passing the barrier of the scan in between, which every
+// reader of the half reaches only after its reads.
+struct ScanBuf {
+    int* w;     // [2][kT / 32]
+    int k;      // scans so far (the same in every thread)
+};
+
+// Exclusive prefix sum over the CTA's kT threads in thread order.  Must be
+// called by all threads, in the same sequence of scans.
+__device__ __forceinline__ int block_excl_scan(int v, ScanBuf& sb, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int* wsum = sb.w + (sb.k & 1) * (kT / 32);
+    sb.k++;
+    int x = warp_incl_scan(v, lane);
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int off = 0;
+    total = 0;
+#pragma unroll
+    for (int k = 0; k < kT / 32; k++) {
+        int s = wsum[k];
+        if (k < w) off += s;
+        total += s;
+    }
+    return off + x - v;
+}
+
+__device__ __forceinline__ void unpack_ab(const Rec& r, int& a, int& b) {
+    int ab = __float_as_int(r.g(F_LB).w);   // a 128-bit load: no bank conflict across consecutive records
+    a = ab & 0xffff;
+    b = (ab >> 16) - 1;
+}
+
+
+// mass-split effective mass along dir
+__device__ __forceinline__ float eff_mass(const Bodies& B, int a, int b, f3 rA, f3 rB, f3 dir) {
+    f3 u = cross3(rA, dir);
+    float kA = (float)B.NCB(a) * (B.IM(a) + dot3(u, imul(B, a, u)));
+    float kB = 0.0f;
+    if (b >= 0) {
+        u = cross3(rB, dir);
+        kB = (float)B.NCB(b) * (B.IM(b) + dot3(u, imul(B, b, u)));
+    }
+    return kA + kB;
+}
+
+__device__ __forceinline__ f3 rel_vel(const Bodies& B, int a, int b, f3 rA, f3 rB) {
+    f3 va = add3(ldvel(B, a), cross3(ldang(B, a), rA));
+    if (b >= 0) {
+        f3 vb = add3(ldvel(B, b), cross3(ldang(B, b), rB));
+        return sub3(va, vb);
+    }
+    return va;
+}
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Bytes of per-env shared memory before the contact records.
+__host__ __device__ inline size_t phys_fixed_bytes(int NB, int cmax) {
+    size_t f = (size_t)kBW * NB * 4;         // body records
+    f += (size_t)(NB + 1) * 4;               // loff[NB+1]
+    f += (size_t)kParts * NB * 4;            // per-part list counters
+    f += (size_t)kPairChunk * (4 + 2);       // passing pairs and their first item
+    f += (size_t)2 * (kT / 32) * 4;          // scan scratch
+    f += (size_t)2 * cmax * 2;               // per-body contact lists (u16: contact << 1 | side)
+    return align16(f);
+}
+
+// First pair (i, j), i < j, of flat index k in lexicographic order.
+__device__ __forceinline__ void pair_of_index(int k, int N, int& i, int& j) {
+    // start(i) = i (2N - i - 1) / 2 is the flat index of (i, i + 1)
+    float b = (float)(2 * N - 1);
+    float disc = b * b - 8.0f * (float)k;
+    int ii = (int)floorf((b - sqrtf(fmaxf(disc, 0.0f))) * 0.5f);
+    ii = max(0, min(ii, N - 2));
+    auto start = [N](int x) { return x * (2 * N - x - 1) / 2; };
+    while (ii > 0 && start(ii) > k) ii--;
+    while (ii < N - 2 && start(ii + 1) <= k) ii++;
+    i = ii;
+    j = k - start(ii) + ii + 1;
+}
+
+// Ordered expansion over the CTA: each thread offers `nsub` sub-items for its
+// unit; returns the exclusive item prefix and the total (block scan).
+// Items are later tested one per thread and their hits compacted in order.
+
+// One environment for nsteps steps, by the whole CTA.  b lives in shared
+// memory (copied there by the kernels below).
+// Per-body contact lists, per-contact constants and the Jacobi iterations of
+// one substep.  CA is the contact-record accessor: shared memory only when
+// every contact of the env fits there (the common case, 32-bit shared
+// addressing), or shared then global spill.
+template <class CA>
+__device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int* qcnt, unsigned short* lists,
+                                              ScanBuf& wsum, int nc, int N, int NB, const SimConst& sc, float h) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    // contacts per body, and per-body lists (contact << 1 | side) in
+    // ascending contact order: the list is cut into kParts parts, the
+    // contacts of each body are counted per part, and warp q fills the
+    // entries of part q
+    for (int i = tid; i < kParts * NB; i += kT) qcnt[i] = 0;
+    __syncthreads();
+    const int qlen = (nc + kParts - 1) / kParts;
+    for (int c = tid; c < nc; c += kT) {
+        int a, bb;
+        unpack_ab(C.rec(c), a, bb);
+        int q;   // c / qlen (c < kParts qlen)
+        if (kParts == 4) q = (c >= qlen) + (c >= 2 * qlen) + (c >= 3 * qlen);
+        else q = c / qlen;
+        atomicAdd(qcnt + q * NB + a, 1);
+        if (bb >= 0) atomicAdd(qcnt + q * NB + bb, 1);
+    }
+    __syncthreads();
+    {
+        int run = 0;
+        for (int i0 = 0; i0 < N; i0 += kT) {
+            int i = i0 + tid;
+            int v = 0;
+            if (i < N)
+                for (int q = 0; q < kParts; q++) v += qcnt[q * NB + i];
+            int tot;
+            int ex = block_excl_scan(v, wsum, tot);
+            if (i < N) {
+                S.NCB(i) = v;
+                S.loff[i] = run + ex;
+            }
+            run += tot;
+        }
+        if (tid == 0) S.loff[N] = run;
+    }
+    __syncthreads();
+    // warp q fills the entries of the contacts of part q
+    for (int i0 = 0; i0 < N; i0 += 32) {
+        int i = i0 + lane;
+        if (i < N) {
+            int o = S.loff[i];
+            for (int q = 0; q < warp; q++) o += qcnt[q * NB + i];
+            int cend = min(nc, (warp + 1) * qlen);
+            int c = warp * qlen;
+            for (; c + 4 <= cend; c += 4) {
+                int ab[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) ab[u] = __float_as_int(C.rec(c + u).g(F_LB).w);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    int a = ab[u] & 0xffff, bb = (ab[u] >> 16) - 1;
+                    if (a == i) lists[o++] = (unsigned short)((c + u) << 1);
+                    else if (bb == i) lists[o++] = (unsigned short)(((c + u) << 1) | 1);
+                }
+            }
+            for (; c < cend; c++) {
+                int a, bb;
+                unpack_ab(C.rec(c), a, bb);
+                if (a == i) lists[o++] = (unsigned short)(c << 1);
+                else if (bb == i) lists[o++] = (unsigned short)((c << 1) | 1);
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. per-contact constants
+    for (int c = tid; c < nc; c += kT) {
+        Rec r = C.rec(c);
+        const float4 gn = r.g(F_N), gp = r.g(F_RA);
+        const int ab = __float_as_int(r.g(F_LB).w);
+        const int a = ab & 0xffff, bb = (ab >> 16) - 1;
+        f3 n{gn.x, gn.y, gn.z};
+        f3 pt{gp.x, gp.y, gp.z};
+        float d = gp.w;
+        f3 rA = sub3(pt, ldpos(S, a));
+        f3 rB = bb >= 0 ? sub3(pt, ldpos(S, bb)) : f3{0.0f, 0.0f, 0.0f};
+        f3 ex = fabsf(n.x) < 0.9f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
+        f3 t = cross3(n, ex);
+        float tl = sqrtf(dot3(t, t));
+        f3 t1{t.x / tl, t.y / tl, t.z / tl};
+        f3 t2 = cross3(n, t1);
+        // inverse effective masses, once per substep
+        float kN = 1.0f / eff_mass(S, a, bb, rA, rB, n);
+        float kT1 = 1.0f / eff_mass(S, a, bb, rA, rB, t1);
+        float kT2 = 1.0f / eff_mass(S, a, bb, rA, rB, t2);
+        float vn0 = dot3(n, rel_vel(S, a, bb, rA, rB));
+        float vmin;
+        if (d >= 0.0f) {
+            vmin = -d / h;
+        } else {
+            float pen = -d - sc.slop;
+            vmin = (sc.beta * (pen > 0.0f ? pen : 0.0f)) / h;
+        }
+        if (d < 0.0f && vn0 < -sc.rest_thr) {
+            float vb = -sc.restitution * vn0;
+            if (vb > vmin) vmin = vb;
+        }
+        r.g(F_N) = make_float4(n.x, n.y, n.z, kN);
+        r.g(F_RA) = make_float4(rA.x, rA.y, rA.z, vmin);
+        r.g(F_RB) = make_float4(rB.x, rB.y, rB.z, 0.0f);     // LN = 0
+        r.g(F_T1) = make_float4(t1.x, t1.y, t1.z, kT1);
+        r.g(F_T2) = make_float4(t2.x, t2.y, t2.z, kT2);
+        r.g(F_P) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);      // LT1 = 0
+        r.g(F_LA) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);     // LT2 = 0
+    }
+    __syncthreads();
+
+    // 4. Jacobi iterations
+    for (int it = 0; it < sc.iterations; it++) {
+        for (int c = tid; c < nc; c += kT) {
+            Rec r = C.rec(c);
+            const float4 gn = r.g(F_N), ga = r.g(F_RA), gb = r.g(F_RB), g1 = r.g(F_T1), g2 = r.g(F_T2);
+            const float l1 = r.g(F_P).w, l2 = r.g(F_LA).w;
+            const int ab = __float_as_int(r.g(F_LB).w);
+            const int a = ab & 0xffff, bb = (ab >> 16) - 1;
+            f3 n{gn.x, gn.y, gn.z}, t1{g1.x, g1.y, g1.z}, t2{g2.x, g2.y, g2.z};
+            f3 rA{ga.x, ga.y, ga.z}, rB{gb.x, gb.y, gb.z};
+            f3 vr = rel_vel(S, a, bb, rA, rB);
+            float vn = dot3(n, vr);
+            float ln = gb.w;
+            float dl = (ga.w - vn) * gn.w;
+            float lnew = ln + dl;
+            if (!(lnew > 0.0f)) lnew = 0.0f;
+            float dln = lnew - ln;
+            r[F_LN] = lnew;
+            float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
+            float a1 = l1 - vt1 * g1.w;
+            float a2 = l2 - vt2 * g2.w;
+            float lim = sc.mu * lnew;
+            float m2 = a1 * a1 + a2 * a2;
+            if (m2 > lim * lim) {
+                float s = lim / sqrtf(m2);
+                a1 = a1 * s;
+                a2 = a2 * s;
+            }
+            float dl1 = a1 - l1, dl2 = a2 - l2;
+            f3 P{(dln * n.x + dl1 * t1.x) + dl2 * t2.x, (dln * n.y + dl1 * t1.y) + dl2 * t2.y,
+                 (dln * n.z + dl1 * t1.z) + dl2 * t2.z};
+            const f3 LA = cross3(rA, P);
+            r.g(F_P) = make_float4(P.x, P.y, P.z, a1);
+            r.g(F_LA) = make_float4(LA.x, LA.y, LA.z, a2);
+            if (bb >= 0) {
+                const f3 LB = cross3(rB, P);
+                r.g(F_LB) = make_float4(LB.x, LB.y, LB.z, __int_as_float(ab));
+            }
+        }
+        __syncthreads();
+        // per-body sums in ascending contact order, applied at once: unit u
+        // is body (u / 64) * 32 + u % 32 and half (u / 32) % 2 -- the impulse
+        // sum and linear velocity (0), or the moment sum and angular
+        // velocity (1); consecutive lanes take consecutive bodies.  The B
+        // side of a contact enters with the opposite sign.
+        for (int u = tid; u < 2 * ((N + 31) & ~31); u += kT) {
+            const int half = (u >> 5) & 1;
+            const int i = ((u >> 6) << 5) + (u & 31);
+            if (i >= N) continue;
+            auto load = [&](int ent, float& x, float& y, float& z) {
+                Rec r = C.rec(ent >> 1);
+                const bool side = ent & 1;
+                const float4 v = r.g(half == 0 ? F_P : (side ? F_LB : F_LA));
+                x = v.x;
+                y = v.y;
+                z = v.z;
+                if (side) {
+                    x = -x;
+                    y = -y;
+                    z = -z;
+                }
+            };
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+            const int k1 = S.loff[i + 1];
+            int k = S.loff[i];
+            // loads of four entries are independent: issue them together,
+            // then add in list order
+            for (; k + 4 <= k1; k += 4) {
+                float x[4], y[4], z[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) load(lists[k + q], x[q], y[q], z[q]);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    s0 = s0 + x[q];
+                    s1 = s1 + y[q];
+                    s2 = s2 + z[q];
+                }
+            }
+            for (; k < k1; k++) {
+                float x, y, z;
+                load(lists[k], x, y, z);
+                s0 = s0 + x;
+                s1 = s1 + y;
+                s2 = s2 + z;
+            }
+            if (half == 0) {
+                const float im = S.IM(i);
+                S.V(0, i) = S.V(0, i) + sc.omega * (im * s0);
+                S.V(1, i) = S.V(1, i) + sc.omega * (im * s1);
+                S.V(2, i) = S.V(2, i) + sc.omega * (im * s2);
+            } else {
+                const f3 dw = imul(S, i, f3{s0, s1, s2});
+                S.W(0, i) = S.W(0, i) + sc.omega * dw.x;
+                S.W(1, i) = S.W(1, i) + sc.omega * dw.y;
+                S.W(2, i) = S.W(2, i) + sc.omega * dw.z;
+            }
+        }
+        __syncthreads();
+    }
+
+}
+
+__device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, const float* __restrict__ force, int slot0,
+                                     int smem_per_env, int NB) {
+    const SimConst& sc = b.sc;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const int b0 = b.body_off[e];
+    const int N = b.body_off[e + 1] - b0;
+    const int B = b.B;
+    const int cmax = sc.mcpb * N;
+    const int cmax_nb = sc.mcpb * NB;
+
+    Bodies S;
+    float* fp = reinterpret_cast<float*>(smem);
+    S.base = fp; fp += kBW * NB;
+    int* ip = reinterpret_cast<int*>(fp);
+    S.loff = ip; ip += NB + 1;
+    int* qcnt = ip; ip += kParts * NB;   // [kParts][NB] contacts of each body in each part of the list
+    int* plist = ip; ip += kPairChunk;   // units (passing pairs or plane bodies) of the current round
+    unsigned short* pitem = reinterpret_cast<unsigned short*>(ip); ip += kPairChunk / 2;   // their first item
+    ScanBuf wsum{ip, 0}; ip += 2 * (kT / 32);
+    unsigned short* lists = reinterpret_cast<unsigned short*>(ip);
+    const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
+    Contacts C;
+    C.s = reinterpret_cast<float*>(smem + fixed);
+    int capS = (int)((smem_per_env - (long)fixed) / (kCS * 4));
+    if (capS > cmax) capS = cmax;
+    if (capS < 0) capS = 0;
+    C.cap = capS;
+    C.g = b.spill + (size_t)b.spill_off[e] * kCS;
+
+    for (int i = tid; i < N; i += kT) {
+        int g = b0 + i;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            S.P(k, i) = b.pos[k * B + g];
+            S.V(k, i) = b.vel[k * B + g];
+            S.W(k, i) = b.ang[k * B + g];
+            S.D(k, i) = b.dims[k * B + g];
+            S.II(k, i) = b.ii[k * B + g];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) S.Q(k, i) = b.quat[k * B + g];
+        S.IM(i) = b.im[g];
+        int t = b.type[g];
+        S.TYPE(i) = t;
+        S.BR(i) = t == kShapeBox
+                        ? sqrtf((S.D(0, i) * S.D(0, i) + S.D(1, i) * S.D(1, i)) + S.D(2, i) * S.D(2, i))
+                        : S.D(0, i);
+    }
+    __syncthreads();
+
+    bool ovf = false;
+    int nc = 0;
+    const float h = sc.h;
+    const int npairs = N * (N - 1) / 2;
+    const f3 up{0.0f, 0.0f, 1.0f};
+    for (int step = 0; step < nsteps; step++) {
+        for (int ss = 0; ss < sc.substeps; ss++) {
+            // 1. velocities, rotation, world inverse inertia
+            for (int i = tid; i < N; i += kT) {
+                float im = S.IM(i);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    float f = force ? force[k * B + b0 + i] : 0.0f;
+                    S.V(k, i) = S.V(k, i) + h * (sc.g[k] + f * im);
+                }
+                float w = S.Q(0, i), x = S.Q(1, i), y = S.Q(2, i), z = S.Q(3, i);
+                float R[9];
+                R[0] = 1.0f - 2.0f * (y * y + z * z);
+                R[1] = 2.0f * (x * y - w * z);
+                R[2] = 2.0f * (x * z + w * y);
+                R[3] = 2.0f * (x * y + w * z);
+                R[4] = 1.0f - 2.0f * (x * x + z * z);
+                R[5] = 2.0f * (y * z - w * x);
+                R[6] = 2.0f * (x * z - w * y);
+                R[7] = 2.0f * (y * z + w * x);
+                R[8] = 1.0f - 2.0f * (x * x + y * y);
+                float ib0 = S.II(0, i), ib1 = S.II(1, i), ib2 = S.II(2, i);
+#pragma unroll
+                for (int k = 0; k < 9; k++) S.Rm(k, i) = R[k];
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        S.I(3 * r + c, i) = ((R[3 * r] * ib0) * R[3 * c] + (R[3 * r + 1] * ib1) * R[3 * c + 1]) +
+                                            (R[3 * r + 2] * ib2) * R[3 * c + 2];
+            }
+            __syncthreads();
+
+            // 2a. plane contacts: units = bodies in order, one item per sphere,
+            // eight per box (its corners in sign-bit order)
+            nc = 0;
+            if (sc.plane) {
+                for (int i0 = 0; i0 < N; i0 += kT) {
+                    int i = i0 + tid;
+                    int nsub = i < N ? (is_box(S, i) ? 8 : 1) : 0;
+                    int tot;
+                    int ex = block_excl_scan(nsub, wsum, tot);
+                    if (nsub) {
+                        plist[tid] = i;
+                        pitem[tid] = (unsigned short)ex;
+                    }
+                    const int nu = min(kT, N - i0);
+                    __syncthreads();
+                    for (int u0 = 0; u0 < tot; u0 += kT) {
+                        int u = u0 + tid;
+                        bool hit = false;
+                        int bi = 0;
+                        f3 pt{0.0f, 0.0f, 0.0f};
+                        float d = 0.0f;
+                        if (u < tot) {
+                            int lo = 0, hi = nu - 1;
+                            while (lo < hi) {
+                                int mid = (lo + hi + 1) >> 1;
+                                if (pitem[mid] <= u) lo = mid; else hi = mid - 1;
+                            }
+                            bi = plist[lo];
+                            int k = u - pitem[lo];
+                            if (is_box(S, bi)) {
+                                pt = box_corner(S, bi, k);
+                                d = pt.z;
+                            } else {
+                                float r = S.D(0, bi);
+                                f3 p = ldpos(S, bi);
+                                d = p.z - r;
+                                pt = f3{p.x, p.y, p.z - r};
+                            }
+                            hit = d < sc.margin;
+                        }
+                        int t2;
+                        int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
+                        if (hit) {
+                            int idx = nc + ex2;
+                            if (idx < cmax) put_contact(C, idx, bi, -1, up, pt, d); else ovf = true;
+                        }
+                        nc += t2;
+                    }
+                }
+            }
+            // 2b. pairs in (i, j) order, kPairChunk candidates per round
+            for (int k0 = 0; k0 < npairs; k0 += kPairChunk) {
+                const int per = kPairChunk / kT;   // consecutive candidates per thread
+                int kbeg = k0 + tid * per;
+                int pi = 0, pj = 0;
+                if (kbeg < npairs) pair_of_index(kbeg, N, pi, pj);
+                unsigned passmask = 0;
+                int npass = 0, nsub = 0;
+                {
+                    int i = pi, j = pj;
+                    for (int r = 0; r < per; r++) {
+                        if (kbeg + r < npairs) {
+                            if (broad(S, i, j, sc.margin)) {
+                                passmask |= 1u << r;
+                                npass++;
+                                nsub += (is_box(S, i) && is_box(S, j)) ? 16 : 1;
+                            }
+                            if (++j == N) { i++; j = i + 1; }
+                        }
+                    }
+                }
+                int tot;
+                int ex = block_excl_scan(npass | (nsub << 16), wsum, tot);
+                int np = tot & 0xffff, nitems = tot >> 16;
+                {
+                    int o = ex & 0xffff, it = ex >> 16;
+                    int i = pi, j = pj;
+                    for (int r = 0; r < per; r++) {
+                        if (kbeg + r < npairs) {
+                            if (passmask & (1u << r)) {
+                                plist[o] = i | (j << 16);
+                                pitem[o] = (unsigned short)it;
+                                o++;
+                                it += (is_box(S, i) && is_box(S, j)) ? 16 : 1;
+                            }
+                            if (++j == N) { i++; j = i + 1; }
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int u0 = 0; u0 < nitems; u0 += kT) {
+                    int u = u0 + tid;
+                    bool hit = false;
+                    int i = 0, j = 0;
+                    f3 n, pt;
+                    float d = 0.0f;
+                    if (u < nitems) {
+                        int lo = 0, hi = np - 1;   // last passing pair whose first item is <= u
+                        while (lo < hi) {
+                            int mid = (lo + hi + 1) >> 1;
+                            if (pitem[mid] <= u) lo = mid; else hi = mid - 1;
+                        }
+                        int pr = plist[lo];
+                        i = pr & 0xffff;
+                        j = pr >> 16;
+                        hit = pair_test(S, i, j, u - pitem[lo], sc.margin, n, pt, d);
+                    }
+                    int t2;
+                    int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
+                    if (hit) {
+                        int idx = nc + ex2;
+                        if (idx < cmax) put_contact(C, idx, i, j, n, pt, d); else ovf = true;
+                    }
+                    nc += t2;
+                }
+            }
+            if (nc > cmax) nc = cmax;
+
+            if (nc <= C.cap) solve_substep(SmemContacts{C.s}, S, qcnt, lists, wsum, nc, N, NB, sc, h);
+            else solve_substep(C, S, qcnt, lists, wsum, nc, N, NB, sc, h);
+
+            // 5. positions and orientations
+            const float hh = 0.5f * h;
+            for (int i = tid; i < N; i += kT) {
+                S.P(0, i) = S.P(0, i) + h * S.V(0, i);
+                S.P(1, i) = S.P(1, i) + h * S.V(1, i);
+                S.P(2, i) = S.P(2, i) + h * S.V(2, i);
+                float qw = S.Q(0, i), qx = S.Q(1, i), qy = S.Q(2, i), qz = S.Q(3, i);
+                float wx = S.W(0, i), wy = S.W(1, i), wz = S.W(2, i);
+                float dw = -((wx * qx + wy * qy) + wz * qz);
+                float dx = qw * wx + (wy * qz - wz * qy);
+                float dy = qw * wy + (wz * qx - wx * qz);
+                float dz = qw * wz + (wx * qy - wy * qx);
+                float nw = qw + hh * dw, nx = qx + hh * dx, ny = qy + hh * dy, nz = qz + hh * dz;
+                float len = sqrtf(((nw * nw + nx * nx) + ny * ny) + nz * nz);
+                S.Q(0, i) = nw / len; S.Q(1, i) = nx / len; S.Q(2, i) = ny / len; S.Q(3, i) = nz / len;
+            }
+            __syncthreads();
+        }
+        // pose of this step for the renderer
+        float* pose = b.pose[(slot0 + step) & 1];
+        for (int i = tid; i < N; i += kT) {
+            int g = b0 + i;
+            pose[0 * B + g] = S.P(0, i);
+            pose[1 * B + g] = S.P(1, i);
+            pose[2 * B + g] = S.P(2, i);
+            pose[3 * B + g] = S.Q(0, i);
+            pose[4 * B + g] = S.Q(1, i);
+            pose[5 * B + g] = S.Q(2, i);
+            pose[6 * B + g] = S.Q(3, i);
+        }
+    }
+    for (int i = tid; i < N; i += kT) {
+        int g = b0 + i;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            b.pos[k * B + g] = S.P(k, i);
+            b.vel[k * B + g] = S.V(k, i);
+            b.ang[k * B + g] = S.W(k, i);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) b.quat[k * B + g] = S.Q(k, i);
+    }
+    int any_ovf = __syncthreads_or(ovf ? 1 : 0);
+    if (tid == 0) {
+        if (nsteps > 0) b.ncontacts[e] = nc;
+        if (any_ovf) atomicOr(b.flags + e, (unsigned)VUDA_FLAG_CONTACT_OVERFLOW);
+    }
+}
+
+// Copies a descriptor into shared memory with the whole CTA.
+__device__ __forceinline__ void load_desc(DevBatch& dst, const DevBatch& src) {
+    const int* a = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(DevBatch) / 4); k += blockDim.x) d[k] = a[k];
+}
+
+// Single batch: CTA e steps environment e.
+__global__ void __launch_bounds__(kT, kMinCtas) sim_kernel(DevBatch b0, SimConst sc0, int nsteps,
+                                                    const float* __restrict__ force, int slot0, int smem_per_env,
+                                                    int NB) {
+    __shared__ DevBatch sb;
+    load_desc(sb, b0);
+    __syncthreads();
+    if (threadIdx.x == 0) sb.sc = sc0;
+    __syncthreads();
+    sim_env(sb, blockIdx.x, nsteps, force, slot0, smem_per_env, NB);
+}
+
+// Work list over several batches: persistent CTAs pull (batch, environment,
+// pose slot) items from an atomic counter; one step each.
+__global__ void __launch_bounds__(kT, kMinCtas) sim_list_kernel(const DevBatch* __restrict__ descs,
+                                                         const int2* __restrict__ items, int nitems, int* counter,
+                                                         const float* __restrict__ force, int smem_per_env, int NB,
+                                                         SmGate gate) {
+    __shared__ DevBatch sb;
+    __shared__ int s_item, s_gate;
+    if (threadIdx.x == 0) s_gate = sm_gate_take(gate);
+    __syncthreads();
+    if (s_gate == kGateFull) return;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const int2 it = items[item];
+        load_desc(sb, descs[it.x & kItemDescMask]);
+        __syncthreads();
+        sim_env(sb, it.y, 1, force, (it.x >> 24) & 1, smem_per_env, NB);
+        __syncthreads();  // everyone is done with sb and s_item
+    }
+    if (threadIdx.x == 0) sm_gate_release(gate, s_gate);
+}
+
+}  // namespace
+
+VUDA_SIM_NS_BEGIN
+
+int phys_contacts_in_smem(int smem_per_env, int max_bodies, int mcpb) {
+    size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
+    if ((size_t)smem_per_env < fixed) return 0;
+    return (int)(((size_t)smem_per_env - fixed) / (kCS * 4));
+}
+
+int phys_min_smem_bytes(int max_bodies, int mcpb) { return (int)phys_fixed_bytes(max_bodies, mcpb * max_bodies); }
+
+int phys_smem_bytes_default(int max_bodies, int mcpb) {
+    size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
+    // room for 4.5 contacts per body in shared memory (a settled pile of
+    // spheres and boxes has about 3.5), more spill to global memory; with 32
+    // bodies this is 31 KB, so 7 environments fit on one SM
+    size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2);
+    if (want > 200 * 1024) want = 200 * 1024;
+    if (want < fixed) want = fixed;
+    return (int)align16(want);
+}
+
+int sim_ctas_per_sm(int smem_per_env) {
+    int n = 0;
+    cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_list_kernel, kT, smem_per_env) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
+
+CtaFootprint sim_list_footprint(int smem_per_env) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, sim_list_kernel) != cudaSuccess) return CtaFootprint{kT, 255, 227 * 1024};
+    return CtaFootprint{kT, fa.numRegs, (int)fa.sharedSizeBytes + smem_per_env};
+}
+
+cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
+                             int smem_per_env, int max_bodies, const float* force, SmGate gate, cudaStream_t stream) {
+    if (nitems == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    sim_list_kernel<<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force, smem_per_env,
+                                                        max_bodies, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const float* force, int slot0,
+                       int smem_per_env, int max_bodies, cudaStream_t stream) {
+    if (b.E == 0 || nsteps == 0) return cudaSuccess;
+    size_t fixed = phys_fixed_bytes(max_bodies, sc.mcpb * max_bodies);
+    if ((size_t)smem_per_env < fixed) smem_per_env = (int)fixed;
+    // set on every launch: the attribute is tracked per context and the
+    // kernel may be launched into different (green) contexts
+    cudaError_t e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    sim_kernel<<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
+    return cudaGetLastError();
+}
+
+VUDA_SIM_NS_END
+
+}  // namespace vuda
