@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--serial-only", action="store_true", help="only the serialized loop (for profiling)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-jobs", type=int, default=8)
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=1000)
     return ap.parse_args()
 
 

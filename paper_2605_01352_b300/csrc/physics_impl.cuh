@@ -583,7 +583,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     const int b0 = b.body_off[e];
     const int N = b.body_off[e + 1] - b0;
     const int B = b.B;
-    const int cmax = sc.mcpb * N;
+    int cmax = sc.mcpb * N;
     const int cmax_nb = sc.mcpb * NB;
 
     Bodies S;
@@ -604,6 +604,9 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     if (capS < 0) capS = 0;
     C.cap = capS;
     C.g = b.spill + (size_t)b.spill_off[e] * kCS;
+    // without a spill area the capacity is what shared memory holds
+    // (contacts beyond it are dropped in order and flagged as overflow)
+    if (b.spill == nullptr) cmax = capS;
 
     for (int i = tid; i < N; i += kT) {
         int g = b0 + i;

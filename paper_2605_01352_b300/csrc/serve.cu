@@ -308,8 +308,36 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
     std::stable_sort(sims.begin(), sims.end(), [](auto& x, auto& y) { return x.first > y.first; });
     for (auto& p : sims) si.h[a++] = p.second;
 
-    const int smem = std::max(phys_smem_bytes_default(max_bodies, max_mcpb), 1);
-    const int sim_grid = std::max(1, std::min((int)nsim, s->sms * sim_ctas_per_sm(smem)));
+    // physics by size class (the items are sorted by body count, so each class
+    // is a contiguous range): more than kWideBodies bodies on 512-thread CTAs,
+    // then up to kWideBodies and up to 32 on 128-thread CTAs, each with the
+    // shared-memory layout of its own largest environment
+    struct Cls {
+        size_t off = 0, n = 0;
+        int nb = 0, smem = 0, grid = 0;
+        bool wide = false;
+    };
+    Cls cls[3];
+    {
+        const int bounds[3] = {1 << 30, kWideBodies, 32};
+        size_t q = 0;
+        for (int k = 0; k < 3; k++) {
+            const int lo = k == 2 ? 0 : bounds[k + 1];
+            cls[k].off = q;
+            cls[k].wide = k == 0;
+            while (q < sims.size() && sims[q].first > lo) {
+                cls[k].nb = std::max(cls[k].nb, sims[q].first);
+                q++;
+            }
+            cls[k].n = q - cls[k].off;
+            if (!cls[k].n) continue;
+            cls[k].smem = cls[k].wide ? wide::phys_smem_bytes_default(cls[k].nb, max_mcpb)
+                                      : phys_smem_bytes_default(cls[k].nb, max_mcpb);
+            const int per_sm = cls[k].wide ? wide::sim_ctas_per_sm(cls[k].smem) : sim_ctas_per_sm(cls[k].smem);
+            cls[k].grid = std::max(1, std::min((int)cls[k].n, s->sms * per_sm));
+        }
+    }
+    (void)max_bodies;
     const int ren_grid = std::max(1, std::min((int)nren, s->sms * render_ctas_per_sm(br, max_w)));
     Iter it;
     it.no = no;
@@ -319,8 +347,14 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
     // pose slots are reused two iterations later: wait for that render
     if (no >= 2) e = cudaStreamWaitEvent(s->sim_s, s->ev_done[(no - 2) % vuda_server::kRing], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(si.d, si.h, nsim * sizeof(int2), cudaMemcpyHostToDevice, s->sim_s);
-    if (e == cudaSuccess) e = launch_sim_items(s->descs, si.d, (int)nsim, s->counters, sim_grid, smem, max_bodies, nullptr,
-                                                SmGate{nullptr, 0}, s->sim_s);
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+        if (!cls[k].n) continue;
+        const int2* items = si.d + cls[k].off;
+        e = cls[k].wide ? wide::launch_sim_items(s->descs, items, (int)cls[k].n, s->counters + 2 + k, cls[k].grid,
+                                                 cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, s->sim_s)
+                        : launch_sim_items(s->descs, items, (int)cls[k].n, s->counters + 2 + k, cls[k].grid,
+                                           cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, s->sim_s);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev_sim, s->sim_s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ri.d, ri.h, nren * sizeof(int4), cudaMemcpyHostToDevice, s->ren_s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hi.d, hi.h, nshade * sizeof(int2), cudaMemcpyHostToDevice, s->ren_s);
@@ -431,7 +465,7 @@ vuda_status vuda_serve_create(const vuda_serve_opts* opts, vuda_server_t* out) {
     vuda_server* s = new vuda_server();
     s->o = o;
     e = cudaMalloc(&s->descs, sizeof(DevBatch) * o.max_jobs);
-    if (e == cudaSuccess) e = cudaMalloc(&s->counters, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&s->counters, 5 * sizeof(int));   // render, then one per physics size class
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sim_s, cudaStreamNonBlocking);
     if (e == cudaSuccess && o.serialized) s->ren_s = s->sim_s;
     else if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->ren_s, cudaStreamNonBlocking);
