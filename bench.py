@@ -338,17 +338,25 @@ def csrc_sha() -> str:
     return h.hexdigest()
 
 
-def kernel_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources."""
+def kernel_counters(kernel: str) -> dict:
+    """The committed ncu counters of `kernel` (DRAM bytes per launch, issue
+    slots active, SM throughput), if they were taken on the current kernel
+    sources; empty otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
         if rec.get("csrc_sha256") != csrc_sha():
-            return None
-        return float(rec["kernels"][kernel]["bytes_per_launch"])
+            return {}
+        return dict(rec["kernels"][kernel])
     except Exception:
-        return None
+        return {}
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    v = kernel_counters(kernel).get("bytes_per_launch")
+    return float(v) if v is not None else None
 
 
 def main():
@@ -529,7 +537,9 @@ def main():
                 "algorithmic_flops_per_launch": flops, "launch_ms": Ts,
                 "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock (unfused ops; the path is built "
                                "without FMA contraction)",
-                "hbm_bytes_per_launch": bytes_state, "hbm_achieved_gbs": bytes_state / (Ts / 1000.0) / 1e9}
+                "hbm_bytes_per_launch": bytes_state, "hbm_achieved_gbs": bytes_state / (Ts / 1000.0) / 1e9,
+                "ncu_issue_active_pct": kernel_counters("sim_kernel").get("issue_active_pct"),
+                "ncu_sm_throughput_pct": kernel_counters("sim_kernel").get("sm_throughput_pct")}
     # renderer: the frame it must write and the poses it reads, over the render phase
     alg = bytes_out + bytes_pose
     ach_r = alg / (Tr / 1000.0) / 1e9
@@ -538,6 +548,8 @@ def main():
                 "achieved": ach_r, "peak": hbm_peak, "unit": "GB/s", "frac": ach_r / hbm_peak,
                 "traffic": kernel_traffic("tile_kernel" if env_info_path == V.RENDER_TILED else "render_kernel"),
                 "algorithmic_bytes_per_launch": alg, "launch_ms": Tr,
+                "ncu_issue_active_pct": kernel_counters("tile_kernel").get("issue_active_pct"),
+                "ncu_sm_throughput_pct": kernel_counters("tile_kernel").get("sm_throughput_pct"),
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
     roof = roof_sim if Ts >= Tr else roof_ren
     roof_other = roof_ren if Ts >= Tr else roof_sim

@@ -102,11 +102,12 @@ def test_physics_cfg2_subset_horizon(V, orc):
     _physics_horizon(V, orc, sc, steps=10)
 
 
-def test_physics_with_forces(V, orc):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_physics_with_forces(V, orc, persistent):
     sc = S.cfg1(4)
     rng = np.random.default_rng(3)
     f = rng.normal(0, 0.5, (3, sc.num_bodies)).astype(np.float32)
-    _physics_horizon(V, orc, sc, steps=5, force=f)
+    _physics_horizon(V, orc, sc, steps=5, force=f, persistent=persistent)
 
 
 def test_physics_contact_overflow_matches(V, orc):
@@ -120,14 +121,17 @@ def test_physics_contact_overflow_matches(V, orc):
     _physics_horizon(V, orc, sc, steps=3)
 
 
-def test_physics_uneven_and_empty_envs(V, orc):
-    """Ragged batch: 0, 1, 3, 40 and 70 bodies; more contacts than the shared
-    memory holds spill to global memory."""
-    nb = np.array([0, 1, 3, 40, 70], np.int32)
-    sc = S.generate(5, nb, 1234, kinds="mixed", res=64, substeps=4)
+@pytest.mark.parametrize("persistent", [False, True])
+def test_physics_uneven_and_empty_envs(V, orc, persistent):
+    """Ragged batch: 0, 1, 3, 40, 70 and 130 bodies; more contacts than the
+    shared memory holds spill to global memory.  Persistent: one work list
+    per size class (up to 32, up to 64 bodies on 128-thread CTAs, more on
+    512-thread CTAs)."""
+    nb = np.array([0, 1, 3, 40, 70, 130], np.int32)
+    sc = S.generate(6, nb, 1234, kinds="mixed", res=64, substeps=4)
     st, _, _ = orc.sim_step(sc, 40)
     sc = dataclasses.replace(sc, **{k: st[k] for k in ("pos", "quat", "vel", "angvel")})
-    _physics_horizon(V, orc, sc, steps=4)
+    _physics_horizon(V, orc, sc, steps=4, persistent=persistent)
 
 
 def test_physics_contact_spill_to_global(V, orc):
