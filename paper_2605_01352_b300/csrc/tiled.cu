@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScrat
         }
     }
     const bool vec = nx == 8 && ((reinterpret_cast<uintptr_t>(fr.depth + p0) & 15) == 0) &&
-                     ((reinterpret_cast<uintptr_t>(fr.rgb + 3 * p0) & 3) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(fr.rgb + 3 * p0) & 7) == 0) &&
                      (!fr.triid || (reinterpret_cast<uintptr_t>(fr.triid + p0) & 15) == 0);
     // the frame is not read again on the device: streaming (evict-first)
     // stores keep the L2 for the triangle records still to be read
@@ -426,15 +426,19 @@ __global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScrat
             __stcs(tp, make_uint4(tid[0], tid[1], tid[2], tid[3]));
             __stcs(tp + 1, make_uint4(tid[4], tid[5], tid[6], tid[7]));
         }
-        // 8 pixels = 24 bytes = 6 words, little endian r g b r | g b r g | b r g b | ...
-        unsigned int* r32 = reinterpret_cast<unsigned int*>(fr.rgb + 3 * p0);
+        // 8 pixels = 24 bytes = 6 words, little endian r g b r | g b r g | b r g b | ...,
+        // written as three 8-byte stores (the run starts 8-byte aligned)
+        uint32_t wd[6];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const uint32_t c0 = col[4 * h], c1 = col[4 * h + 1], c2 = col[4 * h + 2], c3 = col[4 * h + 3];
-            __stcs(r32 + 3 * h, (c0 & 0xFFFFFFu) | ((c1 & 0xFFu) << 24));
-            __stcs(r32 + 3 * h + 1, ((c1 >> 8) & 0xFFFFu) | ((c2 & 0xFFFFu) << 16));
-            __stcs(r32 + 3 * h + 2, ((c2 >> 16) & 0xFFu) | ((c3 & 0xFFFFFFu) << 8));
+            wd[3 * h] = (c0 & 0xFFFFFFu) | ((c1 & 0xFFu) << 24);
+            wd[3 * h + 1] = ((c1 >> 8) & 0xFFFFu) | ((c2 & 0xFFFFu) << 16);
+            wd[3 * h + 2] = ((c2 >> 16) & 0xFFu) | ((c3 & 0xFFFFFFu) << 8);
         }
+        uint2* r64 = reinterpret_cast<uint2*>(fr.rgb + 3 * p0);
+#pragma unroll
+        for (int q = 0; q < 3; q++) __stcs(r64 + q, make_uint2(wd[2 * q], wd[2 * q + 1]));
     } else {
 #pragma unroll
         for (int k = 0; k < 8; k++)
