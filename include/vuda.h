@@ -140,7 +140,7 @@ typedef struct {
  * environment and rasterises the band in shared memory.  TILED: one CTA per
  * camera sets up every triangle once into a device scratch area and bins it
  * into 16 x 16 tiles, then one warp per tile rasterises and resolves it
- * (needs cameras of at most 1024 tiles, and scratch of about
+ * (needs cameras of at most 2048 tiles, e.g. 640 x 480, and scratch of about
  * 120 bytes per triangle and camera, an upper bound of which only the
  * visible part is written).  AUTO: TILED where it applies and its scratch
  * fits (at most half of the free device memory, and within

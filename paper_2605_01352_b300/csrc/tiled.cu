@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kBT = 256;          // bin_kernel threads
 constexpr int kNarrowTiles = 9;   // records over more tiles go to the camera's wide list
-constexpr int kMaxTiles = 1024;   // tiles per camera the counting sort holds in shared memory
+constexpr int kMaxTiles = 2048;   // tiles per camera the counting sort holds in shared memory (640 x 480: 1200)
 constexpr int kLanePx = 64;       // unclipped bounding-box pixels up to which one lane rasterises a record
 constexpr int kTW = 8;            // tiles (warps) per tile_kernel CTA
 constexpr unsigned kFullMask = 0xffffffffu;
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __
         }
     }
     __syncthreads();
-    // list offsets: exclusive prefix sum of the tile counts (at most 4 tiles per thread)
+    // list offsets: exclusive prefix sum of the tile counts (at most kMaxTiles / kBT tiles per thread)
     const int per = (ntiles + kBT - 1) / kBT;
     const int i0 = threadIdx.x * per;
     int loc[kMaxTiles / kBT];

@@ -337,16 +337,20 @@ def _shoemake(st: Streams, mask=None):
 def generate(num_envs: int, bodies, seed: int, *, kinds: str = "spheres",
              res=64, cams_per_env: int = 1, substeps: int = 4, n_hull_meshes: int = 64,
              hull_tris=(500, 2000), sphere_r=(0.05, 0.1), box_h=(0.03, 0.1),
-             name: str = "", env_base: int = 0) -> Scene:
+             name: str = "", env_base: int = 0, height=None) -> Scene:
     """Build a seeded batch of environments.
 
     bodies: int (same count everywhere) or per-env int array.
     kinds: "spheres" | "mixed" (even index sphere, odd index box) | "hulls".
-    res: int or per-env int array (square cameras).
+    res: int or per-env int array: camera width (and height, unless given).
+    height: None (square cameras), or int / per-env int array of camera heights;
+    the 60 degree field of view is vertical.
     """
     E = num_envs
     nb = np.full(E, bodies, np.int32) if np.isscalar(bodies) else np.asarray(bodies, np.int32)
     resv = np.full(E, res, np.int32) if np.isscalar(res) else np.asarray(res, np.int32)
+    resh = resv.copy() if height is None else (np.full(E, height, np.int32) if np.isscalar(height)
+                                                else np.asarray(height, np.int32))
     body_off = np.concatenate([[0], np.cumsum(nb)]).astype(np.int32)
     B = int(body_off[-1])
     nmax = int(nb.max()) if E else 0
@@ -425,6 +429,7 @@ def generate(num_envs: int, bodies, seed: int, *, kinds: str = "spheres",
     cam_off = np.concatenate([[0], np.cumsum(ncam)]).astype(np.int32)
     C = int(cam_off[-1])
     cw = np.zeros(C, np.int32)
+    ch = np.zeros(C, np.int32)
     eye = np.zeros((C, 3), np.float32)
     rr, uu, ff = (np.zeros((C, 3), np.float32) for _ in range(3))
     fpy = np.zeros(C, np.float32)
@@ -433,11 +438,12 @@ def generate(num_envs: int, bodies, seed: int, *, kinds: str = "spheres",
     for e in range(E):
         for c in range(cams_per_env):
             i = cam_off[e] + c
-            key = (c, int(resv[e]))
+            key = (c, int(resh[e]))
             if key not in cache:
-                cache[key] = look_at(eyes[c % 2], (0.0, 0.0, 0.4), 60.0, int(resv[e]))
+                cache[key] = look_at(eyes[c % 2], (0.0, 0.0, 0.4), 60.0, int(resh[e]))
             eye[i], rr[i], uu[i], ff[i], fpy[i] = cache[key]
             cw[i] = resv[e]
+            ch[i] = resh[e]
     L = np.array([0.3, -0.5, 0.8], np.float64)
     L = (L / np.linalg.norm(L)).astype(np.float32)
 
@@ -449,7 +455,7 @@ def generate(num_envs: int, bodies, seed: int, *, kinds: str = "spheres",
         mesh_id=flat(mesh_id).astype(np.int32), mesh_scale=scale, albedo=albedo,
         mesh_vert_off=voff, mesh_verts=verts, mesh_tri_off=toff, mesh_tris=tris,
         ground_mesh=MESH_GROUND, ground_albedo=pack_rgb(GROUND_ALBEDO),
-        cam_off=cam_off, cam_w=cw, cam_h=cw.copy(), cam_eye=eye, cam_right=rr, cam_up=uu,
+        cam_off=cam_off, cam_w=cw, cam_h=ch, cam_eye=eye, cam_right=rr, cam_up=uu,
         cam_fwd=ff, cam_fpy=fpy, light=L, params=params, name=name)
 
 

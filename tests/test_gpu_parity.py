@@ -180,6 +180,17 @@ def test_render_ragged_tiles(V, orc, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
+def test_render_non_square_cameras(V, orc, path):
+    """A 640 x 480 data-generation camera (1200 tiles) beside non-square
+    cameras narrower and taller than wide; the field of view is vertical."""
+    sc = S.generate(3, np.array([10, 6, 8]), 505, kinds="mixed", res=np.array([640, 96, 33]),
+                    height=np.array([480, 40, 70]), substeps=4)
+    assert list(sc.cam_w) == [640, 96, 33] and list(sc.cam_h) == [480, 40, 70]
+    st, _, _ = orc.sim_step(sc, 30)
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], path=path)
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_render_near_plane_flags(V, orc, path):
     sc = S.custom([dict(type="sphere", r=0.1, pos=(0.0, -3.0, 1.5)),
                    dict(type="box", h=(0.05, 0.05, 0.05), pos=(0.1, 0.0, 0.05))], res=64)
