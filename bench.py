@@ -251,10 +251,11 @@ def run_reference(args):
     }), flush=True)
 
 
-def serving_bench(V, S, njobs: int, nreq: int):
+def serving_bench(V, S, njobs: int, nreq: int, load: float = 0.8, burst: int = 16):
     """Serving workload (jobs of 16-1024 envs with 4-256 bodies and 64-256 px
-    cameras): capacity from a burst, then Poisson arrivals at 80 % of it, for
-    continuous batching and for a serialized FIFO (one request at a time)."""
+    cameras): capacity from a burst of `burst` requests per job, then Poisson
+    arrivals at `load` times it, for continuous batching and for a serialized
+    FIFO (one request at a time)."""
     import torch
     jobs = S.cfg5_jobs(njobs)
     free, _ = torch.cuda.mem_get_info()
@@ -268,12 +269,12 @@ def serving_bench(V, S, njobs: int, nreq: int):
         for i in ids:                       # admit and warm up
             srv.submit(i)
         srv.wait_all(len(ids), timeout_s=600)
-        if rate_hz <= 0:                    # capacity: a burst of 4 requests per job
+        if rate_hz <= 0:                    # capacity: a burst of requests from every job
             t = time.perf_counter()
-            for _ in range(4):
+            for _ in range(burst):
                 for i in ids:
                     srv.submit(i)
-            res = srv.wait_all(4 * len(ids), timeout_s=600)
+            res = srv.wait_all(burst * len(ids), timeout_s=600)
             dt = time.perf_counter() - t
             srv.close()
             return len(res) / dt
@@ -303,11 +304,12 @@ def serving_bench(V, S, njobs: int, nreq: int):
 
     cap = run(False, 0.0)
     cap_fifo = run(True, 0.0)
-    rate = 0.8 * cap
+    rate = load * cap
     cb = run(False, rate)
     fifo = run(True, rate)
     return {"workload": "%d jobs of the serving recipe (16-1024 envs, 4-256 bodies, 64-256 px), %d Poisson requests "
-                        "at 80%% of the continuous-batching capacity; HBM budget 60%% of free memory" % (njobs, nreq),
+                        "at %d%% of the continuous-batching capacity; HBM budget 60%% of free memory"
+                        % (njobs, nreq, round(100 * load)),
             "capacity_requests_per_s": cap, "capacity_fifo_requests_per_s": cap_fifo, "arrival_rate_hz": rate,
             "continuous_batching": cb, "serialized_fifo": fifo}
 
