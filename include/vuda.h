@@ -133,16 +133,19 @@ typedef struct {
                                      camera bands) largest first from an atomic counter -- for batches of
                                      uneven environments; 0: one CTA per item */
     int32_t render_path;          /* VUDA_RENDER_AUTO / _BAND / _TILED (see below) */
+    int32_t tile_size;            /* tiled path: tile edge, 8, 16 or 32 pixels (0: 16) */
+    int32_t tile_bin_limit;       /* tiled path: most tile lists one triangle joins; triangles over more
+                                     tiles go to the camera's wide list, read by every tile (1..64, 0: 9) */
 } vuda_env_opts;
 
 /* Render paths (identical frames; they differ in how work is split):
  * BAND: one CTA per band of rows of a camera sets up every triangle of the
  * environment and rasterises the band in shared memory.  TILED: one CTA per
  * camera sets up every triangle once into a device scratch area and bins it
- * into 16 x 16 tiles, then one warp per tile rasterises and resolves it
- * (needs cameras of at most 2048 tiles, e.g. 640 x 480, and scratch of about
- * 120 bytes per triangle and camera, an upper bound of which only the
- * visible part is written).  AUTO: TILED where it applies and its scratch
+ * into tile_size x tile_size tiles, then one warp per tile rasterises and
+ * resolves it (needs cameras of at most 2048 tiles, e.g. 640 x 480 at 16 x 16,
+ * and scratch of about 84 + 4 tile_bin_limit bytes per triangle and camera, an
+ * upper bound of which only the visible part is written).  AUTO: TILED where it applies and its scratch
  * fits (at most half of the free device memory, and within
  * hbm_budget_bytes), else BAND.
  * The render work-list launches of VUDA_COSCHED_SHARED and of the serving
@@ -160,6 +163,7 @@ typedef struct {
     int64_t device_bytes;         /* device memory held by the batch */
     int64_t steps_enqueued;       /* physics steps enqueued so far */
     int32_t render_path;          /* VUDA_RENDER_BAND or VUDA_RENDER_TILED: the path the batch renders with */
+    int32_t tile_size, tile_bin_limit;   /* the tiled path's raster parameters (0 on the band path) */
 } vuda_env_info;
 
 /* Caller-owned device output buffers, concatenated per camera in cam order
@@ -282,8 +286,19 @@ vuda_status vuda_pipeline_capture(vuda_env_t env, int32_t steps_per_graph, const
                                   vuda_stream_t stream);
 vuda_status vuda_pipeline_release_graph(vuda_env_t env);
 
+/* Batching layer, raster parameters (the paper's renderer is Vulkan's and has
+ * no such knobs; these are what the autotuner below chooses between).
+ * Raster parameters of a batch on the tiled render path: tile edge (8, 16 or
+ * 32 pixels) and bin limit (1..64; see vuda_env_opts).  Reallocates the
+ * path's tile lists (VUDA_ERR_INVALID on the band path, for cameras of more
+ * than 2048 tiles, or when the lists would exceed half of the free device
+ * memory; the batch keeps its previous parameters then).  Frames do not
+ * depend on the choice.  Drops a captured graph.  Synchronous. */
+vuda_status vuda_set_tiling(vuda_env_t env, int32_t tile_size, int32_t bin_limit);
+
 /* Autotuner: measures the loop under candidate configurations -- render band
- * height (16/32/64/128 rows), serialized / co-scheduled on shared SMs /
+ * height (16/32/64/128 rows) on the band path, or tile size (8/16/32) x bin
+ * limit (4/9/16) on the tiled path, serialized / co-scheduled on shared SMs /
  * co-scheduled on disjoint partitions of 1/4, 1/2 and 3/4 of the SMs /
  * co-scheduled with per-SM quotas (every pair that fits one SM, the most sim
  * CTAs for each render count), and CUDA graph replay -- and leaves the batch
@@ -301,6 +316,7 @@ typedef struct {
     int32_t trials, from_cache;
     int32_t sim_ctas_per_sm, render_ctas_per_sm;  /* SHARED winner's quotas */
     int32_t priority;                             /* the winner's stream priority */
+    int32_t tile_size, tile_bin_limit;            /* tiled path: the chosen raster parameters (0: band path) */
 } vuda_tune_result;
 vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda_frame* ring, vuda_tune_result* out);
 

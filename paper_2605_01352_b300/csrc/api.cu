@@ -146,6 +146,98 @@ void free_env(vuda_env* env) {
     env->allocs.clear();
 }
 
+// Free one allocation of the batch (nbytes: its size, for the byte count).
+void dfree(vuda_env* env, void* p, int64_t nbytes) {
+    if (!p) return;
+    for (size_t i = 0; i < env->allocs.size(); i++)
+        if (env->allocs[i] == p) {
+            cudaFree(p);
+            env->allocs.erase(env->allocs.begin() + (std::ptrdiff_t)i);
+            env->bytes -= nbytes;
+            return;
+        }
+}
+
+// Layout of the tiled render path for tile size `tile` and bin limit `nlim`:
+// the per-camera records of bin_kernel, the raster work items of
+// tiled_tiles_per_item(tile) tiles, and the scratch element counts.
+struct TiledPlan {
+    std::vector<TileItem> cams, items;
+    int64_t nrec = 0, nent = 0, ntoff = 0;
+    bool fits = true;   // every camera within tiled_max_tiles() tiles
+    int64_t bytes() const {
+        return nrec * (int64_t)(tiled_record_bytes() + 4) + nent * 4 + ntoff * 4 +
+               (int64_t)(cams.size() + items.size()) * (int64_t)sizeof(TileItem);
+    }
+};
+
+TiledPlan plan_tiled(const vuda_env* env, int tile, int nlim) {
+    TiledPlan pl;
+    const int C = env->C;
+    pl.cams.resize(C);
+    const int tpi = tiled_tiles_per_item(tile);
+    for (int c = 0; c < C; c++) {
+        const int e = env->h_cam_env[c];
+        const int64_t tc = env->h_env_tri_base[e + 1] - env->h_env_tri_base[e];
+        const int tx = (env->h_cam_w[c] + tile - 1) / tile;
+        const int ntl = tx * ((env->h_cam_h[c] + tile - 1) / tile);
+        if (ntl > tiled_max_tiles()) pl.fits = false;
+        TileItem ti{};
+        ti.cam = c;
+        ti.W = env->h_cam_w[c];
+        ti.H = env->h_cam_h[c];
+        ti.tiles_x = tx;
+        ti.ntiles = ntl;
+        ti.env = e;
+        ti.rec_base = pl.nrec;
+        ti.ent_base = pl.nent;
+        ti.toff_base = pl.ntoff;
+        ti.pix_off = env->cam_pix_off[c];
+        ti.col_base = env->h_env_tri_base[e];
+        pl.cams[c] = ti;
+        for (int t0 = 0; t0 < ntl; t0 += tpi) {
+            ti.tile0 = t0;
+            pl.items.push_back(ti);
+        }
+        pl.nrec += tc;
+        pl.nent += tc * nlim;
+        pl.ntoff += ntl + 2;
+    }
+    return pl;
+}
+
+// Allocate the tiled path's scratch and work items for plan `pl` (any
+// previous ones freed first; records and wide lists keep their size).
+vuda_status alloc_tiled(vuda_env* env, const TiledPlan& pl, int tile, int nlim) {
+    TileScratch& ts = env->ts;
+    vuda_status s = VUDA_OK;
+    if (!ts.rec) {
+        uint8_t* rec = nullptr;
+        s = dalloc(env, &rec, (size_t)pl.nrec * tiled_record_bytes());
+        ts.rec = rec;
+        if (s == VUDA_OK) s = dalloc(env, &ts.wide, (size_t)pl.nrec);
+    }
+    dfree(env, ts.ent, std::max<int64_t>(env->tiled_nent, 1) * 4);
+    dfree(env, ts.toff, std::max<int64_t>(env->tiled_ntoff, 1) * 4);
+    dfree(env, env->tcams, std::max<int64_t>(env->C, 1) * (int64_t)sizeof(TileItem));
+    dfree(env, env->titems, std::max<int64_t>(env->ntitems, 1) * (int64_t)sizeof(TileItem));
+    ts.ent = nullptr;
+    ts.toff = nullptr;
+    env->tcams = env->titems = nullptr;
+    env->ntitems = 0;
+    if (s == VUDA_OK) s = dalloc(env, &ts.ent, (size_t)pl.nent);
+    if (s == VUDA_OK) s = dalloc(env, &ts.toff, (size_t)pl.ntoff);
+    if (s == VUDA_OK) s = upload(env, &env->tcams, pl.cams.data(), pl.cams.size());
+    if (s == VUDA_OK) s = upload(env, &env->titems, pl.items.data(), pl.items.size());
+    if (s != VUDA_OK) return s;
+    env->tiled_nent = pl.nent;
+    env->tiled_ntoff = pl.ntoff;
+    env->ntitems = (int)pl.items.size();
+    env->tile_size = tile;
+    env->bin_limit = nlim;
+    return VUDA_OK;
+}
+
 void destroy_events(vuda_env* env) {
     {
         ScopedCtx g(env->c_sim);
@@ -372,11 +464,11 @@ vuda_status set_band_rows(vuda_env* env, int br) {
 }
 
 struct TuneKey {
-    int E, B, C, max_bodies, max_w, max_h, persistent;
+    int E, B, C, max_bodies, max_w, max_h, persistent, tiled;
     int64_t T;
     bool operator<(const TuneKey& o) const {
-        return std::tie(E, B, C, max_bodies, max_w, max_h, persistent, T) <
-               std::tie(o.E, o.B, o.C, o.max_bodies, o.max_w, o.max_h, o.persistent, o.T);
+        return std::tie(E, B, C, max_bodies, max_w, max_h, persistent, tiled, T) <
+               std::tie(o.E, o.B, o.C, o.max_bodies, o.max_w, o.max_h, o.persistent, o.tiled, o.T);
     }
 };
 std::mutex g_tune_mu;
@@ -386,7 +478,7 @@ std::map<TuneKey, vuda_tune_result> g_tune_cache;
 
 extern "C" {
 
-int32_t vuda_abi_version(void) { return 2; }
+int32_t vuda_abi_version(void) { return 3; }
 
 vuda_status vuda_env_estimate_bytes(const vuda_scene* scene, const vuda_sim_params* params, int64_t* bytes) {
     return env_estimate_bytes(scene, params, bytes);
@@ -606,43 +698,23 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         delete env;
         return invalid("render_path must be VUDA_RENDER_AUTO, _BAND or _TILED");
     }
-    std::vector<int64_t> rec_base(C + 1, 0), ent_base(C + 1, 0), toff_base(C + 1, 0);
-    std::vector<TileItem> tcams(C), titems;
-    bool can_tile = C > 0;
-    const int tpi = tiled_tiles_per_item();
-    for (int c = 0; c < C; c++) {
-        const int e = cam_env[c];
-        const int64_t tc = env_tri_base[e + 1] - env_tri_base[e];
-        const int tx = (sc->cam_w[c] + 15) / 16;
-        const int ntl = tx * ((sc->cam_h[c] + 15) / 16);
-        if (ntl > tiled_max_tiles()) can_tile = false;
-        rec_base[c + 1] = rec_base[c] + tc;
-        ent_base[c + 1] = ent_base[c] + tc * tiled_narrow_tiles();
-        toff_base[c + 1] = toff_base[c] + ntl + 2;
-        TileItem ti{};
-        ti.cam = c;
-        ti.W = sc->cam_w[c];
-        ti.H = sc->cam_h[c];
-        ti.tiles_x = tx;
-        ti.ntiles = ntl;
-        ti.env = e;
-        ti.rec_base = rec_base[c];
-        ti.ent_base = ent_base[c];
-        ti.toff_base = toff_base[c];
-        ti.pix_off = pix[c];
-        ti.col_base = env_tri_base[e];
-        tcams[c] = ti;
-        for (int t0 = 0; t0 < ntl; t0 += tpi) {
-            ti.tile0 = t0;
-            titems.push_back(ti);
-        }
+    const int tile = o.tile_size ? o.tile_size : 16;
+    const int nlim = o.tile_bin_limit ? o.tile_bin_limit : tiled_default_bin_limit();
+    if (tile != 8 && tile != 16 && tile != 32) {
+        delete env;
+        return invalid("tile_size must be 0, 8, 16 or 32");
     }
-    const int64_t tile_bytes = rec_base[C] * (int64_t)(tiled_record_bytes() + 4) + ent_base[C] * 4 +
-                               toff_base[C] * 4 + ((int64_t)C + (int64_t)titems.size()) * (int64_t)sizeof(TileItem);
+    if (nlim < 1 || nlim > tiled_max_bin_limit()) {
+        delete env;
+        return invalid("tile_bin_limit must be 0 or 1.." + std::to_string(tiled_max_bin_limit()));
+    }
+    const TiledPlan tplan = plan_tiled(env, tile, nlim);
+    const bool can_tile = C > 0 && tplan.fits;
+    const int64_t tile_bytes = tplan.bytes();
     if (o.render_path == VUDA_RENDER_TILED && !can_tile) {
         delete env;
         return invalid("tiled render path: a camera has more than " + std::to_string(tiled_max_tiles()) +
-                       " tiles of 16 x 16 pixels");
+                       " tiles of " + std::to_string(tile) + " x " + std::to_string(tile) + " pixels");
     }
     // the scratch is an upper bound (only records that cover a pixel centre are
     // written): take the tiled path while it stays within half of the free
@@ -726,18 +798,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
         if (s == VUDA_OK && need_spill)
             s = dalloc(env, &d.spill, (size_t)std::max<int64_t>(spill_off[E], 1) * kContactStride);
     }
-    if (s == VUDA_OK && env->tiled) {
-        TileScratch& ts = env->ts;
-        uint8_t* rec = nullptr;
-        s = dalloc(env, &rec, (size_t)rec_base[C] * tiled_record_bytes());
-        ts.rec = rec;
-        if (s == VUDA_OK) s = dalloc(env, &ts.wide, (size_t)rec_base[C]);
-        if (s == VUDA_OK) s = dalloc(env, &ts.ent, (size_t)ent_base[C]);
-        if (s == VUDA_OK) s = dalloc(env, &ts.toff, (size_t)toff_base[C]);
-        if (s == VUDA_OK) s = upload(env, &env->tcams, tcams.data(), tcams.size());
-        if (s == VUDA_OK) s = upload(env, &env->titems, titems.data(), titems.size());
-        env->ntitems = (int)titems.size();
-    }
+    if (s == VUDA_OK && env->tiled) s = alloc_tiled(env, tplan, tile, nlim);
     if (s == VUDA_OK && E) {
         if (cudaMemset(d.flags, 0, sizeof(uint32_t) * E) != cudaSuccess ||
             cudaMemset(d.ncontacts, 0, sizeof(int32_t) * E) != cudaSuccess)
@@ -812,6 +873,8 @@ vuda_status vuda_env_info_get(vuda_env_t env, vuda_env_info* out) {
     out->device_bytes = env->bytes;
     out->steps_enqueued = env->steps;
     out->render_path = env->tiled ? VUDA_RENDER_TILED : VUDA_RENDER_BAND;
+    out->tile_size = env->tiled ? env->tile_size : 0;
+    out->tile_bin_limit = env->tiled ? env->bin_limit : 0;
     return VUDA_OK;
 }
 
@@ -864,6 +927,7 @@ static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, c
     const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
     if (env->tiled && !shared)
         e = launch_render_tiled(env->d, env->d.pose[slot], *fr, env->ts, env->tcams, env->titems, env->ntitems,
+                                env->tile_size, env->bin_limit,
                                 stream);
     else if (env->persistent || shared)
         e = launch_render_list(env->d_desc, env->ren_items[slot], env->nitems, env->counters + 1,
@@ -1254,6 +1318,40 @@ vuda_status vuda_wait(vuda_env_t env, int32_t phase) {
     return VUDA_OK;
 }
 
+vuda_status vuda_set_tiling(vuda_env_t env, int32_t tile, int32_t nlim) {
+    if (!env) return invalid("null env");
+    if (!env->tiled) return invalid("the batch renders on the band path");
+    if (tile != 8 && tile != 16 && tile != 32) return invalid("tile_size must be 8, 16 or 32");
+    if (nlim < 1 || nlim > tiled_max_bin_limit())
+        return invalid("bin limit must be 1.." + std::to_string(tiled_max_bin_limit()));
+    if (tile == env->tile_size && nlim == env->bin_limit) return VUDA_OK;
+    const TiledPlan pl = plan_tiled(env, tile, nlim);
+    if (!pl.fits)
+        return invalid("a camera has more than " + std::to_string(tiled_max_tiles()) + " tiles of " +
+                       std::to_string(tile) + " x " + std::to_string(tile) + " pixels");
+    const int64_t item = (int64_t)sizeof(TileItem);
+    const int64_t old_b = env->tiled_nent * 4 + env->tiled_ntoff * 4 + ((int64_t)env->C + env->ntitems) * item;
+    const int64_t new_b = pl.nent * 4 + pl.ntoff * 4 + (int64_t)(pl.cams.size() + pl.items.size()) * item;
+    // everything enqueued with the present lists finishes before they are freed
+    vuda_status s = vuda_wait(env, 0);
+    if (s == VUDA_OK) s = vuda_wait(env, 1);
+    if (s == VUDA_OK) CK(cudaDeviceSynchronize());
+    if (s != VUDA_OK) return s;
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    if (new_b - old_b > (int64_t)(free_b / 2)) return invalid("tile lists would exceed half of the free device memory");
+    drop_graph(env);
+    const int old_tile = env->tile_size, old_nlim = env->bin_limit;
+    s = alloc_tiled(env, pl, tile, nlim);
+    if (s != VUDA_OK) {
+        // put the previous lists back; failing that, the batch renders on the band path
+        const std::string why = g_err;
+        if (alloc_tiled(env, plan_tiled(env, old_tile, old_nlim), old_tile, old_nlim) != VUDA_OK) env->tiled = 0;
+        set_error(why);
+    }
+    return s;
+}
+
 vuda_status vuda_env_get_state(vuda_env_t env, const vuda_state* out) {
     if (!env || !out) return invalid("null argument");
     CK(cudaDeviceSynchronize());
@@ -1331,7 +1429,7 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
     vuda_tune_opts o{};
     if (opts) o = *opts;
     const int K = o.steps > 0 ? o.steps : 6;
-    TuneKey key{env->E, env->B, env->C, env->max_bodies, env->max_w, env->max_h, env->persistent, env->T};
+    TuneKey key{env->E, env->B, env->C, env->max_bodies, env->max_w, env->max_h, env->persistent, env->tiled, env->T};
     vuda_tune_result best{};
     bool cached = false;
     if (o.use_cache) {
@@ -1373,18 +1471,38 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
     };
     if (!cached) {
         float ms = 0.0f, best_ms = 1e30f;
-        // 1. band height, serialized
+        // 1. raster parameters, serialized: band height on the band path,
+        // tile size x bin limit on the tiled path (candidates whose lists do
+        // not fit are skipped)
         s = vuda_coschedule_reset(env);
-        const int cands[] = {16, 32, 64, 128};
         int best_br = env->band_rows;
-        for (int br : cands) {
-            if (s != VUDA_OK) break;
-            if (br > std::max(16, env->max_h) || render_smem_for(br, env->max_w) > 227 * 1024) continue;
-            s = set_band_rows(env, br);
-            if (s == VUDA_OK) s = measure(&ms);
-            if (s == VUDA_OK && ms < best_ms) { best_ms = ms; best_br = br; }
+        if (env->tiled) {
+            int best_t = env->tile_size, best_n = env->bin_limit;
+            const int tiles[] = {16, 8, 32}, lims[] = {9, 4, 16};
+            for (int t : tiles)
+                for (int n : lims) {
+                    if (s != VUDA_OK) break;
+                    if (vuda_set_tiling(env, t, n) != VUDA_OK) {
+                        if (!env->tiled) s = VUDA_ERR_OOM;
+                        continue;
+                    }
+                    s = measure(&ms);
+                    if (s == VUDA_OK && ms < best_ms) { best_ms = ms; best_t = t; best_n = n; }
+                }
+            if (s == VUDA_OK) s = vuda_set_tiling(env, best_t, best_n);
+            best.tile_size = best_t;
+            best.tile_bin_limit = best_n;
+        } else {
+            const int cands[] = {16, 32, 64, 128};
+            for (int br : cands) {
+                if (s != VUDA_OK) break;
+                if (br > std::max(16, env->max_h) || render_smem_for(br, env->max_w) > 227 * 1024) continue;
+                s = set_band_rows(env, br);
+                if (s == VUDA_OK) s = measure(&ms);
+                if (s == VUDA_OK && ms < best_ms) { best_ms = ms; best_br = br; }
+            }
+            if (s == VUDA_OK) s = set_band_rows(env, best_br);
         }
-        if (s == VUDA_OK) s = set_band_rows(env, best_br);
         best.band_rows = best_br;
         best.ms_per_step_serialized = best_ms;
         best.cosched_mode = 0;
@@ -1448,7 +1566,7 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     } else {
-        s = set_band_rows(env, best.band_rows);
+        s = best.tile_size ? vuda_set_tiling(env, best.tile_size, best.tile_bin_limit) : set_band_rows(env, best.band_rows);
         if (s == VUDA_OK)
             s = apply_mode(best.cosched_mode, best.sim_sms, best.sim_ctas_per_sm, best.render_ctas_per_sm, best.priority);
         if (s == VUDA_OK && best.graph_steps) {

@@ -61,6 +61,8 @@ struct vuda_env {
     int sim_grid_sh = 0, ren_grid_sh = 0;
     // tiled render path: scratch and work items (camera, first tile)
     int tiled = 0;
+    int tile_size = 16, bin_limit = 9;   // tile edge in pixels; most tile lists a triangle joins
+    int64_t tiled_nent = 0, tiled_ntoff = 0;   // elements of ts.ent and ts.toff
     vuda::TileScratch ts{};
     vuda::TileItem* tcams = nullptr;    // [C]
     vuda::TileItem* titems = nullptr;   // [ntitems]

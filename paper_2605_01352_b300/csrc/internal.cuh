@@ -170,10 +170,10 @@ int render_vcap();
 cudaError_t launch_shade(const DevBatch& b, const float* pose, cudaStream_t stream);
 
 // Scratch of the tiled render path (tiled.cu), per camera c of env e with
-// T_e triangles and n_c 16 x 16 tiles: records [rec_base, + T_e) of
-// tiled_record_bytes() each, wide list [rec_base, + T_e), tile lists
-// [ent_base, + kNarrowTiles T_e), offsets [toff_base, + n_c + 2) (n_c + 1
-// list offsets, then the wide-list length).
+// T_e triangles and n_c tiles (of the batch's tile size): records
+// [rec_base, + T_e) of tiled_record_bytes() each, wide list [rec_base, + T_e),
+// tile lists [ent_base, + bin_limit T_e), offsets [toff_base, + n_c + 2)
+// (n_c + 1 list offsets, then the wide-list length).
 struct TileScratch {
     void* rec;
     uint32_t* ent;
@@ -191,14 +191,18 @@ struct __align__(16) TileItem {
     long long pix_off;            // 64: first pixel of the camera in the frame
     long long col_base;           // 72: first triangle of the environment in the colour table
 };
-int tiled_max_tiles();        // tiles per camera the path supports
-int tiled_narrow_tiles();     // list entries per triangle at most
-int tiled_tiles_per_item();   // tiles per raster work item
+int tiled_max_tiles();               // tiles per camera the path supports
+int tiled_default_bin_limit();       // list entries per triangle at most, by default
+int tiled_max_bin_limit();
+int tiled_tiles_per_item(int tile);  // tiles per raster work item for tile size 8, 16 or 32
 size_t tiled_record_bytes();
-// Set up, shade and bin every camera, then rasterise and resolve the work
-// items (camera, first tile) of tiled_tiles_per_item() tiles each.
+// Set up, shade and bin every camera into tile x tile tiles (8, 16, 32),
+// listing a triangle under at most nlim tiles (else on the wide list), then
+// rasterise and resolve the work items (camera, first tile) of
+// tiled_tiles_per_item(tile) tiles each.
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
-                                const TileItem* cams, const TileItem* items, int nitems, cudaStream_t stream);
+                                const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim,
+                                cudaStream_t stream);
 
 void set_error(const std::string& s);
 // Device bytes a batch will hold once created (an upper estimate).

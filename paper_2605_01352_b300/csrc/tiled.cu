@@ -9,16 +9,22 @@
 //   image, edge functions and top-left bits -- and write it as an 80-byte
 //   record to the camera's scratch area in global memory (read back by the
 //   raster kernel from L2).  A counting sort in shared memory lists each
-//   record that overlaps at most kNarrowTiles 16 x 16 tiles under every one
-//   of them; records over more tiles go to one wide list of the camera.
-//   tile_kernel, one warp per tile and no CTA barriers: records whose
-//   unclipped bounding box has at most kLanePx pixel centres are rasterised
-//   one per lane with 32-bit edge functions (exact for boxes that small)
-//   into the warp's 16 x 16 key buffer in shared memory (atomicMin); larger
-//   records and the wide list go through the warp-wide pass, in which every
-//   lane keeps the keys of its run of 8 pixels in registers.  The tile is
-//   then resolved from min(register key, shared key) to RGB8, FP32 depth and
-//   u32 triangle id.
+//   record that overlaps at most `nlim` (the bin limit) T x T tiles under
+//   every one of them; records over more tiles go to one wide list of the
+//   camera.
+//   tile_kernel, one warp per tile and no CTA barriers.  The warp covers its
+//   tile in strips of at most 256 pixels (8 x 8 tiles: one strip, 2 pixels a
+//   lane; 16 x 16: one strip, 8 a lane; 32 x 32: four 32 x 8 strips, 8 a
+//   lane), each strip a pass over the tile's lists: records whose unclipped
+//   bounding box has at most kLanePx pixel centres are rasterised one per
+//   lane with 32-bit edge functions (exact for boxes that small) into the
+//   warp's strip key buffer in shared memory (atomicMin); larger records and
+//   the wide list go through the warp-wide pass, in which every lane keeps
+//   the keys of its run of pixels in registers.  The strip is then resolved
+//   from min(register key, shared key) to RGB8, FP32 depth and u32 triangle
+//   id.
+// The tile size T (8, 16, 32) and the bin limit are the raster parameters
+// the autotuner chooses between; every choice gives the same frames.
 // Coverage rule, depth and key are those of the band kernel (integer edge
 // functions at pixel centres with the top-left rule, depth
 // area2 / (E0/z0 + E1/z1 + E2/z2), minimum of depth_bits << 32 | id), and the
@@ -35,10 +41,22 @@ namespace vuda {
 namespace {
 
 constexpr int kBT = 256;          // bin_kernel threads
-constexpr int kNarrowTiles = 9;   // records over more tiles go to the camera's wide list
+constexpr int kNarrowTiles = 9;   // default bin limit: records over more tiles go to the camera's wide list
+constexpr int kMaxBinLimit = 64;  // largest bin limit accepted
 constexpr int kMaxTiles = 2048;   // tiles per camera the counting sort holds in shared memory (640 x 480: 1200)
 constexpr int kLanePx = 64;       // unclipped bounding-box pixels up to which one lane rasterises a record
-constexpr int kTW = 8;            // tiles (warps) per tile_kernel CTA
+
+// Geometry of one warp's T x T tile: strips of SH rows, R pixels per lane
+// (LPR lanes per strip row), TW tiles (warps) per tile_kernel CTA.
+template <int T>
+struct TileGeom {
+    static constexpr int SH = T * T > 256 ? 256 / T : T;
+    static constexpr int R = T * SH / 32;
+    static constexpr int LPR = T / R;
+    static constexpr int STRIPS = T / SH;
+    static constexpr int TW = 8;
+    static_assert(LPR * SH == 32 && STRIPS * SH == T, "tile geometry");
+};
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr unsigned kSmallBit = 8u;  // TriRec::tl bit: the record takes the per-lane path
 
@@ -114,8 +132,9 @@ __device__ __forceinline__ int cta_excl_scan(int v, int* wsum, int& total) {
     return off + x - v;
 }
 
+template <int T>
 __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts,
-                                                  const TileItem* __restrict__ cams) {
+                                                  const TileItem* __restrict__ cams, int nlim) {
     __shared__ int vX[kVertexCache], vY[kVertexCache], vflag[kVertexCache];
     __shared__ float viz[kVertexCache];
     __shared__ float vW[kVertexCache][3];   // world positions, for the flat colours
@@ -215,8 +234,8 @@ __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __
                 const uint32_t alb = bi < 0 ? b.ground_albedo : __ldg(b.albedo + b0 + bi);
                 colors[g.id] = flat_color(vW[i0], vW[i1], vW[i2], alb, b.light);
             }
-            const int tx0 = px0 / kTile, tx1 = px1 / kTile, ty0 = py0 / kTile, ty1 = py1 / kTile;
-            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kNarrowTiles) {
+            const int tx0 = px0 / T, tx1 = px1 / T, ty0 = py0 / T, ty1 = py1 / T;
+            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= nlim) {
                 for (int ty = ty0; ty <= ty1; ty++)
                     for (int tx = tx0; tx <= tx1; tx++) atomicAdd(&s_cnt[ty * tiles_x + tx], 1);
             } else {
@@ -254,8 +273,8 @@ __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __
         const int2 bb = *reinterpret_cast<const int2*>(reinterpret_cast<const char*>(rec + r) + 64);
         const int px0 = (short)(bb.x & 0xffff), px1 = bb.x >> 16;
         const int py0 = (short)(bb.y & 0xffff), py1 = bb.y >> 16;
-        const int tx0 = px0 / kTile, tx1 = px1 / kTile, ty0 = py0 / kTile, ty1 = py1 / kTile;
-        if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= kNarrowTiles) {
+        const int tx0 = px0 / T, tx1 = px1 / T, ty0 = py0 / T, ty1 = py1 / T;
+        if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= nlim) {
             for (int ty = ty0; ty <= ty1; ty++)
                 for (int tx = tx0; tx <= tx1; tx++) ent[atomicAdd(&s_cnt[ty * tiles_x + tx], 1)] = (uint32_t)r;
         }
@@ -264,13 +283,15 @@ __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __
 }
 
 // One lane rasterises a small record over the pixels [x0, x1] x [y0, y1] of
-// its tile (origin tx0, ty0) into the warp's shared key buffer.  The record's
+// its strip (origin tx0, sy0; rows of T keys) into the warp's shared key
+// buffer.  The record's
 // unclipped bounding box has at most kLanePx pixel centres, so its vertex
 // spans and |A|, |B| stay below 65 x 256 < 2^14.1 and every edge value at a
 // pixel centre of the box (or one step past it) below 2^30: 32-bit integers
 // hold them exactly, and their float conversions are the correctly rounded
 // ones.
-__device__ __forceinline__ void lane_raster(const TriRec& t, int x0, int x1, int y0, int y1, int tx0, int ty0,
+template <int T>
+__device__ __forceinline__ void lane_raster(const TriRec& t, int x0, int x1, int y0, int y1, int tx0, int sy0,
                                             unsigned long long* sk) {
     const long long cx = 256LL * x0 + 128, cy = 256LL * y0 + 128;
     int R0 = (int)((long long)t.A[0] * cx + (long long)t.B[0] * cy + t.C[0]);
@@ -281,7 +302,7 @@ __device__ __forceinline__ void lane_raster(const TriRec& t, int x0, int x1, int
     const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
     for (int py = y0; py <= y1; py++) {
         int E0 = R0, E1 = R1, E2 = R2;
-        unsigned long long* row = sk + (py - ty0) * kTile - tx0;
+        unsigned long long* row = sk + (py - sy0) * T - tx0;
         for (int px = x0; px <= x1; px++) {
             if ((E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) && (E2 > 0 || (E2 == 0 && tl2))) {
                 const float den =
@@ -299,9 +320,11 @@ __device__ __forceinline__ void lane_raster(const TriRec& t, int x0, int x1, int
     }
 }
 
-// Warp-wide pass of one record over the tile: the lane tests its run of nx
-// pixels (row y, columns xs ..) with 64-bit edge functions and keeps the
-// minimum keys in registers.  The record address is the same in all lanes.
+// Warp-wide pass of one record over the strip: the lane tests its run of
+// nx <= R pixels (row y, columns xs ..) with 64-bit edge functions and keeps
+// the minimum keys in registers.  The record address is the same in all
+// lanes.
+template <int R>
 __device__ __forceinline__ void warp_pass(const TriRec* __restrict__ p, int y, int xs, int nx,
                                           unsigned long long* key) {
     const TriRec t = load_rec(p);
@@ -318,7 +341,7 @@ __device__ __forceinline__ void warp_pass(const TriRec* __restrict__ p, int y, i
     if ((E0 < 0 && E0 + m * d0 < 0) || (E1 < 0 && E1 + m * d1 < 0) || (E2 < 0 && E2 + m * d2 < 0)) return;
     const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
+    for (int k = 0; k < R; k++) {
         if (k < nx && (E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) &&
             (E2 > 0 || (E2 == 0 && tl2))) {
             const float den = (i64_to_f32(E0) * t.iz[0] + i64_to_f32(E1) * t.iz[1]) + i64_to_f32(E2) * t.iz[2];
@@ -332,12 +355,91 @@ __device__ __forceinline__ void warp_pass(const TriRec* __restrict__ p, int y, i
     }
 }
 
+// Resolve a lane's run of nx <= R pixels starting at frame pixel p0 from
+// its keys to depth, triangle id and RGB8.  Full runs go out as streaming
+// vector stores (the frame is not read again on the device, and evict-first
+// stores keep the L2 for the triangle records still to be read).
+template <int R>
+__device__ __forceinline__ void resolve_run(const unsigned long long* key, int nx, int64_t p0,
+                                            const uint32_t* __restrict__ colors, const vuda_frame& fr) {
+    float d[R];
+    uint32_t tid[R], col[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+        const unsigned long long kk = key[k];
+        if (kk == ~0ULL) {
+            d[k] = 0.0f;
+            tid[k] = 0xFFFFFFFFu;
+            col[k] = 0u;
+        } else {
+            tid[k] = (uint32_t)(kk & 0xFFFFFFFFull);
+            d[k] = __uint_as_float((uint32_t)(kk >> 32));
+            col[k] = k < nx ? __ldg(colors + tid[k]) : 0u;
+        }
+    }
+    if (R == 8) {
+        const bool vec = nx == 8 && ((reinterpret_cast<uintptr_t>(fr.depth + p0) & 15) == 0) &&
+                         ((reinterpret_cast<uintptr_t>(fr.rgb + 3 * p0) & 7) == 0) &&
+                         (!fr.triid || (reinterpret_cast<uintptr_t>(fr.triid + p0) & 15) == 0);
+        if (vec) {
+            float4* dp = reinterpret_cast<float4*>(fr.depth + p0);
+            __stcs(dp, make_float4(d[0], d[1], d[2], d[3]));
+            __stcs(dp + 1, make_float4(d[4], d[5], d[6], d[7]));
+            if (fr.triid) {
+                uint4* tp = reinterpret_cast<uint4*>(fr.triid + p0);
+                __stcs(tp, make_uint4(tid[0], tid[1], tid[2], tid[3]));
+                __stcs(tp + 1, make_uint4(tid[4], tid[5], tid[6], tid[7]));
+            }
+            // 8 pixels = 24 bytes = 6 words, little endian r g b r | g b r g | b r g b | ...,
+            // written as three 8-byte stores (the run starts 8-byte aligned)
+            uint32_t wd[6];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t c0 = col[4 * h], c1 = col[4 * h + 1], c2 = col[4 * h + 2], c3 = col[4 * h + 3];
+                wd[3 * h] = (c0 & 0xFFFFFFu) | ((c1 & 0xFFu) << 24);
+                wd[3 * h + 1] = ((c1 >> 8) & 0xFFFFu) | ((c2 & 0xFFFFu) << 16);
+                wd[3 * h + 2] = ((c2 >> 16) & 0xFFu) | ((c3 & 0xFFFFFFu) << 8);
+            }
+            uint2* r64 = reinterpret_cast<uint2*>(fr.rgb + 3 * p0);
+#pragma unroll
+            for (int q = 0; q < 3; q++) __stcs(r64 + q, make_uint2(wd[2 * q], wd[2 * q + 1]));
+            return;
+        }
+    } else if (R == 2) {
+        const bool vec = nx == 2 && ((reinterpret_cast<uintptr_t>(fr.depth + p0) & 7) == 0) &&
+                         ((reinterpret_cast<uintptr_t>(fr.rgb + 3 * p0) & 1) == 0) &&
+                         (!fr.triid || (reinterpret_cast<uintptr_t>(fr.triid + p0) & 7) == 0);
+        if (vec) {
+            __stcs(reinterpret_cast<float2*>(fr.depth + p0), make_float2(d[0], d[1]));
+            if (fr.triid) __stcs(reinterpret_cast<uint2*>(fr.triid + p0), make_uint2(tid[0], tid[1]));
+            // 2 pixels = 6 bytes r g | b r | g b, three 2-byte stores
+            unsigned short* r16 = reinterpret_cast<unsigned short*>(fr.rgb + 3 * p0);
+            __stcs(r16, (unsigned short)(col[0] & 0xFFFFu));
+            __stcs(r16 + 1, (unsigned short)(((col[0] >> 16) & 0xFFu) | ((col[1] & 0xFFu) << 8)));
+            __stcs(r16 + 2, (unsigned short)((col[1] >> 8) & 0xFFFFu));
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < R; k++)
+        if (k < nx) {
+            fr.depth[p0 + k] = d[k];
+            if (fr.triid) fr.triid[p0 + k] = tid[k];
+            fr.rgb[3 * (p0 + k)] = col[k] & 255u;
+            fr.rgb[3 * (p0 + k) + 1] = (col[k] >> 8) & 255u;
+            fr.rgb[3 * (p0 + k) + 2] = (col[k] >> 16) & 255u;
+        }
+}
+
 // Work item (camera, first tile): warp w rasterises and resolves tile
-// first + w of the camera.
-__global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr,
-                                                            const TileItem* __restrict__ items) {
-    __shared__ unsigned long long s_key[kTW][kTile * kTile];
-    __shared__ int s_big[kTW][32];
+// first + w of the camera, one strip at a time.
+template <int T>
+__global__ void __launch_bounds__(TileGeom<T>::TW * 32, 4) tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr,
+                                                                        const TileItem* __restrict__ items) {
+    using G = TileGeom<T>;
+    constexpr int R = G::R;
+    __shared__ unsigned long long s_key[G::TW][T * G::SH];
+    __shared__ int s_big[G::TW][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const TileItem* itp = items + blockIdx.x;
     const int4 geo = __ldg(reinterpret_cast<const int4*>(itp));        // cam, tile0, W, H
@@ -352,122 +454,96 @@ __global__ void __launch_bounds__(kTW * 32, 4) tile_kernel(DevBatch b, TileScrat
     const uint32_t* __restrict__ wide = ts.wide + rb.x;
     const uint32_t* __restrict__ ent = ts.ent + rb.y;
     const int32_t* __restrict__ toff = ts.toff + toff_base;
-    const int tx0 = (tile % tiles_x) * kTile, ty0 = (tile / tiles_x) * kTile;
-    const int tx1 = min(tx0 + kTile, W) - 1, ty1 = min(ty0 + kTile, H) - 1;
-    // lane: row lane / 2 of the tile, columns 8 (lane % 2) .. + 7
-    const int y = ty0 + (lane >> 1), xs = tx0 + 8 * (lane & 1);
-    const int nx = y <= ty1 ? max(0, min(8, tx1 - xs + 1)) : 0;
+    const int tx0 = (tile % tiles_x) * T, ty0 = (tile / tiles_x) * T;
+    const int tx1 = min(tx0 + T, W) - 1, ty1 = min(ty0 + T, H) - 1;
     unsigned long long* sk = s_key[w];
+#pragma unroll 1
+    for (int st = 0; st < G::STRIPS; st++) {
+        const int sy0 = ty0 + st * G::SH;
+        if (sy0 > ty1) break;   // warp-uniform
+        const int sy1 = min(sy0 + G::SH - 1, ty1);
+        // lane: row lane / LPR of the strip, columns R (lane % LPR) .. + R - 1
+        const int y = sy0 + lane / G::LPR, xs = tx0 + R * (lane % G::LPR);
+        const int nx = y <= sy1 ? max(0, min(R, tx1 - xs + 1)) : 0;
+        __syncwarp();   // the previous strip's resolve is done with the shared keys
 #pragma unroll
-    for (int k = 0; k < 8; k++) sk[lane + 32 * k] = ~0ULL;
-    __syncwarp();
-    unsigned long long key[8];
-#pragma unroll
-    for (int k = 0; k < 8; k++) key[k] = ~0ULL;
-
-    const int beg = __ldg(toff + tile), end = __ldg(toff + tile + 1);
-    for (int base = beg; base < end; base += 32) {
-        const int i = base + lane;
-        bool big = false;
-        uint32_t r = 0;
-        if (i < end) {
-            r = __ldg(ent + i);
-            const TriRec t = load_rec(rec + r);
-            const int x0 = max((int)t.x0, tx0), x1 = min((int)t.x1, tx1);
-            const int y0 = max((int)t.y0, ty0), y1 = min((int)t.y1, ty1);
-            if (x0 <= x1 && y0 <= y1) {
-                if (t.tl & kSmallBit) lane_raster(t, x0, x1, y0, y1, tx0, ty0, sk);
-                else big = true;
-            }
-        }
-        const unsigned m = __ballot_sync(kFullMask, big);
-        if (big) s_big[w][__popc(m & ((1u << lane) - 1u))] = (int)r;
+        for (int k = 0; k < R; k++) sk[lane + 32 * k] = ~0ULL;
         __syncwarp();
-        const int nb = __popc(m);
-        for (int q = 0; q < nb; q++) warp_pass(rec + s_big[w][q], y, xs, nx, key);
-        __syncwarp();   // s_big is reused by the next batch
-    }
-    const int nw = __ldg(toff + ntiles + 1);
-    for (int q = 0; q < nw; q++) warp_pass(rec + __ldg(wide + q), y, xs, nx, key);
-    __syncwarp();       // the lanes' shared-memory keys are complete
+        unsigned long long key[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) key[k] = ~0ULL;
 
-    if (nx <= 0) return;
-    const longlong2 pc = __ldg(reinterpret_cast<const longlong2*>(itp) + 4);   // pix_off, col_base
-    const uint32_t* colors = b.tri_color + pc.y;
-    const int64_t p0 = pc.x + (int64_t)y * W + xs;
-    const unsigned long long* sl = sk + (lane >> 1) * kTile + 8 * (lane & 1);
-    float d[8];
-    uint32_t tid[8], col[8];
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-        unsigned long long kk = sl[k];
-        kk = key[k] < kk ? key[k] : kk;
-        if (kk == ~0ULL) {
-            d[k] = 0.0f;
-            tid[k] = 0xFFFFFFFFu;
-            col[k] = 0u;
-        } else {
-            tid[k] = (uint32_t)(kk & 0xFFFFFFFFull);
-            d[k] = __uint_as_float((uint32_t)(kk >> 32));
-            col[k] = k < nx ? __ldg(colors + tid[k]) : 0u;
-        }
-    }
-    const bool vec = nx == 8 && ((reinterpret_cast<uintptr_t>(fr.depth + p0) & 15) == 0) &&
-                     ((reinterpret_cast<uintptr_t>(fr.rgb + 3 * p0) & 7) == 0) &&
-                     (!fr.triid || (reinterpret_cast<uintptr_t>(fr.triid + p0) & 15) == 0);
-    // the frame is not read again on the device: streaming (evict-first)
-    // stores keep the L2 for the triangle records still to be read
-    if (vec) {
-        float4* dp = reinterpret_cast<float4*>(fr.depth + p0);
-        __stcs(dp, make_float4(d[0], d[1], d[2], d[3]));
-        __stcs(dp + 1, make_float4(d[4], d[5], d[6], d[7]));
-        if (fr.triid) {
-            uint4* tp = reinterpret_cast<uint4*>(fr.triid + p0);
-            __stcs(tp, make_uint4(tid[0], tid[1], tid[2], tid[3]));
-            __stcs(tp + 1, make_uint4(tid[4], tid[5], tid[6], tid[7]));
-        }
-        // 8 pixels = 24 bytes = 6 words, little endian r g b r | g b r g | b r g b | ...,
-        // written as three 8-byte stores (the run starts 8-byte aligned)
-        uint32_t wd[6];
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const uint32_t c0 = col[4 * h], c1 = col[4 * h + 1], c2 = col[4 * h + 2], c3 = col[4 * h + 3];
-            wd[3 * h] = (c0 & 0xFFFFFFu) | ((c1 & 0xFFu) << 24);
-            wd[3 * h + 1] = ((c1 >> 8) & 0xFFFFu) | ((c2 & 0xFFFFu) << 16);
-            wd[3 * h + 2] = ((c2 >> 16) & 0xFFu) | ((c3 & 0xFFFFFFu) << 8);
-        }
-        uint2* r64 = reinterpret_cast<uint2*>(fr.rgb + 3 * p0);
-#pragma unroll
-        for (int q = 0; q < 3; q++) __stcs(r64 + q, make_uint2(wd[2 * q], wd[2 * q + 1]));
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; k++)
-            if (k < nx) {
-                fr.depth[p0 + k] = d[k];
-                if (fr.triid) fr.triid[p0 + k] = tid[k];
-                fr.rgb[3 * (p0 + k)] = col[k] & 255u;
-                fr.rgb[3 * (p0 + k) + 1] = (col[k] >> 8) & 255u;
-                fr.rgb[3 * (p0 + k) + 2] = (col[k] >> 16) & 255u;
+        const int beg = __ldg(toff + tile), end = __ldg(toff + tile + 1);
+        for (int base = beg; base < end; base += 32) {
+            const int i = base + lane;
+            bool big = false;
+            uint32_t r = 0;
+            if (i < end) {
+                r = __ldg(ent + i);
+                const TriRec t = load_rec(rec + r);
+                const int x0 = max((int)t.x0, tx0), x1 = min((int)t.x1, tx1);
+                const int y0 = max((int)t.y0, sy0), y1 = min((int)t.y1, sy1);
+                if (x0 <= x1 && y0 <= y1) {
+                    if (t.tl & kSmallBit) lane_raster<T>(t, x0, x1, y0, y1, tx0, sy0, sk);
+                    else big = true;
+                }
             }
+            const unsigned m = __ballot_sync(kFullMask, big);
+            if (big) s_big[w][__popc(m & ((1u << lane) - 1u))] = (int)r;
+            __syncwarp();
+            const int nb = __popc(m);
+            for (int q = 0; q < nb; q++) warp_pass<R>(rec + s_big[w][q], y, xs, nx, key);
+            __syncwarp();   // s_big is reused by the next batch
+        }
+        const int nw = __ldg(toff + ntiles + 1);
+        for (int q = 0; q < nw; q++) warp_pass<R>(rec + __ldg(wide + q), y, xs, nx, key);
+        __syncwarp();       // the lanes' shared-memory keys are complete
+
+        if (nx > 0) {
+            const longlong2 pc = __ldg(reinterpret_cast<const longlong2*>(itp) + 4);   // pix_off, col_base
+            const unsigned long long* sl = sk + (lane / G::LPR) * T + R * (lane % G::LPR);
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                const unsigned long long kk = sl[k];
+                key[k] = key[k] < kk ? key[k] : kk;
+            }
+            resolve_run<R>(key, nx, pc.x + (int64_t)y * W + xs, b.tri_color + pc.y, fr);
+        }
     }
 }
 
 }  // namespace
 
 int tiled_max_tiles() { return kMaxTiles; }
-int tiled_narrow_tiles() { return kNarrowTiles; }
-int tiled_tiles_per_item() { return kTW; }
+int tiled_default_bin_limit() { return kNarrowTiles; }
+int tiled_max_bin_limit() { return kMaxBinLimit; }
+int tiled_tiles_per_item(int tile) {
+    return tile == 8 ? TileGeom<8>::TW : tile == 32 ? TileGeom<32>::TW : TileGeom<16>::TW;
+}
 size_t tiled_record_bytes() { return sizeof(TriRec); }
 
-cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
-                                const TileItem* cams, const TileItem* items, int nitems, cudaStream_t stream) {
-    if (b.C == 0) return cudaSuccess;
-    bin_kernel<<<b.C, kBT, 0, stream>>>(b, pose, ts, cams);
-    cudaError_t err;
-    err = cudaGetLastError();
+template <int T>
+static cudaError_t launch_tiled_t(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
+                                  const TileItem* cams, const TileItem* items, int nitems, int nlim,
+                                  cudaStream_t stream) {
+    bin_kernel<T><<<b.C, kBT, 0, stream>>>(b, pose, ts, cams, nlim);
+    cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || nitems == 0) return err;
-    tile_kernel<<<nitems, kTW * 32, 0, stream>>>(b, ts, fr, items);
+    tile_kernel<T><<<nitems, TileGeom<T>::TW * 32, 0, stream>>>(b, ts, fr, items);
     return cudaGetLastError();
+}
+
+cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
+                                const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim,
+                                cudaStream_t stream) {
+    if (b.C == 0) return cudaSuccess;
+    if (nlim < 1 || nlim > kMaxBinLimit) return cudaErrorInvalidValue;
+    switch (tile) {
+        case 8: return launch_tiled_t<8>(b, pose, fr, ts, cams, items, nitems, nlim, stream);
+        case 16: return launch_tiled_t<16>(b, pose, fr, ts, cams, items, nitems, nlim, stream);
+        case 32: return launch_tiled_t<32>(b, pose, fr, ts, cams, items, nitems, nlim, stream);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace vuda

@@ -51,13 +51,15 @@ class Scene(C.Structure):
 
 class EnvOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("device", C.c_int32), ("render_band_rows", C.c_int32),
-                ("phys_smem_bytes", C.c_int32), ("persistent", C.c_int32), ("render_path", C.c_int32)]
+                ("phys_smem_bytes", C.c_int32), ("persistent", C.c_int32), ("render_path", C.c_int32),
+                ("tile_size", C.c_int32), ("tile_bin_limit", C.c_int32)]
 
 
 class EnvInfo(C.Structure):
     _fields_ = [("num_envs", C.c_int32), ("num_bodies", C.c_int32), ("num_cams", C.c_int32),
                 ("max_bodies", C.c_int32), ("num_pixels", C.c_int64), ("num_tris", C.c_int64),
-                ("device_bytes", C.c_int64), ("steps_enqueued", C.c_int64), ("render_path", C.c_int32)]
+                ("device_bytes", C.c_int64), ("steps_enqueued", C.c_int64), ("render_path", C.c_int32),
+                ("tile_size", C.c_int32), ("tile_bin_limit", C.c_int32)]
 
 
 class Frame(C.Structure):
@@ -80,7 +82,8 @@ class TuneResult(C.Structure):
     _fields_ = [("band_rows", C.c_int32), ("cosched_mode", C.c_int32), ("sim_sms", C.c_int32),
                 ("graph_steps", C.c_int32), ("ms_per_step", C.c_float), ("ms_per_step_serialized", C.c_float),
                 ("trials", C.c_int32), ("from_cache", C.c_int32), ("sim_ctas_per_sm", C.c_int32),
-                ("render_ctas_per_sm", C.c_int32), ("priority", C.c_int32)]
+                ("render_ctas_per_sm", C.c_int32), ("priority", C.c_int32), ("tile_size", C.c_int32),
+                ("tile_bin_limit", C.c_int32)]
 
 
 class CoschedOpts(C.Structure):
@@ -118,6 +121,7 @@ _sig("vuda_pipeline_run_host", [vp, C.c_int32, vp, C.c_int32, vp, vp, C.POINTER(
 _sig("vuda_pipeline_capture", [vp, C.c_int32, C.POINTER(Frame), vp])
 _sig("vuda_pipeline_release_graph", [vp])
 _sig("vuda_autotune", [vp, C.POINTER(TuneOpts), C.POINTER(Frame), C.POINTER(TuneResult)])
+_sig("vuda_set_tiling", [vp, C.c_int32, C.c_int32])
 _sig("vuda_wait", [vp, C.c_int32])
 _sig("vuda_env_get_state", [vp, C.POINTER(State)])
 _sig("vuda_env_set_state", [vp, C.POINTER(State)])
@@ -232,7 +236,8 @@ class Env:
     """A batch of environments resident on the GPU."""
 
     def __init__(self, scene, params=None, hbm_budget_bytes: int = 0, device: int = 0, band_rows: int = 0,
-                 phys_smem_bytes: int = 0, persistent: bool = False, render_path: int = 0, _handle=None):
+                 phys_smem_bytes: int = 0, persistent: bool = False, render_path: int = 0, tile_size: int = 0,
+                 tile_bin_limit: int = 0, _handle=None):
         self.scene = scene
         if _handle is not None:            # a handle owned elsewhere (a serving job)
             self.h = _handle
@@ -243,7 +248,8 @@ class Env:
         sc, keep = scene_struct(scene)
         self.params = params or scene.params
         prm = sim_params(self.params)
-        opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes, int(persistent), render_path)
+        opts = EnvOpts(hbm_budget_bytes, device, band_rows, phys_smem_bytes, int(persistent), render_path,
+                       tile_size, tile_bin_limit)
         handle = vp()
         check(lib.vuda_env_create(C.byref(sc), C.byref(prm), C.byref(opts), C.byref(handle)), "vuda_env_create")
         del keep
@@ -281,6 +287,10 @@ class Env:
         i = EnvInfo()
         check(lib.vuda_env_info_get(self.h, C.byref(i)), "vuda_env_info_get")
         return i
+
+    def set_tiling(self, tile_size: int, bin_limit: int):
+        """Tile edge (8, 16, 32) and bin limit of the tiled render path."""
+        check(lib.vuda_set_tiling(self.h, tile_size, bin_limit), "vuda_set_tiling")
 
     # -- frames -------------------------------------------------------------------
     def alloc_frame(self, triid: bool = True):

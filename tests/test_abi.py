@@ -3,6 +3,7 @@ declares (CPU only: no compute calls)."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -37,7 +38,7 @@ def test_library_exports_every_declared_symbol(built):
 
 def test_status_strings_without_gpu(built):
     from paper_2605_01352_b300 import vuda
-    assert vuda.lib.vuda_abi_version() == 2
+    assert vuda.lib.vuda_abi_version() == 3
     assert vuda.lib.vuda_status_str(0) == b"ok"
     assert b"invalid" in vuda.lib.vuda_status_str(1)
 
@@ -48,3 +49,35 @@ def test_invalid_arguments_are_rejected_without_gpu(built):
     assert vuda.lib.vuda_env_create(None, None, None, None) == vuda.ERR_INVALID
     assert vuda.lib.vuda_raster_screen_tris(None, None, 0, 0, 8, None, None, None, None) == vuda.ERR_INVALID
     assert vuda.lib.vuda_sim_step(None, 1, None, None) == vuda.ERR_INVALID
+
+
+def test_binding_structs_match_the_c_header(built, tmp_path):
+    """Every struct of the binding has the size and field offsets that a C
+    compiler gives the header's struct (gcc, host only)."""
+    import ctypes as C
+
+    from paper_2605_01352_b300 import vuda
+    pairs = [("vuda_sim_params", vuda.SimParams), ("vuda_scene", vuda.Scene), ("vuda_env_opts", vuda.EnvOpts),
+             ("vuda_env_info", vuda.EnvInfo), ("vuda_frame", vuda.Frame), ("vuda_state", vuda.State),
+             ("vuda_timing", vuda.Timing), ("vuda_tune_opts", vuda.TuneOpts), ("vuda_tune_result", vuda.TuneResult),
+             ("vuda_cosched_opts", vuda.CoschedOpts), ("vuda_cosched_info", vuda.CoschedInfo),
+             ("vuda_serve_opts", vuda.ServeOpts), ("vuda_result", vuda.Result),
+             ("vuda_serve_stats", vuda.ServeStats)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vuda.h"', "int main(void) {"]
+    expect = []
+    for cname, py in pairs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append((cname, "sizeof", C.sizeof(py)))
+        for f in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f[0]}));')
+            expect.append((cname, f[0], getattr(py, f[0]).offset))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert len(got) == len(expect)
+    bad = [(e, g) for e, g in zip(expect, got) if e[2] != g]
+    assert not bad, bad

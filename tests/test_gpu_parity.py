@@ -179,6 +179,70 @@ def test_render_ragged_tiles(V, orc, path):
     _render_cmp(V, orc, sc, st["pos"], st["quat"], path=path)
 
 
+TILINGS = [(8, 1), (8, 9), (16, 1), (16, 4), (16, 64), (32, 2), (32, 9)]
+
+
+@pytest.mark.parametrize("tile,nlim", TILINGS)
+def test_render_tilings_match_oracle(V, orc, tile, nlim):
+    """Every tile size of the tiled path (8 x 8: two pixels a lane; 32 x 32:
+    four 32 x 8 strips) with small and large bin limits (most triangles on
+    the wide list, or none) gives the oracle's frames, on cameras that are
+    not multiples of any tile size (partial tiles and strips, odd widths
+    that leave runs unaligned)."""
+    sc = S.generate(4, np.array([7, 12, 5, 9]), 303, kinds="mixed", res=np.array([40, 71, 9, 100]), substeps=4)
+    st, _, _ = orc.sim_step(sc, 30)
+    env = V.Env(sc, render_path=V.RENDER_TILED, tile_size=tile, tile_bin_limit=nlim)
+    i = env.info()
+    assert (i.render_path, i.tile_size, i.tile_bin_limit) == (V.RENDER_TILED, tile, nlim)
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], env=env)
+    env.close()
+
+
+def test_set_tiling_switches_without_changing_frames(V):
+    """vuda_set_tiling moves one batch through every tile size and bin limit
+    the autotuner tries; the frames stay bit-identical, and invalid choices
+    are refused with the batch keeping its parameters."""
+    import torch
+    sc = S.cfg2(48)
+    env = V.Env(sc, render_path=V.RENDER_TILED)
+    assert (env.info().tile_size, env.info().tile_bin_limit) == (16, 9)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    env.sim_step(40)
+    ref = None
+    for tile in (16, 8, 32):
+        for nlim in (9, 4, 16):
+            env.set_tiling(tile, nlim)
+            assert (env.info().tile_size, env.info().tile_bin_limit) == (tile, nlim)
+            for k in ring[0]:
+                ring[0][k].zero_()
+            env.render(ring[0], pose_slot=-1)
+            torch.cuda.synchronize()
+            got = {k: v.cpu().numpy().copy() for k, v in ring[0].items()}
+            if ref is None:
+                ref = got
+            for k in ref:
+                np.testing.assert_array_equal(got[k], ref[k], err_msg="%s tile %d limit %d" % (k, tile, nlim))
+    for bad in ((12, 9), (16, 0), (16, 65)):
+        with pytest.raises(V.VudaError):
+            env.set_tiling(*bad)
+        assert (env.info().tile_size, env.info().tile_bin_limit) == (32, 16)
+    env.close()
+    band = V.Env(S.cfg2(4), render_path=V.RENDER_BAND)
+    with pytest.raises(V.VudaError):
+        band.set_tiling(16, 9)
+    assert band.info().tile_size == 0
+    band.close()
+    # 640 x 480 is 4800 tiles of 8 x 8, over the per-camera tile table
+    big = S.generate(1, np.array([4]), 5, kinds="mixed", res=np.array([640]), height=np.array([480]), substeps=4)
+    with pytest.raises(V.VudaError):
+        V.Env(big, render_path=V.RENDER_TILED, tile_size=8)
+    e = V.Env(big, render_path=V.RENDER_TILED, tile_size=32)
+    with pytest.raises(V.VudaError):
+        e.set_tiling(8, 9)
+    assert e.info().tile_size == 32
+    e.close()
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_render_non_square_cameras(V, orc, path):
     """A 640 x 480 data-generation camera (1200 tiles) beside non-square
@@ -498,7 +562,10 @@ def test_autotune_keeps_results_and_caches(V):
     env = V.Env(sc)
     ring = [env.alloc_frame(), env.alloc_frame()]
     res = env.autotune(ring, steps=3, use_cache=True)
-    assert res["trials"] > 0 and res["band_rows"] in (16, 32, 64, 128)
+    assert res["trials"] > 0
+    assert env.info().render_path == V.RENDER_TILED
+    assert res["tile_size"] in (8, 16, 32) and res["tile_bin_limit"] in (4, 9, 16)
+    assert (env.info().tile_size, env.info().tile_bin_limit) == (res["tile_size"], res["tile_bin_limit"])
     assert res["cosched_mode"] in (0, V.COSCHED_STREAMS, V.COSCHED_GREEN, V.COSCHED_SHARED)
     if res["cosched_mode"] == V.COSCHED_SHARED:
         assert res["sim_ctas_per_sm"] >= 1 and res["render_ctas_per_sm"] >= 1
@@ -514,8 +581,16 @@ def test_autotune_keeps_results_and_caches(V):
     ring2 = [env2.alloc_frame(), env2.alloc_frame()]
     res2 = env2.autotune(ring2, use_cache=True)
     assert res2["from_cache"] == 1 and res2["trials"] == 0
-    assert (res2["band_rows"], res2["cosched_mode"]) == (res["band_rows"], res["cosched_mode"])
+    assert (res2["tile_size"], res2["tile_bin_limit"], res2["cosched_mode"]) == \
+        (res["tile_size"], res["tile_bin_limit"], res["cosched_mode"])
+    assert (env2.info().tile_size, env2.info().tile_bin_limit) == (res["tile_size"], res["tile_bin_limit"])
     env2.close()
+    # on the band path the raster parameter is the band height
+    env3 = V.Env(S.cfg2(16), render_path=V.RENDER_BAND)
+    ring3 = [env3.alloc_frame(), env3.alloc_frame()]
+    res3 = env3.autotune(ring3, steps=2, use_cache=False)
+    assert res3["band_rows"] in (16, 32, 64, 128) and res3["tile_size"] == 0
+    env3.close()
 
 
 @pytest.mark.parametrize("path", PATHS)
