@@ -63,7 +63,11 @@ constexpr unsigned kSmallBit = 8u;  // TriRec::tl bit: the record takes the per-
 // A set-up triangle, vertices oriented to positive area (80 bytes, 16-byte
 // aligned in the scratch array).
 struct __align__(16) TriRec {
-    int A[3], B[3];        // edge i: E_i = A_i x + B_i y + C_i in 1/256 px; |A|, |B| <= 2^23
+    // edge i: E_i = A_i x + B_i y + C_i in 1/256 px, |A|, |B| <= 2^23.  C
+    // holds C_i - b_i with b_i = 1 where edge i does not own its pixels (top-
+    // left rule), so that a pixel centre is inside iff every biased value
+    // E_i - b_i is >= 0; E_i itself (for the depth) is the biased value + b_i.
+    int A[3], B[3];
     long long C[3];
     float iz[3];           // 1 / view depth of the vertices
     float af;              // (float) doubled area
@@ -211,8 +215,9 @@ __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __
                 const long long Bv = (long long)X[k] - X[j];
                 g.A[i] = (int)A;
                 g.B[i] = (int)Bv;
-                g.C[i] = -A * X[j] - Bv * Y[j];
-                if ((A > 0) || (A == 0 && Bv > 0)) tl |= 1u << i;
+                const bool owns = (A > 0) || (A == 0 && Bv > 0);
+                g.C[i] = -A * X[j] - Bv * Y[j] - (owns ? 0 : 1);
+                if (owns) tl |= 1u << i;
             }
             const long long pa = ((long long)X[1] - X[0]) * ((long long)Y[2] - Y[0]) -
                                  ((long long)Y[1] - Y[0]) * ((long long)X[2] - X[0]);
@@ -299,14 +304,14 @@ __device__ __forceinline__ void lane_raster(const TriRec& t, int x0, int x1, int
     int R2 = (int)((long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2]);
     const int dx0 = t.A[0] * 256, dx1 = t.A[1] * 256, dx2 = t.A[2] * 256;
     const int dy0 = t.B[0] * 256, dy1 = t.B[1] * 256, dy2 = t.B[2] * 256;
-    const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
+    const int b0 = (~t.tl) & 1u, b1 = (~t.tl >> 1) & 1u, b2 = (~t.tl >> 2) & 1u;
     for (int py = y0; py <= y1; py++) {
         int E0 = R0, E1 = R1, E2 = R2;
         unsigned long long* row = sk + (py - sy0) * T - tx0;
         for (int px = x0; px <= x1; px++) {
-            if ((E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) && (E2 > 0 || (E2 == 0 && tl2))) {
-                const float den =
-                    (__int2float_rn(E0) * t.iz[0] + __int2float_rn(E1) * t.iz[1]) + __int2float_rn(E2) * t.iz[2];
+            if ((E0 | E1 | E2) >= 0) {   // every biased edge value >= 0
+                const float den = (__int2float_rn(E0 + b0) * t.iz[0] + __int2float_rn(E1 + b1) * t.iz[1]) +
+                                  __int2float_rn(E2 + b2) * t.iz[2];
                 const float depth = t.af / den;
                 atomicMin(row + px, ((unsigned long long)__float_as_uint(depth) << 32) | t.id);
             }
@@ -335,16 +340,19 @@ __device__ __forceinline__ void warp_pass(const TriRec* __restrict__ p, int y, i
     long long E1 = (long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1];
     long long E2 = (long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2];
     const long long d0 = 256LL * t.A[0], d1 = 256LL * t.A[1], d2 = 256LL * t.A[2];
-    // the edge functions are affine along the run: negative at both of its
-    // ends for one edge means no pixel of the run is covered
+    // the (biased) edge functions are affine along the run: negative at both
+    // of its ends for one edge means no pixel of the run is covered
     const long long m = nx - 1;
     if ((E0 < 0 && E0 + m * d0 < 0) || (E1 < 0 && E1 + m * d1 < 0) || (E2 < 0 && E2 + m * d2 < 0)) return;
-    const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
 #pragma unroll
     for (int k = 0; k < R; k++) {
-        if (k < nx && (E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) &&
-            (E2 > 0 || (E2 == 0 && tl2))) {
-            const float den = (i64_to_f32(E0) * t.iz[0] + i64_to_f32(E1) * t.iz[1]) + i64_to_f32(E2) * t.iz[2];
+        // inside iff every biased edge value is >= 0: the sign of the OR of their high words
+        const int hi = (int)(((unsigned long long)E0 | (unsigned long long)E1 | (unsigned long long)E2) >> 32);
+        if (k < nx && hi >= 0) {
+            const unsigned nb = ~t.tl;   // bias bits b_i
+            const float den = (i64_to_f32(E0 + (long long)(nb & 1u)) * t.iz[0] +
+                               i64_to_f32(E1 + (long long)((nb >> 1) & 1u)) * t.iz[1]) +
+                              i64_to_f32(E2 + (long long)((nb >> 2) & 1u)) * t.iz[2];
             const float depth = t.af / den;
             const unsigned long long kk = ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
             key[k] = kk < key[k] ? kk : key[k];
