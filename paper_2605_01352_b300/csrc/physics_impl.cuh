@@ -369,10 +369,9 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
     const int lane = tid & 31, warp = tid >> 5;
     // contacts per body, and per-body lists (contact << 1 | side) in
     // ascending contact order: the list is cut into kParts parts, the
-    // contacts of each body are counted per part, and warp q fills the
-    // entries of part q
-    for (int i = tid; i < kParts * NB; i += kT) qcnt[i] = 0;
-    __syncthreads();
+    // contacts of each body are counted per part (qcnt is zero on entry),
+    // and warp q fills the entries of part q
+    __syncthreads();   // the contact records of this substep are written
     const int qlen = (nc + kParts - 1) / kParts;
     for (int c = tid; c < nc; c += kT) {
         int a, bb;
@@ -384,30 +383,32 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
         if (bb >= 0) atomicAdd(qcnt + q * NB + bb, 1);
     }
     __syncthreads();
+    // warp q fills the entries of the contacts of part q; every warp forms
+    // the list offsets itself (a warp scan of the bodies' counts), so no CTA
+    // barrier separates counting from filling; warp 0 keeps the counts and
+    // offsets for the later phases
     {
         int run = 0;
-        for (int i0 = 0; i0 < N; i0 += kT) {
-            int i = i0 + tid;
-            int v = 0;
-            if (i < N)
-                for (int q = 0; q < kParts; q++) v += qcnt[q * NB + i];
-            int tot;
-            int ex = block_excl_scan(v, wsum, tot);
+        for (int i0 = 0; i0 < N; i0 += 32) {
+            const int i = i0 + lane;
+            int v = 0, before = 0;
             if (i < N) {
-                S.NCB(i) = v;
-                S.loff[i] = run + ex;
+#pragma unroll
+                for (int q = 0; q < kParts; q++) {
+                    const int cq = qcnt[q * NB + i];
+                    if (q < warp) before += cq;
+                    v += cq;
+                }
             }
-            run += tot;
-        }
-        if (tid == 0) S.loff[N] = run;
-    }
-    __syncthreads();
-    // warp q fills the entries of the contacts of part q
-    for (int i0 = 0; i0 < N; i0 += 32) {
-        int i = i0 + lane;
-        if (i < N) {
-            int o = S.loff[i];
-            for (int q = 0; q < warp; q++) o += qcnt[q * NB + i];
+            const int incl = warp_incl_scan(v, lane);
+            const int lo = run + incl - v;
+            run += __shfl_sync(kFull, incl, 31);
+            if (i >= N) continue;
+            if (warp == 0) {
+                S.NCB(i) = v;
+                S.loff[i] = lo;
+            }
+            int o = lo + before;
             int cend = min(nc, (warp + 1) * qlen);
             int c = warp * qlen;
             for (; c + 4 <= cend; c += 4) {
@@ -428,6 +429,7 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
                 else if (bb == i) lists[o++] = (unsigned short)((c << 1) | 1);
             }
         }
+        if (warp == 0 && lane == 0) S.loff[N] = run;
     }
     __syncthreads();
 
@@ -665,6 +667,8 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                         S.I(3 * r + c, i) = ((R[3 * r] * ib0) * R[3 * c] + (R[3 * r + 1] * ib1) * R[3 * c + 1]) +
                                             (R[3 * r + 2] * ib2) * R[3 * c + 2];
             }
+            // per-part contact counts of this substep's lists start at zero
+            for (int i = tid; i < kParts * NB; i += kT) qcnt[i] = 0;
             __syncthreads();
 
             // 2a. plane contacts: units = bodies in order, one item per sphere,

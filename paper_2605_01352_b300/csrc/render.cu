@@ -77,6 +77,10 @@ __device__ __forceinline__ bool setup_tri(const int* X, const int* Y, const floa
     return true;
 }
 
+// Edge functions E_i = A_i x + B_i y + C_i (1/256 px) of a triangle.  C
+// holds C_i - b_i with b_i = 1 where edge i does not own its pixels (top-left
+// rule): a pixel centre is inside iff every biased value is >= 0, and E_i
+// (for the depth) is the biased value + b_i.
 struct Edges {
     long long A[3], B[3], C[3];
     bool tl[3];
@@ -91,21 +95,21 @@ __device__ __forceinline__ void edges(const Tri& t, Edges& e) {
         long long B = (long long)t.X[k] - t.X[j];
         e.A[i] = A;
         e.B[i] = B;
-        e.C[i] = -A * t.X[j] - B * t.Y[j];
         e.tl[i] = (A > 0) || (A == 0 && B > 0);
+        e.C[i] = -A * t.X[j] - B * t.Y[j] - (e.tl[i] ? 0 : 1);
     }
     long long area2 = ((long long)t.X[1] - t.X[0]) * ((long long)t.Y[2] - t.Y[0]) -
                       ((long long)t.Y[1] - t.Y[0]) * ((long long)t.X[2] - t.X[0]);
     e.af = i64_to_f32(area2);
 }
 
-__device__ __forceinline__ bool inside(long long E0, long long E1, long long E2, const Edges& e) {
-    return (E0 > 0 || (E0 == 0 && e.tl[0])) && (E1 > 0 || (E1 == 0 && e.tl[1])) && (E2 > 0 || (E2 == 0 && e.tl[2]));
-}
+// Biased edge values: inside iff all three are >= 0.
+__device__ __forceinline__ bool inside(long long E0, long long E1, long long E2) { return (E0 | E1 | E2) >= 0; }
 
 __device__ __forceinline__ unsigned long long frag_key(long long E0, long long E1, long long E2, const Tri& t,
                                                        const Edges& e) {
-    float den = (i64_to_f32(E0) * t.iz[0] + i64_to_f32(E1) * t.iz[1]) + i64_to_f32(E2) * t.iz[2];
+    float den = (i64_to_f32(E0 + (e.tl[0] ? 0 : 1)) * t.iz[0] + i64_to_f32(E1 + (e.tl[1] ? 0 : 1)) * t.iz[1]) +
+                i64_to_f32(E2 + (e.tl[2] ? 0 : 1)) * t.iz[2];
     float depth = e.af / den;
     return ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
 }
@@ -114,12 +118,12 @@ __device__ __forceinline__ unsigned long long frag_key(long long E0, long long E
 // submitted it, for all the lanes of the tile pass.
 struct BigRec {
     int A[3], B[3];       // |A|, |B| < 2^23 inside the guard band
-    long long C[3];
+    long long C[3];       // biased as in Edges
     float iz[3];
     float af;             // (float) area2
     uint32_t id;
     short x0, x1, y0, y1;
-    unsigned tl;          // bit i: edge i owns its pixels
+    unsigned tl;          // bit i: edge i owns its pixels (b_i = 1 - bit i)
 };
 
 // One thread rasterises a small triangle into the shared-memory z-buffer.
@@ -133,7 +137,7 @@ __device__ __forceinline__ void raster_thread(const Tri& t, const Band& bd) {
         long long E1 = e.A[1] * cx + e.B[1] * cy + e.C[1];
         long long E2 = e.A[2] * cx + e.B[2] * cy + e.C[2];
         for (int px = t.x0; px <= t.x1; px++) {
-            if (inside(E0, E1, E2, e)) {
+            if (inside(E0, E1, E2)) {
                 int o = (py - bd.y0) * bd.W + px;
                 atomicMin(bd.z + o, frag_key(E0, E1, E2, t, e));
                 if (bd.count) atomicAdd(bd.count + o, 1u);
@@ -198,12 +202,15 @@ __device__ void tile_pass(const Band& bd, const Bins& bn) {
                 long long E1 = (long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1];
                 long long E2 = (long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2];
                 const long long d0 = 256LL * t.A[0], d1 = 256LL * t.A[1], d2 = 256LL * t.A[2];
-                const bool tl0 = t.tl & 1u, tl1 = t.tl & 2u, tl2 = t.tl & 4u;
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    if (k < nx && (E0 > 0 || (E0 == 0 && tl0)) && (E1 > 0 || (E1 == 0 && tl1)) &&
-                        (E2 > 0 || (E2 == 0 && tl2))) {
-                        float den = (i64_to_f32(E0) * t.iz[0] + i64_to_f32(E1) * t.iz[1]) + i64_to_f32(E2) * t.iz[2];
+                    // inside iff every biased edge value is >= 0: the sign of the OR of their high words
+                    const int hi = (int)(((unsigned long long)E0 | (unsigned long long)E1 | (unsigned long long)E2) >> 32);
+                    if (k < nx && hi >= 0) {
+                        const unsigned nb = ~t.tl;   // bias bits b_i
+                        float den = (i64_to_f32(E0 + (long long)(nb & 1u)) * t.iz[0] +
+                                     i64_to_f32(E1 + (long long)((nb >> 1) & 1u)) * t.iz[1]) +
+                                    i64_to_f32(E2 + (long long)((nb >> 2) & 1u)) * t.iz[2];
                         float depth = t.af / den;
                         unsigned long long kk = ((unsigned long long)__float_as_uint(depth) << 32) | t.id;
                         key[k] = kk < key[k] ? kk : key[k];

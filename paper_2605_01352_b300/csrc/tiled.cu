@@ -47,14 +47,18 @@ constexpr int kMaxTiles = 2048;   // tiles per camera the counting sort holds in
 constexpr int kLanePx = 64;       // unclipped bounding-box pixels up to which one lane rasterises a record
 
 // Geometry of one warp's T x T tile: strips of SH rows, R pixels per lane
-// (LPR lanes per strip row), TW tiles (warps) per tile_kernel CTA.
+// (LPR lanes per strip row), TW tiles (warps) per tile_kernel CTA.  Two
+// warps per CTA: the warps of a CTA finish their tiles at different times
+// (tiles hold different numbers of triangles) and the CTA's slot is freed
+// only with its last warp, so small CTAs keep more warps resident (16 CTAs
+// of 64 registers per thread fill an SM's register file).
 template <int T>
 struct TileGeom {
     static constexpr int SH = T * T > 256 ? 256 / T : T;
     static constexpr int R = T * SH / 32;
     static constexpr int LPR = T / R;
     static constexpr int STRIPS = T / SH;
-    static constexpr int TW = 8;
+    static constexpr int TW = 2;
     static_assert(LPR * SH == 32 && STRIPS * SH == T, "tile geometry");
 };
 constexpr unsigned kFullMask = 0xffffffffu;
@@ -442,7 +446,7 @@ __device__ __forceinline__ void resolve_run(const unsigned long long* key, int n
 // Work item (camera, first tile): warp w rasterises and resolves tile
 // first + w of the camera, one strip at a time.
 template <int T>
-__global__ void __launch_bounds__(TileGeom<T>::TW * 32, 4) tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr,
+__global__ void __launch_bounds__(TileGeom<T>::TW * 32, 32 / TileGeom<T>::TW) tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr,
                                                                         const TileItem* __restrict__ items) {
     using G = TileGeom<T>;
     constexpr int R = G::R;
