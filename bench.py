@@ -509,6 +509,22 @@ def main():
         e2e = {"value": ws * E * args.steps / t_e2e, "unit": "env-steps/s",
                "h2d_bytes_per_step": int(hf.numel() * 4), "d2h_bytes_per_step": int(bytes_out),
                "path": "vuda_pipeline_run_host (co-scheduled), pinned host buffers, wall clock"}
+        # the loop's ceiling: a plain pinned device -> host copy of one step's frame bytes
+        dev_b = torch.empty(int(bytes_out), dtype=torch.uint8, device="cuda")
+        host_b = torch.empty(int(bytes_out), dtype=torch.uint8).pin_memory()
+        for _ in range(2):
+            host_b.copy_(dev_b, non_blocking=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(10):
+            host_b.copy_(dev_b, non_blocking=True)
+        torch.cuda.synchronize()
+        copy_gbs = 10 * bytes_out / (time.perf_counter() - t) / 1e9
+        achieved_gbs = bytes_out * e2e["value"] / (ws * E) / 1e9
+        e2e["d2h_roofline"] = {"bound": "d2h copy", "achieved_gbs": achieved_gbs, "peak_gbs": copy_gbs,
+                               "frac": achieved_gbs / copy_gbs,
+                               "peak_source": "measured here: pinned device -> host copy of one step's frame bytes"}
+        del dev_b, host_b
 
     flags = env.status()[1]
     env_stats = {"contacts_mean": float(env.contact_counts().mean()), "bodies": 32,
