@@ -334,6 +334,7 @@ __host__ __device__ inline size_t phys_fixed_bytes(int NB, int cmax) {
     f += (size_t)kParts * NB * 4;            // per-part list counters
     f += (size_t)kPairChunk * (4 + 2);       // passing pairs and their first item
     f += (size_t)2 * (kT / 32) * 4;          // scan scratch
+    f += (size_t)8 * NB * 2;                 // plane items (u16: body << 3 | corner)
     f += (size_t)2 * cmax * 2;               // per-body contact lists (u16: contact << 1 | side)
     return align16(f);
 }
@@ -597,6 +598,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     int* plist = ip; ip += kPairChunk;   // units (passing pairs or plane bodies) of the current round
     unsigned short* pitem = reinterpret_cast<unsigned short*>(ip); ip += kPairChunk / 2;   // their first item
     ScanBuf wsum{ip, 0}; ip += 2 * (kT / 32);
+    unsigned short* ptab = reinterpret_cast<unsigned short*>(ip); ip += 4 * NB;   // [8 NB] plane items
     unsigned short* lists = reinterpret_cast<unsigned short*>(ip);
     const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
     Contacts C;
@@ -630,6 +632,18 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                         : S.D(0, i);
     }
     __syncthreads();
+    // plane contact items in canonical order, fixed for the launch (shapes
+    // do not change): one per sphere, the eight corners of a box in sign-bit
+    // order, bodies in order
+    int nplane = 0;
+    for (int i0 = 0; i0 < N; i0 += kT) {
+        const int i = i0 + tid;
+        const int nsub = i < N ? (is_box(S, i) ? 8 : 1) : 0;
+        int tot;
+        const int ex = block_excl_scan(nsub, wsum, tot);
+        for (int k = 0; k < nsub; k++) ptab[nplane + ex + k] = (unsigned short)((i << 3) | k);
+        nplane += tot;
+    }
 
     bool ovf = false;
     int nc = 0;
@@ -671,54 +685,38 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
             for (int i = tid; i < kParts * NB; i += kT) qcnt[i] = 0;
             __syncthreads();
 
-            // 2a. plane contacts: units = bodies in order, one item per sphere,
-            // eight per box (its corners in sign-bit order)
+            // 2a. plane contacts: the launch's plane items (one per sphere, a
+            // box's corners in sign-bit order, bodies in order), hits
+            // compacted in item order
             nc = 0;
             if (sc.plane) {
-                for (int i0 = 0; i0 < N; i0 += kT) {
-                    int i = i0 + tid;
-                    int nsub = i < N ? (is_box(S, i) ? 8 : 1) : 0;
-                    int tot;
-                    int ex = block_excl_scan(nsub, wsum, tot);
-                    if (nsub) {
-                        plist[tid] = i;
-                        pitem[tid] = (unsigned short)ex;
-                    }
-                    const int nu = min(kT, N - i0);
-                    __syncthreads();
-                    for (int u0 = 0; u0 < tot; u0 += kT) {
-                        int u = u0 + tid;
-                        bool hit = false;
-                        int bi = 0;
-                        f3 pt{0.0f, 0.0f, 0.0f};
-                        float d = 0.0f;
-                        if (u < tot) {
-                            int lo = 0, hi = nu - 1;
-                            while (lo < hi) {
-                                int mid = (lo + hi + 1) >> 1;
-                                if (pitem[mid] <= u) lo = mid; else hi = mid - 1;
-                            }
-                            bi = plist[lo];
-                            int k = u - pitem[lo];
-                            if (is_box(S, bi)) {
-                                pt = box_corner(S, bi, k);
-                                d = pt.z;
-                            } else {
-                                float r = S.D(0, bi);
-                                f3 p = ldpos(S, bi);
-                                d = p.z - r;
-                                pt = f3{p.x, p.y, p.z - r};
-                            }
-                            hit = d < sc.margin;
+                for (int u0 = 0; u0 < nplane; u0 += kT) {
+                    const int u = u0 + tid;
+                    bool hit = false;
+                    int bi = 0;
+                    f3 pt{0.0f, 0.0f, 0.0f};
+                    float d = 0.0f;
+                    if (u < nplane) {
+                        const int pe = ptab[u];
+                        bi = pe >> 3;
+                        if (is_box(S, bi)) {
+                            pt = box_corner(S, bi, pe & 7);
+                            d = pt.z;
+                        } else {
+                            float r = S.D(0, bi);
+                            f3 p = ldpos(S, bi);
+                            d = p.z - r;
+                            pt = f3{p.x, p.y, p.z - r};
                         }
-                        int t2;
-                        int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
-                        if (hit) {
-                            int idx = nc + ex2;
-                            if (idx < cmax) put_contact(C, idx, bi, -1, up, pt, d); else ovf = true;
-                        }
-                        nc += t2;
+                        hit = d < sc.margin;
                     }
+                    int t2;
+                    int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
+                    if (hit) {
+                        int idx = nc + ex2;
+                        if (idx < cmax) put_contact(C, idx, bi, -1, up, pt, d); else ovf = true;
+                    }
+                    nc += t2;
                 }
             }
             // 2b. pairs in (i, j) order, kPairChunk candidates per round
@@ -900,9 +898,10 @@ int phys_min_smem_bytes(int max_bodies, int mcpb) { return (int)phys_fixed_bytes
 int phys_smem_bytes_default(int max_bodies, int mcpb) {
     size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
     // room for 4.5 contacts per body in shared memory (a settled pile of
-    // spheres and boxes has about 3.5), more spill to global memory; with 32
-    // bodies this is 31 KB, so 7 environments fit on one SM
-    size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2);
+    // spheres and boxes has about 3.5), less the plane item table's 16 bytes
+    // per body; more spill to global memory.  With 32 bodies this is 31 KB,
+    // so 7 environments fit on one SM
+    size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2) - (size_t)16 * max_bodies;
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;
     return (int)align16(want);
