@@ -392,6 +392,40 @@ def test_pipeline_frames_match_oracle(V, orc):
         np.testing.assert_allclose(f["depth"], o_dep, rtol=DEPTH_RTOL)
 
 
+@pytest.mark.parametrize("mode", ["serialized", "streams"])
+def test_host_loop_forces_in_frames_out_match_oracle(V, orc, mode):
+    """vuda_pipeline_run_host, the end-to-end loop: a different force per step
+    is copied in from pinned host memory before each sim step, and the RGB
+    and depth of every step are copied out into the pinned host ring (slot
+    t & 1).  The last two frames in host memory and the final state match
+    the oracle stepped with the same forces (an odd step count, so both ring
+    slots and the wrap-around are checked)."""
+    import torch
+    sc = S.cfg2(8)
+    st, _, _ = orc.sim_step(sc, 40)
+    sc = dataclasses.replace(sc, **{k: st[k] for k in ("pos", "quat", "vel", "angvel")})
+    n = 5
+    f = np.random.default_rng(11).normal(0, 0.3, (n, 3, sc.num_bodies)).astype(np.float32)
+    env = V.Env(sc)
+    if mode == "streams":
+        env.coschedule(V.COSCHED_STREAMS)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    hf = torch.from_numpy(f).pin_memory()
+    hr = torch.zeros((2, env.P, 3), dtype=torch.uint8).pin_memory()
+    hd = torch.zeros((2, env.P), dtype=torch.float32).pin_memory()
+    env.pipeline_run_host(n, ring, hr, hd, h_force=hf, force_per_step=True)
+    g = env.get_state()
+    st_o = sc.state()
+    for t in range(n):
+        st_o, _, _ = orc.sim_step(sc, 1, state=st_o, force=f[t])
+        if t >= n - 2:
+            o_rgb, o_dep, _, _ = orc.render(sc, st_o["pos"], st_o["quat"])
+            np.testing.assert_allclose(hd[t & 1].numpy(), o_dep, rtol=DEPTH_RTOL, atol=0, err_msg="step %d" % t)
+            assert np.abs(hr[t & 1].numpy().astype(int) - o_rgb.astype(int)).max() <= 1
+    _cmp_state(g, st_o, "final")
+    env.close()
+
+
 def test_full_size_cfg2_sampled(V, orc):
     """1024 envs x 32 bodies at 128x128, in the benchmark's launch
     configuration: sampled environments match the oracle run on those
