@@ -255,6 +255,26 @@ def test_render_non_square_cameras(V, orc, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
+def test_render_degenerate_camera_sizes(V, orc, path):
+    """Cameras of one pixel, one row and one column, and a 2 x 3 camera:
+    tiles and runs that are almost empty (most lanes own no pixel)."""
+    sc = S.generate(4, np.array([5, 6, 4, 7]), 909, kinds="mixed", res=np.array([1, 37, 1, 2]),
+                    height=np.array([1, 1, 29, 3]), substeps=4)
+    st, _, _ = orc.sim_step(sc, 20)
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], path=path)
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_render_degenerate_camera_sizes_other_tiles(V, orc, tile):
+    sc = S.generate(4, np.array([5, 6, 4, 7]), 909, kinds="mixed", res=np.array([1, 37, 1, 2]),
+                    height=np.array([1, 1, 29, 3]), substeps=4)
+    st, _, _ = orc.sim_step(sc, 20)
+    env = V.Env(sc, render_path=V.RENDER_TILED, tile_size=tile)
+    _render_cmp(V, orc, sc, st["pos"], st["quat"], env=env)
+    env.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_render_near_plane_flags(V, orc, path):
     sc = S.custom([dict(type="sphere", r=0.1, pos=(0.0, -3.0, 1.5)),
                    dict(type="box", h=(0.05, 0.05, 0.05), pos=(0.1, 0.0, 0.05))], res=64)
