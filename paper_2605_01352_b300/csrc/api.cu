@@ -348,12 +348,23 @@ vuda_status build_render_list(vuda_env* env, int br, const std::vector<int32_t>&
     };
     std::stable_sort(io.begin(), io.end(), [&](int a, int b) { return cost(a) > cost(b); });
     vuda_status s = VUDA_OK;
+    int4* ri_new[2] = {nullptr, nullptr};
     for (int slot = 0; slot < 2 && s == VUDA_OK; slot++) {
         std::vector<int4> ri(io.size());
         for (size_t k = 0; k < io.size(); k++) ri[k] = make_int4(slot << 24, ic[io[k]], iy[io[k]], 0);
-        s = upload(env, &env->ren_items[slot], ri.data(), ri.size());
+        s = upload(env, &ri_new[slot], ri.data(), ri.size());
     }
-    if (s != VUDA_OK) return s;
+    const int64_t new_bytes = std::max<int64_t>((int64_t)ic.size(), 1) * (int64_t)sizeof(int4);
+    if (s != VUDA_OK) {
+        for (int4* p : ri_new) dfree(env, p, new_bytes);
+        return s;
+    }
+    // the previous lists (of env->nitems items; none on the first build) are
+    // replaced as a whole; the caller has let enqueued work finish
+    for (int slot = 0; slot < 2; slot++) {
+        dfree(env, env->ren_items[slot], std::max<int64_t>(env->nitems, 1) * (int64_t)sizeof(int4));
+        env->ren_items[slot] = ri_new[slot];
+    }
     int dev_sms = 0;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, env->device);
     env->ren_grid = std::max(1, std::min((int)ic.size(), dev_sms * render_ctas_per_sm(br, env->max_w)));
@@ -437,7 +448,8 @@ vuda_status build_lists(vuda_env* env) {
 }
 
 // Rebuild the render work items (and their persistent lists) for a new band
-// height.  The previous device arrays stay owned by the batch until destroy.
+// height, freeing the previous ones once the work enqueued with them is done.
+// On failure the batch keeps its previous items.
 vuda_status set_band_rows(vuda_env* env, int br) {
     if (br <= 0 || (env->C && render_smem_for(br, env->max_w) > 227 * 1024)) return invalid("band rows out of range");
     std::vector<int32_t> ic, iy;
@@ -446,11 +458,25 @@ vuda_status set_band_rows(vuda_env* env, int br) {
             ic.push_back(c);
             iy.push_back(y);
         }
-    vuda_status s = upload(env, &env->item_cam, ic.data(), ic.size());
-    if (s == VUDA_OK) s = upload(env, &env->item_y0, iy.data(), iy.size());
+    vuda_status s = vuda_wait(env, 0);
+    if (s == VUDA_OK) s = vuda_wait(env, 1);
     if (s != VUDA_OK) return s;
-    if (env->lists) s = build_render_list(env, br, ic, iy);
-    if (s != VUDA_OK) return s;
+    CK(cudaDeviceSynchronize());
+    int32_t *cam = nullptr, *y0 = nullptr;
+    const int64_t new_bytes = std::max<int64_t>((int64_t)ic.size(), 1) * 4;
+    s = upload(env, &cam, ic.data(), ic.size());
+    if (s == VUDA_OK) s = upload(env, &y0, iy.data(), iy.size());
+    if (s == VUDA_OK && env->lists) s = build_render_list(env, br, ic, iy);
+    if (s != VUDA_OK) {
+        dfree(env, cam, new_bytes);
+        dfree(env, y0, new_bytes);
+        return s;
+    }
+    const int64_t old_bytes = std::max<int64_t>(env->nitems, 1) * 4;
+    dfree(env, env->item_cam, old_bytes);
+    dfree(env, env->item_y0, old_bytes);
+    env->item_cam = cam;
+    env->item_y0 = y0;
     env->band_rows = br;
     env->nitems = (int)ic.size();
     env->h_item_cam = ic;

@@ -206,6 +206,7 @@ def test_set_tiling_switches_without_changing_frames(V):
     sc = S.cfg2(48)
     env = V.Env(sc, render_path=V.RENDER_TILED)
     assert (env.info().tile_size, env.info().tile_bin_limit) == (16, 9)
+    bytes0 = env.info().device_bytes
     ring = [env.alloc_frame(), env.alloc_frame()]
     env.sim_step(40)
     ref = None
@@ -226,6 +227,9 @@ def test_set_tiling_switches_without_changing_frames(V):
         with pytest.raises(V.VudaError):
             env.set_tiling(*bad)
         assert (env.info().tile_size, env.info().tile_bin_limit) == (32, 16)
+    # the replaced tile lists were freed: back at the first parameters, the batch holds what it held
+    env.set_tiling(16, 9)
+    assert env.info().device_bytes == bytes0
     env.close()
     band = V.Env(S.cfg2(4), render_path=V.RENDER_BAND)
     with pytest.raises(V.VudaError):
@@ -644,6 +648,14 @@ def test_autotune_keeps_results_and_caches(V):
     ring3 = [env3.alloc_frame(), env3.alloc_frame()]
     res3 = env3.autotune(ring3, steps=2, use_cache=False)
     assert res3["band_rows"] in (16, 32, 64, 128) and res3["tile_size"] == 0
+    # a second tuning pass (the persistent work lists now exist and are
+    # rebuilt for every band height tried) frees the work items it replaces:
+    # the batch ends up holding one set of them, which at 16 cameras of 128
+    # rows is at most 16 x 8 bands x (4 + 4 + 2 x 16) bytes
+    bytes3 = env3.info().device_bytes
+    env3.autotune(ring3, steps=2, use_cache=False)
+    grown = env3.info().device_bytes - bytes3
+    assert abs(grown) <= 16 * 8 * (4 + 4 + 2 * 16), grown
     env3.close()
 
 
