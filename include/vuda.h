@@ -148,8 +148,9 @@ typedef struct {
  * upper bound of which only the visible part is written).  AUTO: TILED where it applies and its scratch
  * fits (at most half of the free device memory, and within
  * hbm_budget_bytes), else BAND.
- * The render work-list launches of VUDA_COSCHED_SHARED and of the serving
- * loop use the band kernel; persistent = 1 makes the physics a work-list
+ * The render work-list launches of VUDA_COSCHED_SHARED use the band kernel;
+ * the serving loop renders each job on the path its batch chose (work lists
+ * over several jobs for both); persistent = 1 makes the physics a work-list
  * launch and keeps the chosen render path. */
 #define VUDA_RENDER_AUTO 0
 #define VUDA_RENDER_BAND 1

@@ -305,8 +305,30 @@ vuda_status env_estimate_bytes(const vuda_scene* sc, const vuda_sim_params* p, i
     bytes += (int64_t)sc->mesh_vert_off[sc->num_meshes] * 12 + (int64_t)sc->mesh_tri_off[sc->num_meshes] * 12;
     bytes += C * 128 + (P / 16 + C) * 16 + 64 * 1024;                       // cameras, items, slack
     bytes += (int64_t)sc->mesh_tri_off[sc->num_meshes] * 8 + (int64_t)sc->mesh_vert_off[sc->num_meshes] * 8;
+    bytes += tiled_scratch_estimate(sc);   // the tiled render path, where it applies
     *out = bytes;
     return VUDA_OK;
+}
+
+int64_t tiled_scratch_estimate(const vuda_scene* sc) {
+    const int E = sc->num_envs;
+    if (E <= 0) return 0;
+    const int gm = sc->ground_mesh;
+    const int64_t tg = sc->mesh_tri_off[gm + 1] - sc->mesh_tri_off[gm];
+    const int tile = tiled_default_tile(), nlim = tiled_default_bin_limit(), tpi = tiled_tiles_per_item(tile);
+    int64_t bytes = 0;
+    for (int e = 0; e < E; e++) {
+        int64_t tc = tg;
+        for (int b = sc->body_off[e]; b < sc->body_off[e + 1]; b++)
+            tc += sc->mesh_tri_off[sc->mesh_id[b] + 1] - sc->mesh_tri_off[sc->mesh_id[b]];
+        for (int c = sc->cam_off[e]; c < sc->cam_off[e + 1]; c++) {
+            const int64_t ntl = (int64_t)((sc->cam_w[c] + tile - 1) / tile) * ((sc->cam_h[c] + tile - 1) / tile);
+            if (ntl > tiled_max_tiles()) return 0;   // the batch renders on the band path
+            bytes += tc * (int64_t)(tiled_record_bytes() + 4 + 4 * nlim) + (ntl + 2) * 4 +
+                     (1 + (ntl + tpi - 1) / tpi) * (int64_t)sizeof(TileItem);
+        }
+    }
+    return bytes;
 }
 }  // namespace vuda
 

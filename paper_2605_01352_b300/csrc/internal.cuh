@@ -22,6 +22,18 @@ struct SimConst {
     int plane, mcpb;
 };
 
+// Scratch of the tiled render path (tiled.cu), per camera c of env e with
+// T_e triangles and n_c tiles (of the batch's tile size): records
+// [rec_base, + T_e) of tiled_record_bytes() each, wide list [rec_base, + T_e),
+// tile lists [ent_base, + bin_limit T_e), offsets [toff_base, + n_c + 2)
+// (n_c + 1 list offsets, then the wide-list length).
+struct TileScratch {
+    void* rec;
+    uint32_t* ent;
+    uint32_t* wide;
+    int32_t* toff;
+};
+
 // Device-resident batch.  All arrays are device pointers.
 struct DevBatch {
     int E, B, C;
@@ -169,17 +181,6 @@ int render_vcap();
 // Per-triangle flat colours of the batch for the poses `pose` (render.cu).
 cudaError_t launch_shade(const DevBatch& b, const float* pose, cudaStream_t stream);
 
-// Scratch of the tiled render path (tiled.cu), per camera c of env e with
-// T_e triangles and n_c tiles (of the batch's tile size): records
-// [rec_base, + T_e) of tiled_record_bytes() each, wide list [rec_base, + T_e),
-// tile lists [ent_base, + bin_limit T_e), offsets [toff_base, + n_c + 2)
-// (n_c + 1 list offsets, then the wide-list length).
-struct TileScratch {
-    void* rec;
-    uint32_t* ent;
-    uint32_t* wide;
-    int32_t* toff;
-};
 // A camera (bin_kernel, tile0 = 0) or a raster work item of
 // tiled_tiles_per_item() tiles from tile0 (tile_kernel), with everything the
 // kernels need about the camera in one 80-byte record.
@@ -203,6 +204,31 @@ size_t tiled_record_bytes();
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
                                 const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim,
                                 cudaStream_t stream);
+// One batch of a tiled work list over several batches: its device camera
+// and raster items and its scratch (as built for its own launches), the
+// list positions of its first camera and first raster item, and
+// `desc | slot << 24`.  (The scratch is kept here, not in DevBatch: the
+// physics kernels copy DevBatch into shared memory, where 7 CTAs per SM
+// leave no room for it to grow.)
+struct TiledJob {
+    const TileItem* cams;
+    const TileItem* items;
+    TileScratch ts;
+    int cam0, item0;
+    int tag;
+    int pad;
+};
+// Work-list form over several batches with the default tile size and bin
+// limit: camera k of the list is camera k - cam0 of the job holding it (the
+// last job with cam0 <= k), likewise for raster items; batch descs[desc]
+// renders from its pose slot into its own frame (DevBatch::frame) with the
+// job's tiled scratch.
+cudaError_t launch_render_tiled_list(const DevBatch* descs, const TiledJob* jobs, int njobs, int ncams, int nitems,
+                                     cudaStream_t stream);
+int tiled_default_tile();
+// Tiled scratch bytes of a scene at the default tile size and bin limit
+// (0 if a camera has more tiles than the path supports).
+int64_t tiled_scratch_estimate(const vuda_scene* sc);
 
 void set_error(const std::string& s);
 // Device bytes a batch will hold once created (an upper estimate).

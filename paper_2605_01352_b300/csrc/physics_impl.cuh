@@ -900,7 +900,8 @@ int phys_smem_bytes_default(int max_bodies, int mcpb) {
     // room for 4.5 contacts per body in shared memory (a settled pile of
     // spheres and boxes has about 3.5), less the plane item table's 16 bytes
     // per body; more spill to global memory.  With 32 bodies this is 31 KB,
-    // so 7 environments fit on one SM
+    // so 7 environments fit on one SM, with a few hundred bytes to spare: the
+    // kernels' static shared memory (the batch descriptor) must not grow
     size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2) - (size_t)16 * max_bodies;
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;

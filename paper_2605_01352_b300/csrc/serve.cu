@@ -185,6 +185,7 @@ struct vuda_server {
     Buf<int2> sim_items[kRing];
     Buf<int4> ren_items[kRing];
     Buf<int2> shade_items[kRing];
+    Buf<TiledJob> tile_jobs[kRing];   // jobs on the tiled path: their device items and list positions
 };
 
 namespace {
@@ -210,7 +211,7 @@ void admit(vuda_server* s) {
         s->admit_queue.pop_front();
         vuda_env_opts eo{};
         eo.device = s->o.device;
-        eo.render_path = VUDA_RENDER_BAND;   // jobs render through the band work list
+        eo.render_path = VUDA_RENDER_AUTO;   // tiled where its scratch fits, else the band work list
         vuda_status st = vuda_env_create(&j->scene->view, &j->params, &eo, &j->env);
         if (st == VUDA_OK) {
             size_t P = (size_t)j->env->P;
@@ -268,38 +269,59 @@ void retire_job(vuda_server* s, Job* j) {
 bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t>>& batch) {
     const int64_t no = s->iter_no;
     const int slot_buf = (int)(no % vuda_server::kRing);
+    // jobs on the tiled path (created with the default tile size and bin
+    // limit) render through the tiled work lists, the others through the band
+    // work list
+    auto tiled = [](const Job* j) {
+        return j->env->tiled && j->env->tile_size == tiled_default_tile() &&
+               j->env->bin_limit == tiled_default_bin_limit();
+    };
     int max_bodies = 1, max_mcpb = 1, max_w = 1, max_h = 1;
-    size_t nsim = 0, nshade = 0;
+    size_t nsim = 0, nshade = 0, ntj = 0;
     for (auto& pr : batch) {
         Job* j = pr.first;
         max_bodies = std::max(max_bodies, j->env->max_bodies);
         max_mcpb = std::max(max_mcpb, j->params.max_contacts_per_body);
+        nsim += j->env->E;
+        if (tiled(j)) {
+            ntj++;
+            continue;
+        }
         for (int w : j->cam_w) max_w = std::max(max_w, w);
         for (int h : j->cam_h) max_h = std::max(max_h, h);
-        nsim += j->env->E;
         nshade += j->env->B + j->env->E;
     }
     const int br = render_default_band_rows(max_w, max_h);
     size_t nren = 0;
     for (auto& pr : batch)
-        for (size_t c = 0; c < pr.first->cam_h.size(); c++) nren += (pr.first->cam_h[c] + br - 1) / br;
+        if (!tiled(pr.first))
+            for (size_t c = 0; c < pr.first->cam_h.size(); c++) nren += (pr.first->cam_h[c] + br - 1) / br;
     Buf<int2>& si = s->sim_items[slot_buf];
     Buf<int4>& ri = s->ren_items[slot_buf];
     Buf<int2>& hi = s->shade_items[slot_buf];
-    if (si.reserve(nsim) != cudaSuccess || ri.reserve(nren) != cudaSuccess || hi.reserve(nshade) != cudaSuccess) {
+    Buf<TiledJob>& tj = s->tile_jobs[slot_buf];
+    if (si.reserve(nsim) != cudaSuccess || ri.reserve(nren) != cudaSuccess || hi.reserve(nshade) != cudaSuccess ||
+        tj.reserve(ntj) != cudaSuccess) {
         s->fatal = "serving item buffers: out of memory";
         return false;
     }
     // items, largest environments and bands first
     std::vector<std::pair<int, int2>> sims;
     sims.reserve(nsim);
-    size_t a = 0, b = 0, c2 = 0;
+    size_t a = 0, b = 0, c2 = 0, kj = 0;
+    int ncams = 0, nitems = 0;
     for (auto& pr : batch) {
         Job* j = pr.first;
         const int slot = (int)(j->env->steps & 1);
         const int tag = j->desc | (slot << 24);
         const std::vector<int32_t>& boff = j->body_off;
         for (int e = 0; e < j->env->E; e++) sims.push_back({boff[e + 1] - boff[e], make_int2(tag, e)});
+        if (tiled(j)) {
+            tj.h[kj++] = TiledJob{j->env->tcams, j->env->titems, j->env->ts, ncams, nitems, tag, 0};
+            ncams += j->env->C;
+            nitems += j->env->ntitems;
+            continue;
+        }
         int cam = 0;
         for (size_t cc = 0; cc < j->cam_h.size(); cc++, cam++)
             for (int y = 0; y < j->cam_h[cc]; y += br) ri.h[b++] = make_int4(tag, cam, y, 0);
@@ -356,12 +378,17 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
                                            cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, s->sim_s);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_sim, s->sim_s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ri.d, ri.h, nren * sizeof(int4), cudaMemcpyHostToDevice, s->ren_s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hi.d, hi.h, nshade * sizeof(int2), cudaMemcpyHostToDevice, s->ren_s);
+    if (e == cudaSuccess && nren)
+        e = cudaMemcpyAsync(ri.d, ri.h, nren * sizeof(int4), cudaMemcpyHostToDevice, s->ren_s);
+    if (e == cudaSuccess && nshade)
+        e = cudaMemcpyAsync(hi.d, hi.h, nshade * sizeof(int2), cudaMemcpyHostToDevice, s->ren_s);
+    if (e == cudaSuccess && ntj)
+        e = cudaMemcpyAsync(tj.d, tj.h, ntj * sizeof(TiledJob), cudaMemcpyHostToDevice, s->ren_s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->ren_s, ev_sim, 0);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && (nren || nshade))
         e = launch_render_list(s->descs, ri.d, (int)nren, s->counters + 1, ren_grid, hi.d, (int)nshade, br, max_w,
                                nullptr, SmGate{nullptr, 0}, s->ren_s);
+    if (e == cudaSuccess && ntj) e = launch_render_tiled_list(s->descs, tj.d, (int)ntj, ncams, nitems, s->ren_s);
     if (e == cudaSuccess) e = cudaEventRecord(ev_done, s->ren_s);
     if (e != cudaSuccess) {
         s->fatal = std::string("serving launch: ") + cudaGetErrorString(e);
@@ -510,6 +537,7 @@ vuda_status vuda_serve_destroy(vuda_server_t s) {
         s->sim_items[k].release();
         s->ren_items[k].release();
         s->shade_items[k].release();
+        s->tile_jobs[k].release();
     }
     if (s->ren_s && s->ren_s != s->sim_s) cudaStreamDestroy(s->ren_s);
     if (s->sim_s) cudaStreamDestroy(s->sim_s);

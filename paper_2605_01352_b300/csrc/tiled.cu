@@ -140,9 +140,11 @@ __device__ __forceinline__ int cta_excl_scan(int v, int* wsum, int& total) {
     return off + x - v;
 }
 
+// Set-up, shading and binning of camera `ci` of batch b (pose: its pose
+// slot), by the whole CTA.
 template <int T>
-__global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts,
-                                                  const TileItem* __restrict__ cams, int nlim) {
+__device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __restrict__ pose, const TileScratch& ts,
+                                           const TileItem& ci, int nlim) {
     __shared__ int vX[kVertexCache], vY[kVertexCache], vflag[kVertexCache];
     __shared__ float viz[kVertexCache];
     __shared__ float vW[kVertexCache][3];   // world positions, for the flat colours
@@ -151,7 +153,6 @@ __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __
     __shared__ int s_nrec, s_nwide;
     __shared__ unsigned s_flags;
 
-    const TileItem ci = load_item(cams + blockIdx.x);
     const int cam = ci.cam, e = ci.env;
     const int W = ci.W, H = ci.H;
     const int tiles_x = ci.tiles_x, ntiles = ci.ntiles;
@@ -289,6 +290,42 @@ __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __
         }
     }
     if (threadIdx.x == 0 && s_flags) atomicOr(b.flags + e, s_flags);
+}
+
+template <int T>
+__global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts,
+                                                  const TileItem* __restrict__ cams, int nlim) {
+    bin_camera<T>(b, pose, ts, load_item(cams + blockIdx.x), nlim);
+}
+
+// The job of work-list position k: the last job whose first position
+// (cam0, or item0 when `items`) is <= k.  Uniform across the calling threads.
+__device__ __forceinline__ int find_job(const TiledJob* __restrict__ jobs, int njobs, int k, bool items) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int first = items ? __ldg(&jobs[mid].item0) : __ldg(&jobs[mid].cam0);
+        if (first <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Work-list form: CTA k sets up camera k of the list; its job's batch
+// descriptor is copied to shared memory.
+template <int T>
+__global__ void __launch_bounds__(kBT, 4) bin_list_kernel(const DevBatch* __restrict__ descs,
+                                                       const TiledJob* __restrict__ jobs, int njobs, int nlim) {
+    __shared__ DevBatch sd;
+    const int jb = find_job(jobs, njobs, blockIdx.x, false);
+    const int tag = __ldg(&jobs[jb].tag);
+    const TileItem ci = load_item(jobs[jb].cams + (blockIdx.x - __ldg(&jobs[jb].cam0)));
+    const int* src = reinterpret_cast<const int*>(descs + (tag & kItemDescMask));
+    int* dst = reinterpret_cast<int*>(&sd);
+    for (int k = threadIdx.x; k < (int)(sizeof(DevBatch) / 4); k += kBT) dst[k] = src[k];
+    __syncthreads();
+    const TileScratch ts = jobs[jb].ts;
+    bin_camera<T>(sd, sd.pose[(tag >> 24) & 1], ts, ci, nlim);
 }
 
 // One lane rasterises a small record over the pixels [x0, x1] x [y0, y1] of
@@ -446,14 +483,13 @@ __device__ __forceinline__ void resolve_run(const unsigned long long* key, int n
 // Work item (camera, first tile): warp w rasterises and resolves tile
 // first + w of the camera, one strip at a time.
 template <int T>
-__global__ void __launch_bounds__(TileGeom<T>::TW * 32, 32 / TileGeom<T>::TW) tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr,
-                                                                        const TileItem* __restrict__ items) {
+__device__ __forceinline__ void tile_work(const uint32_t* __restrict__ tri_color, const TileScratch& ts,
+                                          const vuda_frame& fr, const TileItem* __restrict__ itp) {
     using G = TileGeom<T>;
     constexpr int R = G::R;
     __shared__ unsigned long long s_key[G::TW][T * G::SH];
     __shared__ int s_big[G::TW][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const TileItem* itp = items + blockIdx.x;
     const int4 geo = __ldg(reinterpret_cast<const int4*>(itp));        // cam, tile0, W, H
     const int2 tl2 = __ldg(reinterpret_cast<const int2*>(itp) + 2);    // tiles_x, ntiles
     const longlong2 rb = __ldg(reinterpret_cast<const longlong2*>(itp) + 2);   // rec_base, ent_base
@@ -519,14 +555,34 @@ __global__ void __launch_bounds__(TileGeom<T>::TW * 32, 32 / TileGeom<T>::TW) ti
                 const unsigned long long kk = sl[k];
                 key[k] = key[k] < kk ? key[k] : kk;
             }
-            resolve_run<R>(key, nx, pc.x + (int64_t)y * W + xs, b.tri_color + pc.y, fr);
+            resolve_run<R>(key, nx, pc.x + (int64_t)y * W + xs, tri_color + pc.y, fr);
         }
     }
+}
+
+template <int T>
+__global__ void __launch_bounds__(TileGeom<T>::TW * 32, 32 / TileGeom<T>::TW)
+    tile_kernel(DevBatch b, TileScratch ts, vuda_frame fr, const TileItem* __restrict__ items) {
+    tile_work<T>(b.tri_color, ts, fr, items + blockIdx.x);
+}
+
+// Work-list form: CTA k rasterises raster item k of the list; the frame,
+// colour table and scratch are its job's batch's.
+template <int T>
+__global__ void __launch_bounds__(TileGeom<T>::TW * 32, 32 / TileGeom<T>::TW)
+    tile_list_kernel(const DevBatch* __restrict__ descs, const TiledJob* __restrict__ jobs, int njobs) {
+    const int jb = find_job(jobs, njobs, blockIdx.x, true);
+    const TileItem* itp = jobs[jb].items + (blockIdx.x - __ldg(&jobs[jb].item0));
+    const DevBatch* d = descs + (__ldg(&jobs[jb].tag) & kItemDescMask);
+    const TileScratch ts = jobs[jb].ts;
+    const vuda_frame fr = d->frame;
+    tile_work<T>(d->tri_color, ts, fr, itp);
 }
 
 }  // namespace
 
 int tiled_max_tiles() { return kMaxTiles; }
+int tiled_default_tile() { return 16; }
 int tiled_default_bin_limit() { return kNarrowTiles; }
 int tiled_max_bin_limit() { return kMaxBinLimit; }
 int tiled_tiles_per_item(int tile) {
@@ -542,6 +598,16 @@ static cudaError_t launch_tiled_t(const DevBatch& b, const float* pose, const vu
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || nitems == 0) return err;
     tile_kernel<T><<<nitems, TileGeom<T>::TW * 32, 0, stream>>>(b, ts, fr, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_tiled_list(const DevBatch* descs, const TiledJob* jobs, int njobs, int ncams, int nitems,
+                                     cudaStream_t stream) {
+    if (njobs == 0 || ncams == 0) return cudaSuccess;
+    bin_list_kernel<16><<<ncams, kBT, 0, stream>>>(descs, jobs, njobs, kNarrowTiles);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || nitems == 0) return err;
+    tile_list_kernel<16><<<nitems, TileGeom<16>::TW * 32, 0, stream>>>(descs, jobs, njobs);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,11 @@ def V():
 
 
 def _jobs():
-    return {"A": S.cfg2(8), "B": S.cfg1(6), "C": S.cfg4(5), "D": S.cfg2(4, env_base=100)}
+    # E's 800 x 660 camera has more tiles than the tiled path holds: it
+    # renders through the band work list beside the others' tiled work lists
+    return {"A": S.cfg2(8), "B": S.cfg1(6), "C": S.cfg4(5), "D": S.cfg2(4, env_base=100),
+            "E": S.generate(2, np.array([5, 7]), 77, kinds="mixed", res=np.array([800, 64]),
+                            height=np.array([660, 48]), substeps=4)}
 
 
 def _alone(V, sc, n):
@@ -41,7 +45,7 @@ def _alone(V, sc, n):
 
 def test_job_results_are_the_same_alone_and_in_a_mix(V, orc):
     jobs = _jobs()
-    counts = {"A": 5, "B": 7, "C": 4, "D": 6}
+    counts = {"A": 5, "B": 7, "C": 4, "D": 6, "E": 3}
     srv = V.Server(max_inflight=2)
     ids = {k: srv.add_job(sc) for k, sc in jobs.items()}
     order = [k for k, n in counts.items() for _ in range(n)]
@@ -63,22 +67,27 @@ def test_job_results_are_the_same_alone_and_in_a_mix(V, orc):
     assert st["requests_done"] == sum(counts.values())
     assert st["max_batch"] >= 2          # requests of several jobs shared a launch
     mixed = {k: (srv.job_env(ids[k]).get_state(), srv.read_frame(ids[k])) for k in jobs}
+    paths = {k: srv.job_env(ids[k]).info().render_path for k in jobs}
+    assert paths == {"A": V.RENDER_TILED, "B": V.RENDER_TILED, "C": V.RENDER_TILED, "D": V.RENDER_TILED,
+                     "E": V.RENDER_BAND}
     srv.close()
-    for k in ("A", "C"):
+    for k in ("A", "C", "E"):
         st_a, fr_a = _alone(V, jobs[k], counts[k])
         st_m, fr_m = mixed[k]
         for f in st_a:
             np.testing.assert_array_equal(st_a[f], st_m[f])
         for x, y in zip(fr_a, fr_m):
             np.testing.assert_array_equal(x, y)
-    # and the job matches the oracle
-    sc = jobs["A"]
-    so, _, _ = orc.sim_step(sc, counts["A"])
-    for f in ("pos", "vel", "quat", "angvel"):
-        np.testing.assert_allclose(mixed["A"][0][f], so[f], rtol=1e-5, atol=1e-5)
-    o_rgb, o_dep, o_tid, _ = orc.render(sc, so["pos"], so["quat"])
-    np.testing.assert_array_equal(mixed["A"][1][2], o_tid)
-    np.testing.assert_allclose(mixed["A"][1][1], o_dep, rtol=1e-6)
+    # and the jobs of both render paths match the oracle
+    for k in ("A", "E"):
+        sc = jobs[k]
+        so, _, _ = orc.sim_step(sc, counts[k])
+        for f in ("pos", "vel", "quat", "angvel"):
+            np.testing.assert_allclose(mixed[k][0][f], so[f], rtol=1e-5, atol=1e-5)
+        o_rgb, o_dep, o_tid, _ = orc.render(sc, so["pos"], so["quat"])
+        np.testing.assert_array_equal(mixed[k][1][2], o_tid)
+        np.testing.assert_allclose(mixed[k][1][1], o_dep, rtol=1e-6)
+        assert np.abs(mixed[k][1][0].astype(int) - o_rgb.astype(int)).max() <= 1
 
 
 def test_admission_waits_for_budget(V):
