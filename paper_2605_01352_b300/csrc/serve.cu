@@ -327,7 +327,18 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
             for (int y = 0; y < j->cam_h[cc]; y += br) ri.h[b++] = make_int4(tag, cam, y, 0);
         for (int u = 0; u < j->env->B + j->env->E; u++) hi.h[c2++] = make_int2(tag, u);
     }
-    std::stable_sort(sims.begin(), sims.end(), [](auto& x, auto& y) { return x.first > y.first; });
+    {
+        // largest environments first: a stable counting sort by body count
+        // (the same order as a stable comparison sort, in linear time)
+        int maxb = 0;
+        for (auto& p : sims) maxb = std::max(maxb, p.first);
+        std::vector<size_t> start((size_t)maxb + 2, 0);
+        for (auto& p : sims) start[(size_t)(maxb - p.first) + 1]++;
+        for (size_t k = 1; k < start.size(); k++) start[k] += start[k - 1];
+        std::vector<std::pair<int, int2>> sorted(sims.size());
+        for (auto& p : sims) sorted[start[(size_t)(maxb - p.first)]++] = p;
+        sims.swap(sorted);
+    }
     for (auto& p : sims) si.h[a++] = p.second;
 
     // physics by size class (the items are sorted by body count, so each class
