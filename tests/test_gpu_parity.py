@@ -450,16 +450,24 @@ def test_host_loop_forces_in_frames_out_match_oracle(V, orc, mode):
     env.close()
 
 
-def test_full_size_cfg2_sampled(V, orc):
-    """1024 envs x 32 bodies at 128x128, in the benchmark's launch
-    configuration: sampled environments match the oracle run on those
-    environments alone (environments are independent)."""
+@pytest.mark.parametrize("launch", ["green", "bench"])
+def test_full_size_cfg2_sampled(V, orc, launch):
+    """1024 envs x 32 bodies at 128x128: sampled environments match the
+    oracle run on those environments alone (environments are independent).
+    Launch configurations: the paper's disjoint partitions (green contexts,
+    3 steps), and the benchmark's headline one (two streams sharing all SMs,
+    sim stream first, 8 pipelined steps replayed from a CUDA graph)."""
     import torch
     sc = S.cfg2()
     env = V.Env(sc)
     ring = [env.alloc_frame(), env.alloc_frame()]
-    env.coschedule(V.COSCHED_GREEN)
-    steps = 3
+    if launch == "green":
+        env.coschedule(V.COSCHED_GREEN)
+        steps = 3
+    else:
+        env.coschedule(V.COSCHED_STREAMS, priority=V.PRIORITY_SIM)
+        steps = 8
+        env.pipeline_capture(steps, ring)
     env.pipeline_run(steps, ring)
     torch.cuda.synchronize()
     g = env.get_state()
