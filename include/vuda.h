@@ -41,7 +41,7 @@ typedef enum {
     VUDA_ERR_OOM = 2,          /* device allocation failed or HBM budget exceeded */
     VUDA_ERR_CUDA = 3,         /* a CUDA call failed; see vuda_last_error() */
     VUDA_ERR_OVERFLOW = 4,     /* a capacity was exceeded (see the env flags) */
-    VUDA_ERR_TIMEOUT = 5,      /* a bounded wait gave up */
+    VUDA_ERR_TIMEOUT = 5,      /* a bounded wait gave up (vuda_serve_poll with wait_ms > 0) */
     VUDA_ERR_BUSY = 6,         /* resource in use (e.g. serving queue full) */
     VUDA_ERR_UNSUPPORTED = 7   /* feature not available on this device/driver */
 } vuda_status;
@@ -52,7 +52,8 @@ typedef enum {
 #define VUDA_FLAG_NEAR_DISCARD     0x2u /* a triangle with a vertex before the near plane was skipped */
 #define VUDA_FLAG_GUARD_DISCARD    0x4u /* a triangle beyond the 2^14 px guard band was skipped */
 #define VUDA_FLAG_MESH_CAPACITY    0x8u /* a mesh larger than the render vertex cache was skipped */
-#define VUDA_FLAG_TIMEOUT          0x10u /* a bounded device wait gave up */
+#define VUDA_FLAG_BAD_RANGE        0x10u /* the environment's body range was invalid (outside the batch, or more
+                                            bodies than max_bodies): the environment was skipped, nothing written */
 
 typedef void* vuda_stream_t;        /* cudaStream_t */
 typedef struct vuda_env* vuda_env_t;
@@ -337,18 +338,24 @@ vuda_status vuda_pipeline_run_host(vuda_env_t env, int32_t nsteps, const float* 
  * render (phase 1) stream has finished (wait_step / wait_render, Table 1). */
 vuda_status vuda_wait(vuda_env_t env, int32_t phase);
 
-/* Copy the state to / from host SoA arrays (synchronous). */
+/* Copy the state to / from host SoA arrays (synchronous).  Not in the paper
+ * (its loop never leaves the device): checkpoint / resume of a batch, and
+ * the common starting state of parity checks. */
 vuda_status vuda_env_get_state(vuda_env_t env, const vuda_state* out);
 vuda_status vuda_env_set_state(vuda_env_t env, const vuda_state* in);
-/* Read the pose slot (pos[3][B], quat[4][B]) to host. */
+/* Read the pose slot (pos[3][B], quat[4][B]) to host.  Not in the paper: the
+ * renderer reads pose slots in place (the zero-copy sharing of Sec. 3.1);
+ * these copies serve inspection and rendering of given poses. */
 vuda_status vuda_env_get_pose(vuda_env_t env, int32_t slot, float* pos, float* quat);
 /* Write a pose slot from host arrays (used to render given poses). */
 vuda_status vuda_env_set_pose(vuda_env_t env, int32_t slot, const float* pos, const float* quat);
 
 /* Read (and optionally clear) per-env status bits into flags[E] (host, may
- * be NULL); or_flags receives their union.  Synchronous. */
+ * be NULL); or_flags receives their union.  Synchronous.  Not in the paper:
+ * the kernels' record of deterministic degradation (VUDA_FLAG_*). */
 vuda_status vuda_env_status(vuda_env_t env, uint32_t* flags, uint32_t* or_flags, int32_t clear);
-/* Number of contacts of each env at the last substep (host int32[E]). */
+/* Number of contacts of each env at the last substep (host int32[E]).  Not
+ * in the paper: a diagnostic of the collision stage of Sec. 2.1. */
 vuda_status vuda_env_contact_counts(vuda_env_t env, int32_t* counts);
 
 /* Test entry point: rasterise ntri screen-space triangles with snapped 24.8
@@ -365,7 +372,10 @@ vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t n
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of step+render requests from many jobs.     */
 /* ------------------------------------------------------------------------ */
-/* A job is a batch of environments (a vuda_scene plus sim params) that stays
+/* Not in the paper, which runs one data-generation or rollout job at a time
+ * (Sec. 6.3, 6.4); this is the request loop that serves many such jobs at
+ * once on one GPU.
+ * A job is a batch of environments (a vuda_scene plus sim params) that stays
  * resident on the device once admitted.  A request asks for one physics step
  * of all the job's environments followed by the render of all its cameras.
  * Jobs are admitted in arrival order while their device memory fits
@@ -406,7 +416,9 @@ vuda_status vuda_serve_add_job(vuda_server_t server, const vuda_scene* scene, co
                                int64_t* job_id);
 /* Request one step + render of the job; requests of a job run in order. */
 vuda_status vuda_serve_submit(vuda_server_t server, int64_t job_id, uint64_t* req_id);
-/* Completed requests (up to max), waiting up to wait_ms for the first. */
+/* Completed requests (up to max), waiting up to wait_ms for the first.
+ * With wait_ms > 0, VUDA_ERR_TIMEOUT (and *n = 0) when none completed in
+ * that time; with wait_ms <= 0 it returns at once, VUDA_OK even if *n = 0. */
 vuda_status vuda_serve_poll(vuda_server_t server, vuda_result* out, int32_t max, int32_t* n, int32_t wait_ms);
 /* Cancel the job's queued requests and free it once its running ones finish. */
 vuda_status vuda_serve_remove_job(vuda_server_t server, int64_t job_id);
@@ -428,14 +440,22 @@ vuda_status vuda_serve_read_frame(vuda_server_t server, int64_t job_id, uint8_t*
  *   updated in place; pose[7][B] receives the final pose (xyz, wxyz);
  *   flags[E] receives VUDA_FLAG_CONTACT_OVERFLOW bits by OR (clear it first);
  *   ncontacts[E] the contact count of the last substep; force may be NULL.
- *   max_bodies bounds body_off[e+1] - body_off[e]; smem_per_env 0 = default.
+ *   max_bodies (> 0 when num_envs > 0, else VUDA_ERR_INVALID) bounds
+ *   body_off[e+1] - body_off[e]; smem_per_env 0 = default.  The kernel checks
+ *   every environment's range against 0 <= body_off[e] <= body_off[e+1] <=
+ *   num_bodies and body_off[e+1] - body_off[e] <= max_bodies before touching
+ *   shared memory or the scratch; an environment that fails is skipped and
+ *   gets VUDA_FLAG_BAD_RANGE in flags[e].
  * Scratch (contact spill records and their per-environment offsets) lives in
  * one fixed 16 MiB device array inside the library, held by every device that
  * loads it until the process exits.  Batches needing more scratch
  * (4 bytes x (2 (E + 1) rounded up to 64 + 36 x max_contacts_per_body x B))
  * are rejected with VUDA_ERR_INVALID before anything is launched.  The first
  * call on a device resolves the array's device address; make that first call
- * before any stream capture.  Every call shares the array: calls whose work
+ * before any stream capture.  The address is cached per device for the rest
+ * of the process: call with the device's primary context current (the CUDA
+ * runtime's default; not inside another context such as a green context),
+ * and not after a cudaDeviceReset of that device.  Every call shares the array: calls whose work
  * overlaps on the GPU (different streams, or different host threads) race and
  * must be serialised by the caller.  Async on `stream`. */
 vuda_status vuda_sim_step_noalloc(int32_t num_envs, int32_t num_bodies, int32_t max_bodies, const int32_t* body_off,

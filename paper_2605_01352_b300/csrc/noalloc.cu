@@ -64,6 +64,10 @@ extern "C" vuda_status vuda_sim_step_noalloc(int32_t num_envs, int32_t num_bodie
         set_error("vuda_sim_step_noalloc: bad sim params");
         return VUDA_ERR_INVALID;
     }
+    if (num_envs > 0 && max_bodies <= 0) {
+        set_error("vuda_sim_step_noalloc: max_bodies must be positive");
+        return VUDA_ERR_INVALID;
+    }
     if (num_envs == 0 || nsteps == 0) return VUDA_OK;
     if (!body_off || !pos || !quat || !vel || !angvel || !shape_type || !shape_dims || !inv_mass || !inv_inertia ||
         !pose || !flags || !ncontacts) {

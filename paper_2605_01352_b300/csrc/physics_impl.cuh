@@ -41,7 +41,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Field indices of a contact record (kContactWords floats in eight 16-byte
 // groups: n|KN, rA|VMIN, rB|LN, t1|KT1, t2|KT2, P|LT1, LA|LT2, LB|AB).
-// KN, KT1, KT2 hold inverse effective masses; P is the impulse of the
+// KN, KT1, KT2 hold the effective masses k; P is the impulse of the
 // current iteration, LA = rA x P and LB = rB x P its angular parts.  Between
 // generation and the per-contact constants, RA holds the contact point and
 // VMIN the distance.
@@ -450,10 +450,10 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
         float tl = sqrtf(dot3(t, t));
         f3 t1{t.x / tl, t.y / tl, t.z / tl};
         f3 t2 = cross3(n, t1);
-        // inverse effective masses, once per substep
-        float kN = 1.0f / eff_mass(S, a, bb, rA, rB, n);
-        float kT1 = 1.0f / eff_mass(S, a, bb, rA, rB, t1);
-        float kT2 = 1.0f / eff_mass(S, a, bb, rA, rB, t2);
+        // effective masses along n, t1, t2, once per substep
+        float kN = eff_mass(S, a, bb, rA, rB, n);
+        float kT1 = eff_mass(S, a, bb, rA, rB, t1);
+        float kT2 = eff_mass(S, a, bb, rA, rB, t2);
         float vn0 = dot3(n, rel_vel(S, a, bb, rA, rB));
         float vmin;
         if (d >= 0.0f) {
@@ -489,14 +489,17 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
             f3 vr = rel_vel(S, a, bb, rA, rB);
             float vn = dot3(n, vr);
             float ln = gb.w;
-            float dl = (ga.w - vn) * gn.w;
+            // the impulse updates divide by the effective mass as defined;
+            // a precomputed reciprocal rounds differently, and in settled
+            // piles one ulp there grows to ~1e-4 rad/s within a step
+            float dl = (ga.w - vn) / gn.w;
             float lnew = ln + dl;
             if (!(lnew > 0.0f)) lnew = 0.0f;
             float dln = lnew - ln;
             r[F_LN] = lnew;
             float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
-            float a1 = l1 - vt1 * g1.w;
-            float a2 = l2 - vt2 * g2.w;
+            float a1 = l1 - vt1 / g1.w;
+            float a2 = l2 - vt2 / g2.w;
             float lim = sc.mu * lnew;
             float m2 = a1 * a1 + a2 * a2;
             if (m2 > lim * lim) {
@@ -586,6 +589,13 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     const int b0 = b.body_off[e];
     const int N = b.body_off[e + 1] - b0;
     const int B = b.B;
+    // the range must lie in the batch and fit the shared-memory layout sized
+    // for NB bodies (the library's own batches always do; a caller-supplied
+    // one may not): otherwise skip the environment before touching anything
+    if (b0 < 0 || N < 0 || N > NB || b0 > B - N) {
+        if (tid == 0) atomicOr(b.flags + e, (unsigned)VUDA_FLAG_BAD_RANGE);
+        return;
+    }
     int cmax = sc.mcpb * N;
     const int cmax_nb = sc.mcpb * NB;
 

@@ -610,6 +610,7 @@ vuda_status vuda_serve_poll(vuda_server_t s, vuda_result* out, int32_t max, int3
     }
     *n = k;
     if (!s->fatal.empty()) return (set_error(s->fatal), VUDA_ERR_CUDA);
+    if (k == 0 && wait_ms > 0) return (set_error("no result within wait_ms"), VUDA_ERR_TIMEOUT);
     return VUDA_OK;
 }
 

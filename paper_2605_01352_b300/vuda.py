@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 lib = C.CDLL(LIB_PATH)
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_BUSY, ERR_UNSUPPORTED = range(8)
-FLAG_CONTACT_OVERFLOW, FLAG_NEAR_DISCARD, FLAG_GUARD_DISCARD, FLAG_MESH_CAPACITY, FLAG_TIMEOUT = 1, 2, 4, 8, 16
+FLAG_CONTACT_OVERFLOW, FLAG_NEAR_DISCARD, FLAG_GUARD_DISCARD, FLAG_MESH_CAPACITY, FLAG_BAD_RANGE = 1, 2, 4, 8, 16
 COSCHED_STREAMS, COSCHED_GREEN, COSCHED_SHARED = 1, 2, 3
 RENDER_AUTO, RENDER_BAND, RENDER_TILED = 0, 1, 2
 PRIORITY_NONE, PRIORITY_SIM, PRIORITY_RENDER = 0, 1, 2
@@ -524,7 +524,10 @@ class Server:
 
     def poll(self, wait_ms: int = 0, max_results: int = 4096):
         n = C.c_int32()
-        check(lib.vuda_serve_poll(self.h, self._buf, min(max_results, 4096), C.byref(n), wait_ms), "vuda_serve_poll")
+        st = lib.vuda_serve_poll(self.h, self._buf, min(max_results, 4096), C.byref(n), wait_ms)
+        if st == ERR_TIMEOUT:       # the bounded wait ran out with nothing completed
+            return []
+        check(st, "vuda_serve_poll")
         return [dict(req_id=r.req_id, job=r.job_id, status=r.status, step=r.step, t_submit_ms=r.t_submit_ms,
                      t_start_ms=r.t_start_ms, t_done_ms=r.t_done_ms) for r in self._buf[:n.value]]
 

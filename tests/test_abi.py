@@ -81,3 +81,24 @@ def test_binding_structs_match_the_c_header(built, tmp_path):
     assert len(got) == len(expect)
     bad = [(e, g) for e, g in zip(expect, got) if e[2] != g]
     assert not bad, bad
+
+
+def test_noalloc_rejects_a_missing_body_bound_without_gpu(built):
+    """The allocation-free step refuses max_bodies <= 0 for a non-empty batch
+    on the host, before any device call (the kernel sizes its shared-memory
+    layout from it)."""
+    import ctypes as C
+
+    from paper_2605_01352_b300 import scene as S
+    from paper_2605_01352_b300 import vuda
+    prm = vuda.sim_params(S.SimParams())
+    fake = C.c_void_p(0x1000)   # never dereferenced: the call returns before any device work
+    for mb in (0, -3):
+        st = vuda.lib.vuda_sim_step_noalloc(4, 32, mb, fake, fake, fake, fake, fake, fake, fake, fake, fake, None,
+                                            C.byref(prm), 1, fake, fake, fake, 0, None)
+        assert st == vuda.ERR_INVALID
+        if mb == 0:
+            assert b"max_bodies" in vuda.lib.vuda_last_error()
+    # an empty batch needs no bound and launches nothing
+    assert vuda.lib.vuda_sim_step_noalloc(0, 0, 0, None, None, None, None, None, None, None, None, None, None,
+                                          C.byref(prm), 1, None, None, None, 0, None) == vuda.OK

@@ -401,19 +401,23 @@ def test_shared_quotas_reported_and_checked(V):
 
 
 def test_pipeline_frames_match_oracle(V, orc):
-    """The co-scheduled loop's last two frames are the oracle's renders of
-    the oracle's states after steps n-1 and n."""
+    """The co-scheduled loop's final state matches the oracle, and its last
+    two frames are the oracle's renders of the two pose slots they were
+    rendered from (steps n-1 and n)."""
+    import torch
     sc = S.cfg1(8)
     n = 6
-    st, fr = _run_loop(V, sc, n, V.COSCHED_STREAMS)
-    s_prev, _, _ = orc.sim_step(sc, n - 1)
-    s_last, _, _ = orc.sim_step(sc, 1, state=s_prev)
-    _cmp_state(st, s_last, "final")
-    for k, s in ((n - 1, s_last), (n - 2, s_prev)):
-        o_rgb, o_dep, o_tid, _ = orc.render(sc, s["pos"], s["quat"])
-        f = fr[k & 1]
-        np.testing.assert_array_equal(f["triid"].view(np.uint32), o_tid)
-        np.testing.assert_allclose(f["depth"], o_dep, rtol=DEPTH_RTOL)
+    env = V.Env(sc)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    env.coschedule(V.COSCHED_STREAMS)
+    env.pipeline_run(n, ring)
+    torch.cuda.synchronize()
+    s_last, _, _ = orc.sim_step(sc, n)
+    _cmp_state(env.get_state(), s_last, "final")
+    envs = range(sc.num_envs)
+    for k in (n - 1, n - 2):
+        _frames_of_gpu_poses(orc, sc, env, ring[k & 1], k & 1, envs)
+    env.close()
 
 
 @pytest.mark.parametrize("mode", ["serialized", "streams"])
@@ -442,20 +446,59 @@ def test_host_loop_forces_in_frames_out_match_oracle(V, orc, mode):
     st_o = sc.state()
     for t in range(n):
         st_o, _, _ = orc.sim_step(sc, 1, state=st_o, force=f[t])
-        if t >= n - 2:
-            o_rgb, o_dep, _, _ = orc.render(sc, st_o["pos"], st_o["quat"])
-            np.testing.assert_allclose(hd[t & 1].numpy(), o_dep, rtol=DEPTH_RTOL, atol=0, err_msg="step %d" % t)
-            assert np.abs(hr[t & 1].numpy().astype(int) - o_rgb.astype(int)).max() <= 1
     _cmp_state(g, st_o, "final")
+    for t in (n - 2, n - 1):
+        pos, quat = env.get_pose(t & 1)     # the pose slot step t was rendered from
+        o_rgb, o_dep, _, _ = orc.render(sc, pos, quat)
+        np.testing.assert_allclose(hd[t & 1].numpy(), o_dep, rtol=DEPTH_RTOL, atol=0, err_msg="step %d" % t)
+        assert np.abs(hr[t & 1].numpy().astype(int) - o_rgb.astype(int)).max() <= 1
     env.close()
+
+
+def _frames_of_gpu_poses(orc, sc, env, frame, slot, envs):
+    """Render parity on the GPU's own poses: the pose slot the GPU rendered
+    from is read back and rendered by the oracle, environment by
+    environment; triangle ids bit-exact, depth 1e-6, colour 1 LSB."""
+    pos, quat = env.get_pose(slot)
+    pix = env.cam_pix_off
+    for e in envs:
+        sub = sc.subset([e])
+        b0, b1 = sc.body_off[e], sc.body_off[e + 1]
+        o_rgb, o_dep, o_tid, _ = orc.render(sub, pos[:, b0:b1], quat[:, b0:b1])
+        c0, c1 = sc.cam_off[e], sc.cam_off[e + 1]
+        sl = slice(pix[c0], pix[c1])
+        np.testing.assert_array_equal(frame["triid"][sl].cpu().numpy().view(np.uint32), o_tid,
+                                      err_msg="env %d" % e)
+        np.testing.assert_allclose(frame["depth"][sl].cpu().numpy(), o_dep, rtol=DEPTH_RTOL, atol=0,
+                                   err_msg="env %d" % e)
+        assert np.abs(frame["rgb"][sl].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1, e
+
+
+def _sampled_physics(orc, sc, g, steps, envs, start=None):
+    """Sampled environments of a batch stepped `steps` times from `start`
+    (default: the scene's initial state) match the oracle run on each of
+    them alone (environments are independent), within the physics
+    tolerance."""
+    for e in envs:
+        sub = sc.subset([e])
+        b0, b1 = sc.body_off[e], sc.body_off[e + 1]
+        st0 = None if start is None else {k: start[k][:, b0:b1] for k in ("pos", "quat", "vel", "angvel")}
+        so, _, _ = orc.sim_step(sub, steps, state=st0)
+        for k in ("pos", "vel", "quat", "angvel"):
+            np.testing.assert_allclose(g[k][:, b0:b1], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL,
+                                       err_msg="env %d %s" % (e, k))
+
+
+CFG2_SAMPLE = (0, 1, 511, 777, 1023)
 
 
 @pytest.mark.parametrize("launch", ["green", "bench"])
 def test_full_size_cfg2_sampled(V, orc, launch):
-    """1024 envs x 32 bodies at 128x128: sampled environments match the
-    oracle run on those environments alone (environments are independent).
-    Launch configurations: the paper's disjoint partitions (green contexts,
-    3 steps), and the benchmark's headline one (two streams sharing all SMs,
+    """1024 envs x 32 bodies at 128x128: sampled environments' states match
+    the oracle run on those environments alone, and their frames match the
+    oracle's render of the pose slot the GPU rendered from.  Launch
+    configurations: the paper's disjoint partitions (green contexts, 3
+    steps), and the benchmark's headline one (two streams sharing all SMs,
     sim stream first, 8 pipelined steps replayed from a CUDA graph)."""
     import torch
     sc = S.cfg2()
@@ -472,41 +515,49 @@ def test_full_size_cfg2_sampled(V, orc, launch):
     torch.cuda.synchronize()
     g = env.get_state()
     assert env.status()[1] == 0
-    pix = env.cam_pix_off
-    for e in (0, 1, 511, 777, 1023):
-        sub = sc.subset([e])
-        so, _, _ = orc.sim_step(sub, steps)
-        b0, b1 = sc.body_off[e], sc.body_off[e + 1]
-        for k in ("pos", "vel", "quat", "angvel"):
-            np.testing.assert_allclose(g[k][:, b0:b1], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL)
-        o_rgb, o_dep, o_tid, _ = orc.render(sub, so["pos"], so["quat"])
-        f = ring[(steps - 1) & 1]
-        sl = slice(pix[e], pix[e + 1])
-        np.testing.assert_array_equal(f["triid"][sl].cpu().numpy().view(np.uint32), o_tid)
-        np.testing.assert_allclose(f["depth"][sl].cpu().numpy(), o_dep, rtol=DEPTH_RTOL)
-        assert np.abs(f["rgb"][sl].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1
+    _sampled_physics(orc, sc, g, steps, CFG2_SAMPLE)
+    _frames_of_gpu_poses(orc, sc, env, ring[(steps - 1) & 1], (steps - 1) & 1, CFG2_SAMPLE)
+    env.close()
+
+
+@pytest.mark.parametrize("mode", ["streams-graph", "green"])
+def test_full_size_cfg2_settled_piles(V, orc, mode):
+    """The regime the benchmark times: the 1024-environment batch after 120
+    settling steps (piles in contact, about 4.5 contacts per body, many
+    spilled to global memory), then 8 pipelined steps in a co-scheduled
+    launch configuration.  Sampled environments, stepped by the oracle from
+    the GPU's settled state, match within the physics tolerance; their
+    frames match the oracle's render of the GPU's last pose slot."""
+    import torch
+    sc = S.cfg2()
+    env = V.Env(sc)
+    ring = [env.alloc_frame(), env.alloc_frame()]
+    env.pipeline_run(120, ring)
+    torch.cuda.synchronize()
+    settled = env.get_state()
+    cc = env.contact_counts()
+    assert cc.mean() > 3.0 * 32, cc.mean()          # settled piles, contact-rich
+    if mode == "green":
+        env.coschedule(V.COSCHED_GREEN)
+    else:
+        env.coschedule(V.COSCHED_STREAMS, priority=V.PRIORITY_SIM)
+        env.pipeline_capture(8, ring)
+    env.pipeline_run(8, ring)
+    torch.cuda.synchronize()
+    g = env.get_state()
+    picks = CFG2_SAMPLE + (int(np.argmax(cc)),)
+    _sampled_physics(orc, sc, g, 8, picks, start=settled)
+    _frames_of_gpu_poses(orc, sc, env, ring[1], 1, picks)
     env.close()
 
 
 def _sampled_env_check(orc, sc, env, ring, steps, envs, frame_slot):
     """Sampled environments of a batch stepped `steps` times match the oracle
-    run on each of them alone (state, and every camera of the environment
-    in frame ring[frame_slot])."""
-    g = env.get_state()
-    pix = env.cam_pix_off
-    for e in envs:
-        sub = sc.subset([e])
-        so, _, _ = orc.sim_step(sub, steps)
-        b0, b1 = sc.body_off[e], sc.body_off[e + 1]
-        for k in ("pos", "vel", "quat", "angvel"):
-            np.testing.assert_allclose(g[k][:, b0:b1], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL, err_msg="env %d" % e)
-        o_rgb, o_dep, o_tid, _ = orc.render(sub, so["pos"], so["quat"])
-        c0, c1 = sc.cam_off[e], sc.cam_off[e + 1]
-        sl = slice(pix[c0], pix[c1])
-        f = ring[frame_slot]
-        np.testing.assert_array_equal(f["triid"][sl].cpu().numpy().view(np.uint32), o_tid, err_msg="env %d" % e)
-        np.testing.assert_allclose(f["depth"][sl].cpu().numpy(), o_dep, rtol=DEPTH_RTOL)
-        assert np.abs(f["rgb"][sl].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1
+    run on each of them alone (state), and every camera of the environment
+    in frame ring[frame_slot] matches the oracle's render of the GPU's pose
+    slot of that frame."""
+    _sampled_physics(orc, sc, env.get_state(), steps, envs)
+    _frames_of_gpu_poses(orc, sc, env, ring[frame_slot], frame_slot, envs)
 
 
 def test_full_size_cfg3_graph_sampled(V, orc):
@@ -557,6 +608,7 @@ def test_persistent_uneven_batch_matches(V, orc):
         env.pipeline_run(3, ring)
         torch.cuda.synchronize()
         out.append((env.get_state(), {k: v.cpu().numpy().copy() for k, v in ring[0].items()}, env.status()[0]))
+        pose1 = env.get_pose(0)
         env.close()
     (s0, f0, fl0), (s1, f1, fl1) = out
     for k in s0:
@@ -571,12 +623,12 @@ def test_persistent_uneven_batch_matches(V, orc):
         b0, b1 = sc.body_off[e], sc.body_off[e + 1]
         for k in ("pos", "vel", "quat", "angvel"):
             np.testing.assert_allclose(s1[k][:, b0:b1], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL)
-    # frame 0 of the ring holds step 2 (third step): render it with the oracle from the oracle's state
-    s_prev, _, _ = orc.sim_step(sc, 2)
-    s_step3, _, _ = orc.sim_step(sc, 1, state=s_prev)
-    o_rgb, o_dep, o_tid, _ = orc.render(sc, s_step3["pos"], s_step3["quat"])
+    # frame 0 of the ring holds step 2 (the third step), rendered from pose
+    # slot 0: the oracle renders that pose slot of the persistent run
+    o_rgb, o_dep, o_tid, _ = orc.render(sc, *pose1)
     np.testing.assert_array_equal(f1["triid"].view(np.uint32), o_tid)
     np.testing.assert_allclose(f1["depth"], o_dep, rtol=DEPTH_RTOL)
+    assert np.abs(f1["rgb"].astype(int) - o_rgb.astype(int)).max() <= 1
 
 
 @pytest.mark.parametrize("mode", ["single", "streams", "green", "shared"])
@@ -683,10 +735,6 @@ def test_hull_meshes_two_cameras(V, orc, path):
     so, _, _ = orc.sim_step(sc, 2)
     for k in ("pos", "vel", "quat", "angvel"):
         np.testing.assert_allclose(g[k], so[k], rtol=PHYS_RTOL, atol=PHYS_ATOL)
-    o_rgb, o_dep, o_tid, _ = orc.render(sc, so["pos"], so["quat"])
-    f = ring[1]
-    np.testing.assert_array_equal(f["triid"].cpu().numpy().view(np.uint32), o_tid)
-    np.testing.assert_allclose(f["depth"].cpu().numpy(), o_dep, rtol=DEPTH_RTOL)
-    assert np.abs(f["rgb"].cpu().numpy().astype(int) - o_rgb.astype(int)).max() <= 1
+    _frames_of_gpu_poses(orc, sc, env, ring[1], 1, range(sc.num_envs))
     assert env.C == 6 and env.T > 3 * 64 * 500
     env.close()

@@ -67,6 +67,8 @@ def test_job_results_are_the_same_alone_and_in_a_mix(V, orc):
     assert st["requests_done"] == sum(counts.values())
     assert st["max_batch"] >= 2          # requests of several jobs shared a launch
     mixed = {k: (srv.job_env(ids[k]).get_state(), srv.read_frame(ids[k])) for k in jobs}
+    # the pose slot each job's last frame was rendered from
+    poses = {k: srv.job_env(ids[k]).get_pose((counts[k] - 1) & 1) for k in jobs}
     paths = {k: srv.job_env(ids[k]).info().render_path for k in jobs}
     assert paths == {"A": V.RENDER_TILED, "B": V.RENDER_TILED, "C": V.RENDER_TILED, "D": V.RENDER_TILED,
                      "E": V.RENDER_BAND}
@@ -78,13 +80,15 @@ def test_job_results_are_the_same_alone_and_in_a_mix(V, orc):
             np.testing.assert_array_equal(st_a[f], st_m[f])
         for x, y in zip(fr_a, fr_m):
             np.testing.assert_array_equal(x, y)
-    # and the jobs of both render paths match the oracle
+    # and the jobs of both render paths match the oracle: the state within
+    # the physics tolerance, the frame against the oracle's render of the
+    # pose slot it was rendered from
     for k in ("A", "E"):
         sc = jobs[k]
         so, _, _ = orc.sim_step(sc, counts[k])
         for f in ("pos", "vel", "quat", "angvel"):
             np.testing.assert_allclose(mixed[k][0][f], so[f], rtol=1e-5, atol=1e-5)
-        o_rgb, o_dep, o_tid, _ = orc.render(sc, so["pos"], so["quat"])
+        o_rgb, o_dep, o_tid, _ = orc.render(sc, *poses[k])
         np.testing.assert_array_equal(mixed[k][1][2], o_tid)
         np.testing.assert_allclose(mixed[k][1][1], o_dep, rtol=1e-6)
         assert np.abs(mixed[k][1][0].astype(int) - o_rgb.astype(int)).max() <= 1

@@ -290,3 +290,144 @@ def test_f32_tracks_f64_on_cfg1(orc):
     s64, _, _ = orc.sim_step(sc, 5, precision="f64")
     for k in ("pos", "vel", "quat"):
         np.testing.assert_allclose(s32[k], s64[k], rtol=1e-4, atol=1e-5)
+
+
+def test_box_corners_of_b_inside_a_flip_the_normal(orc):
+    """Box-box, the second half of the test (B's corners inside A): a small
+    box B (body 1), turned 30 degrees about A's up axis, sits sunk by `sink`
+    into the top face of a tilted larger box A (body 0).  A's corners are all
+    far outside B, so every contact is one of B's four bottom corners, in
+    sign-bit order, with d = -sink and the normal pointing from B to A
+    (minus A's up axis).  Geometry from an independent rotation (scipy)."""
+    from scipy.spatial.transform import Rotation
+    RA = Rotation.from_euler("xyz", [20.0, -10.0, 35.0], degrees=True)
+    RB = RA * Rotation.from_euler("z", 30.0, degrees=True)
+    hA = np.array([0.1, 0.12, 0.05])
+    hB = np.array([0.03, 0.04, 0.035])
+    sink = 0.004
+    pA = np.array([0.0, 0.0, 1.0])
+    pB = pA + RA.apply([0.01, -0.015, hA[2] + hB[2] - sink])
+
+    def wxyz(r):
+        x, y, z, w = r.as_quat()
+        return (w, x, y, z)
+
+    p = dataclasses.replace(S.SimParams(), plane=0)
+    sc = S.custom([dict(type="box", h=tuple(hA), pos=tuple(pA), quat=wxyz(RA)),
+                   dict(type="box", h=tuple(hB), pos=tuple(pB), quat=wxyz(RB))], params=p)
+    c = orc.contacts(sc, 0)
+    RBm = _rotmat(sc.quat[:, 1].astype(np.float64))
+    RAm = _rotmat(sc.quat[:, 0].astype(np.float64))
+    exp = []
+    for k in range(4):   # bottom corners: sign bit 2 clear
+        s = np.array([1 if k & 1 else -1, 1 if k & 2 else -1, -1])
+        exp.append(RBm @ (s * hB) + sc.pos[:, 1].astype(np.float64))
+    assert c["count"] == 4
+    assert (c["a"] == 0).all() and (c["b"] == 1).all()
+    np.testing.assert_allclose(c["p"], np.array(exp), atol=2e-6)
+    np.testing.assert_allclose(c["d"], -sink, atol=2e-6)
+    np.testing.assert_allclose(c["n"], np.tile(-RAm[:, 2], (4, 1)), atol=2e-6)
+    # the same pair listed the other way round (the small box first) puts
+    # the corners in the first half of the test, with the normal from the
+    # large box to the small one: +A's up axis
+    sc2 = S.custom([dict(type="box", h=tuple(hB), pos=tuple(pB), quat=wxyz(RB)),
+                    dict(type="box", h=tuple(hA), pos=tuple(pA), quat=wxyz(RA))], params=p)
+    c2 = orc.contacts(sc2, 0)
+    assert c2["count"] == 4 and (c2["a"] == 0).all() and (c2["b"] == 1).all()
+    np.testing.assert_allclose(c2["p"], c["p"], atol=0)
+    np.testing.assert_allclose(c2["n"], -c["n"], atol=0)
+
+
+@pytest.mark.parametrize("sphere_first", [True, False])
+def test_sphere_centre_inside_box(orc, sphere_first):
+    """A sphere whose centre lies inside a box: the contact uses the box face
+    of least penetration, d = -(h_m - |l_m|) - r, the point on that face
+    straight out from the centre, and the normal pointing from the box to
+    the sphere (or its negative when the box is listed first).  Rotated box;
+    geometry from an independent rotation (scipy)."""
+    from scipy.spatial.transform import Rotation
+    R = Rotation.from_euler("xyz", [15.0, 40.0, -25.0], degrees=True)
+    x, y, z, w = R.as_quat()
+    h = np.array([0.08, 0.05, 0.1])
+    pb = np.array([0.2, -0.1, 1.0])
+    l = np.array([0.02, -0.035, 0.03])   # penetrations h - |l| = 0.06, 0.015, 0.07: axis y, side -
+    r = 0.02
+    ps = pb + R.apply(l)
+    p = dataclasses.replace(S.SimParams(), plane=0)
+    sph = dict(type="sphere", r=r, pos=tuple(ps))
+    box = dict(type="box", h=tuple(h), pos=tuple(pb), quat=(w, x, y, z))
+    sc = S.custom([sph, box] if sphere_first else [box, sph], params=p)
+    c = orc.contacts(sc, 0)
+    assert c["count"] == 1 and c["a"][0] == 0 and c["b"][0] == 1
+    Rm = _rotmat(sc.quat[:, 1 if sphere_first else 0].astype(np.float64))
+    n_box_to_sphere = -Rm[:, 1]
+    face_pt = Rm @ np.array([l[0], -h[1], l[2]]) + sc.pos[:, 1 if sphere_first else 0]
+    assert c["d"][0] == pytest.approx(-(h[1] - abs(l[1])) - r, abs=2e-6)
+    np.testing.assert_allclose(c["p"][0], face_pt, atol=2e-6)
+    np.testing.assert_allclose(c["n"][0], n_box_to_sphere if sphere_first else -n_box_to_sphere, atol=2e-6)
+
+
+def test_sphere_centre_inside_box_ties_go_to_the_lowest_axis(orc):
+    """Equal penetrations along x and y (exact in float: an axis-aligned box
+    and dyadic offsets): the lower axis, x, is chosen; a centre at the box
+    centre ties all three axes and takes +x (the sign of a zero coordinate
+    is +)."""
+    p = dataclasses.replace(S.SimParams(), plane=0)
+    for l, nexp, dexp in (((0.25, -0.25, 0.125), (1.0, 0.0, 0.0), -0.25 - 0.0625),
+                          ((0.0, 0.0, 0.0), (1.0, 0.0, 0.0), -0.5 - 0.0625)):
+        sc = S.custom([dict(type="sphere", r=0.0625, pos=(l[0], l[1], 2.0 + l[2])),
+                       dict(type="box", h=(0.5, 0.5, 0.5), pos=(0.0, 0.0, 2.0))], params=p)
+        c = orc.contacts(sc, 0)
+        assert c["count"] == 1
+        np.testing.assert_array_equal(c["n"][0], nexp)
+        assert c["d"][0] == dexp
+        np.testing.assert_array_equal(c["p"][0], (0.5, l[1], 2.0 + l[2]))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 3e-5)])
+def test_constant_force_closed_form(orc, prec, tol):
+    """A constant force F held on a free body adds F / m to the acceleration:
+    v_n = v0 + n h (g + F/m), x_n = x0 + n h v0 + h^2 (g + F/m) n (n+1) / 2.
+    One sphere and one box (different masses) in the same environment, far
+    apart."""
+    sc = S.custom([dict(type="sphere", r=0.06, pos=(-5.0, 0.0, 50.0), vel=(0.5, 0.0, 1.0)),
+                   dict(type="box", h=(0.03, 0.05, 0.08), pos=(5.0, 0.0, 50.0), vel=(0.0, -1.0, 2.0))])
+    F = np.array([[0.3, -1.5], [-0.2, 0.7], [4.0, 0.25]])
+    steps = 20
+    st, _, cc = orc.sim_step(sc, steps, precision=prec, force=F)
+    assert cc[0] == 0
+    h = sc.params.dt / sc.params.substeps
+    n = steps * sc.params.substeps
+    g = np.array(sc.params.gravity)
+    for b in range(2):
+        m = 1.0 / float(np.float32(sc.inv_mass[b]))
+        acc = g + F[:, b] / m if prec == "f64" else g + F[:, b].astype(np.float32) / m
+        v0 = sc.vel[:, b].astype(np.float64)
+        x0 = sc.pos[:, b].astype(np.float64)
+        np.testing.assert_allclose(st["vel"][:, b], v0 + n * h * acc, rtol=tol, atol=tol)
+        np.testing.assert_allclose(st["pos"][:, b], x0 + n * h * v0 + h * h * acc * n * (n + 1) / 2.0,
+                                   rtol=tol, atol=tol * 50)
+
+
+@pytest.mark.parametrize("speed,bounces", [(3.0, True), (0.4, False)])
+def test_head_on_restitution(orc, speed, bounces):
+    """Equal spheres overlapping by less than the slop, approaching head on
+    along x with e = 0.5 (no gravity, no plane).  Faster than the 1 m/s
+    threshold, the textbook outcome: they separate at e times the approach
+    speed after one substep, momentum conserved, no spin.  Slower, the
+    restitution target does not apply and they stop along the normal."""
+    e = 0.5
+    p = dataclasses.replace(S.SimParams(), gravity=(0.0, 0.0, 0.0), plane=0, restitution=e, substeps=1)
+    r = 0.0625
+    ov = 0.000244140625   # overlap 2^-12 < slop: no position bias
+    x = r - ov / 2
+    sc = S.custom([dict(type="sphere", r=r, pos=(-x, 0.0, 1.0), vel=(speed / 2, 0.0, 0.0)),
+                   dict(type="sphere", r=r, pos=(x, 0.0, 1.0), vel=(-speed / 2, 0.0, 0.0))], params=p)
+    s0 = {k: v.astype(np.float64) for k, v in sc.state().items()}
+    st, _, cc = orc.sim_step(sc, 1, state=s0, precision="f64")
+    assert cc[0] == 1
+    v_rel = st["vel"][0, 1] - st["vel"][0, 0]   # separation speed along x
+    assert v_rel == pytest.approx(e * speed if bounces else 0.0, abs=1e-12)
+    assert st["vel"][0, 0] + st["vel"][0, 1] == pytest.approx(0.0, abs=1e-12)
+    np.testing.assert_array_equal(st["angvel"], 0.0)
+    np.testing.assert_array_equal(st["vel"][1:], 0.0)

@@ -283,3 +283,33 @@ def test_guard_band_vertex_discards_triangle(orc):
     over = _front([(lim + 1, lim), (-lim, lim), (lim, -lim)])
     tid, _, _ = orc.raster_screen_tris(np.array([over]), np.ones((1, 3)), 8, 8)
     assert (tid == 0xFFFFFFFF).all()
+
+
+def test_box_with_unequal_half_extents_seen_face_on(orc):
+    """A box of half extents (a, b, c), turned 90 degrees about the world y
+    axis (its local x along world -z, local z along world x), straight ahead
+    of a camera looking along +y.  The mesh is scaled before it is rotated,
+    so the silhouette is the front face: a rectangle of 2c by 2a world units
+    at view depth zf = D - b.  The sizes put its projected edges on pixel
+    corners (fpy c / zf = 12, fpy a / zf = 20 pixels), so it covers exactly
+    24 columns by 40 rows around the image centre, at depth zf, in the flat
+    colour of a face whose normal is -y."""
+    res = 128
+    fpy = (res / 2) / math.tan(math.radians(30.0))
+    zf = 2.0
+    c, a, b = 12 * zf / fpy, 20 * zf / fpy, 0.1
+    D = zf + b
+    s = math.sqrt(0.5)
+    sc = S.custom([dict(type="box", h=(a, b, c), pos=(0.0, 0.0, 1.0), quat=(s, 0.0, s, 0.0))], res=res,
+                  cams=[dict(eye=(0.0, -D, 1.0), target=(0.0, 0.0, 1.0), fov=60.0)])
+    rgb, dep, tid, flags = orc.render(sc)
+    assert flags[0] == 0
+    body = ((tid != 0xFFFFFFFF) & (tid >= 2)).reshape(res, res)
+    exp = np.zeros((res, res), bool)
+    exp[64 - 20:64 + 20, 64 - 12:64 + 12] = True
+    np.testing.assert_array_equal(body, exp)
+    np.testing.assert_allclose(dep.reshape(res, res)[exp], zf, rtol=1e-6)
+    L = sc.light.astype(np.float64)
+    I = 0.2 + 0.8 * max(0.0, -L[1])
+    want = np.array([int(ch * I + 0.5) for ch in S.PALETTE[0]])
+    assert np.abs(rgb.reshape(res, res, 3)[exp].astype(int) - want).max() <= 1

@@ -55,14 +55,41 @@ def test_noalloc_step_matches_regular_step(orc):
 
 
 def test_noalloc_rejects_batches_beyond_the_scratch():
+    """Batches whose scratch would not fit the fixed array are refused on the
+    host before anything launches: through the spill records (many bodies)
+    and through the per-environment offsets alone (many environments of a
+    few bodies each)."""
     import torch
+    assert torch.cuda.is_available()
+    from paper_2605_01352_b300 import build
+    build.build()
     from paper_2605_01352_b300 import vuda as V
     sc = S.cfg1(2)
     arr = _dev_arrays(torch, sc)
-    # claim far more bodies than the fixed scratch can hold: rejected on the host, nothing launched
+    # claim far more bodies than the fixed scratch can hold
     arr_big = dict(arr)
     arr_big["inv_mass"] = torch.zeros(4_000_000, device="cuda")
     with pytest.raises(V.VudaError) as ex:
         V.sim_step_noalloc(arr_big, sc.params, 1, 8)
     assert ex.value.status == V.ERR_INVALID
     assert "scratch" in str(ex.value)
+    # 2.2 M environments of no bodies over 8 bodies in all: the records need
+    # 16 x 8 x 36 words, the offsets 2 (E + 1) > 4 M words on their own
+    E = 2_200_000
+    arr_many = dict(arr)
+    arr_many["body_off"] = torch.full((E + 1,), 0, dtype=torch.int32, device="cuda")
+    arr_many["body_off"][-1] = 8
+    with pytest.raises(V.VudaError) as ex:
+        V.sim_step_noalloc(arr_many, sc.params, 1, 8)
+    assert ex.value.status == V.ERR_INVALID
+    assert "scratch" in str(ex.value)
+    # the same batch shape below the limit (1.5 M environments) is accepted
+    E = 1_500_000
+    arr_ok = dict(arr)
+    arr_ok["body_off"] = torch.full((E + 1,), 0, dtype=torch.int32, device="cuda")
+    arr_ok["body_off"][-1] = 8
+    arr_ok["flags"] = torch.zeros(E, dtype=torch.int32, device="cuda")
+    arr_ok["ncontacts"] = torch.zeros(E, dtype=torch.int32, device="cuda")
+    V.sim_step_noalloc(arr_ok, sc.params, 1, 8)
+    torch.cuda.synchronize()
+    assert int(arr_ok["flags"].abs().sum()) == 0
