@@ -49,7 +49,9 @@ typedef enum {
 /* Per-environment status bits (vuda_env_status).  They accumulate until
  * cleared and never stop the step: the work degrades deterministically. */
 #define VUDA_FLAG_CONTACT_OVERFLOW 0x1u /* contacts beyond max_contacts_per_body * N dropped */
-#define VUDA_FLAG_NEAR_DISCARD     0x2u /* a triangle with a vertex before the near plane was skipped */
+#define VUDA_FLAG_CLIP_CAPACITY    0x2u /* tiled path: a triangle found no record slot (only the extra fan
+                                            triangles of near-plane clipping can need more slots than the
+                                            camera has triangles) and was skipped */
 #define VUDA_FLAG_GUARD_DISCARD    0x4u /* a triangle beyond the 2^14 px guard band was skipped */
 #define VUDA_FLAG_MESH_CAPACITY    0x8u /* a mesh larger than the render vertex cache was skipped */
 #define VUDA_FLAG_BAD_RANGE        0x10u /* the environment's body range was invalid (outside the batch, or more

@@ -58,7 +58,6 @@ typedef struct {
 /* ------------------------------------------------------------------------ */
 /* Rasteriser                                                                */
 /* ------------------------------------------------------------------------ */
-#define FLAG_NEAR 2u
 #define FLAG_GUARD 4u
 #define SUBPIX 256.0f      /* 8 sub-pixel bits: fixed point 24.8 */
 #define GUARD 16384.0f     /* |sx|, |sy| limit in pixels */
@@ -66,11 +65,12 @@ typedef struct {
 #define NEAR_Z 0.01f
 
 typedef struct {
-    int ok;        /* 0: discarded (near plane or guard band) */
+    int ok;        /* 0: before the near plane or beyond the guard band */
     int X, Y;      /* snapped screen position, 24.8 fixed point */
     float iz;      /* 1 / view depth */
     float w[3];    /* world position */
-    unsigned flag;
+    float v[3];    /* view position (xc, yc, zc) */
+    unsigned flag; /* FLAG_GUARD, or 0 */
 } overt;
 
 /* Rasterise one triangle with snapped vertices (X[i], Y[i]) and inverse
@@ -186,21 +186,92 @@ static void transform_vertex(const float* v, const float* s, const float* p, con
     w[2] = t[2] + p[2];
 }
 
+/* Snapped screen position of a view-space point with zc >= near: sx = W/2 +
+ * fpy xc / zc, sy = H/2 - fpy yc / zc, rounded to 1/256 px (half to even).
+ * Returns 0, or FLAG_GUARD if the point lies beyond the guard band. */
+static unsigned snap_view(float xc, float yc, float zc, float fpy, int W, int H, int* X, int* Y, float* iz) {
+    float sx = (float)W * 0.5f + (fpy * xc) / zc;
+    float sy = (float)H * 0.5f - (fpy * yc) / zc;
+    if (!(fabsf(sx) < GUARD && fabsf(sy) < GUARD)) return FLAG_GUARD;
+    *X = (int)rintf(sx * SUBPIX);
+    *Y = (int)rintf(sy * SUBPIX);
+    *iz = 1.0f / zc;
+    return 0;
+}
+
 static void project_vertex(overt* o, const float* eye, const float* rt, const float* up, const float* fw,
                            float fpy, int W, int H) {
     float d[3] = { o->w[0] - eye[0], o->w[1] - eye[1], o->w[2] - eye[2] };
-    float xc = (rt[0] * d[0] + rt[1] * d[1]) + rt[2] * d[2];
-    float yc = (up[0] * d[0] + up[1] * d[1]) + up[2] * d[2];
-    float zc = (fw[0] * d[0] + fw[1] * d[1]) + fw[2] * d[2];
-    o->ok = 1;
+    o->v[0] = (rt[0] * d[0] + rt[1] * d[1]) + rt[2] * d[2];
+    o->v[1] = (up[0] * d[0] + up[1] * d[1]) + up[2] * d[2];
+    o->v[2] = (fw[0] * d[0] + fw[1] * d[1]) + fw[2] * d[2];
+    o->ok = 0;
     o->flag = 0;
-    if (!(zc >= NEAR_Z)) { o->ok = 0; o->flag = FLAG_NEAR; return; }
-    float sx = (float)W * 0.5f + (fpy * xc) / zc;
-    float sy = (float)H * 0.5f - (fpy * yc) / zc;
-    if (!(fabsf(sx) < GUARD && fabsf(sy) < GUARD)) { o->ok = 0; o->flag = FLAG_GUARD; return; }
-    o->X = (int)rintf(sx * SUBPIX);
-    o->Y = (int)rintf(sy * SUBPIX);
-    o->iz = 1.0f / zc;
+    if (!(o->v[2] >= NEAR_Z)) return;   /* before the near plane: its triangles are clipped */
+    o->flag = snap_view(o->v[0], o->v[1], o->v[2], fpy, W, H, &o->X, &o->Y, &o->iz);
+    o->ok = o->flag == 0;
+}
+
+/* 1 if all three vertices lie beyond the same side plane of the view
+ * frustum -- right of the image (fpy xc > W/2 zc, i.e. sx > W in front of
+ * the camera), left (fpy xc < -W/2 zc), above (fpy yc > H/2 zc) or below
+ * (fpy yc < -H/2 zc).  Each plane passes through the eye, so the triangle
+ * lies in that half-space and covers no pixel, wherever its vertices are
+ * (also behind the camera). */
+static int outside_frustum_side(const overt* const* tv, float fpy, int W, int H) {
+    const float hw = (float)W * 0.5f, hh = (float)H * 0.5f;
+    int r = 1, l = 1, u = 1, d = 1;
+    for (int i = 0; i < 3; i++) {
+        const float* v = tv[i]->v;
+        r &= fpy * v[0] > hw * v[2];
+        l &= fpy * v[0] < -(hw * v[2]);
+        u &= fpy * v[1] > hh * v[2];
+        d &= fpy * v[1] < -(hh * v[2]);
+    }
+    return r | l | u | d;
+}
+
+/* Sutherland-Hodgman clipping of triangle (a, b, c) against the near plane
+ * zc = NEAR_Z, keeping the part with zc >= NEAR_Z.  The clipped polygon (3
+ * or 4 vertices, in the triangle's order) is cut into a fan from its first
+ * vertex; each triangle of the fan is rasterised with the original
+ * triangle's id.  A new vertex on an edge from an inside vertex p to an
+ * outside vertex q is p + t (q - p) with t = (near - p_z) / (q_z - p_z),
+ * always taken from the inside end, so that the two triangles sharing the
+ * edge get the same point; it lies on the plane (zc = near exactly).
+ * Returns FLAG_GUARD (and draws nothing) if a vertex of the polygon lies
+ * beyond the guard band, else 0.  (With every vertex in front of the plane
+ * the polygon is the triangle itself.) */
+static unsigned clip_near_and_raster(const overt* const* tv, uint32_t id, float fpy, int W, int H, uint64_t* zb) {
+    int X[4], Y[4];
+    float iz[4];
+    int n = 0;
+    for (int i = 0; i < 3; i++) {
+        const overt* p = tv[i];
+        const overt* q = tv[(i + 1) % 3];
+        const int pin = p->v[2] >= NEAR_Z, qin = q->v[2] >= NEAR_Z;
+        if (pin) {
+            if (p->flag) return p->flag;
+            X[n] = p->X; Y[n] = p->Y; iz[n] = p->iz;
+            n++;
+        }
+        if (pin != qin) {
+            const overt* a = pin ? p : q;   /* inside end */
+            const overt* b = pin ? q : p;   /* outside end */
+            float t = (NEAR_Z - a->v[2]) / (b->v[2] - a->v[2]);
+            float xc = a->v[0] + t * (b->v[0] - a->v[0]);
+            float yc = a->v[1] + t * (b->v[1] - a->v[1]);
+            unsigned f = snap_view(xc, yc, NEAR_Z, fpy, W, H, X + n, Y + n, iz + n);
+            if (f) return f;
+            n++;
+        }
+    }
+    for (int k = 1; k + 1 < n; k++) {
+        int fx[3] = { X[0], X[k], X[k + 1] }, fy[3] = { Y[0], Y[k], Y[k + 1] };
+        float fz[3] = { iz[0], iz[k], iz[k + 1] };
+        raster_tri(fx, fy, fz, id, W, H, zb, NULL);
+    }
+    return 0;
 }
 
 /* flat colour of a triangle from its world-space face normal */
@@ -282,7 +353,14 @@ int oracle_render(int num_envs, const int32_t* body_off, int B, const float* pos
                     const overt *a = vs + tv[0], *bb = vs + tv[1], *cc = vs + tv[2];
                     color[id] = shade(a->w, bb->w, cc->w, alb, light);
                     if (!a->ok || !bb->ok || !cc->ok) {
-                        env_flags[e] |= a->flag | bb->flag | cc->flag;
+                        /* a vertex before the near plane or beyond the guard
+                         * band: nothing to draw if the triangle lies wholly
+                         * before the near plane or beyond one image edge;
+                         * else clip it (which flags a guard-band vertex) */
+                        const overt* tvs[3] = { a, bb, cc };
+                        const int nin = (a->v[2] >= NEAR_Z) + (bb->v[2] >= NEAR_Z) + (cc->v[2] >= NEAR_Z);
+                        if (nin == 0 || outside_frustum_side(tvs, fpy, W, H)) continue;
+                        env_flags[e] |= clip_near_and_raster(tvs, id, fpy, W, H, zb);
                         continue;
                     }
                     int X[3] = { a->X, bb->X, cc->X }, Y[3] = { a->Y, bb->Y, cc->Y };

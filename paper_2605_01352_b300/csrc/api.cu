@@ -192,6 +192,7 @@ TiledPlan plan_tiled(const vuda_env* env, int tile, int nlim) {
         ti.rec_base = pl.nrec;
         ti.ent_base = pl.nent;
         ti.toff_base = pl.ntoff;
+        ti.rec_cap = tiled_record_cap(tc);
         ti.pix_off = env->cam_pix_off[c];
         ti.col_base = env->h_env_tri_base[e];
         pl.cams[c] = ti;
@@ -199,8 +200,8 @@ TiledPlan plan_tiled(const vuda_env* env, int tile, int nlim) {
             ti.tile0 = t0;
             pl.items.push_back(ti);
         }
-        pl.nrec += tc;
-        pl.nent += tc * nlim;
+        pl.nrec += ti.rec_cap;
+        pl.nent += ti.rec_cap * nlim;
         pl.ntoff += ntl + 2;
     }
     return pl;
@@ -324,7 +325,7 @@ int64_t tiled_scratch_estimate(const vuda_scene* sc) {
         for (int c = sc->cam_off[e]; c < sc->cam_off[e + 1]; c++) {
             const int64_t ntl = (int64_t)((sc->cam_w[c] + tile - 1) / tile) * ((sc->cam_h[c] + tile - 1) / tile);
             if (ntl > tiled_max_tiles()) return 0;   // the batch renders on the band path
-            bytes += tc * (int64_t)(tiled_record_bytes() + 4 + 4 * nlim) + (ntl + 2) * 4 +
+            bytes += tiled_record_cap(tc) * (int64_t)(tiled_record_bytes() + 4 + 4 * nlim) + (ntl + 2) * 4 +
                      (1 + (ntl + tpi - 1) / tpi) * (int64_t)sizeof(TileItem);
         }
     }

@@ -23,10 +23,12 @@ struct SimConst {
 };
 
 // Scratch of the tiled render path (tiled.cu), per camera c of env e with
-// T_e triangles and n_c tiles (of the batch's tile size): records
-// [rec_base, + T_e) of tiled_record_bytes() each, wide list [rec_base, + T_e),
-// tile lists [ent_base, + bin_limit T_e), offsets [toff_base, + n_c + 2)
-// (n_c + 1 list offsets, then the wide-list length).
+// T_e triangles and n_c tiles (of the batch's tile size), R_e =
+// tiled_record_cap(T_e) records (room for the extra fan triangles of
+// near-plane clipping): records [rec_base, + R_e) of tiled_record_bytes()
+// each, wide list [rec_base, + R_e), tile lists [ent_base, + bin_limit R_e),
+// offsets [toff_base, + n_c + 2) (n_c + 1 list offsets, then the wide-list
+// length).
 struct TileScratch {
     void* rec;
     uint32_t* ent;
@@ -188,7 +190,7 @@ struct __align__(16) TileItem {
     int cam, tile0, W, H;         // bytes 0..15
     int tiles_x, ntiles, env, pad;  // 16..31
     long long rec_base, ent_base; // 32..47
-    long long toff_base, pad2;    // 48..63
+    long long toff_base, rec_cap; // 48..63: rec_cap = records (and wide-list entries) of the camera
     long long pix_off;            // 64: first pixel of the camera in the frame
     long long col_base;           // 72: first triangle of the environment in the colour table
 };
@@ -197,6 +199,11 @@ int tiled_default_bin_limit();       // list entries per triangle at most, by de
 int tiled_max_bin_limit();
 int tiled_tiles_per_item(int tile);  // tiles per raster work item for tile size 8, 16 or 32
 size_t tiled_record_bytes();
+// Record slots of a camera whose environment has T triangles: T, plus an
+// eighth for the second fan triangle of a triangle clipped to a
+// quadrilateral at the near plane (bin_kernel flags VUDA_FLAG_CLIP_CAPACITY
+// and drops what does not fit).
+inline long long tiled_record_cap(long long T) { return T + T / 8 + 8; }
 // Set up, shade and bin every camera into tile x tile tiles (8, 16, 32),
 // listing a triangle under at most nlim tiles (else on the wide list), then
 // rasterise and resolve the work items (camera, first tile) of

@@ -7,9 +7,10 @@
 //      fit the shared-memory vertex cache: transform every vertex
 //      world = R(q) (s * v) + p, view = basis . (world - eye), project
 //      sx = W/2 + fpy xc / zc, sy = H/2 - fpy yc / zc, snap to 24.8 fixed
-//      point (round to nearest even).  Vertices before the near plane
-//      (zc < 0.01) or beyond the 2^14 px guard band invalidate their
-//      triangles (flagged, not clipped).
+//      point (round to nearest even).  Triangles crossing the near plane
+//      (zc = 0.01) are clipped there (Sutherland-Hodgman, a fan of one or
+//      two triangles with the original id); vertices beyond the 2^14 px
+//      guard band invalidate their triangles (flagged).
 //   2. one thread per triangle: integer signed area (back faces and
 //      degenerate triangles culled), bounding box clipped to the band, flat
 //      colour from the world face normal.  Triangles covering at most 16
@@ -364,15 +365,22 @@ __device__ __forceinline__ void render_band(const DevBatch& b, int cam, int y0, 
             uint2 tv = tt[t];
             int i0 = tv.x & 0xffff, i1 = tv.x >> 16, i2 = tv.y;
             int fl = vflag[i0] | vflag[i1] | vflag[i2];
-            if (fl) {
-                atomicOr(sflags, (unsigned)fl);
-                continue;
+            if (fl == 0) {
+                int X[3] = {vX[i0], vX[i1], vX[i2]};
+                int Y[3] = {vY[i0], vY[i1], vY[i2]};
+                float iz[3] = {viz[i0], viz[i1], viz[i2]};
+                Tri tri;
+                if (setup_tri(X, Y, iz, tri0 + (uint32_t)t, bd, tri)) submit_tri(tri, bd, bn);
+            } else {
+                // before the near plane or beyond the guard band: cull, clip or flag
+                ClipFan f;
+                const int cf = clip_near_fan(b, a.pose, cv, b0, cb0, vt[i0], vt[i1], vt[i2], f);
+                if (cf) atomicOr(sflags, (unsigned)cf);
+                for (int k = 0; k < f.n; k++) {
+                    Tri tri;
+                    if (setup_tri(f.X[k], f.Y[k], f.iz[k], tri0 + (uint32_t)t, bd, tri)) submit_tri(tri, bd, bn);
+                }
             }
-            int X[3] = {vX[i0], vX[i1], vX[i2]};
-            int Y[3] = {vY[i0], vY[i1], vY[i2]};
-            float iz[3] = {viz[i0], viz[i1], viz[i2]};
-            Tri tri;
-            if (setup_tri(X, Y, iz, tri0 + (uint32_t)t, bd, tri)) submit_tri(tri, bd, bn);
         }
         __syncthreads();
         // 3. binned triangles, tile by tile

@@ -163,6 +163,7 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
     const CamView cv = load_cam(b, cam);
     const int b0 = b.body_off[e];
     uint32_t* colors = b.tri_color + ci.col_base;
+    const int rec_cap = (int)ci.rec_cap;
 
     for (int i = threadIdx.x; i < ntiles; i += kBT) s_cnt[i] = 0;
     if (threadIdx.x == 0) {
@@ -192,64 +193,79 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
         for (int t = threadIdx.x; t < nt; t += kBT) {
             const uint2 tv = tt[t];
             const int i0 = tv.x & 0xffff, i1 = tv.x >> 16, i2 = tv.y;
-            const int fl = vflag[i0] | vflag[i1] | vflag[i2];
-            if (fl) {
-                atomicOr(&s_flags, (unsigned)fl);
-                continue;
-            }
-            const int X0 = vX[i0], X1 = vX[i1], X2 = vX[i2];
-            const int Y0 = vY[i0], Y1 = vY[i1], Y2 = vY[i2];
-            const int mnx = min(X0, min(X1, X2)), mxx = max(X0, max(X1, X2));
-            const int mny = min(Y0, min(Y1, Y2)), mxy = max(Y0, max(Y1, Y2));
-            // pixel centres 256 p + 128 inside [mn, mx], before and after clipping to the image
-            const int ux0 = (mnx - 128 + 255) >> 8, ux1 = (mxx - 128) >> 8;
-            const int uy0 = (mny - 128 + 255) >> 8, uy1 = (mxy - 128) >> 8;
-            const int px0 = max(ux0, 0), px1 = min(ux1, W - 1);
-            const int py0 = max(uy0, 0), py1 = min(uy1, H - 1);
-            if (px0 > px1 || py0 > py1) continue;
-            const long long area2 = ((long long)X1 - X0) * ((long long)Y2 - Y0) - ((long long)Y1 - Y0) * ((long long)X2 - X0);
-            if (area2 >= 0) continue;   // back-facing or degenerate
-            // oriented to positive area: (v0, v2, v1)
-            const int X[3] = {X0, X2, X1}, Y[3] = {Y0, Y2, Y1};
-            TriRec g;
-            unsigned tl = 0u;
+            const uint32_t id = tri0 + (uint32_t)t;
+            // set-up, record, flat colour and binning of one screen triangle
+            // (snapped vertices in mesh order) with the triangle's id
+            auto emit = [&](int X0, int X1, int X2, int Y0, int Y1, int Y2, float z0, float z1, float z2) {
+                const int mnx = min(X0, min(X1, X2)), mxx = max(X0, max(X1, X2));
+                const int mny = min(Y0, min(Y1, Y2)), mxy = max(Y0, max(Y1, Y2));
+                // pixel centres 256 p + 128 inside [mn, mx], before and after clipping to the image
+                const int ux0 = (mnx - 128 + 255) >> 8, ux1 = (mxx - 128) >> 8;
+                const int uy0 = (mny - 128 + 255) >> 8, uy1 = (mxy - 128) >> 8;
+                const int px0 = max(ux0, 0), px1 = min(ux1, W - 1);
+                const int py0 = max(uy0, 0), py1 = min(uy1, H - 1);
+                if (px0 > px1 || py0 > py1) return;
+                const long long area2 =
+                    ((long long)X1 - X0) * ((long long)Y2 - Y0) - ((long long)Y1 - Y0) * ((long long)X2 - X0);
+                if (area2 >= 0) return;   // back-facing or degenerate
+                // oriented to positive area: (v0, v2, v1)
+                const int X[3] = {X0, X2, X1}, Y[3] = {Y0, Y2, Y1};
+                TriRec g;
+                unsigned tl = 0u;
 #pragma unroll
-            for (int i = 0; i < 3; i++) {
-                const int j = i == 2 ? 0 : i + 1, k = i == 0 ? 2 : i - 1;
-                const long long A = (long long)Y[j] - Y[k];
-                const long long Bv = (long long)X[k] - X[j];
-                g.A[i] = (int)A;
-                g.B[i] = (int)Bv;
-                const bool owns = (A > 0) || (A == 0 && Bv > 0);
-                g.C[i] = -A * X[j] - Bv * Y[j] - (owns ? 0 : 1);
-                if (owns) tl |= 1u << i;
-            }
-            const long long pa = ((long long)X[1] - X[0]) * ((long long)Y[2] - Y[0]) -
-                                 ((long long)Y[1] - Y[0]) * ((long long)X[2] - X[0]);
-            g.af = i64_to_f32(pa);
-            g.iz[0] = viz[i0];
-            g.iz[1] = viz[i2];
-            g.iz[2] = viz[i1];
-            g.id = tri0 + (uint32_t)t;
-            g.x0 = (short)px0; g.x1 = (short)px1; g.y0 = (short)py0; g.y1 = (short)py1;
-            if ((long long)(ux1 - ux0 + 1) * (uy1 - uy0 + 1) <= kLanePx) tl |= kSmallBit;
-            g.tl = tl;
-            const int r = atomicAdd(&s_nrec, 1);
-            store_rec(rec + r, g);
-            // flat colour of the recorded triangle (only recorded triangles
-            // can be the nearest at a pixel); the cameras of one environment
-            // write the same value
-            {
-                const int bi = cb0 + vt[i0].y;
-                const uint32_t alb = bi < 0 ? b.ground_albedo : __ldg(b.albedo + b0 + bi);
-                colors[g.id] = flat_color(vW[i0], vW[i1], vW[i2], alb, b.light);
-            }
-            const int tx0 = px0 / T, tx1 = px1 / T, ty0 = py0 / T, ty1 = py1 / T;
-            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= nlim) {
-                for (int ty = ty0; ty <= ty1; ty++)
-                    for (int tx = tx0; tx <= tx1; tx++) atomicAdd(&s_cnt[ty * tiles_x + tx], 1);
+                for (int i = 0; i < 3; i++) {
+                    const int j = i == 2 ? 0 : i + 1, k = i == 0 ? 2 : i - 1;
+                    const long long A = (long long)Y[j] - Y[k];
+                    const long long Bv = (long long)X[k] - X[j];
+                    g.A[i] = (int)A;
+                    g.B[i] = (int)Bv;
+                    const bool owns = (A > 0) || (A == 0 && Bv > 0);
+                    g.C[i] = -A * X[j] - Bv * Y[j] - (owns ? 0 : 1);
+                    if (owns) tl |= 1u << i;
+                }
+                const long long pa = ((long long)X[1] - X[0]) * ((long long)Y[2] - Y[0]) -
+                                     ((long long)Y[1] - Y[0]) * ((long long)X[2] - X[0]);
+                g.af = i64_to_f32(pa);
+                g.iz[0] = z0;
+                g.iz[1] = z2;
+                g.iz[2] = z1;
+                g.id = id;
+                g.x0 = (short)px0; g.x1 = (short)px1; g.y0 = (short)py0; g.y1 = (short)py1;
+                if ((long long)(ux1 - ux0 + 1) * (uy1 - uy0 + 1) <= kLanePx) tl |= kSmallBit;
+                g.tl = tl;
+                const int r = atomicAdd(&s_nrec, 1);
+                if (r >= rec_cap) {   // reachable only through the extra fan triangles of clipping
+                    atomicOr(&s_flags, (unsigned)VUDA_FLAG_CLIP_CAPACITY);
+                    return;
+                }
+                store_rec(rec + r, g);
+                // flat colour of the recorded triangle (only recorded triangles
+                // can be the nearest at a pixel); the cameras of one environment
+                // write the same value
+                {
+                    const int bi = cb0 + vt[i0].y;
+                    const uint32_t alb = bi < 0 ? b.ground_albedo : __ldg(b.albedo + b0 + bi);
+                    colors[id] = flat_color(vW[i0], vW[i1], vW[i2], alb, b.light);
+                }
+                const int tx0 = px0 / T, tx1 = px1 / T, ty0 = py0 / T, ty1 = py1 / T;
+                if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= nlim) {
+                    for (int ty = ty0; ty <= ty1; ty++)
+                        for (int tx = tx0; tx <= tx1; tx++) atomicAdd(&s_cnt[ty * tiles_x + tx], 1);
+                } else {
+                    wide[atomicAdd(&s_nwide, 1)] = (uint32_t)r;
+                }
+            };
+            const int fl = vflag[i0] | vflag[i1] | vflag[i2];
+            if (fl == 0) {
+                emit(vX[i0], vX[i1], vX[i2], vY[i0], vY[i1], vY[i2], viz[i0], viz[i1], viz[i2]);
             } else {
-                wide[atomicAdd(&s_nwide, 1)] = (uint32_t)r;
+                // before the near plane or beyond the guard band: cull, clip or flag
+                ClipFan f;
+                const int cf = clip_near_fan(b, pose, cv, b0, cb0, vt[i0], vt[i1], vt[i2], f);
+                if (cf) atomicOr(&s_flags, (unsigned)cf);
+                for (int k = 0; k < f.n; k++)
+                    emit(f.X[k][0], f.X[k][1], f.X[k][2], f.Y[k][0], f.Y[k][1], f.Y[k][2], f.iz[k][0], f.iz[k][1],
+                         f.iz[k][2]);
             }
         }
     }
@@ -278,7 +294,7 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
     }
     __syncthreads();
     // fill the tile lists (the order inside a list is free: the key minimum does not depend on it)
-    const int nrec = s_nrec;
+    const int nrec = min(s_nrec, rec_cap);
     for (int r = threadIdx.x; r < nrec; r += kBT) {
         const int2 bb = *reinterpret_cast<const int2*>(reinterpret_cast<const char*>(rec + r) + 64);
         const int px0 = (short)(bb.x & 0xffff), px1 = bb.x >> 16;

@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 lib = C.CDLL(LIB_PATH)
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_BUSY, ERR_UNSUPPORTED = range(8)
-FLAG_CONTACT_OVERFLOW, FLAG_NEAR_DISCARD, FLAG_GUARD_DISCARD, FLAG_MESH_CAPACITY, FLAG_BAD_RANGE = 1, 2, 4, 8, 16
+FLAG_CONTACT_OVERFLOW, FLAG_CLIP_CAPACITY, FLAG_GUARD_DISCARD, FLAG_MESH_CAPACITY, FLAG_BAD_RANGE = 1, 2, 4, 8, 16
 COSCHED_STREAMS, COSCHED_GREEN, COSCHED_SHARED = 1, 2, 3
 RENDER_AUTO, RENDER_BAND, RENDER_TILED = 0, 1, 2
 PRIORITY_NONE, PRIORITY_SIM, PRIORITY_RENDER = 0, 1, 2

@@ -278,11 +278,54 @@ def test_render_degenerate_camera_sizes_other_tiles(V, orc, tile):
     env.close()
 
 
+def _near_scenes():
+    """Scenes with triangles crossing the near plane: a large box face
+    2^-9 m below the eye (clipped to a triangle and to a quadrilateral), and
+    spheres and boxes crowding the eye of a 96 x 72 camera (some wholly
+    behind it, others cut by the plane at every angle)."""
+    h = 2.0 ** -9
+    face = S.custom([dict(type="box", h=(1.0, 1.0, 0.125), pos=(0.0, 0.5, 0.875))], res=128,
+                    cams=[dict(eye=(0.0, 0.0, 1.0 + h), target=(0.0, 1.0, 1.0 + h), fov=60.0)])
+    eye, tgt = np.array([0.0, -2.5, 1.5]), np.array([0.0, 0.0, 0.4])
+    f = (tgt - eye) / np.linalg.norm(tgt - eye)
+    r = np.cross(f, [0.0, 0.0, 1.0])
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    out = [face]
+    for seed in (0, 4):     # 22 and 62 triangles cross the plane
+        rng = np.random.default_rng(seed)
+        bodies = []
+        for i in range(24):
+            p = eye + f * rng.uniform(-0.1, 0.5) + r * rng.uniform(-0.15, 0.15) + u * rng.uniform(-0.15, 0.15)
+            q = rng.normal(size=4)
+            q /= np.linalg.norm(q)
+            if i % 2:
+                bodies.append(dict(type="box", h=tuple(rng.uniform(0.02, 0.08, 3)), pos=tuple(p), quat=tuple(q)))
+            else:
+                bodies.append(dict(type="sphere", r=float(rng.uniform(0.02, 0.08)), pos=tuple(p)))
+        crowd = S.custom(bodies, res=96)
+        crowd.cam_h[:] = 72
+        out.append(crowd)
+    return out
+
+
 @pytest.mark.parametrize("path", PATHS)
-def test_render_near_plane_flags(V, orc, path):
-    sc = S.custom([dict(type="sphere", r=0.1, pos=(0.0, -3.0, 1.5)),
-                   dict(type="box", h=(0.05, 0.05, 0.05), pos=(0.1, 0.0, 0.05))], res=64)
-    _render_cmp(V, orc, sc, path=path)
+def test_render_near_plane_clipping(V, orc, path):
+    """Triangles crossing the near plane are clipped (Sutherland-Hodgman,
+    one or two fan triangles with the original id) identically on both
+    paths and in the oracle: ids bit-exact, depth 1e-6, colour 1 LSB."""
+    for sc in _near_scenes():
+        tid = _render_cmp(V, orc, sc, path=path)
+        assert ((tid != 0xFFFFFFFF) & (tid >= 2)).any()
+
+
+@pytest.mark.parametrize("tile,nlim", [(8, 1), (16, 9), (32, 64)])
+def test_render_near_plane_clipping_tilings(V, orc, tile, nlim):
+    for sc in _near_scenes():
+        env = V.Env(sc, render_path=V.RENDER_TILED, tile_size=tile, tile_bin_limit=nlim)
+        _render_cmp(V, orc, sc, env=env)
+        assert env.status()[0][0] & V.FLAG_CLIP_CAPACITY == 0
+        env.close()
 
 
 def test_render_paths_identical_frames_full_size(V):
@@ -523,9 +566,9 @@ def test_full_size_cfg2_sampled(V, orc, launch):
 @pytest.mark.parametrize("mode", ["streams-graph", "green"])
 def test_full_size_cfg2_settled_piles(V, orc, mode):
     """The regime the benchmark times: the 1024-environment batch after 120
-    settling steps (piles in contact, about 4.5 contacts per body, many
-    spilled to global memory), then 8 pipelined steps in a co-scheduled
-    launch configuration.  Sampled environments, stepped by the oracle from
+    settling steps (piles in contact, about 2.7 contacts per body; the most
+    crowded environments spill contacts to global memory), then 8 pipelined
+    steps in a co-scheduled launch configuration.  Sampled environments, stepped by the oracle from
     the GPU's settled state, match within the physics tolerance; their
     frames match the oracle's render of the GPU's last pose slot."""
     import torch
@@ -536,7 +579,7 @@ def test_full_size_cfg2_settled_piles(V, orc, mode):
     torch.cuda.synchronize()
     settled = env.get_state()
     cc = env.contact_counts()
-    assert cc.mean() > 3.0 * 32, cc.mean()          # settled piles, contact-rich
+    assert cc.mean() > 2.0 * 32, cc.mean()          # settled piles, contact-rich
     if mode == "green":
         env.coschedule(V.COSCHED_GREEN)
     else:

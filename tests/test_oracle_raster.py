@@ -241,12 +241,97 @@ def test_sphere_silhouette_area(orc):
     assert dep.reshape(64, 64)[32, 32] == pytest.approx(D - r, rel=0.02)
 
 
-def test_near_plane_discard(orc):
-    """A body behind the camera is discarded and flagged, not drawn."""
+def test_body_behind_the_camera_draws_nothing(orc):
+    """A body wholly behind the camera (every vertex before the near plane)
+    leaves no fragment and raises no flag."""
     sc = S.custom([dict(type="sphere", r=0.1, pos=(0.0, -3.0, 1.5))], res=32)
     rgb, dep, tid, flags = orc.render(sc)
-    assert flags[0] & 2
+    assert flags[0] == 0
     assert not ((tid >= 2) & (tid != 0xFFFFFFFF)).any()
+
+
+def _near_face_scene(res=128):
+    """A camera 2^-9 m above the top face of a large box, looking straight
+    along +y (the camera basis is exact: right = x, up = z, forward = y).
+    The face (z = 1, |x| <= 1, -0.5 <= y <= 1.5) passes through the near
+    plane: its two triangles cross it, one with one vertex behind the
+    camera, the other with two."""
+    h = 2.0 ** -9
+    sc = S.custom([dict(type="box", h=(1.0, 1.0, 0.125), pos=(0.0, 0.5, 0.875))], res=res,
+                  cams=[dict(eye=(0.0, 0.0, 1.0 + h), target=(0.0, 1.0, 1.0 + h), fov=60.0)])
+    assert (sc.cam_right[0] == [1, 0, 0]).all() and (sc.cam_up[0] == [0, 0, 1]).all()
+    assert (sc.cam_fwd[0] == [0, 1, 0]).all()
+    return sc, h
+
+
+def test_face_crossing_the_near_plane_is_clipped_not_dropped(orc):
+    """Sutherland-Hodgman clipping at zc = near: the part of the face in
+    front of the near plane is drawn.  A pixel-centre ray (a, 1, -b) meets
+    the face at view depth t = h / b; it is covered iff t >= near (the
+    clipped edge, projected to row H/2 + fpy h / near) and the hit lies on
+    the face.  Every pixel of rows 64..85 is covered by the face (no gap
+    along the fan diagonal or the triangles' shared edge), no other pixel
+    is, and the depth is the ray's t (down to 1.007 near on the last row,
+    next to the clipped edge)."""
+    res = 128
+    sc, h = _near_face_scene(res)
+    rgb, dep, tid, flags = orc.render(sc)
+    # the ground quad (z = 0, 1 m below) also crosses the near plane, but it
+    # lies wholly below the frustum's bottom plane: culled, no flag (its
+    # clipped corners would project beyond the guard band)
+    assert flags[0] == 0
+    assert not ((tid == 0) | (tid == 1)).any()
+    fpy = float(sc.cam_fpy[0])
+    near = float(np.float32(0.01))
+    face = ((tid != 0xFFFFFFFF) & (tid >= 2)).reshape(res, res)
+    exp = np.zeros((res, res), bool)
+    tray = np.zeros((res, res))
+    for py in range(res):
+        b = (py + 0.5 - res / 2) / fpy
+        if b <= 0:
+            continue
+        t = h / b
+        for px in range(res):
+            a = (px + 0.5 - res / 2) / fpy
+            if near <= t <= 1.5 and abs(a * t) <= 1.0:
+                exp[py, px] = True
+                tray[py, px] = t
+    # the clipped edge lies between pixel-centre rows (no tie to resolve)
+    edge_row = res / 2 + fpy * h / near
+    assert abs(edge_row - round(edge_row - 0.5) - 0.5) > 0.05
+    rows = np.nonzero(exp.any(1))[0]
+    assert rows[0] == 64 and rows[-1] == 85 and exp[64:86].all()
+    np.testing.assert_array_equal(face, exp)
+    # depth: the face is seen at a grazing angle (its far edge projects
+    # 0.14 px below the horizon), so the 1/256 px snapping of its vertices
+    # tilts the interpolated plane by up to a few 1e-4; the interpolation
+    # itself is pinned to 1e-6 elsewhere
+    d = dep.reshape(res, res)
+    np.testing.assert_allclose(d[exp], tray[exp], rtol=1e-3)
+    assert d[85].min() < 1.01 * near
+    # both triangles of the face contribute (one clipped to a triangle, one to a quad)
+    assert len(np.unique(tid.reshape(res, res)[exp])) == 2
+
+
+def test_clipped_edge_shared_by_two_triangles_is_watertight(orc):
+    """The same face split differently: with the box turned 90 degrees about
+    z the face's diagonal runs the other way, so the near plane cuts the
+    triangles' shared edge from the other side; coverage is still exactly
+    the clipped face, with no pixel lost or drawn twice along the cut."""
+    res = 96
+    h = 2.0 ** -9
+    s = math.sqrt(0.5)
+    sc = S.custom([dict(type="box", h=(1.0, 1.0, 0.125), pos=(0.0, 0.5, 0.875), quat=(s, 0.0, 0.0, s))], res=res,
+                  cams=[dict(eye=(0.0, 0.0, 1.0 + h), target=(0.0, 1.0, 1.0 + h), fov=60.0)])
+    _, _, tid, flags = orc.render(sc)
+    assert flags[0] == 0
+    fpy = float(sc.cam_fpy[0])
+    near = float(np.float32(0.01))
+    face = ((tid != 0xFFFFFFFF) & (tid >= 2)).reshape(res, res)
+    rows = [py for py in range(res) if (py + 0.5 - res / 2) > 0 and h * fpy / (py + 0.5 - res / 2) >= near]
+    exp = np.zeros((res, res), bool)
+    exp[rows] = True
+    np.testing.assert_array_equal(face, exp)
 
 
 def test_scene_meshes_are_closed_and_outward():
@@ -313,3 +398,22 @@ def test_box_with_unequal_half_extents_seen_face_on(orc):
     I = 0.2 + 0.8 * max(0.0, -L[1])
     want = np.array([int(ch * I + 0.5) for ch in S.PALETTE[0]])
     assert np.abs(rgb.reshape(res, res, 3)[exp].astype(int) - want).max() <= 1
+
+
+def test_guard_band_flag_only_for_triangles_that_reach_the_image(orc):
+    """A vertex in front of the camera but beyond the 2^14 px guard band
+    discards its triangle with the guard flag -- unless the triangle lies
+    wholly beyond one side plane of the frustum, where it could not cover a
+    pixel anyway (culled silently).  Camera at (0, 0, 1) looking along +y."""
+    cam = [dict(eye=(0.0, 0.0, 1.0), target=(0.0, 1.0, 1.0), fov=60.0)]
+    # a slab 3 cm ahead spanning x = -4 .. 4 m: its front corners project to
+    # |sx| ~ 1.8e4 px, beyond the band, and it crosses the view: flagged
+    wide = S.custom([dict(type="box", h=(4.0, 0.005, 0.05), pos=(0.0, 0.03, 1.0))], res=128, cams=cam)
+    _, _, tid, flags = orc.render(wide)
+    assert flags[0] == 4
+    # the same slab moved 6 m to the right lies wholly right of the image
+    # (fpy xc > W/2 zc at every vertex): culled without a flag
+    right = S.custom([dict(type="box", h=(4.0, 0.005, 0.05), pos=(6.0, 0.03, 1.0))], res=128, cams=cam)
+    _, _, tid, flags = orc.render(right)
+    assert flags[0] == 0
+    assert not ((tid >= 2) & (tid != 0xFFFFFFFF)).any()
