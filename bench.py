@@ -48,8 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serial-only", action="store_true", help="only the serialized loop (for profiling)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-jobs", type=int, default=8)
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-jobs", default="8,16,32,64", help="job counts of the serving grid")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--configs", default="1,3,4", help="other workloads measured beside the headline one")
+    ap.add_argument("--no-rollout", action="store_true", help="skip the RL-rollout measurement")
     return ap.parse_args()
 
 
@@ -311,13 +313,178 @@ def serving_bench(V, S, njobs: int, nreq: int, load: float = 0.8, burst: int = 1
     rate = load * cap
     cb = run(False, rate)
     fifo = run(True, rate)
+    fifo_own = run(True, load * cap_fifo)
     return {"workload": "%d jobs of the serving recipe (16-1024 envs, 4-256 bodies, 64-256 px), %d Poisson requests "
                         "at %d%% of the continuous-batching capacity (the rate served under saturating Poisson "
                         "arrivals); HBM budget 60%% of free memory"
                         % (njobs, nreq, round(100 * load)),
+            "jobs": njobs, "requests": nreq, "load": load,
             "capacity_requests_per_s": cap, "capacity_fifo_requests_per_s": cap_fifo,
             "burst_requests_per_s": burst_cap, "burst_fifo_requests_per_s": burst_fifo, "arrival_rate_hz": rate,
-            "continuous_batching": cb, "serialized_fifo": fifo}
+            "continuous_batching": cb, "serialized_fifo": fifo,
+            "serialized_fifo_at_own_load": dict(fifo_own, arrival_rate_hz=load * cap_fifo)}
+
+
+CONFIGS = {
+    1: ("cfg1: 16 envs x 8 spheres, 4 substeps, one 64x64 RGB-D camera per env; plain serialized sim-then-render, "
+        "100 steps", 100, 0),
+    3: ("cfg3: 4096 envs x 64 convex hulls (500-2000 tris each), 8 substeps, two 128x128 RGB-D cameras per env; "
+        "autotuned (tile size, bin limit, co-scheduling mode and split) and replayed from a CUDA graph", 16, 4),
+    4: ("cfg4: 2048 envs with 4-256 bodies (log-uniform) and 64/128/256 px cameras; one persistent launch per phase "
+        "(work lists by size class)", 40, 20),
+}
+
+
+def phase_roofline(env, sc, Ts: float, Tr: float, fp32_peak: float, hbm_peak: float, bytes_out: int) -> dict:
+    """Both phases of one configuration against their bounds: the physics
+    against the FP32 lanes (the method's operations counted per environment
+    from its body and contact counts), the render against HBM (its output
+    frames and the poses it reads)."""
+    cc = env.contact_counts().astype(np.float64)
+    nb = np.diff(sc.body_off).astype(np.float64)
+    flops = float(sum(sim_flops(c, int(n), sc.params.substeps, sc.params.iterations) for c, n in zip(cc, nb)))
+    sim_ach = flops / (Ts / 1000.0) / 1e12
+    alg = bytes_out + env.B * 28
+    ren_ach = alg / (Tr / 1000.0) / 1e9
+    return {"sim": {"bound": "alu", "achieved": sim_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": sim_ach / fp32_peak, "algorithmic_flops_per_launch": flops, "launch_ms": Ts},
+            "render": {"bound": "hbm", "achieved": ren_ach, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": ren_ach / hbm_peak, "algorithmic_bytes_per_launch": alg, "launch_ms": Tr}}
+
+
+def oracle_sample(sc, secs: float = 1.0, max_envs: int = 8, settle: int = 0) -> dict:
+    """The oracle as it stands, single-threaded, on a bounded sample of a
+    configuration: its first environments (at most max_envs), stepped and
+    rendered for at least `secs` (at least one step)."""
+    import oracle
+    sub = sc.subset(range(min(max_envs, sc.num_envs)))
+    st = sub.state()
+    if settle:
+        st, _, _ = oracle.sim_step(sub, settle)
+    t = time.perf_counter()
+    n = 0
+    while n < 1 or time.perf_counter() - t < secs:
+        st, _, _ = oracle.sim_step(sub, 1, state=st)
+        oracle.render(sub, st["pos"], st["quat"], triid=False)
+        n += 1
+    dt = time.perf_counter() - t
+    return {"value": sub.num_envs * n / dt, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d envs x %d steps of this configuration, sim + render, single-threaded C oracle"
+                      % (sub.num_envs, n)}
+
+
+def config_bench(V, S, k: int, fp32_peak: float, hbm_peak: float, warmup: int, cpu: bool) -> dict:
+    """One of the other configurations: serialized and co-scheduled (cfg3:
+    the autotuner's choice replayed from a CUDA graph; cfg4: persistent work
+    lists) rendered env-steps/s, both phases' rooflines, and the oracle on a
+    sample of the same workload."""
+    import torch
+    desc, steps, settle = CONFIGS[k]
+    sc = {1: S.cfg1, 3: S.cfg3, 4: S.cfg4}[k]()
+    env = V.Env(sc, persistent=(k == 4))
+    ring = [env.alloc_frame(triid=False), env.alloc_frame(triid=False)]
+    bytes_out = env.P * 7
+    if settle:
+        env.pipeline_run(settle, ring)
+    env.pipeline_run(warmup, ring)
+
+    def timed(n, runs=3):
+        res = []
+        for _ in range(runs):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            tm = env.pipeline_run(n, ring, timing=True)
+            wall = time.perf_counter() - t
+            dev = tm["total_ms"] / 1000.0
+            res.append((dev if (dev == dev and dev > 0) else wall, tm))
+        res.sort(key=lambda r: r[0])
+        return res[len(res) // 2]
+
+    t_ser, tm_ser = timed(steps)
+    Ts, Tr = float(np.mean(tm_ser["sim_ms"])), float(np.mean(tm_ser["render_ms"]))
+    out = {"workload": desc, "envs": sc.num_envs, "bodies": sc.num_bodies, "cameras": env.C, "pixels": int(env.P),
+           "steps": steps, "warmup": warmup, "settle_steps": settle,
+           "render_path": "tiled" if env.info().render_path == V.RENDER_TILED else "band",
+           "serialized": {"value": sc.num_envs * steps / t_ser, "ms_per_step": 1000.0 * t_ser / steps},
+           "phase_ms": {"sim": Ts, "render": Tr, "ideal_overlap": (Ts + Tr) / max(Ts, Tr)},
+           "roofline": phase_roofline(env, sc, Ts, Tr, fp32_peak, hbm_peak, bytes_out)}
+    if k == 3:
+        tuned = env.autotune(ring, steps=2, use_cache=False)
+        out["autotuned"] = tuned
+        if tuned.get("graph_steps", 0) <= 0:
+            try:
+                env.pipeline_capture(8, ring, stream=None if env.cosched else torch.cuda.Stream())
+            except Exception:
+                pass
+        t_co, _ = timed(steps)
+        out["coscheduled"] = {"value": sc.num_envs * steps / t_co, "ms_per_step": 1000.0 * t_co / steps,
+                              "mode": "autotuned choice (cosched_mode %d, graph steps %d)"
+                                      % (tuned["cosched_mode"], tuned["graph_steps"])}
+    elif k == 4 or k == 1:
+        env.coschedule(V.COSCHED_STREAMS)
+        env.pipeline_run(warmup, ring)
+        t_co, _ = timed(steps)
+        out["coscheduled"] = {"value": sc.num_envs * steps / t_co, "ms_per_step": 1000.0 * t_co / steps,
+                              "mode": "two streams sharing all SMs" + (", persistent work lists" if k == 4 else "")}
+    out["value"] = max(out["serialized"]["value"], out.get("coscheduled", {}).get("value", 0.0))
+    out["speedup_vs_serialized"] = out["value"] / out["serialized"]["value"]
+    out["status_flags"] = env.status()[1]
+    env.close()
+    if cpu:
+        try:
+            out["cpu_baseline"] = oracle_sample(sc, secs=1.0, max_envs={1: 16, 3: 1, 4: 8}[k])
+        except Exception as ex:
+            out["cpu_baseline"] = {"value": None, "error": repr(ex)}
+    return out
+
+
+def rollout_bench(V, S, E: int, steps: int, warmup: int, settle: int) -> dict:
+    """RL rollout (vuda_rollout_run): the benchmark's environments split into
+    two groups of trajectories, each step sim -> render -> MLP policy (hidden
+    256 and 4096, randomly initialised, FP32) on one GPU; time-sliced (one
+    stream) against the inter-trajectory schedule (one group's sim beside
+    the other's render and policy) on shared SMs and on 50/50 green
+    partitions.  Rendered env-steps/s of both groups together."""
+    import torch
+    from paper_2605_01352_b300.policy import MLPPolicy
+    h = E // 2
+    scenes = [S.cfg2(h, env_base=0), S.cfg2(E - h, env_base=h)]
+    out = {"workload": "%d envs of the benchmark scene in two groups of %d, policy MLP on pooled 16x16 depth and "
+                       "luminance (512 features) -> 3 forces per body" % (E, h), "steps": steps, "warmup": warmup}
+    for hidden in (256, 4096):
+        res = {}
+        for mode in ("serialized", "streams", "green"):
+            envs = [V.Env(sc) for sc in scenes]
+            rings = [[e.alloc_frame(triid=False), e.alloc_frame(triid=False)] for e in envs]
+            forces = [torch.zeros((3, e.B), dtype=torch.float32, device="cuda") for e in envs]
+            pols = [MLPPolicy(sc, hidden, seed=3 + g) for g, sc in enumerate(scenes)]
+            for e, r in zip(envs, rings):
+                e.pipeline_run(settle, r)
+
+            def policy(group, step, slot, stream):
+                with torch.cuda.stream(stream):
+                    pols[group].act(rings[group][slot], forces[group])
+
+            if mode == "streams":
+                envs[0].coschedule(V.COSCHED_STREAMS)
+            elif mode == "green":
+                envs[0].coschedule(V.COSCHED_GREEN)
+            cur = torch.cuda.current_stream()
+            V.rollout_run(envs[0], envs[1], warmup, rings[0], rings[1], forces[0], forces[1], policy, stream=cur)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            V.rollout_run(envs[0], envs[1], steps, rings[0], rings[1], forces[0], forces[1], policy, stream=cur)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t
+            res[mode] = {"value": E * steps / wall, "ms_per_step": 1000.0 * wall / steps}
+            for e in envs:
+                e.close()
+        for mode in ("streams", "green"):
+            res[mode]["speedup_vs_serialized"] = res[mode]["value"] / res["serialized"]["value"]
+        out["hidden_%d" % hidden] = res
+    out["timing"] = "wall clock around vuda_rollout_run (host callbacks enqueue the policy), after %d warm-up steps" \
+        % warmup
+    return out
 
 
 def sim_flops(contacts: float, bodies: int, substeps: int, iterations: int) -> float:
@@ -466,6 +633,16 @@ def main():
     cos = env.coschedule(V.COSCHED_GREEN, args.sim_sms)
     env.pipeline_run(args.warmup, ring)
     t_gr, tm_gr, wall_gr = timed(args.steps)
+    # the other half split the 8-SM granularity allows (72 sim / 76 render)
+    green_alt = None
+    try:
+        cos_alt = env.coschedule(V.COSCHED_GREEN, cos["sim_sms"] - cos["sm_granularity"])
+        env.pipeline_run(args.warmup, ring)
+        t_ga = timed(args.steps)[0]
+        green_alt = {"value": job_throughput(ws, E, args.steps, t_ga), "ms_per_step": 1000.0 * t_ga / args.steps,
+                     "partition": cos_alt}
+    except Exception as ex:  # report why, keep the main line
+        green_alt = {"error": repr(ex)}
     # co-scheduled on two plain streams sharing all SMs, with each stream priority
     st_runs = {}
     for pname, prio in (("none", V.PRIORITY_NONE), ("sim_first", V.PRIORITY_SIM), ("render_first", V.PRIORITY_RENDER)):
@@ -535,23 +712,47 @@ def main():
     flags = env.status()[1]
     env_stats = {"contacts_mean": float(env.contact_counts().mean()), "bodies": 32,
                  "substeps": sc.params.substeps, "iterations": sc.params.iterations}
-    clk.stop()
-    serving = None
-    if not args.no_serve and rank == 0:
-        env.close()
-        try:
-            serving = serving_bench(V, S, args.serve_jobs, args.serve_requests)
-        except Exception as ex:  # report why, keep the main line
-            serving = {"error": repr(ex)}
+    env.close()
     if rank != 0:
-        env.close()
+        clk.stop()
         return
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sm_count * 128 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12   # TFLOP/s, one op per lane
+    # the other configurations, the RL rollout and the serving grid (one GPU)
+    configs = {}
+    if ws == 1:
+        for k in [int(x) for x in args.configs.split(",") if x.strip()]:
+            clk.on = True
+            try:
+                configs["cfg%d" % k] = config_bench(V, S, k, fp32_peak, hbm_peak, max(3, args.warmup),
+                                                    not args.no_cpu_baseline)
+            except Exception as ex:  # report why, keep the main line
+                configs["cfg%d" % k] = {"error": repr(ex)}
+            clk.on = False
+    rollout = None
+    if ws == 1 and not args.no_rollout:
+        clk.on = True
+        try:
+            rollout = rollout_bench(V, S, E, min(args.steps, 50), max(3, args.warmup), args.settle)
+        except Exception as ex:  # report why, keep the main line
+            rollout = {"error": repr(ex)}
+        clk.on = False
+    serving = None
+    if not args.no_serve and ws == 1:
+        serving = []
+        for nj in [int(x) for x in args.serve_jobs.split(",") if x.strip()]:
+            clk.on = True
+            try:
+                serving.append(serving_bench(V, S, nj, args.serve_requests))
+            except Exception as ex:  # report why, keep the main line
+                serving.append({"jobs": nj, "error": repr(ex)})
+            clk.on = False
+        configs["cfg5"] = serving
+    clk.stop()
 
     v_co = job_throughput(ws, E, args.steps, t_co)
     v_ser = job_throughput(ws, E, args.steps, t_ser)
     v_gr = job_throughput(ws, E, args.steps, t_gr)
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak = sm_count * 128 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12   # TFLOP/s, one op per lane
     # physics: plain FP32 arithmetic (no FMA contraction), bound by the FP32 lanes
     flops = sim_flops(env_stats["contacts_mean"], env_stats["bodies"], env_stats["substeps"],
                       env_stats["iterations"]) * E
@@ -598,6 +799,8 @@ def main():
                                "ms_per_step": 1000.0 * t_serg / args.steps}
                               if isinstance(t_serg, float) else {"error": t_serg}),
         "coscheduled_green_50_50": {"value": v_gr, "ms_per_step": 1000.0 * t_gr / args.steps, "partition": cos},
+        "coscheduled_green_other_half_split": green_alt,
+        "speedup_green_50_50_vs_serialized": v_gr / v_ser,
         "coscheduled_streams_shared_sms": {k: {"value": job_throughput(ws, E, args.steps, v[1]),
                                                "ms_per_step": 1000.0 * v[1] / args.steps}
                                            for k, v in st_runs.items()},
@@ -617,14 +820,14 @@ def main():
         "cpu_baseline": cpu,
         "cpu_baseline_single_thread": cpu1,
         "serving": serving,
+        "configs": configs,
+        "rollout": rollout,
         "gpu_launches": launches_per_step * args.steps,
         "status_flags": flags,
         "clocks": clk.summary(),
         "wall_s_coscheduled": wall_co,
     }
     print(json.dumps(out), flush=True)
-    if args.no_serve:
-        env.close()
 
 
 if __name__ == "__main__":

@@ -336,6 +336,35 @@ vuda_status vuda_pipeline_run_host(vuda_env_t env, int32_t nsteps, const float* 
                                    uint8_t* h_rgb, float* h_depth, const vuda_frame* ring, vuda_stream_t stream,
                                    vuda_timing* timing);
 
+/* RL rollout with the inter-trajectory schedule (Sec. 3.1, RL training:
+ * within a trajectory inference(k+1) depends on render(k), but different
+ * trajectories are independent; Sec. 6.4 runs the policy, physics and
+ * rendering on one GPU).  The trajectories form two groups, each its own
+ * batch (g0, g1), and each step of a group is sim -> render -> policy: the
+ * sim uses the group's forces (device [3][B_g], force0 / force1), the
+ * render writes frame ring_g[k & 1] from the new poses, and the policy reads
+ * that frame and writes the forces of the group's next step.  The policy is
+ * the caller's: `policy` is called on this thread, in step order, to
+ * ENQUEUE its work on the stream it is given (it must not synchronise);
+ * `step` is the group's step just rendered; a nonzero return aborts the
+ * run (VUDA_ERR_INVALID).  The first step uses the forces the arrays hold.
+ * Schedule: co-scheduled (vuda_coschedule on g0 with VUDA_COSCHED_STREAMS or
+ * _GREEN; g1 must not be co-scheduled: it uses g0's streams), one group's
+ * sim runs on the sim stream while the other group's render and policy run
+ * on the render stream:
+ *   sim stream:     sim(0,k) sim(1,k)        sim(0,k+1)         sim(1,k+1) ...
+ *   render stream:           ren(0,k) pol(0,k) ren(1,k) pol(1,k) ren(0,k+1) ...
+ * (with GREEN partitions the policy runs on a primary-context stream of its
+ * own, ordered by events).  Not co-scheduled: the same order on `stream`,
+ * one phase at a time (time slicing).  Results do not depend on the
+ * schedule.  timing (may be NULL): total_ms from the first sim to the last
+ * policy (NaN if the driver cannot relate the events).  Blocks until done. */
+typedef int32_t (*vuda_policy_fn)(void* user, int32_t group, int64_t step, const vuda_frame* frame, float* force,
+                                  vuda_stream_t stream);
+vuda_status vuda_rollout_run(vuda_env_t g0, vuda_env_t g1, int32_t nsteps, const vuda_frame* ring0,
+                             const vuda_frame* ring1, float* force0, float* force1, vuda_policy_fn policy,
+                             void* user, vuda_stream_t stream, vuda_timing* timing);
+
 /* Block until all work enqueued by this handle on the sim (phase 0) or
  * render (phase 1) stream has finished (wait_step / wait_render, Table 1). */
 vuda_status vuda_wait(vuda_env_t env, int32_t phase);

@@ -906,6 +906,7 @@ vuda_status vuda_env_destroy(vuda_env_t env) {
     if (env->copy_s) cudaStreamDestroy(env->copy_s);
     for (cudaEvent_t e : env->copy_done)
         if (e) cudaEventDestroy(e);
+    if (env->own_s) cudaStreamDestroy(env->own_s);
     free_env(env);
     delete env;
     return VUDA_OK;
@@ -1356,6 +1357,139 @@ vuda_status vuda_pipeline_run_host(vuda_env_t env, int32_t nsteps, const float* 
                                    vuda_timing* timing) {
     if (!h_rgb || !h_depth) return invalid("host frame ring required");
     return pipeline(env, nsteps, ring, stream, timing, h_force, force_per_step, h_rgb, h_depth);
+}
+
+// RL rollout with the inter-trajectory schedule: two groups of
+// trajectories, each looping sim -> render -> policy, with one group's sim
+// beside the other group's render and policy.
+vuda_status vuda_rollout_run(vuda_env_t g0, vuda_env_t g1, int32_t nsteps, const vuda_frame* ring0,
+                             const vuda_frame* ring1, float* force0, float* force1, vuda_policy_fn policy,
+                             void* user, vuda_stream_t stream, vuda_timing* tm) {
+    if (!g0 || !g1 || !ring0 || !ring1 || !policy) return invalid("null argument");
+    if (g0 == g1) return invalid("the two groups must be different batches");
+    if (nsteps < 0) return invalid("nsteps < 0");
+    if (g0->device != g1->device) return invalid("the two groups must be on one device");
+    if (g1->cos_mode != 0) return invalid("group 1 must not be co-scheduled itself (it uses group 0's streams)");
+    if (g0->cos_mode == VUDA_COSCHED_SHARED)
+        return (set_error("the rollout schedule supports serialized, STREAMS and GREEN co-scheduling"),
+                VUDA_ERR_UNSUPPORTED);
+    if ((g0->B > 0 && !force0) || (g1->B > 0 && !force1)) return invalid("force arrays required");
+    const bool co = g0->cos_mode != 0;
+    const bool green = g0->cos_mode == VUDA_COSCHED_GREEN;
+    cudaStream_t ss = co ? g0->sim_s : (cudaStream_t)stream;
+    cudaStream_t rs = co ? g0->ren_s : (cudaStream_t)stream;
+    // the policy runs in the primary context: on the render stream, or beside
+    // a green render partition on a stream of its own
+    if (green && !g0->own_s) CK(cudaStreamCreateWithFlags(&g0->own_s, cudaStreamNonBlocking));
+    cudaStream_t ps = green ? g0->own_s : rs;
+    vuda_env_t gs[2] = {g0, g1};
+    const vuda_frame* rings[2] = {ring0, ring1};
+    float* forces[2] = {force0, force1};
+    // events: sim done (sim context), render done (render context), policy
+    // done (primary); a wait always refers to the latest record made before it
+    cudaEvent_t ev_sim[2] = {}, ev_ren[2] = {}, ev_pol[2] = {}, t0 = nullptr, t1 = nullptr;
+    auto mk = [](CUcontext c, cudaEvent_t* e, unsigned flags) {
+        ScopedCtx g(c);
+        return cudaEventCreateWithFlags(e, flags);
+    };
+    vuda_status st = VUDA_OK;
+    auto cleanup = [&]() {
+        for (int i = 0; i < 2; i++) {
+            {
+                ScopedCtx g(g0->c_sim);
+                if (ev_sim[i]) cudaEventDestroy(ev_sim[i]);
+            }
+            {
+                ScopedCtx g(g0->c_ren);
+                if (ev_ren[i]) cudaEventDestroy(ev_ren[i]);
+            }
+            if (ev_pol[i]) cudaEventDestroy(ev_pol[i]);
+        }
+        if (t0) {
+            ScopedCtx g(g0->c_sim);
+            cudaEventDestroy(t0);
+        }
+        if (t1) cudaEventDestroy(t1);
+    };
+    cudaError_t ce = cudaSuccess;
+    for (int i = 0; i < 2 && ce == cudaSuccess; i++) {
+        ce = mk(g0->c_sim, &ev_sim[i], cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = mk(g0->c_ren, &ev_ren[i], cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev_pol[i], cudaEventDisableTiming);
+    }
+    if (ce == cudaSuccess && tm) ce = mk(g0->c_sim, &t0, cudaEventDefault);
+    if (ce == cudaSuccess && tm) ce = cudaEventCreateWithFlags(&t1, cudaEventDefault);
+    if (ce != cudaSuccess) {
+        cleanup();
+        set_error(std::string("rollout events: ") + cudaGetErrorString(ce));
+        return VUDA_ERR_CUDA;
+    }
+#define RCK(x)                                                                   \
+    do {                                                                         \
+        cudaError_t e_ = (x);                                                    \
+        if (e_ != cudaSuccess) {                                                 \
+            set_error(std::string("rollout: ") + cudaGetErrorString(e_));        \
+            st = VUDA_ERR_CUDA;                                                  \
+            goto done;                                                           \
+        }                                                                        \
+    } while (0)
+    if (co) RCK(cudaStreamSynchronize((cudaStream_t)stream));   // after the caller's prior work
+    if (tm) {
+        ScopedCtx g(g0->c_sim);
+        RCK(cudaEventRecord(t0, ss));
+    }
+    for (int k = 0; k < nsteps; k++) {
+        for (int gi = 0; gi < 2; gi++) {
+            vuda_env_t env = gs[gi];
+            const int slot = (int)(env->steps & 1);
+            {
+                ScopedCtx g(g0->c_sim);
+                if (k > 0) RCK(cudaStreamWaitEvent(ss, ev_pol[gi], 0));   // this group's forces are written
+                st = vuda_sim_step(env, 1, forces[gi], ss);
+                if (st != VUDA_OK) goto done;
+                RCK(cudaEventRecord(ev_sim[gi], ss));
+            }
+            {
+                ScopedCtx g(g0->c_ren);
+                RCK(cudaStreamWaitEvent(rs, ev_sim[gi], 0));
+                st = render_slot(env, slot, &rings[gi][k & 1], rs);
+                if (st != VUDA_OK) goto done;
+                if (ps != rs) RCK(cudaEventRecord(ev_ren[gi], rs));
+            }
+            if (ps != rs) RCK(cudaStreamWaitEvent(ps, ev_ren[gi], 0));
+            if (policy(user, gi, env->steps - 1, &rings[gi][k & 1], forces[gi], ps) != 0) {
+                st = invalid("the policy callback failed");
+                goto done;
+            }
+            RCK(cudaEventRecord(ev_pol[gi], ps));
+        }
+    }
+    if (tm) RCK(cudaEventRecord(t1, ps));
+    RCK(cudaStreamSynchronize(ss));
+    RCK(cudaStreamSynchronize(rs));
+    if (ps != rs) RCK(cudaStreamSynchronize(ps));
+    if (tm) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+            cudaGetLastError();
+            ms = __builtin_nanf("");
+        }
+        tm->total_ms = ms;
+        for (int t = 0; t < nsteps; t++) {
+            if (tm->step_ms) tm->step_ms[t] = __builtin_nanf("");
+            if (tm->sim_ms) tm->sim_ms[t] = __builtin_nanf("");
+            if (tm->render_ms) tm->render_ms[t] = __builtin_nanf("");
+        }
+    }
+#undef RCK
+done:
+    if (st != VUDA_OK) {
+        cudaStreamSynchronize(ss);
+        cudaStreamSynchronize(rs);
+        if (ps != rs) cudaStreamSynchronize(ps);
+    }
+    cleanup();
+    return st;
 }
 
 vuda_status vuda_wait(vuda_env_t env, int32_t phase) {

@@ -31,7 +31,8 @@ struct vuda_env {
     int max_h = 0;
     // co-scheduling
     int cos_mode = 0;
-    cudaStream_t sim_s = nullptr, ren_s = nullptr, own_s = nullptr;
+    cudaStream_t sim_s = nullptr, ren_s = nullptr;
+    cudaStream_t own_s = nullptr;                 // primary-context stream of the rollout policy beside green partitions
     CUgreenCtx g_sim = nullptr, g_ren = nullptr;
     CUcontext c_sim = nullptr, c_ren = nullptr;  // green contexts as CUcontext (null otherwise)
     vuda_cosched_info cos_info{};

@@ -130,6 +130,9 @@ _sig("vuda_env_set_pose", [vp, C.c_int32, vp, vp])
 _sig("vuda_env_status", [vp, vp, vp, C.c_int32])
 _sig("vuda_env_contact_counts", [vp, vp])
 _sig("vuda_raster_screen_tris", [vp, vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp])
+PolicyFn = C.CFUNCTYPE(C.c_int32, vp, C.c_int32, C.c_int64, C.POINTER(Frame), vp, vp)
+_sig("vuda_rollout_run", [vp, vp, C.c_int32, C.POINTER(Frame), C.POINTER(Frame), vp, vp, PolicyFn, vp, vp,
+                          C.POINTER(Timing)])
 _sig("vuda_sim_step_noalloc", [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                C.POINTER(SimParams), C.c_int32, vp, vp, vp, C.c_int32, vp])
 
@@ -422,6 +425,46 @@ class Env:
         c = np.zeros(max(self.E, 1), np.int32)
         check(lib.vuda_env_contact_counts(self.h, _ptr(c)), "vuda_env_contact_counts")
         return c[:self.E]
+
+
+def rollout_run(g0: "Env", g1: "Env", nsteps: int, ring0: Sequence[dict], ring1: Sequence[dict], force0, force1,
+                policy, stream=None, timing: bool = False):
+    """vuda_rollout_run: two groups of trajectories (batches g0, g1), each
+    step sim -> render -> policy, one group's sim beside the other's render
+    and policy when g0 is co-scheduled (see vuda.h).  policy(group, step,
+    slot, stream) enqueues the group's policy on `stream` (a torch stream):
+    it reads ring_g[slot] and writes force_g (device tensors [3, B_g]).
+    With timing=True returns the device time in ms (NaN if unavailable)."""
+    import torch
+    rings = (ring0, ring1)
+    slots = [{int(f["depth"].data_ptr()): i for i, f in enumerate(r)} for r in rings]
+    streams = {}
+    err = []
+
+    def cb(user, group, step, frame, force, strm):
+        try:
+            ptr = int(strm or 0)
+            ts = streams.get(ptr)
+            if ts is None:
+                ts = torch.cuda.ExternalStream(ptr) if ptr else torch.cuda.default_stream()
+                streams[ptr] = ts
+            slot = slots[group][int(frame.contents.depth or 0)]
+            policy(int(group), int(step), slot, ts)
+            return 0
+        except Exception as ex:  # reported after the call returns
+            err.append(ex)
+            return 1
+
+    fn = PolicyFn(cb)
+    fr0 = (Frame * 2)(Env.frame_struct(ring0[0]), Env.frame_struct(ring0[1 % len(ring0)]))
+    fr1 = (Frame * 2)(Env.frame_struct(ring1[0]), Env.frame_struct(ring1[1 % len(ring1)]))
+    tm = Timing(None, None, None, 0.0)
+    st = lib.vuda_rollout_run(g0.h, g1.h, nsteps, fr0, fr1, _dptr(force0), _dptr(force1), fn, None,
+                              _stream(stream), C.byref(tm) if timing else None)
+    if err:
+        raise err[0]
+    check(st, "vuda_rollout_run")
+    return float(tm.total_ms) if timing else None
 
 
 def raster_screen_tris(xy, z, W: int, H: int, count: bool = False, stream=None):
