@@ -487,6 +487,35 @@ def rollout_bench(V, S, E: int, steps: int, warmup: int, settle: int) -> dict:
     return out
 
 
+def physics_options_bench(V, S, E: int, settle: int) -> dict:
+    """Physics step time on the settled benchmark batch with the options
+    beyond the configured physics: the gyroscopic term of boxes and box-box
+    edge-edge contacts (each off / on; the headline uses neither)."""
+    import dataclasses
+    import torch
+    out = {}
+    s0 = torch.cuda.current_stream()
+    for gyro, edges in ((0, 0), (1, 0), (0, 1), (1, 1)):
+        sc = S.cfg2(E)
+        sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, gyroscopic=gyro, edge_contacts=edges))
+        env = V.Env(sc)
+        ring = [env.alloc_frame(triid=False), env.alloc_frame(triid=False)]
+        env.pipeline_run(settle, ring)
+        for _ in range(3):
+            env.sim_step(1, stream=s0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s0)
+        for _ in range(20):
+            env.sim_step(1, stream=s0)
+        b.record(s0)
+        torch.cuda.synchronize()
+        out["gyroscopic_%d_edge_contacts_%d" % (gyro, edges)] = {
+            "sim_ms": a.elapsed_time(b) / 20, "contacts_mean": float(env.contact_counts().mean())}
+        env.close()
+    return out
+
+
 def sim_flops(contacts: float, bodies: int, substeps: int, iterations: int) -> float:
     """Floating-point operations of one environment-step of the physics as
     the method defines them (each add, mul, div and sqrt counted once): per
@@ -737,6 +766,14 @@ def main():
         except Exception as ex:  # report why, keep the main line
             rollout = {"error": repr(ex)}
         clk.on = False
+    options = None
+    if ws == 1:
+        clk.on = True
+        try:
+            options = physics_options_bench(V, S, E, args.settle)
+        except Exception as ex:  # report why, keep the main line
+            options = {"error": repr(ex)}
+        clk.on = False
     serving = None
     if not args.no_serve and ws == 1:
         serving = []
@@ -822,6 +859,7 @@ def main():
         "serving": serving,
         "configs": configs,
         "rollout": rollout,
+        "physics_options": options,
         "gpu_launches": launches_per_step * args.steps,
         "status_flags": flags,
         "clocks": clk.summary(),

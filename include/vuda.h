@@ -77,6 +77,10 @@ typedef struct {
     float jacobi_omega;           /* relaxation of the mass-split Jacobi update */
     int32_t plane;                /* 1: static ground plane z = 0 */
     int32_t max_contacts_per_body;/* contact capacity per env = this * bodies */
+    int32_t gyroscopic;           /* 1: gyroscopic term of boxes, I dw/dt = -w x I w in the body frame, one
+                                     implicit (Newton) step per substep; spheres and hull proxies have none */
+    int32_t edge_contacts;        /* 1: box-box edge-edge contacts (separating-axis test over 15 axes; one
+                                     contact between crossing edges, after the pair's corner contacts) */
 } vuda_sim_params;
 
 /* Host description of a batch (all arrays host memory, read during

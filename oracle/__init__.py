@@ -42,7 +42,8 @@ class _Params(C.Structure):
                 ("gravity", C.c_double * 3), ("restitution", C.c_double),
                 ("restitution_threshold", C.c_double), ("friction", C.c_double),
                 ("baumgarte", C.c_double), ("slop", C.c_double), ("margin", C.c_double),
-                ("jacobi_omega", C.c_double), ("plane", C.c_int), ("max_contacts_per_body", C.c_int)]
+                ("jacobi_omega", C.c_double), ("plane", C.c_int), ("max_contacts_per_body", C.c_int),
+                ("gyroscopic", C.c_int), ("edge_contacts", C.c_int)]
 
 
 _lib = None
@@ -62,7 +63,7 @@ def _ptr(a: Optional[np.ndarray]):
 def _params(p) -> _Params:
     return _Params(p.dt, p.substeps, p.iterations, (C.c_double * 3)(*p.gravity), p.restitution,
                    p.restitution_threshold, p.friction, p.baumgarte, p.slop, p.margin, p.jacobi_omega,
-                   p.plane, p.max_contacts_per_body)
+                   p.plane, p.max_contacts_per_body, p.gyroscopic, p.edge_contacts)
 
 
 def sim_step(scene, nsteps: int = 1, state: Optional[dict] = None, precision: str = "f32",

@@ -33,6 +33,8 @@ typedef struct {
     double gravity[3];
     double restitution, restitution_threshold, friction, baumgarte, slop, margin, jacobi_omega;
     int plane, max_contacts_per_body;
+    int gyroscopic;     /* 1: gyroscopic term of boxes (physics.inc) */
+    int edge_contacts;  /* 1: box-box edge-edge contacts (physics.inc) */
 } oracle_params;
 
 #define REAL float

@@ -876,6 +876,8 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     k.omega = prm->jacobi_omega;
     k.plane = prm->plane;
     k.mcpb = mcpb;
+    k.gyro = prm->gyroscopic;
+    k.edges = prm->edge_contacts;
     d.sc = k;
     d.max_bodies = max_bodies;
     if (o.persistent) {
@@ -945,7 +947,8 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
         for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
             int slot = (int)((env->steps + t) & 1);
             e = launch_sim_items(env->d_desc, env->sim_items[slot], env->E, env->counters, env->sim_grid_sh,
-                                 env->phys_smem, env->max_bodies, force, gate, (cudaStream_t)stream);
+                                 env->phys_smem, env->max_bodies, force, gate, env->sc.edges != 0,
+                                 (cudaStream_t)stream);
         }
     } else if (env->persistent) {
         // one work-list launch per size class, largest class first
@@ -954,10 +957,11 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
             for (size_t k = 0; k < env->sim_classes.size() && e == cudaSuccess; k++) {
                 const vuda_env::SimClass& cl = env->sim_classes[k];
                 int* counter = env->counters + 2 + k;
+                const bool ed = env->sc.edges != 0;
                 e = cl.wide ? wide::launch_sim_items(env->d_desc, cl.items[slot], cl.nitems, counter, cl.grid, cl.smem,
-                                                     cl.max_bodies, force, SmGate{nullptr, 0}, (cudaStream_t)stream)
+                                                     cl.max_bodies, force, SmGate{nullptr, 0}, ed, (cudaStream_t)stream)
                             : launch_sim_items(env->d_desc, cl.items[slot], cl.nitems, counter, cl.grid, cl.smem,
-                                               cl.max_bodies, force, SmGate{nullptr, 0}, (cudaStream_t)stream);
+                                               cl.max_bodies, force, SmGate{nullptr, 0}, ed, (cudaStream_t)stream);
             }
         }
     } else {

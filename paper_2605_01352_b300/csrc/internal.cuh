@@ -20,6 +20,8 @@ struct SimConst {
     float g[3];
     float restitution, rest_thr, mu, beta, slop, margin, omega;
     int plane, mcpb;
+    int gyro;                     // gyroscopic term of boxes
+    int edges;                    // box-box edge-edge contacts
 };
 
 // Scratch of the tiled render path (tiled.cu), per camera c of env e with
@@ -154,7 +156,7 @@ constexpr int kCamWords = 13;
        over one batch. */                                                                                     \
     cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid, \
                                  int smem_per_env, int max_bodies, const float* force, SmGate gate,           \
-                                 cudaStream_t stream);                                                        \
+                                 bool edges, cudaStream_t stream); /* edges: a listed batch has edge contacts */\
     int sim_ctas_per_sm(int smem_per_env);                                                                    \
     CtaFootprint sim_list_footprint(int smem_per_env);                                                        \
     int phys_smem_bytes_default(int max_bodies, int mcpb);                                                    \

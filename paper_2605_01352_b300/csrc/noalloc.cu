@@ -151,6 +151,8 @@ extern "C" vuda_status vuda_sim_step_noalloc(int32_t num_envs, int32_t num_bodie
     k.omega = prm->jacobi_omega;
     k.plane = prm->plane;
     k.mcpb = prm->max_contacts_per_body;
+    k.gyro = prm->gyroscopic;
+    k.edges = prm->edge_contacts;
     int smem = smem_per_env > 0 ? smem_per_env : phys_smem_bytes_default(max_bodies, k.mcpb);
     ce = launch_sim(d, k, nsteps, force, 0, smem, max_bodies, s);
     if (ce != cudaSuccess) {

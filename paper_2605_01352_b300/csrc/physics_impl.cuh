@@ -211,6 +211,148 @@ __device__ __forceinline__ bool corner_in_box(const Bodies& B, int a, int b, int
 
 __device__ __forceinline__ bool is_box(const Bodies& B, int i) { return B.TYPE(i) == kShapeBox; }
 
+__device__ __forceinline__ f3 rcol(const Bodies& B, int i, int k) { return f3{B.Rm(k, i), B.Rm(3 + k, i), B.Rm(6 + k, i)}; }
+
+// Edge-edge contact of boxes a (the pair's A) and b (B): the separating-
+// axis test of two oriented boxes in the formulation of Gottschalk, Lin and
+// Manocha (OBBTree, 1996), over C_kl = a_k . b_l, t = p_a - p_b, t_k = t . a_k
+// and u_l = t . b_l: A's face k: |t_k| - (h_a,k + sum_m h_b,m |C_km|); B's
+// face l: |u_l| - (sum_m h_a,m |C_ml| + h_b,l); edge a_k x b_l ((k, k1, k2),
+// (l, l1, l2) cyclic): (|t_k2 C_k1,l - t_k1 C_k2,l| - (h_a,k1 |C_k2,l| +
+// h_a,k2 |C_k1,l|) - (h_b,l1 |C_k,l2| + h_b,l2 |C_k,l1|)) / sqrt(1 - C_kl^2),
+// edges with 1 - C_kl^2 <= 1e-6 skipped.  The greatest separation wins (the
+// first on ties; an edge axis must beat the best so far by more than 1e-5 m,
+// near ties with a face go to the face).  An edge axis with a separation
+// below the margin gives one contact: normal +-(a_k x b_l) normalised, from B
+// to A; distance the separation; point midway between the closest points of
+// A's edge along a_k furthest towards B and B's edge along b_l furthest
+// towards A (segment closest points: s clamped, t from s and clamped, then s
+// from t and clamped if t was clamped).
+__device__ __noinline__ bool box_edge_edge(const Bodies& B, int a, int b, float margin, f3& nout, f3& pt,
+                                           float& d) {
+    const f3 dp = sub3(ldpos(B, a), ldpos(B, b));
+    float Cm[3][3], AC[3][3], ta[3], tb[3];
+#pragma unroll 1
+    for (int k = 0; k < 3; k++) {
+        ta[k] = dot3(dp, rcol(B, a, k));
+        tb[k] = dot3(dp, rcol(B, b, k));
+#pragma unroll 1
+        for (int l = 0; l < 3; l++) {
+            Cm[k][l] = dot3(rcol(B, a, k), rcol(B, b, l));
+            AC[k][l] = fabsf(Cm[k][l]);
+        }
+    }
+    const float ha[3] = {B.D(0, a), B.D(1, a), B.D(2, a)};
+    const float hb[3] = {B.D(0, b), B.D(1, b), B.D(2, b)};
+    float best = 0.0f;
+    int bq = -1;
+    // a face axis separating the boxes by the margin or more decides the
+    // test (the winning separation can only be larger): skip the edge axes
+    float face = -3.0e38f;
+#pragma unroll 1
+    for (int k = 0; k < 3; k++) {
+        face = fmaxf(face, fabsf(ta[k]) - (ha[k] + ((hb[0] * AC[k][0] + hb[1] * AC[k][1]) + hb[2] * AC[k][2])));
+        face = fmaxf(face, fabsf(tb[k]) - (((ha[0] * AC[0][k] + ha[1] * AC[1][k]) + ha[2] * AC[2][k]) + hb[k]));
+    }
+    if (!(face < margin)) return false;
+#pragma unroll 1
+    for (int q = 0; q < 15; q++) {
+        float sep;
+        if (q < 3) {
+            const int k = q;
+            sep = fabsf(ta[k]) - (ha[k] + ((hb[0] * AC[k][0] + hb[1] * AC[k][1]) + hb[2] * AC[k][2]));
+        } else if (q < 6) {
+            const int l = q - 3;
+            sep = fabsf(tb[l]) - (((ha[0] * AC[0][l] + ha[1] * AC[1][l]) + ha[2] * AC[2][l]) + hb[l]);
+        } else {
+            const int k = (q - 6) / 3, l = (q - 6) % 3;
+            const int k1 = (k + 1) % 3, k2 = (k + 2) % 3, l1 = (l + 1) % 3, l2 = (l + 2) % 3;
+            const float len2 = 1.0f - Cm[k][l] * Cm[k][l];
+            if (!(len2 > 1e-6f)) continue;
+            const float tl = fabsf(ta[k2] * Cm[k1][l] - ta[k1] * Cm[k2][l]);
+            const float ra = ha[k1] * AC[k2][l] + ha[k2] * AC[k1][l];
+            const float rb = hb[l1] * AC[k][l2] + hb[l2] * AC[k][l1];
+            sep = ((tl - ra) - rb) / sqrtf(len2);
+        }
+        if (bq < 0 || sep > best + (q < 6 ? 0.0f : 1e-5f)) {
+            best = sep;
+            bq = q;
+        }
+    }
+    if (bq < 6 || !(best < margin)) return false;
+    const int k = (bq - 6) / 3, l = (bq - 6) % 3;
+    f3 bu;
+    {
+        const f3 c = cross3(rcol(B, a, k), rcol(B, b, l));
+        const float len = sqrtf(dot3(c, c));
+        bu = f3{c.x / len, c.y / len, c.z / len};
+    }
+    const float sg = dot3(dp, bu) >= 0.0f ? 1.0f : -1.0f;
+    const f3 n{sg * bu.x, sg * bu.y, sg * bu.z};
+    f3 cA = ldpos(B, a), cB = ldpos(B, b);
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        const f3 am = rcol(B, a, m), bm = rcol(B, b, m);
+        if (m != k) {
+            const float s1 = dot3(n, am) > 0.0f ? -B.D(m, a) : B.D(m, a);
+            cA = f3{cA.x + s1 * am.x, cA.y + s1 * am.y, cA.z + s1 * am.z};
+        }
+        if (m != l) {
+            const float s2 = dot3(n, bm) > 0.0f ? B.D(m, b) : -B.D(m, b);
+            cB = f3{cB.x + s2 * bm.x, cB.y + s2 * bm.y, cB.z + s2 * bm.z};
+        }
+    }
+    const f3 ea = rcol(B, a, k), eb = rcol(B, b, l);
+    const f3 r = sub3(cA, cB);
+    const float bb = dot3(ea, eb), cc = dot3(ea, r), ff = dot3(eb, r);
+    const float den = 1.0f - bb * bb;
+    const float hak = B.D(k, a), hbl = B.D(l, b);
+    float sA = (bb * ff - cc) / den;
+    sA = sA < -hak ? -hak : (sA > hak ? hak : sA);
+    float tB = ff + sA * bb;
+    if (tB < -hbl || tB > hbl) {
+        tB = tB < -hbl ? -hbl : hbl;
+        sA = tB * bb - cc;
+        sA = sA < -hak ? -hak : (sA > hak ? hak : sA);
+    }
+    pt = f3{0.5f * ((cA.x + sA * ea.x) + (cB.x + tB * eb.x)), 0.5f * ((cA.y + sA * ea.y) + (cB.y + tB * eb.y)),
+            0.5f * ((cA.z + sA * ea.z) + (cB.z + tB * eb.z))};
+    nout = n;
+    d = best;
+    return true;
+}
+
+// Gyroscopic term of a box: the torque-free Euler equations I dw/dt =
+// -w x I w in the body frame, one implicit step by one Newton iteration
+// from the current angular velocity (E. Catto, "Numerical Methods", GDC
+// 2015): f = h w x (I w), J = I + h (skew(w) I - skew(I w)), D = -J^-1 f
+// (adjugate and determinant), and the world angular velocity gains R D.
+__device__ __forceinline__ void gyroscopic(const Bodies& S, int i, const float* R, float ib0, float ib1, float ib2,
+                                        float h) {
+    const float wx = S.W(0, i), wy = S.W(1, i), wz = S.W(2, i);
+    // w = R^T w_world
+    const float w0 = (R[0] * wx + R[3] * wy) + R[6] * wz;
+    const float w1 = (R[1] * wx + R[4] * wy) + R[7] * wz;
+    const float w2 = (R[2] * wx + R[5] * wy) + R[8] * wz;
+    const float I0 = 1.0f / ib0, I1 = 1.0f / ib1, I2 = 1.0f / ib2;
+    const float L0 = I0 * w0, L1 = I1 * w1, L2 = I2 * w2;
+    const float f0 = h * (w1 * L2 - w2 * L1), f1 = h * (w2 * L0 - w0 * L2), f2 = h * (w0 * L1 - w1 * L0);
+    const float J00 = I0, J11 = I1, J22 = I2;
+    const float J01 = h * (w2 * (I2 - I1)), J02 = h * (w1 * (I2 - I1));
+    const float J10 = h * (w2 * (I0 - I2)), J12 = h * (w0 * (I0 - I2));
+    const float J20 = h * (w1 * (I1 - I0)), J21 = h * (w0 * (I1 - I0));
+    const float A00 = J11 * J22 - J12 * J21, A01 = J02 * J21 - J01 * J22, A02 = J01 * J12 - J02 * J11;
+    const float A10 = J12 * J20 - J10 * J22, A11 = J00 * J22 - J02 * J20, A12 = J02 * J10 - J00 * J12;
+    const float A20 = J10 * J21 - J11 * J20, A21 = J01 * J20 - J00 * J21, A22 = J00 * J11 - J01 * J10;
+    const float det = (J00 * A00 + J01 * A10) + J02 * A20;
+    const float D0 = -(((A00 * f0 + A01 * f1) + A02 * f2) / det);
+    const float D1 = -(((A10 * f0 + A11 * f1) + A12 * f2) / det);
+    const float D2 = -(((A20 * f0 + A21 * f1) + A22 * f2) / det);
+    S.W(0, i) = wx + ((R[0] * D0 + R[1] * D1) + R[2] * D2);
+    S.W(1, i) = wy + ((R[3] * D0 + R[4] * D1) + R[5] * D2);
+    S.W(2, i) = wz + ((R[6] * D0 + R[7] * D1) + R[8] * D2);
+}
+
 constexpr int kT = VUDA_SIM_THREADS;   // threads per environment (one CTA)
 constexpr int kParts = kT / 32;        // parts of the contact list, one per warp, when building per-body lists
 constexpr int kMinCtas = kT == 128 ? 7 : 2;   // CTAs per SM the register budget is set for
@@ -223,9 +365,28 @@ __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margi
     return d2 < rs * rs;
 }
 
+// Edge tests of the box pairs among passing pairs [w0, w1), one thread
+// each, into slots (2 float4 per pair: normal and distance, point and hit).
+// Out of line: it runs on few threads, and inlined into the pair round it
+// would raise that loop's register pressure.
+__device__ __noinline__ void edge_prepass(const Bodies& S, const int* plist, int w0, int w1, float4* slots,
+                                          float margin) {
+    for (int q = w0 + (int)threadIdx.x; q < w1; q += kT) {
+        const int pr = plist[q];
+        const int i = pr & 0xffff, j = pr >> 16;
+        if (!(is_box(S, i) && is_box(S, j))) continue;
+        f3 n{0.0f, 0.0f, 0.0f}, pt{0.0f, 0.0f, 0.0f};
+        float d = 0.0f;
+        const bool h = box_edge_edge(S, i, j, margin, n, pt, d);
+        slots[2 * (q - w0)] = make_float4(n.x, n.y, n.z, d);
+        slots[2 * (q - w0) + 1] = make_float4(pt.x, pt.y, pt.z, h ? 1.0f : 0.0f);
+    }
+}
+
 // One narrow-phase test of pair (i, j): sub 0 for sphere-sphere and
 // sphere-box; for box-box sub 0..7 tests A's corner sub inside B and
-// sub 8..15 tests B's corner sub-8 inside A.
+// sub 8..15 tests B's corner sub-8 inside A (sub 16, the crossing edges,
+// is computed before the item pass).
 __device__ __forceinline__ bool pair_test(const Bodies& B, int i, int j, int sub, float margin, f3& n, f3& pt, float& d) {
     bool bi = is_box(B, i), bj = is_box(B, j);
     if (!bi && !bj) {
@@ -581,6 +742,9 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
 
 }
 
+// kEdges: the variant with box-box edge-edge contacts (sc.edges decides at
+// run time; without them the code is left out, and its register pressure).
+template <bool kEdges>
 __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, const float* __restrict__ force, int slot0,
                                      int smem_per_env, int NB) {
     const SimConst& sc = b.sc;
@@ -611,6 +775,10 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     unsigned short* ptab = reinterpret_cast<unsigned short*>(ip); ip += 4 * NB;   // [8 NB] plane items
     unsigned short* lists = reinterpret_cast<unsigned short*>(ip);
     const size_t fixed = phys_fixed_bytes(NB, cmax_nb);
+    // while contacts are generated the list area (2 cmax_nb u16) holds the
+    // edge-test results of a round's first passing pairs, 32 bytes each
+    float4* edge_slots = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(lists) + 15) & ~(uintptr_t)15);
+    const int nedge_slots = (int)((4 * (size_t)cmax_nb - 12) / 32);
     Contacts C;
     C.s = reinterpret_cast<float*>(smem + fixed);
     int capS = (int)((smem_per_env - (long)fixed) / (kCS * 4));
@@ -658,6 +826,8 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     bool ovf = false;
     int nc = 0;
     const float h = sc.h;
+    const bool edges = kEdges && sc.edges;
+    const int kBoxItems = edges ? 17 : 16;   // narrow-phase items of a box-box pair
     const int npairs = N * (N - 1) / 2;
     const f3 up{0.0f, 0.0f, 1.0f};
     for (int step = 0; step < nsteps; step++) {
@@ -684,6 +854,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                 float ib0 = S.II(0, i), ib1 = S.II(1, i), ib2 = S.II(2, i);
 #pragma unroll
                 for (int k = 0; k < 9; k++) S.Rm(k, i) = R[k];
+                if (sc.gyro && S.TYPE(i) == kShapeBox) gyroscopic(S, i, R, ib0, ib1, ib2, h);
 #pragma unroll
                 for (int r = 0; r < 3; r++)
 #pragma unroll
@@ -744,7 +915,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                             if (broad(S, i, j, sc.margin)) {
                                 passmask |= 1u << r;
                                 npass++;
-                                nsub += (is_box(S, i) && is_box(S, j)) ? 16 : 1;
+                                nsub += (is_box(S, i) && is_box(S, j)) ? kBoxItems : 1;
                             }
                             if (++j == N) { i++; j = i + 1; }
                         }
@@ -762,13 +933,21 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                                 plist[o] = i | (j << 16);
                                 pitem[o] = (unsigned short)it;
                                 o++;
-                                it += (is_box(S, i) && is_box(S, j)) ? 16 : 1;
+                                it += (is_box(S, i) && is_box(S, j)) ? kBoxItems : 1;
                             }
                             if (++j == N) { i++; j = i + 1; }
                         }
                     }
                 }
                 __syncthreads();
+                if (edges) {
+                    // the edge tests of the round's first box pairs, one thread
+                    // each, into the per-body list scratch (unused until the
+                    // solve); the item pass reads them (pairs beyond the slots,
+                    // in crowded rounds only, are tested by their item)
+                    edge_prepass(S, plist, 0, min(np, nedge_slots), edge_slots, sc.margin);
+                    __syncthreads();
+                }
                 for (int u0 = 0; u0 < nitems; u0 += kT) {
                     int u = u0 + tid;
                     bool hit = false;
@@ -784,7 +963,18 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                         int pr = plist[lo];
                         i = pr & 0xffff;
                         j = pr >> 16;
-                        hit = pair_test(S, i, j, u - pitem[lo], sc.margin, n, pt, d);
+                        const int sub = u - pitem[lo];
+                        if (kEdges && sub == 16 && lo < nedge_slots) {   // a box pair's edge test, computed above
+                            const float4 e0 = edge_slots[2 * lo], e1 = edge_slots[2 * lo + 1];
+                            n = f3{e0.x, e0.y, e0.z};
+                            d = e0.w;
+                            pt = f3{e1.x, e1.y, e1.z};
+                            hit = e1.w != 0.0f;
+                        } else if (kEdges && sub == 16) {
+                            hit = box_edge_edge(S, i, j, sc.margin, n, pt, d);
+                        } else {
+                            hit = pair_test(S, i, j, sub, sc.margin, n, pt, d);
+                        }
                     }
                     int t2;
                     int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
@@ -857,6 +1047,7 @@ __device__ __forceinline__ void load_desc(DevBatch& dst, const DevBatch& src) {
 }
 
 // Single batch: CTA e steps environment e.
+template <bool kEdges>
 __global__ void __launch_bounds__(kT, kMinCtas) sim_kernel(DevBatch b0, SimConst sc0, int nsteps,
                                                     const float* __restrict__ force, int slot0, int smem_per_env,
                                                     int NB) {
@@ -865,11 +1056,12 @@ __global__ void __launch_bounds__(kT, kMinCtas) sim_kernel(DevBatch b0, SimConst
     __syncthreads();
     if (threadIdx.x == 0) sb.sc = sc0;
     __syncthreads();
-    sim_env(sb, blockIdx.x, nsteps, force, slot0, smem_per_env, NB);
+    sim_env<kEdges>(sb, blockIdx.x, nsteps, force, slot0, smem_per_env, NB);
 }
 
 // Work list over several batches: persistent CTAs pull (batch, environment,
 // pose slot) items from an atomic counter; one step each.
+template <bool kEdges>
 __global__ void __launch_bounds__(kT, kMinCtas) sim_list_kernel(const DevBatch* __restrict__ descs,
                                                          const int2* __restrict__ items, int nitems, int* counter,
                                                          const float* __restrict__ force, int smem_per_env, int NB,
@@ -887,7 +1079,7 @@ __global__ void __launch_bounds__(kT, kMinCtas) sim_list_kernel(const DevBatch* 
         const int2 it = items[item];
         load_desc(sb, descs[it.x & kItemDescMask]);
         __syncthreads();
-        sim_env(sb, it.y, 1, force, (it.x >> 24) & 1, smem_per_env, NB);
+        sim_env<kEdges>(sb, it.y, 1, force, (it.x >> 24) & 1, smem_per_env, NB);
         __syncthreads();  // everyone is done with sb and s_item
     }
     if (threadIdx.x == 0) sm_gate_release(gate, s_gate);
@@ -920,30 +1112,48 @@ int phys_smem_bytes_default(int max_bodies, int mcpb) {
 
 int sim_ctas_per_sm(int smem_per_env) {
     int n = 0;
-    cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
-    cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_list_kernel, kT, smem_per_env) != cudaSuccess) n = 1;
+    // both variants have the same launch bounds (registers) and shared memory
+    cudaFuncSetAttribute(sim_list_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    cudaFuncSetAttribute(sim_list_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_list_kernel<false>, kT, smem_per_env) != cudaSuccess)
+        n = 1;
     return n > 0 ? n : 1;
 }
 
 CtaFootprint sim_list_footprint(int smem_per_env) {
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, sim_list_kernel) != cudaSuccess) return CtaFootprint{kT, 255, 227 * 1024};
-    return CtaFootprint{kT, fa.numRegs, (int)fa.sharedSizeBytes + smem_per_env};
+    cudaFuncAttributes fe{};
+    if (cudaFuncGetAttributes(&fa, sim_list_kernel<false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fe, sim_list_kernel<true>) != cudaSuccess)
+        return CtaFootprint{kT, 255, 227 * 1024};
+    return CtaFootprint{kT, max(fa.numRegs, fe.numRegs),
+                        (int)max(fa.sharedSizeBytes, fe.sharedSizeBytes) + smem_per_env};
+}
+
+template <class K>
+static cudaError_t prepare(K kernel, int smem_per_env) {
+    // set on every launch: the attribute is tracked per context and the
+    // kernel may be launched into different (green) contexts
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
-                             int smem_per_env, int max_bodies, const float* force, SmGate gate, cudaStream_t stream) {
+                             int smem_per_env, int max_bodies, const float* force, SmGate gate, bool edges,
+                             cudaStream_t stream) {
     if (nitems == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sim_list_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = edges ? prepare(sim_list_kernel<true>, smem_per_env) : prepare(sim_list_kernel<false>, smem_per_env);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    sim_list_kernel<<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force, smem_per_env,
-                                                        max_bodies, gate);
+    if (edges)
+        sim_list_kernel<true><<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force, smem_per_env,
+                                                                  max_bodies, gate);
+    else
+        sim_list_kernel<false><<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force,
+                                                                   smem_per_env, max_bodies, gate);
     return cudaGetLastError();
 }
 
@@ -952,13 +1162,12 @@ cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const 
     if (b.E == 0 || nsteps == 0) return cudaSuccess;
     size_t fixed = phys_fixed_bytes(max_bodies, sc.mcpb * max_bodies);
     if ((size_t)smem_per_env < fixed) smem_per_env = (int)fixed;
-    // set on every launch: the attribute is tracked per context and the
-    // kernel may be launched into different (green) contexts
-    cudaError_t e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    cudaError_t e = sc.edges ? prepare(sim_kernel<true>, smem_per_env) : prepare(sim_kernel<false>, smem_per_env);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    sim_kernel<<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
+    if (sc.edges)
+        sim_kernel<true><<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
+    else
+        sim_kernel<false><<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
     return cudaGetLastError();
 }
 

@@ -185,6 +185,10 @@ class SimParams:
     jacobi_omega: float = 1.0
     plane: int = 1  # 1: static ground plane z = 0 present
     max_contacts_per_body: int = 16
+    # options beyond the configured workloads' physics (off there: no
+    # gyroscopic term, box-box contacts from corners only)
+    gyroscopic: int = 0  # 1: gyroscopic term of boxes (implicit, one Newton step)
+    edge_contacts: int = 0  # 1: box-box edge-edge contacts (separating-axis test)
 
 
 @dataclasses.dataclass

@@ -110,6 +110,46 @@ def test_physics_with_forces(V, orc, persistent):
     _physics_horizon(V, orc, sc, steps=5, force=f, persistent=persistent)
 
 
+def test_physics_edge_contacts_and_gyroscopic_term(V, orc):
+    """Box-box edge-edge contacts (crossed beams touching edge to edge, one
+    in penetration) and the gyroscopic term (boxes spinning near their
+    intermediate axis, in flight) through a 10-step horizon against the
+    oracle, with identical contact counts."""
+    from scipy.spatial.transform import Rotation
+
+    def wxyz(r):
+        x, y, z, w = r.as_quat()
+        return (w, x, y, z)
+    ra, rb = Rotation.from_euler("x", 45, degrees=True), Rotation.from_euler("zy", [20, 45], degrees=True)
+    bodies = []
+    for k, gap in enumerate((0.004, -0.002, 0.01)):
+        x0 = 0.8 * k - 0.8
+        zA = 0.05 + 0.03 * np.sqrt(2)
+        bodies.append(dict(type="box", h=(0.3, 0.03, 0.03), pos=(x0, 0.0, zA), quat=wxyz(ra)))
+        bodies.append(dict(type="box", h=(0.02, 0.3, 0.02), pos=(x0, 0.0, zA + 0.03 * np.sqrt(2) + gap + 0.02 * np.sqrt(2)),
+                           quat=wxyz(rb)))
+    for k in range(3):
+        bodies.append(dict(type="box", h=(0.02, 0.05, 0.1), pos=(0.5 * k - 0.5, 1.5, 1.5),
+                           angvel=(0.05, 12.0 - k, -0.05), quat=wxyz(Rotation.from_euler("xyz", [10 * k, 5, 0],
+                                                                                            degrees=True))))
+    p = dataclasses.replace(S.SimParams(), gyroscopic=1, edge_contacts=1)
+    sc = S.custom(bodies, envs=3, params=p)
+    c = orc.contacts(sc, 0)
+    assert sum(1 for a, b in zip(c["a"], c["b"]) if b >= 0) >= 3    # the crossing edges
+    _physics_horizon(V, orc, sc, steps=10)
+
+
+def test_physics_piles_with_edge_contacts_and_gyroscopic_term(V, orc):
+    """Settled piles of spheres and randomly oriented boxes with both
+    options on: box pairs in crowded pair rounds (more passing pairs than
+    the edge-test slots) and spinning boxes in contact."""
+    sc = S.cfg2(24)
+    sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, gyroscopic=1, edge_contacts=1))
+    st, _, _ = orc.sim_step(sc, 60)
+    sc = dataclasses.replace(sc, **{k: st[k] for k in ("pos", "quat", "vel", "angvel")})
+    _physics_horizon(V, orc, sc, steps=10)
+
+
 def test_physics_contact_overflow_matches(V, orc):
     """A capacity of 1 contact per body truncates identically on both sides."""
     sc = S.cfg2(8)

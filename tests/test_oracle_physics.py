@@ -431,3 +431,202 @@ def test_head_on_restitution(orc, speed, bounces):
     assert st["vel"][0, 0] + st["vel"][0, 1] == pytest.approx(0.0, abs=1e-12)
     np.testing.assert_array_equal(st["angvel"], 0.0)
     np.testing.assert_array_equal(st["vel"][1:], 0.0)
+
+
+def _body_omega(st, i=0):
+    """Body-frame angular velocity R^T w (independent rotation: scipy)."""
+    R = _rotmat(st["quat"][:, i].astype(np.float64))
+    return R.T @ st["angvel"][:, i].astype(np.float64)
+
+
+def _world_momentum(sc, st, i=0):
+    """World angular momentum R I R^T w of body i (I from the scene's inverse inertia)."""
+    R = _rotmat(st["quat"][:, i].astype(np.float64))
+    I = np.diag(1.0 / sc.inv_inertia[:, i].astype(np.float64))
+    return R @ I @ R.T @ st["angvel"][:, i].astype(np.float64)
+
+
+def _spinning_box(w_body, gyro=1):
+    p = dataclasses.replace(S.SimParams(), gravity=(0.0, 0.0, 0.0), plane=0, gyroscopic=gyro)
+    # half extents 0.02, 0.05, 0.1: principal moments I0 > I1 > I2 (y intermediate)
+    return S.custom([dict(type="box", h=(0.02, 0.05, 0.1), pos=(0.0, 0.0, 1.0), angvel=tuple(w_body))], params=p)
+
+
+def test_gyroscopic_intermediate_axis_flips(orc):
+    """Torque-free spin about the intermediate principal axis is unstable
+    (the tennis-racket theorem): with the gyroscopic term the body-frame spin
+    about y reverses within a few seconds while the world angular momentum
+    stays nearly constant (implicit Euler dissipates slowly); without the
+    term the angular velocity never changes."""
+    sc = _spinning_box((0.01, 10.0, 0.01))
+    I = 1.0 / sc.inv_inertia[:, 0].astype(np.float64)
+    assert I[0] > I[1] > I[2]
+    s0 = {k: v.astype(np.float64) for k, v in sc.state().items()}
+    L0 = _world_momentum(sc, s0)
+    st, seen_flip = s0, False
+    for _ in range(60):                       # 60 x 10 steps = 2.5 s
+        st, _, _ = orc.sim_step(sc, 10, state=st, precision="f64")
+        wb = _body_omega(st)
+        seen_flip |= wb[1] < -5.0
+        L = _world_momentum(sc, st)
+        assert np.linalg.norm(L - L0) < 0.02 * np.linalg.norm(L0)
+    assert seen_flip
+    off = _spinning_box((0.01, 10.0, 0.01), gyro=0)
+    st_off, _, _ = orc.sim_step(off, 600, state={k: v.astype(np.float64) for k, v in off.state().items()},
+                                precision="f64")
+    np.testing.assert_allclose(st_off["angvel"][:, 0], (0.01, 10.0, 0.01), atol=1e-12)
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_gyroscopic_major_and_minor_axes_are_stable(orc, axis):
+    """Spin about the axis of the largest or the smallest moment stays close
+    to that axis in the body frame (both are stable)."""
+    w = [0.01, 0.01, 0.01]
+    w[axis] = 10.0
+    sc = _spinning_box(w)
+    st = {k: v.astype(np.float64) for k, v in sc.state().items()}
+    for _ in range(30):
+        st, _, _ = orc.sim_step(sc, 20, state=st, precision="f64")
+        wb = _body_omega(st)
+        assert wb[axis] > 9.8
+        assert np.abs(np.delete(wb, axis)).max() < 0.5
+
+
+def test_gyroscopic_step_is_first_order_euler_equations(orc):
+    """One substep changes the body-frame angular velocity by
+    -h I^-1 (w x I w) to first order in h (the implicit step and the explicit
+    one differ by O(h^2 |w|^2))."""
+    w = np.array([3.0, -2.0, 5.0])
+    sc = _spinning_box(tuple(w))
+    sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, substeps=1, dt=1e-4))
+    st, _, _ = orc.sim_step(sc, 1, state={k: v.astype(np.float64) for k, v in sc.state().items()},
+                            precision="f64")
+    I = 1.0 / sc.inv_inertia[:, 0].astype(np.float64)
+    h = 1e-4
+    explicit = -h * np.cross(w, I * w) / I
+    got = st["angvel"][:, 0] - w        # identity orientation at the start: body = world
+    np.testing.assert_allclose(got, explicit, rtol=5e-3, atol=1e-12)
+    assert np.abs(explicit).max() > 1e-3
+
+
+def test_gyroscopic_step_is_one_newton_step_of_implicit_euler(orc):
+    """A large step (h |w| ~ 0.1), where the implicit and explicit updates
+    differ clearly: the change of the body-frame angular velocity is the
+    Newton step D = -J^-1 f of f(x) = I (x - w) + h x x I x at x = w, with
+    J = I + h (skew(w) I - skew(I w)) assembled from skew matrices and
+    solved by numpy."""
+    w = np.array([4.0, -6.0, 9.0])
+    sc = _spinning_box(tuple(w))
+    h = 0.01
+    sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, substeps=1, dt=h))
+    st, _, _ = orc.sim_step(sc, 1, state={k: v.astype(np.float64) for k, v in sc.state().items()},
+                            precision="f64")
+    I = np.diag(1.0 / sc.inv_inertia[:, 0].astype(np.float64))
+
+    def skew(a):
+        return np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+
+    f = h * np.cross(w, I @ w)
+    J = I + h * (skew(w) @ I - skew(I @ w))
+    D = -np.linalg.solve(J, f)
+    np.testing.assert_allclose(st["angvel"][:, 0], w + D, rtol=1e-12, atol=1e-12)
+    explicit = -h * np.linalg.solve(I, np.cross(w, I @ w))
+    assert np.abs(D - explicit).max() > 0.05 * np.abs(explicit).max()
+
+
+def _crossed_beams(gap, lower_first=True, yaw=0.0):
+    """Two square beams turned 45 degrees about their long axes (diamond
+    cross-sections): A along x with its top edge at z = 1 + hA sqrt 2,
+    B along y (turned `yaw` about z) with its bottom edge `gap` above it.
+    The two edges cross; no corner of either beam is near the other."""
+    from scipy.spatial.transform import Rotation
+    hA, hB = 0.03, 0.02
+    RA = Rotation.from_euler("x", 45.0, degrees=True)
+    RB = Rotation.from_euler("z", yaw, degrees=True) * Rotation.from_euler("y", 45.0, degrees=True)
+
+    def wxyz(r):
+        x, y, z, w = r.as_quat()
+        return (w, x, y, z)
+
+    zA = 1.0
+    zB = zA + hA * math.sqrt(2) + gap + hB * math.sqrt(2)
+    A = dict(type="box", h=(0.3, hA, hA), pos=(0.0, 0.0, zA), quat=wxyz(RA))
+    B = dict(type="box", h=(hB, 0.3, hB), pos=(0.0, 0.0, zB), quat=wxyz(RB))
+    p = dataclasses.replace(S.SimParams(), plane=0, edge_contacts=1)
+    return S.custom([A, B] if lower_first else [B, A], params=p), zA + hA * math.sqrt(2), zB - hB * math.sqrt(2)
+
+
+@pytest.mark.parametrize("gap", [0.005, -0.003])
+def test_box_edges_crossing_give_one_edge_contact(orc, gap):
+    """Crossed diamond beams touch edge to edge: the only contact is the
+    edge-edge one, with the normal along a_x x b_y = z pointing from B to A
+    (down when A is the lower beam), the distance equal to the gap between
+    the edges (speculative when positive, penetration when negative) and
+    the point midway between them."""
+    sc, top, bottom = _crossed_beams(gap)
+    c = orc.contacts(sc, 0)
+    assert c["count"] == 1 and c["a"][0] == 0 and c["b"][0] == 1
+    np.testing.assert_allclose(c["n"][0], (0.0, 0.0, -1.0), atol=1e-6)
+    assert c["d"][0] == pytest.approx(gap, abs=2e-6)
+    np.testing.assert_allclose(c["p"][0], (0.0, 0.0, 0.5 * (top + bottom)), atol=2e-6)
+    # listed the other way round the normal flips (still from B to A)
+    sc2, _, _ = _crossed_beams(gap, lower_first=False)
+    c2 = orc.contacts(sc2, 0)
+    assert c2["count"] == 1
+    np.testing.assert_allclose(c2["n"][0], (0.0, 0.0, 1.0), atol=1e-6)
+    np.testing.assert_allclose(c2["p"][0], c["p"][0], atol=2e-6)
+    # beyond the margin: no contact
+    sc3, _, _ = _crossed_beams(sc.params.margin + 0.004)
+    assert orc.contacts(sc3, 0)["count"] == 0
+    # without edge contacts the corner tests alone miss the crossing
+    sc4 = dataclasses.replace(sc, params=dataclasses.replace(sc.params, edge_contacts=0))
+    assert orc.contacts(sc4, 0)["count"] == 0
+
+
+def test_box_edge_contact_geometry_at_an_angle(orc):
+    """Beams crossing at 60 degrees (B turned 30 degrees about z): the normal
+    is perpendicular to both edge directions, the contact distance is the
+    distance between the two edge lines (independent closed form: the
+    projection of the offset of two points on the lines onto their common
+    normal), and the point is the midpoint of the common perpendicular."""
+    from scipy.spatial.transform import Rotation
+    sc, _, _ = _crossed_beams(0.004, yaw=30.0)
+    c = orc.contacts(sc, 0)
+    assert c["count"] == 1
+    RA = _rotmat(sc.quat[:, 0].astype(np.float64))
+    RB = _rotmat(sc.quat[:, 1].astype(np.float64))
+    ea, eb = RA[:, 0], RB[:, 1]
+    n = c["n"][0].astype(np.float64)
+    assert abs(n @ ea) < 1e-6 and abs(n @ eb) < 1e-6
+    # points on the two supporting edges (A's top edge, B's bottom edge)
+    hA, hB = sc.shape_dims[:, 0].astype(np.float64), sc.shape_dims[:, 1].astype(np.float64)
+    pA, pB = sc.pos[:, 0].astype(np.float64), sc.pos[:, 1].astype(np.float64)
+    cand_a = [pA + RA @ np.array([0.0, sy * hA[1], sz * hA[2]]) for sy in (-1, 1) for sz in (-1, 1)]
+    cand_b = [pB + RB @ np.array([sx * hB[0], 0.0, sz * hB[2]]) for sx in (-1, 1) for sz in (-1, 1)]
+    qa = max(cand_a, key=lambda v: v[2])
+    qb = min(cand_b, key=lambda v: v[2])
+    m = np.cross(ea, eb)
+    m /= np.linalg.norm(m)
+    dist = abs((qb - qa) @ m)
+    assert c["d"][0] == pytest.approx(dist, abs=2e-6)
+    # the common perpendicular's midpoint
+    A_ = np.array([[ea @ ea, -(ea @ eb)], [ea @ eb, -(eb @ eb)]])
+    s, t = np.linalg.solve(A_, [(qb - qa) @ ea, (qb - qa) @ eb])
+    mid = 0.5 * ((qa + s * ea) + (qb + t * eb))
+    np.testing.assert_allclose(c["p"][0], mid, atol=2e-6)
+
+
+def test_box_edge_contact_clamped_to_the_edge_end(orc):
+    """B's edge passes 1 mm beyond the end of A's edge: A's end corner is
+    within the margin of B (the corner test's contact, first) and the edges
+    still give the greatest separation, so an edge contact follows whose
+    point on A's edge is clamped to its end (x = 0.3) while B's stays where
+    the lines cross (x = 0.301): the contact is midway between the two."""
+    sc, top, bottom = _crossed_beams(0.004)
+    sc.pos[0, 1] = 0.301
+    c = orc.contacts(sc, 0)
+    assert c["count"] == 2
+    np.testing.assert_allclose(c["p"][0], (0.3, 0.0, top), atol=2e-6)          # A's corner in B
+    np.testing.assert_allclose(c["p"][1], (0.5 * (0.3 + 0.301), 0.0, 0.5 * (top + bottom)), atol=2e-6)
+    np.testing.assert_allclose(c["n"][1], (0.0, 0.0, -1.0), atol=1e-6)
+    assert c["d"][1] == pytest.approx(0.004, abs=2e-6)
