@@ -418,7 +418,14 @@ vuda_status vuda_raster_screen_tris(const int32_t* xy, const float* z, int32_t n
  * request of every admitted job into one launch per phase, and pipelines the
  * launches (the sim phase of the next batch overlaps the render phase of the
  * current one), so requests arriving while others run join the next batch.
- * A job's results are the same alone and in any mix. */
+ * A job's results are the same alone and in any mix.
+ * Host-side fault injection (read when the server is created; no GPU fault
+ * is made): VUDA_FAULT_REJECT_JOB=<job id> refuses that job's admission (its
+ * requests complete with VUDA_ERR_INVALID); VUDA_FAULT_OOM_JOB=<job id>
+ * fails its admission as if its device memory could not be allocated
+ * (VUDA_ERR_OOM); VUDA_FAULT_STALL_MS=<ms> and VUDA_FAULT_STALL_EVERY=<n>
+ * stall the batching worker for ms before every n-th launch.  Job ids count
+ * from 1 in the order jobs are added. */
 typedef struct vuda_server* vuda_server_t;
 typedef struct {
     int32_t device;

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -186,6 +187,15 @@ struct vuda_server {
     Buf<int4> ren_items[kRing];
     Buf<int2> shade_items[kRing];
     Buf<TiledJob> tile_jobs[kRing];   // jobs on the tiled path: their device items and list positions
+    // host-side fault injection, read from the environment at creation (no
+    // GPU fault is ever made): VUDA_FAULT_REJECT_JOB=<id> refuses that job's
+    // admission (its requests fail with VUDA_ERR_INVALID); VUDA_FAULT_OOM_JOB
+    // =<id> makes its admission fail as if its device memory could not be
+    // allocated (VUDA_ERR_OOM, nothing allocated); VUDA_FAULT_STALL_MS=<ms>
+    // with VUDA_FAULT_STALL_EVERY=<n> (default 1) stalls the worker that
+    // builds and launches batches for ms before every n-th launch
+    int64_t fault_reject_job = -1, fault_oom_job = -1;
+    int fault_stall_ms = 0, fault_stall_every = 1;
 };
 
 namespace {
@@ -212,7 +222,13 @@ void admit(vuda_server* s) {
         vuda_env_opts eo{};
         eo.device = s->o.device;
         eo.render_path = VUDA_RENDER_AUTO;   // tiled where its scratch fits, else the band work list
-        vuda_status st = vuda_env_create(&j->scene->view, &j->params, &eo, &j->env);
+        vuda_status st;
+        if (j->id == s->fault_reject_job)
+            st = VUDA_ERR_INVALID;           // injected: admission refused
+        else if (j->id == s->fault_oom_job)
+            st = VUDA_ERR_OOM;               // injected: the job's allocation failed
+        else
+            st = vuda_env_create(&j->scene->view, &j->params, &eo, &j->env);
         if (st == VUDA_OK) {
             size_t P = (size_t)j->env->P;
             size_t fb = P * 3 + P * 4 + P * 4 + 256;
@@ -471,6 +487,13 @@ void worker_main(vuda_server* s) {
             }
         }
         if (!batch.empty()) {
+            if (s->fault_stall_ms > 0 && (s->iterations + 1) % s->fault_stall_every == 0) {
+                // injected: the producer of launches stalls (the lock is
+                // released: clients keep submitting and polling)
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::milliseconds(s->fault_stall_ms));
+                lk.lock();
+            }
             if (!launch_iteration(s, batch)) break;
             s->iterations++;
             s->batched += (int64_t)batch.size();
@@ -523,6 +546,14 @@ vuda_status vuda_serve_create(const vuda_serve_opts* opts, vuda_server_t* out) {
         return VUDA_ERR_CUDA;
     }
     for (int k = o.max_jobs - 1; k >= 0; k--) s->free_desc.push_back(k);
+    auto env_int = [](const char* name, long long dflt) {
+        const char* v = std::getenv(name);
+        return v && *v ? std::atoll(v) : dflt;
+    };
+    s->fault_reject_job = env_int("VUDA_FAULT_REJECT_JOB", -1);
+    s->fault_oom_job = env_int("VUDA_FAULT_OOM_JOB", -1);
+    s->fault_stall_ms = (int)std::max(0LL, env_int("VUDA_FAULT_STALL_MS", 0));
+    s->fault_stall_every = (int)std::max(1LL, env_int("VUDA_FAULT_STALL_EVERY", 1));
     s->worker = std::thread(worker_main, s);
     *out = s;
     return VUDA_OK;

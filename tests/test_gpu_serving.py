@@ -138,3 +138,93 @@ def test_errors_and_cancellation(V):
     srv.submit(j1)
     assert srv.wait_all(1)[0]["status"] == 0
     srv.close()
+
+
+def _faulted_run(V, monkeypatch, env, jobs, counts, cancel=None):
+    """Jobs run together under an injected host-side fault (environment
+    variables read when the server is created); returns each job's
+    (statuses, state, frame) and the server's job ids."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, str(v))
+    srv = V.Server(max_inflight=2)
+    for k in env:
+        monkeypatch.delenv(k)
+    ids = {k: srv.add_job(sc) for k, sc in jobs.items()}
+    assert sorted(ids.values()) == list(range(1, len(jobs) + 1))
+    order = [k for k, n in counts.items() for _ in range(n)]
+    random.Random(8).shuffle(order)
+    reqs = {k: [] for k in jobs}
+    refused = {k: 0 for k in jobs}
+    for k in order:
+        try:
+            reqs[k].append(srv.submit(ids[k]))
+        except V.VudaError as ex:         # the job already failed its admission
+            assert ex.status == V.ERR_INVALID
+            refused[k] += 1
+    if cancel:
+        srv.remove_job(ids[cancel])       # launched requests finish, queued ones are cancelled
+    total = sum(len(r) for r in reqs.values())
+    res = srv.wait_all(total)
+    by_job = {k: sorted((r for r in res if r["job"] == ids[k]), key=lambda r: r["req_id"]) for k in jobs}
+    out = {}
+    for k in jobs:
+        st = [r["status"] for r in by_job[k]] + ["refused"] * refused[k]
+        if st and all(x == 0 for x in st):
+            out[k] = (st, srv.job_env(ids[k]).get_state(), srv.read_frame(ids[k]))
+        else:
+            out[k] = (st, None, None)
+    srv.close()
+    return out
+
+
+def _same_as_alone(V, sc, n, got):
+    st_a, fr_a = _alone(V, sc, n)
+    for f in st_a:
+        np.testing.assert_array_equal(got[1][f], st_a[f])
+    for x, y in zip(got[2], fr_a):
+        np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("fault,status", [("VUDA_FAULT_REJECT_JOB", 1), ("VUDA_FAULT_OOM_JOB", 2)])
+def test_fault_at_admission_leaves_the_other_jobs_unchanged(V, monkeypatch, fault, status):
+    """The second job's admission is refused (or fails as out of memory):
+    its requests complete with that status (or, once the job has failed, are
+    refused at submission), and the other jobs' states and frames are
+    bit-identical to running alone."""
+    jobs = {"A": S.cfg2(6), "B": S.cfg1(4), "C": S.cfg4(4)}
+    counts = {"A": 4, "B": 3, "C": 5}
+    got = _faulted_run(V, monkeypatch, {fault: 2}, jobs, counts)
+    # submitted before the admission failed: that status; after: refused at submit
+    assert len(got["B"][0]) == 3 and set(got["B"][0]) <= {status, "refused"}
+    for k in ("A", "C"):
+        assert got[k][0] == [0] * counts[k]
+        _same_as_alone(V, jobs[k], counts[k], got[k])
+
+
+def test_fault_stalled_producer_leaves_results_unchanged(V, monkeypatch):
+    """The batching worker stalls 4 ms before every second launch: requests
+    pile up and are batched differently, every job's results are still
+    bit-identical to running alone."""
+    jobs = {"A": S.cfg2(6), "B": S.cfg1(4)}
+    counts = {"A": 6, "B": 5}
+    got = _faulted_run(V, monkeypatch, {"VUDA_FAULT_STALL_MS": 4, "VUDA_FAULT_STALL_EVERY": 2}, jobs, counts)
+    for k in jobs:
+        assert got[k][0] == [0] * counts[k]
+        _same_as_alone(V, jobs[k], counts[k], got[k])
+
+
+def test_cancelled_job_mid_batch_leaves_the_other_jobs_unchanged(V, monkeypatch):
+    """A job removed while some of its requests are on the GPU: its queued
+    requests are cancelled (VUDA_ERR_BUSY), the ones already launched
+    complete, and the other jobs' results are bit-identical to running
+    alone."""
+    jobs = {"A": S.cfg2(6), "B": S.cfg2(5, env_base=50), "C": S.cfg1(4)}
+    counts = {"A": 5, "B": 8, "C": 6}
+    got = _faulted_run(V, monkeypatch, {}, jobs, counts, cancel="B")
+    st_b = got["B"][0]
+    assert len(st_b) == counts["B"] and set(st_b) <= {0, 6}
+    assert st_b == sorted(st_b)                 # launched (in order) before cancelled
+    assert 6 in st_b                            # some were still queued
+    for k in ("A", "C"):
+        assert got[k][0] == [0] * counts[k]
+        _same_as_alone(V, jobs[k], counts[k], got[k])
