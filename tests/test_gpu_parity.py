@@ -368,9 +368,11 @@ def test_render_near_plane_clipping_tilings(V, orc, tile, nlim):
         env.close()
 
 
-def test_render_paths_identical_frames_full_size(V):
+def test_render_paths_identical_frames_full_size(V, orc):
     """The band and tiled paths give identical frames, bit for bit, on the
-    1024-environment batch of 128 x 128 cameras (settled piles)."""
+    1024-environment batch of 128 x 128 cameras (settled piles), and
+    sampled environments' frames match the oracle's render of the pose
+    slot they were rendered from."""
     import torch
     sc = S.cfg2()
     out = []
@@ -382,6 +384,7 @@ def test_render_paths_identical_frames_full_size(V):
         torch.cuda.synchronize()
         out.append({k: v.cpu().numpy() for k, v in ring[1].items()})
         out[-1]["flags"] = env.status()[0]
+        _frames_of_gpu_poses(orc, sc, env, ring[1], 1, (0, 333, 1023))
         env.close()
     for k in out[0]:
         np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
