@@ -909,6 +909,9 @@ vuda_status vuda_env_destroy(vuda_env_t env) {
     for (cudaEvent_t e : env->copy_done)
         if (e) cudaEventDestroy(e);
     if (env->own_s) cudaStreamDestroy(env->own_s);
+    for (cudaStream_t s : env->class_s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : env->class_join) cudaEventDestroy(e);
+    if (env->class_fork) cudaEventDestroy(env->class_fork);
     free_env(env);
     delete env;
     return VUDA_OK;
@@ -936,6 +939,45 @@ vuda_status vuda_env_cam_pix_off(vuda_env_t env, int64_t* out) {
     return VUDA_OK;
 }
 
+// Streams (at the caller stream's priority) and fork / join events for the
+// persistent physics' size classes after the first.  False if they cannot
+// be made (the classes then run one after another on the caller's stream).
+static bool prepare_class_streams(vuda_env_t env, vuda_stream_t stream) {
+    int prio = 0;
+    if (cudaStreamGetPriority((cudaStream_t)stream, &prio) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t need = env->sim_classes.size() - 1;
+    if (env->class_s.size() == need && env->class_prio == prio && env->class_fork) return true;
+    // streams and events are not made while the caller's stream is being
+    // captured: the classes then run in order within the graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    for (cudaStream_t s : env->class_s) cudaStreamDestroy(s);
+    env->class_s.clear();
+    if (!env->class_fork && cudaEventCreateWithFlags(&env->class_fork, cudaEventDisableTiming) != cudaSuccess)
+        return false;
+    while (env->class_join.size() < need) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+        env->class_join.push_back(ev);
+    }
+    for (size_t k = 0; k < need; k++) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        env->class_s.push_back(s);
+    }
+    env->class_prio = prio;
+    return true;
+}
+
 vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vuda_stream_t stream) {
     if (!env) return invalid("null env");
     if (nsteps < 0) return invalid("nsteps < 0");
@@ -951,17 +993,33 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
                                  (cudaStream_t)stream);
         }
     } else if (env->persistent) {
-        // one work-list launch per size class, largest class first
+        // one work-list launch per size class, largest class first; the
+        // classes hold different environments, so beyond green partitions
+        // (whose SMs a primary-context stream would leave) they run side by
+        // side: the small classes fill the SMs around the long chains of the
+        // largest environments
+        const size_t ncls = env->sim_classes.size();
+        const bool fork = ncls > 1 && env->cos_mode != VUDA_COSCHED_GREEN && prepare_class_streams(env, stream);
         for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
             int slot = (int)((env->steps + t) & 1);
-            for (size_t k = 0; k < env->sim_classes.size() && e == cudaSuccess; k++) {
+            if (fork) {
+                e = cudaEventRecord(env->class_fork, (cudaStream_t)stream);
+                for (size_t k = 1; k < ncls && e == cudaSuccess; k++)
+                    e = cudaStreamWaitEvent(env->class_s[k - 1], env->class_fork, 0);
+            }
+            for (size_t k = 0; k < ncls && e == cudaSuccess; k++) {
                 const vuda_env::SimClass& cl = env->sim_classes[k];
                 int* counter = env->counters + 2 + k;
                 const bool ed = env->sc.edges != 0;
+                cudaStream_t cs = (fork && k > 0) ? env->class_s[k - 1] : (cudaStream_t)stream;
                 e = cl.wide ? wide::launch_sim_items(env->d_desc, cl.items[slot], cl.nitems, counter, cl.grid, cl.smem,
-                                                     cl.max_bodies, force, SmGate{nullptr, 0}, ed, (cudaStream_t)stream)
+                                                     cl.max_bodies, force, SmGate{nullptr, 0}, ed, cs)
                             : launch_sim_items(env->d_desc, cl.items[slot], cl.nitems, counter, cl.grid, cl.smem,
-                                               cl.max_bodies, force, SmGate{nullptr, 0}, ed, (cudaStream_t)stream);
+                                               cl.max_bodies, force, SmGate{nullptr, 0}, ed, cs);
+            }
+            for (size_t k = 1; fork && k < ncls && e == cudaSuccess; k++) {
+                e = cudaEventRecord(env->class_join[k - 1], env->class_s[k - 1]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, env->class_join[k - 1], 0);
             }
         }
     } else {

@@ -49,6 +49,12 @@ struct vuda_env {
         int nitems = 0, max_bodies = 0, smem = 0, grid = 0, wide = 0;
     };
     std::vector<SimClass> sim_classes;
+    // the size classes after the first run on streams of their own, forked
+    // from and joined back into the sim stream (independent environments)
+    std::vector<cudaStream_t> class_s;
+    std::vector<cudaEvent_t> class_join;
+    cudaEvent_t class_fork = nullptr;
+    int class_prio = 0;
     int4* ren_items[2] = {nullptr, nullptr};      // per pose slot: (0 | slot << 24, cam, y0, 0), largest first
     int2* shade_items[2] = {nullptr, nullptr};
     int nshade = 0;

@@ -177,6 +177,10 @@ struct vuda_server {
     DevBatch* descs = nullptr;
     std::vector<int> free_desc;
     cudaStream_t sim_s = nullptr, ren_s = nullptr;
+    // physics size classes after the first run on streams of their own,
+    // forked from and joined back into sim_s (they hold different jobs)
+    cudaStream_t cls_s[2] = {nullptr, nullptr};
+    cudaEvent_t cls_fork = nullptr, cls_join[2] = {nullptr, nullptr};
     int* counters = nullptr;
     int sms = 0;
     std::deque<Iter> inflight;
@@ -398,14 +402,35 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
     // pose slots are reused two iterations later: wait for that render
     if (no >= 2) e = cudaStreamWaitEvent(s->sim_s, s->ev_done[(no - 2) % vuda_server::kRing], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(si.d, si.h, nsim * sizeof(int2), cudaMemcpyHostToDevice, s->sim_s);
+    // the classes side by side when more than one has work: the small
+    // environments fill the SMs around the long chains of the largest
+    int nbusy = 0;
+    for (int k = 0; k < 3; k++) nbusy += cls[k].n ? 1 : 0;
+    const bool fork = nbusy > 1 && s->cls_s[0] && s->cls_s[1];
+    if (fork && e == cudaSuccess) {
+        e = cudaEventRecord(s->cls_fork, s->sim_s);
+        for (int q = 0; q < 2 && e == cudaSuccess; q++) e = cudaStreamWaitEvent(s->cls_s[q], s->cls_fork, 0);
+    }
+    int lane = 0;   // the stream the next busy class goes to: sim_s, then cls_s[0], cls_s[1]
+    bool used[2] = {false, false};
     for (int k = 0; k < 3 && e == cudaSuccess; k++) {
         if (!cls[k].n) continue;
+        cudaStream_t cs = s->sim_s;
+        if (fork && lane > 0) {
+            cs = s->cls_s[lane - 1];
+            used[lane - 1] = true;
+        }
+        lane++;
         const int2* items = si.d + cls[k].off;
         e = cls[k].wide ? wide::launch_sim_items(s->descs, items, (int)cls[k].n, s->counters + 2 + k, cls[k].grid,
-                                                 cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_edges,
-                                                 s->sim_s)
+                                                 cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_edges, cs)
                         : launch_sim_items(s->descs, items, (int)cls[k].n, s->counters + 2 + k, cls[k].grid,
-                                           cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_edges, s->sim_s);
+                                           cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_edges, cs);
+    }
+    for (int q = 0; q < 2 && fork && e == cudaSuccess; q++) {
+        if (!used[q]) continue;
+        e = cudaEventRecord(s->cls_join[q], s->cls_s[q]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sim_s, s->cls_join[q], 0);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_sim, s->sim_s);
     if (e == cudaSuccess && nren)
@@ -534,6 +559,11 @@ vuda_status vuda_serve_create(const vuda_serve_opts* opts, vuda_server_t* out) {
     if (e == cudaSuccess && o.serialized) s->ren_s = s->sim_s;
     else if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->ren_s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, o.device);
+    for (int q = 0; q < 2 && e == cudaSuccess; q++) {
+        e = cudaStreamCreateWithFlags(&s->cls_s[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->cls_join[q], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->cls_fork, cudaEventDisableTiming);
     for (int k = 0; k < vuda_server::kRing && e == cudaSuccess; k++) {
         e = cudaEventCreateWithFlags(&s->ev_sim[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done[k], cudaEventDisableTiming);
@@ -542,6 +572,17 @@ vuda_status vuda_serve_create(const vuda_serve_opts* opts, vuda_server_t* out) {
         set_error(std::string("serving setup: ") + cudaGetErrorString(e));
         if (s->descs) cudaFree(s->descs);
         if (s->counters) cudaFree(s->counters);
+        if (s->ren_s && s->ren_s != s->sim_s) cudaStreamDestroy(s->ren_s);
+        if (s->sim_s) cudaStreamDestroy(s->sim_s);
+        for (int k = 0; k < vuda_server::kRing; k++) {
+            if (s->ev_sim[k]) cudaEventDestroy(s->ev_sim[k]);
+            if (s->ev_done[k]) cudaEventDestroy(s->ev_done[k]);
+        }
+        for (int q = 0; q < 2; q++) {
+            if (s->cls_s[q]) cudaStreamDestroy(s->cls_s[q]);
+            if (s->cls_join[q]) cudaEventDestroy(s->cls_join[q]);
+        }
+        if (s->cls_fork) cudaEventDestroy(s->cls_fork);
         delete s;
         return VUDA_ERR_CUDA;
     }
@@ -586,6 +627,11 @@ vuda_status vuda_serve_destroy(vuda_server_t s) {
     }
     if (s->ren_s && s->ren_s != s->sim_s) cudaStreamDestroy(s->ren_s);
     if (s->sim_s) cudaStreamDestroy(s->sim_s);
+    for (int q = 0; q < 2; q++) {
+        if (s->cls_s[q]) cudaStreamDestroy(s->cls_s[q]);
+        if (s->cls_join[q]) cudaEventDestroy(s->cls_join[q]);
+    }
+    if (s->cls_fork) cudaEventDestroy(s->cls_fork);
     cudaFree(s->descs);
     cudaFree(s->counters);
     delete s;
