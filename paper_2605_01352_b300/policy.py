@@ -65,6 +65,30 @@ class MLPPolicy:
         py = F.adaptive_avg_pool2d(y, k).view(E, C * k * k)
         return torch.cat([pd, py], 1)
 
+    def capture(self, frames, force, stream):
+        """Capture act() for each frame of a ring as a CUDA graph on `stream`
+        (the tensors are fixed: the ring's frames and the force array), so
+        that a rollout's callback is one graph launch instead of a dozen
+        kernel launches from Python."""
+        import torch
+        self._graphs = []
+        with torch.cuda.stream(stream):
+            for fr in frames:        # warm-up outside capture (allocator, cuBLAS workspace)
+                self.act(fr, force)
+        stream.synchronize()
+        for fr in frames:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                self.act(fr, force)
+            self._graphs.append(g)
+        return self
+
+    def act_captured(self, slot: int, stream):
+        """Replay the captured act() of frame `slot` on `stream`."""
+        import torch
+        with torch.cuda.stream(stream):
+            self._graphs[slot].replay()
+
     def act(self, frame, force):
         """Writes the forces of every body ([3, E N], in place) from a frame."""
         import torch

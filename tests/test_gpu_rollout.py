@@ -26,19 +26,26 @@ def _groups(make, n):
     return make(n, 0), make(n, n)
 
 
-def _run(V, scenes, steps, mode, hidden=256, record=False):
+def _run(V, scenes, steps, mode, hidden=256, record=False, graph=False):
     import torch
     from paper_2605_01352_b300.policy import MLPPolicy
     envs = [V.Env(sc) for sc in scenes]
     rings = [[e.alloc_frame(), e.alloc_frame()] for e in envs]
     forces = [torch.zeros((3, e.B), dtype=torch.float32, device="cuda") for e in envs]
     pols = [MLPPolicy(sc, hidden, seed=7 + g) for g, sc in enumerate(scenes)]
+    if graph:
+        for g in range(2):
+            pols[g].capture(rings[g], forces[g], torch.cuda.Stream())
+            forces[g].zero_()                 # the capture's warm-up wrote forces
     hist = [[f.clone()] for f in forces]
     order = []
 
     def policy(group, step, slot, stream):
+        if graph:
+            pols[group].act_captured(slot, stream)
         with torch.cuda.stream(stream):
-            pols[group].act(rings[group][slot], forces[group])
+            if not graph:
+                pols[group].act(rings[group][slot], forces[group])
             if record:
                 hist[group].append(forces[group].clone())
         order.append((group, step, slot))
@@ -60,14 +67,15 @@ def _run(V, scenes, steps, mode, hidden=256, record=False):
     return out
 
 
-@pytest.mark.parametrize("mode", ["streams", "green"])
-def test_rollout_schedule_does_not_change_results(V, mode):
+@pytest.mark.parametrize("mode,graph", [("streams", False), ("green", False), ("streams", True), ("green", True)])
+def test_rollout_schedule_does_not_change_results(V, mode, graph):
     """Co-scheduled rollouts (shared SMs, or disjoint green partitions with
     the policy on a stream of its own) equal the time-sliced rollout bit for
-    bit: states, both frames of both groups, and the forces."""
+    bit: states, both frames of both groups, and the forces -- also with the
+    policy replayed from CUDA graphs captured per frame slot."""
     scenes = _groups(lambda n, b: S.cfg2(n, env_base=b), 24)
     ref = _run(V, scenes, 5, "serialized")
-    got = _run(V, scenes, 5, mode)
+    got = _run(V, scenes, 5, mode, graph=graph)
     assert ref["order"] == got["order"] == [(g, k, k & 1) for k in range(5) for g in (0, 1)]
     for g in range(2):
         for k in ref["state"][g]:
