@@ -16,9 +16,10 @@
 //   tile in strips of at most 256 pixels (8 x 8 tiles: one strip, 2 pixels a
 //   lane; 16 x 16: one strip, 8 a lane; 32 x 32: four 32 x 8 strips, 8 a
 //   lane), each strip a pass over the tile's lists: records whose unclipped
-//   bounding box has at most kLanePx pixel centres are rasterised one per
-//   lane with 32-bit edge functions (exact for boxes that small) into the
-//   warp's strip key buffer in shared memory (atomicMin); larger records and
+//   bounding box has at most kLanePx pixel centres are rasterised row by row
+//   with 32-bit edge functions (exact for boxes that small), the rows of a
+//   batch of 32 records dealt to the lanes in turn, into the warp's strip
+//   key buffer in shared memory (atomicMin); larger records and
 //   the wide list go through the warp-wide pass, in which every lane keeps
 //   the keys of its run of pixels in registers.  The strip is then resolved
 //   from min(register key, shared key) to RGB8, FP32 depth and u32 triangle
@@ -44,7 +45,7 @@ constexpr int kBT = 256;          // bin_kernel threads
 constexpr int kNarrowTiles = 9;   // default bin limit: records over more tiles go to the camera's wide list
 constexpr int kMaxBinLimit = 64;  // largest bin limit accepted
 constexpr int kMaxTiles = 2048;   // tiles per camera the counting sort holds in shared memory (640 x 480: 1200)
-constexpr int kLanePx = 64;       // unclipped bounding-box pixels up to which one lane rasterises a record
+constexpr int kLanePx = 64;       // unclipped bounding-box pixels up to which a record takes the 32-bit row path
 
 // Geometry of one warp's T x T tile: strips of SH rows, R pixels per lane
 // (LPR lanes per strip row), TW tiles (warps) per tile_kernel CTA.  Two
@@ -62,7 +63,7 @@ struct TileGeom {
     static_assert(LPR * SH == 32 && STRIPS * SH == T, "tile geometry");
 };
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr unsigned kSmallBit = 8u;  // TriRec::tl bit: the record takes the per-lane path
+constexpr unsigned kSmallBit = 8u;  // TriRec::tl bit: the record takes the 32-bit row path
 
 // A set-up triangle, vertices oriented to positive area (80 bytes, 16-byte
 // aligned in the scratch array).
@@ -344,41 +345,60 @@ __global__ void __launch_bounds__(kBT, 4) bin_list_kernel(const DevBatch* __rest
     bin_camera<T>(sd, sd.pose[(tag >> 24) & 1], ts, ci, nlim);
 }
 
-// One lane rasterises a small record over the pixels [x0, x1] x [y0, y1] of
-// its strip (origin tx0, sy0; rows of T keys) into the warp's shared key
-// buffer.  The record's
-// unclipped bounding box has at most kLanePx pixel centres, so its vertex
-// spans and |A|, |B| stay below 65 x 256 < 2^14.1 and every edge value at a
-// pixel centre of the box (or one step past it) below 2^30: 32-bit integers
-// hold them exactly, and their float conversions are the correctly rounded
-// ones.
-template <int T>
-__device__ __forceinline__ void lane_raster(const TriRec& t, int x0, int x1, int y0, int y1, int tx0, int sy0,
-                                            unsigned long long* sk) {
+// Row set-up of a small record for the dealt raster below: the biased edge
+// values at the first pixel centre (x0, y0) of the record's clipped box,
+// their steps along x and y, and the record's depth constants, in the
+// lane's slot of the warp (four 16-byte groups, one array per group).  A
+// small record's unclipped bounding box has at most kLanePx pixel centres,
+// so its vertex spans and |A|, |B| stay below 65 x 256 < 2^14.1 and every
+// edge value at a pixel centre of the box (or one step past it) below 2^30:
+// 32-bit integers hold them exactly, and their float conversions are the
+// correctly rounded ones.
+struct RowSlots {
+    int4* e;     // [32] E0, E1, E2 at (x0, y0); triangle id
+    int4* dx;    // [32] x steps; x0 - tx0 | (x1 - tx0) << 8
+    int4* dy;    // [32] y steps; bias bits | (y0 - sy0) << 3
+    float4* z;   // [32] 1 / z of the vertices; doubled area
+    int* first;  // [32] the batch's unit index of the record's first row
+};
+
+__device__ __forceinline__ void put_row_slot(const RowSlots& rs, int lane, const TriRec& t, int x0, int x1, int y0,
+                                             int tx0, int sy0) {
     const long long cx = 256LL * x0 + 128, cy = 256LL * y0 + 128;
-    int R0 = (int)((long long)t.A[0] * cx + (long long)t.B[0] * cy + t.C[0]);
-    int R1 = (int)((long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1]);
-    int R2 = (int)((long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2]);
-    const int dx0 = t.A[0] * 256, dx1 = t.A[1] * 256, dx2 = t.A[2] * 256;
-    const int dy0 = t.B[0] * 256, dy1 = t.B[1] * 256, dy2 = t.B[2] * 256;
-    const int b0 = (~t.tl) & 1u, b1 = (~t.tl >> 1) & 1u, b2 = (~t.tl >> 2) & 1u;
-    for (int py = y0; py <= y1; py++) {
-        int E0 = R0, E1 = R1, E2 = R2;
-        unsigned long long* row = sk + (py - sy0) * T - tx0;
-        for (int px = x0; px <= x1; px++) {
-            if ((E0 | E1 | E2) >= 0) {   // every biased edge value >= 0
-                const float den = (__int2float_rn(E0 + b0) * t.iz[0] + __int2float_rn(E1 + b1) * t.iz[1]) +
-                                  __int2float_rn(E2 + b2) * t.iz[2];
-                const float depth = t.af / den;
-                atomicMin(row + px, ((unsigned long long)__float_as_uint(depth) << 32) | t.id);
-            }
-            E0 += dx0;
-            E1 += dx1;
-            E2 += dx2;
+    const int R0 = (int)((long long)t.A[0] * cx + (long long)t.B[0] * cy + t.C[0]);
+    const int R1 = (int)((long long)t.A[1] * cx + (long long)t.B[1] * cy + t.C[1]);
+    const int R2 = (int)((long long)t.A[2] * cx + (long long)t.B[2] * cy + t.C[2]);
+    rs.e[lane] = make_int4(R0, R1, R2, (int)t.id);
+    rs.dx[lane] = make_int4(t.A[0] * 256, t.A[1] * 256, t.A[2] * 256, (x0 - tx0) | ((x1 - tx0) << 8));
+    rs.dy[lane] = make_int4(t.B[0] * 256, t.B[1] * 256, t.B[2] * 256,
+                            (int)((~t.tl) & 7u) | ((y0 - sy0) << 3));
+    rs.z[lane] = make_float4(t.iz[0], t.iz[1], t.iz[2], t.af);
+}
+
+// Rasterises row r of a small record's clipped box from its slot (owner
+// lane o; u is the row's unit index in the batch) into the warp's shared
+// key buffer (atomicMin): the coverage test, depth and key of the warp-wide
+// pass in 32-bit arithmetic, so the keys do not depend on how the rows are
+// dealt.
+template <int T>
+__device__ __forceinline__ void slot_row(const RowSlots& rs, int o, int u, int tx0, unsigned long long* sk) {
+    const int4 e = rs.e[o], dx = rs.dx[o], dy = rs.dy[o];
+    const float4 z = rs.z[o];
+    const int r = u - rs.first[o];
+    const int xa = dx.w & 255, xb = (dx.w >> 8) & 255;
+    int E0 = e.x + r * dy.x, E1 = e.y + r * dy.y, E2 = e.z + r * dy.z;
+    const int b0 = dy.w & 1, b1 = (dy.w >> 1) & 1, b2 = (dy.w >> 2) & 1;
+    unsigned long long* row = sk + ((dy.w >> 3) + r) * T;
+    for (int px = xa; px <= xb; px++) {
+        if ((E0 | E1 | E2) >= 0) {
+            const float den = (__int2float_rn(E0 + b0) * z.x + __int2float_rn(E1 + b1) * z.y) +
+                              __int2float_rn(E2 + b2) * z.z;
+            const float depth = z.w / den;
+            atomicMin(row + px, ((unsigned long long)__float_as_uint(depth) << 32) | (uint32_t)e.w);
         }
-        R0 += dy0;
-        R1 += dy1;
-        R2 += dy2;
+        E0 += dx.x;
+        E1 += dx.y;
+        E2 += dx.z;
     }
 }
 
@@ -505,7 +525,13 @@ __device__ __forceinline__ void tile_work(const uint32_t* __restrict__ tri_color
     constexpr int R = G::R;
     __shared__ unsigned long long s_key[G::TW][T * G::SH];
     __shared__ int s_big[G::TW][32];
+    __shared__ int4 s_rs[G::TW][3][32];
+    __shared__ float4 s_rz[G::TW][32];
+    __shared__ int s_first[G::TW][32];
+    __shared__ unsigned char s_own[G::TW][32 * G::SH];   // owner lane of each dealt row
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const RowSlots rs{s_rs[threadIdx.x >> 5][0], s_rs[threadIdx.x >> 5][1], s_rs[threadIdx.x >> 5][2],
+                      s_rz[threadIdx.x >> 5], s_first[threadIdx.x >> 5]};
     const int4 geo = __ldg(reinterpret_cast<const int4*>(itp));        // cam, tile0, W, H
     const int2 tl2 = __ldg(reinterpret_cast<const int2*>(itp) + 2);    // tiles_x, ntiles
     const longlong2 rb = __ldg(reinterpret_cast<const longlong2*>(itp) + 2);   // rec_base, ent_base
@@ -521,6 +547,7 @@ __device__ __forceinline__ void tile_work(const uint32_t* __restrict__ tri_color
     const int tx0 = (tile % tiles_x) * T, ty0 = (tile / tiles_x) * T;
     const int tx1 = min(tx0 + T, W) - 1, ty1 = min(ty0 + T, H) - 1;
     unsigned long long* sk = s_key[w];
+    const int beg = __ldg(toff + tile), end = __ldg(toff + tile + 1), nw = __ldg(toff + ntiles + 1);
 #pragma unroll 1
     for (int st = 0; st < G::STRIPS; st++) {
         const int sy0 = ty0 + st * G::SH;
@@ -537,20 +564,43 @@ __device__ __forceinline__ void tile_work(const uint32_t* __restrict__ tri_color
 #pragma unroll
         for (int k = 0; k < R; k++) key[k] = ~0ULL;
 
-        const int beg = __ldg(toff + tile), end = __ldg(toff + tile + 1);
         for (int base = beg; base < end; base += 32) {
             const int i = base + lane;
             bool big = false;
             uint32_t r = 0;
+            int nrow = 0;
             if (i < end) {
                 r = __ldg(ent + i);
                 const TriRec t = load_rec(rec + r);
                 const int x0 = max((int)t.x0, tx0), x1 = min((int)t.x1, tx1);
                 const int y0 = max((int)t.y0, sy0), y1 = min((int)t.y1, sy1);
                 if (x0 <= x1 && y0 <= y1) {
-                    if (t.tl & kSmallBit) lane_raster<T>(t, x0, x1, y0, y1, tx0, sy0, sk);
-                    else big = true;
+                    if (t.tl & kSmallBit) {
+                        nrow = y1 - y0 + 1;
+                        put_row_slot(rs, lane, t, x0, x1, y0, tx0, sy0);
+                    } else {
+                        big = true;
+                    }
                 }
+            }
+            // the rows of the batch's small records are dealt to the lanes in
+            // turn (row u of the batch to lane u % 32), so that the warp's
+            // time is the batch's rows / 32 rather than its largest record
+            int incl = nrow;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFullMask, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int nunits = __shfl_sync(kFullMask, incl, 31);
+            if (nunits > 0) {
+                if (nrow > 0) {
+                    rs.first[lane] = incl - nrow;
+                    for (int k = incl - nrow; k < incl; k++) s_own[w][k] = (unsigned char)lane;
+                }
+                __syncwarp();
+                for (int u = lane; u < nunits; u += 32) slot_row<T>(rs, s_own[w][u], u, tx0, sk);
+                __syncwarp();   // the slots and owners are reused by the next batch
             }
             const unsigned m = __ballot_sync(kFullMask, big);
             if (big) s_big[w][__popc(m & ((1u << lane) - 1u))] = (int)r;
@@ -559,7 +609,6 @@ __device__ __forceinline__ void tile_work(const uint32_t* __restrict__ tri_color
             for (int q = 0; q < nb; q++) warp_pass<R>(rec + s_big[w][q], y, xs, nx, key);
             __syncwarp();   // s_big is reused by the next batch
         }
-        const int nw = __ldg(toff + ntiles + 1);
         for (int q = 0; q < nw; q++) warp_pass<R>(rec + __ldg(wide + q), y, xs, nx, key);
         __syncwarp();       // the lanes' shared-memory keys are complete
 
