@@ -43,7 +43,9 @@ class _Params(C.Structure):
                 ("restitution_threshold", C.c_double), ("friction", C.c_double),
                 ("baumgarte", C.c_double), ("slop", C.c_double), ("margin", C.c_double),
                 ("jacobi_omega", C.c_double), ("plane", C.c_int), ("max_contacts_per_body", C.c_int),
-                ("gyroscopic", C.c_int), ("edge_contacts", C.c_int)]
+                ("gyroscopic", C.c_int), ("edge_contacts", C.c_int), ("hull_contacts", C.c_int),
+                ("mesh_id", C.c_void_p), ("mesh_vert_off", C.c_void_p), ("mesh_verts", C.c_void_p),
+                ("mesh_tri_off", C.c_void_p), ("mesh_tris", C.c_void_p)]
 
 
 _lib = None
@@ -60,10 +62,19 @@ def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
-def _params(p) -> _Params:
-    return _Params(p.dt, p.substeps, p.iterations, (C.c_double * 3)(*p.gravity), p.restitution,
-                   p.restitution_threshold, p.friction, p.baumgarte, p.slop, p.margin, p.jacobi_omega,
-                   p.plane, p.max_contacts_per_body, p.gyroscopic, p.edge_contacts)
+def _params(p, scene=None, mesh_id=None) -> _Params:
+    """Parameters; with hull contacts also the scene's meshes (mesh_id: the
+    bodies' meshes in the entry point's indexing, default all the scene's)."""
+    P = _Params(p.dt, p.substeps, p.iterations, (C.c_double * 3)(*p.gravity), p.restitution,
+                p.restitution_threshold, p.friction, p.baumgarte, p.slop, p.margin, p.jacobi_omega,
+                p.plane, p.max_contacts_per_body, p.gyroscopic, p.edge_contacts, getattr(p, "hull_contacts", 0))
+    if P.hull_contacts and scene is not None:
+        keep = [np.ascontiguousarray(scene.mesh_id if mesh_id is None else mesh_id, np.int32),
+                np.ascontiguousarray(scene.mesh_vert_off, np.int32), np.ascontiguousarray(scene.mesh_verts, np.float32),
+                np.ascontiguousarray(scene.mesh_tri_off, np.int32), np.ascontiguousarray(scene.mesh_tris, np.int32)]
+        P.mesh_id, P.mesh_vert_off, P.mesh_verts, P.mesh_tri_off, P.mesh_tris = (a.ctypes.data for a in keep)
+        P._keep = keep   # the arrays live as long as the parameters
+    return P
 
 
 def sim_step(scene, nsteps: int = 1, state: Optional[dict] = None, precision: str = "f32",
@@ -80,7 +91,7 @@ def sim_step(scene, nsteps: int = 1, state: Optional[dict] = None, precision: st
     E = scene.num_envs
     flags = np.zeros(E, np.uint32)
     cc = np.zeros(E, np.int32)
-    P = _params(params or scene.params)
+    P = _params(params or scene.params, scene)
     fn = lib().oracle_sim_step_f32 if precision == "f32" else lib().oracle_sim_step_f64
     rc = fn(C.c_int(E), _ptr(np.ascontiguousarray(scene.body_off, np.int32)), C.c_int(scene.num_bodies),
             _ptr(s["pos"]), _ptr(s["quat"]), _ptr(s["vel"]), _ptr(s["angvel"]),
@@ -100,7 +111,7 @@ def contacts(scene, env: int, state: Optional[dict] = None, params=None):
     quat = np.ascontiguousarray(st["quat"][:, b0:b1], np.float32)
     dims = np.ascontiguousarray(scene.shape_dims[:, b0:b1], np.float32)
     typ = np.ascontiguousarray(scene.shape_type[b0:b1], np.uint8)
-    P = _params(params or scene.params)
+    P = _params(params or scene.params, scene, scene.mesh_id[b0:b1])
     cap = max(1, P.max_contacts_per_body * n)
     a = np.zeros(cap, np.int32)
     b = np.zeros(cap, np.int32)
@@ -109,6 +120,8 @@ def contacts(scene, env: int, state: Optional[dict] = None, params=None):
     d = np.zeros(cap, np.float32)
     nc = lib().oracle_contacts_f32(C.c_int(n), _ptr(pos), _ptr(quat), _ptr(typ), _ptr(dims), C.byref(P),
                                    C.c_int(cap), _ptr(a), _ptr(b), _ptr(nrm), _ptr(pt), _ptr(d))
+    if nc < 0:
+        raise ValueError("oracle_contacts rejected its arguments")
     k = min(nc, cap)
     return dict(a=a[:k], b=b[:k], n=nrm[:k], p=pt[:k], d=d[:k], count=nc)
 

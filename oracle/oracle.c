@@ -35,6 +35,13 @@ typedef struct {
     int plane, max_contacts_per_body;
     int gyroscopic;     /* 1: gyroscopic term of boxes (physics.inc) */
     int edge_contacts;  /* 1: box-box edge-edge contacts (physics.inc) */
+    int hull_contacts;  /* 1: hulls collide through their vertices and faces (physics.inc) */
+    /* meshes of the hull bodies (read only with hull_contacts) */
+    const int* mesh_id;        /* mesh of each body: [B] for oracle_sim_step, [n] for oracle_contacts */
+    const int* mesh_vert_off;  /* [M+1] */
+    const float* mesh_verts;   /* [V][3] unit-size vertices */
+    const int* mesh_tri_off;   /* [M+1] */
+    const int* mesh_tris;      /* [T][3] vertex indices local to the mesh */
 } oracle_params;
 
 #define REAL float

@@ -167,6 +167,30 @@ def convex_hull_mesh(streams: Streams, ntri: int):
             return P.astype(np.float32), T
 
 
+def hull_from_points(points) -> tuple:
+    """Convex hull mesh (vertices, outward triangles) of points on the unit
+    sphere, every point a vertex of the hull (e.g. octahedron())."""
+    from scipy.spatial import ConvexHull
+
+    P = np.asarray(points, np.float64)
+    hull = ConvexHull(P)
+    if len(hull.vertices) != len(P):
+        raise ValueError("every point must be a vertex of the hull")
+    return P.astype(np.float32), _orient_outward(P, hull.simplices.astype(np.int32))
+
+
+def octahedron():
+    """The regular octahedron with vertices +-x, +-y, +-z: 6 vertices, 8
+    faces with normals (+-1, +-1, +-1) / sqrt(3) at distance 1 / sqrt(3)."""
+    V = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], np.float32)
+    T = []
+    for sx in (0, 1):
+        for sy in (2, 3):
+            for sz in (4, 5):
+                T.append([sx, sy, sz])
+    return V, _orient_outward(V.astype(np.float64), np.array(T, np.int32))
+
+
 # ----------------------------------------------------------------------------
 # Scene container
 # ----------------------------------------------------------------------------
@@ -189,6 +213,7 @@ class SimParams:
     # gyroscopic term, box-box contacts from corners only)
     gyroscopic: int = 0  # 1: gyroscopic term of boxes (implicit, one Newton step)
     edge_contacts: int = 0  # 1: box-box edge-edge contacts (separating-axis test)
+    hull_contacts: int = 0  # 1: hulls collide through their vertices and faces (else as spheres of their radius)
 
 
 @dataclasses.dataclass
@@ -345,7 +370,8 @@ def generate(num_envs: int, bodies, seed: int, *, kinds: str = "spheres",
     """Build a seeded batch of environments.
 
     bodies: int (same count everywhere) or per-env int array.
-    kinds: "spheres" | "mixed" (even index sphere, odd index box) | "hulls".
+    kinds: "spheres" | "mixed" (even index sphere, odd index box) | "hulls" |
+    "mixed_hulls" (index mod 3: sphere, box, hull).
     res: int or per-env int array: camera width (and height, unless given).
     height: None (square cameras), or int / per-env int array of camera heights;
     the 60 degree field of view is vertical.
@@ -360,7 +386,7 @@ def generate(num_envs: int, bodies, seed: int, *, kinds: str = "spheres",
     nmax = int(nb.max()) if E else 0
 
     hulls = []
-    if kinds == "hulls":
+    if kinds in ("hulls", "mixed_hulls"):
         ms = Streams(seed ^ 0x4855_4C4C, 1)
         for _ in range(n_hull_meshes):
             lo, hi = hull_tris
@@ -382,6 +408,8 @@ def generate(num_envs: int, bodies, seed: int, *, kinds: str = "spheres",
             typ = SHAPE_BOX
         elif kinds == "hulls":
             typ = SHAPE_HULL
+        elif kinds == "mixed_hulls":
+            typ = (SHAPE_SPHERE, SHAPE_BOX, SHAPE_HULL)[b % 3]
         else:
             typ = SHAPE_SPHERE
         shape_type[:, b] = typ
@@ -506,13 +534,19 @@ def cfg4(num_envs: int = 2048) -> Scene:
 
 def custom(bodies: List[dict], *, res: int = 64, params: Optional[SimParams] = None,
            cams: Optional[List[dict]] = None, envs: int = 1) -> Scene:
-    """A hand-placed scene for tests.  Each body dict: type ('sphere'|'box'),
-    r or h (half extents), pos, quat (w,x,y,z), vel, angvel.  The same bodies are
-    repeated in every env."""
-    voff, verts, toff, tris = _mesh_library()
+    """A hand-placed scene for tests.  Each body dict: type ('sphere'|'box'|
+    'hull'), r (sphere and hull radius) or h (half extents), mesh (a hull's
+    unit-size (vertices, triangles), e.g. octahedron()), pos, quat (w,x,y,z),
+    vel, angvel.  The same bodies are repeated in every env."""
+    hull_meshes = []
+    for b in bodies:
+        if b["type"] == "hull" and not any(b["mesh"] is m for m in hull_meshes):
+            hull_meshes.append(b["mesh"])
+    voff, verts, toff, tris = _mesh_library(hull_meshes)
     n = len(bodies)
     B = n * envs
-    typ = np.array([SHAPE_BOX if b["type"] == "box" else SHAPE_SPHERE for b in bodies] * envs, np.uint8)
+    kind = {"box": SHAPE_BOX, "sphere": SHAPE_SPHERE, "hull": SHAPE_HULL}
+    typ = np.array([kind[b["type"]] for b in bodies] * envs, np.uint8)
     dims = np.zeros((3, B), np.float32)
     pos = np.zeros((3, B), np.float32)
     quat = np.zeros((4, B), np.float32)
@@ -532,6 +566,10 @@ def custom(bodies: List[dict], *, res: int = 64, params: Optional[SimParams] = N
     im, ii = mass_properties(typ, dims)
     scale = np.where(typ[None, :] == SHAPE_BOX, dims, dims[0:1].repeat(3, 0)).astype(np.float32)
     mesh = np.where(typ == SHAPE_BOX, MESH_CUBE, MESH_ICOSPHERE).astype(np.int32)
+    for e in range(envs):
+        for i, b in enumerate(bodies):
+            if b["type"] == "hull":
+                mesh[e * n + i] = 3 + next(k for k, m in enumerate(hull_meshes) if m is b["mesh"])
     cams = cams or [dict(eye=(0.0, -2.5, 1.5), target=(0.0, 0.0, 0.4), fov=60.0)]
     C = len(cams) * envs
     eye = np.zeros((C, 3), np.float32)
