@@ -491,7 +491,8 @@ def rollout_bench(V, S, E: int, steps: int, warmup: int, settle: int) -> dict:
 def physics_options_bench(V, S, E: int, settle: int) -> dict:
     """Physics step time on the settled benchmark batch with the options
     beyond the configured physics: the gyroscopic term of boxes and box-box
-    edge-edge contacts (each off / on; the headline uses neither)."""
+    edge-edge contacts (each off / on; the headline uses neither), and hull
+    contacts on a batch of the same shape with hulls."""
     import dataclasses
     import torch
     out = {}
@@ -513,6 +514,29 @@ def physics_options_bench(V, S, E: int, settle: int) -> dict:
         torch.cuda.synchronize()
         out["gyroscopic_%d_edge_contacts_%d" % (gyro, edges)] = {
             "sim_ms": a.elapsed_time(b) / 20, "contacts_mean": float(env.contact_counts().mean())}
+        env.close()
+    # hull contacts: the benchmark's batch shape with every third body a
+    # convex hull of 8-48 faces (spheres and boxes between), simulated as
+    # spheres of their radius (option off) and through their own faces (on)
+    for hulls in (0, 1):
+        sc = S.generate(E, 32, S.config_seed(2) ^ 0x4855, kinds="mixed_hulls", res=128, substeps=8,
+                        hull_tris=(8, 48), n_hull_meshes=16)
+        sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, hull_contacts=hulls))
+        env = V.Env(sc)
+        ring = [env.alloc_frame(triid=False), env.alloc_frame(triid=False)]
+        env.pipeline_run(settle, ring)
+        for _ in range(3):
+            env.sim_step(1, stream=s0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s0)
+        for _ in range(20):
+            env.sim_step(1, stream=s0)
+        b.record(s0)
+        torch.cuda.synchronize()
+        out["mixed_hulls_hull_contacts_%d" % hulls] = {
+            "sim_ms": a.elapsed_time(b) / 20, "contacts_mean": float(env.contact_counts().mean()),
+            "workload": "%d envs x 32 bodies (sphere, box, hull of 8-48 faces in turn), 8 substeps, settled" % E}
         env.close()
     return out
 

@@ -81,6 +81,12 @@ typedef struct {
                                      implicit (Newton) step per substep; spheres and hull proxies have none */
     int32_t edge_contacts;        /* 1: box-box edge-edge contacts (separating-axis test over 15 axes; one
                                      contact between crossing edges, after the pair's corner contacts) */
+    int32_t hull_contacts;        /* 1: hulls collide as the convex hulls of their meshes scaled by dims[0]
+                                     (their vertices on the plane; a sphere's centre against the deepest face;
+                                     hull-hull and hull-box: separating-axis test over the face normals, the
+                                     incident face clipped by the reference face's sides), after all other
+                                     contacts; 0: hulls are spheres of radius dims[0].  Not accepted by
+                                     vuda_sim_step_noalloc (no meshes there) */
 } vuda_sim_params;
 
 /* Host description of a batch (all arrays host memory, read during
@@ -89,7 +95,7 @@ typedef struct {
  *   body_off[E+1]           CSR: env e owns bodies [body_off[e], body_off[e+1])
  *   pos[3][B] quat[4][B]    pose (quat = w, x, y, z, unit)
  *   vel[3][B] angvel[3][B]  linear / angular velocity (world frame)
- *   shape_type[B]           0 sphere, 1 box, 2 hull (sphere proxy of radius dims[0])
+ *   shape_type[B]           0 sphere, 1 box, 2 hull (a sphere of radius dims[0] unless hull_contacts)
  *   shape_dims[3][B]        sphere/hull: (r, -, -); box: half extents
  *   inv_mass[B] inv_inertia[3][B]   body-frame principal inverse inertia
  *   mesh_id[B] mesh_scale[3][B] albedo[B] (r | g<<8 | b<<16)

@@ -303,7 +303,7 @@ vuda_status env_estimate_bytes(const vuda_scene* sc, const vuda_sim_params* p, i
     int64_t bytes = B * 4 * (3 + 4 + 3 + 3 + 3 + 1 + 3 + 3 + 2 * 7 + 2 + 2) + B + E * 40;
     bytes += (int64_t)p->max_contacts_per_body * B * kContactStride * 4;   // contact spill (upper bound)
     bytes += T * 4;                                                          // colour table
-    bytes += (int64_t)sc->mesh_vert_off[sc->num_meshes] * 12 + (int64_t)sc->mesh_tri_off[sc->num_meshes] * 12;
+    bytes += (int64_t)sc->mesh_vert_off[sc->num_meshes] * 12 + (int64_t)sc->mesh_tri_off[sc->num_meshes] * 28;
     bytes += C * 128 + (P / 16 + C) * 16 + 64 * 1024;                       // cameras, items, slack
     bytes += (int64_t)sc->mesh_tri_off[sc->num_meshes] * 8 + (int64_t)sc->mesh_vert_off[sc->num_meshes] * 8;
     bytes += tiled_scratch_estimate(sc);   // the tiled render path, where it applies
@@ -560,6 +560,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     if (E > 0 && (!sc->body_off || !sc->cam_off)) return invalid("body_off/cam_off missing");
     if (prm->substeps <= 0 || prm->iterations < 0 || prm->max_contacts_per_body <= 0 || !(prm->dt > 0.0f))
         return invalid("bad sim params (dt > 0, substeps > 0, iterations >= 0, max_contacts_per_body > 0)");
+    if (prm->hull_contacts != 0 && prm->hull_contacts != 1) return invalid("hull_contacts must be 0 or 1");
     if (E > 0 && sc->body_off[0] != 0) return invalid("body_off[0] != 0");
     if (E > 0 && sc->cam_off[0] != 0) return invalid("cam_off[0] != 0");
     int max_bodies = 0;
@@ -804,6 +805,16 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     UP(mesh_verts, float, sc->mesh_verts, 3 * (size_t)sc->mesh_vert_off[M]);
     UP(mesh_tri_off, int32_t, sc->mesh_tri_off, M + 1);
     UP(mesh_tris, int32_t, sc->mesh_tris, 3 * (size_t)sc->mesh_tri_off[M]);
+    if (s == VUDA_OK) {   // face planes of the meshes (hull contacts)
+        float4* planes = nullptr;
+        s = dalloc(env, &planes, (size_t)sc->mesh_tri_off[M]);
+        d.mesh_plane = planes;
+        if (s == VUDA_OK && launch_mesh_planes(d.mesh_verts, d.mesh_vert_off, d.mesh_tri_off, d.mesh_tris, M,
+                                               sc->mesh_tri_off[M], planes, 0) != cudaSuccess) {
+            set_error("mesh plane launch failed");
+            s = VUDA_ERR_CUDA;
+        }
+    }
     UP(cam_env, int32_t, cam_env.data(), C);
     UP(cam_w, int32_t, sc->cam_w, C);
     UP(cam_h, int32_t, sc->cam_h, C);
@@ -878,6 +889,7 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     k.mcpb = mcpb;
     k.gyro = prm->gyroscopic;
     k.edges = prm->edge_contacts;
+    k.hulls = prm->hull_contacts;
     d.sc = k;
     d.max_bodies = max_bodies;
     if (o.persistent) {
@@ -989,7 +1001,7 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
         for (int t = 0; t < nsteps && e == cudaSuccess; t++) {
             int slot = (int)((env->steps + t) & 1);
             e = launch_sim_items(env->d_desc, env->sim_items[slot], env->E, env->counters, env->sim_grid_sh,
-                                 env->phys_smem, env->max_bodies, force, gate, env->sc.edges != 0,
+                                 env->phys_smem, env->max_bodies, force, gate, sim_features(env->sc),
                                  (cudaStream_t)stream);
         }
     } else if (env->persistent) {
@@ -1010,7 +1022,7 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
             for (size_t k = 0; k < ncls && e == cudaSuccess; k++) {
                 const vuda_env::SimClass& cl = env->sim_classes[k];
                 int* counter = env->counters + 2 + k;
-                const bool ed = env->sc.edges != 0;
+                const int ed = sim_features(env->sc);
                 cudaStream_t cs = (fork && k > 0) ? env->class_s[k - 1] : (cudaStream_t)stream;
                 e = cl.wide ? wide::launch_sim_items(env->d_desc, cl.items[slot], cl.nitems, counter, cl.grid, cl.smem,
                                                      cl.max_bodies, force, SmGate{nullptr, 0}, ed, cs)

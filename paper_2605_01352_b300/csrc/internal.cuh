@@ -22,7 +22,17 @@ struct SimConst {
     int plane, mcpb;
     int gyro;                     // gyroscopic term of boxes
     int edges;                    // box-box edge-edge contacts
+    int hulls;                    // hull contacts from the hulls' vertices and faces
 };
+
+// Physics kernel variants: the code of an optional contact test is compiled
+// only into the variants that carry its bit (a batch with the option off
+// runs the variant without it).
+constexpr int kFeatEdges = 1;
+constexpr int kFeatHulls = 2;
+__host__ __device__ inline int sim_features(const SimConst& k) {
+    return (k.edges ? kFeatEdges : 0) | (k.hulls ? kFeatHulls : 0);
+}
 
 // Scratch of the tiled render path (tiled.cu), per camera c of env e with
 // T_e triangles and n_c tiles (of the batch's tile size), R_e =
@@ -64,6 +74,7 @@ struct DevBatch {
     const float* mesh_verts;      // [V][3]
     const int32_t* mesh_tri_off;  // [M+1]
     const int32_t* mesh_tris;     // [T][3]
+    const float4* mesh_plane;     // [T] face planes of the unit meshes: outward normal, offset (hull contacts)
     int ground_mesh;
     uint32_t ground_albedo;
     const int32_t* cam_env;       // [C] env of camera c
@@ -156,7 +167,7 @@ constexpr int kCamWords = 13;
        over one batch. */                                                                                     \
     cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid, \
                                  int smem_per_env, int max_bodies, const float* force, SmGate gate,           \
-                                 bool edges, cudaStream_t stream); /* edges: a listed batch has edge contacts */\
+                                 int feat, cudaStream_t stream); /* feat: kFeat bits of any listed batch */     \
     int sim_ctas_per_sm(int smem_per_env);                                                                    \
     CtaFootprint sim_list_footprint(int smem_per_env);                                                        \
     int phys_smem_bytes_default(int max_bodies, int mcpb);                                                    \
@@ -210,6 +221,14 @@ inline long long tiled_record_cap(long long T) { return T + T / 8 + 8; }
 // listing a triangle under at most nlim tiles (else on the wide list), then
 // rasterise and resolve the work items (camera, first tile) of
 // tiled_tiles_per_item(tile) tiles each.
+// Face planes of every triangle of the mesh library (hull contacts): for
+// triangle t of mesh m with unit-mesh vertices u0, u1, u2, c = (u1 - u0) x
+// (u2 - u0), the outward unit normal n = c / |c| and the offset n . u0
+// (planes[t] = (n, offset)); a triangle of zero area gets (0, 0, 0, +inf).
+cudaError_t launch_mesh_planes(const float* verts, const int32_t* vert_off, const int32_t* tri_off,
+                               const int32_t* tris, int num_meshes, int num_tris, float4* planes,
+                               cudaStream_t stream);
+
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
                                 const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim,
                                 cudaStream_t stream);

@@ -68,6 +68,10 @@ extern "C" vuda_status vuda_sim_step_noalloc(int32_t num_envs, int32_t num_bodie
         set_error("vuda_sim_step_noalloc: max_bodies must be positive");
         return VUDA_ERR_INVALID;
     }
+    if (prm->hull_contacts) {
+        set_error("vuda_sim_step_noalloc: hull contacts need the batch's meshes (vuda_env_create)");
+        return VUDA_ERR_INVALID;
+    }
     if (num_envs == 0 || nsteps == 0) return VUDA_OK;
     if (!body_off || !pos || !quat || !vel || !angvel || !shape_type || !shape_dims || !inv_mass || !inv_inertia ||
         !pose || !flags || !ncontacts) {
@@ -153,6 +157,7 @@ extern "C" vuda_status vuda_sim_step_noalloc(int32_t num_envs, int32_t num_bodie
     k.mcpb = prm->max_contacts_per_body;
     k.gyro = prm->gyroscopic;
     k.edges = prm->edge_contacts;
+    k.hulls = 0;
     int smem = smem_per_env > 0 ? smem_per_env : phys_smem_bytes_default(max_bodies, k.mcpb);
     ce = launch_sim(d, k, nsteps, force, 0, smem, max_bodies, s);
     if (ce != cudaSuccess) {

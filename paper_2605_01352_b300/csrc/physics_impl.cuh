@@ -742,9 +742,355 @@ __device__ __forceinline__ void solve_substep(const CA& C, const Bodies& S, int*
 
 }
 
-// kEdges: the variant with box-box edge-edge contacts (sc.edges decides at
-// run time; without them the code is left out, and its register pressure).
-template <bool kEdges>
+// ---- hull contacts (sc.hulls) ------------------------------------------
+// A hull body is the convex hull of its unit mesh scaled by its radius s
+// (body-frame vertices s v_k, face planes n_f . x = s o_f from the mesh's
+// planes); the pair tests treat a box as the polytope of its 8 corners and
+// 6 faces.  Hull contacts follow all others: the plane contacts of the
+// hulls (bodies in order, vertices in mesh order; none for a hull whose
+// centre is at least its radius plus the margin above the plane), then the
+// pairs (i, j), i < j, with a hull that pass the bounding-sphere test, in
+// lexicographic order: a sphere's centre against the hull's deepest face,
+// or the two polytopes (face separating-axis test, reference and incident
+// face, Sutherland-Hodgman clipping).  Each such unit is worked by one warp.
+
+// A box's face loops (corners in sign-bit order), counter-clockwise seen
+// from outside: +x, -x, +y, -y, +z, -z.
+__constant__ signed char kBoxLoop[24] = {1, 3, 7, 5, 0, 4, 6, 2, 2, 6, 7, 3, 0, 1, 5, 4, 4, 5, 7, 6, 0, 2, 3, 1};
+
+struct Poly {
+    bool hull;
+    int nv, nf;
+    const float* v;       // hull: unit-mesh vertices [nv][3]
+    const float4* pl;     // hull: unit-mesh face planes [nf]
+    const int32_t* tri;   // hull: mesh-local vertex indices [nf][3]
+    float s;              // hull: radius
+    float h0, h1, h2;     // box: half extents
+};
+
+__device__ __forceinline__ Poly poly_of(const DevBatch& b, const Bodies& S, int b0, int i) {
+    Poly P;
+    P.hull = S.TYPE(i) == kShapeHull;
+    if (P.hull) {
+        const int m = __ldg(b.mesh_id + b0 + i);
+        const int v0 = __ldg(b.mesh_vert_off + m), t0 = __ldg(b.mesh_tri_off + m);
+        P.nv = __ldg(b.mesh_vert_off + m + 1) - v0;
+        P.nf = __ldg(b.mesh_tri_off + m + 1) - t0;
+        P.v = b.mesh_verts + 3 * (size_t)v0;
+        P.pl = b.mesh_plane + t0;
+        P.tri = b.mesh_tris + 3 * (size_t)t0;
+        P.s = S.D(0, i);
+        P.h0 = P.h1 = P.h2 = 0.0f;
+    } else {
+        P.nv = 8;
+        P.nf = 6;
+        P.v = nullptr;
+        P.pl = nullptr;
+        P.tri = nullptr;
+        P.s = 0.0f;
+        P.h0 = S.D(0, i);
+        P.h1 = S.D(1, i);
+        P.h2 = S.D(2, i);
+    }
+    return P;
+}
+
+// body-frame vertex k
+__device__ __forceinline__ f3 poly_x(const Poly& P, int k) {
+    if (P.hull) return f3{P.s * __ldg(P.v + 3 * k), P.s * __ldg(P.v + 3 * k + 1), P.s * __ldg(P.v + 3 * k + 2)};
+    return f3{(k & 1) ? P.h0 : -P.h0, (k & 2) ? P.h1 : -P.h1, (k & 4) ? P.h2 : -P.h2};
+}
+
+// body-frame face plane f: outward unit normal, offset
+__device__ __forceinline__ float4 poly_plane(const Poly& P, int f) {
+    if (P.hull) {
+        const float4 q = __ldg(P.pl + f);
+        return make_float4(q.x, q.y, q.z, P.s * q.w);
+    }
+    const int ax = f >> 1;
+    const float sg = (f & 1) ? -1.0f : 1.0f;
+    return make_float4(ax == 0 ? sg : 0.0f, ax == 1 ? sg : 0.0f, ax == 2 ? sg : 0.0f,
+                       ax == 0 ? P.h0 : (ax == 1 ? P.h1 : P.h2));
+}
+
+// vertex k of face f's loop, -1 past its end
+__device__ __forceinline__ int poly_loop(const Poly& P, int f, int k) {
+    if (P.hull) return k < 3 ? __ldg(P.tri + 3 * f + k) : -1;
+    return kBoxLoop[4 * f + k];
+}
+
+__device__ __forceinline__ f3 poly_world(const Bodies& S, int i, const Poly& P, int k) {
+    return add3(rmul(S, i, poly_x(P, k)), ldpos(S, i));
+}
+
+// Warp-wide maximum (minimum) of (value, index) pairs, the lowest index
+// among equal values; lanes without a candidate hold index -1.
+__device__ __forceinline__ void warp_best(float& v, int& k, bool want_max) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, v, o);
+        const int ok = __shfl_xor_sync(kFull, k, o);
+        const bool better = want_max ? ov > v : ov < v;
+        if (ok >= 0 && (k < 0 || better || (ov == v && ok < k))) {
+            v = ov;
+            k = ok;
+        }
+    }
+}
+
+// Largest separation of polytope b from polytope a along a's face normals,
+// sep_f = (min_v m . x_v + n . (p_b - p_a)) - offset_f with n = R_a n_f and
+// m = R_b^T n, and its face (the first on ties).  Whole warp.
+__device__ __noinline__ float warp_face_separation(const Bodies& S, int a, const Poly& Pa, int b, const Poly& Pb,
+                                                   int& face) {
+    const int lane = threadIdx.x & 31;
+    const f3 d = sub3(ldpos(S, b), ldpos(S, a));
+    float best = 0.0f;
+    int bf = -1;
+    for (int f = lane; f < Pa.nf; f += 32) {
+        const float4 pl = poly_plane(Pa, f);
+        const f3 n = rmul(S, a, f3{pl.x, pl.y, pl.z});
+        const f3 m = rtmul(S, b, n);
+        float lo = dot3(m, poly_x(Pb, 0));
+#pragma unroll 1
+        for (int v = 1; v < Pb.nv; v++) {
+            const float t = dot3(m, poly_x(Pb, v));
+            if (t < lo) lo = t;
+        }
+        const float sep = (lo + dot3(n, d)) - pl.w;
+        if (bf < 0 || sep > best) {
+            best = sep;
+            bf = f;
+        }
+    }
+    warp_best(best, bf, true);
+    face = bf;
+    return best;
+}
+
+// Contacts of polytope pair (i, j), i < j (see the oracle's reading):
+// reference face of the larger separation (i's unless j's is larger by more
+// than 1e-5 m), incident face of the other body (least n_g . n_ref, the
+// first on ties), the incident loop clipped by the reference face's side
+// planes, and each clipped point whose distance above the reference plane
+// is below the margin, in order: normal n_ref from j to i, point the clipped
+// point (at most 8 points are kept: rounding on nearly collinear points
+// could add some to a convex polygon).  The warp works the face searches;
+// lane 0 clips and, with kWrite,
+// writes the contacts from index base.  Returns the contact count (every
+// lane).
+template <bool kWrite>
+__device__ __noinline__ int polytope_pair(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int i, int j,
+                                          float margin, int base, int cmax, bool& ovf) {
+    const int lane = threadIdx.x & 31;
+    const Poly Pi = poly_of(bt, S, b0, i), Pj = poly_of(bt, S, b0, j);
+    if (Pi.nv == 0 || Pi.nf == 0 || Pj.nv == 0 || Pj.nf == 0) return 0;   // an empty mesh has no contacts
+    int fi, fj;
+    const float si = warp_face_separation(S, i, Pi, j, Pj, fi);
+    const float sj = warp_face_separation(S, j, Pj, i, Pi, fj);
+    const bool ref_j = sj > si + 1e-5f;
+    if (!((ref_j ? sj : si) < margin)) return 0;
+    const int r = ref_j ? j : i, q = ref_j ? i : j, fr = ref_j ? fj : fi;
+    const Poly& Pr = ref_j ? Pj : Pi;
+    const Poly& Pq = ref_j ? Pi : Pj;
+    const float4 plr = poly_plane(Pr, fr);
+    const f3 nr = rmul(S, r, f3{plr.x, plr.y, plr.z});
+    float lo = 0.0f;
+    int fq = -1;
+    for (int g = lane; g < Pq.nf; g += 32) {
+        const float4 pg = poly_plane(Pq, g);
+        const float t = dot3(rmul(S, q, f3{pg.x, pg.y, pg.z}), nr);
+        if (fq < 0 || t < lo) {
+            lo = t;
+            fq = g;
+        }
+    }
+    warp_best(lo, fq, false);
+    int cnt = 0;
+    if (lane == 0) {
+        f3 poly[2][8];
+        int np = 0, cur = 0;
+        for (int k = 0; k < 4; k++) {
+            const int v = poly_loop(Pq, fq, k);
+            if (v < 0) break;
+            poly[0][np++] = poly_world(S, q, Pq, v);
+        }
+        const int nloop = poly_loop(Pr, fr, 3) >= 0 ? 4 : 3;
+        for (int e = 0; e < nloop && np > 0; e++) {
+            const f3 va = poly_world(S, r, Pr, poly_loop(Pr, fr, e));
+            const f3 vb = poly_world(S, r, Pr, poly_loop(Pr, fr, (e + 1) % nloop));
+            const f3 sn = cross3(sub3(vb, va), nr);
+            const float so = dot3(sn, va);
+            int no = 0;
+            for (int k = 0; k < np; k++) {
+                const f3 P0 = poly[cur][k], P1 = poly[cur][(k + 1) % np];
+                const float dp = dot3(sn, P0) - so, dq = dot3(sn, P1) - so;
+                if (dp <= 0.0f && no < 8) poly[cur ^ 1][no++] = P0;
+                if ((dp <= 0.0f) != (dq <= 0.0f) && no < 8) {
+                    const float t = dp / (dp - dq);
+                    poly[cur ^ 1][no++] = f3{P0.x + t * (P1.x - P0.x), P0.y + t * (P1.y - P0.y),
+                                             P0.z + t * (P1.z - P0.z)};
+                }
+            }
+            np = no;
+            cur ^= 1;
+        }
+        const float off = dot3(nr, poly_world(S, r, Pr, poly_loop(Pr, fr, 0)));
+        const f3 n = ref_j ? nr : f3{-nr.x, -nr.y, -nr.z};
+        for (int k = 0; k < np; k++) {
+            const float dd = dot3(nr, poly[cur][k]) - off;
+            if (dd < margin) {
+                if (kWrite) {
+                    if (base + cnt < cmax) put_contact(C, base + cnt, i, j, n, poly[cur][k], dd);
+                    else ovf = true;
+                }
+                cnt++;
+            }
+        }
+    }
+    return __shfl_sync(kFull, cnt, 0);
+}
+
+// One hull unit (code: i | j << 16, j = 0xffff for hull i on the plane) by
+// a warp: its contact count, and with kWrite its contacts from index base.
+template <bool kWrite>
+__device__ __noinline__ int hull_unit(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int code,
+                                      float margin, int base, int cmax, bool& ovf) {
+    const int lane = threadIdx.x & 31;
+    const int i = code & 0xffff, j = (code >> 16) & 0xffff;
+    if (j == 0xffff) {   // the hull's vertices below the margin
+        const Poly P = poly_of(bt, S, b0, i);
+        const f3 up{0.0f, 0.0f, 1.0f};
+        int cnt = 0;
+        for (int k0 = 0; k0 < P.nv; k0 += 32) {
+            const int k = k0 + lane;
+            f3 w{0.0f, 0.0f, 0.0f};
+            bool hit = false;
+            if (k < P.nv) {
+                w = poly_world(S, i, P, k);
+                hit = w.z < margin;
+            }
+            const unsigned m = __ballot_sync(kFull, hit);
+            if (kWrite && hit) {
+                const int idx = base + cnt + __popc(m & ((1u << lane) - 1u));
+                if (idx < cmax) put_contact(C, idx, i, -1, up, w, w.z);
+                else ovf = true;
+            }
+            cnt += __popc(m);
+        }
+        return cnt;
+    }
+    const bool sphere_j = S.TYPE(j) != kShapeHull && S.TYPE(j) != kShapeBox;
+    const bool sphere_i = S.TYPE(i) != kShapeHull && S.TYPE(i) != kShapeBox;
+    if (!sphere_i && !sphere_j) return polytope_pair<kWrite>(bt, S, C, b0, i, j, margin, base, cmax, ovf);
+    // a sphere's centre against the hull's deepest face
+    const int sp = sphere_j ? j : i, hb = sphere_j ? i : j;
+    const Poly P = poly_of(bt, S, b0, hb);
+    if (P.nf == 0) return 0;   // an empty mesh has no contacts
+    const f3 c = ldpos(S, sp);
+    const f3 x = rtmul(S, hb, sub3(c, ldpos(S, hb)));
+    float D = 0.0f;
+    int f = -1;
+    for (int g = lane; g < P.nf; g += 32) {
+        const float4 pl = poly_plane(P, g);
+        const float dd = dot3(f3{pl.x, pl.y, pl.z}, x) - pl.w;
+        if (f < 0 || dd > D) {
+            D = dd;
+            f = g;
+        }
+    }
+    warp_best(D, f, true);
+    const float d = D - S.D(0, sp);
+    if (!(d < margin)) return 0;
+    if (kWrite && lane == 0) {
+        const float4 pl = poly_plane(P, f);
+        f3 nb = rmul(S, hb, f3{pl.x, pl.y, pl.z});
+        const f3 pt{c.x - nb.x * D, c.y - nb.y * D, c.z - nb.z * D};
+        if (sphere_j) nb = f3{-nb.x, -nb.y, -nb.z};   // from the sphere (j) to the hull (i)
+        if (base < cmax) put_contact(C, base, i, j, nb, pt, d);
+        else ovf = true;
+    }
+    return 1;
+}
+
+// The hull contacts of a substep (see above), appended at nc: rounds of
+// kPairChunk candidate units (the N bodies, then the N (N - 1) / 2 pairs);
+// the round's units are listed in order (plist), each warp counts the
+// contacts of its units (pitem), a scan gives their first indices, and the
+// warps write them.  Whole CTA; plist and pitem are free at this point.
+__device__ __noinline__ void hull_pass(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int N,
+                                       int* plist, unsigned short* pitem, ScanBuf& wsum, float margin, bool plane,
+                                       int cmax, int& nc, bool& ovf) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int total = N + N * (N - 1) / 2;
+    constexpr int per = kPairChunk / kT;
+    for (int k0 = 0; k0 < total; k0 += kPairChunk) {
+        unsigned passmask = 0;
+        int npass = 0;
+        int codes[per];
+#pragma unroll
+        for (int r = 0; r < per; r++) {
+            const int u = k0 + tid * per + r;
+            codes[r] = 0;
+            if (u >= total) continue;
+            bool pass;
+            if (u < N) {
+                pass = plane && S.TYPE(u) == kShapeHull && S.P(2, u) - S.BR(u) < margin;
+                codes[r] = u | (0xffff << 16);
+            } else {
+                int i, j;
+                pair_of_index(u - N, N, i, j);
+                pass = (S.TYPE(i) == kShapeHull || S.TYPE(j) == kShapeHull) && broad(S, i, j, margin);
+                codes[r] = i | (j << 16);
+            }
+            if (pass) {
+                passmask |= 1u << r;
+                npass++;
+            }
+        }
+        int nu;
+        int o = block_excl_scan(npass, wsum, nu);
+#pragma unroll
+        for (int r = 0; r < per; r++)
+            if (passmask & (1u << r)) plist[o++] = codes[r];
+        __syncthreads();
+        for (int q = warp; q < nu; q += kT / 32) {
+            const int c = hull_unit<false>(bt, S, C, b0, plist[q], margin, 0, cmax, ovf);
+            if (lane == 0) pitem[q] = (unsigned short)min(c, 0xffff);
+        }
+        __syncthreads();
+        // first contact of each unit (counts and indices beyond the u16 range
+        // are past any contact capacity: those contacts overflow)
+        int sum = 0;
+#pragma unroll
+        for (int r = 0; r < per; r++) {
+            const int q = tid * per + r;
+            if (q < nu) sum += pitem[q];
+        }
+        int nct;
+        int run = block_excl_scan(sum, wsum, nct);
+#pragma unroll
+        for (int r = 0; r < per; r++) {
+            const int q = tid * per + r;
+            if (q < nu) {
+                const int c = pitem[q];
+                pitem[q] = (unsigned short)min(run, 0xffff);
+                run += c;
+            }
+        }
+        __syncthreads();
+        for (int q = warp; q < nu; q += kT / 32)
+            hull_unit<true>(bt, S, C, b0, plist[q], margin, nc + pitem[q], cmax, ovf);
+        nc += nct;
+        __syncthreads();   // plist and pitem are rewritten by the next round
+    }
+}
+
+// kFeat: the optional contact tests compiled in (kFeatEdges: box-box
+// edge-edge contacts, kFeatHulls: hull contacts); sc.edges and sc.hulls
+// decide at run time.  Without them the code is left out, and its register
+// pressure.
+template <int kFeat>
 __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, const float* __restrict__ force, int slot0,
                                      int smem_per_env, int NB) {
     const SimConst& sc = b.sc;
@@ -810,13 +1156,14 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                         : S.D(0, i);
     }
     __syncthreads();
+    const bool hulls = (kFeat & kFeatHulls) && sc.hulls;
     // plane contact items in canonical order, fixed for the launch (shapes
     // do not change): one per sphere, the eight corners of a box in sign-bit
     // order, bodies in order
     int nplane = 0;
     for (int i0 = 0; i0 < N; i0 += kT) {
         const int i = i0 + tid;
-        const int nsub = i < N ? (is_box(S, i) ? 8 : 1) : 0;
+        const int nsub = i < N ? (is_box(S, i) ? 8 : (hulls && S.TYPE(i) == kShapeHull ? 0 : 1)) : 0;
         int tot;
         const int ex = block_excl_scan(nsub, wsum, tot);
         for (int k = 0; k < nsub; k++) ptab[nplane + ex + k] = (unsigned short)((i << 3) | k);
@@ -826,7 +1173,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
     bool ovf = false;
     int nc = 0;
     const float h = sc.h;
-    const bool edges = kEdges && sc.edges;
+    const bool edges = (kFeat & kFeatEdges) && sc.edges;
     const int kBoxItems = edges ? 17 : 16;   // narrow-phase items of a box-box pair
     const int npairs = N * (N - 1) / 2;
     const f3 up{0.0f, 0.0f, 1.0f};
@@ -912,7 +1259,9 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                     int i = pi, j = pj;
                     for (int r = 0; r < per; r++) {
                         if (kbeg + r < npairs) {
-                            if (broad(S, i, j, sc.margin)) {
+                            // pairs with a hull come after all others (hull_pass)
+                            if (!(hulls && (S.TYPE(i) == kShapeHull || S.TYPE(j) == kShapeHull)) &&
+                                broad(S, i, j, sc.margin)) {
                                 passmask |= 1u << r;
                                 npass++;
                                 nsub += (is_box(S, i) && is_box(S, j)) ? kBoxItems : 1;
@@ -964,13 +1313,13 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                         i = pr & 0xffff;
                         j = pr >> 16;
                         const int sub = u - pitem[lo];
-                        if (kEdges && sub == 16 && lo < nedge_slots) {   // a box pair's edge test, computed above
+                        if ((kFeat & kFeatEdges) && sub == 16 && lo < nedge_slots) {   // a box pair's edge test, computed above
                             const float4 e0 = edge_slots[2 * lo], e1 = edge_slots[2 * lo + 1];
                             n = f3{e0.x, e0.y, e0.z};
                             d = e0.w;
                             pt = f3{e1.x, e1.y, e1.z};
                             hit = e1.w != 0.0f;
-                        } else if (kEdges && sub == 16) {
+                        } else if ((kFeat & kFeatEdges) && sub == 16) {
                             hit = box_edge_edge(S, i, j, sc.margin, n, pt, d);
                         } else {
                             hit = pair_test(S, i, j, sub, sc.margin, n, pt, d);
@@ -985,6 +1334,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                     nc += t2;
                 }
             }
+            if (hulls) hull_pass(b, S, C, b0, N, plist, pitem, wsum, sc.margin, sc.plane != 0, cmax, nc, ovf);
             if (nc > cmax) nc = cmax;
 
             if (nc <= C.cap) solve_substep(SmemContacts{C.s}, S, qcnt, lists, wsum, nc, N, NB, sc, h);
@@ -1047,7 +1397,7 @@ __device__ __forceinline__ void load_desc(DevBatch& dst, const DevBatch& src) {
 }
 
 // Single batch: CTA e steps environment e.
-template <bool kEdges>
+template <int kFeat>
 __global__ void __launch_bounds__(kT, kMinCtas) sim_kernel(DevBatch b0, SimConst sc0, int nsteps,
                                                     const float* __restrict__ force, int slot0, int smem_per_env,
                                                     int NB) {
@@ -1056,12 +1406,12 @@ __global__ void __launch_bounds__(kT, kMinCtas) sim_kernel(DevBatch b0, SimConst
     __syncthreads();
     if (threadIdx.x == 0) sb.sc = sc0;
     __syncthreads();
-    sim_env<kEdges>(sb, blockIdx.x, nsteps, force, slot0, smem_per_env, NB);
+    sim_env<kFeat>(sb, blockIdx.x, nsteps, force, slot0, smem_per_env, NB);
 }
 
 // Work list over several batches: persistent CTAs pull (batch, environment,
 // pose slot) items from an atomic counter; one step each.
-template <bool kEdges>
+template <int kFeat>
 __global__ void __launch_bounds__(kT, kMinCtas) sim_list_kernel(const DevBatch* __restrict__ descs,
                                                          const int2* __restrict__ items, int nitems, int* counter,
                                                          const float* __restrict__ force, int smem_per_env, int NB,
@@ -1079,7 +1429,7 @@ __global__ void __launch_bounds__(kT, kMinCtas) sim_list_kernel(const DevBatch* 
         const int2 it = items[item];
         load_desc(sb, descs[it.x & kItemDescMask]);
         __syncthreads();
-        sim_env<kEdges>(sb, it.y, 1, force, (it.x >> 24) & 1, smem_per_env, NB);
+        sim_env<kFeat>(sb, it.y, 1, force, (it.x >> 24) & 1, smem_per_env, NB);
         __syncthreads();  // everyone is done with sb and s_item
     }
     if (threadIdx.x == 0) sm_gate_release(gate, s_gate);
@@ -1101,10 +1451,12 @@ int phys_smem_bytes_default(int max_bodies, int mcpb) {
     size_t fixed = phys_fixed_bytes(max_bodies, mcpb * max_bodies);
     // room for 4.5 contacts per body in shared memory (a settled pile of
     // spheres and boxes has about 3.5), less the plane item table's 16 bytes
-    // per body; more spill to global memory.  With 32 bodies this is 31 KB,
-    // so 7 environments fit on one SM, with a few hundred bytes to spare: the
-    // kernels' static shared memory (the batch descriptor) must not grow
-    size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2) - (size_t)16 * max_bodies;
+    // per body and 64 bytes; more spill to global memory.  With 32 bodies
+    // this is 31,728 bytes (140 records), so that with the kernels' static
+    // shared memory (the 472-byte batch descriptor) rounded up to the
+    // allocation unit 7 environments fit on one SM: the descriptor must not
+    // grow by more than 48 bytes
+    size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2) - (size_t)16 * max_bodies - 64;
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;
     return (int)align16(want);
@@ -1112,23 +1464,28 @@ int phys_smem_bytes_default(int max_bodies, int mcpb) {
 
 int sim_ctas_per_sm(int smem_per_env) {
     int n = 0;
-    // both variants have the same launch bounds (registers) and shared memory
-    cudaFuncSetAttribute(sim_list_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
-    cudaFuncSetAttribute(sim_list_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    // every variant has the same launch bounds (registers) and shared memory
+    cudaFuncSetAttribute(sim_list_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_env);
+    cudaFuncSetAttribute(sim_list_kernel<0>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_list_kernel<false>, kT, smem_per_env) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_list_kernel<0>, kT, smem_per_env) != cudaSuccess)
         n = 1;
     return n > 0 ? n : 1;
 }
 
 CtaFootprint sim_list_footprint(int smem_per_env) {
-    cudaFuncAttributes fa{};
-    cudaFuncAttributes fe{};
-    if (cudaFuncGetAttributes(&fa, sim_list_kernel<false>) != cudaSuccess ||
-        cudaFuncGetAttributes(&fe, sim_list_kernel<true>) != cudaSuccess)
+    cudaFuncAttributes fa[4]{};
+    if (cudaFuncGetAttributes(&fa[0], sim_list_kernel<0>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa[1], sim_list_kernel<1>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa[2], sim_list_kernel<2>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa[3], sim_list_kernel<3>) != cudaSuccess)
         return CtaFootprint{kT, 255, 227 * 1024};
-    return CtaFootprint{kT, max(fa.numRegs, fe.numRegs),
-                        (int)max(fa.sharedSizeBytes, fe.sharedSizeBytes) + smem_per_env};
+    int regs = 0, smem = 0;
+    for (const cudaFuncAttributes& a : fa) {
+        regs = max(regs, a.numRegs);
+        smem = max(smem, (int)a.sharedSizeBytes);
+    }
+    return CtaFootprint{kT, regs, smem + smem_per_env};
 }
 
 template <class K>
@@ -1140,20 +1497,37 @@ static cudaError_t prepare(K kernel, int smem_per_env) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
-cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
-                             int smem_per_env, int max_bodies, const float* force, SmGate gate, bool edges,
-                             cudaStream_t stream) {
-    if (nitems == 0) return cudaSuccess;
-    cudaError_t e = edges ? prepare(sim_list_kernel<true>, smem_per_env) : prepare(sim_list_kernel<false>, smem_per_env);
+template <int kFeat>
+static cudaError_t launch_items_t(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
+                                  int smem_per_env, int max_bodies, const float* force, SmGate gate,
+                                  cudaStream_t stream) {
+    cudaError_t e = prepare(sim_list_kernel<kFeat>, smem_per_env);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    if (edges)
-        sim_list_kernel<true><<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force, smem_per_env,
-                                                                  max_bodies, gate);
-    else
-        sim_list_kernel<false><<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force,
-                                                                   smem_per_env, max_bodies, gate);
+    sim_list_kernel<kFeat><<<grid, kT, smem_per_env, stream>>>(descs, items, nitems, counter, force, smem_per_env,
+                                                               max_bodies, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sim_items(const DevBatch* descs, const int2* items, int nitems, int* counter, int grid,
+                             int smem_per_env, int max_bodies, const float* force, SmGate gate, int feat,
+                             cudaStream_t stream) {
+    if (nitems == 0) return cudaSuccess;
+    switch (feat & (kFeatEdges | kFeatHulls)) {
+        case 0: return launch_items_t<0>(descs, items, nitems, counter, grid, smem_per_env, max_bodies, force, gate, stream);
+        case 1: return launch_items_t<1>(descs, items, nitems, counter, grid, smem_per_env, max_bodies, force, gate, stream);
+        case 2: return launch_items_t<2>(descs, items, nitems, counter, grid, smem_per_env, max_bodies, force, gate, stream);
+        default: return launch_items_t<3>(descs, items, nitems, counter, grid, smem_per_env, max_bodies, force, gate, stream);
+    }
+}
+
+template <int kFeat>
+static cudaError_t launch_env_t(const DevBatch& b, const SimConst& sc, int nsteps, const float* force, int slot0,
+                                int smem_per_env, int max_bodies, cudaStream_t stream) {
+    cudaError_t e = prepare(sim_kernel<kFeat>, smem_per_env);
+    if (e != cudaSuccess) return e;
+    sim_kernel<kFeat><<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
     return cudaGetLastError();
 }
 
@@ -1162,13 +1536,12 @@ cudaError_t launch_sim(const DevBatch& b, const SimConst& sc, int nsteps, const 
     if (b.E == 0 || nsteps == 0) return cudaSuccess;
     size_t fixed = phys_fixed_bytes(max_bodies, sc.mcpb * max_bodies);
     if ((size_t)smem_per_env < fixed) smem_per_env = (int)fixed;
-    cudaError_t e = sc.edges ? prepare(sim_kernel<true>, smem_per_env) : prepare(sim_kernel<false>, smem_per_env);
-    if (e != cudaSuccess) return e;
-    if (sc.edges)
-        sim_kernel<true><<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
-    else
-        sim_kernel<false><<<b.E, kT, smem_per_env, stream>>>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies);
-    return cudaGetLastError();
+    switch (sim_features(sc)) {
+        case 0: return launch_env_t<0>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies, stream);
+        case 1: return launch_env_t<1>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies, stream);
+        case 2: return launch_env_t<2>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies, stream);
+        default: return launch_env_t<3>(b, sc, nsteps, force, slot0, smem_per_env, max_bodies, stream);
+    }
 }
 
 VUDA_SIM_NS_END

@@ -297,13 +297,13 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
                j->env->bin_limit == tiled_default_bin_limit();
     };
     int max_bodies = 1, max_mcpb = 1, max_w = 1, max_h = 1;
-    bool any_edges = false;   // a job of the batch has box-box edge contacts: the physics variant with them
+    int any_feat = 0;   // optional contact tests of any job of the batch: the physics variant with them
     size_t nsim = 0, nshade = 0, ntj = 0;
     for (auto& pr : batch) {
         Job* j = pr.first;
         max_bodies = std::max(max_bodies, j->env->max_bodies);
         max_mcpb = std::max(max_mcpb, j->params.max_contacts_per_body);
-        any_edges = any_edges || j->params.edge_contacts != 0;
+        any_feat |= sim_features(j->env->sc);
         nsim += j->env->E;
         if (tiled(j)) {
             ntj++;
@@ -423,9 +423,9 @@ bool launch_iteration(vuda_server* s, const std::vector<std::pair<Job*, uint64_t
         lane++;
         const int2* items = si.d + cls[k].off;
         e = cls[k].wide ? wide::launch_sim_items(s->descs, items, (int)cls[k].n, s->counters + 2 + k, cls[k].grid,
-                                                 cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_edges, cs)
+                                                 cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_feat, cs)
                         : launch_sim_items(s->descs, items, (int)cls[k].n, s->counters + 2 + k, cls[k].grid,
-                                           cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_edges, cs);
+                                           cls[k].smem, cls[k].nb, nullptr, SmGate{nullptr, 0}, any_feat, cs);
     }
     for (int q = 0; q < 2 && fork && e == cudaSuccess; q++) {
         if (!used[q]) continue;

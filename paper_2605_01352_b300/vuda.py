@@ -37,7 +37,7 @@ class SimParams(C.Structure):
                 ("gravity", C.c_float * 3), ("restitution", C.c_float), ("restitution_threshold", C.c_float),
                 ("friction", C.c_float), ("baumgarte", C.c_float), ("slop", C.c_float), ("margin", C.c_float),
                 ("jacobi_omega", C.c_float), ("plane", C.c_int32), ("max_contacts_per_body", C.c_int32),
-                ("gyroscopic", C.c_int32), ("edge_contacts", C.c_int32)]
+                ("gyroscopic", C.c_int32), ("edge_contacts", C.c_int32), ("hull_contacts", C.c_int32)]
 
 
 class Scene(C.Structure):
@@ -181,7 +181,8 @@ def _stream(s):
 def sim_params(p) -> SimParams:
     return SimParams(p.dt, p.substeps, p.iterations, (C.c_float * 3)(*p.gravity), p.restitution,
                      p.restitution_threshold, p.friction, p.baumgarte, p.slop, p.margin, p.jacobi_omega,
-                     p.plane, p.max_contacts_per_body, p.gyroscopic, p.edge_contacts)
+                     p.plane, p.max_contacts_per_body, p.gyroscopic, p.edge_contacts,
+                     getattr(p, "hull_contacts", 0))
 
 
 def scene_struct(scene):

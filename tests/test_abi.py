@@ -102,3 +102,19 @@ def test_noalloc_rejects_a_missing_body_bound_without_gpu(built):
     # an empty batch needs no bound and launches nothing
     assert vuda.lib.vuda_sim_step_noalloc(0, 0, 0, None, None, None, None, None, None, None, None, None, None,
                                           C.byref(prm), 1, None, None, None, 0, None) == vuda.OK
+
+
+def test_noalloc_refuses_hull_contacts_without_gpu(built):
+    """Hull contacts read the batch's meshes, which the allocation-free step
+    does not have: it refuses the option on the host."""
+    import ctypes as C
+    import dataclasses
+
+    from paper_2605_01352_b300 import scene as S
+    from paper_2605_01352_b300 import vuda
+    prm = vuda.sim_params(dataclasses.replace(S.SimParams(), hull_contacts=1))
+    fake = C.c_void_p(0x1000)   # never dereferenced: the call returns before any device work
+    st = vuda.lib.vuda_sim_step_noalloc(4, 32, 8, fake, fake, fake, fake, fake, fake, fake, fake, fake, None,
+                                        C.byref(prm), 1, fake, fake, fake, 0, None)
+    assert st == vuda.ERR_INVALID
+    assert b"hull" in vuda.lib.vuda_last_error()

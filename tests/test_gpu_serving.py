@@ -228,3 +228,28 @@ def test_cancelled_job_mid_batch_leaves_the_other_jobs_unchanged(V, monkeypatch)
     for k in ("A", "C"):
         assert got[k][0] == [0] * counts[k]
         _same_as_alone(V, jobs[k], counts[k], got[k])
+
+
+def test_hull_contact_job_in_a_mix_matches_the_oracle(V, orc):
+    """A job with hull contacts served in one launch with a job without them
+    (the work lists run the physics variant with hull contacts for both):
+    both match the oracle."""
+    import dataclasses
+    H = S.generate(6, 12, 91, kinds="mixed_hulls", hull_tris=(8, 24), n_hull_meshes=4, substeps=4)
+    H = dataclasses.replace(H, params=dataclasses.replace(H.params, hull_contacts=1))
+    st0, _, _ = orc.sim_step(H, 60)
+    H = dataclasses.replace(H, **{k: st0[k] for k in ("pos", "quat", "vel", "angvel")})
+    P = S.cfg1(4)
+    srv = V.Server(max_inflight=2)
+    jh, jp = srv.add_job(H), srv.add_job(P)
+    for _ in range(3):
+        srv.submit(jh)
+        srv.submit(jp)
+    res = srv.wait_all(6)
+    assert all(r["status"] == 0 for r in res)
+    for sc, j in ((H, jh), (P, jp)):
+        got = srv.job_env(j).get_state()
+        so, _, _ = orc.sim_step(sc, 3)
+        for f in ("pos", "vel", "quat", "angvel"):
+            np.testing.assert_allclose(got[f], so[f], rtol=1e-5, atol=1e-5)
+    srv.close()
