@@ -228,6 +228,9 @@ __device__ __forceinline__ f3 rcol(const Bodies& B, int i, int k) { return f3{B.
 // A's edge along a_k furthest towards B and B's edge along b_l furthest
 // towards A (segment closest points: s clamped, t from s and clamped, then s
 // from t and clamped if t was clamped).
+// (kCopy: one compiled copy per kernel variant, so that the register use of
+// the variant with hull contacts does not shape the copy of the other)
+template <int kCopy>
 __device__ __noinline__ bool box_edge_edge(const Bodies& B, int a, int b, float margin, f3& nout, f3& pt,
                                            float& d) {
     const f3 dp = sub3(ldpos(B, a), ldpos(B, b));
@@ -369,6 +372,7 @@ __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margi
 // each, into slots (2 float4 per pair: normal and distance, point and hit).
 // Out of line: it runs on few threads, and inlined into the pair round it
 // would raise that loop's register pressure.
+template <int kCopy>
 __device__ __noinline__ void edge_prepass(const Bodies& S, const int* plist, int w0, int w1, float4* slots,
                                           float margin) {
     for (int q = w0 + (int)threadIdx.x; q < w1; q += kT) {
@@ -377,7 +381,7 @@ __device__ __noinline__ void edge_prepass(const Bodies& S, const int* plist, int
         if (!(is_box(S, i) && is_box(S, j))) continue;
         f3 n{0.0f, 0.0f, 0.0f}, pt{0.0f, 0.0f, 0.0f};
         float d = 0.0f;
-        const bool h = box_edge_edge(S, i, j, margin, n, pt, d);
+        const bool h = box_edge_edge<kCopy>(S, i, j, margin, n, pt, d);
         slots[2 * (q - w0)] = make_float4(n.x, n.y, n.z, d);
         slots[2 * (q - w0) + 1] = make_float4(pt.x, pt.y, pt.z, h ? 1.0f : 0.0f);
     }
@@ -851,9 +855,23 @@ __device__ __noinline__ float warp_face_separation(const Bodies& S, int a, const
         const float4 pl = poly_plane(Pa, f);
         const f3 n = rmul(S, a, f3{pl.x, pl.y, pl.z});
         const f3 m = rtmul(S, b, n);
+        // the minimum does not depend on the order of the vertices: four
+        // vertices' loads are issued together
         float lo = dot3(m, poly_x(Pb, 0));
+        int v = 1;
 #pragma unroll 1
-        for (int v = 1; v < Pb.nv; v++) {
+        for (; v + 4 <= Pb.nv; v += 4) {
+            f3 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) x[u] = poly_x(Pb, v + u);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const float t = dot3(m, x[u]);
+                if (t < lo) lo = t;
+            }
+        }
+#pragma unroll 1
+        for (; v < Pb.nv; v++) {
             const float t = dot3(m, poly_x(Pb, v));
             if (t < lo) lo = t;
         }
@@ -875,87 +893,125 @@ __device__ __noinline__ float warp_face_separation(const Bodies& S, int a, const
 // planes, and each clipped point whose distance above the reference plane
 // is below the margin, in order: normal n_ref from j to i, point the clipped
 // point (at most 8 points are kept: rounding on nearly collinear points
-// could add some to a convex polygon).  The warp works the face searches;
-// lane 0 clips and, with kWrite,
+// could add some to a convex polygon).  The warp works the face searches
+// and the clipping, and with kWrite
 // writes the contacts from index base.  Returns the contact count (every
 // lane).
 template <bool kWrite>
 __device__ __noinline__ int polytope_pair(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int i, int j,
-                                          float margin, int base, int cmax, bool& ovf) {
+                                          float margin, int base, int cmax, bool& ovf, int* meta) {
     const int lane = threadIdx.x & 31;
     const Poly Pi = poly_of(bt, S, b0, i), Pj = poly_of(bt, S, b0, j);
     if (Pi.nv == 0 || Pi.nf == 0 || Pj.nv == 0 || Pj.nf == 0) return 0;   // an empty mesh has no contacts
-    int fi, fj;
-    const float si = warp_face_separation(S, i, Pi, j, Pj, fi);
-    const float sj = warp_face_separation(S, j, Pj, i, Pi, fj);
-    const bool ref_j = sj > si + 1e-5f;
-    if (!((ref_j ? sj : si) < margin)) return 0;
-    const int r = ref_j ? j : i, q = ref_j ? i : j, fr = ref_j ? fj : fi;
+    // the face searches of the counting pass are kept (meta: ref_j | fr << 1
+    // | fq << 16, or -1 without contacts) and reused by the writing pass
+    bool ref_j;
+    int fr, fq;
+    if (kWrite && meta) {
+        const int mt = *meta;
+        if (mt < 0) return 0;
+        ref_j = mt & 1;
+        fr = (mt >> 1) & 0x7fff;
+        fq = mt >> 16;
+    } else {
+        int fi, fj;
+        const float si = warp_face_separation(S, i, Pi, j, Pj, fi);
+        const float sj = warp_face_separation(S, j, Pj, i, Pi, fj);
+        ref_j = sj > si + 1e-5f;
+        if (!((ref_j ? sj : si) < margin)) {
+            if (meta && lane == 0) *meta = -1;
+            return 0;
+        }
+        fr = ref_j ? fj : fi;
+        fq = -1;
+    }
+    const int r = ref_j ? j : i, q = ref_j ? i : j;
     const Poly& Pr = ref_j ? Pj : Pi;
     const Poly& Pq = ref_j ? Pi : Pj;
     const float4 plr = poly_plane(Pr, fr);
     const f3 nr = rmul(S, r, f3{plr.x, plr.y, plr.z});
-    float lo = 0.0f;
-    int fq = -1;
-    for (int g = lane; g < Pq.nf; g += 32) {
-        const float4 pg = poly_plane(Pq, g);
-        const float t = dot3(rmul(S, q, f3{pg.x, pg.y, pg.z}), nr);
-        if (fq < 0 || t < lo) {
-            lo = t;
-            fq = g;
-        }
-    }
-    warp_best(lo, fq, false);
-    int cnt = 0;
-    if (lane == 0) {
-        f3 poly[2][8];
-        int np = 0, cur = 0;
-        for (int k = 0; k < 4; k++) {
-            const int v = poly_loop(Pq, fq, k);
-            if (v < 0) break;
-            poly[0][np++] = poly_world(S, q, Pq, v);
-        }
-        const int nloop = poly_loop(Pr, fr, 3) >= 0 ? 4 : 3;
-        for (int e = 0; e < nloop && np > 0; e++) {
-            const f3 va = poly_world(S, r, Pr, poly_loop(Pr, fr, e));
-            const f3 vb = poly_world(S, r, Pr, poly_loop(Pr, fr, (e + 1) % nloop));
-            const f3 sn = cross3(sub3(vb, va), nr);
-            const float so = dot3(sn, va);
-            int no = 0;
-            for (int k = 0; k < np; k++) {
-                const f3 P0 = poly[cur][k], P1 = poly[cur][(k + 1) % np];
-                const float dp = dot3(sn, P0) - so, dq = dot3(sn, P1) - so;
-                if (dp <= 0.0f && no < 8) poly[cur ^ 1][no++] = P0;
-                if ((dp <= 0.0f) != (dq <= 0.0f) && no < 8) {
-                    const float t = dp / (dp - dq);
-                    poly[cur ^ 1][no++] = f3{P0.x + t * (P1.x - P0.x), P0.y + t * (P1.y - P0.y),
-                                             P0.z + t * (P1.z - P0.z)};
-                }
-            }
-            np = no;
-            cur ^= 1;
-        }
-        const float off = dot3(nr, poly_world(S, r, Pr, poly_loop(Pr, fr, 0)));
-        const f3 n = ref_j ? nr : f3{-nr.x, -nr.y, -nr.z};
-        for (int k = 0; k < np; k++) {
-            const float dd = dot3(nr, poly[cur][k]) - off;
-            if (dd < margin) {
-                if (kWrite) {
-                    if (base + cnt < cmax) put_contact(C, base + cnt, i, j, n, poly[cur][k], dd);
-                    else ovf = true;
-                }
-                cnt++;
+    if (fq < 0) {
+        float lo = 0.0f;
+        for (int g = lane; g < Pq.nf; g += 32) {
+            const float4 pg = poly_plane(Pq, g);
+            const float t = dot3(rmul(S, q, f3{pg.x, pg.y, pg.z}), nr);
+            if (fq < 0 || t < lo) {
+                lo = t;
+                fq = g;
             }
         }
+        warp_best(lo, fq, false);
+        if (meta && lane == 0) *meta = (ref_j ? 1 : 0) | (fr << 1) | (fq << 16);
     }
-    return __shfl_sync(kFull, cnt, 0);
+    // Sutherland-Hodgman across the lanes: lane k holds point k of the
+    // polygon (k < np <= 8); per side plane each lane emits its point when
+    // inside and the crossing point of its edge (k, k + 1) when the edge
+    // crosses, at the positions of the sequential algorithm (ballot prefix
+    // counts; positions past 8 dropped), and lane j gathers emission j
+    const unsigned lt = (1u << lane) - 1u;
+    f3 P{0.0f, 0.0f, 0.0f};
+    int np = 0;
+    while (np < 4 && poly_loop(Pq, fq, np) >= 0) np++;
+    if (lane < np) P = poly_world(S, q, Pq, poly_loop(Pq, fq, lane));
+    const int nloop = poly_loop(Pr, fr, 3) >= 0 ? 4 : 3;
+    f3 RV{0.0f, 0.0f, 0.0f};   // lane e: vertex e of the reference loop
+    if (lane < nloop) RV = poly_world(S, r, Pr, poly_loop(Pr, fr, lane));
+    for (int e = 0; e < nloop && np > 0; e++) {
+        const int e1 = (e + 1) % nloop;
+        const f3 va{__shfl_sync(kFull, RV.x, e), __shfl_sync(kFull, RV.y, e), __shfl_sync(kFull, RV.z, e)};
+        const f3 vb{__shfl_sync(kFull, RV.x, e1), __shfl_sync(kFull, RV.y, e1), __shfl_sync(kFull, RV.z, e1)};
+        const f3 sn = cross3(sub3(vb, va), nr);
+        const float so = dot3(sn, va);
+        const int nxt = lane + 1 < np ? lane + 1 : 0;
+        const f3 P1{__shfl_sync(kFull, P.x, nxt), __shfl_sync(kFull, P.y, nxt), __shfl_sync(kFull, P.z, nxt)};
+        const bool live = lane < np;
+        const float dp = dot3(sn, P) - so, dq = dot3(sn, P1) - so;
+        const bool in0 = live && dp <= 0.0f;
+        const bool cross = live && ((dp <= 0.0f) != (dq <= 0.0f));
+        f3 I{0.0f, 0.0f, 0.0f};
+        if (cross) {
+            const float t = dp / (dp - dq);
+            I = f3{P.x + t * (P1.x - P.x), P.y + t * (P1.y - P.y), P.z + t * (P1.z - P.z)};
+        }
+        const unsigned bin = __ballot_sync(kFull, in0), bcr = __ballot_sync(kFull, cross);
+        const int pos = __popc(bin & lt) + __popc(bcr & lt);   // this lane's first emission
+        const int nout = min(8, __popc(bin) + __popc(bcr));
+        const bool emits = in0 || cross;
+        // emission j comes from the last emitting lane whose first emission is <= j
+        unsigned mine = 0u;
+#pragma unroll
+        for (int jj = 0; jj < 8; jj++) {
+            const unsigned m = __ballot_sync(kFull, emits && pos <= jj);
+            if (lane == jj) mine = m;
+        }
+        const int src = mine ? 31 - __clz(mine) : 0;
+        const int spos = __shfl_sync(kFull, pos, src);
+        const bool sin0 = __shfl_sync(kFull, in0 ? 1 : 0, src) != 0;
+        const f3 SP{__shfl_sync(kFull, P.x, src), __shfl_sync(kFull, P.y, src), __shfl_sync(kFull, P.z, src)};
+        const f3 SI{__shfl_sync(kFull, I.x, src), __shfl_sync(kFull, I.y, src), __shfl_sync(kFull, I.z, src)};
+        const bool first = lane == spos && sin0;   // the source's own point, else its crossing point
+        if (lane < nout) P = first ? SP : SI;
+        np = nout;
+    }
+    const float off = dot3(nr, f3{__shfl_sync(kFull, RV.x, 0), __shfl_sync(kFull, RV.y, 0),
+                                  __shfl_sync(kFull, RV.z, 0)});
+    const f3 n = ref_j ? nr : f3{-nr.x, -nr.y, -nr.z};
+    const float dd = dot3(nr, P) - off;
+    const bool hit = lane < np && dd < margin;
+    const unsigned bh = __ballot_sync(kFull, hit);
+    if (kWrite && hit) {
+        const int idx = base + __popc(bh & lt);
+        if (idx < cmax) put_contact(C, idx, i, j, n, P, dd);
+        else ovf = true;
+    }
+    return __popc(bh);
 }
 
 // One hull unit (code: i | j << 16, j = 0xffff for hull i on the plane) by
 // a warp: its contact count, and with kWrite its contacts from index base.
 template <bool kWrite>
 __device__ __noinline__ int hull_unit(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int code,
-                                      float margin, int base, int cmax, bool& ovf) {
+                                      float margin, int base, int cmax, bool& ovf, int* meta) {
     const int lane = threadIdx.x & 31;
     const int i = code & 0xffff, j = (code >> 16) & 0xffff;
     if (j == 0xffff) {   // the hull's vertices below the margin
@@ -982,7 +1038,7 @@ __device__ __noinline__ int hull_unit(const DevBatch& bt, const Bodies& S, const
     }
     const bool sphere_j = S.TYPE(j) != kShapeHull && S.TYPE(j) != kShapeBox;
     const bool sphere_i = S.TYPE(i) != kShapeHull && S.TYPE(i) != kShapeBox;
-    if (!sphere_i && !sphere_j) return polytope_pair<kWrite>(bt, S, C, b0, i, j, margin, base, cmax, ovf);
+    if (!sphere_i && !sphere_j) return polytope_pair<kWrite>(bt, S, C, b0, i, j, margin, base, cmax, ovf, meta);
     // a sphere's centre against the hull's deepest face
     const int sp = sphere_j ? j : i, hb = sphere_j ? i : j;
     const Poly P = poly_of(bt, S, b0, hb);
@@ -1019,8 +1075,8 @@ __device__ __noinline__ int hull_unit(const DevBatch& bt, const Bodies& S, const
 // contacts of its units (pitem), a scan gives their first indices, and the
 // warps write them.  Whole CTA; plist and pitem are free at this point.
 __device__ __noinline__ void hull_pass(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int N,
-                                       int* plist, unsigned short* pitem, ScanBuf& wsum, float margin, bool plane,
-                                       int cmax, int& nc, bool& ovf) {
+                                       int* plist, unsigned short* pitem, int* meta, int nmeta, ScanBuf& wsum,
+                                       float margin, bool plane, int cmax, int& nc, bool& ovf) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int total = N + N * (N - 1) / 2;
     constexpr int per = kPairChunk / kT;
@@ -1055,7 +1111,7 @@ __device__ __noinline__ void hull_pass(const DevBatch& bt, const Bodies& S, cons
             if (passmask & (1u << r)) plist[o++] = codes[r];
         __syncthreads();
         for (int q = warp; q < nu; q += kT / 32) {
-            const int c = hull_unit<false>(bt, S, C, b0, plist[q], margin, 0, cmax, ovf);
+            const int c = hull_unit<false>(bt, S, C, b0, plist[q], margin, 0, cmax, ovf, q < nmeta ? meta + q : nullptr);
             if (lane == 0) pitem[q] = (unsigned short)min(c, 0xffff);
         }
         __syncthreads();
@@ -1080,7 +1136,7 @@ __device__ __noinline__ void hull_pass(const DevBatch& bt, const Bodies& S, cons
         }
         __syncthreads();
         for (int q = warp; q < nu; q += kT / 32)
-            hull_unit<true>(bt, S, C, b0, plist[q], margin, nc + pitem[q], cmax, ovf);
+            hull_unit<true>(bt, S, C, b0, plist[q], margin, nc + pitem[q], cmax, ovf, q < nmeta ? meta + q : nullptr);
         nc += nct;
         __syncthreads();   // plist and pitem are rewritten by the next round
     }
@@ -1294,7 +1350,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                     // each, into the per-body list scratch (unused until the
                     // solve); the item pass reads them (pairs beyond the slots,
                     // in crowded rounds only, are tested by their item)
-                    edge_prepass(S, plist, 0, min(np, nedge_slots), edge_slots, sc.margin);
+                    edge_prepass<kFeat>(S, plist, 0, min(np, nedge_slots), edge_slots, sc.margin);
                     __syncthreads();
                 }
                 for (int u0 = 0; u0 < nitems; u0 += kT) {
@@ -1320,7 +1376,7 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                             pt = f3{e1.x, e1.y, e1.z};
                             hit = e1.w != 0.0f;
                         } else if ((kFeat & kFeatEdges) && sub == 16) {
-                            hit = box_edge_edge(S, i, j, sc.margin, n, pt, d);
+                            hit = box_edge_edge<kFeat>(S, i, j, sc.margin, n, pt, d);
                         } else {
                             hit = pair_test(S, i, j, sub, sc.margin, n, pt, d);
                         }
@@ -1334,7 +1390,11 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                     nc += t2;
                 }
             }
-            if (hulls) hull_pass(b, S, C, b0, N, plist, pitem, wsum, sc.margin, sc.plane != 0, cmax, nc, ovf);
+            // the per-body list area (cmax_nb ints, unused until the solve)
+            // keeps the hull units' face searches between the passes
+            if (hulls)
+                hull_pass(b, S, C, b0, N, plist, pitem, reinterpret_cast<int*>(lists), cmax_nb, wsum, sc.margin,
+                          sc.plane != 0, cmax, nc, ovf);
             if (nc > cmax) nc = cmax;
 
             if (nc <= C.cap) solve_substep(SmemContacts{C.s}, S, qcnt, lists, wsum, nc, N, NB, sc, h);
