@@ -136,6 +136,29 @@ def test_sliding_box_stopping_distance(orc):
     assert st["pos"][0, 0] == pytest.approx(v0 * v0 / (2 * mu * g), rel=0.03)
 
 
+@pytest.mark.parametrize("deg", [20.0, 35.0])
+def test_box_on_an_incline_sticks_or_slides(orc, deg):
+    """A flat box on the ground under gravity tilted by theta (the same as a
+    slope of angle theta): its four corner contacts hold it when tan theta
+    < mu (Coulomb static friction), and below the cone's edge it slides with
+    acceleration g (sin theta - mu cos theta)."""
+    th = math.radians(deg)
+    g = 9.81
+    sc = _one(dict(type="box", h=(0.1, 0.1, 0.02), pos=(0.0, 0.0, 0.02)),
+              gravity=(g * math.sin(th), 0.0, -g * math.cos(th)))
+    mu = sc.params.friction
+    st, _, cc = orc.sim_step(sc, 60, precision="f64")            # settle onto the corners
+    assert cc[0] == 4
+    st2, _, _ = orc.sim_step(sc, 120, state=st, precision="f64")  # 0.5 s more
+    t = 120 * sc.params.dt
+    if math.tan(th) < mu:
+        assert abs(st2["vel"][0, 0]) < 1e-3 and abs(st2["pos"][0, 0] - st["pos"][0, 0]) < 1e-3
+    else:
+        acc = g * (math.sin(th) - mu * math.cos(th))
+        assert (st2["vel"][0, 0] - st["vel"][0, 0]) / t == pytest.approx(acc, rel=0.02)
+    assert np.abs(st2["angvel"][:, 0]).max() < 1e-2          # it neither tips nor spins
+
+
 def _sphere_cloud(n, seed, spread=0.25, speed=1.0):
     rng = np.random.default_rng(seed)
     bodies = []
