@@ -1212,7 +1212,14 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
                         : S.D(0, i);
     }
     __syncthreads();
-    const bool hulls = (kFeat & kFeatHulls) && sc.hulls;
+    // hull contacts only where the environment has a hull (shapes do not
+    // change during the launch)
+    bool hulls = (kFeat & kFeatHulls) && sc.hulls;
+    if (kFeat & kFeatHulls) {
+        bool mine = false;
+        for (int i = tid; i < N; i += kT) mine = mine || S.TYPE(i) == kShapeHull;
+        hulls = __syncthreads_or(hulls && mine) != 0;
+    }
     // plane contact items in canonical order, fixed for the launch (shapes
     // do not change): one per sphere, the eight corners of a box in sign-bit
     // order, bodies in order
