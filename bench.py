@@ -457,7 +457,7 @@ def rollout_bench(V, S, E: int, steps: int, warmup: int, settle: int) -> dict:
             envs = [V.Env(sc) for sc in scenes]
             rings = [[e.alloc_frame(triid=False), e.alloc_frame(triid=False)] for e in envs]
             forces = [torch.zeros((3, e.B), dtype=torch.float32, device="cuda") for e in envs]
-            pols = [MLPPolicy(sc, hidden, seed=3 + g) for g, sc in enumerate(scenes)]
+            pols = [MLPPolicy(envs[g], sc, hidden, seed=3 + g) for g, sc in enumerate(scenes)]
             for e, r in zip(envs, rings):
                 e.pipeline_run(settle, r)
             for g in range(2):     # one CUDA graph per group and frame slot

@@ -375,6 +375,21 @@ vuda_status vuda_rollout_run(vuda_env_t g0, vuda_env_t g1, int32_t nsteps, const
                              const vuda_frame* ring1, float* force0, float* force1, vuda_policy_fn policy,
                              void* user, vuda_stream_t stream, vuda_timing* timing);
 
+/* Pooled observation of a rendered frame, for a policy acting between steps
+ * (the action generator of the RL rollout reads it; the paper has no
+ * counterpart: its policies read the Vulkan images).  Each camera's image is
+ * cut into cells x cells equal cells; a cell gives its mean view depth times
+ * depth_scale and its mean luminance (0.299 r + 0.587 g + 0.114 b) / 255,
+ * each summed over the cell's pixels row by row.  out (device, E x 2 C_e
+ * cells^2 floats, C_e the cameras per environment) holds per environment
+ * the depth means of its cameras in order (cells row-major), then the
+ * luminance means in the same order.  Every environment must have the same
+ * number of cameras and every camera a width and height divisible by cells
+ * (1 <= cells <= 64), and frame its rgb and depth buffers, else
+ * VUDA_ERR_INVALID.  Async on stream (capturable). */
+vuda_status vuda_observe(vuda_env_t env, const vuda_frame* frame, int32_t cells, float depth_scale, float* out,
+                         vuda_stream_t stream);
+
 /* Block until all work enqueued by this handle on the sim (phase 0) or
  * render (phase 1) stream has finished (wait_step / wait_render, Table 1). */
 vuda_status vuda_wait(vuda_env_t env, int32_t phase);

@@ -1433,6 +1433,23 @@ vuda_status vuda_pipeline_run_host(vuda_env_t env, int32_t nsteps, const float* 
     return pipeline(env, nsteps, ring, stream, timing, h_force, force_per_step, h_rgb, h_depth);
 }
 
+vuda_status vuda_observe(vuda_env_t env, const vuda_frame* frame, int32_t cells, float depth_scale, float* out,
+                         vuda_stream_t stream) {
+    if (!env || !frame || !out) return invalid("null argument");
+    if (!frame->rgb || !frame->depth) return invalid("the frame needs its rgb and depth buffers");
+    if (cells < 1 || cells > 64) return invalid("cells must be in 1..64");
+    if (env->E == 0) return VUDA_OK;
+    if (env->C % env->E != 0) return invalid("every environment must have the same number of cameras");
+    const int cpe = env->C / env->E;
+    for (int c = 0; c < env->C; c++) {
+        if (env->h_cam_env[c] != c / cpe) return invalid("every environment must have the same number of cameras");
+        if (env->h_cam_w[c] % cells != 0 || env->h_cam_h[c] % cells != 0)
+            return invalid("camera sizes must be divisible by cells");
+    }
+    CK(launch_observe(env->d, *frame, cpe, cells, depth_scale, out, (cudaStream_t)stream));
+    return VUDA_OK;
+}
+
 // RL rollout with the inter-trajectory schedule: two groups of
 // trajectories, each looping sim -> render -> policy, with one group's sim
 // beside the other group's render and policy.

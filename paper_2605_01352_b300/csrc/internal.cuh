@@ -229,6 +229,12 @@ cudaError_t launch_mesh_planes(const float* verts, const int32_t* vert_off, cons
                                const int32_t* tris, int num_meshes, int num_tris, float4* planes,
                                cudaStream_t stream);
 
+// Pooled observation of frame fr (vuda_observe): every camera's cells x
+// cells cells (camera sizes divisible by cells), mean depth x depth_scale and
+// mean luminance, into out[E][2 cams_per_env cells^2].
+cudaError_t launch_observe(const DevBatch& b, const vuda_frame& fr, int cams_per_env, int cells, float depth_scale,
+                           float* out, cudaStream_t stream);
+
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
                                 const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim,
                                 cudaStream_t stream);

@@ -5,16 +5,19 @@ The paper's MLP-based RL runs a small policy network on the same GPU as the
 physics and the rendering, with hidden sizes 256 and 4096 (Sec. 6.4); no
 trained weights are needed to reproduce its cost.  Here the observation of
 an environment is its rendered frame pooled to 16 x 16 cells per camera
-(mean view depth and mean luminance per cell), so that inference(k + 1)
-depends on render(k) as in the paper's rollout loop (Sec. 3.1), and the
-action is one force per body, bounded by tanh.
+(mean view depth / 4 and mean luminance per cell, one pass of the library's
+vuda_observe kernel over the frame), so that inference(k + 1) depends on
+render(k) as in the paper's rollout loop (Sec. 3.1), and the action is one
+force per body, bounded by tanh.
 
     obs [E, 2 * 256 * cams] -> Linear(H) -> ReLU -> Linear(H) -> ReLU
                             -> Linear(3 N) -> tanh * max_force  -> force [3, E N]
 
-Arithmetic is plain FP32 torch (no TF32): the same inputs give the same
-forces, so a rollout's result does not depend on how the two groups of
-trajectories are scheduled.
+The three layers are dense contractions: bf16 GEMMs with FP32 accumulation
+on the tensor cores (cuBLAS through torch; the weights drawn in FP32 and
+rounded once), the output taken back to FP32 for tanh.  The same inputs give
+the same forces, so a rollout's result does not depend on how the two
+groups of trajectories are scheduled.
 """
 from __future__ import annotations
 
@@ -27,8 +30,9 @@ class MLPPolicy:
 
     POOL = 16   # pooled cells per image side
 
-    def __init__(self, scene, hidden: int, seed: int = 0, max_force: float = 2.0, device: str = "cuda"):
+    def __init__(self, env, scene, hidden: int, seed: int = 0, max_force: float = 2.0, device: str = "cuda"):
         import torch
+        self.env = env   # the group's batch: its frames are observed by vuda_observe
         n = np.diff(scene.body_off)
         if len(n) == 0 or (n != n[0]).any():
             raise ValueError("the policy needs the same body count in every environment")
@@ -48,22 +52,18 @@ class MLPPolicy:
             b = 1.0 / np.sqrt(i)
             w = (torch.rand((o, i), generator=g) * 2 - 1) * b
             bias = (torch.rand(o, generator=g) * 2 - 1) * b
-            return w.to(device), bias.to(device)
+            return w.to(device, torch.bfloat16), bias.to(device, torch.bfloat16)
 
         self.layers = [layer(din, hidden), layer(hidden, hidden), layer(hidden, 3 * self.N)]
-        self.luma = torch.tensor([0.299, 0.587, 0.114], device=device) / 255.0
+        self.obs = torch.empty((self.E, din), dtype=torch.float32, device=device)
 
     def observe(self, frame):
         """Observation [E, 2 * 256 * cams] of a frame (dict of rgb [P, 3] u8 and
-        depth [P] f32 device tensors)."""
+        depth [P] f32 device tensors): per environment the 16 x 16 cell means
+        of depth / 4 of its cameras, then those of luminance."""
         import torch
-        import torch.nn.functional as F
-        E, C, H, W, k = self.E, self.cams, self.H, self.W, self.POOL
-        d = frame["depth"].view(E * C, 1, H, W)
-        y = (frame["rgb"].view(E * C, H, W, 3).float() @ self.luma).view(E * C, 1, H, W)
-        pd = F.adaptive_avg_pool2d(d, k).view(E, C * k * k) * 0.25
-        py = F.adaptive_avg_pool2d(y, k).view(E, C * k * k)
-        return torch.cat([pd, py], 1)
+        self.env.observe(frame, self.POOL, 0.25, self.obs, stream=torch.cuda.current_stream())
+        return self.obs
 
     def capture(self, frames, force, stream):
         """Capture act() for each frame of a ring as a CUDA graph on `stream`
@@ -92,9 +92,9 @@ class MLPPolicy:
     def act(self, frame, force):
         """Writes the forces of every body ([3, E N], in place) from a frame."""
         import torch
-        x = self.observe(frame)
+        x = self.observe(frame).to(torch.bfloat16)
         (w0, b0), (w1, b1), (w2, b2) = self.layers
         x = torch.relu(torch.addmm(b0, x, w0.t()))
         x = torch.relu(torch.addmm(b1, x, w1.t()))
-        a = torch.tanh(torch.addmm(b2, x, w2.t())) * self.max_force      # [E, 3 N]
+        a = torch.tanh(torch.addmm(b2, x, w2.t()).float()) * self.max_force      # [E, 3 N]
         force.copy_(a.view(self.E * self.N, 3).t())

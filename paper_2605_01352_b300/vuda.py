@@ -131,6 +131,7 @@ _sig("vuda_env_set_pose", [vp, C.c_int32, vp, vp])
 _sig("vuda_env_status", [vp, vp, vp, C.c_int32])
 _sig("vuda_env_contact_counts", [vp, vp])
 _sig("vuda_raster_screen_tris", [vp, vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp])
+_sig("vuda_observe", [vp, C.POINTER(Frame), C.c_int32, C.c_float, vp, vp])
 PolicyFn = C.CFUNCTYPE(C.c_int32, vp, C.c_int32, C.c_int64, C.POINTER(Frame), vp, vp)
 _sig("vuda_rollout_run", [vp, vp, C.c_int32, C.POINTER(Frame), C.POINTER(Frame), vp, vp, PolicyFn, vp, vp,
                           C.POINTER(Timing)])
@@ -316,6 +317,12 @@ class Env:
     def render(self, frame, pose_slot: int = -1, stream=None):
         fs = self.frame_struct(frame)
         check(lib.vuda_render(self.h, pose_slot, C.byref(fs), _stream(stream)), "vuda_render")
+
+    def observe(self, frame, cells: int, depth_scale: float, out, stream=None):
+        """Pooled observation of a frame (vuda_observe) into the device tensor
+        out [E, 2 * cameras per env * cells^2] (float32)."""
+        fs = self.frame_struct(frame)
+        check(lib.vuda_observe(self.h, C.byref(fs), cells, depth_scale, _dptr(out), _stream(stream)), "vuda_observe")
 
     # -- co-scheduling ----------------------------------------------------------------
     def coschedule(self, mode: int = COSCHED_GREEN, sim_sms: int = 0, sim_ctas_per_sm: int = 0,
