@@ -1281,33 +1281,45 @@ __device__ __forceinline__ void sim_env(const DevBatch& b, int e, int nsteps, co
             // compacted in item order
             nc = 0;
             if (sc.plane) {
-                for (int u0 = 0; u0 < nplane; u0 += kT) {
-                    const int u = u0 + tid;
-                    bool hit = false;
-                    int bi = 0;
-                    f3 pt{0.0f, 0.0f, 0.0f};
-                    float d = 0.0f;
-                    if (u < nplane) {
-                        const int pe = ptab[u];
-                        bi = pe >> 3;
-                        if (is_box(S, bi)) {
-                            pt = box_corner(S, bi, pe & 7);
-                            d = pt.z;
-                        } else {
-                            float r = S.D(0, bi);
-                            f3 p = ldpos(S, bi);
-                            d = p.z - r;
-                            pt = f3{p.x, p.y, p.z - r};
+                // two items per thread (u0 + tid and u0 + kT + tid), compacted
+                // in item order by one scan of both hit counts
+                for (int u0 = 0; u0 < nplane; u0 += 2 * kT) {
+                    bool hit[2];
+                    int bi[2];
+                    f3 pt[2];
+                    float d[2];
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int u = u0 + q * kT + tid;
+                        hit[q] = false;
+                        bi[q] = 0;
+                        pt[q] = f3{0.0f, 0.0f, 0.0f};
+                        d[q] = 0.0f;
+                        if (u < nplane) {
+                            const int pe = ptab[u];
+                            bi[q] = pe >> 3;
+                            if (is_box(S, bi[q])) {
+                                pt[q] = box_corner(S, bi[q], pe & 7);
+                                d[q] = pt[q].z;
+                            } else {
+                                float r = S.D(0, bi[q]);
+                                f3 p = ldpos(S, bi[q]);
+                                d[q] = p.z - r;
+                                pt[q] = f3{p.x, p.y, p.z - r};
+                            }
+                            hit[q] = d[q] < sc.margin;
                         }
-                        hit = d < sc.margin;
                     }
                     int t2;
-                    int ex2 = block_excl_scan(hit ? 1 : 0, wsum, t2);
-                    if (hit) {
-                        int idx = nc + ex2;
-                        if (idx < cmax) put_contact(C, idx, bi, -1, up, pt, d); else ovf = true;
-                    }
-                    nc += t2;
+                    const int ex2 = block_excl_scan((hit[0] ? 1 : 0) | (hit[1] ? 0x10000 : 0), wsum, t2);
+                    const int n0 = t2 & 0xffff;
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        if (hit[q]) {
+                            const int idx = nc + (q == 0 ? (ex2 & 0xffff) : n0 + (ex2 >> 16));
+                            if (idx < cmax) put_contact(C, idx, bi[q], -1, up, pt[q], d[q]); else ovf = true;
+                        }
+                    nc += n0 + (t2 >> 16);
                 }
             }
             // 2b. pairs in (i, j) order, kPairChunk candidates per round
