@@ -439,6 +439,14 @@ vuda_status build_lists(vuda_env* env) {
             cl.smem = cl.wide ? wide::phys_smem_bytes_default(cl.max_bodies, mcpb)
                               : phys_smem_bytes_default(cl.max_bodies, mcpb);
             cl.smem = std::min(std::max(cl.smem, env->phys_smem_user), 227 * 1024);
+            if (cl.wide && env->phys_smem_user == 0) {
+                // two 512-thread CTAs per SM where the layout allows: a
+                // smaller contact area (the rest in the spill area) doubles
+                // the environments in flight (cfg4's large environments:
+                // sim alone 1.96 -> 1.48 ms)
+                const int two = wide::sim_smem_for_ctas(2);
+                if (two >= wide::phys_min_smem_bytes(cl.max_bodies, mcpb)) cl.smem = std::min(cl.smem, two);
+            }
             const int cap = cl.wide ? wide::phys_contacts_in_smem(cl.smem, cl.max_bodies, mcpb)
                                     : phys_contacts_in_smem(cl.smem, cl.max_bodies, mcpb);
             class_spill = class_spill || (int64_t)mcpb * cl.max_bodies > cap;

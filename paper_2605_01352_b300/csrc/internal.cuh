@@ -169,6 +169,7 @@ constexpr int kCamWords = 13;
                                  int smem_per_env, int max_bodies, const float* force, SmGate gate,           \
                                  int feat, cudaStream_t stream); /* feat: kFeat bits of any listed batch */     \
     int sim_ctas_per_sm(int smem_per_env);                                                                    \
+    int sim_smem_for_ctas(int ctas); /* largest per-environment layout that keeps `ctas` CTAs per SM */        \
     CtaFootprint sim_list_footprint(int smem_per_env);                                                        \
     int phys_smem_bytes_default(int max_bodies, int mcpb);                                                    \
     int phys_min_smem_bytes(int max_bodies, int mcpb); /* the layout without contact records */               \

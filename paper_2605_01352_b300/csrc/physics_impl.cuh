@@ -1552,6 +1552,20 @@ int sim_ctas_per_sm(int smem_per_env) {
     return n > 0 ? n : 1;
 }
 
+int sim_smem_for_ctas(int ctas) {
+    // the SM's shared memory shared by `ctas` CTAs, each also holding the
+    // per-block reservation and the kernel's static shared memory (the batch
+    // descriptor), with 256 bytes of slack each, rounded down to 1 KB (the
+    // occupancy calculator's figure one allocation unit higher left one CTA
+    // per SM in practice)
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) reserved = 1024;
+    const int per_cta = per_sm / ctas - reserved - (int)sizeof(DevBatch) - 64 - 256;
+    return per_cta > 0 ? per_cta & ~1023 : 0;
+}
+
 CtaFootprint sim_list_footprint(int smem_per_env) {
     cudaFuncAttributes fa[4]{};
     if (cudaFuncGetAttributes(&fa[0], sim_list_kernel<0>) != cudaSuccess ||
