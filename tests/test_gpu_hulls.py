@@ -104,3 +104,14 @@ def test_hull_contacts_off_keep_the_sphere_proxies(V, orc):
     sc = _hull_scene(envs=2)
     sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, hull_contacts=0))
     _physics_horizon(V, orc, sc, steps=5)
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_hull_and_edge_contacts_together(V, orc, persistent):
+    """Both optional contact tests (and the gyroscopic term) in one batch:
+    the kernel variant compiled with the edge and the hull paths."""
+    sc = S.generate(8, 15, S.config_seed(3) ^ 0x55, kinds="mixed_hulls", hull_tris=(8, 40), n_hull_meshes=6)
+    sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, hull_contacts=1, edge_contacts=1,
+                                                            gyroscopic=1))
+    sc = _settled(orc, sc, 120)
+    _physics_horizon(V, orc, sc, steps=8, persistent=persistent)

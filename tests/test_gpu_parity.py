@@ -824,3 +824,35 @@ def test_hull_meshes_two_cameras(V, orc, path):
     _frames_of_gpu_poses(orc, sc, env, ring[1], 1, range(sc.num_envs))
     assert env.C == 6 and env.T > 3 * 64 * 500
     env.close()
+
+
+@pytest.mark.parametrize("option", ["gyroscopic_edges", "hull_contacts"])
+def test_full_size_physics_options_settled(V, orc, option):
+    """The physics options at the size and in the regime the benchmark times
+    them: 1024 environments of 32 bodies, settled for 120 steps, then 4
+    plain steps -- the benchmark batch with the gyroscopic term and box-box
+    edge contacts, and the batch of spheres, boxes and hulls of 8-48 faces
+    with hull contacts.  Sampled environments (and the most contact-rich
+    one), stepped by the oracle from the GPU's settled state, match within
+    the physics tolerance."""
+    import dataclasses
+    import torch
+    if option == "gyroscopic_edges":
+        sc = S.cfg2()
+        sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, gyroscopic=1, edge_contacts=1))
+    else:
+        sc = S.generate(1024, 32, S.config_seed(2) ^ 0x4855, kinds="mixed_hulls", res=128, substeps=8,
+                        hull_tris=(8, 48), n_hull_meshes=16)
+        sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, hull_contacts=1))
+    env = V.Env(sc)
+    env.sim_step(120)
+    torch.cuda.synchronize()
+    settled = env.get_state()
+    cc = env.contact_counts()
+    assert cc.mean() > 2.0 * 32, cc.mean()
+    env.sim_step(4)
+    torch.cuda.synchronize()
+    assert env.status()[1] == 0
+    picks = CFG2_SAMPLE + (int(np.argmax(cc)),)
+    _sampled_physics(orc, sc, env.get_state(), 4, picks, start=settled)
+    env.close()
