@@ -844,9 +844,13 @@ __device__ __forceinline__ void warp_best(float& v, int& k, bool want_max) {
 
 // Largest separation of polytope b from polytope a along a's face normals,
 // sep_f = (min_v m . x_v + n . (p_b - p_a)) - offset_f with n = R_a n_f and
-// m = R_b^T n, and its face (the first on ties).  Whole warp.
-__device__ __noinline__ float warp_face_separation(const Bodies& S, int a, const Poly& Pa, int b, const Poly& Pb,
-                                                   int& face) {
+// m = R_b^T n, and its face (the first on ties).  Whole warp, a face per
+// lane.  A box's minimum over its corners (+-h0, +-h1, +-h2) is taken in
+// closed form: every product m_k (+-h_k) is +-(m_k h_k) exactly and
+// rounding is monotonic, so the least of the eight sums ((p0 + p1) + p2) is
+// the one with every term negative.
+__device__ __forceinline__ float warp_face_separation(const Bodies& S, int a, const Poly& Pa, int b, const Poly& Pb,
+                                                      int& face) {
     const int lane = threadIdx.x & 31;
     const f3 d = sub3(ldpos(S, b), ldpos(S, a));
     float best = 0.0f;
@@ -855,25 +859,30 @@ __device__ __noinline__ float warp_face_separation(const Bodies& S, int a, const
         const float4 pl = poly_plane(Pa, f);
         const f3 n = rmul(S, a, f3{pl.x, pl.y, pl.z});
         const f3 m = rtmul(S, b, n);
-        // the minimum does not depend on the order of the vertices: four
-        // vertices' loads are issued together
-        float lo = dot3(m, poly_x(Pb, 0));
-        int v = 1;
+        float lo;
+        if (!Pb.hull) {
+            lo = (-fabsf(m.x * Pb.h0) - fabsf(m.y * Pb.h1)) - fabsf(m.z * Pb.h2);
+        } else {
+            // the minimum does not depend on the order of the vertices: four
+            // vertices' loads are issued together
+            lo = dot3(m, poly_x(Pb, 0));
+            int v = 1;
 #pragma unroll 1
-        for (; v + 4 <= Pb.nv; v += 4) {
-            f3 x[4];
+            for (; v + 4 <= Pb.nv; v += 4) {
+                f3 x[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) x[u] = poly_x(Pb, v + u);
+                for (int u = 0; u < 4; u++) x[u] = poly_x(Pb, v + u);
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const float t = dot3(m, x[u]);
+                for (int u = 0; u < 4; u++) {
+                    const float t = dot3(m, x[u]);
+                    if (t < lo) lo = t;
+                }
+            }
+#pragma unroll 1
+            for (; v < Pb.nv; v++) {
+                const float t = dot3(m, poly_x(Pb, v));
                 if (t < lo) lo = t;
             }
-        }
-#pragma unroll 1
-        for (; v < Pb.nv; v++) {
-            const float t = dot3(m, poly_x(Pb, v));
-            if (t < lo) lo = t;
         }
         const float sep = (lo + dot3(n, d)) - pl.w;
         if (bf < 0 || sep > best) {
@@ -898,7 +907,7 @@ __device__ __noinline__ float warp_face_separation(const Bodies& S, int a, const
 // writes the contacts from index base.  Returns the contact count (every
 // lane).
 template <bool kWrite>
-__device__ __noinline__ int polytope_pair(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int i, int j,
+__device__ __forceinline__ int polytope_pair(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int i, int j,
                                           float margin, int base, int cmax, bool& ovf, int* meta) {
     const int lane = threadIdx.x & 31;
     const Poly Pi = poly_of(bt, S, b0, i), Pj = poly_of(bt, S, b0, j);
@@ -916,6 +925,12 @@ __device__ __noinline__ int polytope_pair(const DevBatch& bt, const Bodies& S, c
     } else {
         int fi, fj;
         const float si = warp_face_separation(S, i, Pi, j, Pj, fi);
+        // no contacts whatever j's separation when i's is at least the
+        // margin: the reference separation is then si, or sj > si + 1e-5
+        if (!(si < margin)) {
+            if (meta && lane == 0) *meta = -1;
+            return 0;
+        }
         const float sj = warp_face_separation(S, j, Pj, i, Pi, fj);
         ref_j = sj > si + 1e-5f;
         if (!((ref_j ? sj : si) < margin)) {
@@ -1010,7 +1025,7 @@ __device__ __noinline__ int polytope_pair(const DevBatch& bt, const Bodies& S, c
 // One hull unit (code: i | j << 16, j = 0xffff for hull i on the plane) by
 // a warp: its contact count, and with kWrite its contacts from index base.
 template <bool kWrite>
-__device__ __noinline__ int hull_unit(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int code,
+__device__ __forceinline__ int hull_unit(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int code,
                                       float margin, int base, int cmax, bool& ovf, int* meta) {
     const int lane = threadIdx.x & 31;
     const int i = code & 0xffff, j = (code >> 16) & 0xffff;
