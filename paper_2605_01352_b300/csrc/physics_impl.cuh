@@ -235,11 +235,11 @@ __device__ __noinline__ bool box_edge_edge(const Bodies& B, int a, int b, float 
                                            float& d) {
     const f3 dp = sub3(ldpos(B, a), ldpos(B, b));
     float Cm[3][3], AC[3][3], ta[3], tb[3];
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < 3; k++) {
         ta[k] = dot3(dp, rcol(B, a, k));
         tb[k] = dot3(dp, rcol(B, b, k));
-#pragma unroll 1
+#pragma unroll
         for (int l = 0; l < 3; l++) {
             Cm[k][l] = dot3(rcol(B, a, k), rcol(B, b, l));
             AC[k][l] = fabsf(Cm[k][l]);
@@ -252,13 +252,13 @@ __device__ __noinline__ bool box_edge_edge(const Bodies& B, int a, int b, float 
     // a face axis separating the boxes by the margin or more decides the
     // test (the winning separation can only be larger): skip the edge axes
     float face = -3.0e38f;
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < 3; k++) {
         face = fmaxf(face, fabsf(ta[k]) - (ha[k] + ((hb[0] * AC[k][0] + hb[1] * AC[k][1]) + hb[2] * AC[k][2])));
         face = fmaxf(face, fabsf(tb[k]) - (((ha[0] * AC[0][k] + ha[1] * AC[1][k]) + ha[2] * AC[2][k]) + hb[k]));
     }
     if (!(face < margin)) return false;
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < 15; q++) {
         float sep;
         if (q < 3) {
