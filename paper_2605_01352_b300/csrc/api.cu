@@ -303,7 +303,7 @@ vuda_status env_estimate_bytes(const vuda_scene* sc, const vuda_sim_params* p, i
     int64_t bytes = B * 4 * (3 + 4 + 3 + 3 + 3 + 1 + 3 + 3 + 2 * 7 + 2 + 2) + B + E * 40;
     bytes += (int64_t)p->max_contacts_per_body * B * kContactStride * 4;   // contact spill (upper bound)
     bytes += T * 4;                                                          // colour table
-    bytes += (int64_t)sc->mesh_vert_off[sc->num_meshes] * 12 + (int64_t)sc->mesh_tri_off[sc->num_meshes] * 28;
+    bytes += (int64_t)sc->mesh_vert_off[sc->num_meshes] * 28 + (int64_t)sc->mesh_tri_off[sc->num_meshes] * 28;
     bytes += C * 128 + (P / 16 + C) * 16 + 64 * 1024;                       // cameras, items, slack
     bytes += (int64_t)sc->mesh_tri_off[sc->num_meshes] * 8 + (int64_t)sc->mesh_vert_off[sc->num_meshes] * 8;
     bytes += tiled_scratch_estimate(sc);   // the tiled render path, where it applies
@@ -813,12 +813,16 @@ vuda_status vuda_env_create(const vuda_scene* sc, const vuda_sim_params* prm, co
     UP(mesh_verts, float, sc->mesh_verts, 3 * (size_t)sc->mesh_vert_off[M]);
     UP(mesh_tri_off, int32_t, sc->mesh_tri_off, M + 1);
     UP(mesh_tris, int32_t, sc->mesh_tris, 3 * (size_t)sc->mesh_tri_off[M]);
-    if (s == VUDA_OK) {   // face planes of the meshes (hull contacts)
+    if (s == VUDA_OK) {   // face planes and padded vertices of the meshes (hull contacts)
         float4* planes = nullptr;
+        float4* vert4 = nullptr;
         s = dalloc(env, &planes, (size_t)sc->mesh_tri_off[M]);
+        if (s == VUDA_OK) s = dalloc(env, &vert4, (size_t)sc->mesh_vert_off[M]);
         d.mesh_plane = planes;
+        d.mesh_vert4 = vert4;
         if (s == VUDA_OK && launch_mesh_planes(d.mesh_verts, d.mesh_vert_off, d.mesh_tri_off, d.mesh_tris, M,
-                                               sc->mesh_tri_off[M], planes, 0) != cudaSuccess) {
+                                               sc->mesh_tri_off[M], planes, sc->mesh_vert_off[M], vert4,
+                                               0) != cudaSuccess) {
             set_error("mesh plane launch failed");
             s = VUDA_ERR_CUDA;
         }

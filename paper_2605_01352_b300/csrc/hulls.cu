@@ -3,6 +3,8 @@
 // written in the order that defines them (the library is built without FMA
 // contraction, with IEEE division and square root), so every plane is the
 // correctly rounded evaluation of the same formula wherever it is used.
+// Also the mesh vertices padded to 16 bytes (one load per vertex in the
+// face searches).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,14 +45,21 @@ __global__ void mesh_planes_kernel(const float* __restrict__ verts, const int32_
     }
 }
 
+__global__ void mesh_vert4_kernel(const float* __restrict__ verts, int V, float4* __restrict__ vert4) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V) vert4[v] = make_float4(verts[3 * v], verts[3 * v + 1], verts[3 * v + 2], 0.0f);
+}
+
 }  // namespace
 
 cudaError_t launch_mesh_planes(const float* verts, const int32_t* vert_off, const int32_t* tri_off,
-                               const int32_t* tris, int num_meshes, int num_tris, float4* planes,
-                               cudaStream_t stream) {
-    if (num_tris <= 0 || num_meshes <= 0) return cudaSuccess;
-    mesh_planes_kernel<<<(num_tris + 127) / 128, 128, 0, stream>>>(verts, vert_off, tri_off, tris, num_meshes,
-                                                                    num_tris, planes);
+                               const int32_t* tris, int num_meshes, int num_tris, float4* planes, int num_verts,
+                               float4* vert4, cudaStream_t stream) {
+    if (num_verts > 0)
+        mesh_vert4_kernel<<<(num_verts + 127) / 128, 128, 0, stream>>>(verts, num_verts, vert4);
+    if (num_tris > 0 && num_meshes > 0)
+        mesh_planes_kernel<<<(num_tris + 127) / 128, 128, 0, stream>>>(verts, vert_off, tri_off, tris, num_meshes,
+                                                                        num_tris, planes);
     return cudaGetLastError();
 }
 

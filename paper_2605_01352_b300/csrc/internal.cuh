@@ -75,6 +75,7 @@ struct DevBatch {
     const int32_t* mesh_tri_off;  // [M+1]
     const int32_t* mesh_tris;     // [T][3]
     const float4* mesh_plane;     // [T] face planes of the unit meshes: outward normal, offset (hull contacts)
+    const float4* mesh_vert4;     // [V] the unit meshes' vertices padded to 16 bytes (hull contacts)
     int ground_mesh;
     uint32_t ground_albedo;
     const int32_t* cam_env;       // [C] env of camera c
@@ -227,8 +228,8 @@ inline long long tiled_record_cap(long long T) { return T + T / 8 + 8; }
 // (u2 - u0), the outward unit normal n = c / |c| and the offset n . u0
 // (planes[t] = (n, offset)); a triangle of zero area gets (0, 0, 0, +inf).
 cudaError_t launch_mesh_planes(const float* verts, const int32_t* vert_off, const int32_t* tri_off,
-                               const int32_t* tris, int num_meshes, int num_tris, float4* planes,
-                               cudaStream_t stream);
+                               const int32_t* tris, int num_meshes, int num_tris, float4* planes, int num_verts,
+                               float4* vert4, cudaStream_t stream);
 
 // Pooled observation of frame fr (vuda_observe): every camera's cells x
 // cells cells (camera sizes divisible by cells), mean depth x depth_scale and

@@ -765,7 +765,7 @@ __constant__ signed char kBoxLoop[24] = {1, 3, 7, 5, 0, 4, 6, 2, 2, 6, 7, 3, 0, 
 struct Poly {
     bool hull;
     int nv, nf;
-    const float* v;       // hull: unit-mesh vertices [nv][3]
+    const float4* v;      // hull: unit-mesh vertices [nv] (x, y, z, 0)
     const float4* pl;     // hull: unit-mesh face planes [nf]
     const int32_t* tri;   // hull: mesh-local vertex indices [nf][3]
     float s;              // hull: radius
@@ -780,7 +780,7 @@ __device__ __forceinline__ Poly poly_of(const DevBatch& b, const Bodies& S, int 
         const int v0 = __ldg(b.mesh_vert_off + m), t0 = __ldg(b.mesh_tri_off + m);
         P.nv = __ldg(b.mesh_vert_off + m + 1) - v0;
         P.nf = __ldg(b.mesh_tri_off + m + 1) - t0;
-        P.v = b.mesh_verts + 3 * (size_t)v0;
+        P.v = b.mesh_vert4 + v0;
         P.pl = b.mesh_plane + t0;
         P.tri = b.mesh_tris + 3 * (size_t)t0;
         P.s = S.D(0, i);
@@ -801,7 +801,10 @@ __device__ __forceinline__ Poly poly_of(const DevBatch& b, const Bodies& S, int 
 
 // body-frame vertex k
 __device__ __forceinline__ f3 poly_x(const Poly& P, int k) {
-    if (P.hull) return f3{P.s * __ldg(P.v + 3 * k), P.s * __ldg(P.v + 3 * k + 1), P.s * __ldg(P.v + 3 * k + 2)};
+    if (P.hull) {
+        const float4 q = __ldg(P.v + k);
+        return f3{P.s * q.x, P.s * q.y, P.s * q.z};
+    }
     return f3{(k & 1) ? P.h0 : -P.h0, (k & 2) ? P.h1 : -P.h1, (k & 4) ? P.h2 : -P.h2};
 }
 
@@ -1547,9 +1550,9 @@ int phys_smem_bytes_default(int max_bodies, int mcpb) {
     // spheres and boxes has about 3.5), less the plane item table's 16 bytes
     // per body and 64 bytes; more spill to global memory.  With 32 bodies
     // this is 31,728 bytes (140 records), so that with the kernels' static
-    // shared memory (the 472-byte batch descriptor) rounded up to the
+    // shared memory (the 480-byte batch descriptor) rounded up to the
     // allocation unit 7 environments fit on one SM: the descriptor must not
-    // grow by more than 48 bytes
+    // grow by more than 40 bytes
     size_t want = fixed + (size_t)kCS * 4 * ((9 * max_bodies + 1) / 2) - (size_t)16 * max_bodies - 64;
     if (want > 200 * 1024) want = 200 * 1024;
     if (want < fixed) want = fixed;
