@@ -115,3 +115,16 @@ def test_hull_and_edge_contacts_together(V, orc, persistent):
                                                             gyroscopic=1))
     sc = _settled(orc, sc, 120)
     _physics_horizon(V, orc, sc, steps=8, persistent=persistent)
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_hulls_in_large_environments(V, orc, persistent):
+    """Environments of 80 and 100 bodies beside one of 12 (the persistent
+    launch runs the large ones on the 512-thread size class): the hull pass
+    with sixteen warps and several candidate rounds per substep."""
+    sc = S.generate(3, np.array([80, 12, 100]), S.config_seed(3) ^ 0x33, kinds="mixed_hulls", hull_tris=(8, 40),
+                    n_hull_meshes=6)
+    sc = dataclasses.replace(sc, params=dataclasses.replace(sc.params, hull_contacts=1))
+    sc = _settled(orc, sc, 120)
+    assert orc.contacts(sc, 2)["count"] > 300
+    _physics_horizon(V, orc, sc, steps=6, persistent=persistent)
