@@ -228,10 +228,9 @@ __device__ __forceinline__ f3 rcol(const Bodies& B, int i, int k) { return f3{B.
 // A's edge along a_k furthest towards B and B's edge along b_l furthest
 // towards A (segment closest points: s clamped, t from s and clamped, then s
 // from t and clamped if t was clamped).
-// (kCopy: one compiled copy per kernel variant, so that the register use of
-// the variant with hull contacts does not shape the copy of the other)
+// (kCopy: the kernel variant that uses it)
 template <int kCopy>
-__device__ __noinline__ bool box_edge_edge(const Bodies& B, int a, int b, float margin, f3& nout, f3& pt,
+__device__ __forceinline__ bool box_edge_edge(const Bodies& B, int a, int b, float margin, f3& nout, f3& pt,
                                            float& d) {
     const f3 dp = sub3(ldpos(B, a), ldpos(B, b));
     float Cm[3][3], AC[3][3], ta[3], tb[3];
@@ -370,10 +369,11 @@ __device__ __forceinline__ bool broad(const Bodies& B, int i, int j, float margi
 
 // Edge tests of the box pairs among passing pairs [w0, w1), one thread
 // each, into slots (2 float4 per pair: normal and distance, point and hit).
-// Out of line: it runs on few threads, and inlined into the pair round it
-// would raise that loop's register pressure.
+// Inlined, like the other optional passes: an out-of-line call makes the
+// kernel keep values across it in local memory, which with seven CTAs'
+// shared memory on the SM has little L1 left to hold it (measured slower).
 template <int kCopy>
-__device__ __noinline__ void edge_prepass(const Bodies& S, const int* plist, int w0, int w1, float4* slots,
+__device__ __forceinline__ void edge_prepass(const Bodies& S, const int* plist, int w0, int w1, float4* slots,
                                           float margin) {
     for (int q = w0 + (int)threadIdx.x; q < w1; q += kT) {
         const int pr = plist[q];
@@ -1092,7 +1092,7 @@ __device__ __forceinline__ int hull_unit(const DevBatch& bt, const Bodies& S, co
 // the round's units are listed in order (plist), each warp counts the
 // contacts of its units (pitem), a scan gives their first indices, and the
 // warps write them.  Whole CTA; plist and pitem are free at this point.
-__device__ __noinline__ void hull_pass(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int N,
+__device__ __forceinline__ void hull_pass(const DevBatch& bt, const Bodies& S, const Contacts& C, int b0, int N,
                                        int* plist, unsigned short* pitem, int* meta, int nmeta, ScanBuf& wsum,
                                        float margin, bool plane, int cmax, int& nc, bool& ovf) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
