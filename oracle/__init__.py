@@ -10,6 +10,7 @@ Functions:
   contacts(scene, env, state=None)
   render(scene, pos, quat)
   raster_screen_tris(xy, z, W, H, count=False)
+  observe(scene, rgb, depth, cells, depth_scale)
 """
 from __future__ import annotations
 
@@ -165,3 +166,38 @@ def raster_screen_tris(xy: np.ndarray, z: np.ndarray, W: int, H: int, count: boo
     if rc != 0:
         raise ValueError("oracle_raster_screen_tris rejected its arguments")
     return tid, dep, cnt
+
+
+def observe(scene, rgb: np.ndarray, depth: np.ndarray, cells: int, depth_scale: float) -> np.ndarray:
+    """Pooled observation of a rendered frame, the policy input of the RL
+    rollout (Sec. 3.1 and 6.4: the policy acts on what the renderer produced
+    for the step; the pooling itself is a reading, since the paper's
+    policies read full frames): every camera is cut into cells x cells
+    cells of (W / cells) x (H / cells) pixels, row-major; per cell the mean
+    view depth (background 0) times depth_scale, and the mean luminance
+    (0.299 R + 0.587 G + 0.114 B) / 255.  Output [E][2 * cams_per_env *
+    cells^2]: the depth cells of the environment's cameras in order, then
+    their luminance cells.  Plain float64, no blocking."""
+    off = scene.cam_pix_off()
+    ncam = np.diff(scene.cam_off)
+    cpe = int(ncam[0]) if len(ncam) else 0
+    if len(ncam) and not (ncam == cpe).all():
+        raise ValueError("observe needs the same number of cameras in every environment")
+    E = len(ncam)
+    n = cells * cells
+    out = np.zeros((E, 2 * cpe * n), np.float64)
+    for c in range(int(scene.cam_off[-1]) if E else 0):
+        e, k = c // cpe, c % cpe
+        W, H = int(scene.cam_w[c]), int(scene.cam_h[c])
+        if W % cells or H % cells:
+            raise ValueError("camera %d: %d x %d pixels do not divide into %d x %d cells" % (c, W, H, cells, cells))
+        cw, ch = W // cells, H // cells
+        d = np.asarray(depth[off[c]:off[c + 1]], np.float64).reshape(H, W)
+        px = np.asarray(rgb[off[c]:off[c + 1]], np.float64).reshape(H, W, 3)
+        lum = (0.299 * px[:, :, 0] + 0.587 * px[:, :, 1] + 0.114 * px[:, :, 2]) / 255.0
+        for cy in range(cells):
+            for cx in range(cells):
+                ys, xs = slice(cy * ch, (cy + 1) * ch), slice(cx * cw, (cx + 1) * cw)
+                out[e, k * n + cy * cells + cx] = d[ys, xs].mean() * depth_scale
+                out[e, (cpe + k) * n + cy * cells + cx] = lum[ys, xs].mean()
+    return out

@@ -139,33 +139,24 @@ def test_rollout_rejects_bad_arguments(V):
     b.close()
 
 
-def test_observe_pools_the_frame(V):
+def test_observe_pools_the_frame(V, orc):
     """vuda_observe: per camera and 16 x 16 cell, the mean depth times the
-    scale and the mean luminance, against numpy on the frame read back;
-    bad arguments are refused."""
+    scale and the mean luminance, against the oracle's pooling of the frame
+    read back (square and non-square cameras); bad arguments are refused."""
     import torch
-    sc = S.generate(3, 6, 41, kinds="mixed", res=64, cams_per_env=2)
-    env = V.Env(sc)
-    fr = env.alloc_frame()
-    env.render(fr, pose_slot=-1)
-    out = torch.zeros((3, 2 * 2 * 16 * 16), dtype=torch.float32, device="cuda")
-    env.observe(fr, 16, 0.25, out)
-    torch.cuda.synchronize()
-    got = out.cpu().numpy()
-    rgb = fr["rgb"].cpu().numpy().astype(np.float64)
-    dep = fr["depth"].cpu().numpy().astype(np.float64)
-    pix = sc.cam_pix_off()
-    for c in range(sc.cam_off[-1]):
-        e, cl = c // 2, c % 2
-        H = W = 64
-        d = dep[pix[c]:pix[c + 1]].reshape(H, W)
-        y = (rgb[pix[c]:pix[c + 1]] @ np.array([0.299, 0.587, 0.114]) / 255.0).reshape(H, W)
-        pd = d.reshape(16, 4, 16, 4).mean(axis=(1, 3)).ravel() * 0.25
-        py = y.reshape(16, 4, 16, 4).mean(axis=(1, 3)).ravel()
-        np.testing.assert_allclose(got[e, cl * 256:(cl + 1) * 256], pd, rtol=1e-5, atol=1e-6)
-        np.testing.assert_allclose(got[e, 512 + cl * 256:512 + (cl + 1) * 256], py, rtol=1e-5, atol=1e-6)
-    with pytest.raises(V.VudaError):
-        env.observe(fr, 48, 0.25, out)      # 64 is not divisible by 48
-    with pytest.raises(V.VudaError):
-        env.observe(fr, 0, 0.25, out)
-    env.close()
+    for res, height in ((64, None), (64, 32)):
+        sc = S.generate(3, 6, 41, kinds="mixed", res=res, height=height, cams_per_env=2)
+        env = V.Env(sc)
+        fr = env.alloc_frame()
+        env.render(fr, pose_slot=-1)
+        out = torch.zeros((3, 2 * 2 * 16 * 16), dtype=torch.float32, device="cuda")
+        env.observe(fr, 16, 0.25, out)
+        torch.cuda.synchronize()
+        want = orc.observe(sc, fr["rgb"].cpu().numpy(), fr["depth"].cpu().numpy(), 16, 0.25)
+        np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-5, atol=1e-6)
+        assert np.abs(want[:, 512:]).max() > 0.05        # the frame is not blank
+        with pytest.raises(V.VudaError):
+            env.observe(fr, 48, 0.25, out)      # 64 is not divisible by 48
+        with pytest.raises(V.VudaError):
+            env.observe(fr, 0, 0.25, out)
+        env.close()
