@@ -387,10 +387,13 @@ def config_bench(V, S, k: int, fp32_peak: float, hbm_peak: float, warmup: int, c
     if settle:
         env.pipeline_run(settle, ring)
     env.pipeline_run(warmup, ring)
+    torch.cuda.synchronize()
+    start = env.get_state()   # every timed run (and the autotuner) steps from here
 
     def timed(n, runs=3):
         res = []
         for _ in range(runs):
+            env.set_state(start)
             torch.cuda.synchronize()
             t = time.perf_counter()
             tm = env.pipeline_run(n, ring, timing=True)
@@ -409,6 +412,7 @@ def config_bench(V, S, k: int, fp32_peak: float, hbm_peak: float, warmup: int, c
            "phase_ms": {"sim": Ts, "render": Tr, "ideal_overlap": (Ts + Tr) / max(Ts, Tr)},
            "roofline": phase_roofline(env, sc, Ts, Tr, fp32_peak, hbm_peak, bytes_out)}
     if k == 3:
+        env.set_state(start)
         tuned = env.autotune(ring, steps=2, use_cache=False)
         out["autotuned"] = tuned
         if tuned.get("graph_steps", 0) <= 0:
@@ -621,16 +625,22 @@ def main():
     bytes_pose = env.B * 28                            # pose slot read by the renderer
     bytes_state = env.B * (52 + 52 + 40 + 28)          # physics state in/out, params, pose out
 
-    # settle: bodies land and piles form (untimed)
+    # settle: bodies land and piles form (untimed); every timed run below
+    # starts from this settled state, so that the modes compare the same work
+    # (piles keep settling, and a later run would step heavier contacts)
     env.pipeline_run(args.settle, ring)
+    torch.cuda.synchronize()
+    settled = env.get_state()
     clk = Clocks(local)
     clk.start()
 
     def timed(n, runs=5):
-        """Median over `runs` timed runs of n steps (device time of each run,
-        max over ranks); the per-step timings and wall time of the median run."""
+        """Median over `runs` timed runs of n steps from the settled state
+        (device time of each run, max over ranks); the per-step timings and
+        wall time of the median run."""
         res = []
         for _ in range(runs):
+            env.set_state(settled)
             barrier(ws)
             torch.cuda.synchronize()
             clk.on = True
@@ -665,6 +675,7 @@ def main():
         env.pipeline_run(8, ring, stream=stream)
         res = []
         for _ in range(5):
+            env.set_state(settled)
             barrier(ws)
             torch.cuda.synchronize()
             clk.on = True
@@ -725,6 +736,7 @@ def main():
     lat = lat[np.isfinite(lat)]
     # the autotuner's own choice (band height, co-scheduling mode and split, graph)
     try:
+        env.set_state(settled)
         tuned = env.autotune(ring, steps=6, use_cache=False)
         tuned["env_steps_per_s"] = ws * E * 1000.0 / tuned["ms_per_step"]
     except Exception as ex:  # report why, keep the main line
@@ -738,6 +750,7 @@ def main():
         hr = torch.empty((2, P, 3), dtype=torch.uint8).pin_memory()
         hd = torch.empty((2, P), dtype=torch.float32).pin_memory()
         env.pipeline_run_host(args.warmup, ring, hr, hd, h_force=hf)
+        env.set_state(settled)
         barrier(ws)
         torch.cuda.synchronize()
         t = time.perf_counter()

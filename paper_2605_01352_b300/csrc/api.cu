@@ -1739,7 +1739,12 @@ vuda_status vuda_autotune(vuda_env_t env, const vuda_tune_opts* opts, const vuda
     const int64_t steps0 = env->steps;
     int trials = 0;
     auto measure = [&](float* ms) -> vuda_status {
-        vuda_status r = vuda_pipeline_run(env, 2, ring, nullptr, nullptr);
+        // every trial steps the same work: it starts from the saved state
+        // (a batch still settling gets heavier step by step, which would
+        // favour the earlier candidates)
+        vuda_status r = vuda_env_set_state(env, &st);
+        if (r != VUDA_OK) return r;
+        r = vuda_pipeline_run(env, 2, ring, nullptr, nullptr);
         if (r != VUDA_OK) return r;
         std::vector<float> sm(K), rm(K), stp(K);
         vuda_timing tm{stp.data(), sm.data(), rm.data(), 0.0f};
