@@ -316,10 +316,12 @@ vuda_status vuda_set_tiling(vuda_env_t env, int32_t tile_size, int32_t bin_limit
  * co-scheduled on disjoint partitions of 1/4, 1/2 and 3/4 of the SMs /
  * co-scheduled with per-SM quotas (every pair that fits one SM, the most sim
  * CTAs for each render count), and CUDA graph replay -- and leaves the batch
- * configured with the fastest.  Results
- * are cached per batch shape for the process (use_cache = 1 reuses them
- * without measuring).  The trials step the batch; its state and pose slots
- * are restored afterwards.  ring: the two frames the loop will use. */
+ * configured with the fastest; co-scheduling and graph replay are kept only
+ * when they beat the configuration before them by more than 1 % (the
+ * trials' noise).  Results are cached per batch shape for the process
+ * (use_cache = 1 reuses them without measuring).  Every trial starts from
+ * the batch's state at the call; the state and pose slots are restored
+ * afterwards.  ring: the two frames the loop will use. */
 typedef struct {
     int32_t steps;                /* measured steps per trial (0: 6) */
     int32_t use_cache;
