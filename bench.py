@@ -867,7 +867,9 @@ def main():
         "config": {"workload": WORKLOAD, "envs_per_gpu": E, "bodies_per_env": 32, "substeps": 8,
                    "iterations": 8, "camera": "128x128 RGB8 + f32 depth", "parallelism": "replicas" if ws > 1
                    else "single GPU", "render_path": "tiled" if env_info_path == V.RENDER_TILED else "band",
-                   "l2": "per-step working set (frames 2 x %.0f MB) exceeds the 126 MB L2" % (bytes_out / 1e6)},
+                   "l2": "per-step working set (frames 2 x %.0f MB) exceeds the 126 MB L2" % (bytes_out / 1e6),
+                   "timed_from": "every timed run of every mode starts from the state %d steps after the drop"
+                                 % args.settle},
         "coscheduled_mode": head[0],
         "serialized": {"value": v_ser, "ms_per_step": 1000.0 * t_ser / args.steps},
         "serialized_graph8": ({"value": job_throughput(ws, E, args.steps, t_serg),
