@@ -1061,10 +1061,13 @@ vuda_status vuda_sim_step(vuda_env_t env, int32_t nsteps, const float* force, vu
 static vuda_status render_slot(vuda_env_t env, int slot, const vuda_frame* fr, cudaStream_t stream) {
     cudaError_t e;
     const bool shared = env->cos_mode == VUDA_COSCHED_SHARED;
-    if (env->tiled && !shared)
+    if (env->tiled && !shared) {
+        // fine meshes (more triangles per environment than pixels per
+        // camera: most cover no pixel centre) take the sieved set-up
+        const bool sieve = env->E > 0 && env->C > 0 && (double)env->T * env->C > (double)env->P * env->E;
         e = launch_render_tiled(env->d, env->d.pose[slot], *fr, env->ts, env->tcams, env->titems, env->ntitems,
-                                env->tile_size, env->bin_limit,
-                                stream);
+                                env->tile_size, env->bin_limit, sieve, stream);
+    }
     else if (env->persistent || shared)
         e = launch_render_list(env->d_desc, env->ren_items[slot], env->nitems, env->counters + 1,
                                shared ? env->ren_grid_sh : env->ren_grid, env->shade_items[slot], env->nshade,

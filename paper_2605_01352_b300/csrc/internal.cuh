@@ -237,8 +237,11 @@ cudaError_t launch_mesh_planes(const float* verts, const int32_t* vert_off, cons
 cudaError_t launch_observe(const DevBatch& b, const vuda_frame& fr, int cams_per_env, int cells, float depth_scale,
                            float* out, cudaStream_t stream);
 
+// sieve: set-up in two passes (keep the triangles that can leave a record,
+// then set them up with full warps), for batches whose triangles outnumber
+// their pixels
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
-                                const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim,
+                                const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim, bool sieve,
                                 cudaStream_t stream);
 // One batch of a tiled work list over several batches: its device camera
 // and raster items and its scratch (as built for its own launches), the

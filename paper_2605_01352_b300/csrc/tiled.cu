@@ -42,6 +42,7 @@ namespace vuda {
 namespace {
 
 constexpr int kBT = 256;          // bin_kernel threads
+constexpr int kSieveCap = 2048;   // triangles per window of the bin kernel's sieve
 constexpr int kNarrowTiles = 9;   // default bin limit: records over more tiles go to the camera's wide list
 constexpr int kMaxBinLimit = 64;  // largest bin limit accepted
 constexpr int kMaxTiles = 2048;   // tiles per camera the counting sort holds in shared memory (640 x 480: 1200)
@@ -143,7 +144,7 @@ __device__ __forceinline__ int cta_excl_scan(int v, int* wsum, int& total) {
 
 // Set-up, shading and binning of camera `ci` of batch b (pose: its pose
 // slot), by the whole CTA.
-template <int T>
+template <int T, bool kSieve>
 __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __restrict__ pose, const TileScratch& ts,
                                            const TileItem& ci, int nlim) {
     __shared__ int vX[kVertexCache], vY[kVertexCache], vflag[kVertexCache];
@@ -153,6 +154,8 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
     __shared__ int s_wsum[kBT / 32];
     __shared__ int s_nrec, s_nwide;
     __shared__ unsigned s_flags;
+    __shared__ unsigned short s_q[kSieve ? kSieveCap : 1];   // the sieve's kept triangles (window-relative)
+    __shared__ int s_nq;
 
     const int cam = ci.cam, e = ci.env;
     const int W = ci.W, H = ci.H;
@@ -171,6 +174,7 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
         s_nrec = 0;
         s_nwide = 0;
         s_flags = 0u;
+        s_nq = 0;
     }
     for (int ck = b.chunk_off[e]; ck < b.chunk_off[e + 1]; ck++) {
         const int cb0 = b.chunk_lo[ck];   // env-local first body, -1 = ground
@@ -191,7 +195,8 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
             vW[v][2] = wz;
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < nt; t += kBT) {
+        // set-up, shading and binning of triangle t of the chunk
+        auto triangle = [&](int t) {
             const uint2 tv = tt[t];
             const int i0 = tv.x & 0xffff, i1 = tv.x >> 16, i2 = tv.y;
             const uint32_t id = tri0 + (uint32_t)t;
@@ -268,6 +273,49 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
                     emit(f.X[k][0], f.X[k][1], f.X[k][2], f.Y[k][0], f.Y[k][1], f.Y[k][2], f.iz[k][0], f.iz[k][1],
                          f.iz[k][2]);
             }
+        };
+        if constexpr (kSieve) {
+            // fine meshes: most triangles cover no pixel centre or face away.
+            // A first pass keeps the triangles that can leave a record (the
+            // tests that open the set-up, or a vertex to clip), a second pass
+            // runs the set-up on them with full warps; windows of kSieveCap.
+            const int lane = threadIdx.x & 31;
+            for (int w0 = 0; w0 < nt; w0 += kSieveCap) {
+                const int w1 = min(nt, w0 + kSieveCap);
+                for (int r0 = w0; r0 < w1; r0 += kBT) {
+                    const int t = r0 + threadIdx.x;
+                    bool keep = false;
+                    if (t < w1) {
+                        const uint2 tv = tt[t];
+                        const int i0 = tv.x & 0xffff, i1 = tv.x >> 16, i2 = tv.y;
+                        if (vflag[i0] | vflag[i1] | vflag[i2]) {
+                            keep = true;
+                        } else {
+                            const int X0 = vX[i0], X1 = vX[i1], X2 = vX[i2], Y0 = vY[i0], Y1 = vY[i1], Y2 = vY[i2];
+                            const int mnx = min(X0, min(X1, X2)), mxx = max(X0, max(X1, X2));
+                            const int mny = min(Y0, min(Y1, Y2)), mxy = max(Y0, max(Y1, Y2));
+                            const int px0 = max((mnx - 128 + 255) >> 8, 0), px1 = min((mxx - 128) >> 8, W - 1);
+                            const int py0 = max((mny - 128 + 255) >> 8, 0), py1 = min((mxy - 128) >> 8, H - 1);
+                            const long long area2 = ((long long)X1 - X0) * ((long long)Y2 - Y0) -
+                                                    ((long long)Y1 - Y0) * ((long long)X2 - X0);
+                            keep = px0 <= px1 && py0 <= py1 && area2 < 0;
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(&s_nq, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (keep) s_q[base + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(t - w0);
+                }
+                __syncthreads();
+                const int nq = s_nq;
+                for (int q = threadIdx.x; q < nq; q += kBT) triangle(w0 + s_q[q]);
+                __syncthreads();   // the queue is read
+                if (threadIdx.x == 0) s_nq = 0;
+                __syncthreads();
+            }
+        } else {
+            for (int t = threadIdx.x; t < nt; t += kBT) triangle(t);
         }
     }
     __syncthreads();
@@ -309,10 +357,10 @@ __device__ __forceinline__ void bin_camera(const DevBatch& b, const float* __res
     if (threadIdx.x == 0 && s_flags) atomicOr(b.flags + e, s_flags);
 }
 
-template <int T>
+template <int T, bool kSieve>
 __global__ void __launch_bounds__(kBT, 4) bin_kernel(DevBatch b, const float* __restrict__ pose, TileScratch ts,
                                                   const TileItem* __restrict__ cams, int nlim) {
-    bin_camera<T>(b, pose, ts, load_item(cams + blockIdx.x), nlim);
+    bin_camera<T, kSieve>(b, pose, ts, load_item(cams + blockIdx.x), nlim);
 }
 
 // The job of work-list position k: the last job whose first position
@@ -342,7 +390,7 @@ __global__ void __launch_bounds__(kBT, 4) bin_list_kernel(const DevBatch* __rest
     for (int k = threadIdx.x; k < (int)(sizeof(DevBatch) / 4); k += kBT) dst[k] = src[k];
     __syncthreads();
     const TileScratch ts = jobs[jb].ts;
-    bin_camera<T>(sd, sd.pose[(tag >> 24) & 1], ts, ci, nlim);
+    bin_camera<T, false>(sd, sd.pose[(tag >> 24) & 1], ts, ci, nlim);
 }
 
 // Row set-up of a small record for the dealt raster below: the biased edge
@@ -657,9 +705,10 @@ size_t tiled_record_bytes() { return sizeof(TriRec); }
 
 template <int T>
 static cudaError_t launch_tiled_t(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
-                                  const TileItem* cams, const TileItem* items, int nitems, int nlim,
+                                  const TileItem* cams, const TileItem* items, int nitems, int nlim, bool sieve,
                                   cudaStream_t stream) {
-    bin_kernel<T><<<b.C, kBT, 0, stream>>>(b, pose, ts, cams, nlim);
+    if (sieve) bin_kernel<T, true><<<b.C, kBT, 0, stream>>>(b, pose, ts, cams, nlim);
+    else bin_kernel<T, false><<<b.C, kBT, 0, stream>>>(b, pose, ts, cams, nlim);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || nitems == 0) return err;
     tile_kernel<T><<<nitems, TileGeom<T>::TW * 32, 0, stream>>>(b, ts, fr, items);
@@ -677,14 +726,14 @@ cudaError_t launch_render_tiled_list(const DevBatch* descs, const TiledJob* jobs
 }
 
 cudaError_t launch_render_tiled(const DevBatch& b, const float* pose, const vuda_frame& fr, const TileScratch& ts,
-                                const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim,
+                                const TileItem* cams, const TileItem* items, int nitems, int tile, int nlim, bool sieve,
                                 cudaStream_t stream) {
     if (b.C == 0) return cudaSuccess;
     if (nlim < 1 || nlim > kMaxBinLimit) return cudaErrorInvalidValue;
     switch (tile) {
-        case 8: return launch_tiled_t<8>(b, pose, fr, ts, cams, items, nitems, nlim, stream);
-        case 16: return launch_tiled_t<16>(b, pose, fr, ts, cams, items, nitems, nlim, stream);
-        case 32: return launch_tiled_t<32>(b, pose, fr, ts, cams, items, nitems, nlim, stream);
+        case 8: return launch_tiled_t<8>(b, pose, fr, ts, cams, items, nitems, nlim, sieve, stream);
+        case 16: return launch_tiled_t<16>(b, pose, fr, ts, cams, items, nitems, nlim, sieve, stream);
+        case 32: return launch_tiled_t<32>(b, pose, fr, ts, cams, items, nitems, nlim, sieve, stream);
         default: return cudaErrorInvalidValue;
     }
 }
