@@ -457,7 +457,9 @@ def rollout_bench(V, S, E: int, steps: int, warmup: int, settle: int) -> dict:
                        "luminance (512 features) -> 3 forces per body" % (E, h), "steps": steps, "warmup": warmup}
     for hidden in (256, 4096):
         res = {}
-        for mode in ("serialized", "streams", "green"):
+        # green: the half split; green_88 / green_96: the sim partition one
+        # and two 8-SM steps larger (the sim of both groups sets the step)
+        for mode in ("serialized", "streams", "green", "green_88", "green_96"):
             envs = [V.Env(sc) for sc in scenes]
             rings = [[e.alloc_frame(triid=False), e.alloc_frame(triid=False)] for e in envs]
             forces = [torch.zeros((3, e.B), dtype=torch.float32, device="cuda") for e in envs]
@@ -472,8 +474,8 @@ def rollout_bench(V, S, E: int, steps: int, warmup: int, settle: int) -> dict:
 
             if mode == "streams":
                 envs[0].coschedule(V.COSCHED_STREAMS)
-            elif mode == "green":
-                envs[0].coschedule(V.COSCHED_GREEN)
+            elif mode.startswith("green"):
+                envs[0].coschedule(V.COSCHED_GREEN, int(mode[6:]) if mode != "green" else 0)
             cur = torch.cuda.current_stream()
             V.rollout_run(envs[0], envs[1], warmup, rings[0], rings[1], forces[0], forces[1], policy, stream=cur)
             torch.cuda.synchronize()
@@ -482,9 +484,11 @@ def rollout_bench(V, S, E: int, steps: int, warmup: int, settle: int) -> dict:
             torch.cuda.synchronize()
             wall = time.perf_counter() - t
             res[mode] = {"value": E * steps / wall, "ms_per_step": 1000.0 * wall / steps}
+            if mode.startswith("green"):
+                res[mode]["sim_sms"] = envs[0].cosched["sim_sms"]
             for e in envs:
                 e.close()
-        for mode in ("streams", "green"):
+        for mode in ("streams", "green", "green_88", "green_96"):
             res[mode]["speedup_vs_serialized"] = res[mode]["value"] / res["serialized"]["value"]
         out["hidden_%d" % hidden] = res
     out["timing"] = ("wall clock around vuda_rollout_run (host callbacks replay the policy's CUDA graph), after %d "
