@@ -856,3 +856,48 @@ def test_full_size_physics_options_settled(V, orc, option):
     picks = CFG2_SAMPLE + (int(np.argmax(cc)),)
     _sampled_physics(orc, sc, env.get_state(), 4, picks, start=settled)
     env.close()
+
+
+def _fine_hull(n, seed):
+    """Convex hull of n random points on the unit sphere (2 n - 4 triangles)."""
+    rng = np.random.default_rng(seed)
+    P = rng.normal(size=(n, 3))
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    return S.hull_from_points(P)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_render_fine_meshes_sieved(V, orc, path):
+    """Batches with more triangles per environment than pixels per camera
+    take the sieved set-up on the tiled path: hulls of 400 and 900 triangles
+    crowding the eye of a 32 x 24 camera (four of them cut by the near
+    plane), and one body whose 2,792
+    triangles (a 700-vertex hull listed twice: equal depths, the lower id
+    wins) fill two sieve windows of one chunk.  Frames equal the oracle's on
+    both paths."""
+    m1, m2 = _fine_hull(202, 1), _fine_hull(452, 2)
+    eye, tgt = np.array([0.0, -2.5, 1.5]), np.array([0.0, 0.0, 0.4])
+    f = (tgt - eye) / np.linalg.norm(tgt - eye)
+    r = np.cross(f, [0.0, 0.0, 1.0])
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    rng = np.random.default_rng(7)
+    bodies = []
+    for i in range(10):
+        d = rng.uniform(-0.03, 0.03) if i < 4 else rng.uniform(0.1, 0.6)   # the first four straddle the eye
+        p = eye + f * d + r * rng.uniform(-0.1, 0.1) + u * rng.uniform(-0.08, 0.08)
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        bodies.append(dict(type="hull", mesh=m1 if i % 2 else m2, r=float(rng.uniform(0.05, 0.12)), pos=tuple(p),
+                           quat=tuple(q)))
+    crowd = S.custom(bodies, res=32, envs=2)
+    crowd.cam_h[:] = 24
+    Vd, Td = _fine_hull(700, 3)
+    twice = (Vd, np.concatenate([Td, Td]))   # every triangle twice
+    dense = S.custom([dict(type="hull", mesh=twice, r=0.4, pos=(0.0, 0.0, 0.5))], res=32)
+    assert len(twice[1]) == 2792
+    for sc in (crowd, dense):
+        P = int(sc.cam_pix_off()[-1])
+        assert (np.diff(sc.mesh_tri_off)[sc.mesh_id].sum() / sc.num_envs) > P / sc.cam_off[-1]   # sieved
+        tid = _render_cmp(V, orc, sc, path=path)
+        assert ((tid != 0xFFFFFFFF) & (tid >= 2)).any()
