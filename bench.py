@@ -5,8 +5,9 @@ the other) versus serialized (sim then render on one stream, full GPU).
 
 Workload: 1024 environments x 32 bodies (half spheres, half boxes), 8
 substeps of dt = 1/240 s, one 128 x 128 RGB-D camera each (seeded synthetic
-scene; the paper's ManiSkill scenes are not available).  Prints one JSON
-line (rank 0).
+scene; the paper's ManiSkill scenes are not available), timed after 120
+settling steps, every timed run of every mode from that same state.
+Prints one JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vuda|reference]
 
